@@ -1,0 +1,302 @@
+"""Throughput benchmark of the transmission hot path.
+
+Workload (one GPU): the synthetic AB side-contact junction with N_G = 512
+plane waves and 320 slices, 128 energies x 32 k_par points (4096 (E, k_par)
+points).  One step = one k_par point with all its 128 energies: the slice
+Hamiltonians, their eigenmodes and interface overlaps for that k_par, then
+the left-to-right star-product sweep over all 321 interfaces for the 128
+points, and T = Tr(t^H t).  Metric: (E, k_par)-points/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference   # the CPU oracle on the host cores
+
+Under torchrun each rank takes its own k_par points (weak scaling, no data
+exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synthetic import junction, minimal_cell  # noqa: E402
+
+METRIC = "(E,k∥)-points/s at N_G=512, 320 slices: mixed-precision vs FP64, at 1e-8 rel T"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload(name):
+    if name == "junction512":
+        return junction(ng=512, n_slices=320, n_e=128, n_k=32), 128, 32
+    if name == "junction401":
+        return junction(ng=0, ecut=29.34, n_slices=240, n_e=128, n_k=32), 128, 32
+    if name == "minimal":
+        inst = minimal_cell(energies=np.linspace(0.3, 6.0, 128),
+                            kpar=np.zeros((128, 2)))
+        return inst, 128, 1
+    raise ValueError(name)
+
+
+def sweep_flops_per_point(n, nopen_left):
+    """Algorithmic flops of one interface step of the sweep for one point:
+    R [Q | P] (2 n^3 complex multiply-adds), LU of W (n^3 / 3), forward and
+    back substitution on n + n_open right-hand sides (n^2 (n + n_open));
+    8 real flops per complex multiply-add."""
+    return 8.0 * (2.0 * n ** 3 + n ** 3 / 3.0 + n * n * (n + nopen_left))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, device_index=0):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_oracle_rate(inst, n_e, sample_ifaces=24, sample_slices=24):
+    """Points/s of the CPU oracle, timed on a bounded sample of one point:
+    `sample_slices` slice eigendecompositions (amortised over the n_e energies
+    of a k_par, as in the workload) and `sample_ifaces` interface S-matrices
+    with their star products, scaled to all N+2 slices and N+1 interfaces."""
+    from oracle import pw_oracle as O
+    m = O.Model(inst)
+    k = inst.kpar[0]
+    E = float(inst.energies[min(n_e // 2, len(inst.energies) - 1)])
+    tabs = m.all_tables()
+    t0 = time.perf_counter()
+    modes = [O.slice_modes(O.hamiltonian(m.mn, m.G, k, tabs[q], m.half))
+             for q in range(sample_slices + 1)]
+    t_eig = (time.perf_counter() - t0) / (sample_slices + 1)
+    S = O.identity_s(m.n)
+    t0 = time.perf_counter()
+    for p in range(sample_ifaces):
+        S = O.star(S, m.interface_s(modes, E, p))
+    t_if = (time.perf_counter() - t0) / sample_ifaces
+    per_point = t_if * (m.N + 1) + t_eig * (m.N + 2) / n_e
+    return 1.0 / per_point, {
+        "sample": f"1 point: {sample_slices + 1} slice eigendecompositions and {sample_ifaces} "
+                  f"interface S + star products of N_G={m.n}, scaled to {m.N + 2} slices "
+                  f"(amortised over {n_e} energies) and {m.N + 1} interfaces",
+        "seconds_per_point": per_point}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step is the bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst, n_e, n_k = workload(args.config)
+    cores = os.cpu_count()
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, info = cpu_oracle_rate(inst, n_e, sample_ifaces=8, sample_slices=8)
+        if i >= args.warmup:
+            rates.append(r)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.config},
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--config", default="junction512",
+                    choices=["junction512", "junction401", "minimal"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as g
+    g.build()
+    import paper_1504_01462_gb300 as pw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    inst, n_e, n_k = workload(args.config)
+    prec = pw.MIXED_FP32 if args.precision == "mixed" else pw.FP64
+    stream = torch.cuda.current_stream()
+    ctx = pw.Context.from_instance(inst, precision=prec, stream=stream.cuda_stream)
+    n, N = ctx.ng, ctx.n_slices
+    npts = len(inst.energies)
+
+    def step_points(s):
+        kk = (rank + s * world) % n_k
+        idx = np.arange(kk * n_e, (kk + 1) * n_e)
+        return inst.energies[idx], inst.kpar[idx]
+
+    T = torch.empty(n_e, dtype=torch.float64, device="cuda")
+    nop = torch.empty((n_e, 2), dtype=torch.int32, device="cuda")
+    for s in range(args.warmup):
+        E, k = step_points(s)
+        ctx.transmission(E, k, T, None, nop)
+    barrier()
+
+    # ---- device-timed region: K steps, CUDA events on the library's stream
+    ctx.set_profiling(True)
+    ctx.get_profile(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    flops_launch = []
+    for s in range(args.steps):
+        E, k = step_points(args.warmup + s)
+        ctx.transmission(E, k, T, None, nop)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.get_profile(reset=True)
+    ctx.set_profiling(False)
+    nopen_last = nop.cpu().numpy()
+    flops_per_launch = sum(sweep_flops_per_point(n, int(nl)) for nl in nopen_last[:, 0])
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    total_points = args.steps * n_e * world
+    value = total_points / (ms_max / 1e3)
+
+    # ---- end to end through the public API: host inputs, host T, wall clock
+    T_host = torch.empty(n_e, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        E, k = step_points(args.warmup + s)
+        ctx.transmission(E, k, T, None, None)
+        T_host.copy_(T, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = total_points / float(e2e_t.item())
+
+    if rank == 0:
+        sweep_avg_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
+        achieved = flops_per_launch / (sweep_avg_ms / 1e3) / 1e12
+        sm_mhz_peak = 2070.0
+        if prec == pw.MIXED_FP32:
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
+            peak_src = "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz"
+        else:
+            peak = 1.25
+            peak_src = "FP64 nominal 1.25 TFLOP/s (recipe table)"
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if prec == pw.MIXED_FP32 else "c128", "data": "synthetic",
+            "config": {"workload": f"{args.config}: AB junction, N_G={n}, {N} slices, "
+                                   f"{n_e} E x {n_k} k_par ({npts} points); step = 1 k_par x {n_e} E",
+                       "precision": args.precision, "global_batch": n_e * world,
+                       "l2": "inputs larger than L2 (overlaps of one k_par: "
+                             f"{(N + 1) * n * n * 16 / 1e9:.2f} GB)",
+                       "parallelism": f"replicas over k_par x{world}"},
+            "roofline": {"bound": "alu", "kernel": f"k_sweep<{'float' if prec else 'double'}>",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "avg_launch_ms": sweep_avg_ms},
+            "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
+                          "overlaps": prof["overlap_ms"]},
+            "clocks": clk,
+            "gpu_launches": int(args.steps * (N + 1 + 3)),
+            "e2e": {"value": e2e_value, "unit": "points/s",
+                    "h2d_bytes_per_step": n_e * 32,
+                    "d2h_bytes_per_step": n_e * (8 + 4) + 2 * n * 8 + (N + 2) * 4},
+        }
+        if not args.no_cpu_baseline:
+            r, info = cpu_oracle_rate(inst, n_e)
+            line["cpu_baseline"] = {"value": r, "unit": "points/s", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": info["sample"]}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

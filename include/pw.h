@@ -1,0 +1,177 @@
+/*
+ * pw.h -- C ABI of the GB300 plane-wave multiple-scattering transport library.
+ *
+ * The library computes, for a slice model of a junction between two
+ * z-invariant electrodes, the transmission T(E, k_par) = Tr(t^H t) of Li, Chu,
+ * Zhang & Cheng, "Electron transport in graphene/graphene side-contact junction
+ * by plane-wave multiple scattering method" (PRB 2015):
+ *   - Sec. II A / Eq. loc: 2D plane-wave basis {G_perp}, slice Hamiltonians
+ *     H_p(G,G') = |k+G|^2 delta + V^p(G-G') and their eigenmodes;
+ *   - App. A Eqs. transfer and scatter: the interface scattering matrix S(p,p+1);
+ *   - Eq. recurrence: the star product (layer doubling) of scattering matrices;
+ *   - App. C with z-invariant electrodes (slices 0 and N+1): t = S11(0,N+1)
+ *     on open channels, flux-normalised, and T = Tr(t^H t).
+ * Units: Rydberg atomic units (hbar^2/2m = 1, bohr, Ry).
+ *
+ * Conventions for every entry point
+ *   - All calls return a pw_status.  The first failure inside a context is
+ *     latched: later calls on that context return it until pw_destroy.
+ *   - Arguments named *_dev are device pointers (CUDA global memory of the
+ *     context's device), written asynchronously on the context's stream; all
+ *     other pointers are host pointers read before the call returns.
+ *   - The caller owns every input and output buffer; the context owns its
+ *     workspaces and frees them in pw_destroy.  No C++ exception crosses the ABI.
+ *   - Complex numbers are interleaved (re, im) doubles, i.e. C99 double _Complex.
+ *   - Matrices are column-major n x n blocks (element (i,j) at i + j*n).
+ *   - Channel order: the eigenmodes of every slice and electrode are sorted by
+ *     ascending eigenvalue E_n; the open channels of an electrode at energy E
+ *     are therefore its first n_open modes.
+ */
+#ifndef PW_H
+#define PW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pw_ctx pw_ctx;
+
+typedef enum {
+  PW_OK = 0,
+  PW_EINVAL = 1,      /* bad argument or descriptor */
+  PW_ENOMEM = 2,      /* device allocation failed */
+  PW_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  PW_ESINGULAR = 4,   /* zero pivot in an LU factorisation */
+  PW_ETHRESH = 5,     /* |E - E_n| < 1e-10 Ry for an electrode channel (k_n = 0) */
+  PW_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  PW_ENOTCONV = 7     /* the slice eigensolver did not converge */
+} pw_status;
+
+typedef struct { double re, im; } pw_c128;
+
+/* arithmetic of the star-product sweep (the eigensolver is always FP64) */
+enum { PW_FP64 = 0, PW_MIXED_FP32 = 1 };
+
+/*
+ * Problem description (Sec. II A).  The transverse cell is spanned by a1, a2
+ * (bohr); the basis is every G = m b1 + n b2 with |G|^2 <= ecut (whole shells)
+ * or, if ng_exact > 0, the first ng_exact G ordered by (|G|^2, m, n), with
+ * |G|^2 grouped into shells at 1e-8 Ry.  The device region is cut into
+ * n_slices slices by the increasing z_edges[0..n_slices] (bohr).
+ *
+ * Potential of slice p (Eq. loc, the slice average of V_loc): either
+ *   - n_wells Gaussian wells V(r) = -v0 exp(-|r - R|^2 / (2 sigma^2)), centres
+ *     well_xyz[3*i + {0,1,2}] = (x, y, z) with z along transport, averaged over
+ *     the slice thickness in closed form, or
+ *   - explicit Fourier tables slice_vg (non-NULL overrides the wells): for each
+ *     slice, (2*Dm+1) x (2*Dn+1) values V^p(dm b1 + dn b2) stored row-major
+ *     [p][dm + Dm][dn + Dn], with (Dm, Dn) = vg_half.  Tables must satisfy
+ *     V(-dG) = conj(V(dG)) (a real potential) and cover every G - G'.
+ * Electrodes (slices 0 and N+1, App. C with z-invariant leads): either the
+ * z-average over lead_period of lead_n_wells wells at transverse positions
+ * lead_well_xy (0 wells = the V = 0 electrode), or an explicit table lead_vg
+ * (same layout, one table).
+ */
+typedef struct {
+  double a1[2], a2[2];
+  double ecut;
+  int ng_exact;
+  int n_slices;
+  const double *z_edges;
+  int n_wells;
+  const double *well_xyz;
+  const double *well_v0;
+  const double *well_sigma;
+  int lead_n_wells[2];
+  const double *lead_well_xy[2];
+  const double *lead_well_v0[2];
+  const double *lead_well_sigma[2];
+  double lead_period[2];
+  int vg_half[2];
+  const pw_c128 *slice_vg;
+  const pw_c128 *lead_vg[2];
+  int precision;               /* PW_FP64 or PW_MIXED_FP32 */
+} pw_setup_desc;
+
+/* Builds the basis (Sec. II A) and uploads the slice geometry; the Fourier
+ * tables V^p(dG) are evaluated on the device.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream) on the current device.  On success *out owns
+ * all device state of the problem. */
+pw_status pw_setup(const pw_setup_desc *desc, void *cuda_stream, pw_ctx **out);
+
+/* Frees every workspace of the context (synchronises its stream). */
+void pw_destroy(pw_ctx *ctx);
+
+/* Static text of a status code. */
+const char *pw_status_str(pw_status s);
+
+/* Latched status of the context (PW_OK if no call has failed). */
+pw_status pw_get_error(const pw_ctx *ctx);
+
+/* Basis size N_G and slice count N of the context (0 for NULL). */
+int pw_ng(const pw_ctx *ctx);
+int pw_n_slices(const pw_ctx *ctx);
+
+/* Copies the basis as integer pairs (m, n) into mn_host[2*N_G] (host). */
+pw_status pw_get_gvectors(const pw_ctx *ctx, int *mn_host);
+
+/* Fourier tables of slices 0..N+1 (left electrode, slices 1..N, right
+ * electrode) as (N+2) x (2*Dm+1) x (2*Dn+1) complex values, row-major, into
+ * vg_dev; (Dm, Dn) = twice the largest |m|, |n| of the basis, returned in
+ * half_host[2].  Sec. II A (slice-averaged V_loc). */
+pw_status pw_potential_tables(pw_ctx *ctx, pw_c128 *vg_dev, int *half_host);
+
+/* Eigenmodes of every slice 0..N+1 at transverse wavevector kpar[2]
+ * (Eq. loc / App. A Eq. A8): En_dev[(N+2)*N_G] ascending per slice and
+ * U_dev[(N+2)*N_G*N_G], column j of slice q's block = eigenvector of E_n[j].
+ * Either output may be NULL. */
+pw_status pw_slice_modes(pw_ctx *ctx, const double *kpar, double *En_dev, pw_c128 *U_dev);
+
+/* Interface overlaps O_p = U_p^H U_{p+1}, p = 0..N, i.e. the sums
+ * sum_s (M^{p+1}_{js})^* M^p_{ns} of App. A Eq. transfer, at kpar[2]:
+ * O_dev[(N+1)*N_G*N_G]. */
+pw_status pw_overlaps(pw_ctx *ctx, const double *kpar, pw_c128 *O_dev);
+
+/* Interface scattering matrix S(iface, iface+1), iface in 0..N, for npts
+ * points (E[i], kpar[2i..2i+1]) (App. A Eqs. transfer and scatter):
+ * S_dev[npts * 4 * N_G * N_G], per point the blocks S11, S12, S21, S22. */
+pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double *kpar,
+                           int iface, pw_c128 *S_dev);
+
+/* Star product S(m,k) = S(m,n) * S(n,k) of Eq. recurrence for npts pairs of
+ * caller-supplied scattering matrices (same layout as pw_slice_smatrix);
+ * Sab_dev may not alias the inputs. */
+pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
+                     pw_c128 *Sab_dev);
+
+/* The forward hot path: for each point (E[i], kpar[2i..2i+1]) the junction's
+ * S11(0,N+1) by a left-to-right sweep of star products over all N+1
+ * interfaces, then t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels and
+ * T = Tr(t^H t) (App. C, Sec. II B).
+ *   T_dev[npts]                      transmission (required)
+ *   t_dev[npts * N_G * N_G] or NULL  t, top-left n_open^R x n_open^L block of
+ *                                    each N_G x N_G column-major slot
+ *   nopen_dev[2 * npts] or NULL      (n_open^L, n_open^R) per point
+ *   err_dev[npts] or NULL            estimated relative error of T (0 for FP64)
+ * A point at an electrode threshold gets T = NaN and the call returns
+ * PW_ETHRESH after finishing the others. */
+pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar,
+                          double *T_dev, pw_c128 *t_dev, int *nopen_dev, double *err_dev);
+
+/* Timing of the library's own launches (for benchmarks and roofline
+ * accounting).  While enabled, CUDA events on the context's stream bracket
+ * every stage: the slice-mode stage (Hamiltonian assembly and eigensolver), the
+ * overlap GEMMs, and each batch of sweep launches.  pw_get_profile
+ * synchronises the stream and writes out[6] = {sweep ms, sweep launches,
+ * mode-stage ms, mode stages, overlap ms, overlap stages}; reset != 0 clears
+ * the records. */
+pw_status pw_set_profiling(pw_ctx *ctx, int enable);
+pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PW_H */

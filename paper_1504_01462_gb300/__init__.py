@@ -1,0 +1,271 @@
+"""GB300 plane-wave multiple-scattering transport: Python binding of libpw.
+
+A thin ctypes layer over the C ABI in include/pw.h.  It only marshals
+arguments: every step of the computation runs in the CUDA kernels of
+libpw.so.  Device buffers are passed as objects with a ``data_ptr()`` method
+(e.g. torch CUDA tensors) or as raw integer addresses; host arrays as NumPy
+arrays.  If the compiled library is missing, importing this package raises:
+there is no CPU fallback.
+
+    ctx = Context.from_instance(inst, precision=FP64)
+    T = torch.empty(npts, dtype=torch.float64, device="cuda")
+    ctx.transmission(E, kpar, T)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpw.so")
+
+FP64 = 0
+MIXED_FP32 = 1
+
+STATUS = {0: "PW_OK", 1: "PW_EINVAL", 2: "PW_ENOMEM", 3: "PW_ECUDA", 4: "PW_ESINGULAR",
+          5: "PW_ETHRESH", 6: "PW_ETIMEOUT", 7: "PW_ENOTCONV"}
+PW_ETHRESH = 5
+
+EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "pw_n_slices",
+           "pw_get_gvectors", "pw_potential_tables", "pw_slice_modes", "pw_overlaps",
+           "pw_slice_smatrix", "pw_compose", "pw_transmission", "pw_set_profiling",
+           "pw_get_profile"]
+
+
+class PwError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_lib.pw_status_str(code).decode()})")
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+class SetupDesc(ctypes.Structure):
+    _fields_ = [
+        ("a1", ctypes.c_double * 2), ("a2", ctypes.c_double * 2),
+        ("ecut", ctypes.c_double), ("ng_exact", ctypes.c_int),
+        ("n_slices", ctypes.c_int), ("z_edges", _dp),
+        ("n_wells", ctypes.c_int), ("well_xyz", _dp), ("well_v0", _dp), ("well_sigma", _dp),
+        ("lead_n_wells", ctypes.c_int * 2), ("lead_well_xy", _dp * 2),
+        ("lead_well_v0", _dp * 2), ("lead_well_sigma", _dp * 2),
+        ("lead_period", ctypes.c_double * 2),
+        ("vg_half", ctypes.c_int * 2),
+        ("slice_vg", _vp), ("lead_vg", _vp * 2),
+        ("precision", ctypes.c_int),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpw.so is not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.pw_setup.argtypes = [ctypes.POINTER(SetupDesc), _vp, ctypes.POINTER(_vp)]
+    lib.pw_destroy.argtypes = [_vp]
+    lib.pw_destroy.restype = None
+    lib.pw_status_str.argtypes = [ctypes.c_int]
+    lib.pw_status_str.restype = ctypes.c_char_p
+    lib.pw_get_error.argtypes = [_vp]
+    lib.pw_ng.argtypes = [_vp]
+    lib.pw_n_slices.argtypes = [_vp]
+    lib.pw_get_gvectors.argtypes = [_vp, _ip]
+    lib.pw_potential_tables.argtypes = [_vp, _vp, _ip]
+    lib.pw_slice_modes.argtypes = [_vp, _dp, _vp, _vp]
+    lib.pw_overlaps.argtypes = [_vp, _dp, _vp]
+    lib.pw_slice_smatrix.argtypes = [_vp, ctypes.c_int, _dp, _dp, ctypes.c_int, _vp]
+    lib.pw_compose.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+    lib.pw_transmission.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp, _vp, _vp, _vp]
+    lib.pw_set_profiling.argtypes = [_vp, ctypes.c_int]
+    lib.pw_get_profile.argtypes = [_vp, _dp, ctypes.c_int]
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    """The loaded ctypes library (for symbol checks and direct calls)."""
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _c128(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _as_dp(a):
+    return a.ctypes.data_as(_dp) if a is not None and a.size else None
+
+
+class Context:
+    """An owned pw_ctx: one junction problem on the current CUDA device."""
+
+    def __init__(self, *, a1, a2, z_edges, ecut=0.0, ng_exact=0, wells_xyz=None, v0=None,
+                 sigma=None, leads=((None, None, None, 1.0), (None, None, None, 1.0)),
+                 slice_vg=None, lead_vg=(None, None), vg_half=(0, 0), precision=FP64,
+                 stream=None):
+        keep = []
+        d = SetupDesc()
+        d.a1[:] = [float(v) for v in a1]
+        d.a2[:] = [float(v) for v in a2]
+        d.ecut = float(ecut)
+        d.ng_exact = int(ng_exact)
+        z = _f64(z_edges)
+        keep.append(z)
+        d.n_slices = len(z) - 1
+        d.z_edges = _as_dp(z)
+        if wells_xyz is not None and len(wells_xyz):
+            w, v, s = _f64(wells_xyz).reshape(-1, 3), _f64(v0), _f64(sigma)
+            keep += [w, v, s]
+            d.n_wells = len(w)
+            d.well_xyz, d.well_v0, d.well_sigma = _as_dp(w), _as_dp(v), _as_dp(s)
+        for side, (xy, lv0, ls, period) in enumerate(leads):
+            d.lead_period[side] = float(period)
+            if xy is not None and len(xy):
+                xy, lv0, ls = _f64(xy).reshape(-1, 2), _f64(lv0), _f64(ls)
+                keep += [xy, lv0, ls]
+                d.lead_n_wells[side] = len(xy)
+                d.lead_well_xy[side] = _as_dp(xy)
+                d.lead_well_v0[side] = _as_dp(lv0)
+                d.lead_well_sigma[side] = _as_dp(ls)
+        d.vg_half[:] = [int(vg_half[0]), int(vg_half[1])]
+        if slice_vg is not None:
+            sv = _c128(slice_vg)
+            keep.append(sv)
+            d.slice_vg = sv.ctypes.data
+        for side in (0, 1):
+            if lead_vg[side] is not None:
+                lv = _c128(lead_vg[side])
+                keep.append(lv)
+                d.lead_vg[side] = lv.ctypes.data
+        d.precision = int(precision)
+        h = _vp()
+        st = _lib.pw_setup(ctypes.byref(d), stream, ctypes.byref(h))
+        if st != 0:
+            raise PwError(st, "pw_setup")
+        self._h = h
+        self.precision = int(precision)
+
+    @classmethod
+    def from_instance(cls, inst, precision=FP64, stream=None):
+        """Marshal a problem description object (attributes as in
+        synthetic.Instance) into pw_setup."""
+        leads = []
+        for L in (inst.lead_left, inst.lead_right):
+            leads.append((L.wells_xy, L.v0, L.sigma, L.period))
+        lead_vg = inst.lead_vg if inst.lead_vg is not None else (None, None)
+        return cls(a1=inst.a1, a2=inst.a2, z_edges=inst.z_edges, ecut=inst.ecut,
+                   ng_exact=inst.ng_exact, wells_xyz=inst.wells_xyz, v0=inst.v0,
+                   sigma=inst.sigma, leads=leads, slice_vg=inst.slice_vg, lead_vg=lead_vg,
+                   vg_half=inst.vg_half, precision=precision, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def ng(self) -> int:
+        return _lib.pw_ng(self._h)
+
+    @property
+    def n_slices(self) -> int:
+        return _lib.pw_n_slices(self._h)
+
+    def gvectors(self) -> np.ndarray:
+        out = np.zeros(2 * self.ng, dtype=np.int32)
+        self._check(_lib.pw_get_gvectors(self._h, out.ctypes.data_as(_ip)), "pw_get_gvectors")
+        return out.reshape(-1, 2)
+
+    def table_half(self):
+        half = np.zeros(2, dtype=np.int32)
+        self._check(_lib.pw_potential_tables(self._h, None, half.ctypes.data_as(_ip)),
+                    "pw_potential_tables")
+        return int(half[0]), int(half[1])
+
+    def potential_tables(self, out):
+        self._check(_lib.pw_potential_tables(self._h, _ptr(out), None), "pw_potential_tables")
+
+    def slice_modes(self, kpar, En_out=None, U_out=None):
+        k = _f64(kpar)
+        self._check(_lib.pw_slice_modes(self._h, _as_dp(k), _ptr(En_out), _ptr(U_out)),
+                    "pw_slice_modes")
+
+    def overlaps(self, kpar, O_out):
+        k = _f64(kpar)
+        self._check(_lib.pw_overlaps(self._h, _as_dp(k), _ptr(O_out)), "pw_overlaps")
+
+    def slice_smatrix(self, E, kpar, iface, S_out):
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        self._check(_lib.pw_slice_smatrix(self._h, len(E), _as_dp(E), _as_dp(k), int(iface),
+                                          _ptr(S_out)), "pw_slice_smatrix")
+
+    def compose(self, npts, Sa, Sb, Sab):
+        self._check(_lib.pw_compose(self._h, int(npts), _ptr(Sa), _ptr(Sb), _ptr(Sab)),
+                    "pw_compose")
+
+    def transmission(self, E, kpar, T_out, t_out=None, nopen_out=None, err_out=None,
+                     allow_threshold=False):
+        """T(E, k_par) into T_out (device, float64[npts]).  Returns the status
+        code (PW_OK, or PW_ETHRESH when allow_threshold is set)."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        st = _lib.pw_transmission(self._h, len(E), _as_dp(E), _as_dp(k), _ptr(T_out),
+                                  _ptr(t_out), _ptr(nopen_out), _ptr(err_out))
+        if st == PW_ETHRESH and allow_threshold:
+            return st
+        self._check(st, "pw_transmission")
+        return st
+
+    def set_profiling(self, on=True):
+        self._check(_lib.pw_set_profiling(self._h, int(bool(on))), "pw_set_profiling")
+
+    def get_profile(self, reset=True):
+        """{'sweep_ms', 'sweep_launches', 'modes_ms', 'modes_stages', 'overlap_ms',
+        'overlap_stages'} accumulated since the last reset."""
+        out = np.zeros(6)
+        self._check(_lib.pw_get_profile(self._h, _as_dp(out), int(bool(reset))), "pw_get_profile")
+        keys = ["sweep_ms", "sweep_launches", "modes_ms", "modes_stages", "overlap_ms",
+                "overlap_stages"]
+        return dict(zip(keys, out.tolist()))
+
+    @staticmethod
+    def _check(st, where):
+        if st != 0:
+            raise PwError(st, where)
+
+
+__all__ = ["Context", "PwError", "FP64", "MIXED_FP32", "EXPORTS", "LIB_PATH", "lib"]

@@ -1,0 +1,600 @@
+// Host side of the C ABI declared in include/pw.h: problem setup (basis,
+// slice geometry, device-resident Fourier tables), the per-k_par eigenmode
+// cache, batching of (E, k_par) points and the launch sequence of the sweep.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/pw.h"
+#include "pw_internal.h"
+
+using pw::PointDesc;
+
+
+namespace {
+
+constexpr double kShellQuantum = 1e-8;   // Ry: |G|^2 closer than this is one shell
+constexpr double kThreshold = 1e-10;     // Ry: electrode channel at threshold
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pw_status err = PW_OK;
+  int precision = PW_FP64;
+  int n = 0, N = 0, nq = 0;        // basis size, slices, slices incl. electrodes
+  int Dm = 0, Dn = 0, tsz = 0;     // Fourier-table index ranges
+  double b1[2], b2[2], area = 0.0;
+  std::vector<int> mn;             // 2n
+  std::vector<double> G;           // 2n
+  std::vector<double> dz;          // N+2
+  int num_sms = 152;
+  // device state
+  int *d_mn = nullptr;
+  double *d_G = nullptr, *d_dz = nullptr, *d_z = nullptr;
+  zc *d_tab = nullptr;
+  // eigenmode cache of one k_par
+  bool kvalid = false;
+  double kcur[2] = {0, 0};
+  zc *d_HU = nullptr, *d_V = nullptr, *d_O = nullptr;
+  double *d_En = nullptr;
+  int *d_eigstat = nullptr;
+  std::vector<double> EL, ER;      // electrode eigenvalues at kcur (host)
+  // per-point workspaces
+  DevBuf R, M, piv, pts, status, work;
+  // launch timing (pw_set_profiling)
+  struct Rec { cudaEvent_t a, b; int kind; int count; };
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+cudaEvent_t take_event(pw_ctx *c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets a stage with events on the context stream when profiling is on.
+struct Stage {
+  pw_ctx *c;
+  cudaEvent_t a = nullptr;
+  int kind, count;
+  Stage(pw_ctx *ctx, int k, int n) : c(ctx), kind(k), count(n) {
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  void done() {
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({a, b, kind, count});
+    a = nullptr;
+  }
+};
+
+pw_status latch(pw_ctx *c, pw_status s) {
+  if (c && c->err == PW_OK && s != PW_OK) c->err = s;
+  return s;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return latch(ctx, e_ == cudaErrorMemoryAllocation ? PW_ENOMEM : PW_ECUDA); \
+  } while (0)
+
+pw_status ensure(pw_ctx *ctx, DevBuf &b, size_t bytes) {
+  if (b.bytes >= bytes) return PW_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return latch(ctx, PW_ENOMEM);
+  }
+  b.bytes = bytes;
+  return PW_OK;
+}
+
+// Sec. II A: {G = m b1 + n b2}, ordered by (shell, m, n).
+void build_basis(const double a1[2], const double a2[2], double ecut, int ng_exact, double b1[2],
+                 double b2[2], std::vector<int> &mn, std::vector<double> &G) {
+  const double det = a1[0] * a2[1] - a1[1] * a2[0];
+  b1[0] = 2.0 * M_PI * a2[1] / det;
+  b1[1] = -2.0 * M_PI * a2[0] / det;
+  b2[0] = -2.0 * M_PI * a1[1] / det;
+  b2[1] = 2.0 * M_PI * a1[0] / det;
+  struct Row { long long key; int m, n; double gx, gy; };
+  auto enumerate = [&](double ec, std::vector<Row> &rows) {
+    rows.clear();
+    const double gmax = sqrt(std::max(ec, 0.0));
+    const int mmax = (int)floor(gmax * hypot(a1[0], a1[1]) / (2 * M_PI)) + 1;
+    const int nmax = (int)floor(gmax * hypot(a2[0], a2[1]) / (2 * M_PI)) + 1;
+    for (int m = -mmax; m <= mmax; ++m)
+      for (int n = -nmax; n <= nmax; ++n) {
+        const double gx = m * b1[0] + n * b2[0], gy = m * b1[1] + n * b2[1];
+        const double g2 = gx * gx + gy * gy;
+        if (g2 <= ec) rows.push_back({llrint(g2 / kShellQuantum), m, n, gx, gy});
+      }
+    std::sort(rows.begin(), rows.end(), [](const Row &x, const Row &y) {
+      if (x.key != y.key) return x.key < y.key;
+      if (x.m != y.m) return x.m < y.m;
+      return x.n < y.n;
+    });
+  };
+  std::vector<Row> rows;
+  size_t take;
+  if (ng_exact > 0) {
+    const double amax = std::max(hypot(a1[0], a1[1]), hypot(a2[0], a2[1]));
+    double ec = (2 * M_PI) * (2 * M_PI) / (amax * amax);
+    for (;;) {
+      enumerate(ec, rows);
+      if (rows.size() >= (size_t)ng_exact + 64) break;
+      ec *= 1.5;
+    }
+    take = ng_exact;
+  } else {
+    enumerate(ecut, rows);
+    take = rows.size();
+  }
+  mn.resize(2 * take);
+  G.resize(2 * take);
+  for (size_t i = 0; i < take; ++i) {
+    mn[2 * i] = rows[i].m;
+    mn[2 * i + 1] = rows[i].n;
+    G[2 * i] = rows[i].gx;
+    G[2 * i + 1] = rows[i].gy;
+  }
+}
+
+template <typename T>
+pw_status upload(pw_ctx *ctx, T **dst, const T *src, size_t count) {
+  if (count == 0) { *dst = nullptr; return PW_OK; }
+  CK(cudaMalloc((void **)dst, count * sizeof(T)));
+  CK(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return PW_OK;
+}
+
+// Eigenmodes and overlaps of every slice at k (cached for the last k).
+pw_status ensure_kset(pw_ctx *ctx, const double *k) {
+  if (ctx->kvalid && ctx->kcur[0] == k[0] && ctx->kcur[1] == k[1]) return PW_OK;
+  ctx->kvalid = false;
+  const int n = ctx->n, nq = ctx->nq;
+  const size_t nn = (size_t)n * n;
+  if (!ctx->d_HU) {
+    CK(cudaMalloc(&ctx->d_HU, nq * nn * sizeof(zc)));
+    CK(cudaMalloc(&ctx->d_V, nq * nn * sizeof(zc)));
+    CK(cudaMalloc(&ctx->d_O, (nq - 1) * nn * sizeof(zc)));
+    CK(cudaMalloc(&ctx->d_En, (size_t)nq * n * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_eigstat, nq * sizeof(int)));
+  }
+  Stage s1(ctx, 1, 1);
+  pw::launch_assemble_h(ctx->d_HU, ctx->d_tab, ctx->d_mn, ctx->d_G, k[0], k[1], n, nq, ctx->Dm,
+                        ctx->Dn, ctx->stream);
+  CK(cudaGetLastError());
+  pw::launch_eig(ctx->d_HU, ctx->d_V, ctx->d_En, ctx->d_eigstat, n, nq, ctx->stream);
+  CK(cudaGetLastError());
+  s1.done();
+  Stage s2(ctx, 2, 1);
+  pw::launch_overlaps(ctx->d_HU, ctx->d_O, n, nq, ctx->stream);
+  CK(cudaGetLastError());
+  s2.done();
+  std::vector<int> st(nq);
+  ctx->EL.resize(n);
+  ctx->ER.resize(n);
+  CK(cudaMemcpyAsync(st.data(), ctx->d_eigstat, nq * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->EL.data(), ctx->d_En, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->ER.data(), ctx->d_En + (size_t)(nq - 1) * n, n * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < nq; ++q)
+    if (st[q] != 0) return latch(ctx, PW_ENOTCONV);
+  ctx->kcur[0] = k[0];
+  ctx->kcur[1] = k[1];
+  ctx->kvalid = true;
+  return PW_OK;
+}
+
+int count_open(const std::vector<double> &En, double E, bool *thresh) {
+  int c = 0;
+  for (double v : En) {
+    if (fabs(E - v) < kThreshold) *thresh = true;
+    if (v < E) ++c;
+  }
+  return c;
+}
+
+// Unique k values in first-appearance order and the points of each.
+void group_by_k(int npts, const double *kpar, std::vector<std::vector<int>> &groups) {
+  groups.clear();
+  std::vector<std::pair<double, double>> keys;
+  for (int i = 0; i < npts; ++i) {
+    const std::pair<double, double> k(kpar[2 * i], kpar[2 * i + 1]);
+    size_t g = 0;
+    for (; g < keys.size(); ++g)
+      if (keys[g] == k) break;
+    if (g == keys.size()) {
+      keys.push_back(k);
+      groups.emplace_back();
+    }
+    groups[g].push_back(i);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pw_status_str(pw_status s) {
+  switch (s) {
+    case PW_OK: return "ok";
+    case PW_EINVAL: return "invalid argument";
+    case PW_ENOMEM: return "device allocation failed";
+    case PW_ECUDA: return "CUDA runtime error";
+    case PW_ESINGULAR: return "zero pivot in LU factorisation";
+    case PW_ETHRESH: return "energy at an electrode channel threshold";
+    case PW_ETIMEOUT: return "bounded device wait timed out";
+    case PW_ENOTCONV: return "eigensolver did not converge";
+  }
+  return "unknown status";
+}
+
+pw_status pw_get_error(const pw_ctx *ctx) { return ctx ? ctx->err : PW_EINVAL; }
+int pw_ng(const pw_ctx *ctx) { return ctx ? ctx->n : 0; }
+int pw_n_slices(const pw_ctx *ctx) { return ctx ? ctx->N : 0; }
+
+pw_status pw_get_gvectors(const pw_ctx *ctx, int *mn_host) {
+  if (!ctx || !mn_host) return PW_EINVAL;
+  memcpy(mn_host, ctx->mn.data(), ctx->mn.size() * sizeof(int));
+  return PW_OK;
+}
+
+pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
+  if (!d || !out) return PW_EINVAL;
+  *out = nullptr;
+  if (d->n_slices < 1 || !d->z_edges) return PW_EINVAL;
+  if (d->precision != PW_FP64 && d->precision != PW_MIXED_FP32) return PW_EINVAL;
+  for (int i = 0; i < d->n_slices; ++i)
+    if (!(d->z_edges[i + 1] > d->z_edges[i])) return PW_EINVAL;
+  if (!d->slice_vg && d->n_wells > 0 && (!d->well_xyz || !d->well_v0 || !d->well_sigma))
+    return PW_EINVAL;
+  for (int s = 0; s < 2; ++s)
+    if (!d->lead_vg[s] && d->lead_n_wells[s] > 0 &&
+        (!d->lead_well_xy[s] || !d->lead_well_v0[s] || !d->lead_well_sigma[s] || !(d->lead_period[s] > 0)))
+      return PW_EINVAL;
+  const double det = d->a1[0] * d->a2[1] - d->a1[1] * d->a2[0];
+  if (!(fabs(det) > 0)) return PW_EINVAL;
+  pw_ctx *ctx = new (std::nothrow) pw_ctx();
+  if (!ctx) return PW_ENOMEM;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->precision = d->precision;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return PW_ECUDA; }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  build_basis(d->a1, d->a2, d->ecut, d->ng_exact, ctx->b1, ctx->b2, ctx->mn, ctx->G);
+  ctx->n = (int)(ctx->mn.size() / 2);
+  if (ctx->n < 1 || ctx->n > 1024) { delete ctx; return PW_EINVAL; }
+  ctx->N = d->n_slices;
+  ctx->nq = ctx->N + 2;
+  ctx->area = fabs(det);
+  int mmax = 0, nmax = 0;
+  for (int i = 0; i < ctx->n; ++i) {
+    mmax = std::max(mmax, abs(ctx->mn[2 * i]));
+    nmax = std::max(nmax, abs(ctx->mn[2 * i + 1]));
+  }
+  ctx->Dm = 2 * mmax;
+  ctx->Dn = 2 * nmax;
+  ctx->tsz = (2 * ctx->Dm + 1) * (2 * ctx->Dn + 1);
+  if (d->slice_vg || d->lead_vg[0] || d->lead_vg[1]) {
+    if (d->vg_half[0] < 0 || d->vg_half[1] < 0) { delete ctx; return PW_EINVAL; }
+  }
+  ctx->dz.assign(ctx->nq, 0.0);
+  for (int p = 1; p <= ctx->N; ++p) ctx->dz[p] = d->z_edges[p] - d->z_edges[p - 1];
+  pw_status st;
+  if ((st = upload(ctx, &ctx->d_mn, ctx->mn.data(), ctx->mn.size())) != PW_OK ||
+      (st = upload(ctx, &ctx->d_G, ctx->G.data(), ctx->G.size())) != PW_OK ||
+      (st = upload(ctx, &ctx->d_dz, ctx->dz.data(), ctx->dz.size())) != PW_OK ||
+      (st = upload(ctx, &ctx->d_z, d->z_edges, (size_t)ctx->N + 1)) != PW_OK) {
+    pw_destroy(ctx);
+    return st;
+  }
+  // Fourier tables: explicit ones are embedded on the host, wells on the device
+  const size_t tab_bytes = (size_t)ctx->nq * ctx->tsz * sizeof(zc);
+  if (cudaMalloc(&ctx->d_tab, tab_bytes) != cudaSuccess) { pw_destroy(ctx); return PW_ENOMEM; }
+  std::vector<zc> host_tab;
+  auto embed = [&](const pw_c128 *src, int q) {
+    const int sm = d->vg_half[0], sn = d->vg_half[1];
+    zc *dst = host_tab.data() + (size_t)q * ctx->tsz;
+    for (int i = -std::min(sm, ctx->Dm); i <= std::min(sm, ctx->Dm); ++i)
+      for (int j = -std::min(sn, ctx->Dn); j <= std::min(sn, ctx->Dn); ++j) {
+        const pw_c128 v = src[(size_t)(i + sm) * (2 * sn + 1) + (j + sn)];
+        dst[(size_t)(i + ctx->Dm) * (2 * ctx->Dn + 1) + (j + ctx->Dn)] = mkc<double>(v.re, v.im);
+      }
+  };
+  const bool any_explicit = d->slice_vg || d->lead_vg[0] || d->lead_vg[1];
+  if (any_explicit) {
+    host_tab.assign((size_t)ctx->nq * ctx->tsz, mkc<double>(0.0, 0.0));
+    if (d->slice_vg) {
+      const size_t stride = (size_t)(2 * d->vg_half[0] + 1) * (2 * d->vg_half[1] + 1);
+      for (int p = 1; p <= ctx->N; ++p) embed(d->slice_vg + (p - 1) * stride, p);
+    }
+    if (d->lead_vg[0]) embed(d->lead_vg[0], 0);
+    if (d->lead_vg[1]) embed(d->lead_vg[1], ctx->nq - 1);
+    if (cudaMemcpyAsync(ctx->d_tab, host_tab.data(), tab_bytes, cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess) { pw_destroy(ctx); return PW_ECUDA; }
+  }
+  pw::TableArgs ta;
+  memset(&ta, 0, sizeof(ta));
+  ta.tab = ctx->d_tab;
+  ta.nq = ctx->nq;
+  ta.Dm = ctx->Dm;
+  ta.Dn = ctx->Dn;
+  ta.b1x = ctx->b1[0]; ta.b1y = ctx->b1[1]; ta.b2x = ctx->b2[0]; ta.b2y = ctx->b2[1];
+  ta.area = ctx->area;
+  ta.z_edges = ctx->d_z;
+  ta.explicit_slices = d->slice_vg ? 1 : 0;
+  ta.explicit_lead[0] = d->lead_vg[0] ? 1 : 0;
+  ta.explicit_lead[1] = d->lead_vg[1] ? 1 : 0;
+  std::vector<void *> temps;
+  auto up = [&](const double *src, size_t cnt) -> const double * {
+    if (!src || cnt == 0) return nullptr;
+    double *p = nullptr;
+    if (upload(ctx, &p, src, cnt) != PW_OK) return nullptr;
+    temps.push_back(p);
+    return p;
+  };
+  if (!d->slice_vg && d->n_wells > 0) {
+    ta.slices.xyz = up(d->well_xyz, 3 * (size_t)d->n_wells);
+    ta.slices.v0 = up(d->well_v0, d->n_wells);
+    ta.slices.sigma = up(d->well_sigma, d->n_wells);
+    ta.slices.n = d->n_wells;
+  }
+  for (int s = 0; s < 2; ++s) {
+    ta.period[s] = d->lead_period[s] > 0 ? d->lead_period[s] : 1.0;
+    if (!d->lead_vg[s] && d->lead_n_wells[s] > 0) {
+      ta.lead[s].xyz = up(d->lead_well_xy[s], 2 * (size_t)d->lead_n_wells[s]);
+      ta.lead[s].v0 = up(d->lead_well_v0[s], d->lead_n_wells[s]);
+      ta.lead[s].sigma = up(d->lead_well_sigma[s], d->lead_n_wells[s]);
+      ta.lead[s].n = d->lead_n_wells[s];
+    }
+  }
+  if (ctx->err != PW_OK) { st = ctx->err; pw_destroy(ctx); return st; }
+  pw::launch_tables(ta, ctx->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  for (void *p : temps) cudaFree(p);
+  if (e != cudaSuccess) { pw_destroy(ctx); return PW_ECUDA; }
+  *out = ctx;
+  return PW_OK;
+}
+
+void pw_destroy(pw_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
+                  ctx->d_O, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
+                  ctx->pts.p, ctx->status.p, ctx->work.p};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+pw_status pw_set_profiling(pw_ctx *ctx, int enable) {
+  if (!ctx) return PW_EINVAL;
+  ctx->profiling = enable != 0;
+  return PW_OK;
+}
+
+pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset) {
+  if (!ctx || !out) return PW_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < 6; ++i) out[i] = 0.0;
+  for (auto &r : ctx->recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    out[2 * r.kind] += ms;
+    out[2 * r.kind + 1] += r.count;
+  }
+  if (reset) {
+    for (auto &r : ctx->recs) { ctx->event_pool.push_back(r.a); ctx->event_pool.push_back(r.b); }
+    ctx->recs.clear();
+  }
+  return PW_OK;
+}
+
+pw_status pw_potential_tables(pw_ctx *ctx, pw_c128 *vg_dev, int *half_host) {
+  if (!ctx) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  if (half_host) { half_host[0] = ctx->Dm; half_host[1] = ctx->Dn; }
+  if (vg_dev)
+    CK(cudaMemcpyAsync(vg_dev, ctx->d_tab, (size_t)ctx->nq * ctx->tsz * sizeof(zc),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  return PW_OK;
+}
+
+pw_status pw_slice_modes(pw_ctx *ctx, const double *kpar, double *En_dev, pw_c128 *U_dev) {
+  if (!ctx || !kpar) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  pw_status st = ensure_kset(ctx, kpar);
+  if (st) return st;
+  const size_t nn = (size_t)ctx->n * ctx->n;
+  if (En_dev)
+    CK(cudaMemcpyAsync(En_dev, ctx->d_En, (size_t)ctx->nq * ctx->n * sizeof(double),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  if (U_dev)
+    CK(cudaMemcpyAsync(U_dev, ctx->d_HU, ctx->nq * nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  return PW_OK;
+}
+
+pw_status pw_overlaps(pw_ctx *ctx, const double *kpar, pw_c128 *O_dev) {
+  if (!ctx || !kpar || !O_dev) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  pw_status st = ensure_kset(ctx, kpar);
+  if (st) return st;
+  CK(cudaMemcpyAsync(O_dev, ctx->d_O, (size_t)(ctx->nq - 1) * ctx->n * ctx->n * sizeof(zc),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return PW_OK;
+}
+
+pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface,
+                           pw_c128 *S_dev) {
+  if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !S_dev))) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  if (iface < 0 || iface > ctx->N) return PW_EINVAL;
+  const int n = ctx->n;
+  const size_t nn = (size_t)n * n;
+  std::vector<std::vector<int>> groups;
+  group_by_k(npts, kpar, groups);
+  for (auto &g : groups) {
+    pw_status st = ensure_kset(ctx, kpar + 2 * g[0]);
+    if (st) return st;
+    const int bmax = std::max(1, std::min((int)g.size(), 2 * ctx->num_sms));
+    for (size_t b0 = 0; b0 < g.size(); b0 += bmax) {
+      const int nb = (int)std::min(g.size() - b0, (size_t)bmax);
+      if ((st = ensure(ctx, ctx->work, (size_t)nb * 3 * nn * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+          (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
+          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))) ||
+          (st = ensure(ctx, ctx->M, (size_t)nb * 4 * nn * sizeof(zc))))
+        return st;
+      std::vector<PointDesc> pd(nb);
+      for (int i = 0; i < nb; ++i) {
+        const int idx = g[b0 + i];
+        pd[i] = PointDesc{E[idx], 0, 0, 0, idx, 0};
+      }
+      CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
+      CK(pw::launch_slice_smatrix((PointDesc *)ctx->pts.p, ctx->d_En, ctx->d_O, ctx->d_dz,
+                                  (zc *)ctx->work.p, (int *)ctx->piv.p, (int *)ctx->status.p,
+                                  (zc *)ctx->M.p, n, ctx->N, iface, nb, ctx->stream));
+      // scatter the batch's S blocks to the caller's point order
+      for (int i = 0; i < nb; ++i)
+        CK(cudaMemcpyAsync(S_dev + (size_t)g[b0 + i] * 4 * nn, (zc *)ctx->M.p + (size_t)i * 4 * nn,
+                           4 * nn * sizeof(zc), cudaMemcpyDeviceToDevice, ctx->stream));
+      std::vector<int> st_h(nb);
+      CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int v : st_h)
+        if (v) return latch(ctx, PW_ESINGULAR);
+    }
+  }
+  return PW_OK;
+}
+
+pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
+                     pw_c128 *Sab_dev) {
+  if (!ctx || npts < 0 || (npts > 0 && (!Sa_dev || !Sb_dev || !Sab_dev))) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  const int n = ctx->n;
+  const size_t nn = (size_t)n * n;
+  const int bmax = std::max(1, std::min(npts, 2 * ctx->num_sms));
+  pw_status st;
+  for (int b0 = 0; b0 < npts; b0 += bmax) {
+    const int nb = std::min(npts - b0, bmax);
+    if ((st = ensure(ctx, ctx->work, (size_t)nb * 4 * nn * sizeof(zc))) ||
+        (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
+      return st;
+    CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
+    CK(pw::launch_compose((const zc *)Sa_dev + (size_t)b0 * 4 * nn, (const zc *)Sb_dev + (size_t)b0 * 4 * nn,
+                          (zc *)Sab_dev + (size_t)b0 * 4 * nn, (zc *)ctx->work.p, (int *)ctx->piv.p,
+                          (int *)ctx->status.p, n, nb, ctx->stream));
+    std::vector<int> st_h(nb);
+    CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int v : st_h)
+      if (v) return latch(ctx, PW_ESINGULAR);
+  }
+  return PW_OK;
+}
+
+pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev,
+                          pw_c128 *t_dev, int *nopen_dev, double *err_dev) {
+  if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev))) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  const int n = ctx->n;
+  const size_t nn = (size_t)n * n;
+  const size_t esz = ctx->precision == PW_FP64 ? sizeof(zc) : sizeof(cc);
+  std::vector<std::vector<int>> groups;
+  group_by_k(npts, kpar, groups);
+  pw_status result = PW_OK;
+  for (auto &g : groups) {
+    pw_status st = ensure_kset(ctx, kpar + 2 * g[0]);
+    if (st) return st;
+    const int bmax = std::max(1, std::min((int)g.size(), 2 * ctx->num_sms));
+    for (size_t b0 = 0; b0 < g.size(); b0 += bmax) {
+      const int nb = (int)std::min(g.size() - b0, (size_t)bmax);
+      std::vector<PointDesc> pd(nb);
+      int nc = 1;
+      for (int i = 0; i < nb; ++i) {
+        const int idx = g[b0 + i];
+        bool th = false;
+        const int nL = count_open(ctx->EL, E[idx], &th);
+        const int nR = count_open(ctx->ER, E[idx], &th);
+        pd[i] = PointDesc{E[idx], 0, nL, nR, idx, th ? 1 : 0};
+        if (th) result = PW_ETHRESH;
+        else nc = std::max(nc, nL);
+      }
+      nc = (nc + 3) & ~3;
+      const int ncols = 2 * n + nc;
+      if ((st = ensure(ctx, ctx->R, (size_t)nb * nn * esz)) ||
+          (st = ensure(ctx, ctx->M, (size_t)nb * n * ncols * esz)) ||
+          (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+          (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
+          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
+        return st;
+      CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
+      pw::SweepArgs a;
+      a.pts = (const PointDesc *)ctx->pts.p;
+      a.En = ctx->d_En;
+      a.O = ctx->d_O;
+      a.dz = ctx->d_dz;
+      a.R = ctx->R.p;
+      a.M = ctx->M.p;
+      a.piv = (int *)ctx->piv.p;
+      a.status = (int *)ctx->status.p;
+      a.T = T_dev;
+      a.t = (zc *)t_dev;
+      a.nopen = nopen_dev;
+      a.err = err_dev;
+      a.n = n;
+      a.N = ctx->N;
+      a.nc = nc;
+      Stage s0(ctx, 0, ctx->N + 1);
+      for (int p = 0; p <= ctx->N; ++p) CK(pw::launch_sweep(a, nb, p, ctx->precision, ctx->stream));
+      s0.done();
+      std::vector<int> st_h(nb);
+      CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int v : st_h)
+        if (v) result = PW_ESINGULAR;
+    }
+  }
+  if (result == PW_ESINGULAR) latch(ctx, result);
+  return result;
+}
+
+}  // extern "C"

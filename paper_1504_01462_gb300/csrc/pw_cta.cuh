@@ -1,0 +1,257 @@
+// CTA-wide dense complex linear algebra on column-major matrices in global
+// memory: a tiled GEMM with functor operands/epilogue, and a right-looking
+// blocked LU with partial pivoting that eliminates on an augmented matrix
+// [A | B] and back-substitutes, i.e. solves A X = B in place.
+//
+// One CTA owns one problem (one (E, k_par) point); every function here must be
+// called by all threads of the CTA and ends with a __syncthreads().
+#pragma once
+#include "pw_cx.cuh"
+
+namespace pw {
+
+constexpr int NT = 256;   // threads per CTA for every per-point kernel
+
+template <typename T>
+struct Tile;
+template <>
+struct Tile<double> {
+  static constexpr int BM = 64, BN = 64, BK = 16, NB = 32;
+};
+template <>
+struct Tile<float> {
+  static constexpr int BM = 64, BN = 64, BK = 16, NB = 32;
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t gemm_smem_elems() {
+  return size_t(Tile<T>::BK) * (Tile<T>::BM + 1) + size_t(Tile<T>::BK) * (Tile<T>::BN + 1);
+}
+
+// C(i,j) = fe(i, j, sum_l fa(i,l) fb(l,j)) for 0 <= i < m, 0 <= j < n, 0 <= l < k.
+// fa/fb return cx<T>; fa is read with i fastest (A column-major), fb with l
+// fastest (B column-major), so plain column-major operands load coalesced.
+// smem must hold gemm_smem_elems<T>() elements.
+template <typename T, class FA, class FB, class FE>
+__device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) {
+  constexpr int BM = Tile<T>::BM, BN = Tile<T>::BN, BK = Tile<T>::BK;
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LDA = BM + 1, LDB = BN + 1;
+  cx<T> *As = smem;
+  cx<T> *Bs = smem + BK * LDA;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tilesM = (m + BM - 1) / BM, tilesN = (n + BN - 1) / BN;
+  for (int t = 0; t < tilesM * tilesN; ++t) {
+    const int i0 = (t % tilesM) * BM, j0 = (t / tilesM) * BN;
+    cx<T> acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) acc[r][c] = czero<T>();
+    for (int l0 = 0; l0 < k; l0 += BK) {
+      for (int e = tid; e < BM * BK; e += NT) {
+        const int ii = e % BM, ll = e / BM;
+        const int i = i0 + ii, l = l0 + ll;
+        As[ll * LDA + ii] = (i < m && l < k) ? fa(i, l) : czero<T>();
+      }
+      for (int e = tid; e < BK * BN; e += NT) {
+        const int ll = e % BK, jj = e / BK;
+        const int l = l0 + ll, j = j0 + jj;
+        Bs[ll * LDB + jj] = (l < k && j < n) ? fb(l, j) : czero<T>();
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int ll = 0; ll < BK; ++ll) {
+        cx<T> a[TM], b[TN];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) a[r] = As[ll * LDA + ty + 16 * r];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) b[c] = Bs[ll * LDB + tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+          for (int c = 0; c < TN; ++c) cfma(acc[r][c], a[r], b[c]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+        if (i < m && j < n) fe(i, j, acc[r][c]);
+      }
+  }
+  __syncthreads();
+}
+
+// Plain column-major operand accessors.
+template <typename T>
+struct ColMajor {
+  const cx<T> *p;
+  int ld;
+  __device__ cx<T> operator()(int i, int j) const { return p[i + (size_t)j * ld]; }
+};
+
+// Block-wide arg-max of a per-thread (value, index) pair; returns the winning
+// index to every thread.  Ties go to the smaller index.
+template <typename T>
+__device__ int block_argmax(T v, int idx, T *sval, int *sidx) {
+  for (int off = 16; off > 0; off >>= 1) {
+    T ov = __shfl_down_sync(0xffffffffu, v, off);
+    int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sval[warp] = v; sidx[warp] = idx; }
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < NT / 32 ? sval[lane] : T(-1);
+    idx = lane < NT / 32 ? sidx[lane] : 0x7fffffff;
+    for (int off = 16; off > 0; off >>= 1) {
+      T ov = __shfl_down_sync(0xffffffffu, v, off);
+      int oi = __shfl_down_sync(0xffffffffu, idx, off);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if (lane == 0) sidx[0] = idx;
+  }
+  __syncthreads();
+  const int r = sidx[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T tiny_pivot();
+template <>
+__device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
+template <>
+__device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
+
+// Solves A X = B in place for the n x n matrix A held in columns [0, n) of the
+// n x ncols column-major M (leading dimension ld) and the right-hand sides in
+// columns [n, ncols).  Partial (row) pivoting; A is overwritten by its LU
+// factors, B by X.  `flag` (shared, per CTA) gets bit 1 on a zero pivot.
+// smem: gemm_smem_elems<T>() + NB*NB complex, plus sval/sidx scratch.
+template <typename T>
+__device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T> *smem,
+                             T *sval, int *sidx, int *flag) {
+  constexpr int NB = Tile<T>::NB;
+  const int tid = threadIdx.x;
+  cx<T> *Ls = smem + gemm_smem_elems<T>();   // NB x NB staging
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int nb = min(NB, n - j0);
+    // ---- unblocked panel factorisation, columns j0..j0+nb-1, rows j0..n-1
+    for (int j = j0; j < j0 + nb; ++j) {
+      T best = T(-1);
+      int bi = j;
+      for (int i = j + tid; i < n; i += NT) {
+        const T v = cabs1(M[i + (size_t)j * ld]);
+        if (v > best) { best = v; bi = i; }
+      }
+      const int p = block_argmax<T>(best, bi, sval, sidx);
+      if (tid == 0) piv[j] = p;
+      if (p != j) {
+        for (int c = j0 + tid; c < j0 + nb; c += NT) {
+          const cx<T> a = M[j + (size_t)c * ld];
+          M[j + (size_t)c * ld] = M[p + (size_t)c * ld];
+          M[p + (size_t)c * ld] = a;
+        }
+      }
+      __syncthreads();
+      cx<T> d = M[j + (size_t)j * ld];
+      if (d.re == T(0) && d.im == T(0)) {
+        if (tid == 0) atomicOr(flag, 1);
+        d = mkc<T>(tiny_pivot<T>(), T(0));
+      }
+      const cx<T> inv = cinv(d);
+      for (int i = j + 1 + tid; i < n; i += NT) M[i + (size_t)j * ld] = cmul(M[i + (size_t)j * ld], inv);
+      __syncthreads();
+      const int rows = n - j - 1, cols = j0 + nb - j - 1;
+      for (int e = tid; e < rows * cols; e += NT) {
+        const int i = j + 1 + e % rows, c = j + 1 + e / rows;
+        cx<T> v = M[i + (size_t)c * ld];
+        const cx<T> l = M[i + (size_t)j * ld], u = M[j + (size_t)c * ld];
+        v.re -= l.re * u.re - l.im * u.im;
+        v.im -= l.re * u.im + l.im * u.re;
+        M[i + (size_t)c * ld] = v;
+      }
+      __syncthreads();
+    }
+    // ---- row swaps and U12 = L11^{-1} A12 on every column right of the panel
+    const int c0 = j0 + nb;
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e % nb, s = e / nb;
+      Ls[r + s * NB] = M[j0 + r + (size_t)(j0 + s) * ld];
+    }
+    __syncthreads();
+    for (int c = c0 + tid; c < ncols; c += NT) {
+      cx<T> *col = M + (size_t)c * ld + j0;
+      for (int r = 0; r < nb; ++r) {
+        const int p = piv[j0 + r] - j0;
+        if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
+      }
+      for (int r = 1; r < nb; ++r) {
+        cx<T> x = col[r];
+        for (int s = 0; s < r; ++s) {
+          const cx<T> l = Ls[r + s * NB], y = col[s];
+          x.re -= l.re * y.re - l.im * y.im;
+          x.im -= l.re * y.im + l.im * y.re;
+        }
+        col[r] = x;
+      }
+    }
+    __syncthreads();
+    // ---- trailing update M[c0:, c0:] -= L21 U12
+    if (c0 < n && c0 < ncols) {
+      cx<T> *Mp = M;
+      cta_gemm<T>(
+          n - c0, ncols - c0, nb,
+          [=](int i, int l) { return Mp[c0 + i + (size_t)(j0 + l) * ld]; },
+          [=](int l, int j) { return Mp[j0 + l + (size_t)(c0 + j) * ld]; },
+          [=](int i, int j, cx<T> acc) {
+            cx<T> &v = Mp[c0 + i + (size_t)(c0 + j) * ld];
+            v = csub(v, acc);
+          },
+          smem);
+    }
+  }
+  // ---- back substitution U X = B' on columns [n, ncols)
+  const int jlast = ((n - 1) / NB) * NB;
+  for (int j0 = jlast; j0 >= 0; j0 -= NB) {
+    const int nb = min(NB, n - j0);
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e % nb, s = e / nb;
+      Ls[r + s * NB] = M[j0 + r + (size_t)(j0 + s) * ld];
+    }
+    __syncthreads();
+    for (int c = n + tid; c < ncols; c += NT) {
+      cx<T> *col = M + (size_t)c * ld + j0;
+      for (int r = nb - 1; r >= 0; --r) {
+        cx<T> x = col[r];
+        for (int s = r + 1; s < nb; ++s) {
+          const cx<T> u = Ls[r + s * NB], y = col[s];
+          x.re -= u.re * y.re - u.im * y.im;
+          x.im -= u.re * y.im + u.im * y.re;
+        }
+        col[r] = cdiv(x, Ls[r + r * NB]);
+      }
+    }
+    __syncthreads();
+    if (j0 > 0) {
+      cx<T> *Mp = M;
+      cta_gemm<T>(
+          j0, ncols - n, nb,
+          [=](int i, int l) { return Mp[i + (size_t)(j0 + l) * ld]; },
+          [=](int l, int j) { return Mp[j0 + l + (size_t)(n + j) * ld]; },
+          [=](int i, int j, cx<T> acc) {
+            cx<T> &v = Mp[i + (size_t)(n + j) * ld];
+            v = csub(v, acc);
+          },
+          smem);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace pw

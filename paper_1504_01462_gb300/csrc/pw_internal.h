@@ -1,0 +1,76 @@
+// Internal interface between the host API (pw_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "pw_cx.cuh"
+#include "../../include/pw.h"
+
+namespace pw {
+
+// One (E, k_par) point of a sweep batch.
+struct PointDesc {
+  double E;
+  int kset;     // k-set slot holding its eigenvalues and overlaps
+  int nL, nR;   // open channels of the left / right electrode
+  int out;      // index into the caller's output arrays
+  int skip;     // 1: threshold point, write NaN and do nothing else
+};
+
+// Geometry shared by the potential kernels.
+struct WellSet {
+  const double *xyz;     // 3 per well (slices) or 2 per well (leads)
+  const double *v0;
+  const double *sigma;
+  int n;
+};
+
+struct TableArgs {
+  zc *tab;               // (N+2) x tsz
+  int nq, Dm, Dn;
+  double b1x, b1y, b2x, b2y, area;
+  const double *z_edges; // N+1
+  WellSet slices;        // wells of the device region
+  WellSet lead[2];       // electrode wells (x, y)
+  double period[2];
+  int explicit_slices;   // 1: slices 1..N were uploaded, skip them
+  int explicit_lead[2];
+};
+
+struct SweepArgs {
+  const PointDesc *pts;
+  const double *En;      // kset slots: [kset][q][n], q = 0..N+1
+  const zc *O;           // kset slots: [kset][p][n*n], p = 0..N
+  const double *dz;      // N+2: dz[0] = 0 (left lead), dz[1..N], dz[N+1] = 0
+  void *R;               // per point n*n  (cx<T>)
+  void *M;               // per point n*(2n+nc)  (cx<T>)
+  int *piv;              // per point n
+  int *status;           // per point
+  double *T;             // caller outputs (by PointDesc.out)
+  zc *t;
+  int *nopen;
+  double *err;
+  int n, N, nc;
+};
+
+// potential tables and slice Hamiltonians
+void launch_tables(const TableArgs &a, cudaStream_t s);
+void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, double kx, double ky,
+                       int n, int nq, int Dm, int Dn, cudaStream_t s);
+// batched Hermitian eigensolver: H (in) -> U (out, same buffer); V scratch
+void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s);
+// O_p = U_p^H U_{p+1}, p = 0..nmat-2
+void launch_overlaps(const zc *U, zc *O, int n, int nmat, cudaStream_t s);
+// one interface of the left-to-right sweep for every point of a batch
+cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
+size_t sweep_smem_bytes(int n, int precision);
+// explicit interface S-matrices (FP64)
+cudaError_t launch_slice_smatrix(const PointDesc *pts, const double *En, const zc *O, const double *dz,
+                                 zc *work, int *piv, int *status, zc *S, int n, int N, int iface,
+                                 int npts, cudaStream_t s);
+// star products (FP64)
+cudaError_t launch_compose(const zc *Sa, const zc *Sb, zc *Sab, zc *work, int *piv, int *status,
+                           int n, int npts, cudaStream_t s);
+
+}  // namespace pw

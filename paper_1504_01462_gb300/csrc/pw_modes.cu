@@ -1,0 +1,288 @@
+// Slice potentials, slice Hamiltonians, their eigenmodes and the interface
+// overlaps: everything of the path that depends on k_par but not on E.
+//
+//   k_tables      V^p(dG) of Gaussian wells averaged over each slice (Sec. II A:
+//                 the slice potential is taken z-independent inside a slice)
+//   k_assemble_h  H_p(G,G') = |k+G|^2 delta + V^p(G-G')          (Eq. loc)
+//   k_jacobi_eig  eigenpairs (E_n^p, phi_n^p) of every H_p       (Eq. loc / A8)
+//   k_overlaps    O_p = U_p^H U_{p+1} = sum_s (M^{p+1}_{js})^* M^p_{ns}
+//                 of App. A Eq. transfer
+#include <math.h>
+
+#include "pw_cta.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+// ---------------------------------------------------------------------------
+// Fourier tables.  One thread per (slice, dG).  For a well -v0 exp(-|r-R|^2/2s^2)
+// the transverse-periodic Fourier coefficient is
+//   -(2 pi s^2 / A) v0 exp(-s^2 |G|^2 / 2) exp(-i G.R_perp) x (z-weight),
+// the z-weight being the slice average of exp(-(z-Z)^2/2s^2):
+//   (s sqrt(pi/2) / dz) [erf((z_hi-Z)/(sqrt2 s)) - erf((z_lo-Z)/(sqrt2 s))]
+// for a slice, and s sqrt(2 pi) / period for a z-periodic electrode.
+// ---------------------------------------------------------------------------
+__global__ void k_tables(TableArgs a) {
+  const int tsz = (2 * a.Dm + 1) * (2 * a.Dn + 1);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (e >= tsz) return;
+  const bool is_lead = (q == 0 || q == a.nq - 1);
+  const int side = (q == 0) ? 0 : 1;
+  if (is_lead ? a.explicit_lead[side] : a.explicit_slices) return;
+  const int dm = e / (2 * a.Dn + 1) - a.Dm;
+  const int dn = e % (2 * a.Dn + 1) - a.Dn;
+  const double gx = dm * a.b1x + dn * a.b2x;
+  const double gy = dm * a.b1y + dn * a.b2y;
+  const double g2 = gx * gx + gy * gy;
+  const double pref = -2.0 * M_PI / a.area;
+  double re = 0.0, im = 0.0;
+  if (is_lead) {
+    const WellSet &w = a.lead[side];
+    for (int i = 0; i < w.n; ++i) {
+      const double s = w.sigma[i];
+      const double amp = pref * s * s * w.v0[i] * exp(-0.5 * s * s * g2) *
+                         (s * sqrt(2.0 * M_PI) / a.period[side]);
+      double sn, cs;
+      sincos(gx * w.xyz[2 * i] + gy * w.xyz[2 * i + 1], &sn, &cs);
+      re += amp * cs;
+      im -= amp * sn;
+    }
+  } else {
+    const double zlo = a.z_edges[q - 1], zhi = a.z_edges[q];
+    const WellSet &w = a.slices;
+    for (int i = 0; i < w.n; ++i) {
+      const double s = w.sigma[i];
+      const double Z = w.xyz[3 * i + 2];
+      const double wz = (s * sqrt(0.5 * M_PI) / (zhi - zlo)) *
+                        (erf((zhi - Z) / (M_SQRT2 * s)) - erf((zlo - Z) / (M_SQRT2 * s)));
+      const double amp = pref * s * s * w.v0[i] * exp(-0.5 * s * s * g2) * wz;
+      double sn, cs;
+      sincos(gx * w.xyz[3 * i] + gy * w.xyz[3 * i + 1], &sn, &cs);
+      re += amp * cs;
+      im -= amp * sn;
+    }
+  }
+  a.tab[(size_t)q * tsz + e] = mkc<double>(re, im);
+}
+
+void launch_tables(const TableArgs &a, cudaStream_t s) {
+  const int tsz = (2 * a.Dm + 1) * (2 * a.Dn + 1);
+  dim3 grid((tsz + 255) / 256, a.nq);
+  k_tables<<<grid, 256, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Hamiltonians, column-major, one thread per element.
+// ---------------------------------------------------------------------------
+__global__ void k_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, double kx,
+                             double ky, int n, int Dm, int Dn) {
+  const int q = blockIdx.y;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * n) return;
+  const int i = e % n, j = e / n;
+  const int tw = 2 * Dn + 1;
+  const int dm = mn[2 * i] - mn[2 * j] + Dm;
+  const int dn = mn[2 * i + 1] - mn[2 * j + 1] + Dn;
+  zc v = tab[(size_t)q * (2 * Dm + 1) * tw + dm * tw + dn];
+  if (i == j) {
+    const double x = kx + G[2 * i], y = ky + G[2 * i + 1];
+    v.re += x * x + y * y;
+    v.im = 0.0;
+  }
+  H[(size_t)q * n * n + e] = v;
+}
+
+void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, double kx, double ky,
+                       int n, int nq, int Dm, int Dn, cudaStream_t s) {
+  dim3 grid((unsigned)(((size_t)n * n + 255) / 256), nq);
+  k_assemble_h<<<grid, 256, 0, s>>>(H, tab, mn, G, kx, ky, n, Dm, Dn);
+}
+
+// ---------------------------------------------------------------------------
+// Batched Hermitian eigensolver: cyclic two-sided Jacobi with a parallel
+// (round-robin) ordering, one CTA per matrix, matrix in global memory.
+//
+// For a pair (p, q) with a_pq = |b| e^{i phi}, the unitary
+//   J = [[c, s], [-s e^{-i phi}, c e^{-i phi}]],
+//   theta = (a_qq - a_pp) / (2|b|), t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
+//   c = 1 / sqrt(t^2 + 1), s = t c,
+// makes (J^H A J)_pq = 0 with new diagonal a_pp - t|b|, a_qq + t|b|.  Each round
+// applies n/2 disjoint rotations: columns of A and V first (A J, V J), then
+// rows of A (J^H (A J)).  Sweeps continue until the largest |a_pq| met in a
+// sweep is below 1e-12 max|A|.
+// ---------------------------------------------------------------------------
+constexpr int EIG_THREADS = 512;
+
+__global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_all, double *En_all,
+                                                            int *status, int n, int max_sweeps) {
+  extern __shared__ unsigned char smraw[];
+  const int mat = blockIdx.x;
+  zc *A = HU_all + (size_t)mat * n * n;
+  zc *V = V_all + (size_t)mat * n * n;
+  double *En = En_all + (size_t)mat * n;
+  const int m = (n + 1) & ~1;
+  const int np = m / 2;
+  const int tid = threadIdx.x;
+  // shared layout
+  double *sc = reinterpret_cast<double *>(smraw);   // c
+  double *ss = sc + np;                              // s
+  double *sdp = ss + np;                             // new a_pp
+  double *sdq = sdp + np;                            // new a_qq
+  zc *sph = reinterpret_cast<zc *>(sdq + np);        // e^{-i phi}
+  int *sp = reinterpret_cast<int *>(sph + np);
+  int *sq = sp + np;
+  int *sskip = sq + np;
+  double *slam = reinterpret_cast<double *>(sskip + np + (np & 1));
+  __shared__ unsigned long long s_off;
+  __shared__ unsigned long long s_amax;
+
+  for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) {
+    const int i = e % n, j = e / n;
+    V[e] = mkc<double>(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (tid == 0) s_amax = 0ull;
+  __syncthreads();
+  {
+    double am = 0.0;
+    for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) am = fmax(am, cabs1(A[e]));
+    atomicMax(&s_amax, (unsigned long long)__double_as_longlong(am));
+  }
+  __syncthreads();
+  const double amax = fmax(__longlong_as_double((long long)s_amax), 1e-300);
+  const double rot_thresh = 1e-18 * amax;
+  const double conv = 1e-12 * amax;
+  int converged = 0;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_off = 0ull;
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = tid; k < np; k += EIG_THREADS) {
+        int p, q;
+        if (k == 0) {
+          p = m - 1;
+          q = r;
+        } else {
+          p = (r + k) % (m - 1);
+          q = (r - k + (m - 1)) % (m - 1);
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        sp[k] = p;
+        sq[k] = q;
+        int skip = 1;
+        if (q < n) {
+          const double app = A[p + (size_t)p * n].re, aqq = A[q + (size_t)q * n].re;
+          const zc apq = A[p + (size_t)q * n];
+          const double mag = hypot(apq.re, apq.im);
+          if (mag > 0.0) atomicMax(&s_off, (unsigned long long)__double_as_longlong(mag));
+          if (mag > rot_thresh) {
+            const double theta = (aqq - app) / (2.0 * mag);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0);
+            sc[k] = c;
+            ss[k] = t * c;
+            sph[k] = mkc<double>(apq.re / mag, -apq.im / mag);
+            sdp[k] = app - t * mag;
+            sdq[k] = aqq + t * mag;
+            skip = 0;
+          }
+        }
+        sskip[k] = skip;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (size_t e = tid; e < (size_t)np * n; e += EIG_THREADS) {
+        const int k = e / n, i = e % n;
+        if (sskip[k]) continue;
+        const int p = sp[k], q = sq[k];
+        const double c = sc[k], s = ss[k];
+        const zc ph = sph[k];
+        {
+          const zc x = A[i + (size_t)p * n], y = cmul(ph, A[i + (size_t)q * n]);
+          A[i + (size_t)p * n] = mkc<double>(c * x.re - s * y.re, c * x.im - s * y.im);
+          A[i + (size_t)q * n] = mkc<double>(s * x.re + c * y.re, s * x.im + c * y.im);
+        }
+        {
+          const zc x = V[i + (size_t)p * n], y = cmul(ph, V[i + (size_t)q * n]);
+          V[i + (size_t)p * n] = mkc<double>(c * x.re - s * y.re, c * x.im - s * y.im);
+          V[i + (size_t)q * n] = mkc<double>(s * x.re + c * y.re, s * x.im + c * y.im);
+        }
+      }
+      __syncthreads();
+      // rows: A <- J^H A; the 2x2 blocks take their exact values
+      for (size_t e = tid; e < (size_t)np * n; e += EIG_THREADS) {
+        const int k = e / n, j = e % n;
+        if (sskip[k]) continue;
+        const int p = sp[k], q = sq[k];
+        const double c = sc[k], s = ss[k];
+        const zc phc = cconj(sph[k]);
+        if (j == p) {
+          A[p + (size_t)p * n] = mkc<double>(sdp[k], 0.0);
+          A[q + (size_t)p * n] = czero<double>();
+        } else if (j == q) {
+          A[q + (size_t)q * n] = mkc<double>(sdq[k], 0.0);
+          A[p + (size_t)q * n] = czero<double>();
+        } else {
+          const zc x = A[p + (size_t)j * n], y = cmul(phc, A[q + (size_t)j * n]);
+          A[p + (size_t)j * n] = mkc<double>(c * x.re - s * y.re, c * x.im - s * y.im);
+          A[q + (size_t)j * n] = mkc<double>(s * x.re + c * y.re, s * x.im + c * y.im);
+        }
+      }
+      __syncthreads();
+    }
+    converged = __longlong_as_double((long long)s_off) <= conv;
+    __syncthreads();
+  }
+  // eigenvalues, ascending with ties by index; U columns replace H
+  for (int i = tid; i < n; i += EIG_THREADS) slam[i] = A[i + (size_t)i * n].re;
+  __syncthreads();
+  for (int i = tid; i < n; i += EIG_THREADS) {
+    const double li = slam[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double lj = slam[j];
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    En[rank] = li;
+    // the rank goes to the (now unused) rotation arrays: 2*np >= n ints fit in sc
+    reinterpret_cast<int *>(sc)[i] = rank;
+  }
+  __syncthreads();
+  const int *rk = reinterpret_cast<const int *>(sc);
+  for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) {
+    const int i = e % n, j = e / n;
+    A[i + (size_t)rk[j] * n] = V[e];
+  }
+  if (tid == 0) status[mat] = converged ? 0 : 1;
+}
+
+void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s) {
+  const int np = ((n + 1) & ~1) / 2;
+  const size_t smem = (size_t)np * (4 * sizeof(double) + sizeof(zc) + 3 * sizeof(int)) + 8 +
+                      (size_t)n * sizeof(double) + 64;
+  cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobi_eig<<<nmat, EIG_THREADS, smem, s>>>(HU, V, En, status, n, 40);
+}
+
+// ---------------------------------------------------------------------------
+// Overlaps O_p = U_p^H U_{p+1}: one CTA per interface.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n) {
+  extern __shared__ unsigned char smraw[];
+  zc *sm = reinterpret_cast<zc *>(smraw);
+  const int p = blockIdx.x;
+  const zc *Up = U + (size_t)p * n * n;
+  const zc *Uq = Up + (size_t)n * n;
+  zc *Op = O + (size_t)p * n * n;
+  cta_gemm<double>(
+      n, n, n, [=](int i, int l) { return cconj(Up[l + (size_t)i * n]); },
+      [=](int l, int j) { return Uq[l + (size_t)j * n]; },
+      [=](int i, int j, zc acc) { Op[i + (size_t)j * n] = acc; }, sm);
+}
+
+void launch_overlaps(const zc *U, zc *O, int n, int nmat, cudaStream_t s) {
+  const size_t smem = gemm_smem_elems<double>() * sizeof(zc);
+  k_overlaps<<<nmat - 1, NT, smem, s>>>(U, O, n);
+}
+
+}  // namespace pw

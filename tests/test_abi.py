@@ -1,0 +1,66 @@
+"""The C-ABI library loads without a GPU and exports every entry point that
+include/pw.h declares; argument validation that needs no device works."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pw_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def pw():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1504_01462_gb300 as pw
+    return pw
+
+
+def test_every_declared_symbol_is_exported(pw):
+    names = _declared()
+    assert len(names) >= 13
+    lib = pw.lib()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(pw.EXPORTS) <= set(names)
+
+
+def test_status_strings(pw):
+    lib = pw.lib()
+    for code in range(8):
+        assert lib.pw_status_str(code)
+    assert lib.pw_status_str(0) == b"ok"
+
+
+def test_invalid_descriptors_rejected_before_any_device_call(pw):
+    lib = pw.lib()
+    h = ctypes.c_void_p()
+    assert lib.pw_setup(None, None, ctypes.byref(h)) == 1
+    d = pw.SetupDesc()
+    d.a1[:] = [5.0, 0.0]
+    d.a2[:] = [0.0, 5.0]
+    d.ecut = 8.0
+    d.n_slices = 0
+    assert lib.pw_setup(ctypes.byref(d), None, ctypes.byref(h)) == 1       # no slices
+    z = np.array([0.0, 1.0, 1.0])                                           # not increasing
+    d.n_slices = 2
+    d.z_edges = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.pw_setup(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    z2 = np.array([0.0, 1.0, 2.0])
+    d.z_edges = z2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.precision = 7                                                          # unknown precision
+    assert lib.pw_setup(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    d.precision = 0
+    d.a2[:] = [10.0, 0.0]                                                    # degenerate cell
+    assert lib.pw_setup(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    assert lib.pw_ng(None) == 0 and lib.pw_n_slices(None) == 0
+    assert lib.pw_get_error(None) == 1
+    lib.pw_destroy(None)
