@@ -43,13 +43,15 @@ struct pw_ctx {
   int *d_mn = nullptr;
   double *d_G = nullptr, *d_dz = nullptr, *d_z = nullptr;
   zc *d_tab = nullptr;
-  // eigenmode cache of one k_par
-  bool kvalid = false;
-  double kcur[2] = {0, 0};
+  // eigenmode cache: ks_cap k-set slots, each holding the modes of all N+2
+  // slices and the N+1 overlaps at one k_par
+  int ks_cap = 0;
+  std::vector<double> slot_k;      // 2 per slot
+  std::vector<char> slot_valid;
   zc *d_HU = nullptr, *d_V = nullptr, *d_O = nullptr;
   double *d_En = nullptr;
   int *d_eigstat = nullptr;
-  std::vector<double> EL, ER;      // electrode eigenvalues at kcur (host)
+  std::vector<std::vector<double>> EL, ER;   // electrode eigenvalues per slot (host)
   // per-point workspaces
   DevBuf R, M, piv, pts, status, work;
   // launch timing (pw_set_profiling)
@@ -175,44 +177,82 @@ pw_status upload(pw_ctx *ctx, T **dst, const T *src, size_t count) {
   return PW_OK;
 }
 
-// Eigenmodes and overlaps of every slice at k (cached for the last k).
-pw_status ensure_kset(pw_ctx *ctx, const double *k) {
-  if (ctx->kvalid && ctx->kcur[0] == k[0] && ctx->kcur[1] == k[1]) return PW_OK;
-  ctx->kvalid = false;
+// Allocates the k-set slots (as many as fit in a fifth of free memory, <= 4).
+pw_status alloc_slots(pw_ctx *ctx) {
+  if (ctx->ks_cap) return PW_OK;
   const int n = ctx->n, nq = ctx->nq;
   const size_t nn = (size_t)n * n;
-  if (!ctx->d_HU) {
-    CK(cudaMalloc(&ctx->d_HU, nq * nn * sizeof(zc)));
-    CK(cudaMalloc(&ctx->d_V, nq * nn * sizeof(zc)));
-    CK(cudaMalloc(&ctx->d_O, (nq - 1) * nn * sizeof(zc)));
-    CK(cudaMalloc(&ctx->d_En, (size_t)nq * n * sizeof(double)));
-    CK(cudaMalloc(&ctx->d_eigstat, nq * sizeof(int)));
-  }
-  Stage s1(ctx, 1, 1);
-  pw::launch_assemble_h(ctx->d_HU, ctx->d_tab, ctx->d_mn, ctx->d_G, k[0], k[1], n, nq, ctx->Dm,
-                        ctx->Dn, ctx->stream);
-  CK(cudaGetLastError());
-  pw::launch_eig(ctx->d_HU, ctx->d_V, ctx->d_En, ctx->d_eigstat, n, nq, ctx->stream);
-  CK(cudaGetLastError());
-  s1.done();
-  Stage s2(ctx, 2, 1);
-  pw::launch_overlaps(ctx->d_HU, ctx->d_O, n, nq, ctx->stream);
-  CK(cudaGetLastError());
-  s2.done();
-  std::vector<int> st(nq);
-  ctx->EL.resize(n);
-  ctx->ER.resize(n);
-  CK(cudaMemcpyAsync(st.data(), ctx->d_eigstat, nq * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->EL.data(), ctx->d_En, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->ER.data(), ctx->d_En + (size_t)(nq - 1) * n, n * sizeof(double),
-                     cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  for (int q = 0; q < nq; ++q)
-    if (st[q] != 0) return latch(ctx, PW_ENOTCONV);
-  ctx->kcur[0] = k[0];
-  ctx->kcur[1] = k[1];
-  ctx->kvalid = true;
+  const size_t per = (size_t)(3 * nq - 1) * nn * sizeof(zc) + (size_t)nq * n * sizeof(double);
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  int cap = (int)std::min<size_t>(4, std::max<size_t>(1, free_b / 5 / per));
+  ctx->ks_cap = cap;
+  ctx->slot_k.assign(2 * cap, 0.0);
+  ctx->slot_valid.assign(cap, 0);
+  ctx->EL.assign(cap, std::vector<double>(n));
+  ctx->ER.assign(cap, std::vector<double>(n));
+  CK(cudaMalloc(&ctx->d_HU, (size_t)cap * nq * nn * sizeof(zc)));
+  CK(cudaMalloc(&ctx->d_V, (size_t)cap * nq * nn * sizeof(zc)));
+  CK(cudaMalloc(&ctx->d_O, (size_t)cap * (nq - 1) * nn * sizeof(zc)));
+  CK(cudaMalloc(&ctx->d_En, (size_t)cap * nq * n * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_eigstat, (size_t)cap * nq * sizeof(int)));
   return PW_OK;
+}
+
+// Eigenmodes and overlaps of every slice for the k values ks[0..K-1] in slots
+// 0..K-1 (K <= ks_cap).  Slots that already hold their k are kept; the others
+// are recomputed with one eigensolver launch over all their matrices.
+pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
+  pw_status st = alloc_slots(ctx);
+  if (st) return st;
+  const int n = ctx->n, nq = ctx->nq, K = (int)ks.size();
+  const size_t nn = (size_t)n * n;
+  int s0 = K, s1 = 0;
+  for (int s = 0; s < K; ++s) {
+    const bool same = ctx->slot_valid[s] && ctx->slot_k[2 * s] == ks[s][0] &&
+                      ctx->slot_k[2 * s + 1] == ks[s][1];
+    if (!same) { s0 = std::min(s0, s); s1 = std::max(s1, s + 1); }
+  }
+  if (s0 >= s1) return PW_OK;
+  for (int s = s0; s < s1; ++s) ctx->slot_valid[s] = 0;
+  const int nmat = (s1 - s0) * nq;
+  Stage st1(ctx, 1, s1 - s0);
+  for (int s = s0; s < s1; ++s)
+    pw::launch_assemble_h(ctx->d_HU + (size_t)s * nq * nn, ctx->d_tab, ctx->d_mn, ctx->d_G, ks[s][0],
+                          ks[s][1], n, nq, ctx->Dm, ctx->Dn, ctx->stream);
+  CK(cudaGetLastError());
+  pw::launch_eig(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_V + (size_t)s0 * nq * nn,
+                 ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
+                 ctx->stream);
+  CK(cudaGetLastError());
+  st1.done();
+  Stage st2(ctx, 2, s1 - s0);
+  pw::launch_overlaps(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq,
+                      s1 - s0, ctx->stream);
+  CK(cudaGetLastError());
+  st2.done();
+  std::vector<int> stat(nmat);
+  CK(cudaMemcpyAsync(stat.data(), ctx->d_eigstat + (size_t)s0 * nq, nmat * sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  for (int s = s0; s < s1; ++s) {
+    CK(cudaMemcpyAsync(ctx->EL[s].data(), ctx->d_En + (size_t)s * nq * n, n * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->ER[s].data(), ctx->d_En + ((size_t)s * nq + nq - 1) * n,
+                       n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int v : stat)
+    if (v != 0) return latch(ctx, PW_ENOTCONV);
+  for (int s = s0; s < s1; ++s) {
+    ctx->slot_k[2 * s] = ks[s][0];
+    ctx->slot_k[2 * s + 1] = ks[s][1];
+    ctx->slot_valid[s] = 1;
+  }
+  return PW_OK;
+}
+
+pw_status ensure_kset(pw_ctx *ctx, const double *k) {
+  return ensure_ksets(ctx, std::vector<const double *>{k});
 }
 
 int count_open(const std::vector<double> &En, double E, bool *thresh) {
@@ -540,20 +580,28 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
   std::vector<std::vector<int>> groups;
   group_by_k(npts, kpar, groups);
   pw_status result = PW_OK;
-  for (auto &g : groups) {
-    pw_status st = ensure_kset(ctx, kpar + 2 * g[0]);
-    if (st) return st;
-    const int bmax = std::max(1, std::min((int)g.size(), 2 * ctx->num_sms));
-    for (size_t b0 = 0; b0 < g.size(); b0 += bmax) {
-      const int nb = (int)std::min(g.size() - b0, (size_t)bmax);
+  pw_status st = alloc_slots(ctx);
+  if (st) return st;
+  for (size_t g0 = 0; g0 < groups.size(); g0 += ctx->ks_cap) {
+    const size_t g1 = std::min(groups.size(), g0 + (size_t)ctx->ks_cap);
+    std::vector<const double *> ks;
+    std::vector<std::pair<int, int>> pts;   // (point index, slot)
+    for (size_t gi = g0; gi < g1; ++gi) {
+      ks.push_back(kpar + 2 * groups[gi][0]);
+      for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
+    }
+    if ((st = ensure_ksets(ctx, ks))) return st;
+    const int bmax = std::max(1, std::min((int)pts.size(), 3 * ctx->num_sms));
+    for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
+      const int nb = (int)std::min(pts.size() - b0, (size_t)bmax);
       std::vector<PointDesc> pd(nb);
       int nc = 1;
       for (int i = 0; i < nb; ++i) {
-        const int idx = g[b0 + i];
+        const int idx = pts[b0 + i].first, slot = pts[b0 + i].second;
         bool th = false;
-        const int nL = count_open(ctx->EL, E[idx], &th);
-        const int nR = count_open(ctx->ER, E[idx], &th);
-        pd[i] = PointDesc{E[idx], 0, nL, nR, idx, th ? 1 : 0};
+        const int nL = count_open(ctx->EL[slot], E[idx], &th);
+        const int nR = count_open(ctx->ER[slot], E[idx], &th);
+        pd[i] = PointDesc{E[idx], slot, nL, nR, idx, th ? 1 : 0};
         if (th) result = PW_ETHRESH;
         else nc = std::max(nc, nL);
       }

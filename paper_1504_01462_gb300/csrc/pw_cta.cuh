@@ -37,6 +37,7 @@ __device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) 
   constexpr int BM = Tile<T>::BM, BN = Tile<T>::BN, BK = Tile<T>::BK;
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LDA = BM + 1, LDB = BN + 1;
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;   // staged elements per thread
   cx<T> *As = smem;
   cx<T> *Bs = smem + BK * LDA;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -48,18 +49,36 @@ __device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) 
     for (int r = 0; r < TM; ++r)
 #pragma unroll
       for (int c = 0; c < TN; ++c) acc[r][c] = czero<T>();
-    for (int l0 = 0; l0 < k; l0 += BK) {
-      for (int e = tid; e < BM * BK; e += NT) {
-        const int ii = e % BM, ll = e / BM;
+    // register stage of the next k-tile: global loads overlap the current tile's math
+    cx<T> ra[LA], rb[LB];
+    auto fetch = [&](int l0) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = tid + q * NT, ii = e % BM, ll = e / BM;
         const int i = i0 + ii, l = l0 + ll;
-        As[ll * LDA + ii] = (i < m && l < k) ? fa(i, l) : czero<T>();
+        ra[q] = (i < m && l < k) ? fa(i, l) : czero<T>();
       }
-      for (int e = tid; e < BK * BN; e += NT) {
-        const int ll = e % BK, jj = e / BK;
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        const int e = tid + q * NT, ll = e % BK, jj = e / BK;
         const int l = l0 + ll, j = j0 + jj;
-        Bs[ll * LDB + jj] = (l < k && j < n) ? fb(l, j) : czero<T>();
+        rb[q] = (l < k && j < n) ? fb(l, j) : czero<T>();
+      }
+    };
+    fetch(0);
+    for (int l0 = 0; l0 < k; l0 += BK) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = tid + q * NT;
+        As[(e / BM) * LDA + e % BM] = ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        const int e = tid + q * NT;
+        Bs[(e % BK) * LDB + e / BK] = rb[q];
       }
       __syncthreads();
+      if (l0 + BK < k) fetch(l0 + BK);
 #pragma unroll 4
       for (int ll = 0; ll < BK; ++ll) {
         cx<T> a[TM], b[TN];

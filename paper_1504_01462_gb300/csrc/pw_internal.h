@@ -60,8 +60,8 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
                        int n, int nq, int Dm, int Dn, cudaStream_t s);
 // batched Hermitian eigensolver: H (in) -> U (out, same buffer); V scratch
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s);
-// O_p = U_p^H U_{p+1}, p = 0..nmat-2
-void launch_overlaps(const zc *U, zc *O, int n, int nmat, cudaStream_t s);
+// O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots
+void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s);
 // one interface of the left-to-right sweep for every point of a batch
 cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
 size_t sweep_smem_bytes(int n, int precision);

@@ -267,22 +267,22 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
 // ---------------------------------------------------------------------------
 // Overlaps O_p = U_p^H U_{p+1}: one CTA per interface.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n) {
+__global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n, int nq) {
   extern __shared__ unsigned char smraw[];
   zc *sm = reinterpret_cast<zc *>(smraw);
-  const int p = blockIdx.x;
-  const zc *Up = U + (size_t)p * n * n;
+  const int slot = blockIdx.x / (nq - 1), p = blockIdx.x % (nq - 1);
+  const zc *Up = U + ((size_t)slot * nq + p) * n * n;
   const zc *Uq = Up + (size_t)n * n;
-  zc *Op = O + (size_t)p * n * n;
+  zc *Op = O + ((size_t)slot * (nq - 1) + p) * n * n;
   cta_gemm<double>(
       n, n, n, [=](int i, int l) { return cconj(Up[l + (size_t)i * n]); },
       [=](int l, int j) { return Uq[l + (size_t)j * n]; },
       [=](int i, int j, zc acc) { Op[i + (size_t)j * n] = acc; }, sm);
 }
 
-void launch_overlaps(const zc *U, zc *O, int n, int nmat, cudaStream_t s) {
+void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s) {
   const size_t smem = gemm_smem_elems<double>() * sizeof(zc);
-  k_overlaps<<<nmat - 1, NT, smem, s>>>(U, O, n);
+  k_overlaps<<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq);
 }
 
 }  // namespace pw
