@@ -171,6 +171,11 @@ def main():
     ap.add_argument("--config", default="junction512",
                     choices=["junction512", "junction401", "minimal"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--refine", type=int, default=2,
+                    help="FP64 refinement passes of the mixed form (-1: none)")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="override the slice count (profiling of small cases only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -194,9 +199,12 @@ def main():
         torch.cuda.synchronize()
 
     inst, n_e, n_k = workload(args.config)
+    if args.slices:
+        inst.z_edges = np.linspace(inst.z_edges[0], inst.z_edges[-1], args.slices + 1)
     prec = pw.MIXED_FP32 if args.precision == "mixed" else pw.FP64
     stream = torch.cuda.current_stream()
-    ctx = pw.Context.from_instance(inst, precision=prec, stream=stream.cuda_stream)
+    ctx = pw.Context.from_instance(inst, precision=prec, refine_iters=args.refine,
+                                   stream=stream.cuda_stream)
     n, N = ctx.ng, ctx.n_slices
     npts = len(inst.energies)
 
@@ -207,9 +215,10 @@ def main():
 
     T = torch.empty(n_e, dtype=torch.float64, device="cuda")
     nop = torch.empty((n_e, 2), dtype=torch.int32, device="cuda")
+    err = torch.zeros(n_e, dtype=torch.float64, device="cuda")
     for s in range(args.warmup):
         E, k = step_points(s)
-        ctx.transmission(E, k, T, None, nop)
+        ctx.transmission(E, k, T, None, nop, err)
     barrier()
 
     # ---- device-timed region: K steps, CUDA events on the library's stream
@@ -222,9 +231,10 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     flops_launch = []
+    err_max = 0.0
     for s in range(args.steps):
         E, k = step_points(args.warmup + s)
-        ctx.transmission(E, k, T, None, nop)
+        ctx.transmission(E, k, T, None, nop, err)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -232,6 +242,7 @@ def main():
     prof = ctx.get_profile(reset=True)
     ctx.set_profiling(False)
     nopen_last = nop.cpu().numpy()
+    err_max = float(err.max().item())
     flops_per_launch = sum(sweep_flops_per_point(n, int(nl)) for nl in nopen_last[:, 0])
     t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -244,12 +255,12 @@ def main():
     T_host = torch.empty(n_e, dtype=torch.float64).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    for s in range(args.steps):
+    for s in range(0 if args.no_e2e else args.steps):
         E, k = step_points(args.warmup + s)
         ctx.transmission(E, k, T, None, None)
         T_host.copy_(T, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
     e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
@@ -281,7 +292,10 @@ def main():
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                          "avg_launch_ms": sweep_avg_ms},
             "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
-                          "overlaps": prof["overlap_ms"]},
+                          "overlaps": prof["overlap_ms"], "refine": prof["refine_ms"]},
+            "accuracy": {"refine_iters": (args.refine if prec == pw.MIXED_FP32 else 0),
+                         "err_est_max_last_step": err_max,
+                         "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
             "gpu_launches": int(args.steps * (N + 1 + 3)),
             "e2e": {"value": e2e_value, "unit": "points/s",

@@ -51,7 +51,10 @@ typedef enum {
 
 typedef struct { double re, im; } pw_c128;
 
-/* arithmetic of the star-product sweep (the eigensolver is always FP64) */
+/* Arithmetic of the star-product sweep.  PW_FP64: every step in FP64.
+ * PW_MIXED_FP32: the sweep in FP32, then `refine_iters` passes of iterative
+ * refinement of the whole interface-matching system with FP64 residuals (the
+ * eigenmodes and overlaps are FP64 in both forms). */
 enum { PW_FP64 = 0, PW_MIXED_FP32 = 1 };
 
 /*
@@ -93,6 +96,8 @@ typedef struct {
   const pw_c128 *slice_vg;
   const pw_c128 *lead_vg[2];
   int precision;               /* PW_FP64 or PW_MIXED_FP32 */
+  int refine_iters;            /* PW_MIXED_FP32 only: FP64 refinement passes;
+                                  0 = default (2), -1 = none (plain FP32 sweep) */
 } pw_setup_desc;
 
 /* Builds the basis (Sec. II A) and uploads the slice geometry; the Fourier
@@ -154,7 +159,9 @@ pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128
  *   t_dev[npts * N_G * N_G] or NULL  t, top-left n_open^R x n_open^L block of
  *                                    each N_G x N_G column-major slot
  *   nopen_dev[2 * npts] or NULL      (n_open^L, n_open^R) per point
- *   err_dev[npts] or NULL            estimated relative error of T (0 for FP64)
+ *   err_dev[npts] or NULL            estimated relative error of T: 0 for FP64,
+ *                                    the relative change of T made by the last
+ *                                    refinement pass for PW_MIXED_FP32
  * A point at an electrode threshold gets T = NaN and the call returns
  * PW_ETHRESH after finishing the others. */
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar,
@@ -163,10 +170,10 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
 /* Timing of the library's own launches (for benchmarks and roofline
  * accounting).  While enabled, CUDA events on the context's stream bracket
  * every stage: the slice-mode stage (Hamiltonian assembly and eigensolver), the
- * overlap GEMMs, and each batch of sweep launches.  pw_get_profile
- * synchronises the stream and writes out[6] = {sweep ms, sweep launches,
- * mode-stage ms, mode stages, overlap ms, overlap stages}; reset != 0 clears
- * the records. */
+ * overlap GEMMs, each batch of sweep launches and each batch's refinement.
+ * pw_get_profile synchronises the stream and writes out[8] = {sweep ms,
+ * sweep launches, mode-stage ms, mode stages, overlap ms, overlap stages,
+ * refinement ms, refinement stages}; reset != 0 clears the records. */
 pw_status pw_set_profiling(pw_ctx *ctx, int enable);
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset);
 

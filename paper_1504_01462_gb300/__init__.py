@@ -57,6 +57,7 @@ class SetupDesc(ctypes.Structure):
         ("vg_half", ctypes.c_int * 2),
         ("slice_vg", _vp), ("lead_vg", _vp * 2),
         ("precision", ctypes.c_int),
+        ("refine_iters", ctypes.c_int),
     ]
 
 
@@ -119,7 +120,7 @@ class Context:
     def __init__(self, *, a1, a2, z_edges, ecut=0.0, ng_exact=0, wells_xyz=None, v0=None,
                  sigma=None, leads=((None, None, None, 1.0), (None, None, None, 1.0)),
                  slice_vg=None, lead_vg=(None, None), vg_half=(0, 0), precision=FP64,
-                 stream=None):
+                 refine_iters=0, stream=None):
         keep = []
         d = SetupDesc()
         d.a1[:] = [float(v) for v in a1]
@@ -155,6 +156,7 @@ class Context:
                 keep.append(lv)
                 d.lead_vg[side] = lv.ctypes.data
         d.precision = int(precision)
+        d.refine_iters = int(refine_iters)
         h = _vp()
         st = _lib.pw_setup(ctypes.byref(d), stream, ctypes.byref(h))
         if st != 0:
@@ -163,7 +165,7 @@ class Context:
         self.precision = int(precision)
 
     @classmethod
-    def from_instance(cls, inst, precision=FP64, stream=None):
+    def from_instance(cls, inst, precision=FP64, refine_iters=0, stream=None):
         """Marshal a problem description object (attributes as in
         synthetic.Instance) into pw_setup."""
         leads = []
@@ -173,7 +175,8 @@ class Context:
         return cls(a1=inst.a1, a2=inst.a2, z_edges=inst.z_edges, ecut=inst.ecut,
                    ng_exact=inst.ng_exact, wells_xyz=inst.wells_xyz, v0=inst.v0,
                    sigma=inst.sigma, leads=leads, slice_vg=inst.slice_vg, lead_vg=lead_vg,
-                   vg_half=inst.vg_half, precision=precision, stream=stream)
+                   vg_half=inst.vg_half, precision=precision, refine_iters=refine_iters,
+                   stream=stream)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -255,11 +258,11 @@ class Context:
 
     def get_profile(self, reset=True):
         """{'sweep_ms', 'sweep_launches', 'modes_ms', 'modes_stages', 'overlap_ms',
-        'overlap_stages'} accumulated since the last reset."""
-        out = np.zeros(6)
+        'overlap_stages', 'refine_ms', 'refine_stages'} accumulated since the last reset."""
+        out = np.zeros(8)
         self._check(_lib.pw_get_profile(self._h, _as_dp(out), int(bool(reset))), "pw_get_profile")
         keys = ["sweep_ms", "sweep_launches", "modes_ms", "modes_stages", "overlap_ms",
-                "overlap_stages"]
+                "overlap_stages", "refine_ms", "refine_stages"]
         return dict(zip(keys, out.tolist()))
 
     @staticmethod

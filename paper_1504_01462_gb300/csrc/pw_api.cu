@@ -32,6 +32,7 @@ struct pw_ctx {
   cudaStream_t stream = nullptr;
   pw_status err = PW_OK;
   int precision = PW_FP64;
+  int refine_iters = 0;            // FP64 refinement passes of the mixed form
   int n = 0, N = 0, nq = 0;        // basis size, slices, slices incl. electrodes
   int Dm = 0, Dn = 0, tsz = 0;     // Fourier-table index ranges
   double b1[2], b2[2], area = 0.0;
@@ -50,10 +51,12 @@ struct pw_ctx {
   std::vector<char> slot_valid;
   zc *d_HU = nullptr, *d_V = nullptr, *d_O = nullptr;
   double *d_En = nullptr;
-  int *d_eigstat = nullptr;
+  int *d_eigstat = nullptr;       // Jacobi sweeps per matrix
   std::vector<std::vector<double>> EL, ER;   // electrode eigenvalues per slot (host)
+  int last_sweeps = 0;                       // most Jacobi sweeps of one matrix in the last eig
   // per-point workspaces
   DevBuf R, M, piv, pts, status, work;
+  DevBuf Zst, Ust, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   // launch timing (pw_set_profiling)
   struct Rec { cudaEvent_t a, b; int kind; int count; };
   bool profiling = false;
@@ -241,8 +244,11 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
                        n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
-  for (int v : stat)
-    if (v != 0) return latch(ctx, PW_ENOTCONV);
+  ctx->last_sweeps = 0;
+  for (int i = 0; i < nmat; ++i) {
+    if (stat[i] < 0) return latch(ctx, PW_ENOTCONV);
+    ctx->last_sweeps = std::max(ctx->last_sweeps, stat[i]);
+  }
   for (int s = s0; s < s1; ++s) {
     ctx->slot_k[2 * s] = ks[s][0];
     ctx->slot_k[2 * s + 1] = ks[s][1];
@@ -328,6 +334,8 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
   if (!ctx) return PW_ENOMEM;
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->precision = d->precision;
+  if (d->refine_iters < -1 || d->refine_iters > 16) { delete ctx; return PW_EINVAL; }
+  ctx->refine_iters = d->precision == PW_MIXED_FP32 ? (d->refine_iters == 0 ? 2 : std::max(0, d->refine_iters)) : 0;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return PW_ECUDA; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   build_basis(d->a1, d->a2, d->ecut, d->ng_exact, ctx->b1, ctx->b2, ctx->mn, ctx->G);
@@ -431,8 +439,10 @@ void pw_destroy(pw_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
+
                   ctx->d_O, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
-                  ctx->pts.p, ctx->status.p, ctx->work.p};
+                  ctx->pts.p, ctx->status.p, ctx->work.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
+                  ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -449,7 +459,7 @@ pw_status pw_set_profiling(pw_ctx *ctx, int enable) {
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset) {
   if (!ctx || !out) return PW_EINVAL;
   CK(cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < 6; ++i) out[i] = 0.0;
+  for (int i = 0; i < 8; ++i) out[i] = 0.0;
   for (auto &r : ctx->recs) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
@@ -591,27 +601,53 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
     }
     if ((st = ensure_ksets(ctx, ks))) return st;
-    const int bmax = std::max(1, std::min((int)pts.size(), 3 * ctx->num_sms));
+    // point descriptors and the padded incident-column count of the chunk
+    std::vector<PointDesc> all(pts.size());
+    int nc = 1;
+    for (size_t i = 0; i < pts.size(); ++i) {
+      const int idx = pts[i].first, slot = pts[i].second;
+      bool th = false;
+      const int nL = count_open(ctx->EL[slot], E[idx], &th);
+      const int nR = count_open(ctx->ER[slot], E[idx], &th);
+      all[i] = PointDesc{E[idx], slot, nL, nR, idx, th ? 1 : 0};
+      if (th) result = PW_ETHRESH;
+      else nc = std::max(nc, nL);
+    }
+    nc = (nc + 3) & ~3;
+    const int ncols = 2 * n + nc;
+    const int N = ctx->N;
+    const bool refine = ctx->precision == PW_MIXED_FP32 && ctx->refine_iters > 0;
+    // per-point bytes of the sweep (+ refinement) buffers; the batch fits in 85 %
+    // of the free memory
+    size_t per_pt = nn * esz + (size_t)n * ncols * esz + n * sizeof(int) + 64;
+    if (refine)
+      per_pt += (size_t)(N + 1) * (nn + (size_t)n * nc) * sizeof(cc) +
+                (size_t)(2 * (N + 2) + 2 * (N + 1) + 1) * n * nc * sizeof(zc) + 2 * (size_t)n * nc * sizeof(cc);
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t have = free_b + ctx->R.bytes + ctx->M.bytes + ctx->Zst.bytes + ctx->Ust.bytes +
+                        ctx->Xa.bytes + ctx->Xb.bytes + ctx->Fr.bytes + ctx->Gr.bytes;
+    const int fit = (int)std::max<size_t>(1, (size_t)(0.85 * (double)have) / per_pt);
+    const int bmax = std::max(1, std::min({(int)pts.size(), 3 * ctx->num_sms, fit}));
     for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
       const int nb = (int)std::min(pts.size() - b0, (size_t)bmax);
-      std::vector<PointDesc> pd(nb);
-      int nc = 1;
-      for (int i = 0; i < nb; ++i) {
-        const int idx = pts[b0 + i].first, slot = pts[b0 + i].second;
-        bool th = false;
-        const int nL = count_open(ctx->EL[slot], E[idx], &th);
-        const int nR = count_open(ctx->ER[slot], E[idx], &th);
-        pd[i] = PointDesc{E[idx], slot, nL, nR, idx, th ? 1 : 0};
-        if (th) result = PW_ETHRESH;
-        else nc = std::max(nc, nL);
-      }
-      nc = (nc + 3) & ~3;
-      const int ncols = 2 * n + nc;
+      std::vector<PointDesc> pd(all.begin() + b0, all.begin() + b0 + nb);
       if ((st = ensure(ctx, ctx->R, (size_t)nb * nn * esz)) ||
           (st = ensure(ctx, ctx->M, (size_t)nb * n * ncols * esz)) ||
           (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
           (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
           (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
+        return st;
+      const size_t vec = (size_t)nb * n * nc;
+      if (refine &&
+          ((st = ensure(ctx, ctx->Zst, (size_t)nb * (N + 1) * nn * sizeof(cc))) ||
+           (st = ensure(ctx, ctx->Ust, (size_t)(N + 1) * vec * sizeof(cc))) ||
+           (st = ensure(ctx, ctx->Xa, (size_t)(N + 2) * vec * sizeof(zc))) ||
+           (st = ensure(ctx, ctx->Xb, (size_t)(N + 2) * vec * sizeof(zc))) ||
+           (st = ensure(ctx, ctx->Fr, (size_t)(N + 1) * vec * sizeof(zc))) ||
+           (st = ensure(ctx, ctx->Gr, (size_t)(N + 1) * vec * sizeof(zc))) ||
+           (st = ensure(ctx, ctx->carry, vec * sizeof(zc))) ||
+           (st = ensure(ctx, ctx->tmp, 2 * vec * sizeof(cc)))))
         return st;
       CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
       CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
@@ -625,15 +661,45 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.piv = (int *)ctx->piv.p;
       a.status = (int *)ctx->status.p;
       a.T = T_dev;
-      a.t = (zc *)t_dev;
+      a.t = refine ? nullptr : (zc *)t_dev;
       a.nopen = nopen_dev;
       a.err = err_dev;
       a.n = n;
-      a.N = ctx->N;
+      a.N = N;
       a.nc = nc;
-      Stage s0(ctx, 0, ctx->N + 1);
-      for (int p = 0; p <= ctx->N; ++p) CK(pw::launch_sweep(a, nb, p, ctx->precision, ctx->stream));
+      a.Zst = refine ? ctx->Zst.p : nullptr;
+      a.Ust = refine ? ctx->Ust.p : nullptr;
+      Stage s0(ctx, 0, N + 1);
+      for (int p = 0; p <= N; ++p) CK(pw::launch_sweep(a, nb, p, ctx->precision, ctx->stream));
       s0.done();
+      if (refine) {
+        pw::RefineArgs r;
+        r.pts = a.pts;
+        r.En = a.En;
+        r.O = a.O;
+        r.dz = a.dz;
+        r.Zst = (const cc *)ctx->Zst.p;
+        r.Ust = (cc *)ctx->Ust.p;
+        r.M = (cc *)ctx->M.p;
+        r.piv = a.piv;
+        r.status = a.status;
+        r.Xa = (zc *)ctx->Xa.p;
+        r.Xb = (zc *)ctx->Xb.p;
+        r.Fr = (zc *)ctx->Fr.p;
+        r.Gr = (zc *)ctx->Gr.p;
+        r.carry = (zc *)ctx->carry.p;
+        r.tmp = (cc *)ctx->tmp.p;
+        r.T = T_dev;
+        r.t = (zc *)t_dev;
+        r.nopen = nopen_dev;
+        r.err = err_dev;
+        r.n = n;
+        r.N = N;
+        r.nc = nc;
+        Stage s3(ctx, 3, 1);
+        CK(pw::launch_refine(r, nb, ctx->refine_iters, ctx->stream));
+        s3.done();
+      }
       std::vector<int> st_h(nb);
       CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));

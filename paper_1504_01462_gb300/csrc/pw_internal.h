@@ -52,19 +52,47 @@ struct SweepArgs {
   int *nopen;
   double *err;
   int n, N, nc;
+  void *Zst;             // FP32 sweep with refinement: per point (N+1) x n x n  (Z_p)
+  void *Ust;             // per point (N+1) x n x nc  (u_p)
+};
+
+// Buffers of the FP64 refinement around the FP32 sweep (pw_refine.cu).
+struct RefineArgs {
+  const PointDesc *pts;
+  const double *En;
+  const zc *O;
+  const double *dz;
+  const cc *Zst;         // per point (N+1) x n x n
+  cc *Ust;               // per point (N+1) x n x nc
+  cc *M;                 // per point n x (n + nc)
+  int *piv;
+  int *status;
+  zc *Xa, *Xb;           // per point (N+2) x n x nc amplitudes (FP64)
+  zc *Fr, *Gr;           // per point (N+1) x n x nc residuals (FP64)
+  zc *carry;             // per point n x nc
+  cc *tmp;               // per point 2n x nc
+  double *T;
+  zc *t;
+  int *nopen;
+  double *err;
+  int n, N, nc;
 };
 
 // potential tables and slice Hamiltonians
 void launch_tables(const TableArgs &a, cudaStream_t s);
 void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, double kx, double ky,
                        int n, int nq, int Dm, int Dn, cudaStream_t s);
-// batched Hermitian eigensolver: H (in) -> U (out, same buffer); V scratch
+// batched Hermitian eigensolver: H (in) -> U (out, same buffer); V scratch of
+// the same size; status: Jacobi sweeps per matrix (negative: not converged)
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s);
 // O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s);
 // one interface of the left-to-right sweep for every point of a batch
 cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
 size_t sweep_smem_bytes(int n, int precision);
+// FP64 refinement of an FP32 sweep that stored Z_p and u_p (iters >= 1)
+cudaError_t launch_refine(const RefineArgs &a, int npts, int iters, cudaStream_t s);
+size_t refine_smem_bytes(int n);
 // explicit interface S-matrices (FP64)
 cudaError_t launch_slice_smatrix(const PointDesc *pts, const double *En, const zc *O, const double *dz,
                                  zc *work, int *piv, int *status, zc *S, int n, int N, int iface,

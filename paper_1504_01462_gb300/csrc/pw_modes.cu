@@ -110,50 +110,58 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
 // makes (J^H A J)_pq = 0 with new diagonal a_pp - t|b|, a_qq + t|b|.  Each round
 // applies n/2 disjoint rotations: columns of A and V first (A J, V J), then
 // rows of A (J^H (A J)).  Sweeps continue until the largest |a_pq| met in a
-// sweep is below 1e-12 max|A|.
+// sweep is below conv_rel * max|A| (1e-12 in FP64; convergence is quadratic,
+// so the last sweep leaves off-diagonals at rounding level).  Each round
+// streams A and V through L2/HBM, so the kernel is bandwidth-bound.
 // ---------------------------------------------------------------------------
 constexpr int EIG_THREADS = 512;
 
-__global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_all, double *En_all,
-                                                            int *status, int n, int max_sweeps) {
-  extern __shared__ unsigned char smraw[];
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EIG_THREADS)
+    k_jacobi(cx<T> *A_all, cx<T> *V_all, size_t stride, int n, int init_identity, int max_sweeps,
+             double conv_rel, int *sweeps_out, double *En_all, zc *U_all) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int mat = blockIdx.x;
-  zc *A = HU_all + (size_t)mat * n * n;
-  zc *V = V_all + (size_t)mat * n * n;
-  double *En = En_all + (size_t)mat * n;
+  cx<T> *A = A_all + (size_t)mat * stride;
+  cx<T> *V = V_all + (size_t)mat * stride;
   const int m = (n + 1) & ~1;
   const int np = m / 2;
   const int tid = threadIdx.x;
-  // shared layout
-  double *sc = reinterpret_cast<double *>(smraw);   // c
-  double *ss = sc + np;                              // s
-  double *sdp = ss + np;                             // new a_pp
-  double *sdq = sdp + np;                            // new a_qq
-  zc *sph = reinterpret_cast<zc *>(sdq + np);        // e^{-i phi}
+  T *sc = reinterpret_cast<T *>(smraw);   // c
+  T *ss = sc + np;                         // s
+  T *sdp = ss + np;                        // new a_pp
+  T *sdq = sdp + np;                       // new a_qq
+  cx<T> *sph = reinterpret_cast<cx<T> *>(smraw + (size_t)4 * np * sizeof(double));  // e^{-i phi}
   int *sp = reinterpret_cast<int *>(sph + np);
   int *sq = sp + np;
   int *sskip = sq + np;
   double *slam = reinterpret_cast<double *>(sskip + np + (np & 1));
+  int *srank = reinterpret_cast<int *>(slam + n);
   __shared__ unsigned long long s_off;
   __shared__ unsigned long long s_amax;
 
-  for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) {
-    const int i = e % n, j = e / n;
-    V[e] = mkc<double>(i == j ? 1.0 : 0.0, 0.0);
-  }
+  if (init_identity)
+    for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) {
+      const int i = e % n, j = e / n;
+      V[e] = mkc<T>(i == j ? T(1) : T(0), T(0));
+    }
   if (tid == 0) s_amax = 0ull;
   __syncthreads();
   {
     double am = 0.0;
-    for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) am = fmax(am, cabs1(A[e]));
-    atomicMax(&s_amax, (unsigned long long)__double_as_longlong(am));
+    for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) am = fmax(am, (double)cabs1(A[e]));
+    atomic_max_pos(&s_amax, am);
   }
   __syncthreads();
   const double amax = fmax(__longlong_as_double((long long)s_amax), 1e-300);
   const double rot_thresh = 1e-18 * amax;
-  const double conv = 1e-12 * amax;
-  int converged = 0;
-  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+  const double conv = conv_rel * amax;
+  int converged = 0, sweep = 0;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_off = 0ull;
     __syncthreads();
     for (int r = 0; r < m - 1; ++r) {
@@ -171,17 +179,17 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_al
         sq[k] = q;
         int skip = 1;
         if (q < n) {
-          const double app = A[p + (size_t)p * n].re, aqq = A[q + (size_t)q * n].re;
-          const zc apq = A[p + (size_t)q * n];
-          const double mag = hypot(apq.re, apq.im);
-          if (mag > 0.0) atomicMax(&s_off, (unsigned long long)__double_as_longlong(mag));
-          if (mag > rot_thresh) {
-            const double theta = (aqq - app) / (2.0 * mag);
-            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0);
+          const T app = A[p + (size_t)p * n].re, aqq = A[q + (size_t)q * n].re;
+          const cx<T> apq = A[p + (size_t)q * n];
+          const T mag = hypot(apq.re, apq.im);
+          if (mag > T(0)) atomic_max_pos(&s_off, (double)mag);
+          if ((double)mag > rot_thresh) {
+            const T theta = (aqq - app) / (T(2) * mag);
+            const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+            const T c = T(1) / sqrt(t * t + T(1));
             sc[k] = c;
             ss[k] = t * c;
-            sph[k] = mkc<double>(apq.re / mag, -apq.im / mag);
+            sph[k] = mkc<T>(apq.re / mag, -apq.im / mag);
             sdp[k] = app - t * mag;
             sdq[k] = aqq + t * mag;
             skip = 0;
@@ -195,17 +203,17 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_al
         const int k = e / n, i = e % n;
         if (sskip[k]) continue;
         const int p = sp[k], q = sq[k];
-        const double c = sc[k], s = ss[k];
-        const zc ph = sph[k];
+        const T c = sc[k], s = ss[k];
+        const cx<T> ph = sph[k];
         {
-          const zc x = A[i + (size_t)p * n], y = cmul(ph, A[i + (size_t)q * n]);
-          A[i + (size_t)p * n] = mkc<double>(c * x.re - s * y.re, c * x.im - s * y.im);
-          A[i + (size_t)q * n] = mkc<double>(s * x.re + c * y.re, s * x.im + c * y.im);
+          const cx<T> x = A[i + (size_t)p * n], y = cmul(ph, A[i + (size_t)q * n]);
+          A[i + (size_t)p * n] = mkc<T>(c * x.re - s * y.re, c * x.im - s * y.im);
+          A[i + (size_t)q * n] = mkc<T>(s * x.re + c * y.re, s * x.im + c * y.im);
         }
         {
-          const zc x = V[i + (size_t)p * n], y = cmul(ph, V[i + (size_t)q * n]);
-          V[i + (size_t)p * n] = mkc<double>(c * x.re - s * y.re, c * x.im - s * y.im);
-          V[i + (size_t)q * n] = mkc<double>(s * x.re + c * y.re, s * x.im + c * y.im);
+          const cx<T> x = V[i + (size_t)p * n], y = cmul(ph, V[i + (size_t)q * n]);
+          V[i + (size_t)p * n] = mkc<T>(c * x.re - s * y.re, c * x.im - s * y.im);
+          V[i + (size_t)q * n] = mkc<T>(s * x.re + c * y.re, s * x.im + c * y.im);
         }
       }
       __syncthreads();
@@ -214,18 +222,18 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_al
         const int k = e / n, j = e % n;
         if (sskip[k]) continue;
         const int p = sp[k], q = sq[k];
-        const double c = sc[k], s = ss[k];
-        const zc phc = cconj(sph[k]);
+        const T c = sc[k], s = ss[k];
+        const cx<T> phc = cconj(sph[k]);
         if (j == p) {
-          A[p + (size_t)p * n] = mkc<double>(sdp[k], 0.0);
-          A[q + (size_t)p * n] = czero<double>();
+          A[p + (size_t)p * n] = mkc<T>(sdp[k], T(0));
+          A[q + (size_t)p * n] = czero<T>();
         } else if (j == q) {
-          A[q + (size_t)q * n] = mkc<double>(sdq[k], 0.0);
-          A[p + (size_t)q * n] = czero<double>();
+          A[q + (size_t)q * n] = mkc<T>(sdq[k], T(0));
+          A[p + (size_t)q * n] = czero<T>();
         } else {
-          const zc x = A[p + (size_t)j * n], y = cmul(phc, A[q + (size_t)j * n]);
-          A[p + (size_t)j * n] = mkc<double>(c * x.re - s * y.re, c * x.im - s * y.im);
-          A[q + (size_t)j * n] = mkc<double>(s * x.re + c * y.re, s * x.im + c * y.im);
+          const cx<T> x = A[p + (size_t)j * n], y = cmul(phc, A[q + (size_t)j * n]);
+          A[p + (size_t)j * n] = mkc<T>(c * x.re - s * y.re, c * x.im - s * y.im);
+          A[q + (size_t)j * n] = mkc<T>(s * x.re + c * y.re, s * x.im + c * y.im);
         }
       }
       __syncthreads();
@@ -233,8 +241,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_al
     converged = __longlong_as_double((long long)s_off) <= conv;
     __syncthreads();
   }
-  // eigenvalues, ascending with ties by index; U columns replace H
-  for (int i = tid; i < n; i += EIG_THREADS) slam[i] = A[i + (size_t)i * n].re;
+  if (tid == 0) sweeps_out[mat] = converged ? sweep : -1;
+  if (!En_all) return;
+  // eigenvalues ascending (ties by index); eigenvector columns written to U
+  double *En = En_all + (size_t)mat * n;
+  zc *U = U_all + (size_t)mat * n * n;
+  for (int i = tid; i < n; i += EIG_THREADS) slam[i] = (double)A[i + (size_t)i * n].re;
   __syncthreads();
   for (int i = tid; i < n; i += EIG_THREADS) {
     const double li = slam[i];
@@ -244,24 +256,29 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi_eig(zc *HU_all, zc *V_al
       rank += (lj < li) || (lj == li && j < i);
     }
     En[rank] = li;
-    // the rank goes to the (now unused) rotation arrays: 2*np >= n ints fit in sc
-    reinterpret_cast<int *>(sc)[i] = rank;
+    srank[i] = rank;
   }
   __syncthreads();
-  const int *rk = reinterpret_cast<const int *>(sc);
   for (size_t e = tid; e < (size_t)n * n; e += EIG_THREADS) {
     const int i = e % n, j = e / n;
-    A[i + (size_t)rk[j] * n] = V[e];
+    U[i + (size_t)srank[j] * n] = ccast<double>(V[e]);
   }
-  if (tid == 0) status[mat] = converged ? 0 : 1;
 }
 
-void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s) {
+template <typename T>
+size_t jacobi_smem(int n) {
   const int np = ((n + 1) & ~1) / 2;
-  const size_t smem = (size_t)np * (4 * sizeof(double) + sizeof(zc) + 3 * sizeof(int)) + 8 +
-                      (size_t)n * sizeof(double) + 64;
-  cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_jacobi_eig<<<nmat, EIG_THREADS, smem, s>>>(HU, V, En, status, n, 40);
+  return (size_t)4 * np * sizeof(double) + (size_t)np * sizeof(zc) + (size_t)(3 * np + 2) * sizeof(int) +
+         (size_t)n * (sizeof(double) + sizeof(int)) + 64;
+}
+
+// HU: in H, out U; V: scratch of the same size; status: sweeps used per
+// matrix (negative: not converged).
+void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s) {
+  const size_t sm64 = jacobi_smem<double>(n);
+  cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64);
+  k_jacobi<double><<<nmat, EIG_THREADS, sm64, s>>>(HU, V, (size_t)n * n, n, 1, 40, 1e-12, status,
+                                                    En, HU);
 }
 
 // ---------------------------------------------------------------------------

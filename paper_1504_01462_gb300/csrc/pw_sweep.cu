@@ -146,6 +146,13 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a, int p) {
   }
   // W [Z_Y | Z_T] = [Y | Tacc]
   cta_lu_solve<T>(M, n, n, ncols, piv, s.gemm, s.sval, s.sidx, s.flag);
+  // keep Z_Y and u = Z_T for the refinement's backward pass
+  if (a.Zst) {
+    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)pt * (N + 1) + p) * n * n;
+    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)pt * (N + 1) + p) * n * nc;
+    for (size_t e = tid; e < (size_t)n * n; e += NT) Zs[e] = M[(size_t)n * n + e];
+    for (size_t e = tid; e < (size_t)n * nc; e += NT) Us[e] = M[(size_t)2 * n * n + e];
+  }
   // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
   for (size_t e = tid; e < (size_t)n * n; e += NT) {
     const int i = e % n, j = e / n;

@@ -32,17 +32,19 @@ def _dev(shape, dtype):
     return torch.zeros(shape, dtype=dtype, device="cuda")
 
 
-def _gpu_T(pw, inst, precision=0, E=None, k=None, with_t=False):
+def _gpu_T(pw, inst, precision=0, E=None, k=None, with_t=False, refine_iters=0, with_err=False):
     E = inst.energies if E is None else E
     k = inst.kpar if k is None else k
-    with pw.Context.from_instance(inst, precision=precision) as ctx:
+    with pw.Context.from_instance(inst, precision=precision, refine_iters=refine_iters) as ctx:
         n = ctx.ng
         T = _dev(len(E), torch.float64)
         t = _dev((len(E), n, n), torch.complex128) if with_t else None
         nop = _dev((len(E), 2), torch.int32)
-        ctx.transmission(E, k, T, t, nop)
+        err = _dev(len(E), torch.float64)
+        ctx.transmission(E, k, T, t, nop, err)
         torch.cuda.synchronize()
-        return T.cpu().numpy(), (t.cpu().numpy() if with_t else None), nop.cpu().numpy()
+        out = (T.cpu().numpy(), (t.cpu().numpy() if with_t else None), nop.cpu().numpy())
+        return out + (err.cpu().numpy(),) if with_err else out
 
 
 def _rel(a, b):
@@ -271,12 +273,56 @@ def test_empty_call(pw):
 
 
 # ---------------------------------------------------------------------------
-# mixed form (FP32 sweep)
+# mixed form: FP32 sweep, then FP64 iterative refinement of the whole system
 # ---------------------------------------------------------------------------
-def test_transmission_mixed_fp32_minimal_cell(pw):
+TOL_MIXED = 1e-8
+
+
+def test_transmission_mixed_fp32_unrefined(pw):
+    """The plain FP32 sweep (no refinement) is accurate to FP32 level only."""
     E = np.array([0.5, 2.3, 3.9, 5.5])
     k = np.array([[0.0, 0.0], [0.1, -0.2], [0.1, -0.2], [0.0, 0.0]])
     inst = minimal_cell(energies=E, kpar=k)
     ref = O.transmission(inst)
-    got, _, _ = _gpu_T(pw, inst, 1)
+    got, _, _ = _gpu_T(pw, inst, 1, refine_iters=-1)
     assert np.all(_rel(got, ref) < 1e-4), (got, ref)
+
+
+def test_transmission_mixed_refined_minimal_cell(pw):
+    E = np.array([0.5, 2.3, 3.9, 5.5, 2.3])
+    k = np.array([[0.0, 0.0], [0.1, -0.2], [0.1, -0.2], [0.0, 0.0], [-0.3, 0.25]])
+    inst = minimal_cell(energies=E, kpar=k)
+    ref, ref_t = O.transmission(inst, return_t=True)
+    got, t, _, err = _gpu_T(pw, inst, 1, with_t=True, with_err=True)
+    assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
+    assert np.all((err >= 0) & (err < 1e-6)), err
+    for i in range(len(E)):
+        nR, nL = ref_t[i].shape
+        assert np.abs(t[i].T[:nR, :nL] - ref_t[i]).max() < 1e-8
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_transmission_mixed_refined_junction(pw, iters):
+    inst = junction(ng=97, n_slices=60, n_e=4, n_k=4)
+    sel = [1, 2, 5, 6, 9, 10]
+    ref = O.transmission(inst, points=sel)
+    got, _, _ = _gpu_T(pw, inst, 1, E=inst.energies[sel], k=inst.kpar[sel], refine_iters=iters)
+    assert np.all(_rel(got, ref) < TOL_MIXED), (iters, got, ref)
+
+
+def test_transmission_mixed_refined_random_tables(pw):
+    rng = np.random.default_rng(7)
+    a = 4.0
+    b = 2 * math.pi / a
+    half = (6, 6)
+    nsl = 11
+    tabs = random_tables(rng, nsl, half, 0.3)
+    lt = random_tables(rng, 2, half, 0.2)
+    z = np.concatenate([[0.0], np.cumsum(rng.uniform(0.1, 0.5, nsl))])
+    E = rng.uniform(0.5, 6.0, 5)
+    kp = rng.uniform(-0.5, 0.5, (5, 2))
+    inst = explicit_tables([a, 0], [0, a], 10.0 * b * b * (1 + 1e-9), z, tabs, lt[0], lt[1],
+                           half, E, kp)
+    ref = O.transmission(inst)
+    got, _, _ = _gpu_T(pw, inst, 1)
+    assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
