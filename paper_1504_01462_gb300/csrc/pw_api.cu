@@ -56,7 +56,7 @@ struct pw_ctx {
   int last_sweeps = 0;                       // most Jacobi sweeps of one matrix in the last eig
   // per-point workspaces
   DevBuf R, M, piv, pts, status, work;
-  DevBuf Zst, Ust, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
+  DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   // launch timing (pw_set_profiling)
   struct Rec { cudaEvent_t a, b; int kind; int count; };
   bool profiling = false;
@@ -442,7 +442,8 @@ void pw_destroy(pw_ctx *ctx) {
 
                   ctx->d_O, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
-                  ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p};
+                  ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
+                  ctx->PIVst.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -621,11 +622,12 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
     // of the free memory
     size_t per_pt = nn * esz + (size_t)n * ncols * esz + n * sizeof(int) + 64;
     if (refine)
-      per_pt += (size_t)(N + 1) * (nn + (size_t)n * nc) * sizeof(cc) +
+      per_pt += (size_t)(N + 1) * (2 * nn + (size_t)n * nc) * sizeof(cc) + (size_t)(N + 1) * n * sizeof(int) +
                 (size_t)(2 * (N + 2) + 2 * (N + 1) + 1) * n * nc * sizeof(zc) + 2 * (size_t)n * nc * sizeof(cc);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     const size_t have = free_b + ctx->R.bytes + ctx->M.bytes + ctx->Zst.bytes + ctx->Ust.bytes +
+                        ctx->LUst.bytes + ctx->PIVst.bytes +
                         ctx->Xa.bytes + ctx->Xb.bytes + ctx->Fr.bytes + ctx->Gr.bytes;
     const int fit = (int)std::max<size_t>(1, (size_t)(0.85 * (double)have) / per_pt);
     const int bmax = std::max(1, std::min({(int)pts.size(), 3 * ctx->num_sms, fit}));
@@ -641,6 +643,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       const size_t vec = (size_t)nb * n * nc;
       if (refine &&
           ((st = ensure(ctx, ctx->Zst, (size_t)nb * (N + 1) * nn * sizeof(cc))) ||
+           (st = ensure(ctx, ctx->LUst, (size_t)nb * (N + 1) * nn * sizeof(cc))) ||
+           (st = ensure(ctx, ctx->PIVst, (size_t)nb * (N + 1) * n * sizeof(int))) ||
            (st = ensure(ctx, ctx->Ust, (size_t)(N + 1) * vec * sizeof(cc))) ||
            (st = ensure(ctx, ctx->Xa, (size_t)(N + 2) * vec * sizeof(zc))) ||
            (st = ensure(ctx, ctx->Xb, (size_t)(N + 2) * vec * sizeof(zc))) ||
@@ -669,6 +673,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.nc = nc;
       a.Zst = refine ? ctx->Zst.p : nullptr;
       a.Ust = refine ? ctx->Ust.p : nullptr;
+      a.LUst = refine ? ctx->LUst.p : nullptr;
+      a.PIVst = refine ? (int *)ctx->PIVst.p : nullptr;
       Stage s0(ctx, 0, N + 1);
       for (int p = 0; p <= N; ++p) CK(pw::launch_sweep(a, nb, p, ctx->precision, ctx->stream));
       s0.done();
@@ -680,6 +686,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.dz = a.dz;
         r.Zst = (const cc *)ctx->Zst.p;
         r.Ust = (cc *)ctx->Ust.p;
+        r.LUst = (const cc *)ctx->LUst.p;
+        r.PIVst = (const int *)ctx->PIVst.p;
         r.M = (cc *)ctx->M.p;
         r.piv = a.piv;
         r.status = a.status;

@@ -12,35 +12,35 @@ namespace pw {
 
 constexpr int NT = 256;   // threads per CTA for every per-point kernel
 
-template <typename T>
-struct Tile;
-template <>
-struct Tile<double> {
-  static constexpr int BM = 64, BN = 64, BK = 16, NB = 32;
-};
-template <>
-struct Tile<float> {
-  static constexpr int BM = 64, BN = 64, BK = 16, NB = 32;
+// GEMM tile (BM x BN x BK, 4 x 4 complex micro-tiles) and LU panel width NB
+// for a CTA of NTH threads.
+template <typename T, int NTH = NT>
+struct Tile {
+  static constexpr int BM = NTH >= 512 ? 128 : 64, BN = 64, BK = 16, NB = 32;
 };
 
-template <typename T>
+template <typename T, int NTH = NT>
 __host__ __device__ constexpr size_t gemm_smem_elems() {
-  return size_t(Tile<T>::BK) * (Tile<T>::BM + 1) + size_t(Tile<T>::BK) * (Tile<T>::BN + 1);
+  return size_t(Tile<T, NTH>::BK) * (Tile<T, NTH>::BM + 1) +
+         size_t(Tile<T, NTH>::BK) * (Tile<T, NTH>::BN + 1);
 }
 
 // C(i,j) = fe(i, j, sum_l fa(i,l) fb(l,j)) for 0 <= i < m, 0 <= j < n, 0 <= l < k.
 // fa/fb return cx<T>; fa is read with i fastest (A column-major), fb with l
 // fastest (B column-major), so plain column-major operands load coalesced.
-// smem must hold gemm_smem_elems<T>() elements.
-template <typename T, class FA, class FB, class FE>
-__device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) {
-  constexpr int BM = Tile<T>::BM, BN = Tile<T>::BN, BK = Tile<T>::BK;
-  constexpr int TM = BM / 16, TN = BN / 16;
+// Tile BM x BN x BK; each of the NTH threads owns a (BM/TY) x TN micro-tile with
+// TX = BN/TN threads along N and TY = NTH/TX along M.  smem must hold
+// BK*(BM+1) + BK*(BN+1) elements.
+template <typename T, int BM, int BN, int BK, int TN, int NTH, class FA, class FB, class FE>
+__device__ void cta_gemm_t(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) {
+  constexpr int NT = NTH;
+  constexpr int TX = BN / TN, TY = NT / TX, TM = BM / TY;
+  static_assert(TX * TN == BN && TY * TM == BM && TX * TY == NT, "tile shape");
   constexpr int LDA = BM + 1, LDB = BN + 1;
-  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;   // staged elements per thread
+  constexpr int LA = (BM * BK + NT - 1) / NT, LB = (BK * BN + NT - 1) / NT;
   cx<T> *As = smem;
   cx<T> *Bs = smem + BK * LDA;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   const int tilesM = (m + BM - 1) / BM, tilesN = (n + BN - 1) / BN;
   for (int t = 0; t < tilesM * tilesN; ++t) {
     const int i0 = (t % tilesM) * BM, j0 = (t / tilesM) * BN;
@@ -56,13 +56,13 @@ __device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) 
       for (int q = 0; q < LA; ++q) {
         const int e = tid + q * NT, ii = e % BM, ll = e / BM;
         const int i = i0 + ii, l = l0 + ll;
-        ra[q] = (i < m && l < k) ? fa(i, l) : czero<T>();
+        ra[q] = (e < BM * BK && i < m && l < k) ? fa(i, l) : czero<T>();
       }
 #pragma unroll
       for (int q = 0; q < LB; ++q) {
         const int e = tid + q * NT, ll = e % BK, jj = e / BK;
         const int l = l0 + ll, j = j0 + jj;
-        rb[q] = (l < k && j < n) ? fb(l, j) : czero<T>();
+        rb[q] = (e < BK * BN && l < k && j < n) ? fb(l, j) : czero<T>();
       }
     };
     fetch(0);
@@ -70,12 +70,12 @@ __device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) 
 #pragma unroll
       for (int q = 0; q < LA; ++q) {
         const int e = tid + q * NT;
-        As[(e / BM) * LDA + e % BM] = ra[q];
+        if (e < BM * BK) As[(e / BM) * LDA + e % BM] = ra[q];
       }
 #pragma unroll
       for (int q = 0; q < LB; ++q) {
         const int e = tid + q * NT;
-        Bs[(e % BK) * LDB + e / BK] = rb[q];
+        if (e < BK * BN) Bs[(e % BK) * LDB + e / BK] = rb[q];
       }
       __syncthreads();
       if (l0 + BK < k) fetch(l0 + BK);
@@ -83,9 +83,9 @@ __device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) 
       for (int ll = 0; ll < BK; ++ll) {
         cx<T> a[TM], b[TN];
 #pragma unroll
-        for (int r = 0; r < TM; ++r) a[r] = As[ll * LDA + ty + 16 * r];
+        for (int r = 0; r < TM; ++r) a[r] = As[ll * LDA + ty + TY * r];
 #pragma unroll
-        for (int c = 0; c < TN; ++c) b[c] = Bs[ll * LDB + tx + 16 * c];
+        for (int c = 0; c < TN; ++c) b[c] = Bs[ll * LDB + tx + TX * c];
 #pragma unroll
         for (int r = 0; r < TM; ++r)
 #pragma unroll
@@ -97,11 +97,28 @@ __device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) 
     for (int r = 0; r < TM; ++r)
 #pragma unroll
       for (int c = 0; c < TN; ++c) {
-        const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+        const int i = i0 + ty + TY * r, j = j0 + tx + TX * c;
         if (i < m && j < n) fe(i, j, acc[r][c]);
       }
   }
   __syncthreads();
+}
+
+template <typename T, int NTH = NT, class FA, class FB, class FE>
+__device__ void cta_gemm(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) {
+  cta_gemm_t<T, Tile<T, NTH>::BM, Tile<T, NTH>::BN, Tile<T, NTH>::BK, 4, NTH>(m, n, k, fa, fb, fe, smem);
+}
+
+// Tall-skinny product (n <= 16 columns per tile): 128 x 16 tiles.
+constexpr int SKINNY_BM = 128, SKINNY_BN = 16, SKINNY_BK = 16;
+template <typename T>
+__host__ __device__ constexpr size_t skinny_smem_elems() {
+  return size_t(SKINNY_BK) * (SKINNY_BM + 1) + size_t(SKINNY_BK) * (SKINNY_BN + 1);
+}
+template <typename T, int NTH = NT, class FA, class FB, class FE>
+__device__ void cta_gemm_skinny(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) {
+  constexpr int TNS = NTH / 256;   // 1 column per thread at 256 threads, 2 at 512
+  cta_gemm_t<T, SKINNY_BM, SKINNY_BN, SKINNY_BK, (TNS < 1 ? 1 : TNS), NTH>(m, n, k, fa, fb, fe, smem);
 }
 
 // Plain column-major operand accessors.
@@ -114,8 +131,9 @@ struct ColMajor {
 
 // Block-wide arg-max of a per-thread (value, index) pair; returns the winning
 // index to every thread.  Ties go to the smaller index.
-template <typename T>
+template <typename T, int NTH = NT>
 __device__ int block_argmax(T v, int idx, T *sval, int *sidx) {
+  constexpr int NT = NTH;
   for (int off = 16; off > 0; off >>= 1) {
     T ov = __shfl_down_sync(0xffffffffu, v, off);
     int oi = __shfl_down_sync(0xffffffffu, idx, off);
@@ -152,12 +170,13 @@ __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
 // columns [n, ncols).  Partial (row) pivoting; A is overwritten by its LU
 // factors, B by X.  `flag` (shared, per CTA) gets bit 1 on a zero pivot.
 // smem: gemm_smem_elems<T>() + NB*NB complex, plus sval/sidx scratch.
-template <typename T>
+template <typename T, int NTH = NT>
 __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T> *smem,
                              T *sval, int *sidx, int *flag) {
-  constexpr int NB = Tile<T>::NB;
+  constexpr int NT = NTH;
+  constexpr int NB = Tile<T, NTH>::NB;
   const int tid = threadIdx.x;
-  cx<T> *Ls = smem + gemm_smem_elems<T>();   // NB x NB staging
+  cx<T> *Ls = smem + gemm_smem_elems<T, NTH>();   // NB x NB staging
   for (int j0 = 0; j0 < n; j0 += NB) {
     const int nb = min(NB, n - j0);
     // ---- unblocked panel factorisation, columns j0..j0+nb-1, rows j0..n-1
@@ -168,7 +187,7 @@ __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T>
         const T v = cabs1(M[i + (size_t)j * ld]);
         if (v > best) { best = v; bi = i; }
       }
-      const int p = block_argmax<T>(best, bi, sval, sidx);
+      const int p = block_argmax<T, NTH>(best, bi, sval, sidx);
       if (tid == 0) piv[j] = p;
       if (p != j) {
         for (int c = j0 + tid; c < j0 + nb; c += NT) {
@@ -224,7 +243,7 @@ __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T>
     // ---- trailing update M[c0:, c0:] -= L21 U12
     if (c0 < n && c0 < ncols) {
       cx<T> *Mp = M;
-      cta_gemm<T>(
+      cta_gemm<T, NTH>(
           n - c0, ncols - c0, nb,
           [=](int i, int l) { return Mp[c0 + i + (size_t)(j0 + l) * ld]; },
           [=](int l, int j) { return Mp[j0 + l + (size_t)(c0 + j) * ld]; },
@@ -259,12 +278,94 @@ __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T>
     __syncthreads();
     if (j0 > 0) {
       cx<T> *Mp = M;
-      cta_gemm<T>(
+      cta_gemm<T, NTH>(
           j0, ncols - n, nb,
           [=](int i, int l) { return Mp[i + (size_t)(j0 + l) * ld]; },
           [=](int l, int j) { return Mp[j0 + l + (size_t)(n + j) * ld]; },
           [=](int i, int j, cx<T> acc) {
             cx<T> &v = Mp[i + (size_t)(n + j) * ld];
+            v = csub(v, acc);
+          },
+          smem);
+    }
+  }
+  __syncthreads();
+}
+
+// Applies a factorisation made by cta_lu_solve (LU held in the n x n
+// column-major block `LU`, row swaps `piv`) to new right-hand sides B (n x nrhs,
+// leading dimension ldb): replays the same panel-by-panel elimination, then
+// back-substitutes, so B <- A^{-1} B.  smem: skinny_smem_elems + NB*NB.
+template <typename T, int NTH = NT>
+__device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, int ldb, int nrhs,
+                              cx<T> *smem) {
+  constexpr int NT = NTH;
+  constexpr int NB = Tile<T, NTH>::NB;
+  const int tid = threadIdx.x;
+  cx<T> *Ls = smem + skinny_smem_elems<T>();
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int nb = min(NB, n - j0);
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e % nb, s = e / nb;
+      Ls[r + s * NB] = LU[j0 + r + (size_t)(j0 + s) * n];
+    }
+    __syncthreads();
+    for (int c = tid; c < nrhs; c += NT) {
+      cx<T> *col = B + (size_t)c * ldb + j0;
+      for (int r = 0; r < nb; ++r) {
+        const int p = piv[j0 + r] - j0;
+        if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
+      }
+      for (int r = 1; r < nb; ++r) {
+        cx<T> x = col[r];
+        for (int s2 = 0; s2 < r; ++s2) {
+          const cx<T> l = Ls[r + s2 * NB], y = col[s2];
+          x.re -= l.re * y.re - l.im * y.im;
+          x.im -= l.re * y.im + l.im * y.re;
+        }
+        col[r] = x;
+      }
+    }
+    __syncthreads();
+    if (j0 + nb < n) {
+      const int c0 = j0 + nb;
+      cta_gemm_skinny<T, NTH>(
+          n - c0, nrhs, nb, [=](int i, int l) { return LU[c0 + i + (size_t)(j0 + l) * n]; },
+          [=](int l, int j) { return B[j0 + l + (size_t)j * ldb]; },
+          [=](int i, int j, cx<T> acc) {
+            cx<T> &v = B[c0 + i + (size_t)j * ldb];
+            v = csub(v, acc);
+          },
+          smem);
+    }
+  }
+  const int jlast = ((n - 1) / NB) * NB;
+  for (int j0 = jlast; j0 >= 0; j0 -= NB) {
+    const int nb = min(NB, n - j0);
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e % nb, s = e / nb;
+      Ls[r + s * NB] = LU[j0 + r + (size_t)(j0 + s) * n];
+    }
+    __syncthreads();
+    for (int c = tid; c < nrhs; c += NT) {
+      cx<T> *col = B + (size_t)c * ldb + j0;
+      for (int r = nb - 1; r >= 0; --r) {
+        cx<T> x = col[r];
+        for (int s2 = r + 1; s2 < nb; ++s2) {
+          const cx<T> u = Ls[r + s2 * NB], y = col[s2];
+          x.re -= u.re * y.re - u.im * y.im;
+          x.im -= u.re * y.im + u.im * y.re;
+        }
+        col[r] = cdiv(x, Ls[r + r * NB]);
+      }
+    }
+    __syncthreads();
+    if (j0 > 0) {
+      cta_gemm_skinny<T, NTH>(
+          j0, nrhs, nb, [=](int i, int l) { return LU[i + (size_t)(j0 + l) * n]; },
+          [=](int l, int j) { return B[j0 + l + (size_t)j * ldb]; },
+          [=](int i, int j, cx<T> acc) {
+            cx<T> &v = B[i + (size_t)j * ldb];
             v = csub(v, acc);
           },
           smem);

@@ -54,6 +54,8 @@ struct SweepArgs {
   int n, N, nc;
   void *Zst;             // FP32 sweep with refinement: per point (N+1) x n x n  (Z_p)
   void *Ust;             // per point (N+1) x n x nc  (u_p)
+  void *LUst;            // per point (N+1) x n x n  (LU factors of W_p)
+  int *PIVst;            // per point (N+1) x n      (row swaps of W_p)
 };
 
 // Buffers of the FP64 refinement around the FP32 sweep (pw_refine.cu).
@@ -64,6 +66,8 @@ struct RefineArgs {
   const double *dz;
   const cc *Zst;         // per point (N+1) x n x n
   cc *Ust;               // per point (N+1) x n x nc
+  const cc *LUst;        // per point (N+1) x n x n
+  const int *PIVst;      // per point (N+1) x n
   cc *M;                 // per point n x (n + nc)
   int *piv;
   int *status;

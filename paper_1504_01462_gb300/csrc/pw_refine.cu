@@ -16,8 +16,8 @@
 // and a backward pass recovers every amplitude:
 //     a_q = Z_p e_q b_q + u_p,   b_p = Q_p a_q + P_p e_q b_q + g_p.
 // Refinement: x <- x + M^{-1} (d - L x) with the residual d - L x evaluated in
-// FP64 from FP64 overlaps and wavenumbers, and M^{-1} the FP32 sweep (Z_p
-// kept from the first sweep, W_p rebuilt from R_p = e_p Z_{p-1} e_p).
+// FP64 from FP64 overlaps and wavenumbers, and M^{-1} the FP32 sweep (Z_p and
+// the LU factors of W_p kept from the first sweep, R_p = e_p Z_{p-1} e_p).
 #include <math.h>
 
 #include <algorithm>
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
   if (d.skip || a.status[pt]) return;
   const int n = a.n, nc = a.nc, N = a.N, q = p + 1;
   cc *gsm = reinterpret_cast<cc *>(smraw);
-  KV v = carve_kv(smraw, gemm_smem_elems<float>() * sizeof(cc), n);
+  KV v = carve_kv(smraw, skinny_smem_elems<float>() * sizeof(cc), n);
   load_kv(a, d, p, v);
   const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
   const cc *Z = a.Zst + ((size_t)pt * (N + 1) + p) * n * n;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
   zc *Xa = a.Xa + blk(a, pt, q);
   zc *Xb = a.Xb + blk(a, pt, p);
   // da_q
-  cta_gemm<float>(
+  cta_gemm_skinny<float>(
       n, nc, n, [=](int i, int l) { return Z[i + (size_t)l * n]; },
       [=](int l, int j) { return tmp[n + l + (size_t)j * 2 * n]; },
       [=](int i, int j, cc acc) {
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
   // db_p = [Q | P] [da_q ; e_q db_q] (+ g_p)
   const KV vc = v;
   const zc *G = a.Gr + iblk(a, pt, p);
-  cta_gemm<float>(
+  cta_gemm_skinny<float>(
       n, nc, 2 * n,
       [=](int i, int l) {
         return ccast<float>(l < n ? pq64(O, n, i, l, vc, -1.0) : pq64(O, n, i, l - n, vc, 1.0));
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
   if (d.skip || a.status[pt]) return;
   const int n = a.n, nc = a.nc, N = a.N, q = p + 1;
   zc *gsm = reinterpret_cast<zc *>(smraw);
-  KV v = carve_kv(smraw, gemm_smem_elems<double>() * sizeof(zc), n);
+  KV v = carve_kv(smraw, skinny_smem_elems<double>() * sizeof(zc), n);
   load_kv(a, d, p, v);
   const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
   const zc *ap = a.Xa + blk(a, pt, p);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
   zc *G = a.Gr + iblk(a, pt, p);
   const KV vc = v;
   const bool has_bq = q <= N;
-  cta_gemm<double>(
+  cta_gemm_skinny<double>(
       n, 2 * nc, n, [=](int i, int l) { return O[i + (size_t)l * n]; },
       [=](int l, int j) {
         const int c = j < nc ? j : j - nc;
@@ -190,10 +190,11 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
 
 // ---------------------------------------------------------------------------
 // Forward correction sweep at interface p (launched for p = 0..N):
-//   R_p = e_p Z_{p-1} e_p,  W_p = P - R_p Q,  u_p = W_p^{-1}(c_p + R_p g_p - f_p),
-//   c_{p+1} = e_q u_p;  u_p replaces the stored one for the backward pass.  At
-//   p = N the carry holds the correction of a_{N+1} (= u_N); on the last
-//   iteration (no backward pass follows) it is added to Xa[N+1] here.
+//   u_p = W_p^{-1}(c_p + R_p g_p - f_p),  R_p = e_p Z_{p-1} e_p,  c_{p+1} = e_q u_p,
+// with W_p's LU factors kept by the first sweep (an O(n^2 nc) replay).  u_p
+// replaces the stored one for the backward pass.  At p = N the carry holds the
+// correction of a_{N+1} (= u_N); on the last iteration (no backward pass
+// follows) it is added to Xa[N+1] here.
 __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p, int add_last) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
@@ -201,59 +202,43 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p, int 
   if (d.skip || a.status[pt]) return;
   const int n = a.n, nc = a.nc, N = a.N;
   cc *gsm = reinterpret_cast<cc *>(smraw);
-  const size_t kv_off = (gemm_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc);
+  const size_t kv_off = (skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc);
   KV v = carve_kv(smraw, kv_off, n);
-  float *sval = reinterpret_cast<float *>(smraw + kv_off + 4 * (size_t)n * sizeof(zc));
-  int *sidx = reinterpret_cast<int *>(sval + 32);
-  int *flag = sidx + 32;
-  if (threadIdx.x == 0) *flag = 0;
   load_kv(a, d, p, v);
-  const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
   const cc *Zprev = p > 0 ? a.Zst + ((size_t)pt * (N + 1) + p - 1) * n * n : nullptr;
+  const cc *LU = a.LUst + ((size_t)pt * (N + 1) + p) * n * n;
+  const int *piv = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
   cc *Ust = a.Ust + ((size_t)pt * (N + 1) + p) * n * nc;
-  cc *M = a.M + (size_t)pt * n * (n + nc);
-  int *piv = a.piv + (size_t)pt * n;
+  cc *rhs = a.M + (size_t)pt * n * (n + nc);   // n x nc scratch
   zc *carry = a.carry + (size_t)pt * n * nc;   // c_p in, c_{p+1} out
   const zc *F = a.Fr + iblk(a, pt, p);
   const zc *G = a.Gr + iblk(a, pt, p);
   const KV vc = v;
-  // R_p (i, l) on the fly
-  auto Rel = [=](int i, int l) -> cc {
-    return ccast<float>(cmul(cmul(vc.eL[i], ccast<double>(Zprev[i + (size_t)l * n])), vc.eL[l]));
-  };
   if (p == 0) {
-    for (size_t e = threadIdx.x; e < (size_t)n * (n + nc); e += NT) {
-      const int i = e % n, j = e / n;
-      M[e] = j < n ? ccast<float>(pq64(O, n, i, j, vc, 1.0))
-                   : ccast<float>(csub(mkc<double>(0.0, 0.0), F[i + (size_t)(j - n) * n]));
-    }
+    for (int e = threadIdx.x; e < n * nc; e += NT) rhs[e] = ccast<float>(csub(carry[e], F[e]));
     __syncthreads();
   } else {
-    // W = P - R Q
-    cta_gemm<float>(
-        n, n, n, Rel, [=](int l, int j) { return ccast<float>(pq64(O, n, l, j, vc, -1.0)); },
-        [=](int i, int j, cc acc) {
-          M[i + (size_t)j * n] = csub(ccast<float>(pq64(O, n, i, j, vc, 1.0)), acc);
+    // rhs = c_p + R_p g_p - f_p
+    cta_gemm_skinny<float>(
+        n, nc, n,
+        [=](int i, int l) {
+          return ccast<float>(cmul(cmul(vc.eL[i], ccast<double>(Zprev[i + (size_t)l * n])), vc.eL[l]));
         },
-        gsm);
-    // rhs = c_p + R g_p - f_p
-    cta_gemm<float>(
-        n, nc, n, Rel, [=](int l, int j) { return ccast<float>(G[l + (size_t)j * n]); },
+        [=](int l, int j) { return ccast<float>(G[l + (size_t)j * n]); },
         [=](int i, int j, cc acc) {
           const zc r = csub(cadd(carry[i + (size_t)j * n], ccast<double>(acc)), F[i + (size_t)j * n]);
-          M[i + (size_t)(n + j) * n] = ccast<float>(r);
+          rhs[i + (size_t)j * n] = ccast<float>(r);
         },
         gsm);
   }
-  cta_lu_solve<float>(M, n, n, n + nc, piv, gsm, sval, sidx, flag);
+  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm);
   for (int e = threadIdx.x; e < n * nc; e += NT) {
     const int i = e % n;
-    const cc u = M[(size_t)n * n + e];
+    const cc u = rhs[e];
     Ust[e] = u;
     carry[e] = cmul(vc.eR[i], ccast<double>(u));
   }
   __syncthreads();
-  if (threadIdx.x == 0 && *flag) a.status[pt] = 1;
   if (p == N && add_last) {
     zc *X = a.Xa + blk(a, pt, N + 1);
     for (int e = threadIdx.x; e < n * nc; e += NT) X[e] = cadd(X[e], carry[e]);
@@ -309,10 +294,9 @@ __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
 // ---------------------------------------------------------------------------
 size_t refine_smem_bytes(int n) {
   const size_t kv = 4 * (size_t)n * sizeof(zc);
-  const size_t fwd = (gemm_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc) + kv +
-                     64 * sizeof(float) + 64 * sizeof(int);
-  const size_t bwd = gemm_smem_elems<float>() * sizeof(cc) + kv;
-  const size_t res = gemm_smem_elems<double>() * sizeof(zc) + kv;
+  const size_t fwd = (skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc) + kv;
+  const size_t bwd = skinny_smem_elems<float>() * sizeof(cc) + kv;
+  const size_t res = skinny_smem_elems<double>() * sizeof(zc) + kv;
   return std::max(fwd, std::max(bwd, res)) + 64;
 }
 

@@ -37,12 +37,12 @@ struct SweepSmem {
   int *flag;
 };
 
-template <typename T>
+template <typename T, int NTH = NT>
 __device__ SweepSmem<T> carve(unsigned char *raw, int n) {
   SweepSmem<T> s;
   cx<T> *c = reinterpret_cast<cx<T> *>(raw);
   s.gemm = c;
-  c += gemm_smem_elems<T>() + Tile<T>::NB * Tile<T>::NB;
+  c += gemm_smem_elems<T, NTH>() + Tile<T, NTH>::NB * Tile<T, NTH>::NB;
   s.kinvL = c;
   c += n;
   s.kR = c;
@@ -55,17 +55,17 @@ __device__ SweepSmem<T> carve(unsigned char *raw, int n) {
   return s;
 }
 
-template <typename T>
+template <typename T, int NTH = NT>
 __host__ __device__ size_t carve_bytes(int n) {
-  return (gemm_smem_elems<T>() + Tile<T>::NB * Tile<T>::NB + 3 * (size_t)n) * sizeof(cx<T>) +
-         32 * sizeof(T) + 64 * sizeof(int) + 16;
+  return (gemm_smem_elems<T, NTH>() + Tile<T, NTH>::NB * Tile<T, NTH>::NB + 3 * (size_t)n) *
+             sizeof(cx<T>) + 32 * sizeof(T) + 64 * sizeof(int) + 16;
 }
 
 // k vectors of the interface p -> smem (computed in FP64, stored in T)
 template <typename T>
 __device__ void interface_vectors(const double *Ep, const double *Eq, double E, double dz, int n,
                                   SweepSmem<T> &s) {
-  for (int i = threadIdx.x; i < n; i += NT) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const zc kl = kz_branch(E, Ep[i]);
     const zc kr = kz_branch(E, Eq[i]);
     s.kinvL[i] = ccast<T>(cinv(kl));
@@ -86,8 +86,9 @@ __device__ __forceinline__ cx<T> pq_elem(const zc *O, int n, int l, int j, const
 }
 
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NT) k_sweep(SweepArgs a, int p) {
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH) k_sweep(SweepArgs a, int p) {
+  constexpr int NT = NTH;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
   const PointDesc d = a.pts[pt];
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a, int p) {
     }
     return;
   }
-  SweepSmem<T> s = carve<T>(smraw, n);
+  SweepSmem<T> s = carve<T, NTH>(smraw, n);
   if (tid == 0) *s.flag = 0;
   const double *Ep = a.En + ((size_t)d.kset * (N + 2) + p) * n;
   const double *Eq = Ep + n;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a, int p) {
   } else {
     // [W | Y] = [P | -Q] + [-R Q | R P]
     const SweepSmem<T> sc = s;
-    cta_gemm<T>(
+    cta_gemm<T, NTH>(
         n, 2 * n, n, [=](int i, int l) { return R[i + (size_t)l * n]; },
         [=](int l, int j) {
           return j < n ? pq_elem<T>(O, n, l, j, sc, T(-1)) : pq_elem<T>(O, n, l, j - n, sc, T(1));
@@ -145,13 +146,19 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a, int p) {
         s.gemm);
   }
   // W [Z_Y | Z_T] = [Y | Tacc]
-  cta_lu_solve<T>(M, n, n, ncols, piv, s.gemm, s.sval, s.sidx, s.flag);
-  // keep Z_Y and u = Z_T for the refinement's backward pass
+  cta_lu_solve<T, NTH>(M, n, n, ncols, piv, s.gemm, s.sval, s.sidx, s.flag);
+  // keep Z_Y, u = Z_T and the LU factors of W for the refinement passes
   if (a.Zst) {
     cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)pt * (N + 1) + p) * n * n;
     cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)pt * (N + 1) + p) * n * nc;
-    for (size_t e = tid; e < (size_t)n * n; e += NT) Zs[e] = M[(size_t)n * n + e];
+    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)pt * (N + 1) + p) * n * n;
+    int *Ps = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
+    for (size_t e = tid; e < (size_t)n * n; e += NT) {
+      Zs[e] = M[(size_t)n * n + e];
+      Ls[e] = M[e];
+    }
     for (size_t e = tid; e < (size_t)n * nc; e += NT) Us[e] = M[(size_t)2 * n * n + e];
+    for (int e = tid; e < n; e += NT) Ps[e] = piv[e];
   }
   // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
   for (size_t e = tid; e < (size_t)n * n; e += NT) {
@@ -192,21 +199,27 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a, int p) {
   }
 }
 
+// The FP64 sweep is bound by the FP64 pipe at 256 threads per point; the FP32
+// sweep is latency-bound and runs 512 threads (16 warps) per point.
+constexpr int SWEEP_NT64 = 256, SWEEP_NT32 = 512;
+
 size_t sweep_smem_bytes(int n, int precision) {
-  return precision == PW_FP64 ? carve_bytes<double>(n) : carve_bytes<float>(n);
+  return precision == PW_FP64 ? carve_bytes<double, SWEEP_NT64>(n) : carve_bytes<float, SWEEP_NT32>(n);
 }
 
 cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s) {
   const size_t smem = sweep_smem_bytes(a.n, precision);
   cudaError_t e;
   if (precision == PW_FP64) {
-    e = cudaFuncSetAttribute(k_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_sweep<double, SWEEP_NT64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_sweep<double><<<npts, NT, smem, s>>>(a, p);
+    k_sweep<double, SWEEP_NT64><<<npts, SWEEP_NT64, smem, s>>>(a, p);
   } else {
-    e = cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_sweep<float, SWEEP_NT32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_sweep<float><<<npts, NT, smem, s>>>(a, p);
+    k_sweep<float, SWEEP_NT32><<<npts, SWEEP_NT32, smem, s>>>(a, p);
   }
   return cudaGetLastError();
 }
