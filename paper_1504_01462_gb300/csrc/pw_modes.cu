@@ -272,9 +272,273 @@ size_t jacobi_smem(int n) {
          (size_t)n * (sizeof(double) + sizeof(int)) + 64;
 }
 
-// HU: in H, out U; V: scratch of the same size; status: sweeps used per
-// matrix (negative: not converged).
+// ---------------------------------------------------------------------------
+// Batched Hermitian eigensolver, tridiagonal route (FP64, one CTA per matrix):
+//   1. Householder reduction Q^H A Q = T (T real symmetric tridiagonal).  For
+//      column k, x = A[k+1:, k], alpha = x_0, beta = -sign(Re alpha) ||x||,
+//      tau = (beta - alpha) / beta, v = (1, x_1.. / (alpha - beta)), so that
+//      (I - tau v v^H)^H x = beta e_1; the trailing block is updated as
+//      p = tau A v, c = Re(conj(tau) v^H p) / 2, w = p - c v,
+//      A <- A - v w^H - w v^H.
+//   2. Implicit QL with Wilkinson-type shifts on (d, e), rotations accumulated
+//      into Z (each thread streams its rows; the rotation sequence of a QL
+//      step is formed once in shared memory).
+//   3. Back-transformation U = Q_0 Q_1 ... Q_{n-2} Z, then ascending sort.
+// Memory traffic is O(n^3) bytes per matrix in total (the two-sided Jacobi
+// streams the matrix every round), so this route is FP64-bound.
+// ---------------------------------------------------------------------------
+constexpr int HEEV_THREADS = 512;
+
+template <int NTH>
+__device__ double block_sum(double v, double *scratch) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < NTH / 32 ? scratch[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) scratch[32] = v;
+  }
+  __syncthreads();
+  const double r = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, double *En_all,
+                                                       int *status, int n) {
+  constexpr int NTH = HEEV_THREADS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const size_t nn = (size_t)n * n;
+  zc *A = HU_all + mat * nn;
+  zc *Z = Z_all + mat * nn;
+  double *En = En_all + (size_t)mat * n;
+  zc *v = reinterpret_cast<zc *>(smraw);
+  zc *pw_ = v + n;
+  zc *taus = pw_ + n;
+  double *d = reinterpret_cast<double *>(taus + n);
+  double *e = d + n;
+  double *cs = e + n;
+  double *sn = cs + n;
+  double *red = sn + n;                 // 40 doubles
+  int *ctl = reinterpret_cast<int *>(red + 40);   // [m, lo, converged-flag, failed]
+  int *rank = ctl + 8;
+  if (tid == 0) ctl[3] = 0;
+
+  // ---- 1. Householder tridiagonalisation
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;
+    zc *x = A + (k + 1) + (size_t)k * n;
+    double part = 0.0;
+    for (int i = 1 + tid; i < m; i += NTH) part += cnorm2(x[i]);
+    const double xn2 = block_sum<NTH>(part, red);
+    const zc alpha = x[0];
+    zc tau;
+    double beta;
+    if (xn2 == 0.0 && alpha.im == 0.0) {
+      tau = czero<double>();
+      beta = alpha.re;
+    } else {
+      beta = -copysign(sqrt(cnorm2(alpha) + xn2), alpha.re);
+      tau = mkc<double>((beta - alpha.re) / beta, -alpha.im / beta);
+    }
+    const zc scl = (tau.re == 0.0 && tau.im == 0.0) ? czero<double>()
+                                                    : cinv(mkc<double>(alpha.re - beta, alpha.im));
+    for (int i = tid; i < m; i += NTH) {
+      const zc vi = i == 0 ? mkc<double>(1.0, 0.0) : cmul(x[i], scl);
+      v[i] = vi;
+      if (i > 0) x[i] = vi;   // kept for the back-transformation
+    }
+    if (tid == 0) {
+      d[k] = A[k + (size_t)k * n].re;
+      e[k] = beta;
+      taus[k] = tau;
+    }
+    __syncthreads();
+    if (tau.re == 0.0 && tau.im == 0.0) continue;
+    zc *A22 = A + (k + 1) + (size_t)(k + 1) * n;
+    // p = tau A22 v
+    for (int i = tid; i < m; i += NTH) {
+      zc acc = czero<double>();
+      for (int j = 0; j < m; ++j) cfma(acc, A22[i + (size_t)j * n], v[j]);
+      pw_[i] = cmul(tau, acc);
+    }
+    __syncthreads();
+    double pr = 0.0, pi = 0.0;
+    for (int i = tid; i < m; i += NTH) {
+      const zc t = cjmul(v[i], pw_[i]);
+      pr += t.re;
+      pi += t.im;
+    }
+    const double vr = block_sum<NTH>(pr, red);
+    const double vi_ = block_sum<NTH>(pi, red);
+    const double c = 0.5 * (tau.re * vr + tau.im * vi_);   // Re(conj(tau) v^H p)
+    for (int i = tid; i < m; i += NTH) pw_[i] = csub(pw_[i], cscale(c, v[i]));
+    __syncthreads();
+    // A22 <- A22 - v w^H - w v^H
+    for (size_t q = tid; q < (size_t)m * m; q += NTH) {
+      const int i = q % m, j = q / m;
+      zc a = A22[i + (size_t)j * n];
+      const zc t1 = cmul(v[i], cconj(pw_[j])), t2 = cmul(pw_[i], cconj(v[j]));
+      a.re -= t1.re + t2.re;
+      a.im -= t1.im + t2.im;
+      A22[i + (size_t)j * n] = a;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d[n - 1] = A[(n - 1) + (size_t)(n - 1) * n].re;
+    e[n - 1] = 0.0;
+  }
+  for (size_t q = tid; q < nn; q += NTH) {
+    const int i = q % n, j = q / n;
+    Z[q] = mkc<double>(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+
+  // ---- 2. implicit QL on the tridiagonal (d, e)
+  const double eps = 2.220446049250313e-16;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      if (tid == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          const double dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= eps * dd) break;
+        }
+        ctl[0] = m;
+        ctl[1] = l;
+        ctl[2] = 0;
+        if (m != l) {
+          if (++iter > 60) {
+            ctl[3] = 1;
+            ctl[0] = l;
+          } else {
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int lo = l;
+            bool under = false;
+            for (int i = m - 1; i >= l; --i) {
+              const double f = s * e[i], b = c * e[i];
+              r = hypot(f, g);
+              e[i + 1] = r;
+              if (r == 0.0) {
+                d[i + 1] -= p;
+                e[m] = 0.0;
+                under = true;
+                lo = i + 1;
+                break;
+              }
+              s = f / r;
+              c = g / r;
+              g = d[i + 1] - p;
+              r = (d[i] - g) * s + 2.0 * c * b;
+              p = s * r;
+              d[i + 1] = g + p;
+              g = c * r - b;
+              cs[i] = c;
+              sn[i] = s;
+            }
+            if (!under) {
+              d[l] -= p;
+              e[l] = g;
+              e[m] = 0.0;
+            }
+            ctl[1] = lo;   // rotations i = m-1 .. lo were formed
+            ctl[2] = 1;
+          }
+        }
+      }
+      __syncthreads();
+      const int m = ctl[0], lo = ctl[1];
+      if (m == l) break;
+      if (ctl[2] && lo < m) {
+        for (int row = tid; row < n; row += NTH) {
+          zc x = Z[row + (size_t)m * n];
+          for (int i = m - 1; i >= lo; --i) {
+            const zc y = Z[row + (size_t)i * n];
+            const double c = cs[i], s = sn[i];
+            Z[row + (size_t)(i + 1) * n] = mkc<double>(s * y.re + c * x.re, s * y.im + c * x.im);
+            x = mkc<double>(c * y.re - s * x.re, c * y.im - s * x.im);
+          }
+          Z[row + (size_t)lo * n] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- 3. back-transformation U = Q Z (Q_{n-2} first)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int k = n - 2; k >= 0; --k) {
+    const zc tau = taus[k];
+    if (tau.re == 0.0 && tau.im == 0.0) continue;
+    const int m = n - k - 1;
+    const zc *x = A + (k + 1) + (size_t)k * n;
+    for (int i = tid; i < m; i += NTH) v[i] = i == 0 ? mkc<double>(1.0, 0.0) : x[i];
+    __syncthreads();
+    zc *Zk = Z + (k + 1);
+    for (int j = warp; j < n; j += NTH / 32) {
+      zc acc = czero<double>();
+      for (int i = lane; i < m; i += 32) {
+        const zc t = cjmul(v[i], Zk[i + (size_t)j * n]);
+        acc.re += t.re;
+        acc.im += t.im;
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        acc.re += __shfl_down_sync(0xffffffffu, acc.re, off);
+        acc.im += __shfl_down_sync(0xffffffffu, acc.im, off);
+      }
+      if (lane == 0) pw_[j] = cmul(tau, acc);
+    }
+    __syncthreads();
+    for (size_t q = tid; q < (size_t)m * n; q += NTH) {
+      const int i = q % m, j = q / m;
+      zc z = Zk[i + (size_t)j * n];
+      const zc t = cmul(v[i], pw_[j]);
+      z.re -= t.re;
+      z.im -= t.im;
+      Zk[i + (size_t)j * n] = z;
+    }
+    __syncthreads();
+  }
+
+  // ---- 4. ascending order (ties by index)
+  for (int i = tid; i < n; i += NTH) {
+    const double li = d[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (d[j] < li) || (d[j] == li && j < i);
+    rank[i] = r;
+    En[r] = li;
+  }
+  __syncthreads();
+  for (size_t q = tid; q < nn; q += NTH) {
+    const int i = q % n, j = q / n;
+    A[i + (size_t)rank[j] * n] = Z[q];
+  }
+  if (tid == 0) status[mat] = ctl[3] ? -1 : 1;
+}
+
+size_t heev_smem(int n) {
+  return (size_t)3 * n * sizeof(zc) + (size_t)4 * n * sizeof(double) + 40 * sizeof(double) +
+         (8 + (size_t)n) * sizeof(int) + 64;
+}
+
+// HU: in H, out U; V: scratch of the same size; status: positive on success,
+// negative when an eigenvalue did not converge.
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s) {
+  const size_t smem = heev_smem(n);
+  cudaFuncSetAttribute(k_heev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_heev<<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n);
+}
+
+// The Jacobi route (same interface), kept as an independent second solver.
+void launch_eig_jacobi(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s) {
   const size_t sm64 = jacobi_smem<double>(n);
   cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64);
   k_jacobi<double><<<nmat, EIG_THREADS, sm64, s>>>(HU, V, (size_t)n * n, n, 1, 40, 1e-12, status,
