@@ -49,6 +49,23 @@ def workload(name):
     raise ValueError(name)
 
 
+def shard_kpoints(rank, world, n_k, n_steps, first_step=0):
+    """k_par indices processed by `rank` in steps first_step .. first_step+n_steps-1:
+    step s of rank r takes k = (r + s * world) mod n_k, so the ranks of one step
+    hold disjoint k_par points (weak scaling: each rank has a full step)."""
+    return [(rank + (first_step + s) * world) % n_k for s in range(n_steps)]
+
+
+def reduce_max(value, world, device):
+    """Max over ranks of a scalar (the slowest rank's time sets the job time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def sweep_flops_per_point(n, nopen_left):
     """Algorithmic flops of one interface step of the sweep for one point:
     R [Q | P] (2 n^3 complex multiply-adds), LU of W (n^3 / 3), forward and
@@ -209,7 +226,7 @@ def main():
     npts = len(inst.energies)
 
     def step_points(s):
-        kk = (rank + s * world) % n_k
+        kk = shard_kpoints(rank, world, n_k, 1, first_step=s)[0]
         idx = np.arange(kk * n_e, (kk + 1) * n_e)
         return inst.energies[idx], inst.kpar[idx]
 
@@ -244,10 +261,7 @@ def main():
     nopen_last = nop.cpu().numpy()
     err_max = float(err.max().item())
     flops_per_launch = sum(sweep_flops_per_point(n, int(nl)) for nl in nopen_last[:, 0])
-    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = reduce_max(ms, world, "cuda")
     total_points = args.steps * n_e * world
     value = total_points / (ms_max / 1e3)
 
@@ -261,10 +275,7 @@ def main():
         T_host.copy_(T, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = max(time.perf_counter() - t0, 1e-9)
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = total_points / float(e2e_t.item())
+    e2e_value = total_points / reduce_max(e2e_s, world, "cuda")
 
     if rank == 0:
         sweep_avg_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
