@@ -55,7 +55,7 @@ struct pw_ctx {
   std::vector<std::vector<double>> EL, ER;   // electrode eigenvalues per slot (host)
   int last_sweeps = 0;                       // most Jacobi sweeps of one matrix in the last eig
   // per-point workspaces
-  DevBuf R, M, piv, pts, status, work;
+  DevBuf R, M, piv, pts, status, work, KV;
   DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   // launch timing (pw_set_profiling)
   struct Rec { cudaEvent_t a, b; int kind; int count; };
@@ -441,7 +441,7 @@ void pw_destroy(pw_ctx *ctx) {
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
 
                   ctx->d_O, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
-                  ctx->pts.p, ctx->status.p, ctx->work.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
+                  ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
                   ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
                   ctx->PIVst.p};
   for (void *p : bufs)
@@ -620,7 +620,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
     const bool refine = ctx->precision == PW_MIXED_FP32 && ctx->refine_iters > 0;
     // per-point bytes of the sweep (+ refinement) buffers; the batch fits in 85 %
     // of the free memory
-    size_t per_pt = nn * esz + (size_t)n * ncols * esz + n * sizeof(int) + 64;
+    size_t per_pt = nn * esz + (size_t)n * ncols * esz + 3 * (size_t)n * esz + n * sizeof(int) + 64;
     if (refine)
       per_pt += (size_t)(N + 1) * (2 * nn + (size_t)n * nc) * sizeof(cc) + (size_t)(N + 1) * n * sizeof(int) +
                 (size_t)(2 * (N + 2) + 2 * (N + 1) + 1) * n * nc * sizeof(zc) + 2 * (size_t)n * nc * sizeof(cc);
@@ -637,6 +637,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       if ((st = ensure(ctx, ctx->R, (size_t)nb * nn * esz)) ||
           (st = ensure(ctx, ctx->M, (size_t)nb * n * ncols * esz)) ||
           (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+          (st = ensure(ctx, ctx->KV, (size_t)nb * 3 * n * esz)) ||
           (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
           (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
         return st;
@@ -675,8 +676,10 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.Ust = refine ? ctx->Ust.p : nullptr;
       a.LUst = refine ? ctx->LUst.p : nullptr;
       a.PIVst = refine ? (int *)ctx->PIVst.p : nullptr;
-      Stage s0(ctx, 0, N + 1);
-      for (int p = 0; p <= N; ++p) CK(pw::launch_sweep(a, nb, p, ctx->precision, ctx->stream));
+      a.KV = ctx->KV.p;
+      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n));
+      for (int p = 0; p <= N; ++p)
+        CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream));
       s0.done();
       if (refine) {
         pw::RefineArgs r;

@@ -29,10 +29,13 @@ __host__ __device__ constexpr size_t gemm_smem_elems() {
 // fa/fb return cx<T>; fa is read with i fastest (A column-major), fb with l
 // fastest (B column-major), so plain column-major operands load coalesced.
 // Tile BM x BN x BK; each of the NTH threads owns a (BM/TY) x TN micro-tile with
-// TX = BN/TN threads along N and TY = NTH/TX along M.  smem must hold
+// TX = BN/TN threads along N and TY = NTH/TX along M.  The CTA computes output
+// tiles t_first, t_first + t_step, ... (all of them by default); several CTAs
+// can share one product by striding over its tiles.  smem must hold
 // BK*(BM+1) + BK*(BN+1) elements.
 template <typename T, int BM, int BN, int BK, int TN, int NTH, class FA, class FB, class FE>
-__device__ void cta_gemm_t(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem) {
+__device__ void cta_gemm_t(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem, int t_first = 0,
+                           int t_step = 1) {
   constexpr int NT = NTH;
   constexpr int TX = BN / TN, TY = NT / TX, TM = BM / TY;
   static_assert(TX * TN == BN && TY * TM == BM && TX * TY == NT, "tile shape");
@@ -42,7 +45,7 @@ __device__ void cta_gemm_t(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem
   cx<T> *Bs = smem + BK * LDA;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   const int tilesM = (m + BM - 1) / BM, tilesN = (n + BN - 1) / BN;
-  for (int t = 0; t < tilesM * tilesN; ++t) {
+  for (int t = t_first; t < tilesM * tilesN; t += t_step) {
     const int i0 = (t % tilesM) * BM, j0 = (t / tilesM) * BN;
     cx<T> acc[TM][TN];
 #pragma unroll
@@ -165,129 +168,161 @@ __device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
 template <>
 __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
 
-// Solves A X = B in place for the n x n matrix A held in columns [0, n) of the
-// n x ncols column-major M (leading dimension ld) and the right-hand sides in
-// columns [n, ncols).  Partial (row) pivoting; A is overwritten by its LU
-// factors, B by X.  `flag` (shared, per CTA) gets bit 1 on a zero pivot.
-// smem: gemm_smem_elems<T>() + NB*NB complex, plus sval/sidx scratch.
+// Pieces of a right-looking blocked LU with partial pivoting that eliminates on
+// an augmented n x ncols column-major matrix M = [A | B] (leading dimension ld)
+// and back-substitutes, i.e. solves A X = B in place (X over B).  Every piece
+// is called by all NTH threads of one CTA and ends with a __syncthreads().
+//
+// lu_panel: unblocked factorisation of columns j0..j0+nb-1 (rows j0..n-1) with
+// row pivoting (piv[j] = chosen row), then the panel's row swaps and
+// U12 = L11^{-1} A12 on every column right of the panel.  `flag` gets bit 1 on
+// a zero pivot.  Ls: NB x NB staging in shared memory.
 template <typename T, int NTH = NT>
-__device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T> *smem,
-                             T *sval, int *sidx, int *flag) {
+__device__ void lu_panel(cx<T> *M, int ld, int n, int ncols, int j0, int *piv, cx<T> *Ls, T *sval,
+                         int *sidx, int *flag) {
   constexpr int NT = NTH;
   constexpr int NB = Tile<T, NTH>::NB;
   const int tid = threadIdx.x;
-  cx<T> *Ls = smem + gemm_smem_elems<T, NTH>();   // NB x NB staging
-  for (int j0 = 0; j0 < n; j0 += NB) {
-    const int nb = min(NB, n - j0);
-    // ---- unblocked panel factorisation, columns j0..j0+nb-1, rows j0..n-1
-    for (int j = j0; j < j0 + nb; ++j) {
-      T best = T(-1);
-      int bi = j;
-      for (int i = j + tid; i < n; i += NT) {
-        const T v = cabs1(M[i + (size_t)j * ld]);
-        if (v > best) { best = v; bi = i; }
-      }
-      const int p = block_argmax<T, NTH>(best, bi, sval, sidx);
-      if (tid == 0) piv[j] = p;
-      if (p != j) {
-        for (int c = j0 + tid; c < j0 + nb; c += NT) {
-          const cx<T> a = M[j + (size_t)c * ld];
-          M[j + (size_t)c * ld] = M[p + (size_t)c * ld];
-          M[p + (size_t)c * ld] = a;
-        }
-      }
-      __syncthreads();
-      cx<T> d = M[j + (size_t)j * ld];
-      if (d.re == T(0) && d.im == T(0)) {
-        if (tid == 0) atomicOr(flag, 1);
-        d = mkc<T>(tiny_pivot<T>(), T(0));
-      }
-      const cx<T> inv = cinv(d);
-      for (int i = j + 1 + tid; i < n; i += NT) M[i + (size_t)j * ld] = cmul(M[i + (size_t)j * ld], inv);
-      __syncthreads();
-      const int rows = n - j - 1, cols = j0 + nb - j - 1;
-      for (int e = tid; e < rows * cols; e += NT) {
-        const int i = j + 1 + e % rows, c = j + 1 + e / rows;
-        cx<T> v = M[i + (size_t)c * ld];
-        const cx<T> l = M[i + (size_t)j * ld], u = M[j + (size_t)c * ld];
-        v.re -= l.re * u.re - l.im * u.im;
-        v.im -= l.re * u.im + l.im * u.re;
-        M[i + (size_t)c * ld] = v;
-      }
-      __syncthreads();
+  const int nb = min(NB, n - j0);
+  for (int j = j0; j < j0 + nb; ++j) {
+    T best = T(-1);
+    int bi = j;
+    for (int i = j + tid; i < n; i += NT) {
+      const T v = cabs1(M[i + (size_t)j * ld]);
+      if (v > best) { best = v; bi = i; }
     }
-    // ---- row swaps and U12 = L11^{-1} A12 on every column right of the panel
-    const int c0 = j0 + nb;
-    for (int e = tid; e < nb * nb; e += NT) {
-      const int r = e % nb, s = e / nb;
-      Ls[r + s * NB] = M[j0 + r + (size_t)(j0 + s) * ld];
-    }
-    __syncthreads();
-    for (int c = c0 + tid; c < ncols; c += NT) {
-      cx<T> *col = M + (size_t)c * ld + j0;
-      for (int r = 0; r < nb; ++r) {
-        const int p = piv[j0 + r] - j0;
-        if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
-      }
-      for (int r = 1; r < nb; ++r) {
-        cx<T> x = col[r];
-        for (int s = 0; s < r; ++s) {
-          const cx<T> l = Ls[r + s * NB], y = col[s];
-          x.re -= l.re * y.re - l.im * y.im;
-          x.im -= l.re * y.im + l.im * y.re;
-        }
-        col[r] = x;
+    const int p = block_argmax<T, NTH>(best, bi, sval, sidx);
+    if (tid == 0) piv[j] = p;
+    if (p != j) {
+      for (int c = j0 + tid; c < j0 + nb; c += NT) {
+        const cx<T> a = M[j + (size_t)c * ld];
+        M[j + (size_t)c * ld] = M[p + (size_t)c * ld];
+        M[p + (size_t)c * ld] = a;
       }
     }
     __syncthreads();
-    // ---- trailing update M[c0:, c0:] -= L21 U12
-    if (c0 < n && c0 < ncols) {
-      cx<T> *Mp = M;
-      cta_gemm<T, NTH>(
-          n - c0, ncols - c0, nb,
-          [=](int i, int l) { return Mp[c0 + i + (size_t)(j0 + l) * ld]; },
-          [=](int l, int j) { return Mp[j0 + l + (size_t)(c0 + j) * ld]; },
-          [=](int i, int j, cx<T> acc) {
-            cx<T> &v = Mp[c0 + i + (size_t)(c0 + j) * ld];
-            v = csub(v, acc);
-          },
-          smem);
+    cx<T> d = M[j + (size_t)j * ld];
+    if (d.re == T(0) && d.im == T(0)) {
+      if (tid == 0) atomicOr(flag, 1);
+      d = mkc<T>(tiny_pivot<T>(), T(0));
+    }
+    const cx<T> inv = cinv(d);
+    for (int i = j + 1 + tid; i < n; i += NT) M[i + (size_t)j * ld] = cmul(M[i + (size_t)j * ld], inv);
+    __syncthreads();
+    const int rows = n - j - 1, cols = j0 + nb - j - 1;
+    for (int e = tid; e < rows * cols; e += NT) {
+      const int i = j + 1 + e % rows, c = j + 1 + e / rows;
+      cx<T> v = M[i + (size_t)c * ld];
+      const cx<T> l = M[i + (size_t)j * ld], u = M[j + (size_t)c * ld];
+      v.re -= l.re * u.re - l.im * u.im;
+      v.im -= l.re * u.im + l.im * u.re;
+      M[i + (size_t)c * ld] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += NT) {
+    const int r = e % nb, s2 = e / nb;
+    Ls[r + s2 * NB] = M[j0 + r + (size_t)(j0 + s2) * ld];
+  }
+  __syncthreads();
+  for (int c = j0 + nb + tid; c < ncols; c += NT) {
+    cx<T> *col = M + (size_t)c * ld + j0;
+    for (int r = 0; r < nb; ++r) {
+      const int p = piv[j0 + r] - j0;
+      if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
+    }
+    for (int r = 1; r < nb; ++r) {
+      cx<T> x = col[r];
+      for (int s2 = 0; s2 < r; ++s2) {
+        const cx<T> l = Ls[r + s2 * NB], y = col[s2];
+        x.re -= l.re * y.re - l.im * y.im;
+        x.im -= l.re * y.im + l.im * y.re;
+      }
+      col[r] = x;
     }
   }
-  // ---- back substitution U X = B' on columns [n, ncols)
+  __syncthreads();
+}
+
+// Trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb);
+// output tiles t_first, t_first + t_step, ...
+template <typename T, int NTH = NT>
+__device__ void lu_trailing(cx<T> *M, int ld, int n, int ncols, int j0, cx<T> *gsm, int t_first = 0,
+                            int t_step = 1) {
+  constexpr int NB = Tile<T, NTH>::NB;
+  const int nb = min(NB, n - j0), c0 = j0 + nb;
+  if (c0 >= n || c0 >= ncols) return;
+  cta_gemm_t<T, Tile<T, NTH>::BM, Tile<T, NTH>::BN, Tile<T, NTH>::BK, 4, NTH>(
+      n - c0, ncols - c0, nb, [=](int i, int l) { return M[c0 + i + (size_t)(j0 + l) * ld]; },
+      [=](int l, int j) { return M[j0 + l + (size_t)(c0 + j) * ld]; },
+      [=](int i, int j, cx<T> acc) {
+        cx<T> &v = M[c0 + i + (size_t)(c0 + j) * ld];
+        v = csub(v, acc);
+      },
+      gsm, t_first, t_step);
+}
+
+// Diagonal block j0 of the back substitution: X_b = U_bb^{-1} B_b for the
+// right-hand-side columns [c_first, c_last) (a subset of [n, ncols)).
+template <typename T, int NTH = NT>
+__device__ void lu_bs_diag(cx<T> *M, int ld, int n, int j0, int c_first, int c_last, cx<T> *Ls) {
+  constexpr int NT = NTH;
+  constexpr int NB = Tile<T, NTH>::NB;
+  const int tid = threadIdx.x, nb = min(NB, n - j0);
+  for (int e = tid; e < nb * nb; e += NT) {
+    const int r = e % nb, s2 = e / nb;
+    Ls[r + s2 * NB] = M[j0 + r + (size_t)(j0 + s2) * ld];
+  }
+  __syncthreads();
+  for (int c = c_first + tid; c < c_last; c += NT) {
+    cx<T> *col = M + (size_t)c * ld + j0;
+    for (int r = nb - 1; r >= 0; --r) {
+      cx<T> x = col[r];
+      for (int s2 = r + 1; s2 < nb; ++s2) {
+        const cx<T> u = Ls[r + s2 * NB], y = col[s2];
+        x.re -= u.re * y.re - u.im * y.im;
+        x.im -= u.re * y.im + u.im * y.re;
+      }
+      col[r] = cdiv(x, Ls[r + r * NB]);
+    }
+  }
+  __syncthreads();
+}
+
+// Back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b.
+template <typename T, int NTH = NT>
+__device__ void lu_bs_update(cx<T> *M, int ld, int n, int ncols, int j0, cx<T> *gsm, int t_first = 0,
+                             int t_step = 1) {
+  constexpr int NB = Tile<T, NTH>::NB;
+  const int nb = min(NB, n - j0);
+  if (j0 <= 0) return;
+  cta_gemm_t<T, Tile<T, NTH>::BM, Tile<T, NTH>::BN, Tile<T, NTH>::BK, 4, NTH>(
+      j0, ncols - n, nb, [=](int i, int l) { return M[i + (size_t)(j0 + l) * ld]; },
+      [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * ld]; },
+      [=](int i, int j, cx<T> acc) {
+        cx<T> &v = M[i + (size_t)(n + j) * ld];
+        v = csub(v, acc);
+      },
+      gsm, t_first, t_step);
+}
+
+// Solves A X = B in place for the n x n matrix A held in columns [0, n) of the
+// n x ncols column-major M (leading dimension ld) and the right-hand sides in
+// columns [n, ncols): the pieces above run one after the other in one CTA.
+// smem: gemm_smem_elems<T, NTH>() + NB*NB complex, plus sval/sidx scratch.
+template <typename T, int NTH = NT>
+__device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T> *smem,
+                             T *sval, int *sidx, int *flag) {
+  constexpr int NB = Tile<T, NTH>::NB;
+  cx<T> *Ls = smem + gemm_smem_elems<T, NTH>();
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    lu_panel<T, NTH>(M, ld, n, ncols, j0, piv, Ls, sval, sidx, flag);
+    lu_trailing<T, NTH>(M, ld, n, ncols, j0, smem);
+  }
   const int jlast = ((n - 1) / NB) * NB;
   for (int j0 = jlast; j0 >= 0; j0 -= NB) {
-    const int nb = min(NB, n - j0);
-    for (int e = tid; e < nb * nb; e += NT) {
-      const int r = e % nb, s = e / nb;
-      Ls[r + s * NB] = M[j0 + r + (size_t)(j0 + s) * ld];
-    }
-    __syncthreads();
-    for (int c = n + tid; c < ncols; c += NT) {
-      cx<T> *col = M + (size_t)c * ld + j0;
-      for (int r = nb - 1; r >= 0; --r) {
-        cx<T> x = col[r];
-        for (int s = r + 1; s < nb; ++s) {
-          const cx<T> u = Ls[r + s * NB], y = col[s];
-          x.re -= u.re * y.re - u.im * y.im;
-          x.im -= u.re * y.im + u.im * y.re;
-        }
-        col[r] = cdiv(x, Ls[r + r * NB]);
-      }
-    }
-    __syncthreads();
-    if (j0 > 0) {
-      cx<T> *Mp = M;
-      cta_gemm<T, NTH>(
-          j0, ncols - n, nb,
-          [=](int i, int l) { return Mp[i + (size_t)(j0 + l) * ld]; },
-          [=](int l, int j) { return Mp[j0 + l + (size_t)(n + j) * ld]; },
-          [=](int i, int j, cx<T> acc) {
-            cx<T> &v = Mp[i + (size_t)(n + j) * ld];
-            v = csub(v, acc);
-          },
-          smem);
-    }
+    lu_bs_diag<T, NTH>(M, ld, n, j0, n, ncols, Ls);
+    lu_bs_update<T, NTH>(M, ld, n, ncols, j0, smem);
   }
   __syncthreads();
 }

@@ -56,6 +56,7 @@ struct SweepArgs {
   void *Ust;             // per point (N+1) x n x nc  (u_p)
   void *LUst;            // per point (N+1) x n x n  (LU factors of W_p)
   int *PIVst;            // per point (N+1) x n      (row swaps of W_p)
+  void *KV;              // per point 3 x n: 1/k^p, k^{p+1}, E+ of the current interface
 };
 
 // Buffers of the FP64 refinement around the FP32 sweep (pw_refine.cu).
@@ -93,6 +94,9 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s);
 // one interface of the left-to-right sweep for every point of a batch
 cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
+// the same interface step as a sequence of launches over (tiles x points)
+cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
+int sweep_batched_launches(int n);
 size_t sweep_smem_bytes(int n, int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p and u_p (iters >= 1)
 cudaError_t launch_refine(const RefineArgs &a, int npts, int iters, cudaStream_t s);

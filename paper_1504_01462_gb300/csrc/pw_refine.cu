@@ -65,6 +65,14 @@ __device__ __forceinline__ zc pq64(const zc *O, int n, int l, int j, const KV &v
   return cmul(o, mkc<double>(0.5 * (1.0 + sel * r.re), 0.5 * sel * r.im));
 }
 
+// The same in FP32 (the backward and forward passes apply the FP32
+// preconditioner; only the residual needs FP64)
+__device__ __forceinline__ cc pq32(const zc *O, int n, int l, int j, const KV &v, float sel) {
+  const cc o = ccast<float>(O[l + (size_t)j * n]);
+  const cc r = cmul(ccast<float>(v.kR[j]), ccast<float>(v.kinvL[l]));
+  return cmul(o, mkc<float>(0.5f * (1.0f + sel * r.re), 0.5f * sel * r.im));
+}
+
 __device__ __forceinline__ size_t blk(const RefineArgs &a, int pt, int q) {
   return ((size_t)pt * (a.N + 2) + q) * (size_t)a.n * a.nc;
 }
@@ -129,9 +137,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
   const zc *G = a.Gr + iblk(a, pt, p);
   cta_gemm_skinny<float>(
       n, nc, 2 * n,
-      [=](int i, int l) {
-        return ccast<float>(l < n ? pq64(O, n, i, l, vc, -1.0) : pq64(O, n, i, l - n, vc, 1.0));
-      },
+      [=](int i, int l) { return l < n ? pq32(O, n, i, l, vc, -1.0f) : pq32(O, n, i, l - n, vc, 1.0f); },
       [=](int l, int j) { return tmp[l + (size_t)j * 2 * n]; },
       [=](int i, int j, cc acc) {
         zc db = ccast<double>(acc);
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p, int 
     cta_gemm_skinny<float>(
         n, nc, n,
         [=](int i, int l) {
-          return ccast<float>(cmul(cmul(vc.eL[i], ccast<double>(Zprev[i + (size_t)l * n])), vc.eL[l]));
+          return cmul(cmul(ccast<float>(vc.eL[i]), Zprev[i + (size_t)l * n]), ccast<float>(vc.eL[l]));
         },
         [=](int l, int j) { return ccast<float>(G[l + (size_t)j * n]); },
         [=](int i, int j, cc acc) {

@@ -1,0 +1,256 @@
+// Batched launch sequence of the sweep (the production path of
+// pw_transmission).  One interface step of App. A Eqs. transfer / scatter and
+// Eq. recurrence (the fused update in pw_sweep.cu) is split into phases, each a
+// launch over (output tiles) x (points), so every phase fills the GPU:
+//   vectors   k^p, k^{p+1}, E+ per point            (p = 0 also seeds [P|-Q|I])
+//   wy        [W | Y] = [P | -Q] + [-R Q | R P]     (GEMM tiles x points)
+//   panel     LU panel with row pivoting + U12       (one CTA per point)
+//   trail     trailing update of the panel           (GEMM tiles x points)
+//   bs_diag   diagonal block of the back substitution
+//   bs_upd    back-substitution update               (GEMM tiles x points)
+//   finish    R <- E+ Z_Y E+, Tacc <- E+ Z_T, refinement storage, t and T
+// The arithmetic of each element is the same as in the one-CTA-per-point
+// kernel (same tile loops and accumulation order).
+#include <math.h>
+
+#include "pw_cta.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+namespace {
+
+constexpr int BT = 256;   // threads of every batched launch
+
+template <typename T>
+struct KVb {
+  const cx<T> *kinvL, *kR, *ep;
+};
+
+template <typename T>
+__device__ __forceinline__ KVb<T> kv_of(const SweepArgs &a, int pt) {
+  const cx<T> *base = reinterpret_cast<const cx<T> *>(a.KV) + (size_t)pt * 3 * a.n;
+  return KVb<T>{base, base + a.n, base + 2 * a.n};
+}
+
+// P_lj (sel +1) or Q_lj (sel -1)
+template <typename T>
+__device__ __forceinline__ cx<T> pqb(const zc *O, int n, int l, int j, const KVb<T> &v, T sel) {
+  const cx<T> o = ccast<T>(O[l + (size_t)j * n]);
+  const cx<T> r = cmul(v.kR[j], v.kinvL[l]);
+  return cmul(o, mkc<T>(T(0.5) * (T(1) + sel * r.re), T(0.5) * sel * r.im));
+}
+
+__device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
+  return a.pts[pt].skip || a.status[pt];
+}
+
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_vectors(SweepArgs a, int p) {
+  const int pt = blockIdx.x;
+  if (inactive(a, pt)) return;
+  const PointDesc d = a.pts[pt];
+  const int n = a.n, N = a.N, nc = a.nc, ncols = 2 * n + nc;
+  const double *Ep = a.En + ((size_t)d.kset * (N + 2) + p) * n;
+  const double *Eq = Ep + n;
+  cx<T> *kv = reinterpret_cast<cx<T> *>(a.KV) + (size_t)pt * 3 * n;
+  const double dz = a.dz[p + 1];
+  for (int i = threadIdx.x; i < n; i += BT) {
+    const zc kl = kz_branch(d.E, Ep[i]);
+    const zc kr = kz_branch(d.E, Eq[i]);
+    kv[i] = ccast<T>(cinv(kl));
+    kv[n + i] = ccast<T>(kr);
+    kv[2 * n + i] = ccast<T>(phase_fwd(kr, dz));
+  }
+  if (p != 0) return;
+  __syncthreads();
+  // S(0,0) = I: R = 0, Tacc = the open left columns of I  ->  W = P, Y = -Q
+  const zc *O = a.O + ((size_t)d.kset * (N + 1)) * n * n;
+  const KVb<T> v = kv_of<T>(a, pt);
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  for (size_t e = threadIdx.x; e < (size_t)n * ncols; e += BT) {
+    const int i = e % n, j = e / n;
+    cx<T> val;
+    if (j < n) val = pqb<T>(O, n, i, j, v, T(1));
+    else if (j < 2 * n) { val = pqb<T>(O, n, i, j - n, v, T(-1)); val.re = -val.re; val.im = -val.im; }
+    else { const int c = j - 2 * n; val = mkc<T>((i == c && c < d.nL) ? T(1) : T(0), T(0)); }
+    M[e] = val;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const PointDesc d = a.pts[pt];
+  const int n = a.n, N = a.N, ncols = 2 * n + a.nc;
+  const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
+  const cx<T> *R = reinterpret_cast<const cx<T> *>(a.R) + (size_t)pt * n * n;
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  const KVb<T> v = kv_of<T>(a, pt);
+  cta_gemm_t<T, Tile<T, BT>::BM, Tile<T, BT>::BN, Tile<T, BT>::BK, 4, BT>(
+      n, 2 * n, n, [=](int i, int l) { return R[i + (size_t)l * n]; },
+      [=](int l, int j) {
+        return j < n ? pqb<T>(O, n, l, j, v, T(-1)) : pqb<T>(O, n, l, j - n, v, T(1));
+      },
+      [=](int i, int j, cx<T> acc) {
+        if (j < n) M[i + (size_t)j * n] = csub(pqb<T>(O, n, i, j, v, T(1)), acc);
+        else M[i + (size_t)j * n] = csub(acc, pqb<T>(O, n, i, j - n, v, T(-1)));
+      },
+      reinterpret_cast<cx<T> *>(smraw), blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.x;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  constexpr int NB = Tile<T, BT>::NB;
+  cx<T> *Ls = reinterpret_cast<cx<T> *>(smraw);
+  T *sval = reinterpret_cast<T *>(Ls + NB * NB);
+  int *sidx = reinterpret_cast<int *>(sval + 40);
+  int *flag = sidx + 40;
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
+  if (threadIdx.x == 0 && *flag) a.status[pt] = 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_trail(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  lu_trailing<T, BT>(M, n, n, ncols, j0, reinterpret_cast<cx<T> *>(smraw), blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_bsdiag(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  const int per = (ncols - n + gridDim.x - 1) / gridDim.x;
+  const int c0 = n + blockIdx.x * per, c1 = min(ncols, c0 + per);
+  lu_bs_diag<T, BT>(M, n, n, j0, c0, c1, reinterpret_cast<cx<T> *>(smraw));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_bsupd(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  lu_bs_update<T, BT>(M, n, n, ncols, j0, reinterpret_cast<cx<T> *>(smraw), blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
+  const int pt = blockIdx.x, tid = threadIdx.x;
+  const PointDesc d = a.pts[pt];
+  const int n = a.n, N = a.N, nc = a.nc, ncols = 2 * n + nc;
+  if (inactive(a, pt)) {
+    if (p == N && tid == 0) {
+      a.T[d.out] = __longlong_as_double(0x7ff8000000000000ll);
+      if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
+      if (a.err) a.err[d.out] = 0.0;
+    }
+    return;
+  }
+  cx<T> *R = reinterpret_cast<cx<T> *>(a.R) + (size_t)pt * n * n;
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  const int *piv = a.piv + (size_t)pt * n;
+  const KVb<T> v = kv_of<T>(a, pt);
+  if (a.Zst) {
+    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)pt * (N + 1) + p) * n * n;
+    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)pt * (N + 1) + p) * n * nc;
+    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)pt * (N + 1) + p) * n * n;
+    int *Ps = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
+    for (size_t e = tid; e < (size_t)n * n; e += BT) {
+      Zs[e] = M[(size_t)n * n + e];
+      Ls[e] = M[e];
+    }
+    for (size_t e = tid; e < (size_t)n * nc; e += BT) Us[e] = M[(size_t)2 * n * n + e];
+    for (int e = tid; e < n; e += BT) Ps[e] = piv[e];
+  }
+  // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
+  for (size_t e = tid; e < (size_t)n * n; e += BT) {
+    const int i = e % n, j = e / n;
+    R[e] = cmul(cmul(v.ep[i], M[i + (size_t)(n + j) * n]), v.ep[j]);
+  }
+  for (size_t e = tid; e < (size_t)n * nc; e += BT) {
+    const int i = e % n, c = e / n;
+    cx<T> &x = M[i + (size_t)(2 * n + c) * n];
+    x = cmul(v.ep[i], x);
+  }
+  if (p < N) return;
+  __syncthreads();
+  // t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels, T = sum |t_ij|^2
+  const double *EL = a.En + ((size_t)d.kset * (N + 2)) * n;
+  const double *ER = EL + (size_t)(N + 1) * n;
+  double acc = 0.0;
+  for (int e = tid; e < d.nR * d.nL; e += BT) {
+    const int i = e % d.nR, j = e / d.nR;
+    const double f = sqrt(sqrt(d.E - ER[i]) / sqrt(d.E - EL[j]));
+    const cx<T> x = M[i + (size_t)(2 * n + j) * n];
+    const zc tv = mkc<double>(f * double(x.re), f * double(x.im));
+    acc += tv.re * tv.re + tv.im * tv.im;
+    if (a.t) a.t[(size_t)d.out * n * n + i + (size_t)j * n] = tv;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ double red[BT / 32];
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double tsum = 0.0;
+    for (int w = 0; w < BT / 32; ++w) tsum += red[w];
+    a.T[d.out] = tsum;
+    if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
+    if (a.err) a.err[d.out] = 0.0;
+  }
+}
+
+template <typename T>
+static cudaError_t sweep_step(const SweepArgs &a, int npts, int p, cudaStream_t s) {
+  const int n = a.n, ncols = 2 * n + a.nc;
+  constexpr int BM = Tile<T, BT>::BM, BN = Tile<T, BT>::BN, NB = Tile<T, BT>::NB;
+  const size_t gsm = gemm_smem_elems<T, BT>() * sizeof(cx<T>);
+  const size_t psm = (size_t)NB * NB * sizeof(cx<T>) + 40 * sizeof(T) + 96 * sizeof(int);
+  const size_t dsm = (size_t)NB * NB * sizeof(cx<T>);
+  auto tiles = [](int m, int nn, int bm, int bn) { return ((m + bm - 1) / bm) * ((nn + bn - 1) / bn); };
+  kb_vectors<T><<<npts, BT, 0, s>>>(a, p);
+  if (p > 0) kb_wy<T><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, gsm, s>>>(a, p);
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    kb_panel<T><<<npts, BT, psm, s>>>(a, j0);
+    const int c0 = j0 + min(NB, n - j0);
+    if (c0 < n) kb_trail<T><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
+  }
+  const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
+  for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
+    kb_bsdiag<T><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
+    if (j0 > 0) kb_bsupd<T><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+  }
+  kb_finish<T><<<npts, BT, 0, s>>>(a, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s) {
+  return precision == PW_FP64 ? sweep_step<double>(a, npts, p, s) : sweep_step<float>(a, npts, p, s);
+}
+
+int sweep_batched_launches(int n) {
+  const int NB = Tile<float, BT>::NB;
+  const int panels = (n + NB - 1) / NB;
+  return 3 + 2 * panels + 2 * panels - 2;
+}
+
+}  // namespace pw
