@@ -170,10 +170,11 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
 /* Timing of the library's own launches (for benchmarks and roofline
  * accounting).  While enabled, CUDA events on the context's stream bracket
  * every stage: the slice-mode stage (Hamiltonian assembly and eigensolver), the
- * overlap GEMMs, each batch of sweep launches and each batch's refinement.
- * pw_get_profile synchronises the stream and writes out[8] = {sweep ms,
- * sweep launches, mode-stage ms, mode stages, overlap ms, overlap stages,
- * refinement ms, refinement stages}; reset != 0 clears the records. */
+ * overlap GEMMs, each batch of sweep launches, each batch's refinement, and
+ * every [W|Y] GEMM launch of the sweep.  pw_get_profile synchronises the
+ * stream and writes out[10] = {sweep ms, sweep launches, mode-stage ms, mode
+ * stages, overlap ms, overlap stages, refinement ms, refinement stages,
+ * [W|Y] GEMM ms, [W|Y] GEMM launches}; reset != 0 clears the records. */
 pw_status pw_set_profiling(pw_ctx *ctx, int enable);
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset);
 

@@ -400,3 +400,130 @@ def transmission_dense(model, modes, E):
             M[r0 + n:r0 + 2 * n, cb:cb + n] -= -Uq * (kq * eq)[None, :]
     x = np.linalg.solve(M, rhs)
     return x[col_a(N + 1):col_a(N + 1) + n], x[0:n]
+
+
+# ---------------------------------------------------------------------------
+# adjoint (derivative of T with respect to slice Hamiltonians), for pw_grad
+# ---------------------------------------------------------------------------
+def dense_amplitudes(model, modes, E, inc_left, inc_right):
+    """All slice amplitudes from one dense solve of the interface matching
+    conditions (as in transmission_dense), for given incoming amplitudes:
+    inc_left = a_0 (n x m, forward waves in the left electrode) and
+    inc_right = b_{N+1} (n x m, backward waves in the right electrode,
+    referenced at the right edge of the device).  Returns lists a[q], b[q]
+    (q = 0..N+1) of n x m arrays; a[0] and b[N+1] are the given ones."""
+    n, N = model.n, model.N
+    ks = [kz(E, Ep) for Ep, _ in modes]
+    Us = [U for _, U in modes]
+    es = [np.exp(1j * ks[q] * model.thickness(q)) for q in range(N + 2)]
+    m = inc_left.shape[1]
+    # unknowns: b_0, (a_q, b_q) q = 1..N, a_{N+1}
+    def ca(q):
+        return n + 2 * n * (q - 1) if q <= N else n + 2 * n * N
+
+    def cb(q):
+        return 0 if q == 0 else n + 2 * n * (q - 1) + n
+
+    nunk = 2 * n * (N + 1)
+    M = np.zeros((nunk, nunk), dtype=np.complex128)
+    rhs = np.zeros((nunk, m), dtype=np.complex128)
+    for p in range(N + 1):
+        r0 = 2 * n * p
+        Up, Uq, kp, kq, ep, eq = Us[p], Us[p + 1], ks[p], ks[p + 1], es[p], es[p + 1]
+        q = p + 1
+        # left side (slice p) at z_p
+        if p == 0:
+            rhs[r0:r0 + n] -= Up @ inc_left
+            rhs[r0 + n:r0 + 2 * n] -= (Up * kp[None, :]) @ inc_left
+            M[r0:r0 + n, cb(0):cb(0) + n] += Up
+            M[r0 + n:r0 + 2 * n, cb(0):cb(0) + n] += -Up * kp[None, :]
+        else:
+            M[r0:r0 + n, ca(p):ca(p) + n] += Up * ep[None, :]
+            M[r0:r0 + n, cb(p):cb(p) + n] += Up
+            M[r0 + n:r0 + 2 * n, ca(p):ca(p) + n] += Up * (kp * ep)[None, :]
+            M[r0 + n:r0 + 2 * n, cb(p):cb(p) + n] += -Up * kp[None, :]
+        # right side (slice q) at z_p
+        M[r0:r0 + n, ca(q):ca(q) + n] -= Uq
+        M[r0 + n:r0 + 2 * n, ca(q):ca(q) + n] -= Uq * kq[None, :]
+        if q <= N:
+            M[r0:r0 + n, cb(q):cb(q) + n] -= Uq * eq[None, :]
+            M[r0 + n:r0 + 2 * n, cb(q):cb(q) + n] -= -Uq * (kq * eq)[None, :]
+        else:
+            rhs[r0:r0 + n] += Uq @ inc_right
+            rhs[r0 + n:r0 + 2 * n] += -(Uq * kq[None, :]) @ inc_right
+    x = np.linalg.solve(M, rhs)
+    a = [inc_left] + [x[ca(q):ca(q) + n] for q in range(1, N + 2)]
+    b = [x[cb(q):cb(q) + n] for q in range(0, N + 1)] + [inc_right]
+    return a, b
+
+
+def _slice_integrals(k, dz):
+    """J1(m,n) = int_0^dz e^{i(k_m+k_n)s} ds and
+    J2(m,n) = int_0^dz e^{i k_m s} e^{i k_n (dz - s)} ds (closed forms)."""
+    km = k[:, None]
+    kn = k[None, :]
+    s = km + kn
+    with np.errstate(divide="ignore", invalid="ignore"):
+        J1 = np.where(np.abs(s) * dz < 1e-12, dz, (np.exp(1j * s * dz) - 1.0) / (1j * s))
+        d = km - kn
+        em = np.exp(1j * km * dz)
+        en = np.exp(1j * kn * dz)
+        J2 = np.where(np.abs(d) * dz < 1e-12, dz * em, (em - en) / (1j * np.where(d == 0, 1.0, d)))
+    return J1, J2
+
+
+def grad_T(model, kpar, E, dH_list):
+    """T(E, k_par) and its derivatives dT/dtheta for parameters whose only
+    effect is dH_p/dtheta in the device slices (dH_list[theta][p-1], p = 1..N).
+
+    For the slice ODE c'' = (H(z) - E) c, a solution d of the transposed
+    problem (H^T) incident from the right electrode in channel i and the
+    scattering state c_j incident from the left satisfy
+        int d_i^T dH c_j dz = 2 i k_i^R dt_ij
+    (constant Wronskian d^T c' - d'^T c), so with T = sum (k_i^R/k_j^L)|t_ij|^2,
+        dT = sum_ij Im(conj(t_ij) int d_i^T dH c_j dz) / k_j^L.
+    Inside slice p the z-integral of the mode exponentials is closed-form."""
+    modes = model.modes(kpar)
+    n, N = model.n, model.N
+    EL, ER = modes[0][0], modes[-1][0]
+    oL, oR = open_channels(E, EL), open_channels(E, ER)
+    kL = np.sqrt(E - EL[oL])
+    kR = np.sqrt(E - ER[oR])
+    I = np.eye(n, dtype=np.complex128)
+    a, b = dense_amplitudes(model, modes, E, I[:, oL], np.zeros((n, len(oL)), complex))
+    t = a[N + 1][oR, :]
+    T = float(np.sum((kR[:, None] / kL[None, :]) * np.abs(t) ** 2))
+    tmodes = [(Ep, U.conj()) for Ep, U in modes]
+    ap, bp = dense_amplitudes(model, tmodes, E, np.zeros((n, len(oR)), complex), I[:, oR])
+    W = np.conj(t) / kL[None, :]                       # (nR, nL)
+    grads = []
+    for dH in dH_list:
+        g = 0.0
+        for p in range(1, N + 1):
+            U = modes[p][1]
+            k = kz(E, modes[p][0])
+            J1, J2 = _slice_integrals(k, model.dz[p - 1])
+            D = U.conj().T @ dH[p - 1] @ U
+            Gam = J1 * (ap[p] @ W @ a[p].T + bp[p] @ W @ b[p].T) + \
+                J2 * (ap[p] @ W @ b[p].T + bp[p] @ W @ a[p].T)
+            g += np.imag(np.sum(D * Gam))
+        grads.append(g)
+    return T, np.array(grads)
+
+
+def well_depth_derivatives(model):
+    """dH_p/dV0_i for every device well i and slice p: the slice table of well i
+    alone divided by its depth (the tables are linear in V0)."""
+    inst = model.inst
+    z = inst.z_edges
+    out = []
+    for i in range(len(inst.v0)):
+        per = []
+        for p in range(model.N):
+            tab = slice_vg_wells(inst.a1, inst.a2, model.half, inst.wells_xyz[i:i + 1],
+                                 np.ones(1), inst.sigma[i:i + 1], z[p], z[p + 1])
+            dH = hamiltonian(model.mn, model.G, np.zeros(2), tab, model.half)
+            dH[np.diag_indices(model.n)] -= ((model.G) ** 2).sum(-1)   # no kinetic part
+            per.append(dH)
+        out.append(per)
+    return out

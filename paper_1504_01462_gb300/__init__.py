@@ -258,11 +258,12 @@ class Context:
 
     def get_profile(self, reset=True):
         """{'sweep_ms', 'sweep_launches', 'modes_ms', 'modes_stages', 'overlap_ms',
-        'overlap_stages', 'refine_ms', 'refine_stages'} accumulated since the last reset."""
-        out = np.zeros(8)
+        'overlap_stages', 'refine_ms', 'refine_stages', 'wy_ms', 'wy_launches'}
+        accumulated since the last reset."""
+        out = np.zeros(10)
         self._check(_lib.pw_get_profile(self._h, _as_dp(out), int(bool(reset))), "pw_get_profile")
         keys = ["sweep_ms", "sweep_launches", "modes_ms", "modes_stages", "overlap_ms",
-                "overlap_stages", "refine_ms", "refine_stages"]
+                "overlap_stages", "refine_ms", "refine_stages", "wy_ms", "wy_launches"]
         return dict(zip(keys, out.tolist()))
 
     @staticmethod

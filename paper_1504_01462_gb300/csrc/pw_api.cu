@@ -460,7 +460,7 @@ pw_status pw_set_profiling(pw_ctx *ctx, int enable) {
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset) {
   if (!ctx || !out) return PW_EINVAL;
   CK(cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  for (int i = 0; i < 10; ++i) out[i] = 0.0;
   for (auto &r : ctx->recs) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
@@ -677,9 +677,14 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.LUst = refine ? ctx->LUst.p : nullptr;
       a.PIVst = refine ? (int *)ctx->PIVst.p : nullptr;
       a.KV = ctx->KV.p;
+      a.mirror = 0;
       Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n));
-      for (int p = 0; p <= N; ++p)
-        CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream));
+      for (int p = 0; p <= N; ++p) {
+        cudaEvent_t w0 = nullptr, w1 = nullptr;
+        if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
+        CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream, w0, w1));
+        if (w0) ctx->recs.push_back({w0, w1, 4, 1});
+      }
       s0.done();
       if (refine) {
         pw::RefineArgs r;

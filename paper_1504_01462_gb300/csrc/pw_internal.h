@@ -57,6 +57,8 @@ struct SweepArgs {
   void *LUst;            // per point (N+1) x n x n  (LU factors of W_p)
   int *PIVst;            // per point (N+1) x n      (row swaps of W_p)
   void *KV;              // per point 3 x n: 1/k^p, k^{p+1}, E+ of the current interface
+  int mirror;            // 1: the z-mirrored transposed problem (slice q -> N+1-q,
+                         //    overlap O_p -> O_{N-p}^T), used by the adjoint
 };
 
 // Buffers of the FP64 refinement around the FP32 sweep (pw_refine.cu).
@@ -95,7 +97,9 @@ void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t
 // one interface of the left-to-right sweep for every point of a batch
 cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
 // the same interface step as a sequence of launches over (tiles x points)
-cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
+// (wy0, wy1: optional events recorded around the [W|Y] GEMM launch)
+cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
+                                 cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr);
 int sweep_batched_launches(int n);
 size_t sweep_smem_bytes(int n, int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p and u_p (iters >= 1)

@@ -33,16 +33,30 @@ __device__ __forceinline__ KVb<T> kv_of(const SweepArgs &a, int pt) {
   return KVb<T>{base, base + a.n, base + 2 * a.n};
 }
 
-// P_lj (sel +1) or Q_lj (sel -1)
+// P_lj (sel +1) or Q_lj (sel -1); `tr` reads the overlap transposed
 template <typename T>
-__device__ __forceinline__ cx<T> pqb(const zc *O, int n, int l, int j, const KVb<T> &v, T sel) {
-  const cx<T> o = ccast<T>(O[l + (size_t)j * n]);
+__device__ __forceinline__ cx<T> pqb(const zc *O, int n, int l, int j, const KVb<T> &v, T sel,
+                                     bool tr = false) {
+  const cx<T> o = ccast<T>(tr ? O[j + (size_t)l * n] : O[l + (size_t)j * n]);
   const cx<T> r = cmul(v.kR[j], v.kinvL[l]);
   return cmul(o, mkc<T>(T(0.5) * (T(1) + sel * r.re), T(0.5) * sel * r.im));
 }
 
 __device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
   return a.pts[pt].skip || a.status[pt];
+}
+
+// Slice q and interface p of the problem being swept.  The mirrored problem
+// (slices in reverse order, overlaps transposed) is the transposed problem
+// (H_p -> H_p^T = conj(H_p), eigenvectors conj(U_p), overlaps conj(O_p))
+// seen from the right electrode: its interface p joins original slices
+// N+1-p and N-p, whose overlap conj(U_{N+1-p})^H conj(U_{N-p}) = O_{N-p}^T.
+__device__ __forceinline__ int slice_of(const SweepArgs &a, int q) { return a.mirror ? a.N + 1 - q : q; }
+__device__ __forceinline__ const double *energies_of(const SweepArgs &a, const PointDesc &d, int q) {
+  return a.En + ((size_t)d.kset * (a.N + 2) + slice_of(a, q)) * a.n;
+}
+__device__ __forceinline__ const zc *overlap_of(const SweepArgs &a, const PointDesc &d, int p) {
+  return a.O + ((size_t)d.kset * (a.N + 1) + (a.mirror ? a.N - p : p)) * a.n * a.n;
 }
 
 }  // namespace
@@ -53,10 +67,10 @@ __global__ void __launch_bounds__(BT) kb_vectors(SweepArgs a, int p) {
   if (inactive(a, pt)) return;
   const PointDesc d = a.pts[pt];
   const int n = a.n, N = a.N, nc = a.nc, ncols = 2 * n + nc;
-  const double *Ep = a.En + ((size_t)d.kset * (N + 2) + p) * n;
-  const double *Eq = Ep + n;
+  const double *Ep = energies_of(a, d, p);
+  const double *Eq = energies_of(a, d, p + 1);
   cx<T> *kv = reinterpret_cast<cx<T> *>(a.KV) + (size_t)pt * 3 * n;
-  const double dz = a.dz[p + 1];
+  const double dz = a.dz[slice_of(a, p + 1)];
   for (int i = threadIdx.x; i < n; i += BT) {
     const zc kl = kz_branch(d.E, Ep[i]);
     const zc kr = kz_branch(d.E, Eq[i]);
@@ -67,14 +81,15 @@ __global__ void __launch_bounds__(BT) kb_vectors(SweepArgs a, int p) {
   if (p != 0) return;
   __syncthreads();
   // S(0,0) = I: R = 0, Tacc = the open left columns of I  ->  W = P, Y = -Q
-  const zc *O = a.O + ((size_t)d.kset * (N + 1)) * n * n;
+  const zc *O = overlap_of(a, d, 0);
+  const bool tr = a.mirror != 0;
   const KVb<T> v = kv_of<T>(a, pt);
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   for (size_t e = threadIdx.x; e < (size_t)n * ncols; e += BT) {
     const int i = e % n, j = e / n;
     cx<T> val;
-    if (j < n) val = pqb<T>(O, n, i, j, v, T(1));
-    else if (j < 2 * n) { val = pqb<T>(O, n, i, j - n, v, T(-1)); val.re = -val.re; val.im = -val.im; }
+    if (j < n) val = pqb<T>(O, n, i, j, v, T(1), tr);
+    else if (j < 2 * n) { val = pqb<T>(O, n, i, j - n, v, T(-1), tr); val.re = -val.re; val.im = -val.im; }
     else { const int c = j - 2 * n; val = mkc<T>((i == c && c < d.nL) ? T(1) : T(0), T(0)); }
     M[e] = val;
   }
@@ -87,20 +102,31 @@ __global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
   if (inactive(a, pt)) return;
   const PointDesc d = a.pts[pt];
   const int n = a.n, N = a.N, ncols = 2 * n + a.nc;
-  const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
+  const zc *O = overlap_of(a, d, p);
+  const bool tr = a.mirror != 0;
   const cx<T> *R = reinterpret_cast<const cx<T> *>(a.R) + (size_t)pt * n * n;
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
-  const KVb<T> v = kv_of<T>(a, pt);
+  // the point's 1/k^p and k^{p+1} staged in shared memory for the operand loads
+  cx<T> *gsm = reinterpret_cast<cx<T> *>(smraw);
+  cx<T> *skinv = gsm + gemm_smem_elems<T, BT>();
+  cx<T> *skr = skinv + n;
+  const KVb<T> g = kv_of<T>(a, pt);
+  for (int i = threadIdx.x; i < n; i += BT) {
+    skinv[i] = g.kinvL[i];
+    skr[i] = g.kR[i];
+  }
+  __syncthreads();
+  const KVb<T> v{skinv, skr, nullptr};
   cta_gemm_t<T, Tile<T, BT>::BM, Tile<T, BT>::BN, Tile<T, BT>::BK, 4, BT>(
       n, 2 * n, n, [=](int i, int l) { return R[i + (size_t)l * n]; },
       [=](int l, int j) {
-        return j < n ? pqb<T>(O, n, l, j, v, T(-1)) : pqb<T>(O, n, l, j - n, v, T(1));
+        return j < n ? pqb<T>(O, n, l, j, v, T(-1), tr) : pqb<T>(O, n, l, j - n, v, T(1), tr);
       },
       [=](int i, int j, cx<T> acc) {
-        if (j < n) M[i + (size_t)j * n] = csub(pqb<T>(O, n, i, j, v, T(1)), acc);
-        else M[i + (size_t)j * n] = csub(acc, pqb<T>(O, n, i, j - n, v, T(-1)));
+        if (j < n) M[i + (size_t)j * n] = csub(pqb<T>(O, n, i, j, v, T(1), tr), acc);
+        else M[i + (size_t)j * n] = csub(acc, pqb<T>(O, n, i, j - n, v, T(-1), tr));
       },
-      reinterpret_cast<cx<T> *>(smraw), blockIdx.x, gridDim.x);
+      gsm, blockIdx.x, gridDim.x);
 }
 
 template <typename T>
@@ -173,13 +199,13 @@ __global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
   if (a.Zst) {
     cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)pt * (N + 1) + p) * n * n;
     cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)pt * (N + 1) + p) * n * nc;
+    for (size_t e = tid; e < (size_t)n * n; e += BT) Zs[e] = M[(size_t)n * n + e];
+    for (size_t e = tid; e < (size_t)n * nc; e += BT) Us[e] = M[(size_t)2 * n * n + e];
+  }
+  if (a.LUst) {
     cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)pt * (N + 1) + p) * n * n;
     int *Ps = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
-    for (size_t e = tid; e < (size_t)n * n; e += BT) {
-      Zs[e] = M[(size_t)n * n + e];
-      Ls[e] = M[e];
-    }
-    for (size_t e = tid; e < (size_t)n * nc; e += BT) Us[e] = M[(size_t)2 * n * n + e];
+    for (size_t e = tid; e < (size_t)n * n; e += BT) Ls[e] = M[e];
     for (int e = tid; e < n; e += BT) Ps[e] = piv[e];
   }
   // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
@@ -195,8 +221,8 @@ __global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
   if (p < N) return;
   __syncthreads();
   // t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels, T = sum |t_ij|^2
-  const double *EL = a.En + ((size_t)d.kset * (N + 2)) * n;
-  const double *ER = EL + (size_t)(N + 1) * n;
+  const double *EL = energies_of(a, d, 0);
+  const double *ER = energies_of(a, d, N + 1);
   double acc = 0.0;
   for (int e = tid; e < d.nR * d.nL; e += BT) {
     const int i = e % d.nR, j = e / d.nR;
@@ -220,7 +246,8 @@ __global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
 }
 
 template <typename T>
-static cudaError_t sweep_step(const SweepArgs &a, int npts, int p, cudaStream_t s) {
+static cudaError_t sweep_step(const SweepArgs &a, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
+                              cudaEvent_t wy1) {
   const int n = a.n, ncols = 2 * n + a.nc;
   constexpr int BM = Tile<T, BT>::BM, BN = Tile<T, BT>::BN, NB = Tile<T, BT>::NB;
   const size_t gsm = gemm_smem_elems<T, BT>() * sizeof(cx<T>);
@@ -228,7 +255,13 @@ static cudaError_t sweep_step(const SweepArgs &a, int npts, int p, cudaStream_t 
   const size_t dsm = (size_t)NB * NB * sizeof(cx<T>);
   auto tiles = [](int m, int nn, int bm, int bn) { return ((m + bm - 1) / bm) * ((nn + bn - 1) / bn); };
   kb_vectors<T><<<npts, BT, 0, s>>>(a, p);
-  if (p > 0) kb_wy<T><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, gsm, s>>>(a, p);
+  if (p > 0) {
+    const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
+    cudaFuncSetAttribute(kb_wy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+    if (wy0) cudaEventRecord(wy0, s);
+    kb_wy<T><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
+    if (wy1) cudaEventRecord(wy1, s);
+  }
   for (int j0 = 0; j0 < n; j0 += NB) {
     kb_panel<T><<<npts, BT, psm, s>>>(a, j0);
     const int c0 = j0 + min(NB, n - j0);
@@ -243,8 +276,10 @@ static cudaError_t sweep_step(const SweepArgs &a, int npts, int p, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s) {
-  return precision == PW_FP64 ? sweep_step<double>(a, npts, p, s) : sweep_step<float>(a, npts, p, s);
+cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
+                                 cudaEvent_t wy0, cudaEvent_t wy1) {
+  return precision == PW_FP64 ? sweep_step<double>(a, npts, p, s, wy0, wy1)
+                              : sweep_step<float>(a, npts, p, s, wy0, wy1);
 }
 
 int sweep_batched_launches(int n) {
