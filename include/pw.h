@@ -167,6 +167,31 @@ pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar,
                           double *T_dev, pw_c128 *t_dev, int *nopen_dev, double *err_dev);
 
+/* The star product of pw_compose for callers that must not allocate device
+ * memory at all (no context, no cudaMalloc): for instance code running inside
+ * a host application whose own memory manager owns the whole device, where a
+ * cudaMalloc from a library would fail or fragment that pool, or code that
+ * needs a fixed, known device-memory footprint.  The paper has no counterpart;
+ * this is a deployment variant of pw_compose.
+ *   n                N_G of the matrices (1 <= n <= 362)
+ *   npts             number of (Sa, Sb) pairs
+ *   Sa_dev, Sb_dev   device, npts x 4 blocks (S11, S12, S21, S22) of n x n
+ *                    column-major complex, as for pw_compose
+ *   Sab_dev          device output, same layout; may not alias the inputs
+ *   cuda_stream      cudaStream_t on the current device (NULL = default)
+ * Scratch: a fixed 8 MiB array inside the library's device image, held by
+ * every GPU that loads the library until the process exits; batches larger
+ * than the array run through it in chunks, and n above 362 (one point's
+ * scratch would exceed 8 MiB) returns PW_EINVAL before any device work.  The
+ * first call on each device looks up the array's device address (set-up
+ * without allocation); make that first call before any stream capture.  All
+ * calls share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race; the call synchronises its stream before
+ * returning (it reads back the pivot status), and returns PW_ESINGULAR on a
+ * zero pivot. */
+pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
+                             pw_c128 *Sab_dev, void *cuda_stream);
+
 /* Timing of the library's own launches (for benchmarks and roofline
  * accounting).  While enabled, CUDA events on the context's stream bracket
  * every stage: the slice-mode stage (Hamiltonian assembly and eigensolver), the

@@ -31,7 +31,7 @@ PW_ETHRESH = 5
 EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "pw_n_slices",
            "pw_get_gvectors", "pw_potential_tables", "pw_slice_modes", "pw_overlaps",
            "pw_slice_smatrix", "pw_compose", "pw_transmission", "pw_set_profiling",
-           "pw_get_profile"]
+           "pw_get_profile", "pw_compose_noalloc"]
 
 
 class PwError(RuntimeError):
@@ -81,6 +81,7 @@ def _load():
     lib.pw_slice_smatrix.argtypes = [_vp, ctypes.c_int, _dp, _dp, ctypes.c_int, _vp]
     lib.pw_compose.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
     lib.pw_transmission.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp, _vp, _vp, _vp]
+    lib.pw_compose_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
     lib.pw_set_profiling.argtypes = [_vp, ctypes.c_int]
     lib.pw_get_profile.argtypes = [_vp, _dp, ctypes.c_int]
     return lib
@@ -112,6 +113,16 @@ def _c128(a):
 
 def _as_dp(a):
     return a.ctypes.data_as(_dp) if a is not None and a.size else None
+
+
+def compose_noalloc(n, npts, Sa, Sb, Sab, stream=None):
+    """Star products Sab = Sa * Sb (Eq. recurrence) without any device
+    allocation by the library: for callers that cannot let a library call
+    cudaMalloc (the library's fixed 8 MiB device array is the only scratch;
+    n <= 362).  Raises PwError on failure."""
+    st = _lib.pw_compose_noalloc(int(n), int(npts), _ptr(Sa), _ptr(Sb), _ptr(Sab), stream)
+    if st != 0:
+        raise PwError(st, "pw_compose_noalloc")
 
 
 class Context:
@@ -272,4 +283,5 @@ class Context:
             raise PwError(st, where)
 
 
-__all__ = ["Context", "PwError", "FP64", "MIXED_FP32", "EXPORTS", "LIB_PATH", "lib"]
+__all__ = ["Context", "PwError", "FP64", "MIXED_FP32", "EXPORTS", "LIB_PATH", "lib",
+           "compose_noalloc"]
