@@ -167,6 +167,26 @@ pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar,
                           double *T_dev, pw_c128 *t_dev, int *nopen_dev, double *err_dev);
 
+/* Adjoint: the weighted summed transmission  sumT = sum_i w_i T(E_i, kpar_i)
+ * and its derivatives with respect to the depths v0 of the device-region
+ * wells (pw_setup_desc.well_v0), computed in FP64 whatever the context's
+ * precision.  For the slice model the constant Wronskian of a scattering
+ * state c_j (incident from the left electrode) and a state d_i of the
+ * transposed problem (incident from the right electrode) gives
+ *   dt_ij = (1 / (2 i k_i^R)) sum_p int_{slice p} d_i^T (dH_p) c_j dz,
+ * closed-form in each slice's modes (Eq. loc); both families of states come
+ * from stored sweeps (Eqs. transfer, scatter, recurrence) and a backward pass.
+ *   weight      host, npts, or NULL for w_i = 1
+ *   sumT_host   host scalar (required)
+ *   dV0_host    host, n_wells, or NULL (PW_EINVAL if the context was set up
+ *               from explicit Fourier tables, which carry no wells)
+ *   dgap_host   must be NULL: the sheet-gap derivative is not provided (the
+ *               electrodes move with the sheets, outside the slice integral)
+ * Synchronises the context's stream.  Device memory: about
+ * (N+1)(n^2 + n n_c) + 4 (N+2) n n_c complex doubles per point of a batch. */
+pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, const double *weight,
+                  double *sumT_host, double *dV0_host, double *dgap_host);
+
 /* The star product of pw_compose for callers that must not allocate device
  * memory at all (no context, no cudaMalloc): for instance code running inside
  * a host application whose own memory manager owns the whole device, where a

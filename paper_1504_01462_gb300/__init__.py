@@ -31,7 +31,7 @@ PW_ETHRESH = 5
 EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "pw_n_slices",
            "pw_get_gvectors", "pw_potential_tables", "pw_slice_modes", "pw_overlaps",
            "pw_slice_smatrix", "pw_compose", "pw_transmission", "pw_set_profiling",
-           "pw_get_profile", "pw_compose_noalloc"]
+           "pw_get_profile", "pw_compose_noalloc", "pw_grad"]
 
 
 class PwError(RuntimeError):
@@ -82,6 +82,7 @@ def _load():
     lib.pw_compose.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
     lib.pw_transmission.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp, _vp, _vp, _vp]
     lib.pw_compose_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+    lib.pw_grad.argtypes = [_vp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.pw_set_profiling.argtypes = [_vp, ctypes.c_int]
     lib.pw_get_profile.argtypes = [_vp, _dp, ctypes.c_int]
     return lib
@@ -263,6 +264,20 @@ class Context:
             return st
         self._check(st, "pw_transmission")
         return st
+
+    def grad(self, E, kpar, weight=None, n_wells=None):
+        """(sum_i w_i T_i, d/dV0 of that sum for every device well) by the
+        adjoint in FP64 (pw_grad)."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        w = None if weight is None else _f64(weight).reshape(-1)
+        sumT = np.zeros(1)
+        nw = int(n_wells) if n_wells is not None else 0
+        dV0 = np.zeros(max(nw, 1))
+        st = _lib.pw_grad(self._h, len(E), _as_dp(E), _as_dp(k), _as_dp(w) if w is not None else None,
+                          _as_dp(sumT), _as_dp(dV0) if nw else None, None)
+        self._check(st, "pw_grad")
+        return float(sumT[0]), dV0[:nw]
 
     def set_profiling(self, on=True):
         self._check(_lib.pw_set_profiling(self._h, int(bool(on))), "pw_set_profiling")

@@ -57,6 +57,10 @@ struct pw_ctx {
   // per-point workspaces
   DevBuf R, M, piv, pts, status, work, KV;
   DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
+  DevBuf Xa_m, Xb_m, status_m, Tg, Gam, gtab, T1, dV0, wgt;   // adjoint (pw_grad)
+  // device copies of the device-region wells (kept for the adjoint)
+  double *d_wxyz = nullptr, *d_wv0 = nullptr, *d_wsig = nullptr;
+  int n_wells = 0;
   // launch timing (pw_set_profiling)
   struct Rec { cudaEvent_t a, b; int kind; int count; };
   bool profiling = false;
@@ -411,9 +415,16 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
     return p;
   };
   if (!d->slice_vg && d->n_wells > 0) {
-    ta.slices.xyz = up(d->well_xyz, 3 * (size_t)d->n_wells);
-    ta.slices.v0 = up(d->well_v0, d->n_wells);
-    ta.slices.sigma = up(d->well_sigma, d->n_wells);
+    if ((st = upload(ctx, &ctx->d_wxyz, d->well_xyz, 3 * (size_t)d->n_wells)) != PW_OK ||
+        (st = upload(ctx, &ctx->d_wv0, d->well_v0, (size_t)d->n_wells)) != PW_OK ||
+        (st = upload(ctx, &ctx->d_wsig, d->well_sigma, (size_t)d->n_wells)) != PW_OK) {
+      pw_destroy(ctx);
+      return st;
+    }
+    ctx->n_wells = d->n_wells;
+    ta.slices.xyz = ctx->d_wxyz;
+    ta.slices.v0 = ctx->d_wv0;
+    ta.slices.sigma = ctx->d_wsig;
     ta.slices.n = d->n_wells;
   }
   for (int s = 0; s < 2; ++s) {
@@ -443,7 +454,9 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->d_O, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
                   ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
-                  ctx->PIVst.p};
+                  ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
+                  ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
+                  ctx->d_wsig};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -722,6 +735,200 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       for (int v : st_h)
         if (v) result = PW_ESINGULAR;
     }
+  }
+  if (result == PW_ESINGULAR) latch(ctx, result);
+  return result;
+}
+
+
+pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, const double *weight,
+                  double *sumT_host, double *dV0_host, double *dgap_host) {
+  if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar)) || !sumT_host) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  if (dgap_host) return PW_EINVAL;                  // the gap derivative is not provided
+  if (dV0_host && ctx->n_wells == 0) return PW_EINVAL;   // explicit tables have no wells
+  const int n = ctx->n, N = ctx->N;
+  const size_t nn = (size_t)n * n;
+  const int tsz = ctx->tsz;
+  pw_status st = alloc_slots(ctx);
+  if (st) return st;
+  if ((st = ensure(ctx, ctx->Gam, (size_t)ctx->ks_cap * N * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->gtab, (size_t)N * tsz * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->T1, (size_t)N * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->dV0, (size_t)std::max(1, ctx->n_wells) * sizeof(double))))
+    return st;
+  CK(cudaMemsetAsync(ctx->gtab.p, 0, (size_t)N * tsz * sizeof(zc), ctx->stream));
+  std::vector<std::vector<int>> groups;
+  group_by_k(npts, kpar, groups);
+  double sumT = 0.0;
+  pw_status result = PW_OK;
+  for (size_t g0 = 0; g0 < groups.size(); g0 += ctx->ks_cap) {
+    const size_t g1 = std::min(groups.size(), g0 + (size_t)ctx->ks_cap);
+    std::vector<const double *> ks;
+    std::vector<std::pair<int, int>> pts;
+    for (size_t gi = g0; gi < g1; ++gi) {
+      ks.push_back(kpar + 2 * groups[gi][0]);
+      for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
+    }
+    if ((st = ensure_ksets(ctx, ks))) return st;
+    CK(cudaMemsetAsync(ctx->Gam.p, 0, (size_t)ks.size() * N * nn * sizeof(zc), ctx->stream));
+    std::vector<PointDesc> all(pts.size());
+    int nc = 1;
+    for (size_t i = 0; i < pts.size(); ++i) {
+      const int idx = pts[i].first, slot = pts[i].second;
+      bool th = false;
+      const int nL = count_open(ctx->EL[slot], E[idx], &th);
+      const int nR = count_open(ctx->ER[slot], E[idx], &th);
+      all[i] = PointDesc{E[idx], slot, nL, nR, idx, th ? 1 : 0};
+      if (th) result = PW_ETHRESH;
+      else nc = std::max(nc, std::max(nL, nR));
+    }
+    nc = (nc + 3) & ~3;
+    const int ncols = 2 * n + nc;
+    const size_t vec = (size_t)n * nc;
+    // per point: FP64 sweep buffers, the stored Z_p and u_p, amplitudes of both problems
+    const size_t per_pt = (nn + (size_t)n * ncols + 3 * (size_t)n) * sizeof(zc) + n * sizeof(int) +
+                          (size_t)(N + 1) * (nn + vec) * sizeof(zc) + 4 * (size_t)(N + 2) * vec * sizeof(zc) +
+                          3 * vec * sizeof(zc) + 64;
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t have = free_b + ctx->R.bytes + ctx->M.bytes + ctx->Zst.bytes + ctx->Ust.bytes +
+                        ctx->Xa.bytes + ctx->Xb.bytes + ctx->Xa_m.bytes + ctx->Xb_m.bytes;
+    const int fit = (int)std::max<size_t>(1, (size_t)(0.8 * (double)have) / per_pt);
+    const int bmax = std::max(1, std::min({(int)pts.size(), 3 * ctx->num_sms, fit}));
+    for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
+      const int nb = (int)std::min(pts.size() - b0, (size_t)bmax);
+      std::vector<PointDesc> pd(all.begin() + b0, all.begin() + b0 + nb);
+      std::vector<PointDesc> pm(pd);
+      for (auto &q : pm) std::swap(q.nL, q.nR);     // mirrored: incident from the right electrode
+      std::vector<double> w(nb, 1.0);
+      if (weight)
+        for (int i = 0; i < nb; ++i) w[i] = weight[pd[i].out];
+      if ((st = ensure(ctx, ctx->R, (size_t)nb * nn * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->M, (size_t)nb * n * ncols * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+          (st = ensure(ctx, ctx->KV, (size_t)nb * 3 * n * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->pts, (size_t)2 * nb * sizeof(PointDesc))) ||
+          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))) ||
+          (st = ensure(ctx, ctx->status_m, (size_t)nb * sizeof(int))) ||
+          (st = ensure(ctx, ctx->Zst, (size_t)nb * (N + 1) * nn * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Ust, (size_t)nb * (N + 1) * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Xa, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Xb, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Xa_m, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Xb_m, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->carry, (size_t)nb * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->tmp, (size_t)nb * 2 * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Tg, (size_t)2 * nb * sizeof(double))) ||
+          (st = ensure(ctx, ctx->wgt, (size_t)nb * sizeof(double))))
+        return st;
+      PointDesc *d_pd = (PointDesc *)ctx->pts.p, *d_pm = d_pd + nb;
+      CK(cudaMemcpyAsync(d_pd, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(d_pm, pm.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->wgt.p, w.data(), nb * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
+      CK(cudaMemsetAsync(ctx->status_m.p, 0, nb * sizeof(int), ctx->stream));
+      // outputs of the two sweeps: T of the original, unused T of the mirrored
+      // problem (each point writes slot `out` - remap to the batch index)
+      std::vector<PointDesc> pd_local(pd), pm_local(pm);
+      for (int i = 0; i < nb; ++i) { pd_local[i].out = i; pm_local[i].out = nb + i; }
+      CK(cudaMemcpyAsync(d_pd, pd_local.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(d_pm, pm_local.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      for (int mirror = 0; mirror < 2; ++mirror) {
+        pw::SweepArgs a;
+        memset(&a, 0, sizeof(a));
+        a.pts = mirror ? d_pm : d_pd;
+        a.En = ctx->d_En;
+        a.O = ctx->d_O;
+        a.dz = ctx->d_dz;
+        a.R = ctx->R.p;
+        a.M = ctx->M.p;
+        a.piv = (int *)ctx->piv.p;
+        a.status = (int *)(mirror ? ctx->status_m.p : ctx->status.p);
+        a.T = (double *)ctx->Tg.p;
+        a.n = n;
+        a.N = N;
+        a.nc = nc;
+        a.Zst = ctx->Zst.p;
+        a.Ust = ctx->Ust.p;
+        a.KV = ctx->KV.p;
+        a.mirror = mirror;
+        for (int p = 0; p <= N; ++p) CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream));
+        pw::GradArgs g;
+        g.pts = a.pts;
+        g.En = ctx->d_En;
+        g.O = ctx->d_O;
+        g.dz = ctx->d_dz;
+        g.Zst = (const zc *)ctx->Zst.p;
+        g.Ust = (const zc *)ctx->Ust.p;
+        g.Xa = (zc *)(mirror ? ctx->Xa_m.p : ctx->Xa.p);
+        g.Xb = (zc *)(mirror ? ctx->Xb_m.p : ctx->Xb.p);
+        g.carry = (zc *)ctx->carry.p;
+        g.tmp = (zc *)ctx->tmp.p;
+        g.status = a.status;
+        g.n = n;
+        g.N = N;
+        g.nc = nc;
+        g.mirror = mirror;
+        CK(pw::launch_grad_backward(g, nb, ctx->stream));
+      }
+      pw::GammaArgs h;
+      h.pts = d_pd;
+      h.En = ctx->d_En;
+      h.dz = ctx->d_dz;
+      h.Xa = (const zc *)ctx->Xa.p;
+      h.Xb = (const zc *)ctx->Xb.p;
+      h.Xa_m = (const zc *)ctx->Xa_m.p;
+      h.Xb_m = (const zc *)ctx->Xb_m.p;
+      h.status = (const int *)ctx->status.p;
+      h.status_m = (const int *)ctx->status_m.p;
+      h.weight = (const double *)ctx->wgt.p;
+      h.Gam = (zc *)ctx->Gam.p;
+      h.gtab = (zc *)ctx->gtab.p;
+      h.n = n;
+      h.N = N;
+      h.nc = nc;
+      h.npts = nb;
+      for (size_t sl = 0; sl < ks.size(); ++sl) CK(pw::launch_grad_gamma(h, (int)sl, ctx->stream));
+      std::vector<double> Th(nb);
+      std::vector<int> sth(nb), stm(nb);
+      CK(cudaMemcpyAsync(Th.data(), ctx->Tg.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(sth.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(stm.data(), ctx->status_m.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int i = 0; i < nb; ++i) {
+        if (sth[i] || stm[i]) result = PW_ESINGULAR;
+        else if (!pd[i].skip) sumT += w[i] * Th[i];
+      }
+    }
+    pw::GammaArgs h;
+    memset(&h, 0, sizeof(h));
+    h.Gam = (zc *)ctx->Gam.p;
+    h.gtab = (zc *)ctx->gtab.p;
+    h.n = n;
+    h.N = N;
+    for (size_t sl = 0; sl < ks.size(); ++sl)
+      CK(pw::launch_grad_fold(h, (int)sl, ctx->d_HU, (zc *)ctx->T1.p, ctx->d_mn, ctx->Dm, ctx->Dn,
+                              ctx->stream));
+  }
+  *sumT_host = sumT;
+  if (dV0_host) {
+    pw::GammaArgs h;
+    memset(&h, 0, sizeof(h));
+    h.gtab = (zc *)ctx->gtab.p;
+    h.n = n;
+    h.N = N;
+    pw::WellSet ws;
+    ws.xyz = ctx->d_wxyz;
+    ws.v0 = ctx->d_wv0;
+    ws.sigma = ctx->d_wsig;
+    ws.n = ctx->n_wells;
+    const double b[4] = {ctx->b1[0], ctx->b1[1], ctx->b2[0], ctx->b2[1]};
+    CK(pw::launch_grad_wells(h, ws, ctx->d_z, b, ctx->area, ctx->Dm, ctx->Dn, (double *)ctx->dV0.p,
+                             ctx->stream));
+    CK(cudaMemcpyAsync(dV0_host, ctx->dV0.p, ctx->n_wells * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
   }
   if (result == PW_ESINGULAR) latch(ctx, result);
   return result;

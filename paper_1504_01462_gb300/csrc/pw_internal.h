@@ -85,6 +85,42 @@ struct RefineArgs {
   int n, N, nc;
 };
 
+// Backward pass of a stored FP64 sweep (pw_grad.cu)
+struct GradArgs {
+  const PointDesc *pts;
+  const double *En;
+  const zc *O;
+  const double *dz;
+  const zc *Zst;         // per point (N+1) x n x n
+  const zc *Ust;         // per point (N+1) x n x nc
+  zc *Xa, *Xb;           // per point (N+2) x n x nc amplitudes
+  zc *carry;             // per point n x nc
+  zc *tmp;               // per point 2n x nc
+  const int *status;
+  int n, N, nc, mirror;
+};
+
+// Accumulation of the adjoint's eigenbasis matrices and their folding
+struct GammaArgs {
+  const PointDesc *pts;  // the original problem's descriptors
+  const double *En;
+  const double *dz;
+  const zc *Xa, *Xb;     // original problem, left incidence
+  const zc *Xa_m, *Xb_m; // mirrored transposed problem
+  const int *status, *status_m;
+  const double *weight;  // per point of the batch, or null
+  zc *Gam;               // [slot][p-1][n x n], p = 1..N
+  zc *gtab;              // [p-1][(2Dm+1)(2Dn+1)]
+  int n, N, nc, npts;
+};
+
+cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s);
+cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, cudaStream_t s);
+cudaError_t launch_grad_fold(const GammaArgs &h, int slot, const zc *U, zc *T1, const int *mn, int Dm,
+                             int Dn, cudaStream_t s);
+cudaError_t launch_grad_wells(const GammaArgs &h, const WellSet &w, const double *z_edges, const double *b,
+                              double area, int Dm, int Dn, double *dV0, cudaStream_t s);
+
 // potential tables and slice Hamiltonians
 void launch_tables(const TableArgs &a, cudaStream_t s);
 void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, double kx, double ky,
