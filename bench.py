@@ -79,7 +79,7 @@ def refine_launches(N, iters):
     pass, then the finish."""
     if iters <= 0:
         return 0
-    return 2 + (N + 1) + iters * (1 + (N + 1)) + (iters - 1) * (N + 1)
+    return 3 + (N + 1) + iters * (1 + (N + 1)) + (iters - 1) * (N + 1)
 
 
 def sweep_flops_per_point(n, nopen_left):
@@ -205,8 +205,9 @@ def main():
                     choices=["junction512", "junction401", "minimal"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--refine", type=int, default=2,
-                    help="FP64 refinement passes of the mixed form (-1: none)")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="most FP64 refinement passes of the mixed form (0: library default, "
+                         "-1: none)")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the slice count (profiling of small cases only)")
     args = ap.parse_args()
@@ -333,13 +334,14 @@ def main():
             "roofline_next": other,
             "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
                           "overlaps": prof["overlap_ms"], "refine": prof["refine_ms"]},
-            "accuracy": {"refine_iters": (args.refine if prec == pw.MIXED_FP32 else 0),
+            "accuracy": {"refine_passes_per_step": (prof["refine_stages"] / max(args.steps, 1)
+                                                    if prec == pw.MIXED_FP32 else 0),
                          "err_est_max_last_step": err_max,
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
             "gpu_launches": int(prof["sweep_launches"] + 3 * prof["modes_stages"]
-                                + (refine_launches(N, args.refine) if prec == pw.MIXED_FP32 else 0)
-                                * args.steps),
+                                + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1))
+                                   * args.steps if prec == pw.MIXED_FP32 else 0)),
             "e2e": (None if args.no_e2e else
                     {"value": e2e_value, "unit": "points/s",
                      "h2d_bytes_per_step": n_e * 32,

@@ -52,9 +52,10 @@ typedef enum {
 typedef struct { double re, im; } pw_c128;
 
 /* Arithmetic of the star-product sweep.  PW_FP64: every step in FP64.
- * PW_MIXED_FP32: the sweep in FP32, then `refine_iters` passes of iterative
- * refinement of the whole interface-matching system with FP64 residuals (the
- * eigenmodes and overlaps are FP64 in both forms). */
+ * PW_MIXED_FP32: the sweep in FP32, then passes of iterative refinement of
+ * the whole interface-matching system with FP64 residuals until the estimated
+ * remaining error of t falls below 1e-9 relative (the eigenmodes and overlaps
+ * are FP64 in both forms). */
 enum { PW_FP64 = 0, PW_MIXED_FP32 = 1 };
 
 /*
@@ -96,8 +97,12 @@ typedef struct {
   const pw_c128 *slice_vg;
   const pw_c128 *lead_vg[2];
   int precision;               /* PW_FP64 or PW_MIXED_FP32 */
-  int refine_iters;            /* PW_MIXED_FP32 only: FP64 refinement passes;
-                                  0 = default (2), -1 = none (plain FP32 sweep) */
+  int refine_iters;            /* PW_MIXED_FP32 only: the most FP64 refinement
+                                  passes (at least min(2, this) are made; more
+                                  stop once every point's estimated remaining
+                                  relative error of t, c_i^2 / c_{i-1} from the
+                                  sizes c of successive corrections, is below
+                                  1e-9); 0 = default (4), -1 = none */
 } pw_setup_desc;
 
 /* Builds the basis (Sec. II A) and uploads the slice geometry; the Fourier
@@ -218,7 +223,7 @@ pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c1
  * overlap GEMMs, each batch of sweep launches, each batch's refinement, and
  * every [W|Y] GEMM launch of the sweep.  pw_get_profile synchronises the
  * stream and writes out[10] = {sweep ms, sweep launches, mode-stage ms, mode
- * stages, overlap ms, overlap stages, refinement ms, refinement stages,
+ * stages, overlap ms, overlap stages, refinement ms, refinement passes,
  * [W|Y] GEMM ms, [W|Y] GEMM launches}; reset != 0 clears the records. */
 pw_status pw_set_profiling(pw_ctx *ctx, int enable);
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset);

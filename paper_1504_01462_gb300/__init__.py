@@ -290,6 +290,7 @@ class Context:
         self._check(_lib.pw_get_profile(self._h, _as_dp(out), int(bool(reset))), "pw_get_profile")
         keys = ["sweep_ms", "sweep_launches", "modes_ms", "modes_stages", "overlap_ms",
                 "overlap_stages", "refine_ms", "refine_stages", "wy_ms", "wy_launches"]
+        # refine_stages counts refinement passes
         return dict(zip(keys, out.tolist()))
 
     @staticmethod

@@ -19,6 +19,7 @@ namespace {
 
 constexpr double kShellQuantum = 1e-8;   // Ry: |G|^2 closer than this is one shell
 constexpr double kThreshold = 1e-10;     // Ry: electrode channel at threshold
+constexpr double kRefineTol = 1e-9;      // stop refining once corrections of t are below this
 
 struct DevBuf {
   void *p = nullptr;
@@ -58,6 +59,8 @@ struct pw_ctx {
   DevBuf R, M, piv, pts, status, work, KV;
   DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   DevBuf Xa_m, Xb_m, status_m, Tg, Gam, gtab, T1, dV0, wgt;   // adjoint (pw_grad)
+  DevBuf corr;                     // refinement stopping test
+  int last_passes = 0;             // refinement passes of the last batch
   // device copies of the device-region wells (kept for the adjoint)
   double *d_wxyz = nullptr, *d_wv0 = nullptr, *d_wsig = nullptr;
   int n_wells = 0;
@@ -339,7 +342,7 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->precision = d->precision;
   if (d->refine_iters < -1 || d->refine_iters > 16) { delete ctx; return PW_EINVAL; }
-  ctx->refine_iters = d->precision == PW_MIXED_FP32 ? (d->refine_iters == 0 ? 2 : std::max(0, d->refine_iters)) : 0;
+  ctx->refine_iters = d->precision == PW_MIXED_FP32 ? (d->refine_iters == 0 ? 4 : std::max(0, d->refine_iters)) : 0;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return PW_ECUDA; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   build_basis(d->a1, d->a2, d->ecut, d->ng_exact, ctx->b1, ctx->b2, ctx->mn, ctx->G);
@@ -456,7 +459,7 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
-                  ctx->d_wsig};
+                  ctx->d_wsig, ctx->corr.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -665,6 +668,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
            (st = ensure(ctx, ctx->Fr, (size_t)(N + 1) * vec * sizeof(zc))) ||
            (st = ensure(ctx, ctx->Gr, (size_t)(N + 1) * vec * sizeof(zc))) ||
            (st = ensure(ctx, ctx->carry, vec * sizeof(zc))) ||
+           (st = ensure(ctx, ctx->corr, (size_t)nb * sizeof(double))) ||
            (st = ensure(ctx, ctx->tmp, 2 * vec * sizeof(cc)))))
         return st;
       CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
@@ -718,6 +722,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.Gr = (zc *)ctx->Gr.p;
         r.carry = (zc *)ctx->carry.p;
         r.tmp = (cc *)ctx->tmp.p;
+        r.corr = (double *)ctx->corr.p;
         r.T = T_dev;
         r.t = (zc *)t_dev;
         r.nopen = nopen_dev;
@@ -726,8 +731,12 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.N = N;
         r.nc = nc;
         Stage s3(ctx, 3, 1);
-        CK(pw::launch_refine(r, nb, ctx->refine_iters, ctx->stream));
+        int passes = 0;
+        CK(pw::launch_refine(r, nb, std::min(2, ctx->refine_iters), ctx->refine_iters, kRefineTol,
+                             ctx->stream, &passes));
+        s3.count = passes;
         s3.done();
+        ctx->last_passes = passes;
       }
       std::vector<int> st_h(nb);
       CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

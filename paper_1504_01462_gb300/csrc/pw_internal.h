@@ -78,6 +78,7 @@ struct RefineArgs {
   zc *Fr, *Gr;           // per point (N+1) x n x nc residuals (FP64)
   zc *carry;             // per point n x nc
   cc *tmp;               // per point 2n x nc
+  double *corr;          // per point: relative size of the last correction of a_{N+1}
   double *T;
   zc *t;
   int *nopen;
@@ -138,8 +139,12 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
                                  cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr);
 int sweep_batched_launches(int n);
 size_t sweep_smem_bytes(int n, int precision);
-// FP64 refinement of an FP32 sweep that stored Z_p and u_p (iters >= 1)
-cudaError_t launch_refine(const RefineArgs &a, int npts, int iters, cudaStream_t s);
+// FP64 refinement of an FP32 sweep that stored Z_p, u_p and the LU factors:
+// between min_iters and max_iters passes, stopping once every point's
+// estimated remaining error of a_{N+1} (c_i^2 / c_{i-1} from the relative
+// corrections c) is below tol; *passes = passes made
+cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_iters, double tol,
+                          cudaStream_t s, int *passes);
 size_t refine_smem_bytes(int n);
 // explicit interface S-matrices (FP64)
 cudaError_t launch_slice_smatrix(const PointDesc *pts, const double *En, const zc *O, const double *dz,

@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "pw_cta.cuh"
 #include "pw_internal.h"
@@ -128,8 +129,10 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
       [=](int i, int j, cc acc) {
         const cc da = cadd(acc, U[i + (size_t)j * n]);
         tmp[i + (size_t)j * 2 * n] = da;
-        zc &x = Xa[i + (size_t)j * n];
-        x = cadd(x, ccast<double>(da));
+        if (q <= N || !with_src) {   // a correction of a_{N+1} was added by the forward pass
+          zc &x = Xa[i + (size_t)j * n];
+          x = cadd(x, ccast<double>(da));
+        }
       },
       gsm);
   // db_p = [Q | P] [da_q ; e_q db_q] (+ g_p)
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
 // replaces the stored one for the backward pass.  At p = N the carry holds the
 // correction of a_{N+1} (= u_N); on the last iteration (no backward pass
 // follows) it is added to Xa[N+1] here.
-__global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p, int add_last) {
+__global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
   const PointDesc d = a.pts[pt];
@@ -245,9 +248,29 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p, int 
     carry[e] = cmul(vc.eR[i], ccast<double>(u));
   }
   __syncthreads();
-  if (p == N && add_last) {
+  if (p == N) {
+    // add the correction of a_{N+1}; record its size relative to a_{N+1}
     zc *X = a.Xa + blk(a, pt, N + 1);
-    for (int e = threadIdx.x; e < n * nc; e += NT) X[e] = cadd(X[e], carry[e]);
+    double dn = 0.0, xn = 0.0;
+    for (int e = threadIdx.x; e < n * nc; e += NT) {
+      const zc dx = carry[e];
+      const zc x = cadd(X[e], dx);
+      X[e] = x;
+      dn += cnorm2(dx);
+      xn += cnorm2(x);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      dn += __shfl_down_sync(0xffffffffu, dn, off);
+      xn += __shfl_down_sync(0xffffffffu, xn, off);
+    }
+    __shared__ double red[2][NT / 32];
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = dn; red[1][threadIdx.x >> 5] = xn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sd = 0.0, sx = 0.0;
+      for (int w = 0; w < NT / 32; ++w) { sd += red[0][w]; sx += red[1][w]; }
+      a.corr[pt] = sx > 0.0 ? sqrt(sd / sx) : 0.0;
+    }
   }
 }
 
@@ -306,7 +329,8 @@ size_t refine_smem_bytes(int n) {
   return std::max(fwd, std::max(bwd, res)) + 64;
 }
 
-cudaError_t launch_refine(const RefineArgs &a, int npts, int iters, cudaStream_t s) {
+cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_iters, double tol,
+                          cudaStream_t s, int *passes) {
   const size_t smem = refine_smem_bytes(a.n);
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_refine_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
@@ -315,23 +339,39 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int iters, cudaStream_t
     return e;
   const size_t vec = (size_t)npts * a.n * a.nc * sizeof(zc);
   if ((e = cudaMemsetAsync(a.Xa, 0, vec * (a.N + 2), s)) || (e = cudaMemsetAsync(a.Xb, 0, vec * (a.N + 2), s)) ||
-      (e = cudaMemsetAsync(a.Gr, 0, vec * (a.N + 1), s)))
+      (e = cudaMemsetAsync(a.Gr, 0, vec * (a.N + 1), s)) || (e = cudaMemsetAsync(a.corr, 0, npts * sizeof(double), s)))
     return e;
   k_refine_init<<<npts, NT, 0, s>>>(a);
   // x0: backward pass over the first sweep's Z_p, u_p
   if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
   for (int p = a.N; p >= 0; --p) k_refine_backward<<<npts, NT, smem, s>>>(a, p, 0);
-  for (int it = 0; it < iters; ++it) {
+  // stopping test: the correction of pass i shrinks the error by about
+  // c_i / c_{i-1} (c = relative size of the correction of a_{N+1}), so the
+  // error left after pass i is estimated as c_i^2 / c_{i-1}
+  std::vector<double> corr(npts), prev(npts, 0.0);
+  int it = 0;
+  for (; it < max_iters; ++it) {
     k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a);
     if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
-    const int last = it + 1 == iters;
-    for (int p = 0; p <= a.N; ++p) k_refine_forward<<<npts, NT, smem, s>>>(a, p, last);
-    if (!last) {
-      // interior corrections (da_{N+1} included): backward from db_{N+1} = 0
-      if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
-      for (int p = a.N; p >= 0; --p) k_refine_backward<<<npts, NT, smem, s>>>(a, p, 1);
+    for (int p = 0; p <= a.N; ++p) k_refine_forward<<<npts, NT, smem, s>>>(a, p);
+    if (it + 1 >= max_iters) { ++it; break; }
+    if ((e = cudaMemcpyAsync(corr.data(), a.corr, npts * sizeof(double), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+      return e;
+    if (it + 1 >= min_iters) {
+      double worst = 0.0;
+      for (int i = 0; i < npts; ++i) {
+        const double est = prev[i] > 0.0 ? corr[i] * corr[i] / prev[i] : corr[i];
+        worst = std::max(worst, est);
+      }
+      if (worst < tol) { ++it; break; }
     }
+    prev = corr;
+    // interior corrections: backward from db_{N+1} = 0
+    if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
+    for (int p = a.N; p >= 0; --p) k_refine_backward<<<npts, NT, smem, s>>>(a, p, 1);
   }
+  if (passes) *passes = it;
   k_refine_finish<<<npts, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
