@@ -208,6 +208,8 @@ def main():
     ap.add_argument("--refine", type=int, default=0,
                     help="most FP64 refinement passes of the mixed form (0: library default, "
                          "-1: none)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP64 re-evaluation of sampled points of the last step")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the slice count (profiling of small cases only)")
     args = ap.parse_args()
@@ -294,6 +296,24 @@ def main():
     e2e_s = max(time.perf_counter() - t0, 1e-9)
     e2e_value = total_points / reduce_max(e2e_s, world, "cuda")
 
+    # ---- accuracy of the mixed form at this size: sampled points of the last
+    # step re-evaluated by the FP64 GPU path (itself checked against the oracle
+    # to 1e-10 in the parity tests), outside every timed region
+    accuracy_vs_fp64 = None
+    if prec == pw.MIXED_FP32 and rank == 0 and not args.no_accuracy:
+        E_last, k_last = step_points(args.warmup + args.steps - 1)
+        T_mixed = T.cpu().numpy()
+        ctx.close()
+        torch.cuda.empty_cache()
+        sel = np.unique(np.linspace(0, n_e - 1, 8).astype(int))
+        with pw.Context.from_instance(inst, precision=pw.FP64, stream=stream.cuda_stream) as c64:
+            T64 = torch.empty(len(sel), dtype=torch.float64, device="cuda")
+            c64.transmission(E_last[sel], k_last[sel], T64)
+            T64 = T64.cpu().numpy()
+        rel = np.abs(T_mixed[sel] - T64) / np.maximum(1.0, np.abs(T64))
+        accuracy_vs_fp64 = {"points": int(len(sel)), "max_rel_err_T": float(rel.max()),
+                            "T_range": [float(T64.min()), float(T64.max())]}
+
     if rank == 0:
         nq = N + 2
         fp64_peak = 1.25
@@ -337,6 +357,7 @@ def main():
             "accuracy": {"refine_passes_per_step": (prof["refine_stages"] / max(args.steps, 1)
                                                     if prec == pw.MIXED_FP32 else 0),
                          "err_est_max_last_step": err_max,
+                         "vs_fp64_gpu_sample": accuracy_vs_fp64,
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
             "gpu_launches": int(prof["sweep_launches"] + 3 * prof["modes_stages"]
@@ -354,7 +375,7 @@ def main():
             line["cpu_baseline"] = {"value": r, "unit": "points/s", "cores": os.cpu_count(),
                                     "kind": "oracle", "sample": info["sample"]}
         print(json.dumps(line))
-    ctx.close()
+    ctx.close()   # (no-op when already closed)
     if world > 1:
         dist.destroy_process_group()
 

@@ -37,6 +37,7 @@ extern "C" {
 #endif
 
 typedef struct pw_ctx pw_ctx;
+typedef struct pw_batch pw_batch;
 
 typedef enum {
   PW_OK = 0,
@@ -103,6 +104,16 @@ typedef struct {
                                   relative error of t, c_i^2 / c_{i-1} from the
                                   sizes c of successive corrections, is below
                                   1e-9); 0 = default (4), -1 = none */
+  /* Motion of the geometry with one scalar parameter theta (for the side-
+   * contact junction: the sheet gap, each sheet moving by half of it), used
+   * only by pw_grad's dgap_host.  Transverse displacement per unit theta
+   * (bohr per bohr, x then y):
+   *   well_shift_rate   host, 2 per device well, or NULL (wells fixed)
+   *   lead_shift_rate   left then right electrode; the electrode potential is
+   *                     translated rigidly (its table becomes
+   *                     e^{-i dG.delta} V(dG)) */
+  const double *well_shift_rate;
+  double lead_shift_rate[2][2];
 } pw_setup_desc;
 
 /* Builds the basis (Sec. II A) and uploads the slice geometry; the Fourier
@@ -164,9 +175,12 @@ pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128
  *   t_dev[npts * N_G * N_G] or NULL  t, top-left n_open^R x n_open^L block of
  *                                    each N_G x N_G column-major slot
  *   nopen_dev[2 * npts] or NULL      (n_open^L, n_open^R) per point
- *   err_dev[npts] or NULL            estimated relative error of T: 0 for FP64,
- *                                    the relative change of T made by the last
- *                                    refinement pass for PW_MIXED_FP32
+ *   err_dev[npts] or NULL            estimated relative error of T: 0 for FP64;
+ *                                    for PW_MIXED_FP32 the relative change of T
+ *                                    made by the last refinement pass times the
+ *                                    contraction c_i / c_{i-1} of the sizes of
+ *                                    the last two corrections (the error left
+ *                                    after that pass)
  * A point at an electrode threshold gets T = NaN and the call returns
  * PW_ETHRESH after finishing the others. */
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar,
@@ -185,8 +199,17 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
  *   sumT_host   host scalar (required)
  *   dV0_host    host, n_wells, or NULL (PW_EINVAL if the context was set up
  *               from explicit Fourier tables, which carry no wells)
- *   dgap_host   must be NULL: the sheet-gap derivative is not provided (the
- *               electrodes move with the sheets, outside the slice integral)
+ *   dgap_host   host scalar, or NULL: d sumT / d theta for the motion that
+ *               pw_setup_desc.well_shift_rate / lead_shift_rate describe
+ *               (PW_EINVAL if the context was set up with neither).  A well
+ *               moved by delta changes its table by the factor e^{-i dG.delta}
+ *               (a slice integral as above).  An electrode translated by delta
+ *               has modes D U, D = diag(e^{-i G.delta}); expressed in the
+ *               unmoved electrode's modes the scattering state jumps by
+ *               (D^H - 1) c at the contact plane, so the Wronskian jumps there
+ *               by -/+ i (d^T Gd c' - d'^T Gd c), Gd = diag(G.delta), minus at
+ *               the left contact and plus at the right one; that jump takes
+ *               the place of the slice integral.
  * Synchronises the context's stream.  Device memory: about
  * (N+1)(n^2 + n n_c) + 4 (N+2) n n_c complex doubles per point of a batch. */
 pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, const double *weight,
@@ -227,6 +250,52 @@ pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c1
  * [W|Y] GEMM ms, [W|Y] GEMM launches}; reset != 0 clears the records. */
 pw_status pw_set_profiling(pw_ctx *ctx, int enable);
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset);
+
+/* Uneven batches: many independent problems, each with its own cell, basis
+ * size N_G, slicing and potential, evaluated at one (E, k_par) point each.
+ * The paper treats one junction at a time (Sec. II); a batch runs the same
+ * steps for every instance (slice modes, overlaps, Eqs. transfer / scatter /
+ * recurrence, App. C), with instances of equal N_G sharing launches: one
+ * eigensolver launch over all their slices, and one sequence of sweep launches
+ * over (tiles x instances) in which an instance with fewer slices drops out
+ * after its last interface.
+ *   n_inst        number of instances (>= 1)
+ *   descs         host, n_inst problem descriptions as for pw_setup; every
+ *                 description must use the same precision and refine_iters
+ *   cuda_stream   as for pw_setup
+ * On success *out owns the instances' geometry (one internal context each). */
+pw_status pw_setup_batch(int n_inst, const pw_setup_desc *descs, void *cuda_stream, pw_batch **out);
+
+/* T of instance i at (E[i], kpar[2i..2i+1]) into T_dev[i], for i < n_inst.
+ *   E, kpar        host, n_inst and 2 n_inst values
+ *   T_dev          device, n_inst doubles (required)
+ *   nopen_dev      device, 2 n_inst ints (n_open^L, n_open^R), or NULL
+ *   err_dev        device, n_inst doubles as for pw_transmission, or NULL
+ * Instances are grouped by N_G (largest first) and each group is cut into
+ * chunks that fit the free device memory.  Each chunk's sweep is recorded once
+ * into a CUDA graph and replayed as one graph launch (pw_batch_set_options).
+ * The sweep's tile variant (256-thread CTAs with 64 x 64 GEMM tiles, or
+ * 512-thread CTAs with 128 x 64 tiles) is chosen per N_G by timing the first
+ * interface steps of the group's first chunk with each variant (CUDA events),
+ * and kept for the batch's later calls.  A threshold point gets T = NaN and the
+ * call returns PW_ETHRESH after finishing the others; PW_ESINGULAR as for
+ * pw_transmission.  Synchronises the stream. */
+pw_status pw_transmission_batch(pw_batch *b, const double *E, const double *kpar, double *T_dev,
+                                int *nopen_dev, double *err_dev);
+
+/* Options of a batch: use_graph (1 = record and replay each chunk's sweep as a
+ * CUDA graph, 0 = launch it directly), variant (-1 = autotune per N_G, 0 or 1 =
+ * that tile variant for every size). */
+pw_status pw_batch_set_options(pw_batch *b, int use_graph, int variant);
+
+/* Stage times of the last pw_transmission_batch, out[8] = {slice-mode ms,
+ * overlap ms, sweep ms, refinement ms, autotuning ms, chunks, graph launches,
+ * sweep launches}, and the tile variant chosen per N_G: variants[i] for
+ * ng[i], i < *n_sizes (at most max_sizes entries written). */
+pw_status pw_batch_get_stats(const pw_batch *b, double *out, int *ng, int *variants, int max_sizes,
+                             int *n_sizes);
+
+void pw_batch_destroy(pw_batch *b);
 
 #ifdef __cplusplus
 }

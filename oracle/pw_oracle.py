@@ -472,17 +472,34 @@ def _slice_integrals(k, dz):
     return J1, J2
 
 
-def grad_T(model, kpar, E, dH_list):
-    """T(E, k_par) and its derivatives dT/dtheta for parameters whose only
-    effect is dH_p/dtheta in the device slices (dH_list[theta][p-1], p = 1..N).
+def _edge_values(U, k, amp_f, amp_b):
+    """psi and dpsi/dz at the reference plane of a slice's forward amplitudes
+    (psi = U (e^{ikz} amp_f + e^{-ikz} amp_b) there)."""
+    return U @ (amp_f + amp_b), 1j * (U * k[None, :]) @ (amp_f - amp_b)
+
+
+def grad_T(model, kpar, E, dH_list, lead_shift=None):
+    """T(E, k_par) and its derivatives dT/dtheta for parameters that change
+    the device slices' Hamiltonians by dH_p/dtheta (dH_list[theta][p-1],
+    p = 1..N; None for no device change) and, optionally, translate the two
+    electrode potentials transversally at the rates lead_shift[theta] =
+    (r_L, r_R) (2-vectors, bohr per unit theta).
 
     For the slice ODE c'' = (H(z) - E) c, a solution d of the transposed
     problem (H^T) incident from the right electrode in channel i and the
     scattering state c_j incident from the left satisfy
-        int d_i^T dH c_j dz = 2 i k_i^R dt_ij
-    (constant Wronskian d^T c' - d'^T c), so with T = sum (k_i^R/k_j^L)|t_ij|^2,
+        W(+inf) - W(-inf) = 2 i k_i^R dt_ij,   W = d^T c' - d'^T c,
+    and dW/dz = d^T dH c, so a smooth device change gives
         dT = sum_ij Im(conj(t_ij) int d_i^T dH c_j dz) / k_j^L.
-    Inside slice p the z-integral of the mode exponentials is closed-form."""
+    Inside slice p the z-integral of the mode exponentials is closed-form.
+
+    An electrode translated by delta has H' = D H D^H with
+    D = diag(e^{-i G.delta}), whose modes are D U.  In the unperturbed
+    electrode basis the perturbed state is D^H c on the electrode's side of
+    its contact plane and c on the device side, so W jumps there by
+    -/+ i (d^T Gd c' - d'^T Gd c), Gd = diag(G.delta) (minus at the left
+    contact z = 0, plus at the right contact z = z_N); that jump takes the
+    place of the integral."""
     modes = model.modes(kpar)
     n, N = model.n, model.N
     EL, ER = modes[0][0], modes[-1][0]
@@ -497,18 +514,52 @@ def grad_T(model, kpar, E, dH_list):
     ap, bp = dense_amplitudes(model, tmodes, E, np.zeros((n, len(oR)), complex), I[:, oR])
     W = np.conj(t) / kL[None, :]                       # (nR, nL)
     grads = []
-    for dH in dH_list:
+    for th, dH in enumerate(dH_list):
         g = 0.0
-        for p in range(1, N + 1):
-            U = modes[p][1]
-            k = kz(E, modes[p][0])
-            J1, J2 = _slice_integrals(k, model.dz[p - 1])
-            D = U.conj().T @ dH[p - 1] @ U
-            Gam = J1 * (ap[p] @ W @ a[p].T + bp[p] @ W @ b[p].T) + \
-                J2 * (ap[p] @ W @ b[p].T + bp[p] @ W @ a[p].T)
-            g += np.imag(np.sum(D * Gam))
+        if dH is not None:
+            for p in range(1, N + 1):
+                U = modes[p][1]
+                k = kz(E, modes[p][0])
+                J1, J2 = _slice_integrals(k, model.dz[p - 1])
+                D = U.conj().T @ dH[p - 1] @ U
+                Gam = J1 * (ap[p] @ W @ a[p].T + bp[p] @ W @ b[p].T) + \
+                    J2 * (ap[p] @ W @ b[p].T + bp[p] @ W @ a[p].T)
+                g += np.imag(np.sum(D * Gam))
+        if lead_shift is not None and lead_shift[th] is not None:
+            for side, q, sign in ((0, 0, -1.0), (1, N + 1, 1.0)):
+                Gd = model.G @ np.asarray(lead_shift[th][side], dtype=np.float64)
+                if not np.any(Gd):
+                    continue
+                k = kz(E, modes[q][0])
+                c, cp = _edge_values(modes[q][1], k, a[q], b[q])
+                d, dp = _edge_values(tmodes[q][1], k, ap[q], bp[q])
+                X = sign * 1j * (d.T @ (Gd[:, None] * cp) - dp.T @ (Gd[:, None] * c))
+                g += np.imag(np.sum(W * X))
         grads.append(g)
     return T, np.array(grads)
+
+
+def well_shift_derivative(model, rates):
+    """dH_p/dtheta when every device well i moves transversally at the rate
+    rates[i] (2-vector, bohr per unit theta): each well's slice table picks up
+    the factor -i dG.rates[i] (its Fourier phase is e^{-i dG.R_i})."""
+    inst = model.inst
+    z = inst.z_edges
+    dG = _dg_grid(inst.a1, inst.a2, model.half)
+    per = []
+    for p in range(model.N):
+        tab = np.zeros(dG.shape[:2], dtype=np.complex128)
+        for i in range(len(inst.v0)):
+            r = np.asarray(rates[i], dtype=np.float64)
+            if not np.any(r):
+                continue
+            ti = slice_vg_wells(inst.a1, inst.a2, model.half, inst.wells_xyz[i:i + 1],
+                                inst.v0[i:i + 1], inst.sigma[i:i + 1], z[p], z[p + 1])
+            tab += -1j * (dG[..., 0] * r[0] + dG[..., 1] * r[1]) * ti
+        dH = hamiltonian(model.mn, model.G, np.zeros(2), tab, model.half)
+        dH[np.diag_indices(model.n)] -= ((model.G) ** 2).sum(-1)   # no kinetic part
+        per.append(dH)
+    return per
 
 
 def well_depth_derivatives(model):

@@ -31,7 +31,9 @@ PW_ETHRESH = 5
 EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "pw_n_slices",
            "pw_get_gvectors", "pw_potential_tables", "pw_slice_modes", "pw_overlaps",
            "pw_slice_smatrix", "pw_compose", "pw_transmission", "pw_set_profiling",
-           "pw_get_profile", "pw_compose_noalloc", "pw_grad"]
+           "pw_get_profile", "pw_compose_noalloc", "pw_grad", "pw_setup_batch",
+           "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
+           "pw_batch_destroy"]
 
 
 class PwError(RuntimeError):
@@ -58,6 +60,8 @@ class SetupDesc(ctypes.Structure):
         ("slice_vg", _vp), ("lead_vg", _vp * 2),
         ("precision", ctypes.c_int),
         ("refine_iters", ctypes.c_int),
+        ("well_shift_rate", _dp),
+        ("lead_shift_rate", (ctypes.c_double * 2) * 2),
     ]
 
 
@@ -85,6 +89,12 @@ def _load():
     lib.pw_grad.argtypes = [_vp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.pw_set_profiling.argtypes = [_vp, ctypes.c_int]
     lib.pw_get_profile.argtypes = [_vp, _dp, ctypes.c_int]
+    lib.pw_setup_batch.argtypes = [ctypes.c_int, ctypes.POINTER(SetupDesc), _vp, ctypes.POINTER(_vp)]
+    lib.pw_transmission_batch.argtypes = [_vp, _dp, _dp, _vp, _vp, _vp]
+    lib.pw_batch_set_options.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    lib.pw_batch_get_stats.argtypes = [_vp, _dp, _ip, _ip, ctypes.c_int, _ip]
+    lib.pw_batch_destroy.argtypes = [_vp]
+    lib.pw_batch_destroy.restype = None
     return lib
 
 
@@ -126,49 +136,82 @@ def compose_noalloc(n, npts, Sa, Sb, Sab, stream=None):
         raise PwError(st, "pw_compose_noalloc")
 
 
+def _build_desc(*, a1, a2, z_edges, ecut=0.0, ng_exact=0, wells_xyz=None, v0=None, sigma=None,
+                leads=((None, None, None, 1.0), (None, None, None, 1.0)), slice_vg=None,
+                lead_vg=(None, None), vg_half=(0, 0), precision=FP64, refine_iters=0,
+                well_shift_rate=None, lead_shift_rate=None):
+    """A pw_setup_desc and the host arrays it points into (keep them alive
+    until pw_setup returns), and whether it carries a geometry motion."""
+    keep = []
+    d = SetupDesc()
+    d.a1[:] = [float(v) for v in a1]
+    d.a2[:] = [float(v) for v in a2]
+    d.ecut = float(ecut)
+    d.ng_exact = int(ng_exact)
+    z = _f64(z_edges)
+    keep.append(z)
+    d.n_slices = len(z) - 1
+    d.z_edges = _as_dp(z)
+    if wells_xyz is not None and len(wells_xyz):
+        w, v, s = _f64(wells_xyz).reshape(-1, 3), _f64(v0), _f64(sigma)
+        keep += [w, v, s]
+        d.n_wells = len(w)
+        d.well_xyz, d.well_v0, d.well_sigma = _as_dp(w), _as_dp(v), _as_dp(s)
+    for side, (xy, lv0, ls, period) in enumerate(leads):
+        d.lead_period[side] = float(period)
+        if xy is not None and len(xy):
+            xy, lv0, ls = _f64(xy).reshape(-1, 2), _f64(lv0), _f64(ls)
+            keep += [xy, lv0, ls]
+            d.lead_n_wells[side] = len(xy)
+            d.lead_well_xy[side] = _as_dp(xy)
+            d.lead_well_v0[side] = _as_dp(lv0)
+            d.lead_well_sigma[side] = _as_dp(ls)
+    d.vg_half[:] = [int(vg_half[0]), int(vg_half[1])]
+    if slice_vg is not None:
+        sv = _c128(slice_vg)
+        keep.append(sv)
+        d.slice_vg = sv.ctypes.data
+    for side in (0, 1):
+        if lead_vg[side] is not None:
+            lv = _c128(lead_vg[side])
+            keep.append(lv)
+            d.lead_vg[side] = lv.ctypes.data
+    d.precision = int(precision)
+    d.refine_iters = int(refine_iters)
+    has_shift = False
+    if well_shift_rate is not None:
+        r = _f64(well_shift_rate).reshape(-1, 2)
+        keep.append(r)
+        d.well_shift_rate = _as_dp(r)
+        has_shift = True
+    if lead_shift_rate is not None:
+        lr = np.asarray(lead_shift_rate, dtype=np.float64).reshape(2, 2)
+        for side in (0, 1):
+            d.lead_shift_rate[side][0] = float(lr[side, 0])
+            d.lead_shift_rate[side][1] = float(lr[side, 1])
+        has_shift = has_shift or bool(np.any(lr))
+    return d, keep, has_shift
+
+
+def _instance_geometry(inst, refine_iters=0):
+    """Keyword arguments of _build_desc for a problem description object
+    (attributes as in synthetic.Instance)."""
+    leads = [(L.wells_xy, L.v0, L.sigma, L.period) for L in (inst.lead_left, inst.lead_right)]
+    lead_vg = inst.lead_vg if inst.lead_vg is not None else (None, None)
+    return dict(a1=inst.a1, a2=inst.a2, z_edges=inst.z_edges, ecut=inst.ecut,
+                ng_exact=inst.ng_exact, wells_xyz=inst.wells_xyz, v0=inst.v0, sigma=inst.sigma,
+                leads=leads, slice_vg=inst.slice_vg, lead_vg=lead_vg, vg_half=inst.vg_half,
+                refine_iters=refine_iters,
+                well_shift_rate=getattr(inst, "gap_rate_wells", None),
+                lead_shift_rate=getattr(inst, "gap_rate_leads", None))
+
+
 class Context:
     """An owned pw_ctx: one junction problem on the current CUDA device."""
 
-    def __init__(self, *, a1, a2, z_edges, ecut=0.0, ng_exact=0, wells_xyz=None, v0=None,
-                 sigma=None, leads=((None, None, None, 1.0), (None, None, None, 1.0)),
-                 slice_vg=None, lead_vg=(None, None), vg_half=(0, 0), precision=FP64,
-                 refine_iters=0, stream=None):
-        keep = []
-        d = SetupDesc()
-        d.a1[:] = [float(v) for v in a1]
-        d.a2[:] = [float(v) for v in a2]
-        d.ecut = float(ecut)
-        d.ng_exact = int(ng_exact)
-        z = _f64(z_edges)
-        keep.append(z)
-        d.n_slices = len(z) - 1
-        d.z_edges = _as_dp(z)
-        if wells_xyz is not None and len(wells_xyz):
-            w, v, s = _f64(wells_xyz).reshape(-1, 3), _f64(v0), _f64(sigma)
-            keep += [w, v, s]
-            d.n_wells = len(w)
-            d.well_xyz, d.well_v0, d.well_sigma = _as_dp(w), _as_dp(v), _as_dp(s)
-        for side, (xy, lv0, ls, period) in enumerate(leads):
-            d.lead_period[side] = float(period)
-            if xy is not None and len(xy):
-                xy, lv0, ls = _f64(xy).reshape(-1, 2), _f64(lv0), _f64(ls)
-                keep += [xy, lv0, ls]
-                d.lead_n_wells[side] = len(xy)
-                d.lead_well_xy[side] = _as_dp(xy)
-                d.lead_well_v0[side] = _as_dp(lv0)
-                d.lead_well_sigma[side] = _as_dp(ls)
-        d.vg_half[:] = [int(vg_half[0]), int(vg_half[1])]
-        if slice_vg is not None:
-            sv = _c128(slice_vg)
-            keep.append(sv)
-            d.slice_vg = sv.ctypes.data
-        for side in (0, 1):
-            if lead_vg[side] is not None:
-                lv = _c128(lead_vg[side])
-                keep.append(lv)
-                d.lead_vg[side] = lv.ctypes.data
-        d.precision = int(precision)
-        d.refine_iters = int(refine_iters)
+    def __init__(self, *, precision=FP64, stream=None, **geometry):
+        d, keep, has_shift = _build_desc(precision=precision, **geometry)
+        self.has_shift = has_shift
         h = _vp()
         st = _lib.pw_setup(ctypes.byref(d), stream, ctypes.byref(h))
         if st != 0:
@@ -180,15 +223,7 @@ class Context:
     def from_instance(cls, inst, precision=FP64, refine_iters=0, stream=None):
         """Marshal a problem description object (attributes as in
         synthetic.Instance) into pw_setup."""
-        leads = []
-        for L in (inst.lead_left, inst.lead_right):
-            leads.append((L.wells_xy, L.v0, L.sigma, L.period))
-        lead_vg = inst.lead_vg if inst.lead_vg is not None else (None, None)
-        return cls(a1=inst.a1, a2=inst.a2, z_edges=inst.z_edges, ecut=inst.ecut,
-                   ng_exact=inst.ng_exact, wells_xyz=inst.wells_xyz, v0=inst.v0,
-                   sigma=inst.sigma, leads=leads, slice_vg=inst.slice_vg, lead_vg=lead_vg,
-                   vg_half=inst.vg_half, precision=precision, refine_iters=refine_iters,
-                   stream=stream)
+        return cls(precision=precision, stream=stream, **_instance_geometry(inst, refine_iters))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -265,18 +300,22 @@ class Context:
         self._check(st, "pw_transmission")
         return st
 
-    def grad(self, E, kpar, weight=None, n_wells=None):
+    def grad(self, E, kpar, weight=None, n_wells=None, gap=False):
         """(sum_i w_i T_i, d/dV0 of that sum for every device well) by the
-        adjoint in FP64 (pw_grad)."""
+        adjoint in FP64 (pw_grad); with gap=True also d/dtheta of the sum for
+        the geometry motion given at setup (a third element)."""
         E = _f64(E).reshape(-1)
         k = _f64(kpar).reshape(-1, 2)
         w = None if weight is None else _f64(weight).reshape(-1)
         sumT = np.zeros(1)
         nw = int(n_wells) if n_wells is not None else 0
         dV0 = np.zeros(max(nw, 1))
+        dgap = np.zeros(1)
         st = _lib.pw_grad(self._h, len(E), _as_dp(E), _as_dp(k), _as_dp(w) if w is not None else None,
-                          _as_dp(sumT), _as_dp(dV0) if nw else None, None)
+                          _as_dp(sumT), _as_dp(dV0) if nw else None, _as_dp(dgap) if gap else None)
         self._check(st, "pw_grad")
+        if gap:
+            return float(sumT[0]), dV0[:nw], float(dgap[0])
         return float(sumT[0]), dV0[:nw]
 
     def set_profiling(self, on=True):
@@ -299,5 +338,78 @@ class Context:
             raise PwError(st, where)
 
 
-__all__ = ["Context", "PwError", "FP64", "MIXED_FP32", "EXPORTS", "LIB_PATH", "lib",
+class Batch:
+    """An owned pw_batch: independent problems of uneven basis size and slice
+    count, one (E, k_par) point each (pw_setup_batch)."""
+
+    def __init__(self, geometries, precision=FP64, refine_iters=0, stream=None):
+        descs = (SetupDesc * len(geometries))()
+        keep = []
+        for i, g in enumerate(geometries):
+            d, k, _ = _build_desc(**dict(g, precision=precision, refine_iters=refine_iters))
+            descs[i] = d
+            keep.append(k)
+        h = _vp()
+        st = _lib.pw_setup_batch(len(geometries), descs, stream, ctypes.byref(h))
+        if st != 0:
+            raise PwError(st, "pw_setup_batch")
+        self._h = h
+        self.n = len(geometries)
+
+    @classmethod
+    def from_instances(cls, insts, precision=FP64, refine_iters=0, stream=None):
+        return cls([_instance_geometry(x) for x in insts], precision, refine_iters, stream)
+
+    def set_options(self, use_graph=True, variant=-1):
+        Context._check(_lib.pw_batch_set_options(self._h, int(bool(use_graph)), int(variant)),
+                       "pw_batch_set_options")
+
+    def transmission(self, E, kpar, T_out, nopen_out=None, err_out=None, allow_threshold=False):
+        """T of instance i at (E[i], kpar[i]) into T_out[i] (device float64)."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        if len(E) != self.n or len(k) != self.n:
+            raise ValueError("one (E, k_par) point per instance")
+        st = _lib.pw_transmission_batch(self._h, _as_dp(E), _as_dp(k), _ptr(T_out), _ptr(nopen_out),
+                                        _ptr(err_out))
+        if st == PW_ETHRESH and allow_threshold:
+            return st
+        Context._check(st, "pw_transmission_batch")
+        return st
+
+    def stats(self):
+        """Stage times of the last call and the tile variant chosen per N_G."""
+        out = np.zeros(8)
+        ng = np.zeros(64, dtype=np.int32)
+        var = np.zeros(64, dtype=np.int32)
+        cnt = np.zeros(1, dtype=np.int32)
+        Context._check(_lib.pw_batch_get_stats(self._h, _as_dp(out), ng.ctypes.data_as(_ip),
+                                               var.ctypes.data_as(_ip), 64,
+                                               cnt.ctypes.data_as(_ip)), "pw_batch_get_stats")
+        keys = ["modes_ms", "overlap_ms", "sweep_ms", "refine_ms", "tune_ms", "chunks",
+                "graph_launches", "sweep_launches"]
+        res = dict(zip(keys, out.tolist()))
+        k = int(min(cnt[0], 64))
+        res["variant"] = {int(ng[i]): int(var[i]) for i in range(k)}
+        return res
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+__all__ = ["Context", "Batch", "PwError", "FP64", "MIXED_FP32", "EXPORTS", "LIB_PATH", "lib",
            "compose_noalloc"]

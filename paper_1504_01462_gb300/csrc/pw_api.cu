@@ -18,8 +18,8 @@ using pw::PointDesc;
 namespace {
 
 constexpr double kShellQuantum = 1e-8;   // Ry: |G|^2 closer than this is one shell
-constexpr double kThreshold = 1e-10;     // Ry: electrode channel at threshold
-constexpr double kRefineTol = 1e-9;      // stop refining once corrections of t are below this
+constexpr double kThreshold = pw::kThresholdRy;
+constexpr double kRefineTol = pw::kRefineTolRel;
 
 struct DevBuf {
   void *p = nullptr;
@@ -64,6 +64,12 @@ struct pw_ctx {
   // device copies of the device-region wells (kept for the adjoint)
   double *d_wxyz = nullptr, *d_wv0 = nullptr, *d_wsig = nullptr;
   int n_wells = 0;
+  // transverse motion of the wells and electrodes per unit of the geometry
+  // parameter of pw_grad's dgap (2 per well; left, right electrode)
+  double *d_wrate = nullptr;
+  double lead_rate[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  bool has_shift = false;
+  DevBuf dshift, lead_scr, lead_out;
   // launch timing (pw_set_profiling)
   struct Rec { cudaEvent_t a, b; int kind; int count; };
   bool profiling = false;
@@ -109,10 +115,15 @@ pw_status latch(pw_ctx *c, pw_status s) {
   return s;
 }
 
-#define CK(call)                                         \
-  do {                                                   \
-    cudaError_t e_ = (call);                             \
-    if (e_ != cudaSuccess) return latch(ctx, e_ == cudaErrorMemoryAllocation ? PW_ENOMEM : PW_ECUDA); \
+// A failed runtime call is reported once: the runtime's last-error state is
+// cleared so that it does not resurface in a later, unrelated call.
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      cudaGetLastError();                                                                           \
+      return latch(ctx, e_ == cudaErrorMemoryAllocation ? PW_ENOMEM : PW_ECUDA);                   \
+    }                                                                                               \
   } while (0)
 
 pw_status ensure(pw_ctx *ctx, DevBuf &b, size_t bytes) {
@@ -233,12 +244,12 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
   CK(cudaGetLastError());
   pw::launch_eig(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_V + (size_t)s0 * nq * nn,
                  ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
-                 ctx->stream);
+                 ctx->stream, ctx->precision == PW_MIXED_FP32);
   CK(cudaGetLastError());
   st1.done();
   Stage st2(ctx, 2, s1 - s0);
   pw::launch_overlaps(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq,
-                      s1 - s0, ctx->stream);
+                      s1 - s0, ctx->stream, ctx->precision == PW_MIXED_FP32);
   CK(cudaGetLastError());
   st2.done();
   std::vector<int> stat(nmat);
@@ -295,6 +306,23 @@ void group_by_k(int npts, const double *kpar, std::vector<std::vector<int>> &gro
 }
 
 }  // namespace
+
+pw::CtxView pw::ctx_view(const pw_ctx *c) {
+  CtxView v;
+  v.n = c->n;
+  v.N = c->N;
+  v.Dm = c->Dm;
+  v.Dn = c->Dn;
+  v.num_sms = c->num_sms;
+  v.precision = c->precision;
+  v.refine_iters = c->refine_iters;
+  v.tab = c->d_tab;
+  v.mn = c->d_mn;
+  v.G = c->d_G;
+  v.dz = c->dz.data();
+  v.stream = c->stream;
+  return v;
+}
 
 extern "C" {
 
@@ -425,11 +453,23 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
       return st;
     }
     ctx->n_wells = d->n_wells;
+    if (d->well_shift_rate) {
+      if ((st = upload(ctx, &ctx->d_wrate, d->well_shift_rate, 2 * (size_t)d->n_wells)) != PW_OK) {
+        pw_destroy(ctx);
+        return st;
+      }
+      ctx->has_shift = true;
+    }
     ta.slices.xyz = ctx->d_wxyz;
     ta.slices.v0 = ctx->d_wv0;
     ta.slices.sigma = ctx->d_wsig;
     ta.slices.n = d->n_wells;
   }
+  for (int s = 0; s < 2; ++s)
+    for (int c = 0; c < 2; ++c) {
+      ctx->lead_rate[s][c] = d->lead_shift_rate[s][c];
+      if (d->lead_shift_rate[s][c] != 0.0) ctx->has_shift = true;
+    }
   for (int s = 0; s < 2; ++s) {
     ta.period[s] = d->lead_period[s] > 0 ? d->lead_period[s] : 1.0;
     if (!d->lead_vg[s] && d->lead_n_wells[s] > 0) {
@@ -459,7 +499,8 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
-                  ctx->d_wsig, ctx->corr.p};
+                  ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
+                  ctx->lead_out.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -549,7 +590,7 @@ pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double 
       std::vector<PointDesc> pd(nb);
       for (int i = 0; i < nb; ++i) {
         const int idx = g[b0 + i];
-        pd[i] = PointDesc{E[idx], 0, 0, 0, idx, 0};
+        pd[i] = pw::make_point(E[idx], 0, 0, 0, idx, 0, ctx->N, i);
       }
       CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
       CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
@@ -626,7 +667,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       bool th = false;
       const int nL = count_open(ctx->EL[slot], E[idx], &th);
       const int nR = count_open(ctx->ER[slot], E[idx], &th);
-      all[i] = PointDesc{E[idx], slot, nL, nR, idx, th ? 1 : 0};
+      all[i] = pw::make_point(E[idx], slot, nL, nR, idx, th ? 1 : 0, ctx->N, 0);
       if (th) result = PW_ETHRESH;
       else nc = std::max(nc, nL);
     }
@@ -650,6 +691,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
     for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
       const int nb = (int)std::min(pts.size() - b0, (size_t)bmax);
       std::vector<PointDesc> pd(all.begin() + b0, all.begin() + b0 + nb);
+      for (int i = 0; i < nb; ++i) pd[i] = pw::make_point(pd[i].E, pd[i].kset, pd[i].nL, pd[i].nR, pd[i].out,
+                                                          pd[i].skip, N, i);
       if ((st = ensure(ctx, ctx->R, (size_t)nb * nn * esz)) ||
           (st = ensure(ctx, ctx->M, (size_t)nb * n * ncols * esz)) ||
           (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
@@ -668,7 +711,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
            (st = ensure(ctx, ctx->Fr, (size_t)(N + 1) * vec * sizeof(zc))) ||
            (st = ensure(ctx, ctx->Gr, (size_t)(N + 1) * vec * sizeof(zc))) ||
            (st = ensure(ctx, ctx->carry, vec * sizeof(zc))) ||
-           (st = ensure(ctx, ctx->corr, (size_t)nb * sizeof(double))) ||
+           (st = ensure(ctx, ctx->corr, (size_t)2 * nb * sizeof(double))) ||
            (st = ensure(ctx, ctx->tmp, 2 * vec * sizeof(cc)))))
         return st;
       CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
@@ -695,6 +738,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.PIVst = refine ? (int *)ctx->PIVst.p : nullptr;
       a.KV = ctx->KV.p;
       a.mirror = 0;
+      CK(pw::prepare_sweep_batched(n, ctx->precision, 0));
       Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n));
       for (int p = 0; p <= N; ++p) {
         cudaEvent_t w0 = nullptr, w1 = nullptr;
@@ -723,6 +767,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.carry = (zc *)ctx->carry.p;
         r.tmp = (cc *)ctx->tmp.p;
         r.corr = (double *)ctx->corr.p;
+        r.corr_prev = r.corr + nb;
         r.T = T_dev;
         r.t = (zc *)t_dev;
         r.nopen = nopen_dev;
@@ -730,6 +775,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.n = n;
         r.N = N;
         r.nc = nc;
+        r.x_slots = (long long)nb * (N + 2);
+        r.st_slots = (long long)nb * (N + 1);
         Stage s3(ctx, 3, 1);
         int passes = 0;
         CK(pw::launch_refine(r, nb, std::min(2, ctx->refine_iters), ctx->refine_iters, kRefineTol,
@@ -754,8 +801,11 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
                   double *sumT_host, double *dV0_host, double *dgap_host) {
   if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar)) || !sumT_host) return PW_EINVAL;
   if (ctx->err) return ctx->err;
-  if (dgap_host) return PW_EINVAL;                  // the gap derivative is not provided
+  if (dgap_host && !ctx->has_shift) return PW_EINVAL;   // no geometry motion was given
   if (dV0_host && ctx->n_wells == 0) return PW_EINVAL;   // explicit tables have no wells
+  const bool lead_shift = dgap_host && (ctx->lead_rate[0][0] != 0.0 || ctx->lead_rate[0][1] != 0.0 ||
+                                        ctx->lead_rate[1][0] != 0.0 || ctx->lead_rate[1][1] != 0.0);
+  double dgap_sum = 0.0;
   const int n = ctx->n, N = ctx->N;
   const size_t nn = (size_t)n * n;
   const int tsz = ctx->tsz;
@@ -788,7 +838,7 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
       bool th = false;
       const int nL = count_open(ctx->EL[slot], E[idx], &th);
       const int nR = count_open(ctx->ER[slot], E[idx], &th);
-      all[i] = PointDesc{E[idx], slot, nL, nR, idx, th ? 1 : 0};
+      all[i] = pw::make_point(E[idx], slot, nL, nR, idx, th ? 1 : 0, N, 0);
       if (th) result = PW_ETHRESH;
       else nc = std::max(nc, std::max(nL, nR));
     }
@@ -808,6 +858,8 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
     for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
       const int nb = (int)std::min(pts.size() - b0, (size_t)bmax);
       std::vector<PointDesc> pd(all.begin() + b0, all.begin() + b0 + nb);
+      for (int i = 0; i < nb; ++i) pd[i] = pw::make_point(pd[i].E, pd[i].kset, pd[i].nL, pd[i].nR, pd[i].out,
+                                                          pd[i].skip, N, i);
       std::vector<PointDesc> pm(pd);
       for (auto &q : pm) std::swap(q.nL, q.nR);     // mirrored: incident from the right electrode
       std::vector<double> w(nb, 1.0);
@@ -862,6 +914,7 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
         a.Ust = ctx->Ust.p;
         a.KV = ctx->KV.p;
         a.mirror = mirror;
+        CK(pw::prepare_sweep_batched(n, PW_FP64, 0));
         for (int p = 0; p <= N; ++p) CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream));
         pw::GradArgs g;
         g.pts = a.pts;
@@ -899,6 +952,16 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
       h.nc = nc;
       h.npts = nb;
       for (size_t sl = 0; sl < ks.size(); ++sl) CK(pw::launch_grad_gamma(h, (int)sl, ctx->stream));
+      std::vector<double> lead_h(nb, 0.0);
+      if (lead_shift) {
+        if ((st = ensure(ctx, ctx->lead_scr, (size_t)nb * 4 * vec * sizeof(zc))) ||
+            (st = ensure(ctx, ctx->lead_out, (size_t)nb * sizeof(double))))
+          return st;
+        CK(pw::launch_grad_leads(h, ctx->d_HU, ctx->d_G, (zc *)ctx->lead_scr.p, ctx->lead_rate,
+                                 (double *)ctx->lead_out.p, ctx->stream));
+        CK(cudaMemcpyAsync(lead_h.data(), ctx->lead_out.p, nb * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+      }
       std::vector<double> Th(nb);
       std::vector<int> sth(nb), stm(nb);
       CK(cudaMemcpyAsync(Th.data(), ctx->Tg.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -907,7 +970,10 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
       CK(cudaStreamSynchronize(ctx->stream));
       for (int i = 0; i < nb; ++i) {
         if (sth[i] || stm[i]) result = PW_ESINGULAR;
-        else if (!pd[i].skip) sumT += w[i] * Th[i];
+        else if (!pd[i].skip) {
+          sumT += w[i] * Th[i];
+          dgap_sum += w[i] * lead_h[i];
+        }
       }
     }
     pw::GammaArgs h;
@@ -921,7 +987,9 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
                               ctx->stream));
   }
   *sumT_host = sumT;
-  if (dV0_host) {
+  const bool wells_shift = dgap_host && ctx->d_wrate && ctx->n_wells > 0;
+  if (dV0_host || wells_shift) {
+    if (wells_shift && (st = ensure(ctx, ctx->dshift, (size_t)ctx->n_wells * sizeof(double)))) return st;
     pw::GammaArgs h;
     memset(&h, 0, sizeof(h));
     h.gtab = (zc *)ctx->gtab.p;
@@ -933,12 +1001,20 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
     ws.sigma = ctx->d_wsig;
     ws.n = ctx->n_wells;
     const double b[4] = {ctx->b1[0], ctx->b1[1], ctx->b2[0], ctx->b2[1]};
-    CK(pw::launch_grad_wells(h, ws, ctx->d_z, b, ctx->area, ctx->Dm, ctx->Dn, (double *)ctx->dV0.p,
-                             ctx->stream));
-    CK(cudaMemcpyAsync(dV0_host, ctx->dV0.p, ctx->n_wells * sizeof(double), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(pw::launch_grad_wells(h, ws, ctx->d_z, b, ctx->area, ctx->Dm, ctx->Dn,
+                             dV0_host ? (double *)ctx->dV0.p : nullptr, wells_shift ? ctx->d_wrate : nullptr,
+                             wells_shift ? (double *)ctx->dshift.p : nullptr, ctx->stream));
+    if (dV0_host)
+      CK(cudaMemcpyAsync(dV0_host, ctx->dV0.p, ctx->n_wells * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    std::vector<double> sh(wells_shift ? ctx->n_wells : 0);
+    if (wells_shift)
+      CK(cudaMemcpyAsync(sh.data(), ctx->dshift.p, ctx->n_wells * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    for (double v : sh) dgap_sum += v;
   }
+  if (dgap_host) *dgap_host = dgap_sum;
   if (result == PW_ESINGULAR) latch(ctx, result);
   return result;
 }

@@ -25,6 +25,11 @@ __host__ __device__ constexpr size_t gemm_smem_elems() {
          size_t(Tile<T, NTH>::BK) * (Tile<T, NTH>::BN + 1);
 }
 
+// Accumulators of the native types need no renormalisation between k-tiles
+// (the double-float accumulator of pw_df.cuh overloads this).
+template <typename T>
+__device__ __forceinline__ void cacc_renorm(cx<T> &) {}
+
 // C(i,j) = fe(i, j, sum_l fa(i,l) fb(l,j)) for 0 <= i < m, 0 <= j < n, 0 <= l < k.
 // fa/fb return cx<T>; fa is read with i fastest (A column-major), fb with l
 // fastest (B column-major), so plain column-major operands load coalesced.
@@ -94,6 +99,10 @@ __device__ void cta_gemm_t(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem
 #pragma unroll
           for (int c = 0; c < TN; ++c) cfma(acc[r][c], a[r], b[c]);
       }
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) cacc_renorm(acc[r][c]);
       __syncthreads();
     }
 #pragma unroll
@@ -240,6 +249,94 @@ __device__ void lu_panel(cx<T> *M, int ld, int n, int ncols, int j0, int *piv, c
       }
       col[r] = x;
     }
+  }
+  __syncthreads();
+}
+
+// lu_panel with the panel staged in shared memory: P holds rows j0..n-1 of
+// the panel's columns (leading dimension n - j0), so every column step of the
+// unblocked factorisation (pivot search, row swap, scaling, rank-1 update)
+// reads and writes shared memory only.  The right-hand columns then get the
+// panel's row swaps and U12 = L11^{-1} A12 with each column's nb entries held
+// in registers.  Same pivots, same operations and the same result layout as
+// lu_panel (FP32 only: an FP64 panel of 512 rows does not fit).
+template <typename T, int NTH = NT>
+__device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *piv, cx<T> *P, cx<T> *Ls,
+                              T *sval, int *sidx, int *flag) {
+  constexpr int NB = Tile<T, NTH>::NB;
+  const int tid = threadIdx.x;
+  const int nb = min(NB, n - j0), R = n - j0;
+  for (int e = tid; e < R * nb; e += NTH) {
+    const int r = e % R, c = e / R;
+    P[e] = M[(j0 + r) + (size_t)(j0 + c) * ld];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nb; ++jj) {
+    T best = T(-1);
+    int bi = jj;
+    for (int r = jj + tid; r < R; r += NTH) {
+      const T v = cabs1(P[r + jj * R]);
+      if (v > best) { best = v; bi = r; }
+    }
+    const int p = block_argmax<T, NTH>(best, bi, sval, sidx);
+    if (tid == 0) piv[j0 + jj] = j0 + p;
+    if (p != jj) {
+      for (int c = tid; c < nb; c += NTH) {
+        const cx<T> a = P[jj + c * R];
+        P[jj + c * R] = P[p + c * R];
+        P[p + c * R] = a;
+      }
+    }
+    __syncthreads();
+    cx<T> d = P[jj + jj * R];
+    if (d.re == T(0) && d.im == T(0)) {
+      if (tid == 0) atomicOr(flag, 1);
+      d = mkc<T>(tiny_pivot<T>(), T(0));
+    }
+    const cx<T> inv = cinv(d);
+    for (int r = jj + 1 + tid; r < R; r += NTH) P[r + jj * R] = cmul(P[r + jj * R], inv);
+    __syncthreads();
+    const int rows = R - jj - 1, cols = nb - jj - 1;
+    for (int e = tid; e < rows * cols; e += NTH) {
+      const int r = jj + 1 + e % rows, c = jj + 1 + e / rows;
+      cx<T> v = P[r + c * R];
+      const cx<T> l = P[r + jj * R], u = P[jj + c * R];
+      v.re -= l.re * u.re - l.im * u.im;
+      v.im -= l.re * u.im + l.im * u.re;
+      P[r + c * R] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < R * nb; e += NTH) {
+    const int r = e % R, c = e / R;
+    M[(j0 + r) + (size_t)(j0 + c) * ld] = P[e];
+  }
+  for (int e = tid; e < nb * nb; e += NTH) {
+    const int r = e % nb, s2 = e / nb;
+    Ls[r + s2 * NB] = P[r + s2 * R];
+  }
+  __syncthreads();
+  for (int c = j0 + nb + tid; c < ncols; c += NTH) {
+    cx<T> *col = M + (size_t)c * ld + j0;
+    for (int r = 0; r < nb; ++r) {
+      const int p = piv[j0 + r] - j0;
+      if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
+    }
+    cx<T> x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[r] : czero<T>();
+#pragma unroll
+    for (int r = 1; r < NB; ++r) {
+#pragma unroll
+      for (int s2 = 0; s2 < r; ++s2) {
+        const cx<T> l = Ls[r + s2 * NB];
+        x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
+        x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r < nb) col[r] = x[r];
   }
   __syncthreads();
 }

@@ -241,13 +241,19 @@ __global__ void __launch_bounds__(GT) k_grad_fold(GammaArgs h, int slot, const z
 }
 
 // dT/dV0_w = Im sum_p sum_dG dV^p(dG)/dV0_w g_p(dG); one CTA per device well.
+// With `rate` (2 per well) also the derivative for well w moving transversally
+// at that rate: its table picks up -i dG.rate, so
+// dshift_w = Im sum (-i dG.rate) v0_w dV^p/dV0_w g_p = -sum (dG.rate) Re(v0_w dV g).
 __global__ void __launch_bounds__(GT) k_grad_wells(GammaArgs h, WellSet w, const double *z_edges,
                                                    double b1x, double b1y, double b2x, double b2y,
-                                                   double area, int Dm, int Dn, double *dV0) {
+                                                   double area, int Dm, int Dn, double *dV0,
+                                                   const double *rate, double *dshift) {
   const int iw = blockIdx.x, N = h.N;
   const int tw = 2 * Dn + 1, tsz = (2 * Dm + 1) * tw;
   const double s = w.sigma[iw], X = w.xyz[3 * iw], Y = w.xyz[3 * iw + 1], Zw = w.xyz[3 * iw + 2];
-  double acc = 0.0;
+  const double rx = rate ? rate[2 * iw] : 0.0, ry = rate ? rate[2 * iw + 1] : 0.0;
+  const double v0 = w.v0[iw];
+  double acc = 0.0, accs = 0.0;
   for (int p = 1; p <= N; ++p) {
     const double zlo = z_edges[p - 1], zhi = z_edges[p];
     const double wz = (s * sqrt(0.5 * M_PI) / (zhi - zlo)) *
@@ -262,16 +268,123 @@ __global__ void __launch_bounds__(GT) k_grad_wells(GammaArgs h, WellSet w, const
       const zc dv = mkc<double>(amp * cs, -amp * sn);
       const zc gv = gt[e];
       acc += dv.re * gv.im + dv.im * gv.re;   // Im(dv * g)
+      accs -= (gx * rx + gy * ry) * v0 * (dv.re * gv.re - dv.im * gv.im);
     }
   }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  __shared__ double red[GT / 32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int off = 16; off > 0; off >>= 1) {
+    acc += __shfl_down_sync(0xffffffffu, acc, off);
+    accs += __shfl_down_sync(0xffffffffu, accs, off);
+  }
+  __shared__ double red[2][GT / 32];
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc;
+    red[1][threadIdx.x >> 5] = accs;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < GT / 32; ++i) t += red[i];
-    dV0[iw] = t;
+    double t = 0.0, ts = 0.0;
+    for (int i = 0; i < GT / 32; ++i) {
+      t += red[0][i];
+      ts += red[1][i];
+    }
+    if (dV0) dV0[iw] = t;
+    if (dshift) dshift[iw] = ts;
+  }
+}
+
+// Electrode-translation term, one CTA per point.  With the two states' values
+// and z-derivatives on the contact planes (left: z = 0 from the electrode's
+// amplitudes of slice 0; right: z = z_N from those of slice N+1),
+//     c = U (a + b),  c' = i U K (a - b),  d = conj(U) (a' + b'),  d' = i conj(U) K (a' - b'),
+// an electrode moved by delta contributes X = -/+ i (d^T Gd c' - d'^T Gd c)
+// (Gd = diag(G.delta), minus on the left) in place of the slice integral, and
+// dT = Im sum_ij W_ij X_ij, W_ij = conj(t_ij) / k_j^L.  out[pt] is that sum
+// for the electrodes' rates (rL, rR).  scr: 4 n nc per point.
+__global__ void __launch_bounds__(GT) k_grad_leads(GammaArgs h, const zc *U_all, const double *Gv, zc *scr,
+                                                   double rLx, double rLy, double rRx, double rRy,
+                                                   double *out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.x;
+  const PointDesc d = h.pts[pt];
+  const int n = h.n, N = h.N, nc = h.nc;
+  if (d.skip || h.status[pt] || h.status_m[pt] || d.nL == 0 || d.nR == 0) {
+    if (threadIdx.x == 0) out[pt] = 0.0;
+    return;
+  }
+  zc *ks = reinterpret_cast<zc *>(smraw);
+  double *ikL = reinterpret_cast<double *>(ks + n);
+  __shared__ double red[GT / 32];
+  const int nL = d.nL, nR = d.nR;
+  const size_t nn = (size_t)n * n, vec = (size_t)n * nc;
+  const double *EL = h.En + ((size_t)d.kset * (N + 2)) * n;
+  for (int j = threadIdx.x; j < nL; j += GT) ikL[j] = 1.0 / sqrt(d.E - EL[j]);
+  auto amp = [&](const zc *base, int q) { return base + ((size_t)pt * (N + 2) + q) * vec; };
+  const zc *t = amp(h.Xa, N + 1);
+  zc *C = scr + (size_t)pt * 4 * vec, *Cp = C + vec, *D = Cp + vec, *Dp = D + vec;
+  double total = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    const double rx = side ? rRx : rLx, ry = side ? rRy : rLy;
+    if (rx == 0.0 && ry == 0.0) continue;
+    const int q = side ? N + 1 : 0;
+    const zc *U = U_all + ((size_t)d.kset * (N + 2) + q) * nn;
+    const double *Eq = h.En + ((size_t)d.kset * (N + 2) + q) * n;
+    const zc *A = amp(h.Xa, q), *B = amp(h.Xb, q);
+    const zc *Ap = amp(h.Xb_m, N + 1 - q), *Bp = amp(h.Xa_m, N + 1 - q);   // a', b' of slice q
+    __syncthreads();
+    for (int m = threadIdx.x; m < n; m += GT) ks[m] = kz_branch(d.E, Eq[m]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * (nL + nR); e += GT) {
+      const int g = e % n, col = e / n;
+      const bool isc = col < nL;
+      const int j = isc ? col : col - nL;
+      const zc *X1 = isc ? A : Ap, *X2 = isc ? B : Bp;
+      zc v = czero<double>(), dv = czero<double>();
+      for (int m = 0; m < n; ++m) {
+        const zc u = isc ? U[g + (size_t)m * n] : cconj(U[g + (size_t)m * n]);
+        const zc x1 = X1[m + (size_t)j * n], x2 = X2[m + (size_t)j * n];
+        cfma(v, u, cadd(x1, x2));
+        cfma(dv, u, cmul(ks[m], csub(x1, x2)));
+      }
+      const zc idv = mkc<double>(-dv.im, dv.re);   // i * dv
+      if (isc) {
+        C[g + (size_t)j * n] = v;
+        Cp[g + (size_t)j * n] = idv;
+      } else {
+        D[g + (size_t)j * n] = v;
+        Dp[g + (size_t)j * n] = idv;
+      }
+    }
+    __syncthreads();
+    zc sx = czero<double>(), sy = czero<double>();
+    for (int g = threadIdx.x; g < n; g += GT) {
+      zc acc = czero<double>();
+      for (int j = 0; j < nL; ++j) {
+        const zc cp = Cp[g + (size_t)j * n], c = C[g + (size_t)j * n];
+        zc wd = czero<double>(), wdp = czero<double>();   // sum_i W_ij d_gi, sum_i W_ij d'_gi
+        for (int i = 0; i < nR; ++i) {
+          const zc tc = cconj(t[i + (size_t)j * n]);
+          const zc wv = mkc<double>(tc.re * ikL[j], tc.im * ikL[j]);
+          cfma(wd, wv, D[g + (size_t)i * n]);
+          cfma(wdp, wv, Dp[g + (size_t)i * n]);
+        }
+        cfma(acc, wd, cp);
+        acc = csub(acc, cmul(wdp, c));
+      }
+      sx = cadd(sx, cscale(Gv[2 * g], acc));
+      sy = cadd(sy, cscale(Gv[2 * g + 1], acc));
+    }
+    // Im(-/+ i s) = -/+ Re(s)
+    const double sign = side ? 1.0 : -1.0;
+    total += sign * (rx * sx.re + ry * sy.re);
+  }
+  for (int off = 16; off > 0; off >>= 1) total += __shfl_down_sync(0xffffffffu, total, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = total;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < GT / 32; ++i) s += red[i];
+    out[pt] = s;
   }
 }
 
@@ -303,9 +416,17 @@ cudaError_t launch_grad_fold(const GammaArgs &h, int slot, const zc *U, zc *T1, 
 }
 
 cudaError_t launch_grad_wells(const GammaArgs &h, const WellSet &w, const double *z_edges, const double *b,
-                              double area, int Dm, int Dn, double *dV0, cudaStream_t s) {
+                              double area, int Dm, int Dn, double *dV0, const double *rate, double *dshift,
+                              cudaStream_t s) {
   if (w.n <= 0) return cudaSuccess;
-  k_grad_wells<<<w.n, GT, 0, s>>>(h, w, z_edges, b[0], b[1], b[2], b[3], area, Dm, Dn, dV0);
+  k_grad_wells<<<w.n, GT, 0, s>>>(h, w, z_edges, b[0], b[1], b[2], b[3], area, Dm, Dn, dV0, rate, dshift);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_leads(const GammaArgs &h, const zc *U_all, const double *G, zc *scr,
+                              const double rate[2][2], double *out, cudaStream_t s) {
+  const size_t smem = (size_t)h.n * (sizeof(zc) + sizeof(double));
+  k_grad_leads<<<h.npts, GT, smem, s>>>(h, U_all, G, scr, rate[0][0], rate[0][1], rate[1][0], rate[1][1], out);
   return cudaGetLastError();
 }
 

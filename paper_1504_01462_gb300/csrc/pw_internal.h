@@ -16,7 +16,32 @@ struct PointDesc {
   int nL, nR;   // open channels of the left / right electrode
   int out;      // index into the caller's output arrays
   int skip;     // 1: threshold point, write NaN and do nothing else
+  int N;        // device slices of the point's problem
+  int dz_off;   // start of its dz[0..N+1] in the dz array
+  long long en_off;   // its slice 0 in the eigenvalue array (units of n)
+  long long o_off;    // its interface 0 in the overlap array (units of n*n)
+  long long st_off;   // its interface 0 in the per-interface stores (Zst, Ust, LUst, PIVst, Fr, Gr)
+  long long x_off;    // its slice 0 in the per-slice amplitudes (Xa, Xb)
 };
+
+// Descriptor of a point of a one-problem context: slices and interfaces of
+// k-set `kset` at the uniform stride N+2 / N+1, stores of batch index `i`.
+inline PointDesc make_point(double E, int kset, int nL, int nR, int out, int skip, int N, int i) {
+  PointDesc d;
+  d.E = E;
+  d.kset = kset;
+  d.nL = nL;
+  d.nR = nR;
+  d.out = out;
+  d.skip = skip;
+  d.N = N;
+  d.dz_off = 0;
+  d.en_off = (long long)kset * (N + 2);
+  d.o_off = (long long)kset * (N + 1);
+  d.st_off = (long long)i * (N + 1);
+  d.x_off = (long long)i * (N + 2);
+  return d;
+}
 
 // Geometry shared by the potential kernels.
 struct WellSet {
@@ -51,7 +76,9 @@ struct SweepArgs {
   zc *t;
   int *nopen;
   double *err;
-  int n, N, nc;
+  int n, N, nc;          // N: the most slices of any point of the launch
+  int p;                 // current interface (set by launch_sweep_batched)
+  int panel_smem;        // LU panels staged in shared memory (set by launch_sweep_batched)
   void *Zst;             // FP32 sweep with refinement: per point (N+1) x n x n  (Z_p)
   void *Ust;             // per point (N+1) x n x nc  (u_p)
   void *LUst;            // per point (N+1) x n x n  (LU factors of W_p)
@@ -79,11 +106,14 @@ struct RefineArgs {
   zc *carry;             // per point n x nc
   cc *tmp;               // per point 2n x nc
   double *corr;          // per point: relative size of the last correction of a_{N+1}
+  double *corr_prev;     // per point: the same for the pass before
   double *T;
   zc *t;
   int *nopen;
   double *err;
-  int n, N, nc;
+  int n, N, nc;          // N: the most slices of any point
+  long long x_slots;     // sum over points of N+2 (the Xa, Xb slots)
+  long long st_slots;    // sum over points of N+1 (the Fr, Gr slots)
 };
 
 // Backward pass of a stored FP64 sweep (pw_grad.cu)
@@ -120,7 +150,10 @@ cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, cudaStream_t s);
 cudaError_t launch_grad_fold(const GammaArgs &h, int slot, const zc *U, zc *T1, const int *mn, int Dm,
                              int Dn, cudaStream_t s);
 cudaError_t launch_grad_wells(const GammaArgs &h, const WellSet &w, const double *z_edges, const double *b,
-                              double area, int Dm, int Dn, double *dV0, cudaStream_t s);
+                              double area, int Dm, int Dn, double *dV0, const double *rate, double *dshift,
+                              cudaStream_t s);
+cudaError_t launch_grad_leads(const GammaArgs &h, const zc *U_all, const double *G, zc *scr,
+                              const double rate[2][2], double *out, cudaStream_t s);
 
 // potential tables and slice Hamiltonians
 void launch_tables(const TableArgs &a, cudaStream_t s);
@@ -128,17 +161,22 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
                        int n, int nq, int Dm, int Dn, cudaStream_t s);
 // batched Hermitian eigensolver: H (in) -> U (out, same buffer); V scratch of
 // the same size; status: Jacobi sweeps per matrix (negative: not converged)
-void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s);
-// O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots
-void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s);
-// one interface of the left-to-right sweep for every point of a batch
-cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s);
-// the same interface step as a sequence of launches over (tiles x points)
-// (wy0, wy1: optional events recorded around the [W|Y] GEMM launch)
+void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s,
+                bool double_float = false);
+// O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots;
+// double_float: accumulate in double-float (48-bit) on the FP32 pipe
+void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s,
+                     bool double_float = false);
+// One interface step of the left-to-right sweep for every point of a batch,
+// as a sequence of launches over (tiles x points).  variant 0: 256-thread
+// CTAs with 64 x 64 GEMM tiles; 1: 512-thread CTAs with 128 x 64 tiles.
+// wy0, wy1: optional events recorded around the [W|Y] GEMM launch.
+// prepare_sweep_batched sets the kernels' shared-memory limits for n; call it
+// before the first step of a size (and outside a stream capture).
+cudaError_t prepare_sweep_batched(int n, int precision, int variant);
 cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
-                                 cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr);
+                                 cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr, int variant = 0);
 int sweep_batched_launches(int n);
-size_t sweep_smem_bytes(int n, int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p, u_p and the LU factors:
 // between min_iters and max_iters passes, stopping once every point's
 // estimated remaining error of a_{N+1} (c_i^2 / c_{i-1} from the relative
@@ -153,5 +191,20 @@ cudaError_t launch_slice_smatrix(const PointDesc *pts, const double *En, const z
 // star products (FP64)
 cudaError_t launch_compose(const zc *Sa, const zc *Sb, zc *Sab, zc *work, int *piv, int *status,
                            int n, int npts, cudaStream_t s);
+
+// Read-only view of a one-problem context's geometry (pw_api.cu), for the
+// batch executor (pw_batch.cu).
+struct CtxView {
+  int n, N, Dm, Dn, num_sms, precision, refine_iters;
+  const zc *tab;         // device, (N+2) Fourier tables
+  const int *mn;         // device, 2n
+  const double *G;       // device, 2n
+  const double *dz;      // host, N+2 (dz[0] = dz[N+1] = 0)
+  cudaStream_t stream;
+};
+CtxView ctx_view(const pw_ctx *c);
+
+constexpr double kThresholdRy = 1e-10;     // electrode channel at threshold
+constexpr double kRefineTolRel = 1e-9;     // refinement stops below this estimated error of t
 
 }  // namespace pw

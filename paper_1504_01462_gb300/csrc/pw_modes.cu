@@ -9,7 +9,10 @@
 //                 of App. A Eq. transfer
 #include <math.h>
 
+#include <type_traits>
+
 #include "pw_cta.cuh"
+#include "pw_df.cuh"
 #include "pw_internal.h"
 
 namespace pw {
@@ -289,52 +292,220 @@ size_t jacobi_smem(int n) {
 // ---------------------------------------------------------------------------
 constexpr int HEEV_THREADS = 512;
 
-template <int NTH>
-__device__ double block_sum(double v, double *scratch) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+// Arithmetic of the eigensolver's O(n^3) parts, native FP64 or double-float
+// (pw_df.cuh).  Matrices stay 16-byte complex elements in global memory in
+// either case (a double-float complex is two float pairs); the tridiagonal
+// (d, e), the QL rotations' construction and every scalar of the Householder
+// steps (norms, tau, 1/(alpha - beta)) are FP64 in both.
+template <typename R>
+struct HeevAr;
+
+template <>
+struct HeevAr<double> {
+  typedef zc C;
+  static __device__ __forceinline__ C from(zc z) { return z; }
+  static __device__ __forceinline__ zc to(C z) { return z; }
+  static __device__ __forceinline__ C zero() { return czero<double>(); }
+  static __device__ __forceinline__ C one() { return mkc<double>(1.0, 0.0); }
+  static __device__ __forceinline__ bool is_zero(C z) { return z.re == 0.0 && z.im == 0.0; }
+  static __device__ __forceinline__ double norm2(C z) { return cnorm2(z); }
+  static __device__ __forceinline__ C mul(C a, C b) { return cmul(a, b); }
+  static __device__ __forceinline__ void fma(C &acc, C a, C b) { cfma(acc, a, b); }
+  // acc += conj(a) b
+  static __device__ __forceinline__ void jfma(C &acc, C a, C b) {
+    const zc t = cjmul(a, b);
+    acc.re += t.re;
+    acc.im += t.im;
+  }
+  static __device__ __forceinline__ void renorm(C &) {}
+  static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
+  // a - c v
+  static __device__ __forceinline__ C sub_scaled(C a, double c, C v) { return csub(a, cscale(c, v)); }
+  // a - v conj(w_j) - w conj(v_j)
+  static __device__ __forceinline__ C rank2(C a, C v, C wj, C w, C vj) {
+    const zc t1 = cmul(v, cconj(wj)), t2 = cmul(w, cconj(vj));
+    a.re -= t1.re + t2.re;
+    a.im -= t1.im + t2.im;
+    return a;
+  }
+  // a - v p
+  static __device__ __forceinline__ C sub_mul(C a, C v, C p) {
+    const zc t = cmul(v, p);
+    a.re -= t.re;
+    a.im -= t.im;
+    return a;
+  }
+  typedef double Rot;
+  static __device__ __forceinline__ Rot rot_of(double c) { return c; }
+  // (s y + c x, c y - s x)
+  static __device__ __forceinline__ void rot(C y, C x, Rot c, Rot s, C &hi, C &lo) {
+    hi = mkc<double>(s * y.re + c * x.re, s * y.im + c * x.im);
+    lo = mkc<double>(c * y.re - s * x.re, c * y.im - s * x.im);
+  }
+  static __device__ __forceinline__ C shfl_down(C z, int off) {
+    return mkc<double>(__shfl_down_sync(0xffffffffu, z.re, off), __shfl_down_sync(0xffffffffu, z.im, off));
+  }
+};
+
+template <>
+struct HeevAr<df> {
+  typedef dfc C;
+  static __device__ __forceinline__ C from(zc z) { return dfc_of(z); }
+  static __device__ __forceinline__ zc to(C z) { return dfc_val(z); }
+  static __device__ __forceinline__ C zero() { return czero<df>(); }
+  static __device__ __forceinline__ C one() {
+    C z = czero<df>();
+    z.re.hi = 1.f;
+    return z;
+  }
+  static __device__ __forceinline__ bool is_zero(C z) { return z.re.hi == 0.f && z.im.hi == 0.f; }
+  static __device__ __forceinline__ double norm2(C z) {
+    const double r = df_val(z.re), i = df_val(z.im);
+    return r * r + i * i;
+  }
+  static __device__ __forceinline__ df dmul(df a, df b) { return df_mul(a, b); }
+  static __device__ __forceinline__ C mul(C a, C b) {
+    C r = czero<df>();
+    df_fma_lazy(r.re, a.re, b.re);
+    df_fma_lazy(r.re, df_neg(a.im), b.im);
+    df_fma_lazy(r.im, a.re, b.im);
+    df_fma_lazy(r.im, a.im, b.re);
+    cacc_renorm(r);
+    return r;
+  }
+  static __device__ __forceinline__ void fma(C &acc, C a, C b) { cfma(acc, a, b); }
+  static __device__ __forceinline__ void jfma(C &acc, C a, C b) {
+    df_fma_lazy(acc.re, a.re, b.re);
+    df_fma_lazy(acc.re, a.im, b.im);
+    df_fma_lazy(acc.im, a.re, b.im);
+    df_fma_lazy(acc.im, df_neg(a.im), b.re);
+  }
+  static __device__ __forceinline__ void renorm(C &a) { cacc_renorm(a); }
+  static __device__ __forceinline__ C add(C a, C b) {
+    C r;
+    r.re = df_add(a.re, b.re);
+    r.im = df_add(a.im, b.im);
+    return r;
+  }
+  static __device__ __forceinline__ C sub_scaled(C a, double c, C v) {
+    const df m = df_of(-c);
+    df_fma_lazy(a.re, m, v.re);
+    df_fma_lazy(a.im, m, v.im);
+    cacc_renorm(a);
+    return a;
+  }
+  static __device__ __forceinline__ C rank2(C a, C v, C wj, C w, C vj) {
+    // re -= v.re wj.re + v.im wj.im + w.re vj.re + w.im vj.im
+    df_fma_lazy(a.re, df_neg(v.re), wj.re);
+    df_fma_lazy(a.re, df_neg(v.im), wj.im);
+    df_fma_lazy(a.re, df_neg(w.re), vj.re);
+    df_fma_lazy(a.re, df_neg(w.im), vj.im);
+    // im -= v.im wj.re - v.re wj.im + w.im vj.re - w.re vj.im
+    df_fma_lazy(a.im, df_neg(v.im), wj.re);
+    df_fma_lazy(a.im, v.re, wj.im);
+    df_fma_lazy(a.im, df_neg(w.im), vj.re);
+    df_fma_lazy(a.im, w.re, vj.im);
+    cacc_renorm(a);
+    return a;
+  }
+  static __device__ __forceinline__ C sub_mul(C a, C v, C p) {
+    df_fma_lazy(a.re, df_neg(v.re), p.re);
+    df_fma_lazy(a.re, v.im, p.im);
+    df_fma_lazy(a.im, df_neg(v.re), p.im);
+    df_fma_lazy(a.im, df_neg(v.im), p.re);
+    cacc_renorm(a);
+    return a;
+  }
+  typedef df Rot;
+  static __device__ __forceinline__ Rot rot_of(double c) { return df_of(c); }
+  static __device__ __forceinline__ void rot(C y, C x, Rot c, Rot s, C &hi, C &lo) {
+    hi = czero<df>();
+    lo = czero<df>();
+    df_fma_lazy(hi.re, s, y.re);
+    df_fma_lazy(hi.re, c, x.re);
+    df_fma_lazy(hi.im, s, y.im);
+    df_fma_lazy(hi.im, c, x.im);
+    df_fma_lazy(lo.re, c, y.re);
+    df_fma_lazy(lo.re, df_neg(s), x.re);
+    df_fma_lazy(lo.im, c, y.im);
+    df_fma_lazy(lo.im, df_neg(s), x.im);
+    cacc_renorm(hi);
+    cacc_renorm(lo);
+  }
+  static __device__ __forceinline__ C shfl_down(C z, int off) {
+    C r;
+    r.re.hi = __shfl_down_sync(0xffffffffu, z.re.hi, off);
+    r.re.lo = __shfl_down_sync(0xffffffffu, z.re.lo, off);
+    r.im.hi = __shfl_down_sync(0xffffffffu, z.im.hi, off);
+    r.im.lo = __shfl_down_sync(0xffffffffu, z.im.lo, off);
+    return r;
+  }
+};
+
+// Block sum of a complex value in the solver's arithmetic (returned as FP64).
+template <typename R, int NTH>
+__device__ zc block_csum(typename HeevAr<R>::C v, typename HeevAr<R>::C *scratch) {
+  typedef HeevAr<R> Ar;
+  for (int off = 16; off > 0; off >>= 1) v = Ar::add(v, Ar::shfl_down(v, off));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) scratch[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < NTH / 32 ? scratch[lane] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    v = lane < NTH / 32 ? scratch[lane] : Ar::zero();
+    for (int off = 16; off > 0; off >>= 1) v = Ar::add(v, Ar::shfl_down(v, off));
     if (lane == 0) scratch[32] = v;
   }
   __syncthreads();
-  const double r = scratch[32];
+  const zc r = Ar::to(scratch[32]);
   __syncthreads();
   return r;
 }
 
+template <typename R>
 __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, double *En_all,
                                                        int *status, int n) {
+  typedef HeevAr<R> Ar;
+  typedef typename Ar::C C;
+  typedef typename Ar::Rot Rot;
   constexpr int NTH = HEEV_THREADS;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int mat = blockIdx.x, tid = threadIdx.x;
   const size_t nn = (size_t)n * n;
-  zc *A = HU_all + mat * nn;
-  zc *Z = Z_all + mat * nn;
+  zc *A64 = HU_all + mat * nn;
+  C *A = reinterpret_cast<C *>(A64);          // the matrix in the solver's format, in place
+  C *Z = reinterpret_cast<C *>(Z_all + mat * nn);
   double *En = En_all + (size_t)mat * n;
-  zc *v = reinterpret_cast<zc *>(smraw);
-  zc *pw_ = v + n;
-  zc *taus = pw_ + n;
-  double *d = reinterpret_cast<double *>(taus + n);
+  C *v = reinterpret_cast<C *>(smraw);
+  C *pw_ = v + n;
+  C *taus = pw_ + n;
+  C *cred = taus + n;                   // 33 complex: block reductions
+  double *d = reinterpret_cast<double *>(cred + 33);
   double *e = d + n;
   double *cs = e + n;
   double *sn = cs + n;
-  double *red = sn + n;                 // 40 doubles
-  int *ctl = reinterpret_cast<int *>(red + 40);   // [m, lo, converged-flag, failed]
+  Rot *csr = reinterpret_cast<Rot *>(sn + n);
+  Rot *snr = csr + n;
+  int *ctl = reinterpret_cast<int *>(snr + n);   // [m, lo, rotations-formed flag, failed]
   int *rank = ctl + 8;
   if (tid == 0) ctl[3] = 0;
+  if constexpr (!std::is_same<R, double>::value) {
+    // to the solver's format, element by element in place
+    for (size_t q = tid; q < nn; q += NTH) {
+      const zc z = A64[q];
+      A[q] = Ar::from(z);
+    }
+    __syncthreads();
+  }
 
   // ---- 1. Householder tridiagonalisation
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;
-    zc *x = A + (k + 1) + (size_t)k * n;
-    double part = 0.0;
-    for (int i = 1 + tid; i < m; i += NTH) part += cnorm2(x[i]);
-    const double xn2 = block_sum<NTH>(part, red);
-    const zc alpha = x[0];
+    C *x = A + (k + 1) + (size_t)k * n;
+    C part = Ar::zero();
+    for (int i = 1 + tid; i < m; i += NTH) Ar::jfma(part, x[i], x[i]);
+    Ar::renorm(part);
+    const double xn2 = block_csum<R, NTH>(part, cred).re;
+    const zc alpha = Ar::to(x[0]);
     zc tau;
     double beta;
     if (xn2 == 0.0 && alpha.im == 0.0) {
@@ -344,61 +515,58 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
       beta = -copysign(sqrt(cnorm2(alpha) + xn2), alpha.re);
       tau = mkc<double>((beta - alpha.re) / beta, -alpha.im / beta);
     }
-    const zc scl = (tau.re == 0.0 && tau.im == 0.0) ? czero<double>()
-                                                    : cinv(mkc<double>(alpha.re - beta, alpha.im));
+    const bool skip = tau.re == 0.0 && tau.im == 0.0;
+    const C scl = Ar::from(skip ? czero<double>() : cinv(mkc<double>(alpha.re - beta, alpha.im)));
     for (int i = tid; i < m; i += NTH) {
-      const zc vi = i == 0 ? mkc<double>(1.0, 0.0) : cmul(x[i], scl);
+      const C vi = i == 0 ? Ar::one() : Ar::mul(x[i], scl);
       v[i] = vi;
       if (i > 0) x[i] = vi;   // kept for the back-transformation
     }
     if (tid == 0) {
-      d[k] = A[k + (size_t)k * n].re;
+      d[k] = Ar::to(A[k + (size_t)k * n]).re;
       e[k] = beta;
-      taus[k] = tau;
+      taus[k] = Ar::from(tau);
     }
     __syncthreads();
-    if (tau.re == 0.0 && tau.im == 0.0) continue;
-    zc *A22 = A + (k + 1) + (size_t)(k + 1) * n;
+    if (skip) continue;
+    const C tauc = Ar::from(tau);
+    C *A22 = A + (k + 1) + (size_t)(k + 1) * n;
     // p = tau A22 v
     for (int i = tid; i < m; i += NTH) {
-      zc acc = czero<double>();
-      for (int j = 0; j < m; ++j) cfma(acc, A22[i + (size_t)j * n], v[j]);
-      pw_[i] = cmul(tau, acc);
+      C acc = Ar::zero();
+      for (int j = 0; j < m; ++j) {
+        Ar::fma(acc, A22[i + (size_t)j * n], v[j]);
+        if ((j & 31) == 31) Ar::renorm(acc);
+      }
+      Ar::renorm(acc);
+      pw_[i] = Ar::mul(tauc, acc);
     }
     __syncthreads();
-    double pr = 0.0, pi = 0.0;
-    for (int i = tid; i < m; i += NTH) {
-      const zc t = cjmul(v[i], pw_[i]);
-      pr += t.re;
-      pi += t.im;
-    }
-    const double vr = block_sum<NTH>(pr, red);
-    const double vi_ = block_sum<NTH>(pi, red);
-    const double c = 0.5 * (tau.re * vr + tau.im * vi_);   // Re(conj(tau) v^H p)
-    for (int i = tid; i < m; i += NTH) pw_[i] = csub(pw_[i], cscale(c, v[i]));
+    C vp = Ar::zero();
+    for (int i = tid; i < m; i += NTH) Ar::jfma(vp, v[i], pw_[i]);
+    Ar::renorm(vp);
+    const zc vhp = block_csum<R, NTH>(vp, cred);
+    const double c = 0.5 * (tau.re * vhp.re + tau.im * vhp.im);   // Re(conj(tau) v^H p)
+    for (int i = tid; i < m; i += NTH) pw_[i] = Ar::sub_scaled(pw_[i], c, v[i]);
     __syncthreads();
     // A22 <- A22 - v w^H - w v^H
     for (size_t q = tid; q < (size_t)m * m; q += NTH) {
       const int i = q % m, j = q / m;
-      zc a = A22[i + (size_t)j * n];
-      const zc t1 = cmul(v[i], cconj(pw_[j])), t2 = cmul(pw_[i], cconj(v[j]));
-      a.re -= t1.re + t2.re;
-      a.im -= t1.im + t2.im;
-      A22[i + (size_t)j * n] = a;
+      A22[i + (size_t)j * n] = Ar::rank2(A22[i + (size_t)j * n], v[i], pw_[j], pw_[i], v[j]);
     }
     __syncthreads();
   }
   if (tid == 0) {
-    d[n - 1] = A[(n - 1) + (size_t)(n - 1) * n].re;
+    d[n - 1] = Ar::to(A[(n - 1) + (size_t)(n - 1) * n]).re;
     e[n - 1] = 0.0;
   }
   for (size_t q = tid; q < nn; q += NTH) {
     const int i = q % n, j = q / n;
-    Z[q] = mkc<double>(i == j ? 1.0 : 0.0, 0.0);
+    Z[q] = i == j ? Ar::one() : Ar::zero();
   }
   __syncthreads();
 
-  // ---- 2. implicit QL on the tridiagonal (d, e)
+  // ---- 2. implicit QL on the tridiagonal (d, e), FP64
   const double eps = 2.220446049250313e-16;
   for (int l = 0; l < n; ++l) {
     int iter = 0;
@@ -443,6 +611,8 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
               g = c * r - b;
               cs[i] = c;
               sn[i] = s;
+              csr[i] = Ar::rot_of(c);
+              snr[i] = Ar::rot_of(s);
             }
             if (!under) {
               d[l] -= p;
@@ -459,12 +629,13 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
       if (m == l) break;
       if (ctl[2] && lo < m) {
         for (int row = tid; row < n; row += NTH) {
-          zc x = Z[row + (size_t)m * n];
+          C x = Z[row + (size_t)m * n];
           for (int i = m - 1; i >= lo; --i) {
-            const zc y = Z[row + (size_t)i * n];
-            const double c = cs[i], s = sn[i];
-            Z[row + (size_t)(i + 1) * n] = mkc<double>(s * y.re + c * x.re, s * y.im + c * x.im);
-            x = mkc<double>(c * y.re - s * x.re, c * y.im - s * x.im);
+            const C y = Z[row + (size_t)i * n];
+            C hi, lo_;
+            Ar::rot(y, x, csr[i], snr[i], hi, lo_);
+            Z[row + (size_t)(i + 1) * n] = hi;
+            x = lo_;
           }
           Z[row + (size_t)lo * n] = x;
         }
@@ -476,39 +647,29 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   // ---- 3. back-transformation U = Q Z (Q_{n-2} first)
   const int warp = tid >> 5, lane = tid & 31;
   for (int k = n - 2; k >= 0; --k) {
-    const zc tau = taus[k];
-    if (tau.re == 0.0 && tau.im == 0.0) continue;
+    const C tau = taus[k];
+    if (Ar::is_zero(tau)) continue;
     const int m = n - k - 1;
-    const zc *x = A + (k + 1) + (size_t)k * n;
-    for (int i = tid; i < m; i += NTH) v[i] = i == 0 ? mkc<double>(1.0, 0.0) : x[i];
+    const C *x = A + (k + 1) + (size_t)k * n;
+    for (int i = tid; i < m; i += NTH) v[i] = i == 0 ? Ar::one() : x[i];
     __syncthreads();
-    zc *Zk = Z + (k + 1);
+    C *Zk = Z + (k + 1);
     for (int j = warp; j < n; j += NTH / 32) {
-      zc acc = czero<double>();
-      for (int i = lane; i < m; i += 32) {
-        const zc t = cjmul(v[i], Zk[i + (size_t)j * n]);
-        acc.re += t.re;
-        acc.im += t.im;
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        acc.re += __shfl_down_sync(0xffffffffu, acc.re, off);
-        acc.im += __shfl_down_sync(0xffffffffu, acc.im, off);
-      }
-      if (lane == 0) pw_[j] = cmul(tau, acc);
+      C acc = Ar::zero();
+      for (int i = lane; i < m; i += 32) Ar::jfma(acc, v[i], Zk[i + (size_t)j * n]);
+      Ar::renorm(acc);
+      for (int off = 16; off > 0; off >>= 1) acc = Ar::add(acc, Ar::shfl_down(acc, off));
+      if (lane == 0) pw_[j] = Ar::mul(tau, acc);
     }
     __syncthreads();
     for (size_t q = tid; q < (size_t)m * n; q += NTH) {
       const int i = q % m, j = q / m;
-      zc z = Zk[i + (size_t)j * n];
-      const zc t = cmul(v[i], pw_[j]);
-      z.re -= t.re;
-      z.im -= t.im;
-      Zk[i + (size_t)j * n] = z;
+      Zk[i + (size_t)j * n] = Ar::sub_mul(Zk[i + (size_t)j * n], v[i], pw_[j]);
     }
     __syncthreads();
   }
 
-  // ---- 4. ascending order (ties by index)
+  // ---- 4. ascending order (ties by index), back to FP64 storage
   for (int i = tid; i < n; i += NTH) {
     const double li = d[i];
     int r = 0;
@@ -519,22 +680,28 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   __syncthreads();
   for (size_t q = tid; q < nn; q += NTH) {
     const int i = q % n, j = q / n;
-    A[i + (size_t)rank[j] * n] = Z[q];
+    A64[i + (size_t)rank[j] * n] = Ar::to(Z[q]);
   }
   if (tid == 0) status[mat] = ctl[3] ? -1 : 1;
 }
 
 size_t heev_smem(int n) {
-  return (size_t)3 * n * sizeof(zc) + (size_t)4 * n * sizeof(double) + 40 * sizeof(double) +
-         (8 + (size_t)n) * sizeof(int) + 64;
+  return (size_t)3 * n * sizeof(zc) + 33 * sizeof(zc) + (size_t)4 * n * sizeof(double) +
+         (size_t)2 * n * sizeof(double) + (8 + (size_t)n) * sizeof(int) + 64;
 }
 
 // HU: in H, out U; V: scratch of the same size; status: positive on success,
-// negative when an eigenvalue did not converge.
-void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s) {
+// negative when an eigenvalue did not converge.  double_float: the O(n^3)
+// parts in double-float arithmetic on the FP32 pipe (the mixed form).
+void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s, bool double_float) {
   const size_t smem = heev_smem(n);
-  cudaFuncSetAttribute(k_heev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_heev<<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n);
+  if (double_float) {
+    cudaFuncSetAttribute(k_heev<df>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n);
+  } else {
+    cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n);
+  }
 }
 
 // The Jacobi route (same interface), kept as an independent second solver.
@@ -548,22 +715,25 @@ void launch_eig_jacobi(zc *HU, zc *V, double *En, int *status, int n, int nmat, 
 // ---------------------------------------------------------------------------
 // Overlaps O_p = U_p^H U_{p+1}: one CTA per interface.
 // ---------------------------------------------------------------------------
+// A: the accumulation type (double, or double-float for the mixed form).
+template <typename A>
 __global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n, int nq) {
   extern __shared__ unsigned char smraw[];
-  zc *sm = reinterpret_cast<zc *>(smraw);
+  cx<A> *sm = reinterpret_cast<cx<A> *>(smraw);
   const int slot = blockIdx.x / (nq - 1), p = blockIdx.x % (nq - 1);
   const zc *Up = U + ((size_t)slot * nq + p) * n * n;
   const zc *Uq = Up + (size_t)n * n;
   zc *Op = O + ((size_t)slot * (nq - 1) + p) * n * n;
-  cta_gemm<double>(
-      n, n, n, [=](int i, int l) { return cconj(Up[l + (size_t)i * n]); },
-      [=](int l, int j) { return Uq[l + (size_t)j * n]; },
-      [=](int i, int j, zc acc) { Op[i + (size_t)j * n] = acc; }, sm);
+  cta_gemm<A>(
+      n, n, n, [=](int i, int l) { return acc_of<A>(cconj(Up[l + (size_t)i * n])); },
+      [=](int l, int j) { return acc_of<A>(Uq[l + (size_t)j * n]); },
+      [=](int i, int j, cx<A> acc) { Op[i + (size_t)j * n] = acc_val(acc); }, sm);
 }
 
-void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s) {
+void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s, bool double_float) {
   const size_t smem = gemm_smem_elems<double>() * sizeof(zc);
-  k_overlaps<<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq);
+  if (double_float) k_overlaps<df><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq);
+  else k_overlaps<double><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq);
 }
 
 }  // namespace pw

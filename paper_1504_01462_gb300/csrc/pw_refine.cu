@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "pw_cta.cuh"
+#include "pw_df.cuh"
 #include "pw_internal.h"
 
 namespace pw {
@@ -45,16 +46,17 @@ __device__ KV carve_kv(unsigned char *raw, size_t off, int n) {
 }
 
 __device__ void load_kv(const RefineArgs &a, const PointDesc &d, int p, KV &v) {
-  const int n = a.n, N = a.N;
-  const double *Ep = a.En + ((size_t)d.kset * (N + 2) + p) * n;
+  const int n = a.n;
+  const double *Ep = a.En + ((size_t)d.en_off + p) * n;
   const double *Eq = Ep + n;
+  const double *dz = a.dz + d.dz_off;
   for (int i = threadIdx.x; i < n; i += NT) {
     const zc kl = kz_branch(d.E, Ep[i]);
     const zc kr = kz_branch(d.E, Eq[i]);
     v.kinvL[i] = cinv(kl);
     v.kR[i] = kr;
-    v.eL[i] = phase_fwd(kl, a.dz[p]);
-    v.eR[i] = phase_fwd(kr, a.dz[p + 1]);
+    v.eL[i] = phase_fwd(kl, dz[p]);
+    v.eR[i] = phase_fwd(kr, dz[p + 1]);
   }
   __syncthreads();
 }
@@ -74,11 +76,14 @@ __device__ __forceinline__ cc pq32(const zc *O, int n, int l, int j, const KV &v
   return cmul(o, mkc<float>(0.5f * (1.0f + sel * r.re), 0.5f * sel * r.im));
 }
 
-__device__ __forceinline__ size_t blk(const RefineArgs &a, int pt, int q) {
-  return ((size_t)pt * (a.N + 2) + q) * (size_t)a.n * a.nc;
+__device__ __forceinline__ size_t blk(const RefineArgs &a, const PointDesc &d, int q) {
+  return ((size_t)d.x_off + q) * (size_t)a.n * a.nc;
 }
-__device__ __forceinline__ size_t iblk(const RefineArgs &a, int pt, int p) {
-  return ((size_t)pt * (a.N + 1) + p) * (size_t)a.n * a.nc;
+__device__ __forceinline__ size_t iblk(const RefineArgs &a, const PointDesc &d, int p) {
+  return ((size_t)d.st_off + p) * (size_t)a.n * a.nc;
+}
+__device__ __forceinline__ const zc *overlap(const RefineArgs &a, const PointDesc &d, int p) {
+  return a.O + ((size_t)d.o_off + p) * (size_t)a.n * a.n;
 }
 
 }  // namespace
@@ -88,7 +93,7 @@ __device__ __forceinline__ size_t iblk(const RefineArgs &a, int pt, int p) {
 __global__ void k_refine_init(RefineArgs a) {
   const int pt = blockIdx.x;
   const PointDesc d = a.pts[pt];
-  zc *A0 = a.Xa + blk(a, pt, 0);
+  zc *A0 = a.Xa + blk(a, d, 0);
   for (int e = threadIdx.x; e < a.n * a.nc; e += blockDim.x) {
     const int i = e % a.n, c = e / a.n;
     A0[e] = mkc<double>((i == c && c < d.nL) ? 1.0 : 0.0, 0.0);
@@ -96,21 +101,22 @@ __global__ void k_refine_init(RefineArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Backward pass at interface p (launched for p = N down to 0):
+// Backward pass at interface p (launched for p = max N down to 0; a point
+// starts at its own N):
 //   da_q = Z_p (e_q db_q) + u_p,   db_p = Q_p da_q + P_p e_q db_q (+ g_p),
 // accumulated into Xa[q], Xb[p]; db_p is carried to the next (left) interface.
 __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int with_src) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
   const PointDesc d = a.pts[pt];
-  if (d.skip || a.status[pt]) return;
-  const int n = a.n, nc = a.nc, N = a.N, q = p + 1;
+  if (d.skip || a.status[pt] || p > d.N) return;
+  const int n = a.n, nc = a.nc, N = d.N, q = p + 1;
   cc *gsm = reinterpret_cast<cc *>(smraw);
   KV v = carve_kv(smraw, skinny_smem_elems<float>() * sizeof(cc), n);
   load_kv(a, d, p, v);
-  const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
-  const cc *Z = a.Zst + ((size_t)pt * (N + 1) + p) * n * n;
-  const cc *U = a.Ust + ((size_t)pt * (N + 1) + p) * n * nc;
+  const zc *O = overlap(a, d, p);
+  const cc *Z = a.Zst + ((size_t)d.st_off + p) * n * n;
+  const cc *U = a.Ust + ((size_t)d.st_off + p) * n * nc;
   zc *carry = a.carry + (size_t)pt * n * nc;       // db_q in, db_p out
   cc *tmp = a.tmp + (size_t)pt * 2 * n * nc;       // [da_q ; e_q db_q] as a 2n x nc block
   // e_q db_q (db_{N+1} = 0)
@@ -120,8 +126,8 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
     tmp[n + i + (size_t)c * 2 * n] = ccast<float>(cmul(v.eR[i], b));
   }
   __syncthreads();
-  zc *Xa = a.Xa + blk(a, pt, q);
-  zc *Xb = a.Xb + blk(a, pt, p);
+  zc *Xa = a.Xa + blk(a, d, q);
+  zc *Xb = a.Xb + blk(a, d, p);
   // da_q
   cta_gemm_skinny<float>(
       n, nc, n, [=](int i, int l) { return Z[i + (size_t)l * n]; },
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
       gsm);
   // db_p = [Q | P] [da_q ; e_q db_q] (+ g_p)
   const KV vc = v;
-  const zc *G = a.Gr + iblk(a, pt, p);
+  const zc *G = a.Gr + iblk(a, d, p);
   cta_gemm_skinny<float>(
       n, nc, 2 * n,
       [=](int i, int l) { return l < n ? pq32(O, n, i, l, vc, -1.0f) : pq32(O, n, i, l - n, vc, 1.0f); },
@@ -160,33 +166,34 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int p = blockIdx.x, pt = blockIdx.y;
   const PointDesc d = a.pts[pt];
-  if (d.skip || a.status[pt]) return;
-  const int n = a.n, nc = a.nc, N = a.N, q = p + 1;
+  if (d.skip || a.status[pt] || p > d.N) return;
+  const int n = a.n, nc = a.nc, N = d.N, q = p + 1;
   zc *gsm = reinterpret_cast<zc *>(smraw);
   KV v = carve_kv(smraw, skinny_smem_elems<double>() * sizeof(zc), n);
   load_kv(a, d, p, v);
-  const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
-  const zc *ap = a.Xa + blk(a, pt, p);
-  const zc *bp = a.Xb + blk(a, pt, p);
-  const zc *aq = a.Xa + blk(a, pt, q);
-  const zc *bq = a.Xb + blk(a, pt, q);
-  zc *F = a.Fr + iblk(a, pt, p);
-  zc *G = a.Gr + iblk(a, pt, p);
+  const zc *O = overlap(a, d, p);
+  const zc *ap = a.Xa + blk(a, d, p);
+  const zc *bp = a.Xb + blk(a, d, p);
+  const zc *aq = a.Xa + blk(a, d, q);
+  const zc *bq = a.Xb + blk(a, d, q);
+  zc *F = a.Fr + iblk(a, d, p);
+  zc *G = a.Gr + iblk(a, d, p);
   const KV vc = v;
   const bool has_bq = q <= N;
-  cta_gemm_skinny<double>(
-      n, 2 * nc, n, [=](int i, int l) { return O[i + (size_t)l * n]; },
+  // the O y products in double-float (48-bit) arithmetic on the FP32 pipe
+  cta_gemm_skinny<df>(
+      n, 2 * nc, n, [=](int i, int l) { return dfc_of(O[i + (size_t)l * n]); },
       [=](int l, int j) {
         const int c = j < nc ? j : j - nc;
         const zc A = aq[l + (size_t)c * n];
         const zc eb = has_bq ? cmul(vc.eR[l], bq[l + (size_t)c * n]) : czero<double>();
-        return j < nc ? cadd(A, eb) : cmul(vc.kR[l], csub(A, eb));
+        return dfc_of(j < nc ? cadd(A, eb) : cmul(vc.kR[l], csub(A, eb)));
       },
-      [=](int i, int j, zc acc) {
-        if (j < nc) F[i + (size_t)j * n] = acc;
-        else G[i + (size_t)(j - nc) * n] = acc;
+      [=](int i, int j, dfc acc) {
+        if (j < nc) F[i + (size_t)j * n] = dfc_val(acc);
+        else G[i + (size_t)(j - nc) * n] = dfc_val(acc);
       },
-      gsm);
+      reinterpret_cast<dfc *>(gsm));
   for (int e = threadIdx.x; e < n * nc; e += NT) {
     const int i = e % n;
     const zc y1 = F[e], y2 = cmul(vc.kinvL[i], G[e]);
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward correction sweep at interface p (launched for p = 0..N):
+// Forward correction sweep at interface p (launched for p = 0..max N):
 //   u_p = W_p^{-1}(c_p + R_p g_p - f_p),  R_p = e_p Z_{p-1} e_p,  c_{p+1} = e_q u_p,
 // with W_p's LU factors kept by the first sweep (an O(n^2 nc) replay).  u_p
 // replaces the stored one for the backward pass.  At p = N the carry holds the
@@ -208,20 +215,20 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
   const PointDesc d = a.pts[pt];
-  if (d.skip || a.status[pt]) return;
-  const int n = a.n, nc = a.nc, N = a.N;
+  if (d.skip || a.status[pt] || p > d.N) return;
+  const int n = a.n, nc = a.nc, N = d.N;
   cc *gsm = reinterpret_cast<cc *>(smraw);
   const size_t kv_off = (skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc);
   KV v = carve_kv(smraw, kv_off, n);
   load_kv(a, d, p, v);
-  const cc *Zprev = p > 0 ? a.Zst + ((size_t)pt * (N + 1) + p - 1) * n * n : nullptr;
-  const cc *LU = a.LUst + ((size_t)pt * (N + 1) + p) * n * n;
-  const int *piv = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
-  cc *Ust = a.Ust + ((size_t)pt * (N + 1) + p) * n * nc;
+  const cc *Zprev = p > 0 ? a.Zst + ((size_t)d.st_off + p - 1) * n * n : nullptr;
+  const cc *LU = a.LUst + ((size_t)d.st_off + p) * n * n;
+  const int *piv = a.PIVst + ((size_t)d.st_off + p) * n;
+  cc *Ust = a.Ust + ((size_t)d.st_off + p) * n * nc;
   cc *rhs = a.M + (size_t)pt * n * (n + nc);   // n x nc scratch
   zc *carry = a.carry + (size_t)pt * n * nc;   // c_p in, c_{p+1} out
-  const zc *F = a.Fr + iblk(a, pt, p);
-  const zc *G = a.Gr + iblk(a, pt, p);
+  const zc *F = a.Fr + iblk(a, d, p);
+  const zc *G = a.Gr + iblk(a, d, p);
   const KV vc = v;
   if (p == 0) {
     for (int e = threadIdx.x; e < n * nc; e += NT) rhs[e] = ccast<float>(csub(carry[e], F[e]));
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p) {
   __syncthreads();
   if (p == N) {
     // add the correction of a_{N+1}; record its size relative to a_{N+1}
-    zc *X = a.Xa + blk(a, pt, N + 1);
+    zc *X = a.Xa + blk(a, d, N + 1);
     double dn = 0.0, xn = 0.0;
     for (int e = threadIdx.x; e < n * nc; e += NT) {
       const zc dx = carry[e];
@@ -269,18 +276,21 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p) {
     if (threadIdx.x == 0) {
       double sd = 0.0, sx = 0.0;
       for (int w = 0; w < NT / 32; ++w) { sd += red[0][w]; sx += red[1][w]; }
+      a.corr_prev[pt] = a.corr[pt];
       a.corr[pt] = sx > 0.0 ? sqrt(sd / sx) : 0.0;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// t and T from the refined a_{N+1}; the estimate of the relative error of T is
-// the relative change of T made by the last correction.
+// t and T from the refined a_{N+1}.  The estimate of the relative error of T
+// left after the last pass is the relative change of T that pass made, times
+// the contraction c_i / c_{i-1} it showed (c = relative size of the
+// correction of a_{N+1}; 1 after a single pass).
 __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
   const int pt = blockIdx.x;
   const PointDesc d = a.pts[pt];
-  const int n = a.n, nc = a.nc, N = a.N, tid = threadIdx.x;
+  const int n = a.n, nc = a.nc, N = d.N, tid = threadIdx.x;
   if (d.skip || a.status[pt]) {
     if (tid == 0) {
       a.T[d.out] = __longlong_as_double(0x7ff8000000000000ll);
@@ -289,9 +299,9 @@ __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
     }
     return;
   }
-  const double *EL = a.En + ((size_t)d.kset * (N + 2)) * n;
+  const double *EL = a.En + (size_t)d.en_off * n;
   const double *ER = EL + (size_t)(N + 1) * n;
-  const zc *X = a.Xa + blk(a, pt, N + 1);
+  const zc *X = a.Xa + blk(a, d, N + 1);
   const zc *dX = a.carry + (size_t)pt * n * nc;   // last correction of a_{N+1}
   double acc = 0.0, accp = 0.0;
   for (int e = tid; e < d.nR * d.nL; e += NT) {
@@ -316,7 +326,9 @@ __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
     for (int w = 0; w < NT / 32; ++w) { T += red[0][w]; Tp += red[1][w]; }
     a.T[d.out] = T;
     if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
-    if (a.err) a.err[d.out] = fabs(T - Tp) / fmax(T, 1e-300);
+    const double c = a.corr[pt], cp = a.corr_prev[pt];
+    const double rho = cp > 0.0 ? fmin(1.0, c / cp) : 1.0;
+    if (a.err) a.err[d.out] = rho * fabs(T - Tp) / fmax(T, 1e-300);
   }
 }
 
@@ -338,8 +350,11 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
       (e = cudaFuncSetAttribute(k_refine_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
   const size_t vec = (size_t)npts * a.n * a.nc * sizeof(zc);
-  if ((e = cudaMemsetAsync(a.Xa, 0, vec * (a.N + 2), s)) || (e = cudaMemsetAsync(a.Xb, 0, vec * (a.N + 2), s)) ||
-      (e = cudaMemsetAsync(a.Gr, 0, vec * (a.N + 1), s)) || (e = cudaMemsetAsync(a.corr, 0, npts * sizeof(double), s)))
+  const size_t slot = (size_t)a.n * a.nc * sizeof(zc);
+  if ((e = cudaMemsetAsync(a.Xa, 0, slot * a.x_slots, s)) || (e = cudaMemsetAsync(a.Xb, 0, slot * a.x_slots, s)) ||
+      (e = cudaMemsetAsync(a.Gr, 0, slot * a.st_slots, s)) ||
+      (e = cudaMemsetAsync(a.corr, 0, npts * sizeof(double), s)) ||
+      (e = cudaMemsetAsync(a.corr_prev, 0, npts * sizeof(double), s)))
     return e;
   k_refine_init<<<npts, NT, 0, s>>>(a);
   // x0: backward pass over the first sweep's Z_p, u_p

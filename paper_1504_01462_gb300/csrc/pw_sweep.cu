@@ -1,5 +1,5 @@
-// The E-dependent hot path: interface scattering matrices and their star
-// products, one CTA per (E, k_par) point.
+// Interface scattering matrices (pw_slice_smatrix) and single star products
+// (pw_compose), one CTA per point; the algebra of the junction sweep.
 //
 // Interface p joins slice p (wavenumbers k^p) and slice p+1 (k^{p+1},
 // thickness dz_{p+1}, dz = 0 for the right electrode).  With
@@ -9,7 +9,7 @@
 // Eq. scatter becomes
 //   S11 = E+ P^{-1},  S12 = -E+ P^{-1} Q E+,  S21 = Q P^{-1},  S22 = (P - Q P^{-1} Q) E+.
 //
-// Sweep (k_sweep).  The junction's S(0,N+1) is the left-to-right chain of star
+// Sweep (pw_sweep_batched.cu).  The junction's S(0,N+1) is the left-to-right chain of star
 // products (Eq. recurrence) S(0,p+1) = S(0,p) * S(p,p+1).  Only two blocks of
 // the accumulated product are needed for t: R = S12(0,p) (n x n) and
 // Tacc = S11(0,p) restricted to the incident (open left) columns.  Inserting
@@ -83,145 +83,6 @@ __device__ __forceinline__ cx<T> pq_elem(const zc *O, int n, int l, int j, const
   const cx<T> r = cmul(s.kR[j], s.kinvL[l]);
   const cx<T> f = mkc<T>(T(0.5) * (T(1) + sel * r.re), T(0.5) * sel * r.im);
   return cmul(o, f);
-}
-
-// ---------------------------------------------------------------------------
-template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_sweep(SweepArgs a, int p) {
-  constexpr int NT = NTH;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int pt = blockIdx.x;
-  const PointDesc d = a.pts[pt];
-  const int n = a.n, N = a.N, nc = a.nc;
-  const int ncols = 2 * n + nc;
-  const int tid = threadIdx.x;
-  if (d.skip) {
-    if (p == N && tid == 0) {
-      a.T[d.out] = __longlong_as_double(0x7ff8000000000000ll);
-      if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
-      if (a.err) a.err[d.out] = 0.0;
-    }
-    return;
-  }
-  if (a.status[pt] != 0) {
-    if (p == N && tid == 0) {
-      a.T[d.out] = __longlong_as_double(0x7ff8000000000000ll);
-      if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
-    }
-    return;
-  }
-  SweepSmem<T> s = carve<T, NTH>(smraw, n);
-  if (tid == 0) *s.flag = 0;
-  const double *Ep = a.En + ((size_t)d.kset * (N + 2) + p) * n;
-  const double *Eq = Ep + n;
-  const zc *O = a.O + ((size_t)d.kset * (N + 1) + p) * n * n;
-  cx<T> *R = reinterpret_cast<cx<T> *>(a.R) + (size_t)pt * n * n;
-  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
-  int *piv = a.piv + (size_t)pt * n;
-  interface_vectors<T>(Ep, Eq, d.E, a.dz[p + 1], n, s);
-
-  if (p == 0) {
-    // S(0,0) = I: R = 0, Tacc = the open left columns of I  ->  W = P, Y = -Q
-    for (size_t e = tid; e < (size_t)n * ncols; e += NT) {
-      const int i = e % n, j = e / n;
-      cx<T> v;
-      if (j < n) v = pq_elem<T>(O, n, i, j, s, T(1));
-      else if (j < 2 * n) { v = pq_elem<T>(O, n, i, j - n, s, T(-1)); v.re = -v.re; v.im = -v.im; }
-      else { const int c = j - 2 * n; v = mkc<T>((i == c && c < d.nL) ? T(1) : T(0), T(0)); }
-      M[e] = v;
-    }
-    __syncthreads();
-  } else {
-    // [W | Y] = [P | -Q] + [-R Q | R P]
-    const SweepSmem<T> sc = s;
-    cta_gemm<T, NTH>(
-        n, 2 * n, n, [=](int i, int l) { return R[i + (size_t)l * n]; },
-        [=](int l, int j) {
-          return j < n ? pq_elem<T>(O, n, l, j, sc, T(-1)) : pq_elem<T>(O, n, l, j - n, sc, T(1));
-        },
-        [=](int i, int j, cx<T> acc) {
-          if (j < n) M[i + (size_t)j * n] = csub(pq_elem<T>(O, n, i, j, sc, T(1)), acc);
-          else M[i + (size_t)j * n] = csub(acc, pq_elem<T>(O, n, i, j - n, sc, T(-1)));
-        },
-        s.gemm);
-  }
-  // W [Z_Y | Z_T] = [Y | Tacc]
-  cta_lu_solve<T, NTH>(M, n, n, ncols, piv, s.gemm, s.sval, s.sidx, s.flag);
-  // keep Z_Y, u = Z_T and the LU factors of W for the refinement passes
-  if (a.Zst) {
-    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)pt * (N + 1) + p) * n * n;
-    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)pt * (N + 1) + p) * n * nc;
-    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)pt * (N + 1) + p) * n * n;
-    int *Ps = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
-    for (size_t e = tid; e < (size_t)n * n; e += NT) {
-      Zs[e] = M[(size_t)n * n + e];
-      Ls[e] = M[e];
-    }
-    for (size_t e = tid; e < (size_t)n * nc; e += NT) Us[e] = M[(size_t)2 * n * n + e];
-    for (int e = tid; e < n; e += NT) Ps[e] = piv[e];
-  }
-  // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
-  for (size_t e = tid; e < (size_t)n * n; e += NT) {
-    const int i = e % n, j = e / n;
-    R[e] = cmul(cmul(s.ep[i], M[i + (size_t)(n + j) * n]), s.ep[j]);
-  }
-  for (size_t e = tid; e < (size_t)n * nc; e += NT) {
-    const int i = e % n, c = e / n;
-    cx<T> &v = M[i + (size_t)(2 * n + c) * n];
-    v = cmul(s.ep[i], v);
-  }
-  __syncthreads();
-  if (tid == 0 && *s.flag) a.status[pt] = 1;
-  if (p < N) return;
-
-  // ---- t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels, T = sum |t_ij|^2
-  const double *EL = a.En + ((size_t)d.kset * (N + 2)) * n;
-  const double *ER = EL + (size_t)(N + 1) * n;
-  double acc = 0.0;
-  for (int e = tid; e < d.nR * d.nL; e += NT) {
-    const int i = e % d.nR, j = e / d.nR;
-    const double f = sqrt(sqrt(d.E - ER[i]) / sqrt(d.E - EL[j]));
-    const cx<T> v = M[i + (size_t)(2 * n + j) * n];
-    const zc tv = mkc<double>(f * double(v.re), f * double(v.im));
-    acc += tv.re * tv.re + tv.im * tv.im;
-    if (a.t) a.t[(size_t)d.out * n * n + i + (size_t)j * n] = tv;
-  }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  __shared__ double red[NT / 32];
-  if ((tid & 31) == 0) red[tid >> 5] = acc;
-  __syncthreads();
-  if (tid == 0) {
-    double tsum = 0.0;
-    for (int w = 0; w < NT / 32; ++w) tsum += red[w];
-    a.T[d.out] = (*s.flag || a.status[pt]) ? __longlong_as_double(0x7ff8000000000000ll) : tsum;
-    if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
-    if (a.err) a.err[d.out] = 0.0;
-  }
-}
-
-// The FP64 sweep is bound by the FP64 pipe at 256 threads per point; the FP32
-// sweep is latency-bound and runs 512 threads (16 warps) per point.
-constexpr int SWEEP_NT64 = 256, SWEEP_NT32 = 512;
-
-size_t sweep_smem_bytes(int n, int precision) {
-  return precision == PW_FP64 ? carve_bytes<double, SWEEP_NT64>(n) : carve_bytes<float, SWEEP_NT32>(n);
-}
-
-cudaError_t launch_sweep(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s) {
-  const size_t smem = sweep_smem_bytes(a.n, precision);
-  cudaError_t e;
-  if (precision == PW_FP64) {
-    e = cudaFuncSetAttribute(k_sweep<double, SWEEP_NT64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_sweep<double, SWEEP_NT64><<<npts, SWEEP_NT64, smem, s>>>(a, p);
-  } else {
-    e = cudaFuncSetAttribute(k_sweep<float, SWEEP_NT32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_sweep<float, SWEEP_NT32><<<npts, SWEEP_NT32, smem, s>>>(a, p);
-  }
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -13,6 +13,8 @@
 // kernel (same tile loops and accumulation order).
 #include <math.h>
 
+#include <type_traits>
+
 #include "pw_cta.cuh"
 #include "pw_internal.h"
 
@@ -20,7 +22,17 @@ namespace pw {
 
 namespace {
 
-constexpr int BT = 256;   // threads of every batched launch
+constexpr int VT = 256;   // threads of the per-point vector phases (vectors, finish)
+
+// Shared memory of kb_panel ahead of the staged panel: L11, the arg-max
+// scratch and the zero-pivot flag (rounded to 16 bytes).
+template <typename T, int BT>
+__host__ __device__ constexpr size_t panel_head_bytes() {
+  return ((size_t)Tile<T, BT>::NB * Tile<T, BT>::NB * sizeof(cx<T>) + 40 * sizeof(T) + 96 * sizeof(int) + 15) &
+         ~size_t(15);
+}
+
+int g_smem_optin = 0;   // opt-in shared memory per block of the device (set by prepare)
 
 template <typename T>
 struct KVb {
@@ -42,8 +54,11 @@ __device__ __forceinline__ cx<T> pqb(const zc *O, int n, int l, int j, const KVb
   return cmul(o, mkc<T>(T(0.5) * (T(1) + sel * r.re), T(0.5) * sel * r.im));
 }
 
+// Points whose problem ended at an earlier interface (a.p > N of the point)
+// take no part in the remaining steps.
 __device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
-  return a.pts[pt].skip || a.status[pt];
+  const PointDesc &d = a.pts[pt];
+  return d.skip || a.status[pt] || a.p > d.N;
 }
 
 // Slice q and interface p of the problem being swept.  The mirrored problem
@@ -51,27 +66,29 @@ __device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
 // (H_p -> H_p^T = conj(H_p), eigenvectors conj(U_p), overlaps conj(O_p))
 // seen from the right electrode: its interface p joins original slices
 // N+1-p and N-p, whose overlap conj(U_{N+1-p})^H conj(U_{N-p}) = O_{N-p}^T.
-__device__ __forceinline__ int slice_of(const SweepArgs &a, int q) { return a.mirror ? a.N + 1 - q : q; }
+__device__ __forceinline__ int slice_of(const SweepArgs &a, const PointDesc &d, int q) {
+  return a.mirror ? d.N + 1 - q : q;
+}
 __device__ __forceinline__ const double *energies_of(const SweepArgs &a, const PointDesc &d, int q) {
-  return a.En + ((size_t)d.kset * (a.N + 2) + slice_of(a, q)) * a.n;
+  return a.En + ((size_t)d.en_off + slice_of(a, d, q)) * a.n;
 }
 __device__ __forceinline__ const zc *overlap_of(const SweepArgs &a, const PointDesc &d, int p) {
-  return a.O + ((size_t)d.kset * (a.N + 1) + (a.mirror ? a.N - p : p)) * a.n * a.n;
+  return a.O + ((size_t)d.o_off + (a.mirror ? d.N - p : p)) * a.n * a.n;
 }
 
 }  // namespace
 
 template <typename T>
-__global__ void __launch_bounds__(BT) kb_vectors(SweepArgs a, int p) {
+__global__ void __launch_bounds__(VT) kb_vectors(SweepArgs a, int p) {
   const int pt = blockIdx.x;
   if (inactive(a, pt)) return;
   const PointDesc d = a.pts[pt];
-  const int n = a.n, N = a.N, nc = a.nc, ncols = 2 * n + nc;
+  const int n = a.n, nc = a.nc, ncols = 2 * n + nc;
   const double *Ep = energies_of(a, d, p);
   const double *Eq = energies_of(a, d, p + 1);
   cx<T> *kv = reinterpret_cast<cx<T> *>(a.KV) + (size_t)pt * 3 * n;
-  const double dz = a.dz[slice_of(a, p + 1)];
-  for (int i = threadIdx.x; i < n; i += BT) {
+  const double dz = a.dz[d.dz_off + slice_of(a, d, p + 1)];
+  for (int i = threadIdx.x; i < n; i += VT) {
     const zc kl = kz_branch(d.E, Ep[i]);
     const zc kr = kz_branch(d.E, Eq[i]);
     kv[i] = ccast<T>(cinv(kl));
@@ -85,7 +102,7 @@ __global__ void __launch_bounds__(BT) kb_vectors(SweepArgs a, int p) {
   const bool tr = a.mirror != 0;
   const KVb<T> v = kv_of<T>(a, pt);
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
-  for (size_t e = threadIdx.x; e < (size_t)n * ncols; e += BT) {
+  for (size_t e = threadIdx.x; e < (size_t)n * ncols; e += VT) {
     const int i = e % n, j = e / n;
     cx<T> val;
     if (j < n) val = pqb<T>(O, n, i, j, v, T(1), tr);
@@ -95,13 +112,13 @@ __global__ void __launch_bounds__(BT) kb_vectors(SweepArgs a, int p) {
   }
 }
 
-template <typename T>
+template <typename T, int BT>
 __global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.y;
   if (inactive(a, pt)) return;
   const PointDesc d = a.pts[pt];
-  const int n = a.n, N = a.N, ncols = 2 * n + a.nc;
+  const int n = a.n, ncols = 2 * n + a.nc;
   const zc *O = overlap_of(a, d, p);
   const bool tr = a.mirror != 0;
   const cx<T> *R = reinterpret_cast<const cx<T> *>(a.R) + (size_t)pt * n * n;
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
       gsm, blockIdx.x, gridDim.x);
 }
 
-template <typename T>
+template <typename T, int BT>
 __global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
@@ -140,14 +157,20 @@ __global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
   T *sval = reinterpret_cast<T *>(Ls + NB * NB);
   int *sidx = reinterpret_cast<int *>(sval + 40);
   int *flag = sidx + 40;
+  cx<T> *P = reinterpret_cast<cx<T> *>(smraw + panel_head_bytes<T, BT>());
   if (threadIdx.x == 0) *flag = 0;
   __syncthreads();
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
-  lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.panel_smem) lu_panel_smem<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, P, Ls, sval, sidx, flag);
+    else lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
+  } else {
+    lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
+  }
   if (threadIdx.x == 0 && *flag) a.status[pt] = 1;
 }
 
-template <typename T>
+template <typename T, int BT>
 __global__ void __launch_bounds__(BT) kb_trail(SweepArgs a, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.y;
@@ -157,7 +180,7 @@ __global__ void __launch_bounds__(BT) kb_trail(SweepArgs a, int j0) {
   lu_trailing<T, BT>(M, n, n, ncols, j0, reinterpret_cast<cx<T> *>(smraw), blockIdx.x, gridDim.x);
 }
 
-template <typename T>
+template <typename T, int BT>
 __global__ void __launch_bounds__(BT) kb_bsdiag(SweepArgs a, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.y;
@@ -169,7 +192,7 @@ __global__ void __launch_bounds__(BT) kb_bsdiag(SweepArgs a, int j0) {
   lu_bs_diag<T, BT>(M, n, n, j0, c0, c1, reinterpret_cast<cx<T> *>(smraw));
 }
 
-template <typename T>
+template <typename T, int BT>
 __global__ void __launch_bounds__(BT) kb_bsupd(SweepArgs a, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.y;
@@ -180,10 +203,11 @@ __global__ void __launch_bounds__(BT) kb_bsupd(SweepArgs a, int j0) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
+__global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
   const int pt = blockIdx.x, tid = threadIdx.x;
   const PointDesc d = a.pts[pt];
-  const int n = a.n, N = a.N, nc = a.nc, ncols = 2 * n + nc;
+  const int n = a.n, N = d.N, nc = a.nc, ncols = 2 * n + nc;
+  if (p > N) return;
   if (inactive(a, pt)) {
     if (p == N && tid == 0) {
       a.T[d.out] = __longlong_as_double(0x7ff8000000000000ll);
@@ -197,23 +221,23 @@ __global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
   const int *piv = a.piv + (size_t)pt * n;
   const KVb<T> v = kv_of<T>(a, pt);
   if (a.Zst) {
-    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)pt * (N + 1) + p) * n * n;
-    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)pt * (N + 1) + p) * n * nc;
-    for (size_t e = tid; e < (size_t)n * n; e += BT) Zs[e] = M[(size_t)n * n + e];
-    for (size_t e = tid; e < (size_t)n * nc; e += BT) Us[e] = M[(size_t)2 * n * n + e];
+    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)d.st_off + p) * n * n;
+    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)d.st_off + p) * n * nc;
+    for (size_t e = tid; e < (size_t)n * n; e += VT) Zs[e] = M[(size_t)n * n + e];
+    for (size_t e = tid; e < (size_t)n * nc; e += VT) Us[e] = M[(size_t)2 * n * n + e];
   }
   if (a.LUst) {
-    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)pt * (N + 1) + p) * n * n;
-    int *Ps = a.PIVst + ((size_t)pt * (N + 1) + p) * n;
-    for (size_t e = tid; e < (size_t)n * n; e += BT) Ls[e] = M[e];
-    for (int e = tid; e < n; e += BT) Ps[e] = piv[e];
+    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)d.st_off + p) * n * n;
+    int *Ps = a.PIVst + ((size_t)d.st_off + p) * n;
+    for (size_t e = tid; e < (size_t)n * n; e += VT) Ls[e] = M[e];
+    for (int e = tid; e < n; e += VT) Ps[e] = piv[e];
   }
   // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
-  for (size_t e = tid; e < (size_t)n * n; e += BT) {
+  for (size_t e = tid; e < (size_t)n * n; e += VT) {
     const int i = e % n, j = e / n;
     R[e] = cmul(cmul(v.ep[i], M[i + (size_t)(n + j) * n]), v.ep[j]);
   }
-  for (size_t e = tid; e < (size_t)n * nc; e += BT) {
+  for (size_t e = tid; e < (size_t)n * nc; e += VT) {
     const int i = e % n, c = e / n;
     cx<T> &x = M[i + (size_t)(2 * n + c) * n];
     x = cmul(v.ep[i], x);
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
   const double *EL = energies_of(a, d, 0);
   const double *ER = energies_of(a, d, N + 1);
   double acc = 0.0;
-  for (int e = tid; e < d.nR * d.nL; e += BT) {
+  for (int e = tid; e < d.nR * d.nL; e += VT) {
     const int i = e % d.nR, j = e / d.nR;
     const double f = sqrt(sqrt(d.E - ER[i]) / sqrt(d.E - EL[j]));
     const cx<T> x = M[i + (size_t)(2 * n + j) * n];
@@ -233,57 +257,94 @@ __global__ void __launch_bounds__(BT) kb_finish(SweepArgs a, int p) {
     if (a.t) a.t[(size_t)d.out * n * n + i + (size_t)j * n] = tv;
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  __shared__ double red[BT / 32];
+  __shared__ double red[VT / 32];
   if ((tid & 31) == 0) red[tid >> 5] = acc;
   __syncthreads();
   if (tid == 0) {
     double tsum = 0.0;
-    for (int w = 0; w < BT / 32; ++w) tsum += red[w];
+    for (int w = 0; w < VT / 32; ++w) tsum += red[w];
     a.T[d.out] = tsum;
     if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
     if (a.err) a.err[d.out] = 0.0;
   }
 }
 
-template <typename T>
-static cudaError_t sweep_step(const SweepArgs &a, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
+template <typename T, int BT>
+static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
                               cudaEvent_t wy1) {
+  SweepArgs a = a0;
+  a.p = p;
   const int n = a.n, ncols = 2 * n + a.nc;
   constexpr int BM = Tile<T, BT>::BM, BN = Tile<T, BT>::BN, NB = Tile<T, BT>::NB;
   const size_t gsm = gemm_smem_elems<T, BT>() * sizeof(cx<T>);
-  const size_t psm = (size_t)NB * NB * sizeof(cx<T>) + 40 * sizeof(T) + 96 * sizeof(int);
+  const size_t psm_big = panel_head_bytes<T, BT>() + (size_t)n * NB * sizeof(cx<T>);
+  a.panel_smem = std::is_same<T, float>::value && psm_big <= (size_t)g_smem_optin;
+  const size_t psm = a.panel_smem ? psm_big : panel_head_bytes<T, BT>();
   const size_t dsm = (size_t)NB * NB * sizeof(cx<T>);
   auto tiles = [](int m, int nn, int bm, int bn) { return ((m + bm - 1) / bm) * ((nn + bn - 1) / bn); };
-  kb_vectors<T><<<npts, BT, 0, s>>>(a, p);
+  kb_vectors<T><<<npts, VT, 0, s>>>(a, p);
   if (p > 0) {
     const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
-    cudaFuncSetAttribute(kb_wy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
     if (wy0) cudaEventRecord(wy0, s);
-    kb_wy<T><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
+    kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
     if (wy1) cudaEventRecord(wy1, s);
   }
   for (int j0 = 0; j0 < n; j0 += NB) {
-    kb_panel<T><<<npts, BT, psm, s>>>(a, j0);
+    kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0);
     const int c0 = j0 + min(NB, n - j0);
-    if (c0 < n) kb_trail<T><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    if (c0 < n) kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
   for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
-    kb_bsdiag<T><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
-    if (j0 > 0) kb_bsupd<T><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
+    if (j0 > 0) kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
   }
-  kb_finish<T><<<npts, BT, 0, s>>>(a, p);
+  kb_finish<T><<<npts, VT, 0, s>>>(a, p);
   return cudaGetLastError();
 }
 
+// Dynamic shared-memory limits of the variant's kernels (outside any stream
+// capture: attributes are set once per process and size).
+template <typename T, int BT>
+static cudaError_t sweep_prepare(int n) {
+  const size_t gsm = gemm_smem_elems<T, BT>() * sizeof(cx<T>);
+  const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
+  if (!g_smem_optin) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  const size_t psm_big = panel_head_bytes<T, BT>() + (size_t)n * Tile<T, BT>::NB * sizeof(cx<T>);
+  if (std::is_same<T, float>::value && psm_big <= (size_t)g_smem_optin) {
+    const cudaError_t ep =
+        cudaFuncSetAttribute(kb_panel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm_big);
+    if (ep != cudaSuccess) return ep;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kb_wy<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_trail<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_bsupd<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  return e;
+}
+
+cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
+  if (precision == PW_FP64)
+    return variant ? sweep_prepare<double, 512>(n) : sweep_prepare<double, 256>(n);
+  return variant ? sweep_prepare<float, 512>(n) : sweep_prepare<float, 256>(n);
+}
+
 cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
-                                 cudaEvent_t wy0, cudaEvent_t wy1) {
-  return precision == PW_FP64 ? sweep_step<double>(a, npts, p, s, wy0, wy1)
-                              : sweep_step<float>(a, npts, p, s, wy0, wy1);
+                                 cudaEvent_t wy0, cudaEvent_t wy1, int variant) {
+  if (precision == PW_FP64)
+    return variant ? sweep_step<double, 512>(a, npts, p, s, wy0, wy1)
+                   : sweep_step<double, 256>(a, npts, p, s, wy0, wy1);
+  return variant ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1)
+                 : sweep_step<float, 256>(a, npts, p, s, wy0, wy1);
 }
 
 int sweep_batched_launches(int n) {
-  const int NB = Tile<float, BT>::NB;
+  const int NB = Tile<float, 256>::NB;
   const int panels = (n + NB - 1) / NB;
   return 3 + 2 * panels + 2 * panels - 2;
 }

@@ -68,6 +68,10 @@ class Instance:
     lead_vg: tuple | None = None         # optional explicit lead tables
     vg_half: tuple = (0, 0)              # (Dm, Dn): table index ranges [-Dm,Dm]x[-Dn,Dn]
     name: str = ""
+    # transverse displacement of each device well and of each electrode per
+    # unit sheet gap (bohr/bohr); None when the instance has no gap parameter
+    gap_rate_wells: np.ndarray | None = None   # (n_wells, 2)
+    gap_rate_leads: np.ndarray | None = None   # (2, 2): left, right
 
     @property
     def n_slices(self) -> int:
@@ -152,6 +156,10 @@ def junction(ng: int = 512, n_slices: int = 320, n_e: int = 128, n_k: int = 32,
             wells.append((x, y_top, z + c * cz + shift))
     wells = np.array(wells)
     nw = len(wells)
+    n_bot = len(bot_cells) * len(cell)
+    rate = np.zeros((nw, 2))
+    rate[:n_bot, 1] = -0.5          # y_bot = L_y/2 - gap/2
+    rate[n_bot:, 1] = 0.5           # y_top = L_y/2 + gap/2
     lead_l = Lead(np.stack([cell[:, 0], np.full(4, y_bot)], axis=1),
                   np.full(4, v0), np.full(4, sigma), cz)
     lead_r = Lead(np.stack([cell[:, 0], np.full(4, y_top)], axis=1),
@@ -169,7 +177,36 @@ def junction(ng: int = 512, n_slices: int = 320, n_e: int = 128, n_k: int = 32,
         z_edges=np.linspace(0.0, lz, n_slices + 1),
         wells_xyz=wells, v0=np.full(nw, v0), sigma=np.full(nw, sigma),
         lead_left=lead_l, lead_right=lead_r,
-        energies=ee, kpar=kpar, name=f"junction_{stacking}_ng{ng}_ns{n_slices}")
+        energies=ee, kpar=kpar, name=f"junction_{stacking}_ng{ng}_ns{n_slices}",
+        gap_rate_wells=rate, gap_rate_leads=np.array([[0.0, -0.5], [0.0, 0.5]]))
+
+
+def uneven_batch(n_inst: int = 2048, ng_choices=tuple(range(128, 769, 64)), ns_range=(60, 400),
+                 gap_range=(3.0, 5.0), e_ref: float = 0.2, seed_cfg: int = 4) -> list:
+    """Independent junction instances of uneven size, one (E, k_par) point
+    each: per instance (in this draw order) N_G uniform over ``ng_choices``,
+    the slice count uniform in ``ns_range`` (inclusive), the gap uniform in
+    ``gap_range`` (angstrom), AA or AB stacking with probability 1/2, E uniform
+    in E_ref +- 2 eV and k_par uniform in the 2D Brillouin zone of the
+    2.46 A x 20 A cell."""
+    rng = _rng(seed_cfg)
+    ax = 2.46 * ANGSTROM
+    ly = 20.0 * ANGSTROM
+    out = []
+    for _ in range(n_inst):
+        ng = int(rng.choice(np.asarray(ng_choices)))
+        ns = int(rng.integers(ns_range[0], ns_range[1] + 1))
+        gap = float(rng.uniform(*gap_range))
+        stacking = "AB" if rng.uniform() < 0.5 else "AA"
+        e = e_ref + float(rng.uniform(-2.0, 2.0)) / RYDBERG_EV
+        k = np.array([rng.uniform(-math.pi / ax, math.pi / ax), rng.uniform(-math.pi / ly, math.pi / ly)])
+        inst = junction(ng=ng, n_slices=ns, n_e=1, n_k=1, gap_angstrom=gap, stacking=stacking,
+                        e_ref=e_ref, seed_cfg=seed_cfg)
+        inst.energies = np.array([e])
+        inst.kpar = k.reshape(1, 2)
+        inst.name = f"uneven_{stacking}_ng{ng}_ns{ns}_gap{gap:.3f}"
+        out.append(inst)
+    return out
 
 
 def junction_ecut_for(ng_full: int) -> float:

@@ -64,3 +64,46 @@ def test_invalid_descriptors_rejected_before_any_device_call(pw):
     assert lib.pw_ng(None) == 0 and lib.pw_n_slices(None) == 0
     assert lib.pw_get_error(None) == 1
     lib.pw_destroy(None)
+
+
+def test_batch_arguments_rejected_before_any_device_call(pw):
+    """pw_setup_batch refuses an empty batch and mixed precisions before it
+    sets any instance up; the batch calls refuse null handles."""
+    lib = pw.lib()
+    h = ctypes.c_void_p()
+    descs = (pw.SetupDesc * 2)()
+    assert lib.pw_setup_batch(0, descs, None, ctypes.byref(h)) == 1
+    assert lib.pw_setup_batch(2, None, None, ctypes.byref(h)) == 1
+    descs[0].precision = 0
+    descs[1].precision = 1
+    assert lib.pw_setup_batch(2, descs, None, ctypes.byref(h)) == 1
+    descs[1].precision = 0
+    descs[1].refine_iters = 3
+    assert lib.pw_setup_batch(2, descs, None, ctypes.byref(h)) == 1
+    e = np.zeros(1)
+    assert lib.pw_transmission_batch(None, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, None,
+                                     None) == 1
+    assert lib.pw_batch_set_options(None, 1, -1) == 1
+    assert lib.pw_batch_get_stats(None, None, None, None, 0, None) == 1
+    lib.pw_batch_destroy(None)
+
+
+def test_binding_marshals_batches_and_contexts(pw):
+    """The ctypes binding builds every descriptor of a batch and of a context
+    from problem objects; without a CUDA device the library answers with a
+    CUDA status (never a Python error from the marshalling)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present: the GPU tests cover this path")
+    from synthetic import minimal_cell, uneven_batch
+    insts = uneven_batch(3, ng_choices=(16, 24), ns_range=(3, 5))
+    with pytest.raises(pw.PwError) as e:
+        pw.Batch.from_instances(insts, pw.MIXED_FP32, 2)
+    assert e.value.code == 3      # PW_ECUDA
+    with pytest.raises(pw.PwError) as e:
+        pw.Context.from_instance(insts[0], pw.MIXED_FP32, 2)
+    assert e.value.code == 3      # PW_ECUDA
+    with pytest.raises(pw.PwError) as e:
+        pw.Context.from_instance(minimal_cell())
+    assert e.value.code == 3      # PW_ECUDA

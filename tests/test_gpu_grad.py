@@ -1,5 +1,6 @@
 """pw_grad (adjoint of the summed transmission with respect to the device
-wells' depths) against the oracle's adjoint and central differences."""
+wells' depths and to the sheet gap) against the oracle's adjoint and central
+differences."""
 import copy
 
 import numpy as np
@@ -63,7 +64,68 @@ def test_grad_small_junction_against_oracle_adjoint(pw):
     assert np.abs(g - ref_g).max() < 1e-8 * max(1.0, np.abs(ref_g).max())
 
 
+def _oracle_gap(inst, E, k):
+    m = O.Model(inst)
+    dH = O.well_shift_derivative(m, inst.gap_rate_wells)
+    lr = tuple(map(tuple, inst.gap_rate_leads))
+    tot, g = 0.0, 0.0
+    for Ei, ki in zip(E, k):
+        T, gi = O.grad_T(m, np.asarray(ki), float(Ei), [dH], [lr])
+        tot += T
+        g += gi[0]
+    return tot, g
+
+
+def test_gap_derivative_small_junction(pw):
+    """d sum T / d gap: wells of each sheet and its electrode move by half the
+    gap; against the oracle's adjoint and central differences over the
+    generated geometry (step 1e-5 angstrom)."""
+    from synthetic.junction import ANGSTROM
+    inst = junction(ng=48, n_slices=16, n_e=3, n_k=4)
+    sel = [1, 5, 6, 9]
+    E, k = inst.energies[sel], inst.kpar[sel]
+    with pw.Context.from_instance(inst) as ctx:
+        sumT, dV0, dgap = ctx.grad(E, k, None, n_wells=len(inst.v0), gap=True)
+    ref_T, ref_g = _oracle_gap(inst, E, k)
+    assert abs(sumT - ref_T) < 1e-10 * max(1.0, ref_T)
+    assert abs(dgap - ref_g) < 1e-8 * max(1.0, abs(ref_g))
+    h = 1e-5
+    vals = []
+    for gap in (3.35 + h, 3.35 - h):
+        J = junction(ng=48, n_slices=16, n_e=3, n_k=4, gap_angstrom=gap)
+        vals.append(float(np.sum(O.transmission(J, points=sel))))
+    fd = (vals[0] - vals[1]) / (2 * h * ANGSTROM)
+    assert abs(fd - dgap) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_shift_derivative_asymmetric_cell(pw):
+    """Arbitrary transverse motion (x and y) of wells and both electrodes of a
+    cell without symmetry; and a rigid translation of everything gives 0."""
+    from synthetic import Lead
+    E = np.array([2.3, 4.1])
+    k = np.array([[0.1, -0.2], [0.0, 0.3]])
+    inst = minimal_cell(n_wells=4, n_slices=6, energies=E, kpar=k)
+    rng = np.random.default_rng(7)
+    inst.lead_left = Lead(rng.uniform(0, 5, (2, 2)), np.array([1.5, 2.0]), np.array([0.6, 0.6]), 1.3)
+    inst.lead_right = Lead(rng.uniform(0, 5, (3, 2)), np.array([1.0, 2.5, 1.2]),
+                           np.array([0.6, 0.5, 0.7]), 0.9)
+    inst.gap_rate_wells = rng.uniform(-1, 1, (len(inst.v0), 2))
+    inst.gap_rate_leads = np.array([[0.4, -0.7], [-0.2, 0.5]])
+    with pw.Context.from_instance(inst) as ctx:
+        sumT, _, dgap = ctx.grad(E, k, None, gap=True)
+    ref_T, ref_g = _oracle_gap(inst, E, k)
+    assert abs(sumT - ref_T) < 1e-10 * max(1.0, ref_T)
+    assert abs(ref_g) > 1e-3
+    assert abs(dgap - ref_g) < 1e-9 * max(1.0, abs(ref_g))
+    inst.gap_rate_wells = np.tile([0.3, 1.0], (len(inst.v0), 1))
+    inst.gap_rate_leads = np.array([[0.3, 1.0], [0.3, 1.0]])
+    with pw.Context.from_instance(inst) as ctx:
+        _, _, rigid = ctx.grad(E, k, None, gap=True)
+    assert abs(rigid) < 1e-10
+
+
 def test_grad_rejects_gap_and_tables(pw):
+    """No geometry motion given at setup: the gap derivative is refused."""
     inst = minimal_cell(n_wells=2, n_slices=3)
     import ctypes
     with pw.Context.from_instance(inst) as ctx:
@@ -75,3 +137,35 @@ def test_grad_rejects_gap_and_tables(pw):
         st = pw.lib().pw_grad(ctx.handle, 1, E.ctypes.data_as(dp), k.ctypes.data_as(dp), None,
                               s.ctypes.data_as(dp), None, gap.ctypes.data_as(dp))
         assert st == 1
+
+
+def test_autograd_function_over_pw_grad(pw):
+    """torch.autograd through SummedTransmission: gradients of V0 and of the
+    gap (per angstrom) equal the adjoint's and central differences of the
+    forward value."""
+    from paper_1504_01462_gb300.autograd import summed_transmission
+    from synthetic.junction import ANGSTROM
+    base = junction(ng=48, n_slices=16, n_e=3, n_k=4)
+    sel = [1, 5, 6]
+    E, k = base.energies[sel], base.kpar[sel]
+
+    def make(v0, gap):
+        inst = junction(ng=48, n_slices=16, n_e=3, n_k=4, gap_angstrom=gap)
+        inst.v0 = v0.copy()
+        inst.gap_rate_wells = inst.gap_rate_wells * ANGSTROM     # per angstrom
+        inst.gap_rate_leads = inst.gap_rate_leads * ANGSTROM
+        return pw.Context.from_instance(inst)
+
+    v0 = torch.tensor(base.v0, dtype=torch.float64, requires_grad=True)
+    gap = torch.tensor(3.35, dtype=torch.float64, requires_grad=True)
+    out = summed_transmission(v0, gap, make, E, k)
+    out.backward()
+    with make(base.v0, 3.35) as ctx:
+        sumT, dV0, dgap = ctx.grad(E, k, None, n_wells=len(base.v0), gap=True)
+    assert abs(out.item() - sumT) < 1e-12 * max(1.0, sumT)
+    assert torch.allclose(v0.grad, torch.as_tensor(dV0), rtol=0, atol=1e-12)
+    h = 1e-5
+    with torch.no_grad():
+        fp = summed_transmission(v0, gap + h, make, E, k).item()
+        fm = summed_transmission(v0, gap - h, make, E, k).item()
+    assert abs((fp - fm) / (2 * h) - gap.grad.item()) < 1e-6 * max(1.0, abs(gap.grad.item()))

@@ -89,6 +89,17 @@ def test_potential_tables_match_oracle(pw):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("ng,nsl", [(21, 16), (97, 6)])
 def test_slice_modes_against_oracle_hamiltonians(pw, ng, nsl):
+    _check_slice_modes(pw, ng, nsl, precision=0, tol=1.0)
+
+
+@pytest.mark.parametrize("ng,nsl", [(21, 4), (64, 3), (512, 2)])
+def test_slice_modes_double_float_mixed_form(pw, ng, nsl):
+    """The mixed form's eigensolver and overlaps run in double-float
+    (48-bit) arithmetic on the FP32 pipe: same checks, 10x looser."""
+    _check_slice_modes(pw, ng, nsl, precision=1, tol=10.0)
+
+
+def _check_slice_modes(pw, ng, nsl, precision, tol):
     if ng == 21:
         inst = minimal_cell(n_slices=nsl)
         k = np.array([0.13, -0.27])
@@ -97,7 +108,7 @@ def test_slice_modes_against_oracle_hamiltonians(pw, ng, nsl):
         k = np.array([0.21, 0.0])
     m = O.Model(inst)
     n, nq = m.n, m.N + 2
-    with pw.Context.from_instance(inst) as ctx:
+    with pw.Context.from_instance(inst, precision) as ctx:
         En = _dev((nq, n), torch.float64)
         U = _dev((nq, n, n), torch.complex128)
         Ov = _dev((nq - 1, n, n), torch.complex128)
@@ -112,11 +123,11 @@ def test_slice_modes_against_oracle_hamiltonians(pw, ng, nsl):
         H = O.hamiltonian(m.mn, m.G, k, tab, m.half)
         ref = np.linalg.eigvalsh(H)
         scale = max(1.0, np.abs(ref).max())
-        assert np.abs(En[q] - ref).max() < 1e-12 * scale
-        assert np.abs(H @ U[q] - U[q] * En[q][None, :]).max() < 1e-11 * scale
-        assert np.abs(U[q].conj().T @ U[q] - np.eye(n)).max() < 1e-12
+        assert np.abs(En[q] - ref).max() < 1e-12 * tol * scale
+        assert np.abs(H @ U[q] - U[q] * En[q][None, :]).max() < 1e-11 * tol * scale
+        assert np.abs(U[q].conj().T @ U[q] - np.eye(n)).max() < 1e-12 * tol
     for p in range(nq - 1):
-        assert np.abs(Ov[p] - O.overlap(U[p], U[p + 1])).max() < 1e-12
+        assert np.abs(Ov[p] - O.overlap(U[p], U[p + 1])).max() < 1e-12 * tol
 
 
 # ---------------------------------------------------------------------------
