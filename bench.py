@@ -9,6 +9,11 @@ points, and T = Tr(t^H t).  Metric: (E, k_par)-points/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
     python bench.py --impl reference   # the CPU oracle on the host cores
+    python bench.py --config uneven [--instances K]   # uneven-batch form
+
+The uneven-batch line times pw_transmission_batch over the first K of the
+2048 seeded instances of uneven N_G (128..768) and slice count (60..400), one
+(E, k_par) point each; a step is one call over those K instances.
 
 Under torchrun each rank takes its own k_par points (weak scaling, no data
 exchange); rank 0 prints one JSON line.
@@ -29,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synthetic import junction, minimal_cell  # noqa: E402
+from synthetic import junction, minimal_cell, uneven_batch  # noqa: E402
 
 METRIC = "(E,k∥)-points/s at N_G=512, 320 slices: mixed-precision vs FP64, at 1e-8 rel T"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -194,6 +199,55 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_uneven(args, torch, pw, local):
+    """The uneven-batch form on one GPU: K instances per step, one call."""
+    insts = uneven_batch(2048)[:args.instances]
+    prec = pw.MIXED_FP32 if args.precision == "mixed" else pw.FP64
+    E = np.array([float(x.energies[0]) for x in insts])
+    k = np.array([x.kpar[0] for x in insts])
+    stream = torch.cuda.current_stream()
+    b = pw.Batch.from_instances(insts, prec, 0 if prec == pw.FP64 else 4, stream=stream.cuda_stream)
+    T = torch.empty(len(insts), dtype=torch.float64, device="cuda")
+    err = torch.zeros(len(insts), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        b.transmission(E, k, T, err_out=err, allow_threshold=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stage = None
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.transmission(E, k, T, err_out=err, allow_threshold=True)
+        st = b.stats()
+        stage = st if stage is None else {kk: stage[kk] + st[kk] if kk != "variant" else st[kk]
+                                           for kk in st}
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ng = [x.ng_exact for x in insts]
+    ns = [x.n_slices for x in insts]
+    line = {
+        "metric": "uneven-batch instances/s (one (E,k_par) point each)",
+        "value": args.steps * len(insts) / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64" if prec == pw.MIXED_FP32 else "c128", "data": "synthetic",
+        "config": {"workload": f"uneven: first {len(insts)} of 2048 seeded instances, N_G "
+                               f"{min(ng)}..{max(ng)}, {min(ns)}..{max(ns)} slices",
+                   "precision": args.precision, "l2": "inputs larger than L2",
+                   "sum_n3_slices": float(sum(float(a) ** 3 * (b_ + 2) for a, b_ in zip(ng, ns)))},
+        "stages_ms": {kk: vv for kk, vv in stage.items() if kk != "variant"},
+        "variant_per_ng": stage["variant"],
+        "clocks": clk,
+        "accuracy": {"err_est_max": float(torch.nan_to_num(err).max().item())},
+    }
+    print(json.dumps(line))
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,7 +256,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--config", default="junction512",
-                    choices=["junction512", "junction401", "minimal"])
+                    choices=["junction512", "junction401", "minimal", "uneven"])
+    ap.add_argument("--instances", type=int, default=96,
+                    help="uneven config: how many of the 2048 instances one step covers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--refine", type=int, default=0,
@@ -226,6 +282,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.config == "uneven":
+        return run_uneven(args, torch, pw, local)
     if world > 1:
         dist.init_process_group("nccl")
 

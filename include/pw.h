@@ -130,6 +130,12 @@ const char *pw_status_str(pw_status s);
 
 /* Latched status of the context (PW_OK if no call has failed). */
 pw_status pw_get_error(const pw_ctx *ctx);
+/* The first failing CUDA runtime call behind a latched PW_ECUDA / PW_ENOMEM:
+ * "<cudaError name> at <source>:<line>" (empty when none), NUL-terminated into
+ * buf[len].  Setting PW_SYNC_CHECK=1 in the environment makes every stage
+ * synchronise its stream, so an asynchronous kernel failure is reported by
+ * the stage that launched it. */
+pw_status pw_get_error_detail(const pw_ctx *ctx, char *buf, int len);
 
 /* Basis size N_G and slice count N of the context (0 for NULL). */
 int pw_ng(const pw_ctx *ctx);

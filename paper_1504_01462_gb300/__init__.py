@@ -33,7 +33,7 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_slice_smatrix", "pw_compose", "pw_transmission", "pw_set_profiling",
            "pw_get_profile", "pw_compose_noalloc", "pw_grad", "pw_setup_batch",
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
-           "pw_batch_destroy"]
+           "pw_batch_destroy", "pw_get_error_detail"]
 
 
 class PwError(RuntimeError):
@@ -94,6 +94,7 @@ def _load():
     lib.pw_batch_set_options.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     lib.pw_batch_get_stats.argtypes = [_vp, _dp, _ip, _ip, ctypes.c_int, _ip]
     lib.pw_batch_destroy.argtypes = [_vp]
+    lib.pw_get_error_detail.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
     lib.pw_batch_destroy.restype = None
     return lib
 
@@ -204,6 +205,11 @@ def _instance_geometry(inst, refine_iters=0):
                 refine_iters=refine_iters,
                 well_shift_rate=getattr(inst, "gap_rate_wells", None),
                 lead_shift_rate=getattr(inst, "gap_rate_leads", None))
+
+
+def _check_status(st, where):
+    if st != 0:
+        raise PwError(st, where)
 
 
 class Context:
@@ -332,10 +338,14 @@ class Context:
         # refine_stages counts refinement passes
         return dict(zip(keys, out.tolist()))
 
-    @staticmethod
-    def _check(st, where):
+    def _check(self, st, where):
+        """Raise PwError for a failing status, with the library's record of
+        the first failing CUDA call of this context when it has one."""
         if st != 0:
-            raise PwError(st, where)
+            buf = ctypes.create_string_buffer(160)
+            if getattr(self, "_h", None):
+                _lib.pw_get_error_detail(self._h, buf, 160)
+            raise PwError(st, f"{where} [{buf.value.decode()}]" if buf.value else where)
 
 
 class Batch:
@@ -361,7 +371,7 @@ class Batch:
         return cls([_instance_geometry(x) for x in insts], precision, refine_iters, stream)
 
     def set_options(self, use_graph=True, variant=-1):
-        Context._check(_lib.pw_batch_set_options(self._h, int(bool(use_graph)), int(variant)),
+        _check_status(_lib.pw_batch_set_options(self._h, int(bool(use_graph)), int(variant)),
                        "pw_batch_set_options")
 
     def transmission(self, E, kpar, T_out, nopen_out=None, err_out=None, allow_threshold=False):
@@ -374,7 +384,7 @@ class Batch:
                                         _ptr(err_out))
         if st == PW_ETHRESH and allow_threshold:
             return st
-        Context._check(st, "pw_transmission_batch")
+        _check_status(st, "pw_transmission_batch")
         return st
 
     def stats(self):
@@ -383,7 +393,7 @@ class Batch:
         ng = np.zeros(64, dtype=np.int32)
         var = np.zeros(64, dtype=np.int32)
         cnt = np.zeros(1, dtype=np.int32)
-        Context._check(_lib.pw_batch_get_stats(self._h, _as_dp(out), ng.ctypes.data_as(_ip),
+        _check_status(_lib.pw_batch_get_stats(self._h, _as_dp(out), ng.ctypes.data_as(_ip),
                                                var.ctypes.data_as(_ip), 64,
                                                cnt.ctypes.data_as(_ip)), "pw_batch_get_stats")
         keys = ["modes_ms", "overlap_ms", "sweep_ms", "refine_ms", "tune_ms", "chunks",

@@ -3,6 +3,8 @@
 // cache, batching of (E, k_par) points and the launch sequence of the sweep.
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -32,6 +34,7 @@ struct pw_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   pw_status err = PW_OK;
+  char err_detail[160] = {0};      // first failing runtime call (pw_get_error_detail)
   int precision = PW_FP64;
   int refine_iters = 0;            // FP64 refinement passes of the mixed form
   int n = 0, N = 0, nq = 0;        // basis size, slices, slices incl. electrodes
@@ -115,6 +118,13 @@ pw_status latch(pw_ctx *c, pw_status s) {
   return s;
 }
 
+// The first failing runtime call of a context: its CUDA error and source line.
+pw_status latch_cuda(pw_ctx *c, cudaError_t e, int line) {
+  if (c && c->err == PW_OK && c->err_detail[0] == 0)
+    snprintf(c->err_detail, sizeof(c->err_detail), "%s at pw_api.cu:%d", cudaGetErrorName(e), line);
+  return latch(c, e == cudaErrorMemoryAllocation ? PW_ENOMEM : PW_ECUDA);
+}
+
 // A failed runtime call is reported once: the runtime's last-error state is
 // cleared so that it does not resurface in a later, unrelated call.
 #define CK(call)                                                                                    \
@@ -122,8 +132,22 @@ pw_status latch(pw_ctx *c, pw_status s) {
     cudaError_t e_ = (call);                                                                        \
     if (e_ != cudaSuccess) {                                                                        \
       cudaGetLastError();                                                                           \
-      return latch(ctx, e_ == cudaErrorMemoryAllocation ? PW_ENOMEM : PW_ECUDA);                   \
+      return latch_cuda(ctx, e_, __LINE__);                                                         \
     }                                                                                               \
+  } while (0)
+
+// With PW_SYNC_CHECK=1 in the environment every stage is followed by a stream
+// synchronisation, so that a failing kernel is reported at its own stage.
+bool sync_check() {
+  static const int on = [] {
+    const char *v = getenv("PW_SYNC_CHECK");
+    return v && v[0] == '1' ? 1 : 0;
+  }();
+  return on != 0;
+}
+#define SYNC_CHECK()                                                                                \
+  do {                                                                                              \
+    if (sync_check()) CK(cudaStreamSynchronize(ctx->stream));                                       \
   } while (0)
 
 pw_status ensure(pw_ctx *ctx, DevBuf &b, size_t bytes) {
@@ -246,11 +270,13 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
                  ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
                  ctx->stream, ctx->precision == PW_MIXED_FP32);
   CK(cudaGetLastError());
+  SYNC_CHECK();
   st1.done();
   Stage st2(ctx, 2, s1 - s0);
   pw::launch_overlaps(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq,
                       s1 - s0, ctx->stream, ctx->precision == PW_MIXED_FP32);
   CK(cudaGetLastError());
+  SYNC_CHECK();
   st2.done();
   std::vector<int> stat(nmat);
   CK(cudaMemcpyAsync(stat.data(), ctx->d_eigstat + (size_t)s0 * nq, nmat * sizeof(int),
@@ -341,6 +367,11 @@ const char *pw_status_str(pw_status s) {
 }
 
 pw_status pw_get_error(const pw_ctx *ctx) { return ctx ? ctx->err : PW_EINVAL; }
+pw_status pw_get_error_detail(const pw_ctx *ctx, char *buf, int len) {
+  if (!ctx || !buf || len <= 0) return PW_EINVAL;
+  snprintf(buf, (size_t)len, "%s", ctx->err_detail);
+  return PW_OK;
+}
 int pw_ng(const pw_ctx *ctx) { return ctx ? ctx->n : 0; }
 int pw_n_slices(const pw_ctx *ctx) { return ctx ? ctx->N : 0; }
 
@@ -745,6 +776,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
         CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream, w0, w1));
         if (w0) ctx->recs.push_back({w0, w1, 4, 1});
+        SYNC_CHECK();
       }
       s0.done();
       if (refine) {
@@ -781,6 +813,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         int passes = 0;
         CK(pw::launch_refine(r, nb, std::min(2, ctx->refine_iters), ctx->refine_iters, kRefineTol,
                              ctx->stream, &passes));
+        SYNC_CHECK();
         s3.count = passes;
         s3.done();
         ctx->last_passes = passes;

@@ -6,6 +6,7 @@
 // One CTA owns one problem (one (E, k_par) point); every function here must be
 // called by all threads of the CTA and ends with a __syncthreads().
 #pragma once
+#include <type_traits>
 #include "pw_cx.cuh"
 
 namespace pw {
@@ -278,7 +279,11 @@ __device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *p
       const T v = cabs1(P[r + jj * R]);
       if (v > best) { best = v; bi = r; }
     }
-    const int p = block_argmax<T, NTH>(best, bi, sval, sidx);
+    int p = block_argmax<T, NTH>(best, bi, sval, sidx);
+    if (p < jj || p >= R) {   // cannot happen; recorded rather than followed
+      if (tid == 0) atomicOr(flag, 4);
+      p = jj;
+    }
     if (tid == 0) piv[j0 + jj] = j0 + p;
     if (p != jj) {
       for (int c = tid; c < nb; c += NTH) {
@@ -320,6 +325,7 @@ __device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *p
     cx<T> *col = M + (size_t)c * ld + j0;
     for (int r = 0; r < nb; ++r) {
       const int p = piv[j0 + r] - j0;
+      if (p < r || p >= R) continue;   // cannot happen (checked above)
       if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
     }
     cx<T> x[NB];
@@ -361,6 +367,7 @@ __device__ void lu_trailing(cx<T> *M, int ld, int n, int ncols, int j0, cx<T> *g
 
 // Diagonal block j0 of the back substitution: X_b = U_bb^{-1} B_b for the
 // right-hand-side columns [c_first, c_last) (a subset of [n, ncols)).
+// Ls: 2*NB*NB elements (the FP32 variant keeps the inverted block after it).
 template <typename T, int NTH = NT>
 __device__ void lu_bs_diag(cx<T> *M, int ld, int n, int j0, int c_first, int c_last, cx<T> *Ls) {
   constexpr int NT = NTH;
@@ -371,16 +378,56 @@ __device__ void lu_bs_diag(cx<T> *M, int ld, int n, int j0, int c_first, int c_l
     Ls[r + s2 * NB] = M[j0 + r + (size_t)(j0 + s2) * ld];
   }
   __syncthreads();
-  for (int c = c_first + tid; c < c_last; c += NT) {
-    cx<T> *col = M + (size_t)c * ld + j0;
-    for (int r = nb - 1; r >= 0; --r) {
-      cx<T> x = col[r];
-      for (int s2 = r + 1; s2 < nb; ++s2) {
-        const cx<T> u = Ls[r + s2 * NB], y = col[s2];
-        x.re -= u.re * y.re - u.im * y.im;
-        x.im -= u.re * y.im + u.im * y.re;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: X = U11^{-1} B with U11^{-1} formed once per block in shared memory
+    // (column j by back substitution on e_j, one thread per column), then every
+    // RHS column is an independent triangular matrix-vector product
+    cx<T> *Ui = Ls + NB * NB;   // NB x NB, upper triangular
+    for (int j = tid; j < nb; j += NT) {
+      for (int r = nb - 1; r >= 0; --r) {
+        cx<T> x = mkc<T>(r == j ? T(1) : T(0), T(0));
+        if (r > j) {
+          Ui[r + j * NB] = czero<T>();
+          continue;
+        }
+        for (int s2 = r + 1; s2 <= j; ++s2) {
+          const cx<T> u = Ls[r + s2 * NB], y = Ui[s2 + j * NB];
+          x.re -= u.re * y.re - u.im * y.im;
+          x.im -= u.re * y.im + u.im * y.re;
+        }
+        Ui[r + j * NB] = cdiv(x, Ls[r + r * NB]);
       }
-      col[r] = cdiv(x, Ls[r + r * NB]);
+    }
+    __syncthreads();
+    for (int c = c_first + tid; c < c_last; c += NT) {
+      cx<T> *col = M + (size_t)c * ld + j0;
+      cx<T> x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = czero<T>();
+#pragma unroll
+      for (int s2 = 0; s2 < NB; ++s2) {
+        if (s2 < nb) {
+          const cx<T> b = col[s2];
+#pragma unroll
+          for (int r = 0; r <= s2; ++r) cfma(x[r], Ui[r + s2 * NB], b);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < nb) col[r] = x[r];
+    }
+  } else {
+    for (int c = c_first + tid; c < c_last; c += NT) {
+      cx<T> *col = M + (size_t)c * ld + j0;
+      for (int r = nb - 1; r >= 0; --r) {
+        cx<T> x = col[r];
+        for (int s2 = r + 1; s2 < nb; ++s2) {
+          const cx<T> u = Ls[r + s2 * NB], y = col[s2];
+          x.re -= u.re * y.re - u.im * y.im;
+          x.im -= u.re * y.im + u.im * y.re;
+        }
+        col[r] = cdiv(x, Ls[r + r * NB]);
+      }
     }
   }
   __syncthreads();

@@ -8,6 +8,7 @@
 //   k_overlaps    O_p = U_p^H U_{p+1} = sum_s (M^{p+1}_{js})^* M^p_{ns}
 //                 of App. A Eq. transfer
 #include <math.h>
+#include <stdio.h>
 
 #include <type_traits>
 
@@ -487,6 +488,19 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   Rot *snr = csr + n;
   int *ctl = reinterpret_cast<int *>(snr + n);   // [m, lo, rotations-formed flag, failed]
   int *rank = ctl + 8;
+  {
+    // the carve above must fit the launch's dynamic shared memory
+    unsigned dyn = 0;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const size_t need = (size_t)(reinterpret_cast<unsigned char *>(rank + n) - smraw);
+    if (need > dyn) {
+      if (tid == 0) {
+        printf("k_heev: needs %llu bytes of shared memory, launched with %u\n", (unsigned long long)need, dyn);
+        status[mat] = -2;
+      }
+      return;
+    }
+  }
   if (tid == 0) ctl[3] = 0;
   if constexpr (!std::is_same<R, double>::value) {
     // to the solver's format, element by element in place
@@ -625,9 +639,19 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
         }
       }
       __syncthreads();
-      const int m = ctl[0], lo = ctl[1];
+      const int m = ctl[0], lo = ctl[1], formed = ctl[2];
+      // every thread has read this step's control words before thread 0 can
+      // write the next step's (a break below skips the barrier at the end)
+      __syncthreads();
       if (m == l) break;
-      if (ctl[2] && lo < m) {
+      if (m < 0 || m >= n || lo < 0 || lo > m) {   // cannot happen; recorded, not followed
+        if (tid == 0) {
+          printf("k_heev: QL step out of range (matrix %d, l %d, m %d, lo %d)\n", mat, l, m, lo);
+          ctl[3] = 1;
+        }
+        break;
+      }
+      if (formed && lo < m) {
         for (int row = tid; row < n; row += NTH) {
           C x = Z[row + (size_t)m * n];
           for (int i = m - 1; i >= lo; --i) {

@@ -12,6 +12,7 @@
 // The arithmetic of each element is the same as in the one-CTA-per-point
 // kernel (same tile loops and accumulation order).
 #include <math.h>
+#include <stdio.h>
 
 #include <type_traits>
 
@@ -33,6 +34,7 @@ __host__ __device__ constexpr size_t panel_head_bytes() {
 }
 
 int g_smem_optin = 0;   // opt-in shared memory per block of the device (set by prepare)
+constexpr int FINISH_BLOCKS = 8;   // blocks per point of kb_finish
 
 template <typename T>
 struct KVb {
@@ -162,11 +164,19 @@ __global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
   __syncthreads();
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   if constexpr (std::is_same<T, float>::value) {
-    if (a.panel_smem) lu_panel_smem<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, P, Ls, sval, sidx, flag);
+    // the staged panel must fit the launch's dynamic shared memory
+    unsigned dyn = 0;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const bool fits = panel_head_bytes<T, BT>() + (size_t)(n - j0) * NB * sizeof(cx<T>) <= dyn;
+    if (a.panel_smem && !fits && threadIdx.x == 0 && pt == 0 && j0 == 0)
+      printf("kb_panel: staged panel of %d rows does not fit %u bytes; global path taken\n", n - j0, dyn);
+    if (a.panel_smem && fits)
+      lu_panel_smem<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, P, Ls, sval, sidx, flag);
     else lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
   } else {
     lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
   }
+  if (threadIdx.x == 0 && (*flag & 4)) printf("kb_panel: pivot row out of range (point %d, panel %d)\n", pt, j0);
   if (threadIdx.x == 0 && *flag) a.status[pt] = 1;
 }
 
@@ -204,12 +214,15 @@ __global__ void __launch_bounds__(BT) kb_bsupd(SweepArgs a, int j0) {
 
 template <typename T>
 __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
-  const int pt = blockIdx.x, tid = threadIdx.x;
+  // grid (FINISH_BLOCKS, points): the n x n stores and the R update are spread
+  // over all blocks of a point; block 0 also stores u_p and the pivots, scales
+  // Tacc and, after the last interface, forms t and T
+  const int pt = blockIdx.y, tid = threadIdx.x, blk = blockIdx.x, nblk = gridDim.x;
   const PointDesc d = a.pts[pt];
   const int n = a.n, N = d.N, nc = a.nc, ncols = 2 * n + nc;
   if (p > N) return;
   if (inactive(a, pt)) {
-    if (p == N && tid == 0) {
+    if (p == N && tid == 0 && blk == 0) {
       a.T[d.out] = __longlong_as_double(0x7ff8000000000000ll);
       if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
       if (a.err) a.err[d.out] = 0.0;
@@ -220,23 +233,31 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   const int *piv = a.piv + (size_t)pt * n;
   const KVb<T> v = kv_of<T>(a, pt);
+  const size_t nn = (size_t)n * n;
+  const size_t e0 = nn * blk / nblk, e1 = nn * (blk + 1) / nblk;
   if (a.Zst) {
-    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)d.st_off + p) * n * n;
-    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)d.st_off + p) * n * nc;
-    for (size_t e = tid; e < (size_t)n * n; e += VT) Zs[e] = M[(size_t)n * n + e];
-    for (size_t e = tid; e < (size_t)n * nc; e += VT) Us[e] = M[(size_t)2 * n * n + e];
+    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)d.st_off + p) * nn;
+    for (size_t e = e0 + tid; e < e1; e += VT) Zs[e] = M[nn + e];
   }
   if (a.LUst) {
-    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)d.st_off + p) * n * n;
-    int *Ps = a.PIVst + ((size_t)d.st_off + p) * n;
-    for (size_t e = tid; e < (size_t)n * n; e += VT) Ls[e] = M[e];
-    for (int e = tid; e < n; e += VT) Ps[e] = piv[e];
+    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)d.st_off + p) * nn;
+    for (size_t e = e0 + tid; e < e1; e += VT) Ls[e] = M[e];
   }
-  // R <- E+ Z_Y E+,  Tacc <- E+ Z_T
-  for (size_t e = tid; e < (size_t)n * n; e += VT) {
+  // R <- E+ Z_Y E+
+  for (size_t e = e0 + tid; e < e1; e += VT) {
     const int i = e % n, j = e / n;
     R[e] = cmul(cmul(v.ep[i], M[i + (size_t)(n + j) * n]), v.ep[j]);
   }
+  if (blk != 0) return;
+  if (a.Zst) {
+    cx<T> *Us = reinterpret_cast<cx<T> *>(a.Ust) + ((size_t)d.st_off + p) * n * nc;
+    for (size_t e = tid; e < (size_t)n * nc; e += VT) Us[e] = M[2 * nn + e];
+  }
+  if (a.LUst) {
+    int *Ps = a.PIVst + ((size_t)d.st_off + p) * n;
+    for (int e = tid; e < n; e += VT) Ps[e] = piv[e];
+  }
+  // Tacc <- E+ Z_T (after its store above: the same thread owns each element)
   for (size_t e = tid; e < (size_t)n * nc; e += VT) {
     const int i = e % n, c = e / n;
     cx<T> &x = M[i + (size_t)(2 * n + c) * n];
@@ -280,7 +301,7 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   const size_t psm_big = panel_head_bytes<T, BT>() + (size_t)n * NB * sizeof(cx<T>);
   a.panel_smem = std::is_same<T, float>::value && psm_big <= (size_t)g_smem_optin;
   const size_t psm = a.panel_smem ? psm_big : panel_head_bytes<T, BT>();
-  const size_t dsm = (size_t)NB * NB * sizeof(cx<T>);
+  const size_t dsm = (size_t)2 * NB * NB * sizeof(cx<T>);
   auto tiles = [](int m, int nn, int bm, int bn) { return ((m + bm - 1) / bm) * ((nn + bn - 1) / bn); };
   kb_vectors<T><<<npts, VT, 0, s>>>(a, p);
   if (p > 0) {
@@ -299,7 +320,7 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
     if (j0 > 0) kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
   }
-  kb_finish<T><<<npts, VT, 0, s>>>(a, p);
+  kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p);
   return cudaGetLastError();
 }
 
