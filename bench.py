@@ -264,6 +264,9 @@ def main():
     ap.add_argument("--refine", type=int, default=0,
                     help="most FP64 refinement passes of the mixed form (0: library default, "
                          "-1: none)")
+    ap.add_argument("--sweep-variant", type=int, default=-1,
+                    help="sweep launch variant (bit 0: 512-thread SIMT tiles, bit 1: [W|Y], LU and "
+                         "back-substitution GEMMs on the tcgen05 tensor cores); -1: library default")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP64 re-evaluation of sampled points of the last step")
     ap.add_argument("--slices", type=int, default=0,
@@ -299,6 +302,8 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = pw.Context.from_instance(inst, precision=prec, refine_iters=args.refine,
                                    stream=stream.cuda_stream)
+    if args.sweep_variant >= 0:
+        ctx.set_sweep_variant(args.sweep_variant)
     n, N = ctx.ng, ctx.n_slices
     npts = len(inst.energies)
 

@@ -246,6 +246,15 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
 pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
                              pw_c128 *Sab_dev, void *cuda_stream);
 
+/* Launch variant of the star-product sweep of pw_transmission (default 0).
+ * Bit 0: 512-thread CTAs with 128 x 64 SIMT GEMM tiles (else 256 threads with
+ * 64 x 64 tiles).  Bit 1 (PW_MIXED_FP32 only): the [W|Y] product of every
+ * interface on the fifth-generation tensor cores (tcgen05, TF32 operands split
+ * into hi + lo parts, three products accumulated in FP32 in tensor memory).
+ * PW_EINVAL for a variant the context's precision does not have (0..1 for
+ * PW_FP64, 0..3 for PW_MIXED_FP32). */
+pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant);
+
 /* Timing of the library's own launches (for benchmarks and roofline
  * accounting).  While enabled, CUDA events on the context's stream bracket
  * every stage: the slice-mode stage (Hamiltonian assembly and eigensolver), the
@@ -280,9 +289,8 @@ pw_status pw_setup_batch(int n_inst, const pw_setup_desc *descs, void *cuda_stre
  * Instances are grouped by N_G (largest first) and each group is cut into
  * chunks that fit the free device memory.  Each chunk's sweep is recorded once
  * into a CUDA graph and replayed as one graph launch (pw_batch_set_options).
- * The sweep's tile variant (256-thread CTAs with 64 x 64 GEMM tiles, or
- * 512-thread CTAs with 128 x 64 tiles) is chosen per N_G by timing the first
- * interface steps of the group's first chunk with each variant (CUDA events),
+ * The sweep variant (pw_set_sweep_variant) is chosen per N_G by timing the
+ * first interface steps of the group's first chunk with each variant (CUDA events),
  * and kept for the batch's later calls.  A threshold point gets T = NaN and the
  * call returns PW_ETHRESH after finishing the others; PW_ESINGULAR as for
  * pw_transmission.  Synchronises the stream. */
@@ -290,8 +298,8 @@ pw_status pw_transmission_batch(pw_batch *b, const double *E, const double *kpar
                                 int *nopen_dev, double *err_dev);
 
 /* Options of a batch: use_graph (1 = record and replay each chunk's sweep as a
- * CUDA graph, 0 = launch it directly), variant (-1 = autotune per N_G, 0 or 1 =
- * that tile variant for every size). */
+ * CUDA graph, 0 = launch it directly), variant (-1 = autotune per N_G, else a
+ * sweep variant as for pw_set_sweep_variant, for every size). */
 pw_status pw_batch_set_options(pw_batch *b, int use_graph, int variant);
 
 /* Stage times of the last pw_transmission_batch, out[8] = {slice-mode ms,
@@ -302,6 +310,17 @@ pw_status pw_batch_get_stats(const pw_batch *b, double *out, int *ng, int *varia
                              int *n_sizes);
 
 void pw_batch_destroy(pw_batch *b);
+
+/* Self-test of the tensor-core path used by the FP32 sweep: one 128 x 64
+ * tile product with K = 32 on the fifth-generation tensor cores (tcgen05,
+ * TF32 inputs, FP32 accumulation in tensor memory), compared on the host with
+ * an FP64 product of the same FP32 inputs.  Writes the relative error
+ * max|C - C_ref| / max|C_ref| of a single TF32 product (about 1e-3) and of
+ * the three-product split A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32 level,
+ * about 1e-6).  Runs on the current device and synchronises it; returns
+ * PW_ETIMEOUT if the tensor core did not signal completion within its bounded
+ * wait.  The paper has no counterpart; this is a deployment check. */
+pw_status pw_selftest_tensor_core(double *rel_err_tf32, double *rel_err_split);
 
 #ifdef __cplusplus
 }

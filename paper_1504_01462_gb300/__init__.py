@@ -33,7 +33,8 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_slice_smatrix", "pw_compose", "pw_transmission", "pw_set_profiling",
            "pw_get_profile", "pw_compose_noalloc", "pw_grad", "pw_setup_batch",
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
-           "pw_batch_destroy", "pw_get_error_detail"]
+           "pw_batch_destroy", "pw_get_error_detail", "pw_selftest_tensor_core",
+           "pw_set_sweep_variant"]
 
 
 class PwError(RuntimeError):
@@ -95,6 +96,8 @@ def _load():
     lib.pw_batch_get_stats.argtypes = [_vp, _dp, _ip, _ip, ctypes.c_int, _ip]
     lib.pw_batch_destroy.argtypes = [_vp]
     lib.pw_get_error_detail.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
+    lib.pw_selftest_tensor_core.argtypes = [_dp, _dp]
+    lib.pw_set_sweep_variant.argtypes = [_vp, ctypes.c_int]
     lib.pw_batch_destroy.restype = None
     return lib
 
@@ -205,6 +208,15 @@ def _instance_geometry(inst, refine_iters=0):
                 refine_iters=refine_iters,
                 well_shift_rate=getattr(inst, "gap_rate_wells", None),
                 lead_shift_rate=getattr(inst, "gap_rate_leads", None))
+
+
+def selftest_tensor_core():
+    """(relative error of one TF32 tile product, of the three-product split)
+    from the library's tcgen05 self-test on the current device."""
+    a = np.zeros(1)
+    b = np.zeros(1)
+    _check_status(_lib.pw_selftest_tensor_core(_as_dp(a), _as_dp(b)), "pw_selftest_tensor_core")
+    return float(a[0]), float(b[0])
 
 
 def _check_status(st, where):
@@ -324,6 +336,11 @@ class Context:
             return float(sumT[0]), dV0[:nw], float(dgap[0])
         return float(sumT[0]), dV0[:nw]
 
+    def set_sweep_variant(self, variant):
+        """Sweep launch variant: bit 0 = 512-thread SIMT tiles, bit 1 = [W|Y]
+        on the tcgen05 tensor cores (mixed form only)."""
+        self._check(_lib.pw_set_sweep_variant(self._h, int(variant)), "pw_set_sweep_variant")
+
     def set_profiling(self, on=True):
         self._check(_lib.pw_set_profiling(self._h, int(bool(on))), "pw_set_profiling")
 
@@ -422,4 +439,4 @@ class Batch:
 
 
 __all__ = ["Context", "Batch", "PwError", "FP64", "MIXED_FP32", "EXPORTS", "LIB_PATH", "lib",
-           "compose_noalloc"]
+           "compose_noalloc", "selftest_tensor_core"]

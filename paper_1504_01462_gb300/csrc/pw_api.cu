@@ -37,6 +37,7 @@ struct pw_ctx {
   char err_detail[160] = {0};      // first failing runtime call (pw_get_error_detail)
   int precision = PW_FP64;
   int refine_iters = 0;            // FP64 refinement passes of the mixed form
+  int sweep_variant = 0;           // launch variant of the sweep (pw_set_sweep_variant)
   int n = 0, N = 0, nq = 0;        // basis size, slices, slices incl. electrodes
   int Dm = 0, Dn = 0, tsz = 0;     // Fourier-table index ranges
   double b1[2], b2[2], area = 0.0;
@@ -539,6 +540,12 @@ void pw_destroy(pw_ctx *ctx) {
   delete ctx;
 }
 
+pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant) {
+  if (!ctx || variant < 0 || variant >= pw::sweep_variants(ctx->precision)) return PW_EINVAL;
+  ctx->sweep_variant = variant;
+  return PW_OK;
+}
+
 pw_status pw_set_profiling(pw_ctx *ctx, int enable) {
   if (!ctx) return PW_EINVAL;
   ctx->profiling = enable != 0;
@@ -769,12 +776,12 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.PIVst = refine ? (int *)ctx->PIVst.p : nullptr;
       a.KV = ctx->KV.p;
       a.mirror = 0;
-      CK(pw::prepare_sweep_batched(n, ctx->precision, 0));
+      CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
       Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n));
       for (int p = 0; p <= N; ++p) {
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
-        CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream, w0, w1));
+        CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream, w0, w1, ctx->sweep_variant));
         if (w0) ctx->recs.push_back({w0, w1, 4, 1});
         SYNC_CHECK();
       }

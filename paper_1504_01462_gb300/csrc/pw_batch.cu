@@ -264,7 +264,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     const int steps = std::min(maxN, 3) + 1;
     float best = 0.f;
     BCK(cudaEventRecord(ev[3], s));
-    for (int cand = 0; cand < 2; ++cand) {
+    for (int cand = 0; cand < pw::sweep_variants(b->precision); ++cand) {
       BCK(pw::prepare_sweep_batched(n, b->precision, cand));
       BCK(cudaMemsetAsync(b->status.p, 0, m * sizeof(int), s));
       BCK(cudaEventRecord(ev[6], s));
@@ -396,7 +396,7 @@ pw_status pw_setup_batch(int n_inst, const pw_setup_desc *descs, void *cuda_stre
 }
 
 pw_status pw_batch_set_options(pw_batch *b, int use_graph, int variant) {
-  if (!b || variant < -1 || variant > 1) return PW_EINVAL;
+  if (!b || variant < -1 || variant >= pw::sweep_variants(b->precision)) return PW_EINVAL;
   b->use_graph = use_graph != 0;
   b->force_variant = variant;
   return PW_OK;

@@ -168,8 +168,10 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s,
                      bool double_float = false);
 // One interface step of the left-to-right sweep for every point of a batch,
-// as a sequence of launches over (tiles x points).  variant 0: 256-thread
-// CTAs with 64 x 64 GEMM tiles; 1: 512-thread CTAs with 128 x 64 tiles.
+// as a sequence of launches over (tiles x points).  variant bit 0: 512-thread
+// CTAs with 128 x 64 GEMM tiles (else 256 threads, 64 x 64); bit 1 (FP32
+// only): the [W|Y] product on the tcgen05 tensor cores (TF32 hi/lo split).
+// sweep_variants: how many variants a precision has (0 .. count-1).
 // wy0, wy1: optional events recorded around the [W|Y] GEMM launch.
 // prepare_sweep_batched sets the kernels' shared-memory limits for n; call it
 // before the first step of a size (and outside a stream capture).
@@ -177,6 +179,7 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant);
 cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
                                  cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr, int variant = 0);
 int sweep_batched_launches(int n);
+int sweep_variants(int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p, u_p and the LU factors:
 // between min_iters and max_iters passes, stopping once every point's
 // estimated remaining error of a_{N+1} (c_i^2 / c_{i-1} from the relative

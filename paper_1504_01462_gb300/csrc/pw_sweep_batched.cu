@@ -18,6 +18,7 @@
 
 #include "pw_cta.cuh"
 #include "pw_internal.h"
+#include "pw_tc.cuh"
 
 namespace pw {
 
@@ -146,6 +147,90 @@ __global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
         else M[i + (size_t)j * n] = csub(acc, pqb<T>(O, n, i, j - n, v, T(-1), tr));
       },
       gsm, blockIdx.x, gridDim.x);
+}
+
+// The GEMM phases of the FP32 sweep on the fifth-generation tensor cores
+// (tc::cgemm_tile: TF32 hi/lo split, FP32 accumulation in tensor memory).
+// Grid (64-row x 128-column output tiles, points), CG_THREADS threads.
+size_t wy_tc_smem_bytes(int n) { return tc::cg_smem_bytes() + 2 * (size_t)n * sizeof(cc); }
+
+// [W | Y] = [P | -Q] + [-R Q | R P]
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const PointDesc d = a.pts[pt];
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int tiles_m = (n + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), c0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const zc *O = overlap_of(a, d, p);
+  const bool tr = a.mirror != 0;
+  const cc *R = reinterpret_cast<const cc *>(a.R) + (size_t)pt * n * n;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  cc *skinv = reinterpret_cast<cc *>(smraw + tc::cg_smem_bytes());
+  cc *skr = skinv + n;
+  const KVb<float> g = kv_of<float>(a, pt);
+  for (int i = threadIdx.x; i < n; i += tc::CG_THREADS) {
+    skinv[i] = g.kinvL[i];
+    skr[i] = g.kR[i];
+  }
+  __syncthreads();
+  const KVb<float> v{skinv, skr, nullptr};
+  const bool ok = tc::cgemm_tile(
+      n, 2 * n, n, r0, c0, [=](int i, int l) { return R[i + (size_t)l * n]; },
+      [=](int l, int j) { return j < n ? pqb<float>(O, n, l, j, v, -1.f, tr) : pqb<float>(O, n, l, j - n, v, 1.f, tr); },
+      [=](int i, int j, cc acc) {
+        if (j < n) M[i + (size_t)j * n] = csub(pqb<float>(O, n, i, j, v, 1.f, tr), acc);
+        else M[i + (size_t)j * n] = csub(acc, pqb<float>(O, n, i, j - n, v, -1.f, tr));
+      },
+      smraw);
+  if (!ok && threadIdx.x == 0) a.status[pt] = 2;
+}
+
+// trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb)
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j0) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int nb = min(Tile<float, 256>::NB, n - j0), c0 = j0 + nb;
+  const int m = n - c0, ncol = ncols - c0;
+  const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  if (q0 >= ncol) return;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  const bool ok = tc::cgemm_tile(
+      m, ncol, nb, r0, q0, [=](int i, int l) { return M[c0 + i + (size_t)(j0 + l) * n]; },
+      [=](int l, int j) { return M[j0 + l + (size_t)(c0 + j) * n]; },
+      [=](int i, int j, cc acc) {
+        cc &x = M[c0 + i + (size_t)(c0 + j) * n];
+        x = csub(x, acc);
+      },
+      smraw);
+  if (!ok && threadIdx.x == 0) a.status[pt] = 2;
+}
+
+// back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt) || j0 <= 0) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int nb = min(Tile<float, 256>::NB, n - j0);
+  const int m = j0, ncol = ncols - n;
+  const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  if (q0 >= ncol) return;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  const bool ok = tc::cgemm_tile(
+      m, ncol, nb, r0, q0, [=](int i, int l) { return M[i + (size_t)(j0 + l) * n]; },
+      [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
+      [=](int i, int j, cc acc) {
+        cc &x = M[i + (size_t)(n + j) * n];
+        x = csub(x, acc);
+      },
+      smraw);
+  if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
 template <typename T, int BT>
@@ -292,7 +377,7 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
 
 template <typename T, int BT>
 static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
-                              cudaEvent_t wy1) {
+                              cudaEvent_t wy1, bool tensor_core) {
   SweepArgs a = a0;
   a.p = p;
   const int n = a.n, ncols = 2 * n + a.nc;
@@ -307,18 +392,34 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   if (p > 0) {
     const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
     if (wy0) cudaEventRecord(wy0, s);
-    kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
+    if (std::is_same<T, float>::value && tensor_core)
+      kb_wy_tc<<<dim3(tiles(n, 2 * n, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS, wy_tc_smem_bytes(n), s>>>(
+          a, p);
+    else
+      kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
     if (wy1) cudaEventRecord(wy1, s);
   }
   for (int j0 = 0; j0 < n; j0 += NB) {
     kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0);
     const int c0 = j0 + min(NB, n - j0);
-    if (c0 < n) kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    if (c0 < n) {
+      if (std::is_same<T, float>::value && tensor_core)
+        kb_trail_tc<<<dim3(tiles(n - c0, ncols - c0, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS,
+                      tc::cg_smem_bytes(), s>>>(a, j0);
+      else
+        kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    }
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
   for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
     kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
-    if (j0 > 0) kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    if (j0 > 0) {
+      if (std::is_same<T, float>::value && tensor_core)
+        kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS,
+                      tc::cg_smem_bytes(), s>>>(a, j0);
+      else
+        kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    }
   }
   kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p);
   return cudaGetLastError();
@@ -351,18 +452,28 @@ static cudaError_t sweep_prepare(int n) {
 
 cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
   if (precision == PW_FP64)
-    return variant ? sweep_prepare<double, 512>(n) : sweep_prepare<double, 256>(n);
-  return variant ? sweep_prepare<float, 512>(n) : sweep_prepare<float, 256>(n);
+    return (variant & 1) ? sweep_prepare<double, 512>(n) : sweep_prepare<double, 256>(n);
+  cudaError_t e = (variant & 1) ? sweep_prepare<float, 512>(n) : sweep_prepare<float, 256>(n);
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_wy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wy_tc_smem_bytes(n));
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_trail_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes());
+  return e;
 }
 
 cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
                                  cudaEvent_t wy0, cudaEvent_t wy1, int variant) {
+  const bool tcore = (variant & 2) != 0;
   if (precision == PW_FP64)
-    return variant ? sweep_step<double, 512>(a, npts, p, s, wy0, wy1)
-                   : sweep_step<double, 256>(a, npts, p, s, wy0, wy1);
-  return variant ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1)
-                 : sweep_step<float, 256>(a, npts, p, s, wy0, wy1);
+    return (variant & 1) ? sweep_step<double, 512>(a, npts, p, s, wy0, wy1, false)
+                         : sweep_step<double, 256>(a, npts, p, s, wy0, wy1, false);
+  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore)
+                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore);
 }
+
+int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 4; }
 
 int sweep_batched_launches(int n) {
   const int NB = Tile<float, 256>::NB;

@@ -1,0 +1,266 @@
+// Fifth-generation tensor-core building blocks (sm_100a / sm_103a): tcgen05
+// MMA with operands in shared memory and the accumulator in tensor memory
+// (TMEM), completion through an mbarrier, results read back with tcgen05.ld.
+//
+// Operand layout: "K-major, no swizzle".  A tile of R rows by K elements is a
+// grid of core matrices of 8 rows x 16 bytes (8 rows x 4 FP32/TF32 values),
+// each stored as 128 contiguous bytes (row r of the core matrix at 16 r).
+// The shared-memory matrix descriptor gives the byte distance between core
+// matrices that are adjacent along K (leading byte offset, LBO) and along the
+// rows (stride byte offset, SBO).  Here LBO = 128 (the two K-chunks of one MMA
+// step are adjacent) and SBO = 256, so one MMA step (K = 8 for TF32) of an
+// R-row operand occupies R * 32 contiguous bytes.
+//
+// Every wait is bounded: a wait that runs out records an error and returns.
+#pragma once
+#include <stdint.h>
+
+#include "pw_cx.cuh"
+
+namespace pw {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05 format, no swizzle).
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;   // descriptor version of the tcgen05 family
+  return d;          // base offset 0, relative LBO mode, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)                      // D format: FP32
+         | (2u << 7)                    // A format: TF32
+         | (2u << 10)                   // B format: TF32
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+// TMEM allocation by one full warp; the address is written to *slot.
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] B[smem], issued by one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on the mbarrier once every MMA issued so far by this thread is done.
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false when it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_polls = 1u << 22) {
+  for (uint32_t i = 0; i < max_polls; ++i) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Generic-proxy shared-memory writes become visible to the tensor core.
+__device__ __forceinline__ void fence_smem_to_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 TMEM lanes x 16 consecutive 32-bit columns: thread t of the warp gets
+// lane (lane field of taddr) + t, columns col .. col + 15.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Round to TF32 (10 explicit mantissa bits), nearest with ties away.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (row, k) of a K-major no-swizzle operand whose MMA
+// steps of 8 K-values are stored one after another (rows x 32 bytes each).
+__host__ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int rows) {
+  const int step = k >> 3, kk = k & 7;
+  return (uint32_t)step * (uint32_t)rows * 32u + (uint32_t)(row >> 3) * 256u + (uint32_t)(kk >> 2) * 128u +
+         (uint32_t)(row & 7) * 16u + (uint32_t)(kk & 3) * 4u;
+}
+
+// ---------------------------------------------------------------------------
+// Complex FP32 GEMM tile on tcgen05 with FP32-level accuracy.
+//
+// The complex product C = A B is the real product of
+//   A' (rows 2r, 2r+1; inner columns 2l, 2l+1) = [[Re A, -Im A], [Im A, Re A]]
+//   B' (inner rows 2l, 2l+1; columns j)         = [Re B ; Im B],
+// so row 2r of D holds Re C(r, .) and row 2r+1 holds Im C(r, .).  Each
+// operand is split into TF32 hi + lo parts, D = A'_hi B'_hi + A'_hi B'_lo +
+// A'_lo B'_hi, accumulated in FP32 in tensor memory.  The CTA (CG_THREADS
+// threads) computes complex rows [r0, r0 + 64) x columns [c0, c0 + 128) of C
+// (m x ncol, inner k), K in stages of 8 complex values (two MMA steps of 8
+// real), double-buffered in shared memory so that the CTA stages block s+1
+// while the tensor core multiplies block s.  fa(i, l) and fb(l, j) return the
+// operands (zero outside the matrix is supplied here), fe(i, j, acc) consumes
+// each in-range result.  smem: cg_smem_bytes().  Returns false (and skips fe)
+// if the tensor core did not signal completion within the bounded waits.
+constexpr int CG_THREADS = 256;
+constexpr int CG_M = 128, CG_N = 128, CG_KC = 8;   // real rows, complex columns, complex K per stage
+constexpr int CG_AB = CG_M * 2 * CG_KC * 4;        // bytes of one A' part (hi or lo) per stage
+constexpr int CG_BB = CG_N * 2 * CG_KC * 4;        // bytes of one B' part per stage
+constexpr int CG_STAGE = 2 * CG_AB + 2 * CG_BB;
+__host__ __device__ constexpr size_t cg_smem_bytes() { return 2 * (size_t)CG_STAGE + 64; }
+
+template <class FA, class FB, class FE>
+__device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb, FE fe, unsigned char *smem) {
+  unsigned char *stage0 = smem;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * CG_STAGE);   // [2]
+  uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(slot, CG_N);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *slot;
+  const int nstage = (k + CG_KC - 1) / CG_KC;
+  bool ok = true;
+  for (int s = 0; s < nstage; ++s) {
+    const int b = s & 1;
+    unsigned char *Ahi = stage0 + b * CG_STAGE, *Alo = Ahi + CG_AB;
+    unsigned char *Bhi = Alo + CG_AB, *Blo = Bhi + CG_BB;
+    if (s >= 2) ok = mbar_wait(&mbar[b], ((s - 2) >> 1) & 1) && ok;   // buffer b is free again
+    const int l0 = s * CG_KC;
+    for (int e = tid; e < (CG_M / 2) * CG_KC; e += CG_THREADS) {
+      const int rr = e % (CG_M / 2), ll = e / (CG_M / 2);
+      const int r = r0 + rr, l = l0 + ll;
+      const cc z = (r < m && l < k) ? fa(r, l) : czero<float>();
+      const float vals[4] = {z.re, -z.im, z.im, z.re};   // (2rr, 2ll), (2rr, 2ll+1), (2rr+1, 2ll), (2rr+1, 2ll+1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float hi = to_tf32(vals[q]);
+        const uint32_t off = kmajor_offset(2 * rr + (q >> 1), 2 * ll + (q & 1), CG_M);
+        *reinterpret_cast<float *>(Ahi + off) = hi;
+        *reinterpret_cast<float *>(Alo + off) = vals[q] - hi;
+      }
+    }
+    for (int e = tid; e < CG_N * CG_KC; e += CG_THREADS) {
+      const int ll = e % CG_KC, jj = e / CG_KC;
+      const int l = l0 + ll, j = c0 + jj;
+      const cc z = (l < k && j < ncol) ? fb(l, j) : czero<float>();
+      const float vals[2] = {z.re, z.im};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float hi = to_tf32(vals[q]);
+        const uint32_t off = kmajor_offset(jj, 2 * ll + q, CG_N);
+        *reinterpret_cast<float *>(Bhi + off) = hi;
+        *reinterpret_cast<float *>(Blo + off) = vals[q] - hi;
+      }
+    }
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      constexpr uint32_t idesc = idesc_tf32(CG_M, CG_N);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t ah = smem_desc(Ahi + ks * CG_M * 32, 128, 256);
+        const uint64_t al = smem_desc(Alo + ks * CG_M * 32, 128, 256);
+        const uint64_t bh = smem_desc(Bhi + ks * CG_N * 32, 128, 256);
+        const uint64_t bl = smem_desc(Blo + ks * CG_N * 32, 128, 256);
+        mma_tf32(tmem, ah, bh, idesc, (s > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, idesc, 1u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+      }
+      mma_commit(&mbar[b]);
+    }
+  }
+  // the last commit covers every MMA of the tile
+  ok = mbar_wait(&mbar[(nstage - 1) & 1], ((nstage - 1) >> 1) & 1) && ok;
+  fence_after_sync();
+  if (ok) {
+    // warp w: TMEM lanes 32 (w % 4) .. (real rows), complex columns 64 (w / 4) .. + 64
+    const int lrow = 32 * (warp & 3) + lane;
+    const int r = r0 + (lrow >> 1), im = lrow & 1;
+    for (int cb = 0; cb < 64; cb += 16) {
+      const int cbase = 64 * (warp >> 2) + cb;
+      float vv[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cbase, vv);
+      float other[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) other[i] = __shfl_xor_sync(0xffffffffu, vv[i], 1);
+      // the real-row lane writes columns cbase .. +7, the imaginary-row lane +8 .. +15
+      cc accs[8];
+      if (im) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) accs[i] = mkc<float>(other[i + 8], vv[i + 8]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) accs[i] = mkc<float>(vv[i], other[i]);
+      }
+      const int jb = c0 + cbase + (im ? 8 : 0);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (r < m && jb + i < ncol) fe(r, jb + i, accs[i]);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, CG_N);
+  return ok;
+}
+
+}  // namespace tc
+}  // namespace pw

@@ -1,0 +1,56 @@
+"""The tcgen05 tensor-core path: one TF32 tile product and the three-product
+split against an FP64 product of the same inputs."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pw():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1504_01462_gb300 as pw
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return pw
+
+
+def test_tcgen05_tile_product(pw):
+    e1, e3 = pw.selftest_tensor_core()
+    # TF32 keeps 10 explicit mantissa bits (2^-11 relative rounding per input)
+    assert 1e-6 < e1 < 5e-3, e1
+    # hi/lo split: FP32-level products, FP32 accumulation over K = 32
+    assert e3 < 2e-6, e3
+    assert e3 < e1 / 50
+
+
+def _T(pw, inst, E, k, variant, refine_iters):
+    T = torch.zeros(len(E), dtype=torch.float64, device="cuda")
+    with pw.Context.from_instance(inst, pw.MIXED_FP32, refine_iters) as ctx:
+        ctx.set_sweep_variant(variant)
+        ctx.transmission(E, k, T)
+    torch.cuda.synchronize()
+    return T.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_sweep_with_tensor_core_products(pw, variant):
+    """The sweep with its [W|Y] products on tcgen05 (TF32 hi/lo split): the
+    unrefined sweep is FP32-accurate, the refined one meets 1e-8; the junction
+    size (N_G = 97, 60 slices) spans two M tiles, a ragged N tile and 8
+    K stages."""
+    import numpy as np
+    from oracle import pw_oracle as O
+    from synthetic import junction
+    inst = junction(ng=97, n_slices=60, n_e=4, n_k=4)
+    sel = [1, 2, 5, 6, 9, 10]
+    E, k = inst.energies[sel], inst.kpar[sel]
+    ref = O.transmission(inst, points=sel)
+    scale = np.maximum(1.0, np.abs(ref))
+    raw = _T(pw, inst, E, k, variant, -1)
+    assert np.all(np.abs(raw - ref) / scale < 1e-4), (raw, ref)
+    simt = _T(pw, inst, E, k, variant & 1, -1)
+    assert np.all(np.abs(raw - simt) / scale < 1e-4)
+    got = _T(pw, inst, E, k, variant, 4)
+    assert np.all(np.abs(got - ref) / scale < 1e-8), (got, ref)
