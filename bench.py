@@ -389,16 +389,35 @@ def main():
         wy_ms = prof["wy_ms"] / max(prof["wy_launches"], 1)
         wy_flops = n_e * 8.0 * 2.0 * n ** 3
         wy_ach = wy_flops / (wy_ms / 1e3) / 1e12 if prof["wy_launches"] else 0.0
-        wy_peak = fp32_peak if prec == pw.MIXED_FP32 else fp64_peak
-        heev_obj = {"bound": "alu", "kernel": "k_heev (FP64 Householder + QL, one launch per step)",
-                    "achieved": heev_ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": heev_ach / fp64_peak, "traffic": None,
-                    "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no measured FP64 peak)",
+        variant = args.sweep_variant if args.sweep_variant >= 0 else (2 if prec == pw.MIXED_FP32 else 0)
+        tensor = prec == pw.MIXED_FP32 and (variant & 2) != 0
+        peaks = measured_peaks()
+        # TF32 dense peak = measured bf16 x the nominal TF32/BF16 ratio (1.1 / 2.25); the hi/lo
+        # split executes three TF32 products per algorithmic product
+        tf32_peak = (peaks.get("bf16_tflops") or 1900.0) * (1.1 / 2.25)
+        wy_peak = tf32_peak / 3.0 if tensor else (fp32_peak if prec == pw.MIXED_FP32 else fp64_peak)
+        # the mixed form's eigensolver runs in double-float on the FP32 pipe: about 12 FP32
+        # instructions per real multiply-add (2 algorithmic flops) against 2 flops per FMA
+        # instruction, so its ceiling is the FP32 rate / 12 in algorithmic flops
+        heev_peak = fp32_peak / 12.0 if prec == pw.MIXED_FP32 else fp64_peak
+        heev_obj = {"bound": "alu",
+                    "kernel": ("k_heev<df> (double-float Householder + QL, one launch per step)"
+                               if prec == pw.MIXED_FP32 else
+                               "k_heev<double> (FP64 Householder + QL, one launch per step)"),
+                    "achieved": heev_ach, "peak": heev_peak, "unit": "TFLOP/s",
+                    "frac": heev_ach / heev_peak, "traffic": None,
+                    "peak_source": ("FP32 FMA rate / 12 (12 FP32 instructions per double-float multiply-add)"
+                                    if prec == pw.MIXED_FP32 else
+                                    "FP64 nominal 1.25 TFLOP/s (recipe table; no measured FP64 peak)"),
                     "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
-        wy_obj = {"bound": "alu", "kernel": f"kb_wy<{'float' if prec == pw.MIXED_FP32 else 'double'}>",
+        wy_obj = {"bound": "tensor" if tensor else "alu",
+                  "kernel": ("kb_wy_tc (tcgen05 kind::tf32, hi/lo split)" if tensor else
+                             f"kb_wy<{'float' if prec == pw.MIXED_FP32 else 'double'}>"),
                   "achieved": wy_ach, "peak": wy_peak, "unit": "TFLOP/s", "frac": wy_ach / wy_peak,
                   "traffic": None,
-                  "peak_source": ("FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz"
+                  "peak_source": ("of measured: bf16 burst x 1.1/2.25 (nominal TF32/BF16) / 3 products"
+                                  if tensor else
+                                  "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz"
                                   if prec == pw.MIXED_FP32 else "FP64 nominal 1.25 TFLOP/s"),
                   "avg_launch_ms": wy_ms, "total_ms": prof["wy_ms"]}
         dominant, other = ((heev_obj, wy_obj) if prof["modes_ms"] >= prof["wy_ms"] else (wy_obj, heev_obj))

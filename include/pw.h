@@ -246,7 +246,8 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
 pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
                              pw_c128 *Sab_dev, void *cuda_stream);
 
-/* Launch variant of the star-product sweep of pw_transmission (default 0).
+/* Launch variant of the star-product sweep of pw_transmission (default 2 for
+ * PW_MIXED_FP32, 0 for PW_FP64).
  * Bit 0: 512-thread CTAs with 128 x 64 SIMT GEMM tiles (else 256 threads with
  * 64 x 64 tiles).  Bit 1 (PW_MIXED_FP32 only): the [W|Y] product of every
  * interface on the fifth-generation tensor cores (tcgen05, TF32 operands split

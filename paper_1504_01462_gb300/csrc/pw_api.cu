@@ -403,6 +403,7 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
   ctx->precision = d->precision;
   if (d->refine_iters < -1 || d->refine_iters > 16) { delete ctx; return PW_EINVAL; }
   ctx->refine_iters = d->precision == PW_MIXED_FP32 ? (d->refine_iters == 0 ? 4 : std::max(0, d->refine_iters)) : 0;
+  ctx->sweep_variant = d->precision == PW_MIXED_FP32 ? 2 : 0;   // tensor-core GEMMs for the FP32 sweep
   if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return PW_ECUDA; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   build_basis(d->a1, d->a2, d->ecut, d->ng_exact, ctx->b1, ctx->b2, ctx->mn, ctx->G);
