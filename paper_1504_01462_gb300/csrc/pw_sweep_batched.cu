@@ -59,6 +59,13 @@ __device__ __forceinline__ cx<T> pqb(const zc *O, int n, int l, int j, const KVb
 
 // Points whose problem ended at an earlier interface (a.p > N of the point)
 // take no part in the remaining steps.
+// P_lj (sel +1) or Q_lj (sel -1) from the transposed FP32 overlaps Ot[j + l n]
+__device__ __forceinline__ cc pqt(const cc *Ot, int n, int l, int j, const KVb<float> &v, float sel) {
+  const cc o = Ot[j + (size_t)l * n];
+  const cc r = cmul(v.kR[j], v.kinvL[l]);
+  return cmul(o, mkc<float>(0.5f * (1.f + sel * r.re), 0.5f * sel * r.im));
+}
+
 __device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
   const PointDesc &d = a.pts[pt];
   return d.skip || a.status[pt] || a.p > d.N;
@@ -176,9 +183,15 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
   }
   __syncthreads();
   const KVb<float> v{skinv, skr, nullptr};
-  const bool ok = tc::cgemm_tile(
+  // B from the FP32 copy of O (transposed: element (l, j) at j + l n) when the
+  // k-set has one, else from the FP64 overlaps
+  const cc *Ot = a.O32t ? a.O32t + ((size_t)d.o_off + p) * n * n : nullptr;
+  const bool ok = tc::cgemm_tile<false>(
       n, 2 * n, n, r0, c0, [=](int i, int l) { return R[i + (size_t)l * n]; },
-      [=](int l, int j) { return j < n ? pqb<float>(O, n, l, j, v, -1.f, tr) : pqb<float>(O, n, l, j - n, v, 1.f, tr); },
+      [=](int l, int j) {
+        if (Ot && !tr) return j < n ? pqt(Ot, n, l, j, v, -1.f) : pqt(Ot, n, l, j - n, v, 1.f);
+        return j < n ? pqb<float>(O, n, l, j, v, -1.f, tr) : pqb<float>(O, n, l, j - n, v, 1.f, tr);
+      },
       [=](int i, int j, cc acc) {
         if (j < n) M[i + (size_t)j * n] = csub(pqb<float>(O, n, i, j, v, 1.f, tr), acc);
         else M[i + (size_t)j * n] = csub(acc, pqb<float>(O, n, i, j - n, v, -1.f, tr));
@@ -199,7 +212,7 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * tc::CG_N;
   if (q0 >= ncol) return;
   cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
-  const bool ok = tc::cgemm_tile(
+  const bool ok = tc::cgemm_tile<true>(
       m, ncol, nb, r0, q0, [=](int i, int l) { return M[c0 + i + (size_t)(j0 + l) * n]; },
       [=](int l, int j) { return M[j0 + l + (size_t)(c0 + j) * n]; },
       [=](int i, int j, cc acc) {
@@ -222,7 +235,7 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * tc::CG_N;
   if (q0 >= ncol) return;
   cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
-  const bool ok = tc::cgemm_tile(
+  const bool ok = tc::cgemm_tile<true>(
       m, ncol, nb, r0, q0, [=](int i, int l) { return M[i + (size_t)(j0 + l) * n]; },
       [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
       [=](int i, int j, cc acc) {

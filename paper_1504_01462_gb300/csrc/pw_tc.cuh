@@ -159,7 +159,18 @@ constexpr int CG_BB = CG_N * 2 * CG_KC * 4;        // bytes of one B' part per s
 constexpr int CG_STAGE = 2 * CG_AB + 2 * CG_BB;
 __host__ __device__ constexpr size_t cg_smem_bytes() { return 2 * (size_t)CG_STAGE + 64; }
 
-template <class FA, class FB, class FE>
+// Four values as TF32 hi parts and FP32 remainders, one 16-byte store each.
+__device__ __forceinline__ void store_split(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, float a,
+                                            float b, float c, float d) {
+  const float4 h = make_float4(to_tf32(a), to_tf32(b), to_tf32(c), to_tf32(d));
+  *reinterpret_cast<float4 *>(hi_base + off) = h;
+  *reinterpret_cast<float4 *>(lo_base + off) = make_float4(a - h.x, b - h.y, c - h.z, d - h.w);
+}
+
+// B_RUNS: fb(l .. l+3, j) lie contiguously in memory for fixed j (one thread
+// reads the run); otherwise consecutive j are contiguous for fixed l (one
+// thread per column, consecutive threads on consecutive columns).
+template <bool B_RUNS, class FA, class FB, class FE>
 __device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb, FE fe, unsigned char *smem) {
   unsigned char *stage0 = smem;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * CG_STAGE);   // [2]
@@ -182,30 +193,34 @@ __device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb,
     unsigned char *Bhi = Alo + CG_AB, *Blo = Bhi + CG_BB;
     if (s >= 2) ok = mbar_wait(&mbar[b], ((s - 2) >> 1) & 1) && ok;   // buffer b is free again
     const int l0 = s * CG_KC;
-    for (int e = tid; e < (CG_M / 2) * CG_KC; e += CG_THREADS) {
-      const int rr = e % (CG_M / 2), ll = e / (CG_M / 2);
-      const int r = r0 + rr, l = l0 + ll;
-      const cc z = (r < m && l < k) ? fa(r, l) : czero<float>();
-      const float vals[4] = {z.re, -z.im, z.im, z.re};   // (2rr, 2ll), (2rr, 2ll+1), (2rr+1, 2ll), (2rr+1, 2ll+1)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float hi = to_tf32(vals[q]);
-        const uint32_t off = kmajor_offset(2 * rr + (q >> 1), 2 * ll + (q & 1), CG_M);
-        *reinterpret_cast<float *>(Ahi + off) = hi;
-        *reinterpret_cast<float *>(Alo + off) = vals[q] - hi;
-      }
+    // A': one task = complex (r, l), (r, l+1) -> rows 2r, 2r+1, one 16-byte chunk each
+    for (int e = tid; e < (CG_M / 2) * (CG_KC / 2); e += CG_THREADS) {
+      const int rr = e % (CG_M / 2), lp = e / (CG_M / 2);
+      const int r = r0 + rr, l = l0 + 2 * lp;
+      const cc z0 = (r < m && l < k) ? fa(r, l) : czero<float>();
+      const cc z1 = (r < m && l + 1 < k) ? fa(r, l + 1) : czero<float>();
+      store_split(Ahi, Alo, kmajor_offset(2 * rr, 4 * lp, CG_M), z0.re, -z0.im, z1.re, -z1.im);
+      store_split(Ahi, Alo, kmajor_offset(2 * rr + 1, 4 * lp, CG_M), z0.im, z0.re, z1.im, z1.re);
     }
-    for (int e = tid; e < CG_N * CG_KC; e += CG_THREADS) {
-      const int ll = e % CG_KC, jj = e / CG_KC;
-      const int l = l0 + ll, j = c0 + jj;
-      const cc z = (l < k && j < ncol) ? fb(l, j) : czero<float>();
-      const float vals[2] = {z.re, z.im};
+    if (B_RUNS) {
+      // B': one task = column j, complex l .. l+3 (a contiguous run in the source)
+      for (int e = tid; e < CG_N * 2; e += CG_THREADS) {
+        const int jj = e % CG_N, half = e / CG_N;
+        const int j = c0 + jj, l = l0 + 4 * half;
+        cc z[4];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float hi = to_tf32(vals[q]);
-        const uint32_t off = kmajor_offset(jj, 2 * ll + q, CG_N);
-        *reinterpret_cast<float *>(Bhi + off) = hi;
-        *reinterpret_cast<float *>(Blo + off) = vals[q] - hi;
+        for (int q = 0; q < 4; ++q) z[q] = (l + q < k && j < ncol) ? fb(l + q, j) : czero<float>();
+        store_split(Bhi, Blo, kmajor_offset(jj, 8 * half, CG_N), z[0].re, z[0].im, z[1].re, z[1].im);
+        store_split(Bhi, Blo, kmajor_offset(jj, 8 * half + 4, CG_N), z[2].re, z[2].im, z[3].re, z[3].im);
+      }
+    } else {
+      // B': one task = complex (l, j), (l+1, j) -> row j, one 16-byte chunk
+      for (int e = tid; e < CG_N * (CG_KC / 2); e += CG_THREADS) {
+        const int jj = e % CG_N, lp = e / CG_N;
+        const int j = c0 + jj, l = l0 + 2 * lp;
+        const cc z0 = (l < k && j < ncol) ? fb(l, j) : czero<float>();
+        const cc z1 = (l + 1 < k && j < ncol) ? fb(l + 1, j) : czero<float>();
+        store_split(Bhi, Blo, kmajor_offset(jj, 4 * lp, CG_N), z0.re, z0.im, z1.re, z1.im);
       }
     }
     fence_smem_to_async();
