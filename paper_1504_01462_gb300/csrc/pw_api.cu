@@ -55,7 +55,7 @@ struct pw_ctx {
   std::vector<double> slot_k;      // 2 per slot
   std::vector<char> slot_valid;
   zc *d_HU = nullptr, *d_V = nullptr, *d_O = nullptr;
-  cc *d_O32 = nullptr;             // mixed form: FP32 transposed copies of the overlaps, same slots
+  cc *d_O32 = nullptr;             // mixed form: FP32 copies of the overlaps, same slots
   double *d_En = nullptr;
   int *d_eigstat = nullptr;       // Jacobi sweeps per matrix
   std::vector<std::vector<double>> EL, ER;   // electrode eigenvalues per slot (host)
@@ -281,8 +281,8 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
   pw::launch_overlaps(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq,
                       s1 - s0, ctx->stream, ctx->precision == PW_MIXED_FP32);
   if (ctx->d_O32)
-    pw::launch_overlaps_fp32t(ctx->d_O + (size_t)s0 * (nq - 1) * nn, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn, n,
-                              (s1 - s0) * (nq - 1), ctx->stream);
+    pw::launch_overlaps_fp32(ctx->d_O + (size_t)s0 * (nq - 1) * nn, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn, n,
+                             (s1 - s0) * (nq - 1), ctx->stream);
   CK(cudaGetLastError());
   SYNC_CHECK();
   st2.done();
@@ -766,7 +766,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.pts = (const PointDesc *)ctx->pts.p;
       a.En = ctx->d_En;
       a.O = ctx->d_O;
-      a.O32t = ctx->d_O32;
+      a.O32 = ctx->d_O32;
       a.dz = ctx->d_dz;
       a.R = ctx->R.p;
       a.M = ctx->M.p;
@@ -800,6 +800,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.pts = a.pts;
         r.En = a.En;
         r.O = a.O;
+        r.O32 = a.O32;
         r.dz = a.dz;
         r.Zst = (const cc *)ctx->Zst.p;
         r.Ust = (cc *)ctx->Ust.p;

@@ -176,7 +176,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   for (int j = 0; j < m; ++j)
     pw::launch_overlaps(HU + mb[j] * nn, O + ob[j] * nn, n, b->view[ids[j]].N + 2, 1, s,
                         b->precision == PW_MIXED_FP32);
-  if (mixed) pw::launch_overlaps_fp32t(O, (cc *)b->O32.p, n, (int)nov, s);
+  if (mixed) pw::launch_overlaps_fp32(O, (cc *)b->O32.p, n, (int)nov, s);
   BCK(cudaGetLastError());
   BCK(cudaEventRecord(ev[2], s));
   // electrode eigenvalues -> open channels
@@ -239,7 +239,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   a.pts = (const PointDesc *)b->pts.p;
   a.En = En;
   a.O = O;
-  a.O32t = mixed ? (const cc *)b->O32.p : nullptr;
+  a.O32 = mixed ? (const cc *)b->O32.p : nullptr;
   a.dz = (const double *)b->dz.p;
   a.R = b->R.p;
   a.M = b->M.p;
@@ -327,6 +327,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     r.pts = a.pts;
     r.En = En;
     r.O = O;
+    r.O32 = a.O32;
     r.dz = a.dz;
     r.Zst = (const cc *)b->Zst.p;
     r.Ust = (cc *)b->Ust.p;

@@ -70,8 +70,8 @@ __device__ __forceinline__ zc pq64(const zc *O, int n, int l, int j, const KV &v
 
 // The same in FP32 (the backward and forward passes apply the FP32
 // preconditioner; only the residual needs FP64)
-__device__ __forceinline__ cc pq32(const zc *O, int n, int l, int j, const KV &v, float sel) {
-  const cc o = ccast<float>(O[l + (size_t)j * n]);
+__device__ __forceinline__ cc pq32(const zc *O, const cc *O32, int n, int l, int j, const KV &v, float sel) {
+  const cc o = O32 ? O32[l + (size_t)j * n] : ccast<float>(O[l + (size_t)j * n]);
   const cc r = cmul(ccast<float>(v.kR[j]), ccast<float>(v.kinvL[l]));
   return cmul(o, mkc<float>(0.5f * (1.0f + sel * r.re), 0.5f * sel * r.im));
 }
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
   KV v = carve_kv(smraw, skinny_smem_elems<float>() * sizeof(cc), n);
   load_kv(a, d, p, v);
   const zc *O = overlap(a, d, p);
+  const cc *O32 = a.O32 ? a.O32 + ((size_t)d.o_off + p) * (size_t)n * n : nullptr;
   const cc *Z = a.Zst + ((size_t)d.st_off + p) * n * n;
   const cc *U = a.Ust + ((size_t)d.st_off + p) * n * nc;
   zc *carry = a.carry + (size_t)pt * n * nc;       // db_q in, db_p out
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int
   const zc *G = a.Gr + iblk(a, d, p);
   cta_gemm_skinny<float>(
       n, nc, 2 * n,
-      [=](int i, int l) { return l < n ? pq32(O, n, i, l, vc, -1.0f) : pq32(O, n, i, l - n, vc, 1.0f); },
+      [=](int i, int l) { return l < n ? pq32(O, O32, n, i, l, vc, -1.0f) : pq32(O, O32, n, i, l - n, vc, 1.0f); },
       [=](int l, int j) { return tmp[l + (size_t)j * 2 * n]; },
       [=](int i, int j, cc acc) {
         zc db = ccast<double>(acc);

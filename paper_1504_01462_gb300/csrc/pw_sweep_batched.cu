@@ -48,24 +48,19 @@ __device__ __forceinline__ KVb<T> kv_of(const SweepArgs &a, int pt) {
   return KVb<T>{base, base + a.n, base + 2 * a.n};
 }
 
-// P_lj (sel +1) or Q_lj (sel -1); `tr` reads the overlap transposed
+// P_lj (sel +1) or Q_lj (sel -1); `tr` reads the overlap transposed.  The FP32
+// kernels read the FP32 copy O32 of the overlaps when there is one.
 template <typename T>
-__device__ __forceinline__ cx<T> pqb(const zc *O, int n, int l, int j, const KVb<T> &v, T sel,
+__device__ __forceinline__ cx<T> pqb(const zc *O, const cc *O32, int n, int l, int j, const KVb<T> &v, T sel,
                                      bool tr = false) {
-  const cx<T> o = ccast<T>(tr ? O[j + (size_t)l * n] : O[l + (size_t)j * n]);
+  const size_t e = tr ? j + (size_t)l * n : l + (size_t)j * n;
+  const cx<T> o = (std::is_same<T, float>::value && O32) ? ccast<T>(O32[e]) : ccast<T>(O[e]);
   const cx<T> r = cmul(v.kR[j], v.kinvL[l]);
   return cmul(o, mkc<T>(T(0.5) * (T(1) + sel * r.re), T(0.5) * sel * r.im));
 }
 
 // Points whose problem ended at an earlier interface (a.p > N of the point)
 // take no part in the remaining steps.
-// P_lj (sel +1) or Q_lj (sel -1) from the transposed FP32 overlaps Ot[j + l n]
-__device__ __forceinline__ cc pqt(const cc *Ot, int n, int l, int j, const KVb<float> &v, float sel) {
-  const cc o = Ot[j + (size_t)l * n];
-  const cc r = cmul(v.kR[j], v.kinvL[l]);
-  return cmul(o, mkc<float>(0.5f * (1.f + sel * r.re), 0.5f * sel * r.im));
-}
-
 __device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
   const PointDesc &d = a.pts[pt];
   return d.skip || a.status[pt] || a.p > d.N;
@@ -84,6 +79,9 @@ __device__ __forceinline__ const double *energies_of(const SweepArgs &a, const P
 }
 __device__ __forceinline__ const zc *overlap_of(const SweepArgs &a, const PointDesc &d, int p) {
   return a.O + ((size_t)d.o_off + (a.mirror ? d.N - p : p)) * a.n * a.n;
+}
+__device__ __forceinline__ const cc *overlap32_of(const SweepArgs &a, const PointDesc &d, int p) {
+  return a.O32 ? a.O32 + ((size_t)d.o_off + (a.mirror ? d.N - p : p)) * a.n * a.n : nullptr;
 }
 
 }  // namespace
@@ -109,14 +107,15 @@ __global__ void __launch_bounds__(VT) kb_vectors(SweepArgs a, int p) {
   __syncthreads();
   // S(0,0) = I: R = 0, Tacc = the open left columns of I  ->  W = P, Y = -Q
   const zc *O = overlap_of(a, d, 0);
+  const cc *O32 = overlap32_of(a, d, 0);
   const bool tr = a.mirror != 0;
   const KVb<T> v = kv_of<T>(a, pt);
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   for (size_t e = threadIdx.x; e < (size_t)n * ncols; e += VT) {
     const int i = e % n, j = e / n;
     cx<T> val;
-    if (j < n) val = pqb<T>(O, n, i, j, v, T(1), tr);
-    else if (j < 2 * n) { val = pqb<T>(O, n, i, j - n, v, T(-1), tr); val.re = -val.re; val.im = -val.im; }
+    if (j < n) val = pqb<T>(O, O32, n, i, j, v, T(1), tr);
+    else if (j < 2 * n) { val = pqb<T>(O, O32, n, i, j - n, v, T(-1), tr); val.re = -val.re; val.im = -val.im; }
     else { const int c = j - 2 * n; val = mkc<T>((i == c && c < d.nL) ? T(1) : T(0), T(0)); }
     M[e] = val;
   }
@@ -130,6 +129,7 @@ __global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
   const PointDesc d = a.pts[pt];
   const int n = a.n, ncols = 2 * n + a.nc;
   const zc *O = overlap_of(a, d, p);
+  const cc *O32 = overlap32_of(a, d, p);
   const bool tr = a.mirror != 0;
   const cx<T> *R = reinterpret_cast<const cx<T> *>(a.R) + (size_t)pt * n * n;
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
@@ -147,11 +147,11 @@ __global__ void __launch_bounds__(BT) kb_wy(SweepArgs a, int p) {
   cta_gemm_t<T, Tile<T, BT>::BM, Tile<T, BT>::BN, Tile<T, BT>::BK, 4, BT>(
       n, 2 * n, n, [=](int i, int l) { return R[i + (size_t)l * n]; },
       [=](int l, int j) {
-        return j < n ? pqb<T>(O, n, l, j, v, T(-1), tr) : pqb<T>(O, n, l, j - n, v, T(1), tr);
+        return j < n ? pqb<T>(O, O32, n, l, j, v, T(-1), tr) : pqb<T>(O, O32, n, l, j - n, v, T(1), tr);
       },
       [=](int i, int j, cx<T> acc) {
-        if (j < n) M[i + (size_t)j * n] = csub(pqb<T>(O, n, i, j, v, T(1), tr), acc);
-        else M[i + (size_t)j * n] = csub(acc, pqb<T>(O, n, i, j - n, v, T(-1), tr));
+        if (j < n) M[i + (size_t)j * n] = csub(pqb<T>(O, O32, n, i, j, v, T(1), tr), acc);
+        else M[i + (size_t)j * n] = csub(acc, pqb<T>(O, O32, n, i, j - n, v, T(-1), tr));
       },
       gsm, blockIdx.x, gridDim.x);
 }
@@ -183,18 +183,16 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
   }
   __syncthreads();
   const KVb<float> v{skinv, skr, nullptr};
-  // B from the FP32 copy of O (transposed: element (l, j) at j + l n) when the
-  // k-set has one, else from the FP64 overlaps
-  const cc *Ot = a.O32t ? a.O32t + ((size_t)d.o_off + p) * n * n : nullptr;
-  const bool ok = tc::cgemm_tile<false>(
+  const cc *O32 = overlap32_of(a, d, p);
+  // B(l .. l+3, j) is a contiguous run of O for fixed j (column-major)
+  const bool ok = tc::cgemm_tile<true>(
       n, 2 * n, n, r0, c0, [=](int i, int l) { return R[i + (size_t)l * n]; },
       [=](int l, int j) {
-        if (Ot && !tr) return j < n ? pqt(Ot, n, l, j, v, -1.f) : pqt(Ot, n, l, j - n, v, 1.f);
-        return j < n ? pqb<float>(O, n, l, j, v, -1.f, tr) : pqb<float>(O, n, l, j - n, v, 1.f, tr);
+        return j < n ? pqb<float>(O, O32, n, l, j, v, -1.f, tr) : pqb<float>(O, O32, n, l, j - n, v, 1.f, tr);
       },
       [=](int i, int j, cc acc) {
-        if (j < n) M[i + (size_t)j * n] = csub(pqb<float>(O, n, i, j, v, 1.f, tr), acc);
-        else M[i + (size_t)j * n] = csub(acc, pqb<float>(O, n, i, j - n, v, -1.f, tr));
+        if (j < n) M[i + (size_t)j * n] = csub(pqb<float>(O, O32, n, i, j, v, 1.f, tr), acc);
+        else M[i + (size_t)j * n] = csub(acc, pqb<float>(O, O32, n, i, j - n, v, -1.f, tr));
       },
       smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
