@@ -68,6 +68,7 @@ struct SweepArgs {
   const double *En;      // kset slots: [kset][q][n], q = 0..N+1
   const zc *O;           // kset slots: [kset][p][n*n], p = 0..N
   const cc *O32;         // null, or FP32 copies of O (same layout and slots), read by the FP32 kernels
+  const cc *O32t;        // null, or the same transposed (element (l, j) at j + l n), for the tensor-core B
   const double *dz;      // N+2: dz[0] = 0 (left lead), dz[1..N], dz[N+1] = 0
   void *R;               // per point n*n  (cx<T>)
   void *M;               // per point n*(2n+nc)  (cx<T>)
@@ -165,8 +166,9 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
 // the same size; status: Jacobi sweeps per matrix (negative: not converged)
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s,
                 bool double_float = false);
-// FP32 copies of `count` n x n overlaps
-void launch_overlaps_fp32(const zc *O, cc *O32, int n, int count, cudaStream_t s);
+// FP32 copies of `count` n x n overlaps, plain and (when O32t is not null)
+// transposed: O32t[j + l n] = O[l + j n]
+void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, int n, int count, cudaStream_t s);
 // O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots;
 // double_float: accumulate in double-float (48-bit) on the FP32 pipe
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s,

@@ -760,10 +760,37 @@ __global__ void __launch_bounds__(NT) k_o32(const zc *O, cc *O32, size_t count) 
     O32[e] = ccast<float>(O[e]);
 }
 
-void launch_overlaps_fp32(const zc *O, cc *O32, int n, int count, cudaStream_t s) {
-  const size_t total = (size_t)count * n * n;
+// FP32 transposed copies (32 x 32 tiles through shared memory, coalesced on
+// both sides); grid (tiles, count).
+__global__ void __launch_bounds__(NT) k_o32t(const zc *O, cc *Ot, int n) {
+  __shared__ cc tile[32][33];
+  const size_t nn = (size_t)n * n;
+  const zc *src = O + (size_t)blockIdx.y * nn;
+  cc *dst = Ot + (size_t)blockIdx.y * nn;
+  const int tn = (n + 31) / 32;
+  const int i0 = (blockIdx.x % tn) * 32, j0 = (blockIdx.x / tn) * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8
+  for (int r = ty; r < 32; r += NT / 32) {
+    const int i = i0 + tx, j = j0 + r;
+    if (i < n && j < n) tile[r][tx] = ccast<float>(src[i + (size_t)j * n]);   // (i, j) -> tile[j - j0][i - i0]
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += NT / 32) {
+    const int j = j0 + tx, i = i0 + r;
+    if (i < n && j < n) dst[j + (size_t)i * n] = tile[tx][r];   // Ot[j + i n] = O[i + j n]
+  }
+}
+
+void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, int n, int count, cudaStream_t s) {
+  const size_t nn = (size_t)n * n, total = (size_t)count * nn;
   const size_t blocks = (total + NT - 1) / NT;
   k_o32<<<(unsigned)(blocks < 4096 ? blocks : 4096), NT, 0, s>>>(O, O32, total);
+  if (!O32t) return;
+  const int tn = (n + 31) / 32;
+  for (int c0 = 0; c0 < count; c0 += 65535) {   // grid.y limit
+    const int c = count - c0 < 65535 ? count - c0 : 65535;
+    k_o32t<<<dim3(tn * tn, c), NT, 0, s>>>(O + c0 * nn, O32t + c0 * nn, n);
+  }
 }
 
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s, bool double_float) {

@@ -31,8 +31,9 @@ namespace pw {
 
 namespace {
 
-struct KV {   // per-interface vectors, FP64, in shared memory
+struct KV {   // per-interface vectors in shared memory: FP64, and FP32 copies for the FP32 passes
   zc *kinvL, *kR, *eL, *eR;
+  cc *fkinvL, *fkR, *feL, *feR;
 };
 
 __device__ KV carve_kv(unsigned char *raw, size_t off, int n) {
@@ -42,6 +43,11 @@ __device__ KV carve_kv(unsigned char *raw, size_t off, int n) {
   v.kR = c + n;
   v.eL = c + 2 * n;
   v.eR = c + 3 * n;
+  cc *f = reinterpret_cast<cc *>(c + 4 * n);
+  v.fkinvL = f;
+  v.fkR = f + n;
+  v.feL = f + 2 * n;
+  v.feR = f + 3 * n;
   return v;
 }
 
@@ -53,10 +59,15 @@ __device__ void load_kv(const RefineArgs &a, const PointDesc &d, int p, KV &v) {
   for (int i = threadIdx.x; i < n; i += NT) {
     const zc kl = kz_branch(d.E, Ep[i]);
     const zc kr = kz_branch(d.E, Eq[i]);
-    v.kinvL[i] = cinv(kl);
+    const zc ki = cinv(kl), el = phase_fwd(kl, dz[p]), er = phase_fwd(kr, dz[p + 1]);
+    v.kinvL[i] = ki;
     v.kR[i] = kr;
-    v.eL[i] = phase_fwd(kl, dz[p]);
-    v.eR[i] = phase_fwd(kr, dz[p + 1]);
+    v.eL[i] = el;
+    v.eR[i] = er;
+    v.fkinvL[i] = ccast<float>(ki);
+    v.fkR[i] = ccast<float>(kr);
+    v.feL[i] = ccast<float>(el);
+    v.feR[i] = ccast<float>(er);
   }
   __syncthreads();
 }
@@ -72,7 +83,7 @@ __device__ __forceinline__ zc pq64(const zc *O, int n, int l, int j, const KV &v
 // preconditioner; only the residual needs FP64)
 __device__ __forceinline__ cc pq32(const zc *O, const cc *O32, int n, int l, int j, const KV &v, float sel) {
   const cc o = O32 ? O32[l + (size_t)j * n] : ccast<float>(O[l + (size_t)j * n]);
-  const cc r = cmul(ccast<float>(v.kR[j]), ccast<float>(v.kinvL[l]));
+  const cc r = cmul(v.fkR[j], v.fkinvL[l]);
   return cmul(o, mkc<float>(0.5f * (1.0f + sel * r.re), 0.5f * sel * r.im));
 }
 
@@ -239,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p) {
     cta_gemm_skinny<float>(
         n, nc, n,
         [=](int i, int l) {
-          return cmul(cmul(ccast<float>(vc.eL[i]), Zprev[i + (size_t)l * n]), ccast<float>(vc.eL[l]));
+          return cmul(cmul(vc.feL[i], Zprev[i + (size_t)l * n]), vc.feL[l]);
         },
         [=](int l, int j) { return ccast<float>(G[l + (size_t)j * n]); },
         [=](int i, int j, cc acc) {
@@ -335,7 +346,7 @@ __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
 
 // ---------------------------------------------------------------------------
 size_t refine_smem_bytes(int n) {
-  const size_t kv = 4 * (size_t)n * sizeof(zc);
+  const size_t kv = 4 * (size_t)n * (sizeof(zc) + sizeof(cc));
   const size_t fwd = (skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc) + kv;
   const size_t bwd = skinny_smem_elems<float>() * sizeof(cc) + kv;
   const size_t res = skinny_smem_elems<double>() * sizeof(zc) + kv;

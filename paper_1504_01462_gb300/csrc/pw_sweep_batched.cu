@@ -61,6 +61,13 @@ __device__ __forceinline__ cx<T> pqb(const zc *O, const cc *O32, int n, int l, i
 
 // Points whose problem ended at an earlier interface (a.p > N of the point)
 // take no part in the remaining steps.
+// P_lj (sel +1) or Q_lj (sel -1) from the transposed FP32 overlaps Ot[j + l n]
+__device__ __forceinline__ cc pqt(const cc *Ot, int n, int l, int j, const KVb<float> &v, float sel) {
+  const cc o = Ot[j + (size_t)l * n];
+  const cc r = cmul(v.kR[j], v.kinvL[l]);
+  return cmul(o, mkc<float>(0.5f * (1.f + sel * r.re), 0.5f * sel * r.im));
+}
+
 __device__ __forceinline__ bool inactive(const SweepArgs &a, int pt) {
   const PointDesc &d = a.pts[pt];
   return d.skip || a.status[pt] || a.p > d.N;
@@ -184,10 +191,13 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
   __syncthreads();
   const KVb<float> v{skinv, skr, nullptr};
   const cc *O32 = overlap32_of(a, d, p);
-  // B(l .. l+3, j) is a contiguous run of O for fixed j (column-major)
-  const bool ok = tc::cgemm_tile<true>(
+  // B(l, j) from the transposed FP32 copy (consecutive j contiguous for fixed l:
+  // one column per thread, coalesced across the warp) when the k-set has one
+  const cc *Ot = (a.O32t && !tr) ? a.O32t + ((size_t)d.o_off + p) * n * n : nullptr;
+  const bool ok = tc::cgemm_tile<false>(
       n, 2 * n, n, r0, c0, [=](int i, int l) { return R[i + (size_t)l * n]; },
       [=](int l, int j) {
+        if (Ot) return j < n ? pqt(Ot, n, l, j, v, -1.f) : pqt(Ot, n, l, j - n, v, 1.f);
         return j < n ? pqb<float>(O, O32, n, l, j, v, -1.f, tr) : pqb<float>(O, O32, n, l, j - n, v, 1.f, tr);
       },
       [=](int i, int j, cc acc) {
