@@ -31,9 +31,8 @@ namespace pw {
 
 namespace {
 
-struct KV {   // per-interface vectors in shared memory: FP64, and FP32 copies for the FP32 passes
+struct KV {   // per-interface vectors, FP64, in shared memory (the residual)
   zc *kinvL, *kR, *eL, *eR;
-  cc *fkinvL, *fkR, *feL, *feR;
 };
 
 __device__ KV carve_kv(unsigned char *raw, size_t off, int n) {
@@ -43,11 +42,6 @@ __device__ KV carve_kv(unsigned char *raw, size_t off, int n) {
   v.kR = c + n;
   v.eL = c + 2 * n;
   v.eR = c + 3 * n;
-  cc *f = reinterpret_cast<cc *>(c + 4 * n);
-  v.fkinvL = f;
-  v.fkR = f + n;
-  v.feL = f + 2 * n;
-  v.feR = f + 3 * n;
   return v;
 }
 
@@ -59,32 +53,12 @@ __device__ void load_kv(const RefineArgs &a, const PointDesc &d, int p, KV &v) {
   for (int i = threadIdx.x; i < n; i += NT) {
     const zc kl = kz_branch(d.E, Ep[i]);
     const zc kr = kz_branch(d.E, Eq[i]);
-    const zc ki = cinv(kl), el = phase_fwd(kl, dz[p]), er = phase_fwd(kr, dz[p + 1]);
-    v.kinvL[i] = ki;
+    v.kinvL[i] = cinv(kl);
     v.kR[i] = kr;
-    v.eL[i] = el;
-    v.eR[i] = er;
-    v.fkinvL[i] = ccast<float>(ki);
-    v.fkR[i] = ccast<float>(kr);
-    v.feL[i] = ccast<float>(el);
-    v.feR[i] = ccast<float>(er);
+    v.eL[i] = phase_fwd(kl, dz[p]);
+    v.eR[i] = phase_fwd(kr, dz[p + 1]);
   }
   __syncthreads();
-}
-
-// P_lj (sel +1) or Q_lj (sel -1) in FP64 from O and the k vectors
-__device__ __forceinline__ zc pq64(const zc *O, int n, int l, int j, const KV &v, double sel) {
-  const zc o = O[l + (size_t)j * n];
-  const zc r = cmul(v.kR[j], v.kinvL[l]);
-  return cmul(o, mkc<double>(0.5 * (1.0 + sel * r.re), 0.5 * sel * r.im));
-}
-
-// The same in FP32 (the backward and forward passes apply the FP32
-// preconditioner; only the residual needs FP64)
-__device__ __forceinline__ cc pq32(const zc *O, const cc *O32, int n, int l, int j, const KV &v, float sel) {
-  const cc o = O32 ? O32[l + (size_t)j * n] : ccast<float>(O[l + (size_t)j * n]);
-  const cc r = cmul(v.fkR[j], v.fkinvL[l]);
-  return cmul(o, mkc<float>(0.5f * (1.0f + sel * r.re), 0.5f * sel * r.im));
 }
 
 __device__ __forceinline__ size_t blk(const RefineArgs &a, const PointDesc &d, int q) {
@@ -112,62 +86,209 @@ __global__ void k_refine_init(RefineArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Backward pass at interface p (launched for p = max N down to 0; a point
-// starts at its own N):
-//   da_q = Z_p (e_q db_q) + u_p,   db_p = Q_p da_q + P_p e_q db_q (+ g_p),
-// accumulated into Xa[q], Xb[p]; db_p is carried to the next (left) interface.
-__global__ void __launch_bounds__(NT) k_refine_backward(RefineArgs a, int p, int with_src) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int pt = blockIdx.x;
-  const PointDesc d = a.pts[pt];
-  if (d.skip || a.status[pt] || p > d.N) return;
-  const int n = a.n, nc = a.nc, N = d.N, q = p + 1;
-  cc *gsm = reinterpret_cast<cc *>(smraw);
-  KV v = carve_kv(smraw, skinny_smem_elems<float>() * sizeof(cc), n);
-  load_kv(a, d, p, v);
-  const zc *O = overlap(a, d, p);
-  const cc *O32 = a.O32 ? a.O32 + ((size_t)d.o_off + p) * (size_t)n * n : nullptr;
-  const cc *Z = a.Zst + ((size_t)d.st_off + p) * n * n;
-  const cc *U = a.Ust + ((size_t)d.st_off + p) * n * nc;
-  zc *carry = a.carry + (size_t)pt * n * nc;       // db_q in, db_p out
-  cc *tmp = a.tmp + (size_t)pt * 2 * n * nc;       // [da_q ; e_q db_q] as a 2n x nc block
-  // e_q db_q (db_{N+1} = 0)
-  for (int e = threadIdx.x; e < n * nc; e += NT) {
-    const int i = e % n, c = e / n;
-    const zc b = (q <= N) ? carry[e] : czero<double>();
-    tmp[n + i + (size_t)c * 2 * n] = ccast<float>(cmul(v.eR[i], b));
+// The FP32 preconditioner passes, several CTAs per point (row blocks of
+// SKINNY_BM rows): grid (row blocks, points).
+//   backward (p = N .. 0):  da_q = Z_p (e_q db_q) + u_p,  db_p = Q_p da_q + P_p e_q db_q (+ g_p),
+//                           accumulated into Xa[q], Xb[p]; db_p is carried to interface p-1;
+//   forward  (p = 0 .. N):  u_p = W_p^{-1} (c_p + R_p g_p - f_p),  R_p = e_p Z_{p-1} e_p,
+//                           c_{p+1} = e_q u_p, with W_p's LU factors kept by the first sweep
+//                           (an O(n^2 n_c) replay); u_p replaces the stored one for the next
+//                           backward pass, and at p = N the carry is the correction of a_{N+1}.
+namespace {
+
+// 1/k^p, k^{p+1}, e^{i k^p dz_p}, e^{i k^{p+1} dz_{p+1}} in FP32 (null = not needed);
+// E - E_n is formed in FP64 before the FP32 root, so thresholds keep their branch.
+__device__ void load_kv32(const RefineArgs &a, const PointDesc &d, int p, cc *kinvL, cc *kR, cc *eL, cc *eR) {
+  const int n = a.n;
+  const double *Ep = a.En + ((size_t)d.en_off + p) * n;
+  const double *Eq = Ep + n;
+  const float dzl = (float)a.dz[d.dz_off + p], dzr = (float)a.dz[d.dz_off + p + 1];
+  auto kz32 = [](double diff) {
+    const float m = sqrtf((float)fabs(diff));
+    return diff > 0.0 ? mkc<float>(m, 0.f) : mkc<float>(0.f, m);
+  };
+  auto ph32 = [](cc k, float dz) {
+    const float mag = expf(-k.im * dz);
+    float sn, cs;
+    sincosf(k.re * dz, &sn, &cs);
+    return mkc<float>(mag * cs, mag * sn);
+  };
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const cc kl = kz32(d.E - Ep[i]), kr = kz32(d.E - Eq[i]);
+    if (kinvL) kinvL[i] = cinv(kl);
+    if (kR) kR[i] = kr;
+    if (eL) eL[i] = ph32(kl, dzl);
+    if (eR) eR[i] = ph32(kr, dzr);
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ bool refine_skip(const RefineArgs &a, const PointDesc &d, int pt, int p) {
+  return d.skip || a.status[pt] || p > d.N;
+}
+
+}  // namespace
+
+// Backward pass, part 1 at interface p (rows i0 .. i0+SKINNY_BM of this CTA):
+//   da_q = Z_p (e_q db_q) + u_p  -> tmp[0:n] (rows), Xa[q];  e_q db_q -> tmp[n:2n] (rows)
+__global__ void __launch_bounds__(NT) k_refine_bwd_a(RefineArgs a, int p, int with_src) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y, i0 = blockIdx.x * SKINNY_BM;
+  const PointDesc d = a.pts[pt];
+  if (refine_skip(a, d, pt, p) || i0 >= a.n) return;
+  const int n = a.n, nc = a.nc, N = d.N, q = p + 1;
+  const int rows = min(SKINNY_BM, n - i0);
+  cc *gsm = reinterpret_cast<cc *>(smraw);
+  cc *eR = gsm + skinny_smem_elems<float>();
+  load_kv32(a, d, p, nullptr, nullptr, nullptr, eR);
+  const zc *carry = a.carry + (size_t)pt * n * nc;   // db_q (db_{N+1} = 0)
+  const bool has_b = q <= N;
+  auto edb = [=](int l, int j) {
+    return has_b ? cmul(eR[l], ccast<float>(carry[l + (size_t)j * n])) : czero<float>();
+  };
+  const cc *Z = a.Zst + ((size_t)d.st_off + p) * n * n;
+  const cc *U = a.Ust + ((size_t)d.st_off + p) * n * nc;
+  cc *tmp = a.tmp + (size_t)pt * 2 * n * nc;         // [da_q ; e_q db_q] as a 2n x nc block
+  for (int e = threadIdx.x; e < rows * nc; e += NT) {
+    const int i = i0 + e % rows, c = e / rows;
+    tmp[n + i + (size_t)c * 2 * n] = edb(i, c);
+  }
   zc *Xa = a.Xa + blk(a, d, q);
-  zc *Xb = a.Xb + blk(a, d, p);
-  // da_q
+  const bool add = q <= N || !with_src;   // a correction of a_{N+1} was added by the forward pass
   cta_gemm_skinny<float>(
-      n, nc, n, [=](int i, int l) { return Z[i + (size_t)l * n]; },
-      [=](int l, int j) { return tmp[n + l + (size_t)j * 2 * n]; },
+      rows, nc, n, [=](int i, int l) { return Z[i0 + i + (size_t)l * n]; },
+      [=](int l, int j) { return edb(l, j); },
       [=](int i, int j, cc acc) {
-        const cc da = cadd(acc, U[i + (size_t)j * n]);
-        tmp[i + (size_t)j * 2 * n] = da;
-        if (q <= N || !with_src) {   // a correction of a_{N+1} was added by the forward pass
-          zc &x = Xa[i + (size_t)j * n];
+        const cc da = cadd(acc, U[i0 + i + (size_t)j * n]);
+        tmp[i0 + i + (size_t)j * 2 * n] = da;
+        if (add) {
+          zc &x = Xa[i0 + i + (size_t)j * n];
           x = cadd(x, ccast<double>(da));
         }
       },
       gsm);
-  // db_p = [Q | P] [da_q ; e_q db_q] (+ g_p)
-  const KV vc = v;
+}
+
+// Backward pass, part 2: db_p = [Q | P] [da_q ; e_q db_q] (+ g_p) for this CTA's
+// rows -> carry (db_p, carried to interface p-1), Xb[p].
+__global__ void __launch_bounds__(NT) k_refine_bwd_b(RefineArgs a, int p, int with_src) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y, i0 = blockIdx.x * SKINNY_BM;
+  const PointDesc d = a.pts[pt];
+  if (refine_skip(a, d, pt, p) || i0 >= a.n) return;
+  const int n = a.n, nc = a.nc;
+  const int rows = min(SKINNY_BM, n - i0);
+  cc *gsm = reinterpret_cast<cc *>(smraw);
+  cc *kinvL = gsm + skinny_smem_elems<float>();
+  cc *kR = kinvL + n;
+  load_kv32(a, d, p, kinvL, kR, nullptr, nullptr);
+  const cc *O32 = a.O32 ? a.O32 + ((size_t)d.o_off + p) * (size_t)n * n : nullptr;
+  const zc *O = overlap(a, d, p);
+  const cc *tmp = a.tmp + (size_t)pt * 2 * n * nc;
+  zc *carry = a.carry + (size_t)pt * n * nc;
+  zc *Xb = a.Xb + blk(a, d, p);
   const zc *G = a.Gr + iblk(a, d, p);
+  auto pq = [=](int l, int j, float sel) {
+    const cc o = O32 ? O32[l + (size_t)j * n] : ccast<float>(O[l + (size_t)j * n]);
+    const cc r = cmul(kR[j], kinvL[l]);
+    return cmul(o, mkc<float>(0.5f * (1.0f + sel * r.re), 0.5f * sel * r.im));
+  };
   cta_gemm_skinny<float>(
-      n, nc, 2 * n,
-      [=](int i, int l) { return l < n ? pq32(O, O32, n, i, l, vc, -1.0f) : pq32(O, O32, n, i, l - n, vc, 1.0f); },
+      rows, nc, 2 * n,
+      [=](int i, int l) { return l < n ? pq(i0 + i, l, -1.0f) : pq(i0 + i, l - n, 1.0f); },
       [=](int l, int j) { return tmp[l + (size_t)j * 2 * n]; },
       [=](int i, int j, cc acc) {
         zc db = ccast<double>(acc);
-        if (with_src) db = cadd(db, G[i + (size_t)j * n]);
-        carry[i + (size_t)j * n] = db;
-        zc &x = Xb[i + (size_t)j * n];
+        if (with_src) db = cadd(db, G[i0 + i + (size_t)j * n]);
+        carry[i0 + i + (size_t)j * n] = db;
+        zc &x = Xb[i0 + i + (size_t)j * n];
         x = cadd(x, db);
       },
       gsm);
+}
+
+// Forward correction, part 1 (p > 0): rhs = c_p + R_p g_p - f_p for this CTA's
+// rows, R_p = e_p Z_{p-1} e_p.
+__global__ void __launch_bounds__(NT) k_refine_fwd_a(RefineArgs a, int p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y, i0 = blockIdx.x * SKINNY_BM;
+  const PointDesc d = a.pts[pt];
+  if (refine_skip(a, d, pt, p) || i0 >= a.n) return;
+  const int n = a.n, nc = a.nc;
+  const int rows = min(SKINNY_BM, n - i0);
+  cc *gsm = reinterpret_cast<cc *>(smraw);
+  cc *eL = gsm + skinny_smem_elems<float>();
+  load_kv32(a, d, p, nullptr, nullptr, eL, nullptr);
+  const cc *Zprev = a.Zst + ((size_t)d.st_off + p - 1) * n * n;
+  cc *rhs = a.M + (size_t)pt * n * (n + nc);   // n x nc scratch
+  const zc *carry = a.carry + (size_t)pt * n * nc;
+  const zc *F = a.Fr + iblk(a, d, p);
+  const zc *G = a.Gr + iblk(a, d, p);
+  cta_gemm_skinny<float>(
+      rows, nc, n, [=](int i, int l) { return cmul(cmul(eL[i0 + i], Zprev[i0 + i + (size_t)l * n]), eL[l]); },
+      [=](int l, int j) { return ccast<float>(G[l + (size_t)j * n]); },
+      [=](int i, int j, cc acc) {
+        const size_t e = i0 + i + (size_t)j * n;
+        rhs[e] = ccast<float>(csub(cadd(carry[e], ccast<double>(acc)), F[e]));
+      },
+      gsm);
+}
+
+// Forward correction, part 2 (one CTA per point): u_p = W_p^{-1} rhs by the
+// stored LU factors, c_{p+1} = e_q u_p; at the point's last interface the
+// correction of a_{N+1} is added and its relative size recorded.
+__global__ void __launch_bounds__(NT) k_refine_fwd_b(RefineArgs a, int p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.x;
+  const PointDesc d = a.pts[pt];
+  if (refine_skip(a, d, pt, p)) return;
+  const int n = a.n, nc = a.nc, N = d.N;
+  cc *gsm = reinterpret_cast<cc *>(smraw);
+  cc *eR = gsm + skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB;
+  load_kv32(a, d, p, nullptr, nullptr, nullptr, eR);
+  const cc *LU = a.LUst + ((size_t)d.st_off + p) * n * n;
+  const int *piv = a.PIVst + ((size_t)d.st_off + p) * n;
+  cc *Ust = a.Ust + ((size_t)d.st_off + p) * n * nc;
+  cc *rhs = a.M + (size_t)pt * n * (n + nc);
+  zc *carry = a.carry + (size_t)pt * n * nc;
+  if (p == 0) {
+    const zc *F = a.Fr + iblk(a, d, p);
+    for (int e = threadIdx.x; e < n * nc; e += NT) rhs[e] = ccast<float>(csub(carry[e], F[e]));
+    __syncthreads();
+  }
+  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm);
+  for (int e = threadIdx.x; e < n * nc; e += NT) {
+    const int i = e % n;
+    const cc u = rhs[e];
+    Ust[e] = u;
+    carry[e] = ccast<double>(cmul(eR[i], u));
+  }
+  __syncthreads();
+  if (p == N) {
+    // add the correction of a_{N+1}; record its size relative to a_{N+1}
+    zc *X = a.Xa + blk(a, d, N + 1);
+    double dn = 0.0, xn = 0.0;
+    for (int e = threadIdx.x; e < n * nc; e += NT) {
+      const zc dx = carry[e];
+      const zc x = cadd(X[e], dx);
+      X[e] = x;
+      dn += cnorm2(dx);
+      xn += cnorm2(x);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      dn += __shfl_down_sync(0xffffffffu, dn, off);
+      xn += __shfl_down_sync(0xffffffffu, xn, off);
+    }
+    __shared__ double red[2][NT / 32];
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = dn; red[1][threadIdx.x >> 5] = xn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sd = 0.0, sx = 0.0;
+      for (int w = 0; w < NT / 32; ++w) { sd += red[0][w]; sx += red[1][w]; }
+      a.corr_prev[pt] = a.corr[pt];
+      a.corr[pt] = sx > 0.0 ? sqrt(sd / sx) : 0.0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -213,84 +334,6 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
     const zc bwd = mkc<double>(0.5 * (y1.re - y2.re), 0.5 * (y1.im - y2.im));
     F[e] = csub(fwd, cmul(vc.eL[i], ap[e]));
     G[e] = csub(bwd, bp[e]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Forward correction sweep at interface p (launched for p = 0..max N):
-//   u_p = W_p^{-1}(c_p + R_p g_p - f_p),  R_p = e_p Z_{p-1} e_p,  c_{p+1} = e_q u_p,
-// with W_p's LU factors kept by the first sweep (an O(n^2 nc) replay).  u_p
-// replaces the stored one for the backward pass.  At p = N the carry holds the
-// correction of a_{N+1} (= u_N); on the last iteration (no backward pass
-// follows) it is added to Xa[N+1] here.
-__global__ void __launch_bounds__(NT) k_refine_forward(RefineArgs a, int p) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int pt = blockIdx.x;
-  const PointDesc d = a.pts[pt];
-  if (d.skip || a.status[pt] || p > d.N) return;
-  const int n = a.n, nc = a.nc, N = d.N;
-  cc *gsm = reinterpret_cast<cc *>(smraw);
-  const size_t kv_off = (skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc);
-  KV v = carve_kv(smraw, kv_off, n);
-  load_kv(a, d, p, v);
-  const cc *Zprev = p > 0 ? a.Zst + ((size_t)d.st_off + p - 1) * n * n : nullptr;
-  const cc *LU = a.LUst + ((size_t)d.st_off + p) * n * n;
-  const int *piv = a.PIVst + ((size_t)d.st_off + p) * n;
-  cc *Ust = a.Ust + ((size_t)d.st_off + p) * n * nc;
-  cc *rhs = a.M + (size_t)pt * n * (n + nc);   // n x nc scratch
-  zc *carry = a.carry + (size_t)pt * n * nc;   // c_p in, c_{p+1} out
-  const zc *F = a.Fr + iblk(a, d, p);
-  const zc *G = a.Gr + iblk(a, d, p);
-  const KV vc = v;
-  if (p == 0) {
-    for (int e = threadIdx.x; e < n * nc; e += NT) rhs[e] = ccast<float>(csub(carry[e], F[e]));
-    __syncthreads();
-  } else {
-    // rhs = c_p + R_p g_p - f_p
-    cta_gemm_skinny<float>(
-        n, nc, n,
-        [=](int i, int l) {
-          return cmul(cmul(vc.feL[i], Zprev[i + (size_t)l * n]), vc.feL[l]);
-        },
-        [=](int l, int j) { return ccast<float>(G[l + (size_t)j * n]); },
-        [=](int i, int j, cc acc) {
-          const zc r = csub(cadd(carry[i + (size_t)j * n], ccast<double>(acc)), F[i + (size_t)j * n]);
-          rhs[i + (size_t)j * n] = ccast<float>(r);
-        },
-        gsm);
-  }
-  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm);
-  for (int e = threadIdx.x; e < n * nc; e += NT) {
-    const int i = e % n;
-    const cc u = rhs[e];
-    Ust[e] = u;
-    carry[e] = cmul(vc.eR[i], ccast<double>(u));
-  }
-  __syncthreads();
-  if (p == N) {
-    // add the correction of a_{N+1}; record its size relative to a_{N+1}
-    zc *X = a.Xa + blk(a, d, N + 1);
-    double dn = 0.0, xn = 0.0;
-    for (int e = threadIdx.x; e < n * nc; e += NT) {
-      const zc dx = carry[e];
-      const zc x = cadd(X[e], dx);
-      X[e] = x;
-      dn += cnorm2(dx);
-      xn += cnorm2(x);
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      dn += __shfl_down_sync(0xffffffffu, dn, off);
-      xn += __shfl_down_sync(0xffffffffu, xn, off);
-    }
-    __shared__ double red[2][NT / 32];
-    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = dn; red[1][threadIdx.x >> 5] = xn; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sd = 0.0, sx = 0.0;
-      for (int w = 0; w < NT / 32; ++w) { sd += red[0][w]; sx += red[1][w]; }
-      a.corr_prev[pt] = a.corr[pt];
-      a.corr[pt] = sx > 0.0 ? sqrt(sd / sx) : 0.0;
-    }
   }
 }
 
@@ -346,7 +389,7 @@ __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
 
 // ---------------------------------------------------------------------------
 size_t refine_smem_bytes(int n) {
-  const size_t kv = 4 * (size_t)n * (sizeof(zc) + sizeof(cc));
+  const size_t kv = 4 * (size_t)n * sizeof(zc);
   const size_t fwd = (skinny_smem_elems<float>() + Tile<float>::NB * Tile<float>::NB) * sizeof(cc) + kv;
   const size_t bwd = skinny_smem_elems<float>() * sizeof(cc) + kv;
   const size_t res = skinny_smem_elems<double>() * sizeof(zc) + kv;
@@ -357,10 +400,25 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
                           cudaStream_t s, int *passes) {
   const size_t smem = refine_smem_bytes(a.n);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_refine_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_refine_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_refine_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  if ((e = cudaFuncSetAttribute(k_refine_bwd_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_refine_bwd_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_refine_fwd_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_refine_fwd_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_refine_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
+  const dim3 rgrid((a.n + SKINNY_BM - 1) / SKINNY_BM, npts);
+  auto backward = [&](int with_src) {
+    for (int p = a.N; p >= 0; --p) {
+      k_refine_bwd_a<<<rgrid, NT, smem, s>>>(a, p, with_src);
+      k_refine_bwd_b<<<rgrid, NT, smem, s>>>(a, p, with_src);
+    }
+  };
+  auto forward = [&]() {
+    for (int p = 0; p <= a.N; ++p) {
+      if (p > 0) k_refine_fwd_a<<<rgrid, NT, smem, s>>>(a, p);
+      k_refine_fwd_b<<<npts, NT, smem, s>>>(a, p);
+    }
+  };
   const size_t vec = (size_t)npts * a.n * a.nc * sizeof(zc);
   const size_t slot = (size_t)a.n * a.nc * sizeof(zc);
   if ((e = cudaMemsetAsync(a.Xa, 0, slot * a.x_slots, s)) || (e = cudaMemsetAsync(a.Xb, 0, slot * a.x_slots, s)) ||
@@ -371,7 +429,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
   k_refine_init<<<npts, NT, 0, s>>>(a);
   // x0: backward pass over the first sweep's Z_p, u_p
   if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
-  for (int p = a.N; p >= 0; --p) k_refine_backward<<<npts, NT, smem, s>>>(a, p, 0);
+  backward(0);
   // stopping test: the correction of pass i shrinks the error by about
   // c_i / c_{i-1} (c = relative size of the correction of a_{N+1}), so the
   // error left after pass i is estimated as c_i^2 / c_{i-1}
@@ -380,7 +438,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
   for (; it < max_iters; ++it) {
     k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a);
     if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
-    for (int p = 0; p <= a.N; ++p) k_refine_forward<<<npts, NT, smem, s>>>(a, p);
+    forward();
     if (it + 1 >= max_iters) { ++it; break; }
     if ((e = cudaMemcpyAsync(corr.data(), a.corr, npts * sizeof(double), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
@@ -396,7 +454,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
     prev = corr;
     // interior corrections: backward from db_{N+1} = 0
     if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
-    for (int p = a.N; p >= 0; --p) k_refine_backward<<<npts, NT, smem, s>>>(a, p, 1);
+    backward(1);
   }
   if (passes) *passes = it;
   k_refine_finish<<<npts, NT, 0, s>>>(a);
