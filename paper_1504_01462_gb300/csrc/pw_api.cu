@@ -55,7 +55,8 @@ struct pw_ctx {
   std::vector<double> slot_k;      // 2 per slot
   std::vector<char> slot_valid;
   zc *d_HU = nullptr, *d_V = nullptr, *d_O = nullptr;
-  cc *d_O32 = nullptr, *d_O32t = nullptr;   // mixed form: FP32 copies of the overlaps (plain, transposed)
+  cc *d_O32 = nullptr, *d_O32t = nullptr, *d_O32lo = nullptr;   // mixed form: FP32 copies of the
+                                                               // overlaps (plain, transposed, remainders)
   double *d_En = nullptr;
   int *d_eigstat = nullptr;       // Jacobi sweeps per matrix
   std::vector<std::vector<double>> EL, ER;   // electrode eigenvalues per slot (host)
@@ -231,7 +232,7 @@ pw_status alloc_slots(pw_ctx *ctx) {
   const size_t nn = (size_t)n * n;
   const bool mixed = ctx->precision == PW_MIXED_FP32;
   const size_t per = (size_t)(3 * nq - 1) * nn * sizeof(zc) + (size_t)nq * n * sizeof(double) +
-                     (mixed ? 2 * (size_t)(nq - 1) * nn * sizeof(cc) : 0);
+                     (mixed ? 3 * (size_t)(nq - 1) * nn * sizeof(cc) : 0);
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
   int cap = (int)std::min<size_t>(4, std::max<size_t>(1, free_b / 5 / per));
@@ -245,6 +246,7 @@ pw_status alloc_slots(pw_ctx *ctx) {
   CK(cudaMalloc(&ctx->d_O, (size_t)cap * (nq - 1) * nn * sizeof(zc)));
   if (mixed) CK(cudaMalloc(&ctx->d_O32, (size_t)cap * (nq - 1) * nn * sizeof(cc)));
   if (mixed) CK(cudaMalloc(&ctx->d_O32t, (size_t)cap * (nq - 1) * nn * sizeof(cc)));
+  if (mixed) CK(cudaMalloc(&ctx->d_O32lo, (size_t)cap * (nq - 1) * nn * sizeof(cc)));
   CK(cudaMalloc(&ctx->d_En, (size_t)cap * nq * n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_eigstat, (size_t)cap * nq * sizeof(int)));
   return PW_OK;
@@ -283,7 +285,8 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
                       s1 - s0, ctx->stream, ctx->precision == PW_MIXED_FP32);
   if (ctx->d_O32)
     pw::launch_overlaps_fp32(ctx->d_O + (size_t)s0 * (nq - 1) * nn, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn,
-                             ctx->d_O32t + (size_t)s0 * (nq - 1) * nn, n, (s1 - s0) * (nq - 1), ctx->stream);
+                             ctx->d_O32t + (size_t)s0 * (nq - 1) * nn, ctx->d_O32lo + (size_t)s0 * (nq - 1) * nn,
+                             n, (s1 - s0) * (nq - 1), ctx->stream);
   CK(cudaGetLastError());
   SYNC_CHECK();
   st2.done();
@@ -535,7 +538,7 @@ void pw_destroy(pw_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
 
-                  ctx->d_O, ctx->d_O32, ctx->d_O32t, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
+                  ctx->d_O, ctx->d_O32, ctx->d_O32t, ctx->d_O32lo, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
                   ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
@@ -803,6 +806,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.En = a.En;
         r.O = a.O;
         r.O32 = a.O32;
+        r.O32lo = ctx->d_O32lo;
         r.dz = a.dz;
         r.Zst = (const cc *)ctx->Zst.p;
         r.Ust = (cc *)ctx->Ust.p;

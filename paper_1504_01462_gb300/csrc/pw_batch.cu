@@ -46,7 +46,7 @@ struct pw_batch {
   int force_variant = -1;                 // -1: autotune per N_G
   std::map<int, int> variant;             // chosen sweep variant per N_G
   double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  Buf HU, V, En, stat, O, O32, O32t, dz, pts, R, M, piv, KV, status;
+  Buf HU, V, En, stat, O, O32, O32t, O32lo, dz, pts, R, M, piv, KV, status;
   Buf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp, corr;
 };
 
@@ -82,7 +82,7 @@ pw_status grow(pw_batch *b, Buf &x, size_t bytes) {
 }
 
 size_t held(const pw_batch *b) {
-  const Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
+  const Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->O32lo, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
                       &b->KV, &b->status, &b->Zst, &b->Ust, &b->LUst, &b->PIVst, &b->Xa, &b->Xb,
                       &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr};
   size_t s = 0;
@@ -95,7 +95,7 @@ size_t held(const pw_batch *b) {
 size_t instance_bytes(int n, int N, int nc, int precision, bool refine) {
   const size_t nn = (size_t)n * n, esz = precision == PW_FP64 ? sizeof(zc) : sizeof(cc);
   size_t b = (size_t)(N + 2) * (2 * nn * sizeof(zc) + n * sizeof(double) + sizeof(int) + sizeof(double)) +
-             (size_t)(N + 1) * nn * (sizeof(zc) + (precision == PW_MIXED_FP32 ? 2 * sizeof(cc) : 0));
+             (size_t)(N + 1) * nn * (sizeof(zc) + (precision == PW_MIXED_FP32 ? 3 * sizeof(cc) : 0));
   b += nn * esz + (size_t)n * (2 * n + nc) * esz + 3 * (size_t)n * esz + n * sizeof(int) + 256;
   if (refine)
     b += (size_t)(N + 1) * (2 * nn + (size_t)n * nc) * sizeof(cc) + (size_t)(N + 1) * n * sizeof(int) +
@@ -146,7 +146,8 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     return st;
   const bool mixed = b->precision == PW_MIXED_FP32;
   if (mixed && ((st = grow(b, b->O32, (size_t)nov * nn * sizeof(cc))) ||
-                (st = grow(b, b->O32t, (size_t)nov * nn * sizeof(cc)))))
+                (st = grow(b, b->O32t, (size_t)nov * nn * sizeof(cc))) ||
+                (st = grow(b, b->O32lo, (size_t)nov * nn * sizeof(cc)))))
     return st;
   zc *HU = (zc *)b->HU.p, *O = (zc *)b->O.p;
   double *En = (double *)b->En.p;
@@ -178,7 +179,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   for (int j = 0; j < m; ++j)
     pw::launch_overlaps(HU + mb[j] * nn, O + ob[j] * nn, n, b->view[ids[j]].N + 2, 1, s,
                         b->precision == PW_MIXED_FP32);
-  if (mixed) pw::launch_overlaps_fp32(O, (cc *)b->O32.p, (cc *)b->O32t.p, n, (int)nov, s);
+  if (mixed) pw::launch_overlaps_fp32(O, (cc *)b->O32.p, (cc *)b->O32t.p, (cc *)b->O32lo.p, n, (int)nov, s);
   BCK(cudaGetLastError());
   BCK(cudaEventRecord(ev[2], s));
   // electrode eigenvalues -> open channels
@@ -331,6 +332,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     r.En = En;
     r.O = O;
     r.O32 = a.O32;
+    r.O32lo = mixed ? (const cc *)b->O32lo.p : nullptr;
     r.dz = a.dz;
     r.Zst = (const cc *)b->Zst.p;
     r.Ust = (cc *)b->Ust.p;
@@ -466,7 +468,7 @@ void pw_batch_destroy(pw_batch *b) {
   cudaStreamSynchronize(b->stream);
   if (b->capture) cudaStreamDestroy(b->capture);
   for (pw_ctx *c : b->inst) pw_destroy(c);
-  Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
+  Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->O32lo, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
                 &b->KV, &b->status, &b->Zst, &b->Ust, &b->LUst, &b->PIVst, &b->Xa, &b->Xb,
                 &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr};
   for (Buf *x : all)

@@ -96,6 +96,7 @@ struct RefineArgs {
   const double *En;
   const zc *O;
   const cc *O32;         // null, or FP32 copies of O (the FP32 preconditioner passes read these)
+  const cc *O32lo;       // null, or the FP32 remainders O - O32 (the double-float residual reads O32 + O32lo)
   const double *dz;
   const cc *Zst;         // per point (N+1) x n x n
   cc *Ust;               // per point (N+1) x n x nc
@@ -166,9 +167,10 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
 // the same size; status: Jacobi sweeps per matrix (negative: not converged)
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s,
                 bool double_float = false);
-// FP32 copies of `count` n x n overlaps, plain and (when O32t is not null)
-// transposed: O32t[j + l n] = O[l + j n]
-void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, int n, int count, cudaStream_t s);
+// FP32 copies of `count` n x n overlaps, plain, (when O32t is not null)
+// transposed: O32t[j + l n] = O[l + j n], and (when O32lo is not null) the FP32
+// remainders O - O32 (O32 + O32lo is O as a double-float)
+void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, cc *O32lo, int n, int count, cudaStream_t s);
 // O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots;
 // double_float: accumulate in double-float (48-bit) on the FP32 pipe
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s,

@@ -755,9 +755,15 @@ __global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n, int 
 }
 
 // FP32 copies of the overlaps (same column-major layout).
-__global__ void __launch_bounds__(NT) k_o32(const zc *O, cc *O32, size_t count) {
-  for (size_t e = (size_t)blockIdx.x * NT + threadIdx.x; e < count; e += (size_t)gridDim.x * NT)
-    O32[e] = ccast<float>(O[e]);
+// (with O32lo: the FP32 remainders O - O32, so that O32 + O32lo is O as a
+// double-float, 48 bits)
+__global__ void __launch_bounds__(NT) k_o32(const zc *O, cc *O32, cc *O32lo, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * NT + threadIdx.x; e < count; e += (size_t)gridDim.x * NT) {
+    const zc o = O[e];
+    const cc h = ccast<float>(o);
+    O32[e] = h;
+    if (O32lo) O32lo[e] = mkc<float>((float)(o.re - (double)h.re), (float)(o.im - (double)h.im));
+  }
 }
 
 // FP32 transposed copies (32 x 32 tiles through shared memory, coalesced on
@@ -781,10 +787,10 @@ __global__ void __launch_bounds__(NT) k_o32t(const zc *O, cc *Ot, int n) {
   }
 }
 
-void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, int n, int count, cudaStream_t s) {
+void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, cc *O32lo, int n, int count, cudaStream_t s) {
   const size_t nn = (size_t)n * n, total = (size_t)count * nn;
   const size_t blocks = (total + NT - 1) / NT;
-  k_o32<<<(unsigned)(blocks < 4096 ? blocks : 4096), NT, 0, s>>>(O, O32, total);
+  k_o32<<<(unsigned)(blocks < 4096 ? blocks : 4096), NT, 0, s>>>(O, O32, O32lo, total);
   if (!O32t) return;
   const int tn = (n + 31) / 32;
   for (int c0 = 0; c0 < count; c0 += 65535) {   // grid.y limit

@@ -305,6 +305,9 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
   KV v = carve_kv(smraw, skinny_smem_elems<double>() * sizeof(zc), n);
   load_kv(a, d, p, v);
   const zc *O = overlap(a, d, p);
+  const size_t ooff = ((size_t)d.o_off + p) * (size_t)n * n;
+  const cc *Ohi = (a.O32 && a.O32lo) ? a.O32 + ooff : nullptr;
+  const cc *Olo = Ohi ? a.O32lo + ooff : nullptr;
   const zc *ap = a.Xa + blk(a, d, p);
   const zc *bp = a.Xb + blk(a, d, p);
   const zc *aq = a.Xa + blk(a, d, q);
@@ -315,7 +318,18 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
   const bool has_bq = q <= N;
   // the O y products in double-float (48-bit) arithmetic on the FP32 pipe
   cta_gemm_skinny<df>(
-      n, 2 * nc, n, [=](int i, int l) { return dfc_of(O[i + (size_t)l * n]); },
+      n, 2 * nc, n,
+      [=](int i, int l) {
+        const size_t e = i + (size_t)l * n;
+        if (Ohi) {   // the double-float O from its two FP32 planes (no FP64 arithmetic)
+          const cc h = Ohi[e], lo = Olo[e];
+          dfc z;
+          z.re = mkdf(h.re, lo.re);
+          z.im = mkdf(h.im, lo.im);
+          return z;
+        }
+        return dfc_of(O[e]);
+      },
       [=](int l, int j) {
         const int c = j < nc ? j : j - nc;
         const zc A = aq[l + (size_t)c * n];
