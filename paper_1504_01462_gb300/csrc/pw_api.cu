@@ -66,6 +66,7 @@ struct pw_ctx {
   DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   DevBuf Xa_m, Xb_m, status_m, Tg, Gam, gtab, T1, dV0, wgt;   // adjoint (pw_grad)
   DevBuf corr;                     // refinement stopping test
+  DevBuf eigws;                    // workspace of the double-float eigensolver
   int last_passes = 0;             // refinement passes of the last batch
   // device copies of the device-region wells (kept for the adjoint)
   double *d_wxyz = nullptr, *d_wv0 = nullptr, *d_wsig = nullptr;
@@ -274,9 +275,11 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
     pw::launch_assemble_h(ctx->d_HU + (size_t)s * nq * nn, ctx->d_tab, ctx->d_mn, ctx->d_G, ks[s][0],
                           ks[s][1], n, nq, ctx->Dm, ctx->Dn, ctx->stream);
   CK(cudaGetLastError());
+  const bool dfe = ctx->precision == PW_MIXED_FP32;
+  if (dfe && (st = ensure(ctx, ctx->eigws, pw::heev_ws_bytes(n, nmat)))) return st;
   pw::launch_eig(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_V + (size_t)s0 * nq * nn,
                  ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
-                 ctx->stream, ctx->precision == PW_MIXED_FP32);
+                 ctx->stream, dfe, dfe ? ctx->eigws.p : nullptr, dfe ? ctx->eigws.bytes : 0);
   CK(cudaGetLastError());
   SYNC_CHECK();
   st1.done();
@@ -537,14 +540,13 @@ void pw_destroy(pw_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
-
                   ctx->d_O, ctx->d_O32, ctx->d_O32t, ctx->d_O32lo, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
                   ctx->Xb.p, ctx->Fr.p, ctx->Gr.p, ctx->carry.p, ctx->tmp.p, ctx->LUst.p,
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
-                  ctx->lead_out.p};
+                  ctx->lead_out.p, ctx->eigws.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

@@ -48,6 +48,7 @@ struct pw_batch {
   double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   Buf HU, V, En, stat, O, O32, O32t, O32lo, dz, pts, R, M, piv, KV, status;
   Buf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp, corr;
+  Buf eigws;                              // workspace of the double-float eigensolver
 };
 
 namespace {
@@ -84,7 +85,7 @@ pw_status grow(pw_batch *b, Buf &x, size_t bytes) {
 size_t held(const pw_batch *b) {
   const Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->O32lo, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
                       &b->KV, &b->status, &b->Zst, &b->Ust, &b->LUst, &b->PIVst, &b->Xa, &b->Xb,
-                      &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr};
+                      &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr, &b->eigws};
   size_t s = 0;
   for (const Buf *x : all) s += x->bytes;
   return s;
@@ -97,6 +98,7 @@ size_t instance_bytes(int n, int N, int nc, int precision, bool refine) {
   size_t b = (size_t)(N + 2) * (2 * nn * sizeof(zc) + n * sizeof(double) + sizeof(int) + sizeof(double)) +
              (size_t)(N + 1) * nn * (sizeof(zc) + (precision == PW_MIXED_FP32 ? 3 * sizeof(cc) : 0));
   b += nn * esz + (size_t)n * (2 * n + nc) * esz + 3 * (size_t)n * esz + n * sizeof(int) + 256;
+  if (precision == PW_MIXED_FP32) b += pw::heev_ws_bytes(n, N + 2);
   if (refine)
     b += (size_t)(N + 1) * (2 * nn + (size_t)n * nc) * sizeof(cc) + (size_t)(N + 1) * n * sizeof(int) +
          (size_t)(2 * (N + 2) + 2 * (N + 1) + 1) * n * nc * sizeof(zc) + 2 * (size_t)n * nc * sizeof(cc);
@@ -147,7 +149,8 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   const bool mixed = b->precision == PW_MIXED_FP32;
   if (mixed && ((st = grow(b, b->O32, (size_t)nov * nn * sizeof(cc))) ||
                 (st = grow(b, b->O32t, (size_t)nov * nn * sizeof(cc))) ||
-                (st = grow(b, b->O32lo, (size_t)nov * nn * sizeof(cc)))))
+                (st = grow(b, b->O32lo, (size_t)nov * nn * sizeof(cc))) ||
+                (st = grow(b, b->eigws, pw::heev_ws_bytes(n, (int)nmat)))))
     return st;
   zc *HU = (zc *)b->HU.p, *O = (zc *)b->O.p;
   double *En = (double *)b->En.p;
@@ -173,7 +176,8 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     pw::launch_assemble_h(HU + mb[j] * nn, v.tab, v.mn, v.G, kpar[2 * i], kpar[2 * i + 1], n, v.N + 2, v.Dm,
                           v.Dn, s);
   }
-  pw::launch_eig(HU, (zc *)b->V.p, En, (int *)b->stat.p, n, (int)nmat, s, b->precision == PW_MIXED_FP32);
+  pw::launch_eig(HU, (zc *)b->V.p, En, (int *)b->stat.p, n, (int)nmat, s, b->precision == PW_MIXED_FP32,
+                 mixed ? b->eigws.p : nullptr, mixed ? b->eigws.bytes : 0);
   BCK(cudaGetLastError());
   BCK(cudaEventRecord(ev[1], s));
   for (int j = 0; j < m; ++j)
@@ -470,7 +474,7 @@ void pw_batch_destroy(pw_batch *b) {
   for (pw_ctx *c : b->inst) pw_destroy(c);
   Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->O32lo, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
                 &b->KV, &b->status, &b->Zst, &b->Ust, &b->LUst, &b->PIVst, &b->Xa, &b->Xb,
-                &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr};
+                &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr, &b->eigws};
   for (Buf *x : all)
     if (x->p) cudaFree(x->p);
   delete b;

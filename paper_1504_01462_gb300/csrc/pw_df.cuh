@@ -81,6 +81,41 @@ __device__ __forceinline__ void df_renorm(df &a) {
   a.lo = l;
 }
 
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_from_float(float x) { return mkdf(x, 0.f); }
+// a * b for a float b (exact product of the high parts plus the low term)
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  const float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return mkdf(h, l);
+}
+// a / b by one correction of the FP32 quotient (Dekker's division):
+// q1 = a_hi / b_hi, r = a - q1 b (formed exactly enough in double-float),
+// q = q1 + r_hi / b_hi
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = a.hi / b.hi;
+  const df r = df_sub(a, df_mul_f(b, q1));
+  const float q2 = r.hi / b.hi;
+  float h, l;
+  fast_two_sum(q1, q2, h, l);
+  return mkdf(h, l);
+}
+// sqrt(a), a >= 0, by one Newton correction of the FP32 root:
+// x = sqrt(a_hi), x + (a - x^2) / (2 x) with x^2 formed exactly (TwoProd)
+__device__ __forceinline__ df df_sqrt(df a) {
+  if (!(a.hi > 0.f)) return mkdf(0.f, 0.f);
+  const float x = sqrtf(a.hi);
+  const float p = x * x, pe = fmaf(x, x, -p);
+  const float r = ((a.hi - p) - pe) + a.lo;
+  float h, l;
+  fast_two_sum(x, r / (2.f * x), h, l);
+  return mkdf(h, l);
+}
+__device__ __forceinline__ df df_abs(df a) { return a.hi < 0.f ? df_neg(a) : a; }
+
 // complex double-float
 typedef cx<df> dfc;
 

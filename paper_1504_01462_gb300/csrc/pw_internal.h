@@ -165,8 +165,12 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
                        int n, int nq, int Dm, int Dn, cudaStream_t s);
 // batched Hermitian eigensolver: H (in) -> U (out, same buffer); V scratch of
 // the same size; status: Jacobi sweeps per matrix (negative: not converged)
+// double_float: the mixed form's double-float solver; ws (ws_bytes >=
+// heev_ws_bytes(n, 1), else null) lets its QL recurrence run in double-float
+// as a separate launch over groups of as many matrices as the workspace holds
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s,
-                bool double_float = false);
+                bool double_float = false, void *ws = nullptr, size_t ws_bytes = 0);
+size_t heev_ws_bytes(int n, int nmat);
 // FP32 copies of `count` n x n overlaps, plain, (when O32t is not null)
 // transposed: O32t[j + l n] = O[l + j n], and (when O32lo is not null) the FP32
 // remainders O - O32 (O32 + O32lo is O as a double-float)

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "pw_cta.cuh"
@@ -462,9 +463,227 @@ __device__ zc block_csum(typename HeevAr<R>::C v, typename HeevAr<R>::C *scratch
   return r;
 }
 
+// Workspace of the split double-float route (per matrix of a launch group):
+// the tridiagonal (d, e), the Householder scalars, and the QL rotation stream
+// (steps (m, lo), then the rotations i = m-1 .. lo of each step as
+// (c_hi, c_lo, s_hi, s_lo)).
+struct HeevWS {
+  double *d, *e;        // n per matrix; d holds the eigenvalues after the QL kernel
+  dfc *tau;             // n per matrix
+  float4 *rot;          // rot_cap per matrix
+  int2 *steps;          // step_cap per matrix
+  int *nsteps;          // 1 per matrix
+  int rot_cap, step_cap;
+};
+
+// Eigenvectors of the split route (one CTA per matrix, all HEEV_THREADS
+// threads): Z = the product of the recorded QL rotations (each thread owns
+// one row of Z and streams every rotation over it, so no barrier is needed
+// between QL steps), then U = Q Z by the stored Householder vectors, then the
+// ascending sort.  A: the reduced matrix in double-float (Householder vectors
+// below the subdiagonal), left by part 1.
+template <typename R>
+__device__ void heev_vectors_from_stream(typename HeevAr<R>::C *A, typename HeevAr<R>::C *Z, double *En,
+                                         int *status, int n, const HeevWS &ws, int mat,
+                                         typename HeevAr<R>::C *v, typename HeevAr<R>::C *pw_,
+                                         typename HeevAr<R>::C *taus, double *d, int *rank) {
+  typedef HeevAr<R> Ar;
+  typedef typename Ar::C C;
+  typedef typename Ar::Rot Rot;
+  constexpr int NTH = HEEV_THREADS;
+  const int tid = threadIdx.x;
+  const size_t nn = (size_t)n * n;
+  for (int i = tid; i < n; i += NTH) {
+    d[i] = ws.d[(size_t)mat * n + i];
+    taus[i] = ws.tau[(size_t)mat * n + i];
+  }
+  for (size_t q = tid; q < nn; q += NTH) {
+    const int i = q % n, j = q / n;
+    Z[q] = i == j ? Ar::one() : Ar::zero();
+  }
+  __syncthreads();
+  const int nst = min(max(ws.nsteps[mat], 0), ws.step_cap);
+  const int2 *steps = ws.steps + (size_t)mat * ws.step_cap;
+  const float4 *rot = ws.rot + (size_t)mat * ws.rot_cap;
+  bool bad = false;
+  for (int row = tid; row < n; row += NTH) {
+    int r0 = 0;
+    for (int st = 0; st < nst; ++st) {
+      const int2 ml = steps[st];
+      const int m = ml.x, lo = ml.y, cnt = m - lo;
+      // a step outside the matrix or the stream cannot come from k_ql_df;
+      // it is recorded, not followed
+      if (m >= n || lo < 0 || cnt < 0 || r0 + cnt > ws.rot_cap) {
+        bad = true;
+        break;
+      }
+      if (cnt == 0) continue;
+      C x = Z[row + (size_t)m * n];
+      C y = Z[row + (size_t)(m - 1) * n];
+      for (int t = 0; t < cnt; ++t) {
+        const int i = m - 1 - t;
+        const C ynext = (t + 1 < cnt) ? Z[row + (size_t)(i - 1) * n] : y;   // issued ahead of the chain
+        const float4 q = rot[r0 + t];
+        Rot c, sn;
+        if constexpr (std::is_same<R, double>::value) {
+          c = (double)q.x + (double)q.y;
+          sn = (double)q.z + (double)q.w;
+        } else {
+          c = mkdf(q.x, q.y);
+          sn = mkdf(q.z, q.w);
+        }
+        C hi, lo_;
+        Ar::rot(y, x, c, sn, hi, lo_);
+        Z[row + (size_t)(i + 1) * n] = hi;
+        x = lo_;
+        y = ynext;
+      }
+      Z[row + (size_t)lo * n] = x;
+      r0 += cnt;
+    }
+  }
+  if (bad) status[mat] = -1;
+  __syncthreads();
+  // back-transformation U = Q Z (Q_{n-2} first)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int k = n - 2; k >= 0; --k) {
+    const C tau = taus[k];
+    if (Ar::is_zero(tau)) continue;
+    const int m = n - k - 1;
+    const C *x = A + (k + 1) + (size_t)k * n;
+    for (int i = tid; i < m; i += NTH) v[i] = i == 0 ? Ar::one() : x[i];
+    __syncthreads();
+    C *Zk = Z + (k + 1);
+    for (int j = warp; j < n; j += NTH / 32) {
+      C acc = Ar::zero();
+      for (int i = lane; i < m; i += 32) Ar::jfma(acc, v[i], Zk[i + (size_t)j * n]);
+      Ar::renorm(acc);
+      for (int off = 16; off > 0; off >>= 1) acc = Ar::add(acc, Ar::shfl_down(acc, off));
+      if (lane == 0) pw_[j] = Ar::mul(tau, acc);
+    }
+    __syncthreads();
+    for (size_t q = tid; q < (size_t)m * n; q += NTH) {
+      const int i = q % m, j = q / m;
+      Zk[i + (size_t)j * n] = Ar::sub_mul(Zk[i + (size_t)j * n], v[i], pw_[j]);
+    }
+    __syncthreads();
+  }
+  // ascending order (ties by index), back to FP64 storage (A is reused: its
+  // double-float contents are no longer needed)
+  zc *A64 = reinterpret_cast<zc *>(A);
+  for (int i = tid; i < n; i += NTH) {
+    const double li = d[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (d[j] < li) || (d[j] == li && j < i);
+    rank[i] = r;
+    En[r] = li;
+  }
+  __syncthreads();
+  for (size_t q = tid; q < nn; q += NTH) {
+    const int i = q % n, j = q / n;
+    A64[i + (size_t)rank[j] * n] = Ar::to(Z[q]);
+  }
+  __syncthreads();
+  if (tid == 0 && status[mat] >= 0) status[mat] = 1;
+}
+
+// The QL recurrence of the split route in double-float on the FP32 pipe, one
+// matrix per 32-thread block (thread 0 runs the scalar recurrence; GB300's
+// FP64 pipe retires a scalar FP64 operation far slower than the FP32 pipe
+// retires the ~10 FP32 operations of its double-float counterpart).  Same
+// implicit QL as part 0 (shift from the leading 2 x 2 block, rotations from
+// the bottom of the unreduced block up); the deflation test uses the
+// double-float resolution (4e-15 relative).  Writes the eigenvalues into
+// ws.d, the step list and the rotations; status -1 when an eigenvalue needs
+// more than 60 iterations or the stream exceeds its capacity.
+__device__ __forceinline__ df hypot_df(df a, df b) {
+  const float big = fmaxf(fabsf(a.hi), fabsf(b.hi));
+  if (big == 0.f) return mkdf(0.f, 0.f);
+  // scale small arguments by an exact power of two so that the squares stay normal
+  const float sc = big < 1e-15f ? 18446744073709551616.f : 1.f;   // 2^64
+  const df as = df_mul_f(a, sc), bs = df_mul_f(b, sc);
+  const df r = df_sqrt(df_add(df_mul(as, as), df_mul(bs, bs)));
+  return sc == 1.f ? r : df_mul_f(r, 1.f / sc);
+}
+
+__global__ void __launch_bounds__(32) k_ql_df(HeevWS ws, int *status, int n) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  df *dd = reinterpret_cast<df *>(smraw);
+  df *ee = dd + n;
+  const int mat = blockIdx.x;
+  double *gd = ws.d + (size_t)mat * n;
+  const double *ge = ws.e + (size_t)mat * n;
+  for (int i = threadIdx.x; i < n; i += 32) {
+    dd[i] = df_of(gd[i]);
+    ee[i] = df_of(ge[i]);
+  }
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  float4 *rot = ws.rot + (size_t)mat * ws.rot_cap;
+  int2 *steps = ws.steps + (size_t)mat * ws.step_cap;
+  const float eps = 4e-15f;
+  int nrot = 0, nst = 0;
+  bool failed = false;
+  for (int l = 0; l < n && !failed; ++l) {
+    int iter = 0;
+    for (;;) {
+      int m = l;
+      for (; m < n - 1; ++m) {
+        const float s2 = fabsf(dd[m].hi) + fabsf(dd[m + 1].hi);
+        if (fabsf(ee[m].hi) <= eps * s2) break;
+      }
+      if (m == l) break;
+      if (++iter > 60 || nst >= ws.step_cap || nrot + (m - l) > ws.rot_cap) {
+        failed = true;
+        break;
+      }
+      df g = df_div(df_sub(dd[l + 1], dd[l]), df_mul_f(ee[l], 2.f));
+      df r = hypot_df(g, df_from_float(1.f));
+      g = df_add(df_sub(dd[m], dd[l]), df_div(ee[l], g.hi >= 0.f ? df_add(g, r) : df_sub(g, r)));
+      df sn = df_from_float(1.f), c = df_from_float(1.f), p = df_from_float(0.f);
+      int lo = l;
+      bool under = false;
+      for (int i = m - 1; i >= l; --i) {
+        const df f = df_mul(sn, ee[i]), b = df_mul(c, ee[i]);
+        r = hypot_df(f, g);
+        ee[i + 1] = r;
+        if (r.hi == 0.f) {
+          dd[i + 1] = df_sub(dd[i + 1], p);
+          ee[m] = df_from_float(0.f);
+          under = true;
+          lo = i + 1;
+          break;
+        }
+        const df inv = df_div(df_from_float(1.f), r);
+        sn = df_mul(f, inv);
+        c = df_mul(g, inv);
+        g = df_sub(dd[i + 1], p);
+        r = df_add(df_mul(df_sub(dd[i], g), sn), df_mul_f(df_mul(c, b), 2.f));
+        p = df_mul(sn, r);
+        dd[i + 1] = df_add(g, p);
+        g = df_sub(df_mul(c, r), b);
+        rot[nrot++] = make_float4(c.hi, c.lo, sn.hi, sn.lo);
+      }
+      if (!under) {
+        dd[l] = df_sub(dd[l], p);
+        ee[l] = g;
+        ee[m] = df_from_float(0.f);
+      }
+      steps[nst++] = make_int2(m, lo);
+    }
+  }
+  for (int i = 0; i < n; ++i) gd[i] = df_val(dd[i]);
+  ws.nsteps[mat] = nst;
+  status[mat] = failed ? -1 : 0;
+}
+
+// part 0: the whole solver in one kernel (thread 0 runs the QL recurrence);
+// part 1: Householder reduction only, (d, e, tau) to the workspace;
+// part 2: eigenvectors from the workspace's rotation stream, back-
+// transformation and sort (after k_ql_df).
 template <typename R>
 __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, double *En_all,
-                                                       int *status, int n) {
+                                                       int *status, int n, int part, HeevWS ws) {
   typedef HeevAr<R> Ar;
   typedef typename Ar::C C;
   typedef typename Ar::Rot Rot;
@@ -503,6 +722,10 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   }
   if (tid == 0) ctl[3] = 0;
   if constexpr (!std::is_same<R, double>::value) {
+    if (part == 2) {
+      heev_vectors_from_stream<R>(A, Z, En, status, n, ws, mat, v, pw_, taus, d, rank);
+      return;
+    }
     // to the solver's format, element by element in place
     for (size_t q = tid; q < nn; q += NTH) {
       const zc z = A64[q];
@@ -573,6 +796,17 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   if (tid == 0) {
     d[n - 1] = Ar::to(A[(n - 1) + (size_t)(n - 1) * n]).re;
     e[n - 1] = 0.0;
+  }
+  if constexpr (!std::is_same<R, double>::value) {
+    if (part == 1) {
+      __syncthreads();
+      for (int i = tid; i < n; i += NTH) {
+        ws.d[(size_t)mat * n + i] = d[i];
+        ws.e[(size_t)mat * n + i] = e[i];
+        ws.tau[(size_t)mat * n + i] = taus[i];
+      }
+      return;
+    }
   }
   for (size_t q = tid; q < nn; q += NTH) {
     const int i = q % n, j = q / n;
@@ -714,17 +948,73 @@ size_t heev_smem(int n) {
          (size_t)2 * n * sizeof(double) + (8 + (size_t)n) * sizeof(int) + 64;
 }
 
+// Workspace of the split double-float route for nmat matrices of order n.
+namespace {
+inline size_t ws_align(size_t b) { return (b + 255) & ~(size_t)255; }
+inline int heev_rot_cap(int n) { return 3 * n * n + 64; }
+inline int heev_step_cap(int n) { return 8 * n + 64; }
+size_t heev_ws_per(int n) {
+  return (size_t)n * (2 * sizeof(double) + sizeof(dfc)) + (size_t)heev_rot_cap(n) * sizeof(float4) +
+         (size_t)heev_step_cap(n) * sizeof(int2) + sizeof(int);
+}
+}  // namespace
+
+size_t heev_ws_bytes(int n, int nmat) {
+  if (n <= 0 || nmat <= 0) return 0;
+  const size_t m = (size_t)nmat;
+  return ws_align(m * n * sizeof(double)) * 2 + ws_align(m * n * sizeof(dfc)) +
+         ws_align(m * heev_rot_cap(n) * sizeof(float4)) + ws_align(m * heev_step_cap(n) * sizeof(int2)) +
+         ws_align(m * sizeof(int));
+}
+
 // HU: in H, out U; V: scratch of the same size; status: positive on success,
 // negative when an eigenvalue did not converge.  double_float: the O(n^3)
-// parts in double-float arithmetic on the FP32 pipe (the mixed form).
-void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s, bool double_float) {
+// parts in double-float arithmetic on the FP32 pipe (the mixed form); with a
+// workspace (ws, ws_bytes >= heev_ws_bytes(n, 1)) the QL recurrence runs in
+// double-float too, split into three launches per group of matrices
+// (reduction, QL stream, vectors); without one, in FP64 inside k_heev.
+void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s, bool double_float,
+                void *ws, size_t ws_bytes) {
   const size_t smem = heev_smem(n);
+  const size_t nn = (size_t)n * n;
+  HeevWS w{};
   if (double_float) {
     cudaFuncSetAttribute(k_heev<df>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n);
+    int group = 0;
+    if (ws && nmat > 0) {
+      group = nmat;
+      while (group > 0 && heev_ws_bytes(n, group) > ws_bytes) group = std::max(0, group - std::max(1, group / 8));
+    }
+    if (group <= 0) {
+      k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w);
+      return;
+    }
+    const size_t g = (size_t)group;
+    unsigned char *p = static_cast<unsigned char *>(ws);
+    w.d = reinterpret_cast<double *>(p);
+    p += ws_align(g * n * sizeof(double));
+    w.e = reinterpret_cast<double *>(p);
+    p += ws_align(g * n * sizeof(double));
+    w.tau = reinterpret_cast<dfc *>(p);
+    p += ws_align(g * n * sizeof(dfc));
+    w.rot = reinterpret_cast<float4 *>(p);
+    p += ws_align(g * heev_rot_cap(n) * sizeof(float4));
+    w.steps = reinterpret_cast<int2 *>(p);
+    p += ws_align(g * heev_step_cap(n) * sizeof(int2));
+    w.nsteps = reinterpret_cast<int *>(p);
+    w.rot_cap = heev_rot_cap(n);
+    w.step_cap = heev_step_cap(n);
+    for (int m0 = 0; m0 < nmat; m0 += group) {
+      const int cnt = std::min(group, nmat - m0);
+      zc *H = HU + (size_t)m0 * nn;
+      zc *Z = V + (size_t)m0 * nn;
+      k_heev<df><<<cnt, HEEV_THREADS, smem, s>>>(H, Z, En + (size_t)m0 * n, status + m0, n, 1, w);
+      k_ql_df<<<cnt, 32, 2 * (size_t)n * sizeof(df), s>>>(w, status + m0, n);
+      k_heev<df><<<cnt, HEEV_THREADS, smem, s>>>(H, Z, En + (size_t)m0 * n, status + m0, n, 2, w);
+    }
   } else {
     cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n);
+    k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w);
   }
 }
 
