@@ -476,115 +476,212 @@ struct HeevWS {
   int rot_cap, step_cap;
 };
 
-// Eigenvectors of the split route (one CTA per matrix, all HEEV_THREADS
-// threads): Z = the product of the recorded QL rotations (each thread owns
-// one row of Z and streams every rotation over it, so no barrier is needed
-// between QL steps), then U = Q Z by the stored Householder vectors, then the
-// ascending sort.  A: the reduced matrix in double-float (Householder vectors
-// below the subdiagonal), left by part 1.
-template <typename R>
-__device__ void heev_vectors_from_stream(typename HeevAr<R>::C *A, typename HeevAr<R>::C *Z, double *En,
-                                         int *status, int n, const HeevWS &ws, int mat,
-                                         typename HeevAr<R>::C *v, typename HeevAr<R>::C *pw_,
-                                         typename HeevAr<R>::C *taus, double *d, int *rank) {
-  typedef HeevAr<R> Ar;
-  typedef typename Ar::C C;
-  typedef typename Ar::Rot Rot;
-  constexpr int NTH = HEEV_THREADS;
-  const int tid = threadIdx.x;
-  const size_t nn = (size_t)n * n;
-  for (int i = tid; i < n; i += NTH) {
-    d[i] = ws.d[(size_t)mat * n + i];
-    taus[i] = ws.tau[(size_t)mat * n + i];
-  }
-  for (size_t q = tid; q < nn; q += NTH) {
-    const int i = q % n, j = q / n;
-    Z[q] = i == j ? Ar::one() : Ar::zero();
-  }
-  __syncthreads();
+// ---- eigenvectors of the split route: Z = product of the recorded QL
+// rotations, U = Q Z, then the ascending sort (three launches after k_ql_df).
+//
+// Rotation (s, i) of QL step s replaces columns (i, i+1) of every row z of Z by
+// (c z_i - s z_{i+1}, s z_i + c z_{i+1}).  Rows are independent: one thread per
+// row.  Step s+1 may rotate columns (i, i+1) as soon as step s has finished
+// every rotation touching column i, i.e. its rotation i-1, so ROT_K consecutive
+// steps run as a wavefront with a lag of two columns: at time c step k applies
+// its rotation i = c + 2k, and the ROT_K rotations of one time touch disjoint
+// column pairs inside the window [c, c + 2 ROT_K - 1], which lives in
+// registers.  Each pass over the row therefore applies ROT_K steps while
+// reading and writing every column once (the column-by-column form streams the
+// whole of Z from memory once per step).  A step with no rotation at some time
+// applies the identity (c = 1, s = 0, exact in double-float), so the body of a
+// time is straight-line code.
+constexpr int ROT_ROWS = 128;   // rows (threads) per CTA
+constexpr int ROT_K = 8;        // QL steps per pass
+
+// a b + c d in double-float (products formed exactly by FMA, one
+// normalisation)
+__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+  const float p1 = a.hi * b.hi;
+  float e1 = fmaf(a.hi, b.hi, -p1);
+  e1 = fmaf(a.hi, b.lo, e1);
+  e1 = fmaf(a.lo, b.hi, e1);
+  const float p2 = c.hi * d.hi;
+  float e2 = fmaf(c.hi, d.hi, -p2);
+  e2 = fmaf(c.hi, d.lo, e2);
+  e2 = fmaf(c.lo, d.hi, e2);
+  float sh, sl;
+  two_sum(p1, p2, sh, sl);
+  sl += e1 + e2;
+  float h, l;
+  fast_two_sum(sh, sl, h, l);
+  return mkdf(h, l);
+}
+// (y, x) <- (c y - s x, s y + c x)
+__device__ __forceinline__ void rot_df(dfc &y, dfc &x, df c, df sn) {
+  const df nsn = df_neg(sn);
+  const dfc hi = {df_dot2(sn, y.re, c, x.re), df_dot2(sn, y.im, c, x.im)};
+  const dfc lo = {df_dot2(c, y.re, nsn, x.re), df_dot2(c, y.im, nsn, x.im)};
+  x = hi;
+  y = lo;
+}
+
+// grid (ceil(n / ROT_ROWS), nmat); Z (n x n per matrix, column-major,
+// double-float) is written from the identity.
+__global__ void __launch_bounds__(ROT_ROWS) k_rot_apply(HeevWS ws, dfc *Z_all, int *status, int n) {
+  constexpr int W2 = 2 * ROT_K;
+  __shared__ int sm_m[ROT_K], sm_lo[ROT_K], sm_r0[ROT_K];
+  const int mat = blockIdx.y;
+  const int row = blockIdx.x * ROT_ROWS + threadIdx.x;
+  const bool act = row < n;
+  dfc *Z = Z_all + (size_t)mat * n * n;
   const int nst = min(max(ws.nsteps[mat], 0), ws.step_cap);
   const int2 *steps = ws.steps + (size_t)mat * ws.step_cap;
   const float4 *rot = ws.rot + (size_t)mat * ws.rot_cap;
+  dfc zero = czero<df>(), one = zero;
+  one.re.hi = 1.f;
+  if (act)
+    for (int j = 0; j < n; ++j) Z[row + (size_t)j * n] = j == row ? one : zero;
+  int r0 = 0;          // thread 0: rotations of the steps before this pass
   bool bad = false;
-  for (int row = tid; row < n; row += NTH) {
-    int r0 = 0;
-    for (int st = 0; st < nst; ++st) {
-      const int2 ml = steps[st];
-      const int m = ml.x, lo = ml.y, cnt = m - lo;
-      // a step outside the matrix or the stream cannot come from k_ql_df;
-      // it is recorded, not followed
-      if (m >= n || lo < 0 || cnt < 0 || r0 + cnt > ws.rot_cap) {
-        bad = true;
-        break;
-      }
-      if (cnt == 0) continue;
-      C x = Z[row + (size_t)m * n];
-      C y = Z[row + (size_t)(m - 1) * n];
-      for (int t = 0; t < cnt; ++t) {
-        const int i = m - 1 - t;
-        const C ynext = (t + 1 < cnt) ? Z[row + (size_t)(i - 1) * n] : y;   // issued ahead of the chain
-        const float4 q = rot[r0 + t];
-        Rot c, sn;
-        if constexpr (std::is_same<R, double>::value) {
-          c = (double)q.x + (double)q.y;
-          sn = (double)q.z + (double)q.w;
-        } else {
-          c = mkdf(q.x, q.y);
-          sn = mkdf(q.z, q.w);
+  for (int s0 = 0; s0 < nst; s0 += ROT_K) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < ROT_K; ++k) {
+        int m = 0, lo = 0;
+        if (s0 + k < nst) {
+          const int2 ml = steps[s0 + k];
+          m = ml.x;
+          lo = ml.y;
+          // a step outside the matrix or the stream cannot come from k_ql_df;
+          // it is recorded, not followed
+          if (m >= n || lo < 0 || lo > m || r0 + (m - lo) > ws.rot_cap) {
+            bad = true;
+            m = lo = 0;
+          }
         }
-        C hi, lo_;
-        Ar::rot(y, x, c, sn, hi, lo_);
-        Z[row + (size_t)(i + 1) * n] = hi;
-        x = lo_;
-        y = ynext;
+        sm_m[k] = m;
+        sm_lo[k] = lo;
+        sm_r0[k] = r0;
+        r0 += m - lo;
       }
-      Z[row + (size_t)lo * n] = x;
-      r0 += cnt;
+    }
+    __syncthreads();
+    int mk[ROT_K], lk[ROT_K], rk[ROT_K];
+    int c_hi = -(1 << 30), c_lo = 1 << 30;
+#pragma unroll
+    for (int k = 0; k < ROT_K; ++k) {
+      mk[k] = sm_m[k];
+      lk[k] = sm_lo[k];
+      rk[k] = sm_r0[k] + sm_m[k] - 1;   // stream index of rotation i: rk - i
+      if (mk[k] > lk[k]) {
+        c_hi = max(c_hi, mk[k] - 1 - 2 * k);
+        c_lo = min(c_lo, lk[k] - 2 * k);
+      }
+    }
+    if (!act || c_hi < c_lo) continue;
+    // w[q] holds column c + q at time c; columns outside [0, n) are never
+    // rotated (every rotated column lies in [lo_k, m_k] of its step)
+    dfc w[W2];
+#pragma unroll
+    for (int q = 0; q < W2; ++q) {
+      const int cc = c_hi + q;
+      w[q] = cc >= 0 && cc < n ? Z[row + (size_t)cc * n] : zero;
+    }
+    dfc nxt = c_hi - 1 >= 0 ? Z[row + (size_t)(c_hi - 1) * n] : zero;
+    for (int c = c_hi;; --c) {
+#pragma unroll
+      for (int k = 0; k < ROT_K; ++k) {
+        const int i = c + 2 * k;
+        const bool on = i >= lk[k] && i < mk[k];
+        const float4 q = on ? rot[rk[k] - i] : make_float4(1.f, 0.f, 0.f, 0.f);
+        rot_df(w[2 * k], w[2 * k + 1], mkdf(q.x, q.y), mkdf(q.z, q.w));
+      }
+      if (c == c_lo) break;
+      // column c + W2 - 1 leaves the window, column c - 1 enters
+      if (c + W2 - 1 < n) Z[row + (size_t)(c + W2 - 1) * n] = w[W2 - 1];
+#pragma unroll
+      for (int q = W2 - 1; q > 0; --q) w[q] = w[q - 1];
+      w[0] = nxt;
+      if (c - 2 >= 0) nxt = Z[row + (size_t)(c - 2) * n];
+    }
+#pragma unroll
+    for (int q = 0; q < W2; ++q) {
+      const int cc = c_lo + q;
+      if (cc >= 0 && cc < n) Z[row + (size_t)cc * n] = w[q];
     }
   }
   if (bad) status[mat] = -1;
-  __syncthreads();
-  // back-transformation U = Q Z (Q_{n-2} first)
-  const int warp = tid >> 5, lane = tid & 31;
+}
+
+// U = Q Z by the stored Householder vectors (Q_{n-2} applied first): one warp
+// per BT_COLS columns of Z, held in shared memory (each loaded Householder
+// element serves all of them, and their reductions interleave); Householder
+// vector k is column k of the reduced matrix A below the subdiagonal (unit
+// leading element implied).  The result goes back to Z's columns (FP64
+// complex in place of the double-float element, both 16 bytes).
+constexpr int BT_WARPS = 4, BT_COLS = 2;
+__global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(const dfc *A_all, dfc *Z_all, HeevWS ws, int n) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  typedef HeevAr<df> Ar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mat = blockIdx.y, j0 = (blockIdx.x * BT_WARPS + warp) * BT_COLS;
+  if (j0 >= n) return;
+  const int ncol = min(BT_COLS, n - j0);
+  const size_t nn = (size_t)n * n;
+  const dfc *A = A_all + mat * nn;
+  dfc *Zc = Z_all + mat * nn + (size_t)j0 * n;
+  dfc *z = reinterpret_cast<dfc *>(smraw) + (size_t)warp * BT_COLS * n;   // z[i + c n]
+  const dfc *tau_m = ws.tau + (size_t)mat * n;
+  for (int q = lane; q < ncol * n; q += 32) z[q] = Zc[q];
+  for (int q = ncol * n + lane; q < BT_COLS * n; q += 32) z[q] = Ar::zero();   // a missing last column
+  __syncwarp();
   for (int k = n - 2; k >= 0; --k) {
-    const C tau = taus[k];
+    const dfc tau = tau_m[k];
     if (Ar::is_zero(tau)) continue;
-    const int m = n - k - 1;
-    const C *x = A + (k + 1) + (size_t)k * n;
-    for (int i = tid; i < m; i += NTH) v[i] = i == 0 ? Ar::one() : x[i];
-    __syncthreads();
-    C *Zk = Z + (k + 1);
-    for (int j = warp; j < n; j += NTH / 32) {
-      C acc = Ar::zero();
-      for (int i = lane; i < m; i += 32) Ar::jfma(acc, v[i], Zk[i + (size_t)j * n]);
-      Ar::renorm(acc);
-      for (int off = 16; off > 0; off >>= 1) acc = Ar::add(acc, Ar::shfl_down(acc, off));
-      if (lane == 0) pw_[j] = Ar::mul(tau, acc);
+    const dfc *x = A + (size_t)k * n;   // v_r = x[r] for r > k + 1, v_{k+1} = 1
+    dfc acc[BT_COLS];
+#pragma unroll
+    for (int c = 0; c < BT_COLS; ++c) acc[c] = Ar::zero();
+    for (int r = k + 1 + lane; r < n; r += 32) {
+      const dfc v = r == k + 1 ? Ar::one() : x[r];
+#pragma unroll
+      for (int c = 0; c < BT_COLS; ++c) Ar::jfma(acc[c], v, z[r + c * n]);
     }
-    __syncthreads();
-    for (size_t q = tid; q < (size_t)m * n; q += NTH) {
-      const int i = q % m, j = q / m;
-      Zk[i + (size_t)j * n] = Ar::sub_mul(Zk[i + (size_t)j * n], v[i], pw_[j]);
+    dfc p[BT_COLS];
+#pragma unroll
+    for (int c = 0; c < BT_COLS; ++c) {
+      Ar::renorm(acc[c]);
+      for (int off = 16; off > 0; off >>= 1) acc[c] = Ar::add(acc[c], Ar::shfl_down(acc[c], off));
+      acc[c] = Ar::mul(tau, acc[c]);
+      p[c] = {mkdf(__shfl_sync(0xffffffffu, acc[c].re.hi, 0), __shfl_sync(0xffffffffu, acc[c].re.lo, 0)),
+              mkdf(__shfl_sync(0xffffffffu, acc[c].im.hi, 0), __shfl_sync(0xffffffffu, acc[c].im.lo, 0))};
     }
-    __syncthreads();
+    for (int r = k + 1 + lane; r < n; r += 32) {
+      const dfc v = r == k + 1 ? Ar::one() : x[r];
+#pragma unroll
+      for (int c = 0; c < BT_COLS; ++c) z[r + c * n] = Ar::sub_mul(z[r + c * n], v, p[c]);
+    }
+    __syncwarp();
   }
-  // ascending order (ties by index), back to FP64 storage (A is reused: its
-  // double-float contents are no longer needed)
-  zc *A64 = reinterpret_cast<zc *>(A);
-  for (int i = tid; i < n; i += NTH) {
-    const double li = d[i];
-    int r = 0;
-    for (int j = 0; j < n; ++j) r += (d[j] < li) || (d[j] == li && j < i);
-    rank[i] = r;
-    En[r] = li;
-  }
-  __syncthreads();
-  for (size_t q = tid; q < nn; q += NTH) {
-    const int i = q % n, j = q / n;
-    A64[i + (size_t)rank[j] * n] = Ar::to(Z[q]);
-  }
-  __syncthreads();
-  if (tid == 0 && status[mat] >= 0) status[mat] = 1;
+  zc *out = reinterpret_cast<zc *>(Zc);
+  for (int q = lane; q < ncol * n; q += 32) out[q] = Ar::to(z[q]);
+}
+
+// Ascending eigenvalues (ties by index) and the matching columns into HU and
+// En; the last launch of the split route, so it also completes the status.
+__global__ void __launch_bounds__(256) k_eig_sort(const zc *U_all, zc *HU_all, double *En_all, const double *d_all,
+                                                 int *status, int n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mat = blockIdx.y, j = blockIdx.x * 8 + warp;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && status[mat] >= 0) status[mat] = 1;
+  if (j >= n) return;
+  const size_t nn = (size_t)n * n;
+  const double *d = d_all + (size_t)mat * n;
+  const double lj = d[j];
+  int r = 0;
+  for (int i = lane; i < n; i += 32) r += (d[i] < lj) || (d[i] == lj && i < j);
+  for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+  r = __shfl_sync(0xffffffffu, r, 0);
+  if (lane == 0) En_all[(size_t)mat * n + r] = lj;
+  const zc *src = U_all + mat * nn + (size_t)j * n;
+  zc *dst = HU_all + mat * nn + (size_t)r * n;
+  for (int i = lane; i < n; i += 32) dst[i] = src[i];
 }
 
 // The QL recurrence of the split route in double-float on the FP32 pipe, one
@@ -678,9 +775,9 @@ __global__ void __launch_bounds__(32) k_ql_df(HeevWS ws, int *status, int n) {
 }
 
 // part 0: the whole solver in one kernel (thread 0 runs the QL recurrence);
-// part 1: Householder reduction only, (d, e, tau) to the workspace;
-// part 2: eigenvectors from the workspace's rotation stream, back-
-// transformation and sort (after k_ql_df).
+// part 1: Householder reduction only, (d, e, tau) to the workspace (the
+// split route continues with k_ql_df, k_rot_apply, k_backtransform and
+// k_eig_sort).
 template <typename R>
 __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, double *En_all,
                                                        int *status, int n, int part, HeevWS ws) {
@@ -722,10 +819,6 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   }
   if (tid == 0) ctl[3] = 0;
   if constexpr (!std::is_same<R, double>::value) {
-    if (part == 2) {
-      heev_vectors_from_stream<R>(A, Z, En, status, n, ws, mat, v, pw_, taus, d, rank);
-      return;
-    }
     // to the solver's format, element by element in place
     for (size_t q = tid; q < nn; q += NTH) {
       const zc z = A64[q];
@@ -990,6 +1083,8 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
       return;
     }
     const size_t g = (size_t)group;
+    const size_t bt_smem = (size_t)BT_WARPS * BT_COLS * n * sizeof(dfc);
+    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem);
     unsigned char *p = static_cast<unsigned char *>(ws);
     w.d = reinterpret_cast<double *>(p);
     p += ws_align(g * n * sizeof(double));
@@ -1010,7 +1105,11 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
       zc *Z = V + (size_t)m0 * nn;
       k_heev<df><<<cnt, HEEV_THREADS, smem, s>>>(H, Z, En + (size_t)m0 * n, status + m0, n, 1, w);
       k_ql_df<<<cnt, 32, 2 * (size_t)n * sizeof(df), s>>>(w, status + m0, n);
-      k_heev<df><<<cnt, HEEV_THREADS, smem, s>>>(H, Z, En + (size_t)m0 * n, status + m0, n, 2, w);
+      k_rot_apply<<<dim3((n + ROT_ROWS - 1) / ROT_ROWS, cnt), ROT_ROWS, 0, s>>>(w, reinterpret_cast<dfc *>(Z),
+                                                                               status + m0, n);
+      k_backtransform<<<dim3((n + BT_WARPS * BT_COLS - 1) / (BT_WARPS * BT_COLS), cnt), BT_WARPS * 32, bt_smem, s>>>(
+          reinterpret_cast<const dfc *>(H), reinterpret_cast<dfc *>(Z), w, n);
+      k_eig_sort<<<dim3((n + 7) / 8, cnt), 256, 0, s>>>(Z, H, En + (size_t)m0 * n, w.d, status + m0, n);
     }
   } else {
     cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
