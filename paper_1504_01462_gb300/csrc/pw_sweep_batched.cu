@@ -194,19 +194,24 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
   // B(l, j) from the transposed FP32 copy (consecutive j contiguous for fixed l:
   // one column per thread, coalesced across the warp) when the k-set has one
   const cc *Ot = (a.O32t && !tr) ? a.O32t + ((size_t)d.o_off + p) * n * n : nullptr;
-  const bool ok = tc::cgemm_tile<false>(
+  const bool ok = tc::cgemm_tile<false, false>(
       n, 2 * n, n, r0, c0, [=](int i, int l) { return R[i + (size_t)l * n]; },
       [=](int l, int j) {
         if (Ot) return j < n ? pqt(Ot, n, l, j, v, -1.f) : pqt(Ot, n, l, j - n, v, 1.f);
         return j < n ? pqb<float>(O, O32, n, l, j, v, -1.f, tr) : pqb<float>(O, O32, n, l, j - n, v, 1.f, tr);
       },
-      [=](int i, int j, cc acc) {
+      [=](int, int) { return czero<float>(); },
+      [=](int i, int j, cc acc, cc) {
         if (j < n) M[i + (size_t)j * n] = csub(pqb<float>(O, O32, n, i, j, v, 1.f, tr), acc);
         else M[i + (size_t)j * n] = csub(acc, pqb<float>(O, O32, n, i, j - n, v, -1.f, tr));
       },
       smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
+
+// Tile width of the update kernels (read-modify-write of C): 64 complex
+// columns keep the prefetched C values of a thread in 32 registers.
+constexpr int RMW_TN = 64;
 
 // trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb)
 __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j0) {
@@ -217,17 +222,14 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
   const int nb = min(Tile<float, 256>::NB, n - j0), c0 = j0 + nb;
   const int m = n - c0, ncol = ncols - c0;
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
-  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
   if (q0 >= ncol) return;
   cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
-  const bool ok = tc::cgemm_tile<true>(
+  const bool ok = tc::cgemm_tile<true, true, RMW_TN>(
       m, ncol, nb, r0, q0, [=](int i, int l) { return M[c0 + i + (size_t)(j0 + l) * n]; },
       [=](int l, int j) { return M[j0 + l + (size_t)(c0 + j) * n]; },
-      [=](int i, int j, cc acc) {
-        cc &x = M[c0 + i + (size_t)(c0 + j) * n];
-        x = csub(x, acc);
-      },
-      smraw);
+      [=](int i, int j) { return M[c0 + i + (size_t)(c0 + j) * n]; },
+      [=](int i, int j, cc acc, cc old) { M[c0 + i + (size_t)(c0 + j) * n] = csub(old, acc); }, smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
@@ -240,17 +242,14 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j
   const int nb = min(Tile<float, 256>::NB, n - j0);
   const int m = j0, ncol = ncols - n;
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
-  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
   if (q0 >= ncol) return;
   cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
-  const bool ok = tc::cgemm_tile<true>(
+  const bool ok = tc::cgemm_tile<true, true, RMW_TN>(
       m, ncol, nb, r0, q0, [=](int i, int l) { return M[i + (size_t)(j0 + l) * n]; },
       [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
-      [=](int i, int j, cc acc) {
-        cc &x = M[i + (size_t)(n + j) * n];
-        x = csub(x, acc);
-      },
-      smraw);
+      [=](int i, int j) { return M[i + (size_t)(n + j) * n]; },
+      [=](int i, int j, cc acc, cc old) { M[i + (size_t)(n + j) * n] = csub(old, acc); }, smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
@@ -425,8 +424,8 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     const int c0 = j0 + min(NB, n - j0);
     if (c0 < n) {
       if (std::is_same<T, float>::value && tensor_core)
-        kb_trail_tc<<<dim3(tiles(n - c0, ncols - c0, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes(), s>>>(a, j0);
+        kb_trail_tc<<<dim3(tiles(n - c0, ncols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
       else
         kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
     }
@@ -436,8 +435,8 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
     if (j0 > 0) {
       if (std::is_same<T, float>::value && tensor_core)
-        kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes(), s>>>(a, j0);
+        kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
       else
         kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
     }
@@ -478,9 +477,9 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_wy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wy_tc_smem_bytes(n));
   if (e == cudaSuccess && (variant & 2))
-    e = cudaFuncSetAttribute(kb_trail_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes());
+    e = cudaFuncSetAttribute(kb_trail_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
-    e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes());
+    e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   return e;
 }
 

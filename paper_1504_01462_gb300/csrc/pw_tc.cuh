@@ -121,6 +121,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 TMEM lanes x 8 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Round to TF32 (10 explicit mantissa bits), nearest with ties away.
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
@@ -155,9 +167,14 @@ __host__ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int r
 constexpr int CG_THREADS = 256;
 constexpr int CG_M = 128, CG_N = 128, CG_KC = 8;   // real rows, complex columns, complex K per stage
 constexpr int CG_AB = CG_M * 2 * CG_KC * 4;        // bytes of one A' part (hi or lo) per stage
-constexpr int CG_BB = CG_N * 2 * CG_KC * 4;        // bytes of one B' part per stage
-constexpr int CG_STAGE = 2 * CG_AB + 2 * CG_BB;
-__host__ __device__ constexpr size_t cg_smem_bytes() { return 2 * (size_t)CG_STAGE + 64; }
+// bytes of one B' part per stage, of one stage, of the tile's shared memory
+// for TN complex columns (64 or 128)
+template <int TN>
+__host__ __device__ constexpr int cg_bb() { return TN * 2 * CG_KC * 4; }
+template <int TN>
+__host__ __device__ constexpr int cg_stage() { return 2 * CG_AB + 2 * cg_bb<TN>(); }
+template <int TN = CG_N>
+__host__ __device__ constexpr size_t cg_smem_bytes() { return 2 * (size_t)cg_stage<TN>() + 64; }
 
 // Four values as TF32 hi parts and FP32 remainders, one 16-byte store each.
 __device__ __forceinline__ void store_split(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, float a,
@@ -167,16 +184,105 @@ __device__ __forceinline__ void store_split(unsigned char *hi_base, unsigned cha
   *reinterpret_cast<float4 *>(lo_base + off) = make_float4(a - h.x, b - h.y, c - h.z, d - h.w);
 }
 
+// Operands of one K stage as this thread loads them (the staging is
+// software-pipelined: the loads of stage s+1 are in flight while stage s is
+// split into shared memory and multiplied).
+struct CgStage {
+  cc a0, a1;   // A task: complex (r, l), (r, l+1)
+  cc b[4];     // B tasks
+};
+static_assert((CG_M / 2) * (CG_KC / 2) == CG_THREADS, "one A task per thread and stage");
+
+// The tile is 64 complex rows x TN complex columns (TN = 64 or 128).
 // B_RUNS: fb(l .. l+3, j) lie contiguously in memory for fixed j (one thread
 // reads the run); otherwise consecutive j are contiguous for fixed l (one
 // thread per column, consecutive threads on consecutive columns).
-template <bool B_RUNS, class FA, class FB, class FE>
-__device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb, FE fe, unsigned char *smem) {
+// RMW: the result updates an existing C; fc(i, j) reads it, and the reads of
+// this thread's results are issued before the first stage so that they are in
+// flight during the whole product.  fe(i, j, acc, c) receives the old value c
+// (zero when !RMW).
+template <bool B_RUNS, bool RMW, int TN = CG_N, class FA, class FB, class FC, class FE>
+__device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb, FC fc, FE fe,
+                           unsigned char *smem) {
+  static_assert(TN == 64 || TN == 128, "tile width");
+  constexpr int BB = cg_bb<TN>(), STAGE = cg_stage<TN>();
+  constexpr int BTASKS = B_RUNS ? TN * 2 : TN * (CG_KC / 2);   // B tasks per stage
+  constexpr int BPER = (BTASKS + CG_THREADS - 1) / CG_THREADS;  // per thread
+  static_assert(BPER * (B_RUNS ? 4 : 2) <= 4, "B staging registers");
+  constexpr int NCH = TN / 16;                                  // 8-column chunks per warp
   unsigned char *stage0 = smem;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * CG_STAGE);   // [2]
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);   // [2]
   uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tmem_alloc(slot, CG_N);
+  const cc zero = czero<float>();
+  auto load = [&](int s, CgStage &t) {
+    const int l0 = s * CG_KC;
+    {
+      const int rr = tid % (CG_M / 2), lp = tid / (CG_M / 2);
+      const int r = r0 + rr, l = l0 + 2 * lp;
+      t.a0 = (r < m && l < k) ? fa(r, l) : zero;
+      t.a1 = (r < m && l + 1 < k) ? fa(r, l + 1) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < BPER; ++u) {
+      const int e = tid + u * CG_THREADS;
+      if (e >= BTASKS) break;
+      if (B_RUNS) {
+        const int jj = e % TN, half = e / TN;
+        const int j = c0 + jj, l = l0 + 4 * half;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t.b[q] = (l + q < k && j < ncol) ? fb(l + q, j) : zero;
+      } else {
+        const int jj = e % TN, lp = e / TN;
+        const int j = c0 + jj, l = l0 + 2 * lp;
+        t.b[2 * u] = (l < k && j < ncol) ? fb(l, j) : zero;
+        t.b[2 * u + 1] = (l + 1 < k && j < ncol) ? fb(l + 1, j) : zero;
+      }
+    }
+  };
+  auto store = [&](unsigned char *Ahi, unsigned char *Alo, unsigned char *Bhi, unsigned char *Blo,
+                   const CgStage &t) {
+    {
+      // A': complex (r, l), (r, l+1) -> real rows 2r, 2r+1, one 16-byte chunk each
+      const int rr = tid % (CG_M / 2), lp = tid / (CG_M / 2);
+      store_split(Ahi, Alo, kmajor_offset(2 * rr, 4 * lp, CG_M), t.a0.re, -t.a0.im, t.a1.re, -t.a1.im);
+      store_split(Ahi, Alo, kmajor_offset(2 * rr + 1, 4 * lp, CG_M), t.a0.im, t.a0.re, t.a1.im, t.a1.re);
+    }
+#pragma unroll
+    for (int u = 0; u < BPER; ++u) {
+      const int e = tid + u * CG_THREADS;
+      if (e >= BTASKS) break;
+      if (B_RUNS) {
+        const int jj = e % TN, half = e / TN;
+        store_split(Bhi, Blo, kmajor_offset(jj, 8 * half, TN), t.b[0].re, t.b[0].im, t.b[1].re, t.b[1].im);
+        store_split(Bhi, Blo, kmajor_offset(jj, 8 * half + 4, TN), t.b[2].re, t.b[2].im, t.b[3].re, t.b[3].im);
+      } else {
+        const int jj = e % TN, lp = e / TN;
+        store_split(Bhi, Blo, kmajor_offset(jj, 4 * lp, TN), t.b[2 * u].re, t.b[2 * u].im, t.b[2 * u + 1].re,
+                    t.b[2 * u + 1].im);
+      }
+    }
+  };
+  // epilogue mapping: warp w reads TMEM lanes 32 (w % 4) .. (real rows) and
+  // complex columns (TN / 2) (w / 4) .. + TN / 2 in chunks of 8; of a lane
+  // pair (real and imaginary row of one complex row) the real-row lane writes
+  // columns 0 .. 3 of each chunk, the imaginary-row lane 4 .. 7
+  const int lrow = 32 * (warp & 3) + lane;
+  const int er = r0 + (lrow >> 1), eim = lrow & 1;
+  auto ecol = [&](int q) { return c0 + (TN / 2) * (warp >> 2) + 8 * q + (eim ? 4 : 0); };
+  CgStage cur;
+  load(0, cur);
+  cc cold[RMW ? NCH : 1][4];
+  if constexpr (RMW) {
+#pragma unroll
+    for (int q = 0; q < NCH; ++q)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = ecol(q) + i;
+        cold[q][i] = (er < m && j < ncol) ? fc(er, j) : zero;
+      }
+  }
+  if (warp == 0) tmem_alloc(slot, TN);
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -189,52 +295,23 @@ __device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb,
   bool ok = true;
   for (int s = 0; s < nstage; ++s) {
     const int b = s & 1;
-    unsigned char *Ahi = stage0 + b * CG_STAGE, *Alo = Ahi + CG_AB;
-    unsigned char *Bhi = Alo + CG_AB, *Blo = Bhi + CG_BB;
+    unsigned char *Ahi = stage0 + b * STAGE, *Alo = Ahi + CG_AB;
+    unsigned char *Bhi = Alo + CG_AB, *Blo = Bhi + BB;
     if (s >= 2) ok = mbar_wait(&mbar[b], ((s - 2) >> 1) & 1) && ok;   // buffer b is free again
-    const int l0 = s * CG_KC;
-    // A': one task = complex (r, l), (r, l+1) -> rows 2r, 2r+1, one 16-byte chunk each
-    for (int e = tid; e < (CG_M / 2) * (CG_KC / 2); e += CG_THREADS) {
-      const int rr = e % (CG_M / 2), lp = e / (CG_M / 2);
-      const int r = r0 + rr, l = l0 + 2 * lp;
-      const cc z0 = (r < m && l < k) ? fa(r, l) : czero<float>();
-      const cc z1 = (r < m && l + 1 < k) ? fa(r, l + 1) : czero<float>();
-      store_split(Ahi, Alo, kmajor_offset(2 * rr, 4 * lp, CG_M), z0.re, -z0.im, z1.re, -z1.im);
-      store_split(Ahi, Alo, kmajor_offset(2 * rr + 1, 4 * lp, CG_M), z0.im, z0.re, z1.im, z1.re);
-    }
-    if (B_RUNS) {
-      // B': one task = column j, complex l .. l+3 (a contiguous run in the source)
-      for (int e = tid; e < CG_N * 2; e += CG_THREADS) {
-        const int jj = e % CG_N, half = e / CG_N;
-        const int j = c0 + jj, l = l0 + 4 * half;
-        cc z[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) z[q] = (l + q < k && j < ncol) ? fb(l + q, j) : czero<float>();
-        store_split(Bhi, Blo, kmajor_offset(jj, 8 * half, CG_N), z[0].re, z[0].im, z[1].re, z[1].im);
-        store_split(Bhi, Blo, kmajor_offset(jj, 8 * half + 4, CG_N), z[2].re, z[2].im, z[3].re, z[3].im);
-      }
-    } else {
-      // B': one task = complex (l, j), (l+1, j) -> row j, one 16-byte chunk
-      for (int e = tid; e < CG_N * (CG_KC / 2); e += CG_THREADS) {
-        const int jj = e % CG_N, lp = e / CG_N;
-        const int j = c0 + jj, l = l0 + 2 * lp;
-        const cc z0 = (l < k && j < ncol) ? fb(l, j) : czero<float>();
-        const cc z1 = (l + 1 < k && j < ncol) ? fb(l + 1, j) : czero<float>();
-        store_split(Bhi, Blo, kmajor_offset(jj, 4 * lp, CG_N), z0.re, z0.im, z1.re, z1.im);
-      }
-    }
+    store(Ahi, Alo, Bhi, Blo, cur);
+    if (s + 1 < nstage) load(s + 1, cur);
     fence_smem_to_async();
     fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-      constexpr uint32_t idesc = idesc_tf32(CG_M, CG_N);
+      constexpr uint32_t idesc = idesc_tf32(CG_M, TN);
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
         const uint64_t ah = smem_desc(Ahi + ks * CG_M * 32, 128, 256);
         const uint64_t al = smem_desc(Alo + ks * CG_M * 32, 128, 256);
-        const uint64_t bh = smem_desc(Bhi + ks * CG_N * 32, 128, 256);
-        const uint64_t bl = smem_desc(Blo + ks * CG_N * 32, 128, 256);
+        const uint64_t bh = smem_desc(Bhi + ks * TN * 32, 128, 256);
+        const uint64_t bl = smem_desc(Blo + ks * TN * 32, 128, 256);
         mma_tf32(tmem, ah, bh, idesc, (s > 0 || ks > 0) ? 1u : 0u);
         mma_tf32(tmem, ah, bl, idesc, 1u);
         mma_tf32(tmem, al, bh, idesc, 1u);
@@ -246,34 +323,23 @@ __device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb,
   ok = mbar_wait(&mbar[(nstage - 1) & 1], ((nstage - 1) >> 1) & 1) && ok;
   fence_after_sync();
   if (ok) {
-    // warp w: TMEM lanes 32 (w % 4) .. (real rows), complex columns 64 (w / 4) .. + 64
-    const int lrow = 32 * (warp & 3) + lane;
-    const int r = r0 + (lrow >> 1), im = lrow & 1;
-    for (int cb = 0; cb < 64; cb += 16) {
-      const int cbase = 64 * (warp >> 2) + cb;
-      float vv[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cbase, vv);
-      float other[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) other[i] = __shfl_xor_sync(0xffffffffu, vv[i], 1);
-      // the real-row lane writes columns cbase .. +7, the imaginary-row lane +8 .. +15
-      cc accs[8];
-      if (im) {
+    for (int q = 0; q < NCH; ++q) {
+      float vv[8], other[8];
+      tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((TN / 2) * (warp >> 2) + 8 * q), vv);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) accs[i] = mkc<float>(other[i + 8], vv[i + 8]);
-      } else {
+      for (int i = 0; i < 8; ++i) other[i] = __shfl_xor_sync(0xffffffffu, vv[i], 1);
+      const int jb = ecol(q);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) accs[i] = mkc<float>(vv[i], other[i]);
+      for (int i = 0; i < 4; ++i) {
+        const cc acc = eim ? mkc<float>(other[i + 4], vv[i + 4]) : mkc<float>(vv[i], other[i]);
+        if (er < m && jb + i < ncol) fe(er, jb + i, acc, RMW ? cold[RMW ? q : 0][i] : zero);
       }
-      const int jb = c0 + cbase + (im ? 8 : 0);
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (r < m && jb + i < ncol) fe(r, jb + i, accs[i]);
     }
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, CG_N);
+  if (warp == 0) tmem_dealloc(tmem, TN);
   return ok;
 }
 
