@@ -381,6 +381,10 @@ def main():
         nq = N + 2
         fp64_peak = 1.25
         fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+        # per k-set: Hamiltonians, the eigensolver (five launches in double-float: reduction,
+        # QL stream, rotations, back-transformation, sort; one in FP64), overlaps, and the
+        # mixed form's FP32 copies of the overlaps (plain and transposed)
+        modes_launches = 1 + (5 if prec == pw.MIXED_FP32 else 1) + 1 + (2 if prec == pw.MIXED_FP32 else 0)
         # eigensolver launch: one per step, nq matrices
         heev_ms = prof["modes_ms"] / max(prof["modes_stages"], 1)
         heev_flops = nq * heev_flops_per_matrix(n)
@@ -401,7 +405,8 @@ def main():
         # instruction, so its ceiling is the FP32 rate / 12 in algorithmic flops
         heev_peak = fp32_peak / 12.0 if prec == pw.MIXED_FP32 else fp64_peak
         heev_obj = {"bound": "alu",
-                    "kernel": ("k_heev<df> (double-float Householder + QL, one launch per step)"
+                    "kernel": ("k_heev<df> + k_ql_df + k_rot_apply + k_backtransform + k_eig_sort "
+                               "(double-float eigensolver, five launches per step)"
                                if prec == pw.MIXED_FP32 else
                                "k_heev<double> (FP64 Householder + QL, one launch per step)"),
                     "achieved": heev_ach, "peak": heev_peak, "unit": "TFLOP/s",
@@ -442,7 +447,7 @@ def main():
                          "vs_fp64_gpu_sample": accuracy_vs_fp64,
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
-            "gpu_launches": int(prof["sweep_launches"] + 3 * prof["modes_stages"]
+            "gpu_launches": int(prof["sweep_launches"] + modes_launches * prof["modes_stages"]
                                 + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1))
                                    * args.steps if prec == pw.MIXED_FP32 else 0)),
             "e2e": (None if args.no_e2e else

@@ -171,6 +171,29 @@ __device__ int block_argmax(T v, int idx, T *sval, int *sidx) {
   return r;
 }
 
+// block_argmax with one barrier: every warp reduces the per-warp partials
+// itself.  sval/sidx may be written again only after a later barrier of the
+// whole block (the caller's next step has one).
+template <typename T, int NTH = NT>
+__device__ int block_argmax1(T v, int idx, T *sval, int *sidx) {
+  for (int off = 16; off > 0; off >>= 1) {
+    T ov = __shfl_down_sync(0xffffffffu, v, off);
+    int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sval[warp] = v; sidx[warp] = idx; }
+  __syncthreads();
+  v = lane < NTH / 32 ? sval[lane] : T(-1);
+  idx = lane < NTH / 32 ? sidx[lane] : 0x7fffffff;
+  for (int off = 16; off > 0; off >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, v, off);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  return idx;
+}
+
 template <typename T>
 __device__ __forceinline__ T tiny_pivot();
 template <>
@@ -178,18 +201,130 @@ __device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
 template <>
 __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
 
+// Right-hand columns [c_begin, c_end) of panel j0 (rows j0 ..; the panel
+// spans columns j0 .. j0+nb-1): the panel's row swaps, then U12 = L11^{-1} A12 with each column's nb
+// entries in registers (Ls: the factored nb x nb diagonal block, leading
+// dimension NB).  The swap sequence r <-> p_r (p_r >= r, in order r = 0 ..
+// nb-1) is first folded into a gather: row r < nb ends up holding original row
+// src[r], and each displaced row q >= nb (some p_r) an original row from
+// [0, nb) -- a row below the panel only ever receives the value that sat in
+// row r at step r, which is an original panel row.  So a column's new rows are
+// read before any row is written and the reads are independent (the
+// sequential swaps make every step wait for the previous one's memory round
+// trip).  `flag` gets bit 4 if the pivots break p_r >= r or the fold finds a
+// displaced source outside the panel (neither can come from the
+// factorisation).
+// FP64 keeps the sequential swaps and an in-place solve: a register column of
+// NB FP64 complex values would not fit beside the rest of the kernel.
+template <typename T, int NTH = NT>
+__device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int j0, int nb, int R,
+                                  const int *piv, const cx<T> *Ls, int *flag) {
+  constexpr int NB = Tile<T, NTH>::NB;
+  const int tid = threadIdx.x;
+  if constexpr (sizeof(T) != 4) {
+    for (int c = c_begin + tid; c < c_end; c += NTH) {
+      cx<T> *col = M + (size_t)c * ld + j0;
+      for (int r = 0; r < nb; ++r) {
+        const int p = piv[j0 + r] - j0;
+        if (p < r || p >= R) continue;   // cannot happen (flagged by the factorisation)
+        if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
+      }
+      for (int r = 1; r < nb; ++r) {
+        cx<T> x = col[r];
+        for (int s2 = 0; s2 < r; ++s2) {
+          const cx<T> l = Ls[r + s2 * NB], y = col[s2];
+          x.re -= l.re * y.re - l.im * y.im;
+          x.im -= l.re * y.im + l.im * y.re;
+        }
+        col[r] = x;
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  __shared__ int s_src[NB], s_dpos[NB], s_dsrc[NB], s_piv[NB], s_nd;
+  // the pivots are read in parallel: the fold below is one thread's serial loop
+  for (int r = tid; r < nb; r += NTH) s_piv[r] = piv[j0 + r] - j0;
+  __syncthreads();
+  if (tid == 0) {
+    int nd = 0;
+    for (int r = 0; r < nb; ++r) s_src[r] = r;
+    for (int r = 0; r < nb; ++r) {
+      const int p = s_piv[r];
+      if (p < r || p >= R) {
+        atomicOr(flag, 4);
+        continue;
+      }
+      if (p == r) continue;
+      if (p < nb) {
+        const int t = s_src[r];
+        s_src[r] = s_src[p];
+        s_src[p] = t;
+        continue;
+      }
+      int k = 0;
+      while (k < nd && s_dpos[k] != p) ++k;
+      if (k == nd) {
+        s_dpos[nd] = p;
+        s_dsrc[nd] = p;
+        ++nd;
+      }
+      const int t = s_src[r];
+      s_src[r] = s_dsrc[k];
+      s_dsrc[k] = t;
+    }
+    for (int k = 0; k < nd; ++k)
+      if (s_dsrc[k] >= nb) {
+        atomicOr(flag, 4);
+        nd = 0;
+        break;
+      }
+    s_nd = nd;
+  }
+  __syncthreads();
+  const int nd = s_nd;
+  for (int c = c_begin + tid; c < c_end; c += NTH) {
+    cx<T> *col = M + (size_t)c * ld + j0;
+    cx<T> x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[s_src[r]] : czero<T>();
+    // displaced rows: sources in [0, nb) (still original), targets >= nb
+    for (int k0 = 0; k0 < nd; k0 += 8) {
+      cx<T> y[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) y[k] = k0 + k < nd ? col[s_dsrc[k0 + k]] : czero<T>();
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k0 + k < nd) col[s_dpos[k0 + k]] = y[k];
+    }
+#pragma unroll
+    for (int r = 1; r < NB; ++r) {
+#pragma unroll
+      for (int s2 = 0; s2 < r; ++s2) {
+        const cx<T> l = Ls[r + s2 * NB];
+        x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
+        x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r < nb) col[r] = x[r];
+  }
+  __syncthreads();
+}
+
 // Pieces of a right-looking blocked LU with partial pivoting that eliminates on
 // an augmented n x ncols column-major matrix M = [A | B] (leading dimension ld)
 // and back-substitutes, i.e. solves A X = B in place (X over B).  Every piece
 // is called by all NTH threads of one CTA and ends with a __syncthreads().
 //
 // lu_panel: unblocked factorisation of columns j0..j0+nb-1 (rows j0..n-1) with
-// row pivoting (piv[j] = chosen row), then the panel's row swaps and
-// U12 = L11^{-1} A12 on every column right of the panel.  `flag` gets bit 1 on
+// row pivoting (piv[j] = chosen row), then (right = true) the panel's row
+// swaps and U12 = L11^{-1} A12 on every column right of the panel.  `flag` gets bit 1 on
 // a zero pivot.  Ls: NB x NB staging in shared memory.
 template <typename T, int NTH = NT>
 __device__ void lu_panel(cx<T> *M, int ld, int n, int ncols, int j0, int *piv, cx<T> *Ls, T *sval,
-                         int *sidx, int *flag) {
+                         int *sidx, int *flag, bool right = true) {
   constexpr int NT = NTH;
   constexpr int NB = Tile<T, NTH>::NB;
   const int tid = threadIdx.x;
@@ -235,35 +370,20 @@ __device__ void lu_panel(cx<T> *M, int ld, int n, int ncols, int j0, int *piv, c
     Ls[r + s2 * NB] = M[j0 + r + (size_t)(j0 + s2) * ld];
   }
   __syncthreads();
-  for (int c = j0 + nb + tid; c < ncols; c += NT) {
-    cx<T> *col = M + (size_t)c * ld + j0;
-    for (int r = 0; r < nb; ++r) {
-      const int p = piv[j0 + r] - j0;
-      if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
-    }
-    for (int r = 1; r < nb; ++r) {
-      cx<T> x = col[r];
-      for (int s2 = 0; s2 < r; ++s2) {
-        const cx<T> l = Ls[r + s2 * NB], y = col[s2];
-        x.re -= l.re * y.re - l.im * y.im;
-        x.im -= l.re * y.im + l.im * y.re;
-      }
-      col[r] = x;
-    }
-  }
-  __syncthreads();
+  if (right) panel_right_apply<T, NTH>(M, ld, j0 + nb, ncols, j0, nb, n - j0, piv, Ls, flag);
 }
 
 // lu_panel with the panel staged in shared memory: P holds rows j0..n-1 of
 // the panel's columns (leading dimension n - j0), so every column step of the
 // unblocked factorisation (pivot search, row swap, scaling, rank-1 update)
 // reads and writes shared memory only.  The right-hand columns then get the
-// panel's row swaps and U12 = L11^{-1} A12 with each column's nb entries held
-// in registers.  Same pivots, same operations and the same result layout as
-// lu_panel (FP32 only: an FP64 panel of 512 rows does not fit).
+// panel's row swaps and U12 = L11^{-1} A12 (panel_right_apply; with right =
+// false that is left to a separate launch over column blocks).  Same pivots,
+// same operations and the same result layout as lu_panel (FP32 only: an FP64
+// panel of 512 rows does not fit).
 template <typename T, int NTH = NT>
 __device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *piv, cx<T> *P, cx<T> *Ls,
-                              T *sval, int *sidx, int *flag) {
+                              T *sval, int *sidx, int *flag, bool right = true) {
   constexpr int NB = Tile<T, NTH>::NB;
   const int tid = threadIdx.x;
   const int nb = min(NB, n - j0), R = n - j0;
@@ -272,14 +392,18 @@ __device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *p
     P[e] = M[(j0 + r) + (size_t)(j0 + c) * ld];
   }
   __syncthreads();
+  // Each thread owns the rows r = tid (mod NTH) for the whole panel: it scales
+  // and updates them, and the update of column jj+1 yields its candidates for
+  // the next pivot, so a column step needs two barriers (pivot choice, row
+  // swap).  Pivot ties go to the smaller row, as in lu_panel.
+  T best = T(-1);
+  int bi = 0;
+  for (int r = tid; r < R; r += NTH) {
+    const T v = cabs1(P[r]);
+    if (v > best) { best = v; bi = r; }
+  }
   for (int jj = 0; jj < nb; ++jj) {
-    T best = T(-1);
-    int bi = jj;
-    for (int r = jj + tid; r < R; r += NTH) {
-      const T v = cabs1(P[r + jj * R]);
-      if (v > best) { best = v; bi = r; }
-    }
-    int p = block_argmax<T, NTH>(best, bi, sval, sidx);
+    int p = block_argmax1<T, NTH>(best, bi, sval, sidx);
     if (p < jj || p >= R) {   // cannot happen; recorded rather than followed
       if (tid == 0) atomicOr(flag, 4);
       p = jj;
@@ -299,19 +423,28 @@ __device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *p
       d = mkc<T>(tiny_pivot<T>(), T(0));
     }
     const cx<T> inv = cinv(d);
-    for (int r = jj + 1 + tid; r < R; r += NTH) P[r + jj * R] = cmul(P[r + jj * R], inv);
-    __syncthreads();
-    const int rows = R - jj - 1, cols = nb - jj - 1;
-    for (int e = tid; e < rows * cols; e += NTH) {
-      const int r = jj + 1 + e % rows, c = jj + 1 + e / rows;
-      cx<T> v = P[r + c * R];
-      const cx<T> l = P[r + jj * R], u = P[jj + c * R];
-      v.re -= l.re * u.re - l.im * u.im;
-      v.im -= l.re * u.im + l.im * u.re;
-      P[r + c * R] = v;
+    best = T(-1);
+    bi = jj + 1;
+    // rows below the pivot: l = a / d, then a_rc -= l u_c for the panel's
+    // remaining columns (u = the pivot row)
+    for (int r = (jj + 1) + ((tid - (jj + 1)) % NTH + NTH) % NTH; r < R; r += NTH) {
+      const cx<T> l = cmul(P[r + jj * R], inv);
+      P[r + jj * R] = l;
+      for (int c = jj + 1; c < nb; ++c) {
+        cx<T> v = P[r + c * R];
+        const cx<T> u = P[jj + c * R];
+        v.re -= l.re * u.re - l.im * u.im;
+        v.im -= l.re * u.im + l.im * u.re;
+        P[r + c * R] = v;
+        if (c == jj + 1) {
+          const T av = cabs1(v);
+          if (av > best) { best = av; bi = r; }
+        }
+      }
     }
-    __syncthreads();
+    // the next step's pivot barrier orders these updates before its row swap
   }
+  __syncthreads();
   for (int e = tid; e < R * nb; e += NTH) {
     const int r = e % R, c = e / R;
     M[(j0 + r) + (size_t)(j0 + c) * ld] = P[e];
@@ -321,30 +454,7 @@ __device__ void lu_panel_smem(cx<T> *M, int ld, int n, int ncols, int j0, int *p
     Ls[r + s2 * NB] = P[r + s2 * R];
   }
   __syncthreads();
-  for (int c = j0 + nb + tid; c < ncols; c += NTH) {
-    cx<T> *col = M + (size_t)c * ld + j0;
-    for (int r = 0; r < nb; ++r) {
-      const int p = piv[j0 + r] - j0;
-      if (p < r || p >= R) continue;   // cannot happen (checked above)
-      if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
-    }
-    cx<T> x[NB];
-#pragma unroll
-    for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[r] : czero<T>();
-#pragma unroll
-    for (int r = 1; r < NB; ++r) {
-#pragma unroll
-      for (int s2 = 0; s2 < r; ++s2) {
-        const cx<T> l = Ls[r + s2 * NB];
-        x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
-        x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < NB; ++r)
-      if (r < nb) col[r] = x[r];
-  }
-  __syncthreads();
+  if (right) panel_right_apply<T, NTH>(M, ld, j0 + nb, ncols, j0, nb, R, piv, Ls, flag);
 }
 
 // Trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb);

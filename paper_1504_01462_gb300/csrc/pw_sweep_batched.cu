@@ -275,14 +275,42 @@ __global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
     const bool fits = panel_head_bytes<T, BT>() + (size_t)(n - j0) * NB * sizeof(cx<T>) <= dyn;
     if (a.panel_smem && !fits && threadIdx.x == 0 && pt == 0 && j0 == 0)
       printf("kb_panel: staged panel of %d rows does not fit %u bytes; global path taken\n", n - j0, dyn);
+    // FP32: the right-hand columns are left to kb_panel_apply (many CTAs per point)
     if (a.panel_smem && fits)
-      lu_panel_smem<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, P, Ls, sval, sidx, flag);
-    else lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
+      lu_panel_smem<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, P, Ls, sval, sidx, flag, false);
+    else lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag, false);
   } else {
     lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
   }
   if (threadIdx.x == 0 && (*flag & 4)) printf("kb_panel: pivot row out of range (point %d, panel %d)\n", pt, j0);
   if (threadIdx.x == 0 && *flag) a.status[pt] = 1;
+}
+
+// Right-hand columns of panel j0 after kb_panel (FP32): row swaps and
+// U12 = L11^{-1} A12, BT columns per CTA; grid (column blocks, points).
+template <typename T, int BT>
+__global__ void __launch_bounds__(BT) kb_panel_apply(SweepArgs a, int j0) {
+  constexpr int NB = Tile<T, BT>::NB;
+  __shared__ cx<T> Ls[NB * NB];
+  __shared__ int flag;
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int nb = min(NB, n - j0), c0 = j0 + nb;
+  const int cb = c0 + blockIdx.x * BT, ce = min(ncols, cb + BT);
+  if (cb >= ce) return;
+  cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
+  for (int e = threadIdx.x; e < nb * nb; e += BT) {
+    const int r = e % nb, s2 = e / nb;
+    Ls[r + s2 * NB] = M[j0 + r + (size_t)(j0 + s2) * n];
+  }
+  if (threadIdx.x == 0) flag = 0;
+  __syncthreads();
+  panel_right_apply<T, BT>(M, n, cb, ce, j0, nb, n - j0, a.piv + (size_t)pt * n, Ls, &flag);
+  if (threadIdx.x == 0 && (flag & 4)) {
+    printf("kb_panel_apply: pivot row out of range (point %d, panel %d)\n", pt, j0);
+    a.status[pt] = 1;
+  }
 }
 
 template <typename T, int BT>
@@ -422,6 +450,8 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   for (int j0 = 0; j0 < n; j0 += NB) {
     kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0);
     const int c0 = j0 + min(NB, n - j0);
+    if constexpr (std::is_same<T, float>::value)
+      kb_panel_apply<T, BT><<<dim3((ncols - c0 + BT - 1) / BT, npts), BT, 0, s>>>(a, j0);
     if (c0 < n) {
       if (std::is_same<T, float>::value && tensor_core)
         kb_trail_tc<<<dim3(tiles(n - c0, ncols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
@@ -495,10 +525,13 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
 
 int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 4; }
 
-int sweep_batched_launches(int n) {
+int sweep_batched_launches(int n, int precision) {
   const int NB = Tile<float, 256>::NB;
   const int panels = (n + NB - 1) / NB;
-  return 3 + 2 * panels + 2 * panels - 2;
+  // vectors, [W|Y], finish; per panel: factorisation, trailing update (not
+  // after the last), the FP32 form's right-hand apply, diagonal solve and
+  // back-substitution update (not for the first block)
+  return 3 + 2 * panels - 1 + (precision == PW_FP64 ? 0 : panels) + 2 * panels - 1;
 }
 
 }  // namespace pw
