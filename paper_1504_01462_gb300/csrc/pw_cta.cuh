@@ -585,35 +585,74 @@ __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T>
 // column-major block `LU`, row swaps `piv`) to new right-hand sides B (n x nrhs,
 // leading dimension ldb): replays the same panel-by-panel elimination, then
 // back-substitutes, so B <- A^{-1} B.  smem: skinny_smem_elems + NB*NB.
+// Per block of NB = 32 rows, the block's row swaps are folded into a gather
+// (as in panel_right_apply) and each right-hand side is solved by one warp,
+// lane r holding row r (the diagonal block from shared memory, the solved
+// values passed by shuffles), so no step waits on a global-memory round trip.
 template <typename T, int NTH = NT>
 __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, int ldb, int nrhs,
                               cx<T> *smem) {
-  constexpr int NT = NTH;
   constexpr int NB = Tile<T, NTH>::NB;
-  const int tid = threadIdx.x;
+  static_assert(NB == 32, "one lane per row of a diagonal block");
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   cx<T> *Ls = smem + skinny_smem_elems<T>();
+  __shared__ int s_src[NB], s_dpos[NB], s_dsrc[NB], s_piv[NB], s_nd;
+  auto shfl = [](cx<T> v, int src) {
+    return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+  };
   for (int j0 = 0; j0 < n; j0 += NB) {
-    const int nb = min(NB, n - j0);
-    for (int e = tid; e < nb * nb; e += NT) {
-      const int r = e % nb, s = e / nb;
-      Ls[r + s * NB] = LU[j0 + r + (size_t)(j0 + s) * n];
+    const int nb = min(NB, n - j0), R = n - j0;
+    for (int e = tid; e < nb * nb; e += NTH) {
+      const int r = e % nb, c = e / nb;
+      Ls[r + c * NB] = LU[j0 + r + (size_t)(j0 + c) * n];
+    }
+    if (tid < nb) s_piv[tid] = piv[j0 + tid] - j0;
+    __syncthreads();
+    if (tid == 0) {
+      int nd = 0;
+      for (int r = 0; r < nb; ++r) s_src[r] = r;
+      for (int r = 0; r < nb; ++r) {
+        const int p = s_piv[r];
+        if (p <= r || p >= R) continue;   // p < r or out of range cannot come from the factorisation
+        if (p < nb) {
+          const int t = s_src[r];
+          s_src[r] = s_src[p];
+          s_src[p] = t;
+          continue;
+        }
+        int k = 0;
+        while (k < nd && s_dpos[k] != p) ++k;
+        if (k == nd) {
+          s_dpos[nd] = p;
+          s_dsrc[nd] = p;
+          ++nd;
+        }
+        const int t = s_src[r];
+        s_src[r] = s_dsrc[k];
+        s_dsrc[k] = t;
+      }
+      for (int k = 0; k < nd; ++k)
+        if (s_dsrc[k] >= nb) nd = 0;   // cannot happen (the fold keeps displaced sources in the block)
+      s_nd = nd;
     }
     __syncthreads();
-    for (int c = tid; c < nrhs; c += NT) {
+    const int nd = s_nd;
+    for (int c = warp; c < nrhs; c += NTH / 32) {
       cx<T> *col = B + (size_t)c * ldb + j0;
-      for (int r = 0; r < nb; ++r) {
-        const int p = piv[j0 + r] - j0;
-        if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
-      }
-      for (int r = 1; r < nb; ++r) {
-        cx<T> x = col[r];
-        for (int s2 = 0; s2 < r; ++s2) {
-          const cx<T> l = Ls[r + s2 * NB], y = col[s2];
-          x.re -= l.re * y.re - l.im * y.im;
-          x.im -= l.re * y.im + l.im * y.re;
+      cx<T> x = lane < nb ? col[s_src[lane]] : czero<T>();
+      const cx<T> y = lane < nd ? col[s_dsrc[lane]] : czero<T>();
+      __syncwarp();
+      if (lane < nd) col[s_dpos[lane]] = y;
+      // x <- L11^{-1} x (unit lower triangular)
+      for (int s2 = 0; s2 + 1 < nb; ++s2) {
+        const cx<T> xs = shfl(x, s2);
+        if (lane > s2 && lane < nb) {
+          const cx<T> l = Ls[lane + s2 * NB];
+          x.re -= l.re * xs.re - l.im * xs.im;
+          x.im -= l.re * xs.im + l.im * xs.re;
         }
-        col[r] = x;
       }
+      if (lane < nb) col[lane] = x;
     }
     __syncthreads();
     if (j0 + nb < n) {
@@ -631,22 +670,25 @@ __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, 
   const int jlast = ((n - 1) / NB) * NB;
   for (int j0 = jlast; j0 >= 0; j0 -= NB) {
     const int nb = min(NB, n - j0);
-    for (int e = tid; e < nb * nb; e += NT) {
-      const int r = e % nb, s = e / nb;
-      Ls[r + s * NB] = LU[j0 + r + (size_t)(j0 + s) * n];
+    for (int e = tid; e < nb * nb; e += NTH) {
+      const int r = e % nb, c = e / nb;
+      Ls[r + c * NB] = LU[j0 + r + (size_t)(j0 + c) * n];
     }
     __syncthreads();
-    for (int c = tid; c < nrhs; c += NT) {
+    for (int c = warp; c < nrhs; c += NTH / 32) {
       cx<T> *col = B + (size_t)c * ldb + j0;
-      for (int r = nb - 1; r >= 0; --r) {
-        cx<T> x = col[r];
-        for (int s2 = r + 1; s2 < nb; ++s2) {
-          const cx<T> u = Ls[r + s2 * NB], y = col[s2];
-          x.re -= u.re * y.re - u.im * y.im;
-          x.im -= u.re * y.im + u.im * y.re;
+      cx<T> x = lane < nb ? col[lane] : czero<T>();
+      // x <- U11^{-1} x
+      for (int s2 = nb - 1; s2 >= 0; --s2) {
+        if (lane == s2) x = cdiv(x, Ls[s2 + s2 * NB]);
+        const cx<T> xs = shfl(x, s2);
+        if (lane < s2) {
+          const cx<T> u = Ls[lane + s2 * NB];
+          x.re -= u.re * xs.re - u.im * xs.im;
+          x.im -= u.re * xs.im + u.im * xs.re;
         }
-        col[r] = cdiv(x, Ls[r + r * NB]);
       }
+      if (lane < nb) col[lane] = x;
     }
     __syncthreads();
     if (j0 > 0) {
