@@ -490,23 +490,24 @@ __device__ void lu_bs_diag(cx<T> *M, int ld, int n, int j0, int c_first, int c_l
   __syncthreads();
   if constexpr (std::is_same<T, float>::value) {
     // FP32: X = U11^{-1} B with U11^{-1} formed once per block in shared memory
-    // (column j by back substitution on e_j, one thread per column), then every
-    // RHS column is an independent triangular matrix-vector product
+    // (column j by back substitution on e_j: one warp per column, lane r holding
+    // row r, solved values passed by shuffles), then every RHS column is an
+    // independent triangular matrix-vector product
+    static_assert(NB == 32, "one lane per row of a diagonal block");
     cx<T> *Ui = Ls + NB * NB;   // NB x NB, upper triangular
-    for (int j = tid; j < nb; j += NT) {
-      for (int r = nb - 1; r >= 0; --r) {
-        cx<T> x = mkc<T>(r == j ? T(1) : T(0), T(0));
-        if (r > j) {
-          Ui[r + j * NB] = czero<T>();
-          continue;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int j = warp; j < nb; j += NT / 32) {
+      cx<T> x = mkc<T>(lane == j ? T(1) : T(0), T(0));
+      for (int s2 = j; s2 >= 0; --s2) {
+        if (lane == s2) x = cdiv(x, Ls[s2 + s2 * NB]);
+        const cx<T> xs = mkc<T>(__shfl_sync(0xffffffffu, x.re, s2), __shfl_sync(0xffffffffu, x.im, s2));
+        if (lane < s2) {
+          const cx<T> u = Ls[lane + s2 * NB];
+          x.re -= u.re * xs.re - u.im * xs.im;
+          x.im -= u.re * xs.im + u.im * xs.re;
         }
-        for (int s2 = r + 1; s2 <= j; ++s2) {
-          const cx<T> u = Ls[r + s2 * NB], y = Ui[s2 + j * NB];
-          x.re -= u.re * y.re - u.im * y.im;
-          x.im -= u.re * y.im + u.im * y.re;
-        }
-        Ui[r + j * NB] = cdiv(x, Ls[r + r * NB]);
       }
+      if (lane < nb) Ui[lane + j * NB] = lane <= j ? x : czero<T>();
     }
     __syncthreads();
     for (int c = c_first + tid; c < c_last; c += NT) {

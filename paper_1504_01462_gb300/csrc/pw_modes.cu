@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(ROT_ROWS) k_rot_apply(HeevWS ws, dfc *Z_all, i
 // vector k is column k of the reduced matrix A below the subdiagonal (unit
 // leading element implied).  The result goes back to Z's columns (FP64
 // complex in place of the double-float element, both 16 bytes).
-constexpr int BT_WARPS = 4, BT_COLS = 2;
+constexpr int BT_WARPS = 8, BT_COLS = 1;
 __global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(const dfc *A_all, dfc *Z_all, HeevWS ws, int n) {
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef HeevAr<df> Ar;
@@ -1099,17 +1099,71 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
     w.nsteps = reinterpret_cast<int *>(p);
     w.rot_cap = heev_rot_cap(n);
     w.step_cap = heev_step_cap(n);
+    auto shifted = [&](int k) {   // the workspace of matrices k .. of a group
+      HeevWS x = w;
+      x.d += (size_t)k * n;
+      x.e += (size_t)k * n;
+      x.tau += (size_t)k * n;
+      x.rot += (size_t)k * w.rot_cap;
+      x.steps += (size_t)k * w.step_cap;
+      x.nsteps += k;
+      return x;
+    };
+    // QL, rotations, back-transformation and sort of matrices m .. m+c-1
+    auto chain = [&](int m, int c, const HeevWS &wk, cudaStream_t st) {
+      zc *H = HU + (size_t)m * nn;
+      zc *Z = V + (size_t)m * nn;
+      k_ql_df<<<c, 32, 2 * (size_t)n * sizeof(df), st>>>(wk, status + m, n);
+      k_rot_apply<<<dim3((n + ROT_ROWS - 1) / ROT_ROWS, c), ROT_ROWS, 0, st>>>(wk, reinterpret_cast<dfc *>(Z),
+                                                                              status + m, n);
+      k_backtransform<<<dim3((n + BT_WARPS * BT_COLS - 1) / (BT_WARPS * BT_COLS), c), BT_WARPS * 32, bt_smem,
+                        st>>>(reinterpret_cast<const dfc *>(H), reinterpret_cast<dfc *>(Z), wk, n);
+      k_eig_sort<<<dim3((n + 7) / 8, c), 256, 0, st>>>(Z, H, En + (size_t)m * n, wk.d, status + m, n);
+    };
+    // The reduction runs two CTAs per SM.  When a group has more matrices than
+    // that, the ones beyond the first full wave go through their own chain on
+    // a second stream: the first wave's single-thread QL recurrences (a nearly
+    // idle GPU otherwise) overlap the reduction of the rest, and the rest's QL
+    // overlaps the first wave's vector kernels.
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wave = 2 * std::max(sms, 1);
     for (int m0 = 0; m0 < nmat; m0 += group) {
       const int cnt = std::min(group, nmat - m0);
-      zc *H = HU + (size_t)m0 * nn;
-      zc *Z = V + (size_t)m0 * nn;
-      k_heev<df><<<cnt, HEEV_THREADS, smem, s>>>(H, Z, En + (size_t)m0 * n, status + m0, n, 1, w);
-      k_ql_df<<<cnt, 32, 2 * (size_t)n * sizeof(df), s>>>(w, status + m0, n);
-      k_rot_apply<<<dim3((n + ROT_ROWS - 1) / ROT_ROWS, cnt), ROT_ROWS, 0, s>>>(w, reinterpret_cast<dfc *>(Z),
-                                                                               status + m0, n);
-      k_backtransform<<<dim3((n + BT_WARPS * BT_COLS - 1) / (BT_WARPS * BT_COLS), cnt), BT_WARPS * 32, bt_smem, s>>>(
-          reinterpret_cast<const dfc *>(H), reinterpret_cast<dfc *>(Z), w, n);
-      k_eig_sort<<<dim3((n + 7) / 8, cnt), 256, 0, s>>>(Z, H, En + (size_t)m0 * n, w.d, status + m0, n);
+      const int nA = cnt > wave ? wave : cnt;
+      cudaStream_t s2 = nullptr;
+      cudaEvent_t fork = nullptr, join = nullptr;
+      if (nA < cnt && (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();   // no second stream: one chain over the group
+        if (s2) cudaStreamDestroy(s2);
+        if (fork) cudaEventDestroy(fork);
+        s2 = nullptr;
+      }
+      const int a_cnt = s2 ? nA : cnt;
+      if (s2) {
+        cudaEventRecord(fork, s);
+        cudaStreamWaitEvent(s2, fork, 0);
+      }
+      k_heev<df><<<a_cnt, HEEV_THREADS, smem, s>>>(HU + (size_t)m0 * nn, V + (size_t)m0 * nn, En + (size_t)m0 * n,
+                                                   status + m0, n, 1, w);
+      if (s2) {
+        const int mb = m0 + nA, cb = cnt - nA;
+        const HeevWS wb = shifted(nA);
+        k_heev<df><<<cb, HEEV_THREADS, smem, s2>>>(HU + (size_t)mb * nn, V + (size_t)mb * nn, En + (size_t)mb * n,
+                                                   status + mb, n, 1, wb);
+        chain(mb, cb, wb, s2);
+        cudaEventRecord(join, s2);
+      }
+      chain(m0, a_cnt, w, s);
+      if (s2) {
+        cudaStreamWaitEvent(s, join, 0);
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
+        cudaStreamDestroy(s2);
+      }
     }
   } else {
     cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
