@@ -188,7 +188,10 @@ pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128
  *                                    the last two corrections (the error left
  *                                    after that pass)
  * A point at an electrode threshold gets T = NaN and the call returns
- * PW_ETHRESH after finishing the others. */
+ * PW_ETHRESH after finishing the others; a zero pivot gives PW_ESINGULAR,
+ * and a tensor-core completion wait of the mixed form that ran out (bounded,
+ * the kernel skips its result instead of hanging) gives PW_ETIMEOUT; both
+ * latch in the context. */
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar,
                           double *T_dev, pw_c128 *t_dev, int *nopen_dev, double *err_dev);
 

@@ -846,11 +846,13 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       std::vector<int> st_h(nb);
       CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
-      for (int v : st_h)
-        if (v) result = PW_ESINGULAR;
+      for (int v : st_h) {
+        if (v == 2) result = PW_ETIMEOUT;   // a tensor-core wait ran out (kept over a zero pivot)
+        else if (v && result != PW_ETIMEOUT) result = PW_ESINGULAR;
+      }
     }
   }
-  if (result == PW_ESINGULAR) latch(ctx, result);
+  if (result == PW_ESINGULAR || result == PW_ETIMEOUT) latch(ctx, result);
   return result;
 }
 

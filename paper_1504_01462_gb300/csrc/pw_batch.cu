@@ -375,6 +375,8 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   b->stats[3] += elapsed(ev[4], ev[5]);
   b->stats[5] += 1;
   for (int v : sth)
+    if (v == 2) return blatch(b, PW_ETIMEOUT);   // a tensor-core wait ran out
+  for (int v : sth)
     if (v) return blatch(b, PW_ESINGULAR);
   return PW_OK;
 }
