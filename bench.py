@@ -415,11 +415,15 @@ def main():
                                     if prec == pw.MIXED_FP32 else
                                     "FP64 nominal 1.25 TFLOP/s (recipe table; no measured FP64 peak)"),
                     "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
+        # DRAM bytes of one kb_wy_tc launch (one interface, 128 points) from the ncu capture
+        # summarised in profiles/kb_wy_tc_junction512_small.md; None for any other kernel or
+        # shape, and to be reset to None whenever the kernel changes
+        wy_traffic = 759.8e6 if (tensor and n == 512 and n_e == 128) else None
         wy_obj = {"bound": "tensor" if tensor else "alu",
                   "kernel": ("kb_wy_tc (tcgen05 kind::tf32, hi/lo split)" if tensor else
                              f"kb_wy<{'float' if prec == pw.MIXED_FP32 else 'double'}>"),
                   "achieved": wy_ach, "peak": wy_peak, "unit": "TFLOP/s", "frac": wy_ach / wy_peak,
-                  "traffic": None,
+                  "traffic": wy_traffic,
                   "peak_source": ("of measured: bf16 burst x 1.1/2.25 (nominal TF32/BF16) / 3 products"
                                   if tensor else
                                   "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz"
