@@ -792,6 +792,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.PIVst = refine ? (int *)ctx->PIVst.p : nullptr;
       a.KV = ctx->KV.p;
       a.mirror = 0;
+      a.wy_pairs = pw::points_pair_up(pd.data(), nb);
       CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
       Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision));
       for (int p = 0; p <= N; ++p) {

@@ -266,6 +266,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   a.PIVst = refine ? (int *)b->PIVst.p : nullptr;
   a.KV = b->KV.p;
   a.mirror = 0;
+  a.wy_pairs = pw::points_pair_up(pd.data(), m);
   // tile variant: timed on the first interface steps of this chunk
   int var = b->force_variant;
   if (var < 0) {

@@ -88,7 +88,17 @@ struct SweepArgs {
   void *KV;              // per point 3 x n: 1/k^p, k^{p+1}, E+ of the current interface
   int mirror;            // 1: the z-mirrored transposed problem (slice q -> N+1-q,
                          //    overlap O_p -> O_{N-p}^T), used by the adjoint
+  int wy_pairs;          // 1: points 2i and 2i+1 share overlaps and slice count (the
+                         //    tensor-core [W|Y] then stages one B tile for both)
 };
+
+// 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and
+// slice count (wy_pairs of SweepArgs).
+inline int points_pair_up(const PointDesc *pd, int npts) {
+  for (int i = 0; i + 1 < npts; i += 2)
+    if (pd[i].o_off != pd[i + 1].o_off || pd[i].N != pd[i + 1].N) return 0;
+  return 1;
+}
 
 // Buffers of the FP64 refinement around the FP32 sweep (pw_refine.cu).
 struct RefineArgs {

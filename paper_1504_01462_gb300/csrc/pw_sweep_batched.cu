@@ -209,6 +209,93 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
+// [W | Y] for two points that share their overlaps (same k-set, same slices):
+// with P = (O + K_L^{-1} O K_R)/2 and Q = (O - K_L^{-1} O K_R)/2 (K_L^{-1} =
+// diag(kinvL), K_R = diag(kR)),
+//   R Q = (X1 - X2 K_R)/2,  R P = (X1 + X2 K_R)/2,  X1 = R O,  X2 = (R K_L^{-1}) O,
+// so the four products X1, X2 of both points share the B operand O (one tile
+// staged per four A tiles).  W = P - R Q, Y = R P - Q are formed in the
+// epilogue.  Grid (64-row x 128-column tiles of the n x n products, point
+// pairs); one CTA per SM (the four accumulators fill tensor memory).
+size_t wy2_tc_smem_bytes(int n) { return tc::c4_smem_bytes() + 4 * (size_t)n * sizeof(cc); }
+
+__global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc(SweepArgs a, int p, int npts) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pt0 = 2 * blockIdx.y, pt1 = pt0 + 1;
+  const bool act0 = !inactive(a, pt0), act1 = pt1 < npts && !inactive(a, pt1);
+  if (!act0 && !act1) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int tiles_m = (n + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), c0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const PointDesc d = a.pts[act0 ? pt0 : pt1];   // both points have this one's overlaps
+  const bool tr = a.mirror != 0;
+  const int pi = tr ? d.N - p : p;
+  const zc *O = overlap_of(a, d, p);
+  const cc *O32 = overlap32_of(a, d, p);
+  const cc *O32t = a.O32t ? a.O32t + ((size_t)d.o_off + pi) * n * n : nullptr;
+  // the (possibly transposed) overlap, element (l, j) of the product's O
+  auto ov = [=](int l, int j) -> cc {
+    if (tr) {
+      if (O32) return tc::ldg_cc(O32 + j + (size_t)l * n);
+      return ccast<float>(O[j + (size_t)l * n]);
+    }
+    if (O32t) return tc::ldg_cc(O32t + j + (size_t)l * n);
+    if (O32) return tc::ldg_cc(O32 + l + (size_t)j * n);
+    return ccast<float>(O[l + (size_t)j * n]);
+  };
+  // the same element read along a column (consecutive l contiguous)
+  auto ovc = [=](int l, int j) -> cc {
+    if (tr) {
+      if (O32t) return O32t[l + (size_t)j * n];
+      if (O32) return O32[j + (size_t)l * n];
+      return ccast<float>(O[j + (size_t)l * n]);
+    }
+    if (O32) return O32[l + (size_t)j * n];
+    return ccast<float>(O[l + (size_t)j * n]);
+  };
+  const cc *R0 = reinterpret_cast<const cc *>(a.R) + (size_t)pt0 * n * n;
+  const cc *R1 = reinterpret_cast<const cc *>(a.R) + (size_t)(act1 ? pt1 : pt0) * n * n;
+  cc *M0 = reinterpret_cast<cc *>(a.M) + (size_t)pt0 * n * ncols;
+  cc *M1 = reinterpret_cast<cc *>(a.M) + (size_t)(act1 ? pt1 : pt0) * n * ncols;
+  cc *sk = reinterpret_cast<cc *>(smraw + tc::c4_smem_bytes());   // kinvL0, kR0, kinvL1, kR1
+  const KVb<float> g0 = kv_of<float>(a, pt0), g1 = kv_of<float>(a, act1 ? pt1 : pt0);
+  for (int i = threadIdx.x; i < n; i += tc::CG_THREADS) {
+    sk[i] = g0.kinvL[i];
+    sk[n + i] = g0.kR[i];
+    sk[2 * n + i] = g1.kinvL[i];
+    sk[3 * n + i] = g1.kR[i];
+  }
+  __syncthreads();
+  const unsigned amask = (act0 ? 3u : 0u) | (act1 ? 12u : 0u);
+  const bool ok = tc::cgemm_tile_shared_b(
+      n, n, n, r0, c0, amask,
+      [=](int h, int i, int l) { return tc::ldg_cc((h ? R1 : R0) + i + (size_t)l * n); },
+      [=](int h, int l) { return sk[h * 2 * n + l]; },   // kinvL of point h
+      [=](int l, int j) { return ov(l, j); },
+      [=](int i, int j, const cc (&x)[4]) {
+        const cc o = ovc(i, j);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!((amask >> (2 * h)) & 1u)) continue;
+          const cc *kinv = sk + h * 2 * n, *kr = kinv + n;
+          const cc r = cmul(kr[j], kinv[i]);
+          const cc P = cmul(o, mkc<float>(0.5f * (1.f + r.re), 0.5f * r.im));
+          const cc Q = cmul(o, mkc<float>(0.5f * (1.f - r.re), -0.5f * r.im));
+          const cc t = cmul(kr[j], x[2 * h + 1]);
+          const cc rq = mkc<float>(0.5f * (x[2 * h].re - t.re), 0.5f * (x[2 * h].im - t.im));
+          const cc rp = mkc<float>(0.5f * (x[2 * h].re + t.re), 0.5f * (x[2 * h].im + t.im));
+          cc *M = h ? M1 : M0;
+          M[i + (size_t)j * n] = csub(P, rq);
+          M[i + (size_t)(n + j) * n] = csub(rp, Q);
+        }
+      },
+      smraw);
+  if (!ok && threadIdx.x == 0) {
+    if (act0) a.status[pt0] = 2;
+    if (act1) a.status[pt1] = 2;
+  }
+}
+
 // Tile width of the update kernels (read-modify-write of C): 64 complex
 // columns keep the prefetched C values of a thread in 32 registers.
 constexpr int RMW_TN = 64;
@@ -440,7 +527,10 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   if (p > 0) {
     const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
     if (wy0) cudaEventRecord(wy0, s);
-    if (std::is_same<T, float>::value && tensor_core)
+    if (std::is_same<T, float>::value && tensor_core && a.wy_pairs)
+      kb_wy2_tc<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
+                  wy2_tc_smem_bytes(n), s>>>(a, p, npts);
+    else if (std::is_same<T, float>::value && tensor_core)
       kb_wy_tc<<<dim3(tiles(n, 2 * n, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS, wy_tc_smem_bytes(n), s>>>(
           a, p);
     else
@@ -506,6 +596,8 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
   cudaError_t e = (variant & 1) ? sweep_prepare<float, 512>(n) : sweep_prepare<float, 256>(n);
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_wy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wy_tc_smem_bytes(n));
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_wy2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wy2_tc_smem_bytes(n));
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_trail_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))

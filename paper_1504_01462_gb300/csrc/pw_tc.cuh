@@ -343,5 +343,177 @@ __device__ bool cgemm_tile(int m, int ncol, int k, int r0, int c0, FA fa, FB fb,
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Four complex products sharing one B operand: D_{2h} = A_h B and
+// D_{2h+1} = (A_h S_h) B for h = 0, 1, S_h = diag(s_h(l)) a column scaling
+// (D_q active when bit q of amask is set), same split, layout and pipeline as
+// cgemm_tile with TN = 128; the four accumulators fill the SM's tensor memory
+// (4 x 128 columns), so the kernel runs one CTA per SM.  Staging one B tile
+// for four A tiles quarters the B staging work per MMA, and A_h is loaded
+// once for both of its products.  fa(h, i, l) and fb(l, j) load the operands
+// (with ldg_cc: issued where written, so two stages of loads stay in
+// flight), fs(h, l) gives s_h(l); fe(i, j, x) receives x[q] = D_q(i, j) (zero
+// for inactive q).
+constexpr int C4 = 4;
+__host__ __device__ constexpr size_t c4_stage() { return (size_t)C4 * 2 * CG_AB + 2 * (size_t)cg_bb<CG_N>(); }
+__host__ __device__ constexpr size_t c4_smem_bytes() { return 2 * c4_stage() + 64; }
+
+// One complex FP32 value from global memory, issued at this point of the
+// program (the compiler may not sink it towards its use).
+__device__ __forceinline__ cc ldg_cc(const cc *p) {
+  float re, im;
+  asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(re), "=f"(im) : "l"(p));
+  return mkc<float>(re, im);
+}
+
+template <class FA, class FS, class FB, class FE>
+__device__ bool cgemm_tile_shared_b(int m, int ncol, int k, int r0, int c0, unsigned amask, FA fa, FS fs, FB fb,
+                                    FE fe, unsigned char *smem) {
+  constexpr int TN = CG_N, BB = cg_bb<CG_N>();
+  constexpr size_t STAGE = c4_stage();
+  constexpr int NCH = TN / 16;
+  unsigned char *stage0 = smem;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);   // [2]
+  uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const cc zero = czero<float>();
+  struct Stg {
+    cc a[2][2];   // A_h (r, l), (r, l+1)
+    cc b[4];
+  };
+  auto load = [&](int s, Stg &t) {
+    const int l0 = s * CG_KC;
+    const int rr = tid % (CG_M / 2), lp = tid / (CG_M / 2);
+    const int r = r0 + rr, l = l0 + 2 * lp;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool on = (amask >> (2 * h)) & 3u;
+      t.a[h][0] = (on && r < m && l < k) ? fa(h, r, l) : zero;
+      t.a[h][1] = (on && r < m && l + 1 < k) ? fa(h, r, l + 1) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * CG_THREADS;
+      const int jj = e % TN, lq = e / TN;
+      const int j = c0 + jj, lb = l0 + 2 * lq;
+      t.b[2 * u] = (lb < k && j < ncol) ? fb(lb, j) : zero;
+      t.b[2 * u + 1] = (lb + 1 < k && j < ncol) ? fb(lb + 1, j) : zero;
+    }
+  };
+  auto store = [&](unsigned char *base, int s, const Stg &t) {
+    const int rr = tid % (CG_M / 2), lp = tid / (CG_M / 2);
+    const int l = s * CG_KC + 2 * lp;
+#pragma unroll
+    for (int q = 0; q < C4; ++q) {
+      if (!((amask >> q) & 1u)) continue;
+      const int h = q >> 1;
+      cc a0 = t.a[h][0], a1 = t.a[h][1];
+      if (q & 1) {
+        if (l < k) a0 = cmul(a0, fs(h, l));
+        if (l + 1 < k) a1 = cmul(a1, fs(h, l + 1));
+      }
+      unsigned char *Ahi = base + (size_t)q * 2 * CG_AB, *Alo = Ahi + CG_AB;
+      store_split(Ahi, Alo, kmajor_offset(2 * rr, 4 * lp, CG_M), a0.re, -a0.im, a1.re, -a1.im);
+      store_split(Ahi, Alo, kmajor_offset(2 * rr + 1, 4 * lp, CG_M), a0.im, a0.re, a1.im, a1.re);
+    }
+    unsigned char *Bhi = base + (size_t)C4 * 2 * CG_AB, *Blo = Bhi + BB;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * CG_THREADS;
+      const int jj = e % TN, lq = e / TN;
+      store_split(Bhi, Blo, kmajor_offset(jj, 4 * lq, TN), t.b[2 * u].re, t.b[2 * u].im, t.b[2 * u + 1].re,
+                  t.b[2 * u + 1].im);
+    }
+  };
+  const int lrow = 32 * (warp & 3) + lane;
+  const int er = r0 + (lrow >> 1), eim = lrow & 1;
+  // two register stages in flight: the loads of stage s+2 are issued while
+  // stage s is split and multiplied (one CTA per SM leaves few warps to hide
+  // the memory latency otherwise)
+  Stg st0, st1;
+  const int nstage = (k + CG_KC - 1) / CG_KC;
+  load(0, st0);
+  if (nstage > 1) load(1, st1);
+  if (warp == 0) tmem_alloc(slot, C4 * TN);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *slot;
+  bool ok = true;
+  auto step = [&](int s, Stg &t) {
+    const int b = s & 1;
+    unsigned char *base = stage0 + b * STAGE;
+    if (s >= 2) ok = mbar_wait(&mbar[b], ((s - 2) >> 1) & 1) && ok;   // buffer b is free again
+    store(base, s, t);
+    if (s + 2 < nstage) load(s + 2, t);
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      constexpr uint32_t idesc = idesc_tf32(CG_M, TN);
+      const unsigned char *Bhi = base + (size_t)C4 * 2 * CG_AB, *Blo = Bhi + BB;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t bh = smem_desc(Bhi + ks * TN * 32, 128, 256);
+        const uint64_t bl = smem_desc(Blo + ks * TN * 32, 128, 256);
+#pragma unroll
+        for (int q = 0; q < C4; ++q) {
+          if (!((amask >> q) & 1u)) continue;
+          const unsigned char *Ahi = base + (size_t)q * 2 * CG_AB, *Alo = Ahi + CG_AB;
+          const uint64_t ah = smem_desc(Ahi + ks * CG_M * 32, 128, 256);
+          const uint64_t al = smem_desc(Alo + ks * CG_M * 32, 128, 256);
+          const uint32_t d = tmem + (uint32_t)(q * TN);
+          mma_tf32(d, ah, bh, idesc, (s > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(d, ah, bl, idesc, 1u);
+          mma_tf32(d, al, bh, idesc, 1u);
+        }
+      }
+      mma_commit(&mbar[b]);
+    }
+  };
+  for (int s = 0; s < nstage; s += 2) {
+    step(s, st0);
+    if (s + 1 < nstage) step(s + 1, st1);
+  }
+  ok = mbar_wait(&mbar[(nstage - 1) & 1], ((nstage - 1) >> 1) & 1) && ok;
+  fence_after_sync();
+  if (ok) {
+#pragma unroll 1
+    for (int qq = 0; qq < NCH; ++qq) {
+      float vv[C4][8], other[C4][8];
+#pragma unroll
+      for (int q = 0; q < C4; ++q) {
+        if ((amask >> q) & 1u) {
+          tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(q * TN + (TN / 2) * (warp >> 2) + 8 * qq),
+                   vv[q]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) vv[q][i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) other[q][i] = __shfl_xor_sync(0xffffffffu, vv[q][i], 1);
+      }
+      const int jb = c0 + (TN / 2) * (warp >> 2) + 8 * qq + (eim ? 4 : 0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        cc x[C4];
+#pragma unroll
+        for (int q = 0; q < C4; ++q)
+          x[q] = eim ? mkc<float>(other[q][i + 4], vv[q][i + 4]) : mkc<float>(vv[q][i], other[q][i]);
+        if (er < m && jb + i < ncol) fe(er, jb + i, x);
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, C4 * TN);
+  return ok;
+}
+
 }  // namespace tc
 }  // namespace pw
