@@ -415,12 +415,15 @@ def main():
                                     if prec == pw.MIXED_FP32 else
                                     "FP64 nominal 1.25 TFLOP/s (recipe table; no measured FP64 peak)"),
                     "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
-        # DRAM bytes of one kb_wy_tc launch (one interface, 128 points) from the ncu capture
-        # summarised in profiles/kb_wy_tc_junction512_small.md; None for any other kernel or
-        # shape, and to be reset to None whenever the kernel changes
-        wy_traffic = 759.8e6 if (tensor and n == 512 and n_e == 128) else None
+        # every step is one k_par, so neighbouring points share their overlaps and the
+        # tensor-core [W|Y] runs as kb_wy2_tc (point pairs sharing the B operand).  DRAM bytes
+        # of one launch (one interface, 128 points) from the ncu capture summarised in
+        # profiles/kb_wy2_tc_junction512_small.md; None for any other kernel or shape, and to
+        # be reset to None whenever the kernel changes
+        wy_traffic = 770.7e6 if (tensor and n == 512 and n_e == 128) else None
         wy_obj = {"bound": "tensor" if tensor else "alu",
-                  "kernel": ("kb_wy_tc (tcgen05 kind::tf32, hi/lo split)" if tensor else
+                  "kernel": ("kb_wy2_tc (tcgen05 kind::tf32, hi/lo split, point pairs share the B operand)"
+                             if tensor else
                              f"kb_wy<{'float' if prec == pw.MIXED_FP32 else 'double'}>"),
                   "achieved": wy_ach, "peak": wy_peak, "unit": "TFLOP/s", "frac": wy_ach / wy_peak,
                   "traffic": wy_traffic,

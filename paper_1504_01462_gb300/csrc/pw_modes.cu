@@ -491,8 +491,8 @@ struct HeevWS {
 // whole of Z from memory once per step).  A step with no rotation at some time
 // applies the identity (c = 1, s = 0, exact in double-float), so the body of a
 // time is straight-line code.
-constexpr int ROT_ROWS = 128;   // rows (threads) per CTA
-constexpr int ROT_K = 8;        // QL steps per pass
+constexpr int ROT_ROWS = 64;    // rows (threads) per CTA
+constexpr int ROT_K = 16;       // QL steps per pass
 
 // a b + c d in double-float (products formed exactly by FMA, one
 // normalisation)
