@@ -78,13 +78,17 @@ def heev_flops_per_matrix(n):
     return (16.0 / 3.0 + 4.5 + 8.0) * n ** 3
 
 
-def refine_launches(N, iters):
-    """Launches of the mixed form's refinement: init, a backward pass, then per
-    pass one residual launch, a forward pass and (except the last) a backward
-    pass, then the finish."""
+def refine_launches(N, iters, batched=True):
+    """Launches of the mixed form's refinement: init; a backward pass; per pass
+    one residual launch and a forward pass (fwd_b at every interface, fwd_a
+    after the first), then (except after the last pass) a backward pass; the
+    finish.  A backward step is bwd_a + bwd_b per interface, or bwd_a, the
+    batched tensor-core product and its combine when every point of the launch
+    shares its overlaps (one k_par per step here)."""
     if iters <= 0:
         return 0
-    return 3 + (N + 1) + iters * (1 + (N + 1)) + (iters - 1) * (N + 1)
+    bw = 3 if batched else 2
+    return 2 + bw * (N + 1) + iters * (1 + 2 * N + 1) + (iters - 1) * bw * (N + 1)
 
 
 def sweep_flops_per_point(n, nopen_left):

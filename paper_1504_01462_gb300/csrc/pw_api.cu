@@ -67,6 +67,7 @@ struct pw_ctx {
   DevBuf Xa_m, Xb_m, status_m, Tg, Gam, gtab, T1, dV0, wgt;   // adjoint (pw_grad)
   DevBuf corr;                     // refinement stopping test
   DevBuf eigws;                    // workspace of the double-float eigensolver
+  DevBuf bw;                       // batched backward product of the refinement (operands, result)
   int last_passes = 0;             // refinement passes of the last batch
   // device copies of the device-region wells (kept for the adjoint)
   double *d_wxyz = nullptr, *d_wv0 = nullptr, *d_wsig = nullptr;
@@ -546,7 +547,7 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
-                  ctx->lead_out.p, ctx->eigws.p};
+                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -835,6 +836,13 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.nc = nc;
         r.x_slots = (long long)nb * (N + 2);
         r.st_slots = (long long)nb * (N + 1);
+        r.Bw = r.Yw = nullptr;
+        if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32 &&
+            (st = ensure(ctx, ctx->bw, (size_t)4 * nb * n * nc * sizeof(cc))) == PW_OK) {
+          r.Bw = (cc *)ctx->bw.p;
+          r.Yw = r.Bw + (size_t)2 * nb * n * nc;
+        }
+        if (st) return st;
         Stage s3(ctx, 3, 1);
         int passes = 0;
         CK(pw::launch_refine(r, nb, std::min(2, ctx->refine_iters), ctx->refine_iters, kRefineTol,

@@ -128,7 +128,17 @@ struct RefineArgs {
   int n, N, nc;          // N: the most slices of any point
   long long x_slots;     // sum over points of N+2 (the Xa, Xb slots)
   long long st_slots;    // sum over points of N+1 (the Fr, Gr slots)
+  cc *Bw, *Yw;           // null, or n x (2 nc npts) each: when every point shares its overlaps
+                         //   and slice count, the backward pass's O products of all points
+                         //   run as one tensor-core GEMM (operands Bw, result Yw)
 };
+
+// 1 when every point of a launch has the same overlaps and slice count.
+inline int points_share_overlaps(const PointDesc *pd, int npts) {
+  for (int i = 1; i < npts; ++i)
+    if (pd[i].o_off != pd[0].o_off || pd[i].N != pd[0].N) return 0;
+  return npts > 0;
+}
 
 // Backward pass of a stored FP64 sweep (pw_grad.cu)
 struct GradArgs {

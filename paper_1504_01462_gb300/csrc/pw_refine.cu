@@ -26,6 +26,7 @@
 #include "pw_cta.cuh"
 #include "pw_df.cuh"
 #include "pw_internal.h"
+#include "pw_tc.cuh"
 
 namespace pw {
 
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(NT) k_refine_bwd_a(RefineArgs a, int p, int wi
   const int rows = min(SKINNY_BM, n - i0);
   cc *gsm = reinterpret_cast<cc *>(smraw);
   cc *eR = gsm + skinny_smem_elems<float>();
-  load_kv32(a, d, p, nullptr, nullptr, nullptr, eR);
+  cc *kR = eR + n;
+  load_kv32(a, d, p, nullptr, a.Bw ? kR : nullptr, nullptr, eR);
   const zc *carry = a.carry + (size_t)pt * n * nc;   // db_q (db_{N+1} = 0)
   const bool has_b = q <= N;
   auto edb = [=](int l, int j) {
@@ -165,8 +167,61 @@ __global__ void __launch_bounds__(NT) k_refine_bwd_a(RefineArgs a, int p, int wi
           zc &x = Xa[i0 + i + (size_t)j * n];
           x = cadd(x, ccast<double>(da));
         }
+        if (a.Bw) {
+          // operands of the batched backward product (k_refine_bwd_mm):
+          // u = da + e db, w = K_q (e db - da)
+          const cc e = tmp[n + i0 + i + (size_t)j * 2 * n];
+          cc *Bw = a.Bw + (size_t)pt * 2 * nc * n;
+          Bw[i0 + i + (size_t)j * n] = cadd(da, e);
+          Bw[i0 + i + (size_t)(nc + j) * n] = cmul(kR[i0 + i], csub(e, da));
+        }
       },
       gsm);
+}
+
+// Backward pass, part 2 when every point shares its overlaps: with
+// Q = (O - K_p^{-1} O K_q)/2 and P = (O + K_p^{-1} O K_q)/2,
+//   db_p = Q da_q + P e db_q = (O u + K_p^{-1} O w)/2,  u = da + e db, w = K_q (e db - da),
+// so one product O [u_1 w_1 u_2 w_2 ...] on the tensor cores (TF32 hi/lo split,
+// FP32 level like the rest of the preconditioner) serves every point;
+// k_refine_bwd_c combines it.  Grid (64 x 128 tiles of n x 2 nc npts).
+__global__ void __launch_bounds__(tc::CG_THREADS) k_refine_bwd_mm(RefineArgs a, int p, int npts) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int n = a.n, ncol = 2 * a.nc * npts;
+  const int tiles_m = (n + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), c0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const cc *O = a.O32 + ((size_t)a.pts[0].o_off + p) * n * n;
+  const cc *B = a.Bw;
+  cc *Y = a.Yw;
+  const bool ok = tc::cgemm_tile<true, false>(
+      n, ncol, n, r0, c0, [=](int i, int l) { return O[i + (size_t)l * n]; },
+      [=](int l, int j) { return B[l + (size_t)j * n]; }, [=](int, int) { return czero<float>(); },
+      [=](int i, int j, cc acc, cc) { Y[i + (size_t)j * n] = acc; }, smraw);
+  if (!ok && threadIdx.x == 0)
+    for (int pt = 0; pt < npts; ++pt) a.status[pt] = 2;
+}
+
+__global__ void __launch_bounds__(NT) k_refine_bwd_c(RefineArgs a, int p, int with_src) {
+  __shared__ cc kinvL[1024];
+  const int pt = blockIdx.y, i0 = blockIdx.x * SKINNY_BM;
+  const PointDesc d = a.pts[pt];
+  if (refine_skip(a, d, pt, p) || i0 >= a.n) return;
+  const int n = a.n, nc = a.nc;
+  const int rows = min(SKINNY_BM, n - i0);
+  load_kv32(a, d, p, kinvL, nullptr, nullptr, nullptr);
+  const cc *Y = a.Yw + (size_t)pt * 2 * nc * n;
+  zc *carry = a.carry + (size_t)pt * n * nc;
+  zc *Xb = a.Xb + blk(a, d, p);
+  const zc *G = a.Gr + iblk(a, d, p);
+  for (int e = threadIdx.x; e < rows * nc; e += NT) {
+    const int i = i0 + e % rows, c = e / rows;
+    const cc y1 = Y[i + (size_t)c * n], y2 = cmul(kinvL[i], Y[i + (size_t)(nc + c) * n]);
+    zc db = mkc<double>(0.5 * ((double)y1.re + (double)y2.re), 0.5 * ((double)y1.im + (double)y2.im));
+    if (with_src) db = cadd(db, G[i + (size_t)c * n]);
+    carry[i + (size_t)c * n] = db;
+    zc &x = Xb[i + (size_t)c * n];
+    x = cadd(x, db);
+  }
 }
 
 // Backward pass, part 2: db_p = [Q | P] [da_q ; e_q db_q] (+ g_p) for this CTA's
@@ -421,10 +476,20 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
       (e = cudaFuncSetAttribute(k_refine_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
   const dim3 rgrid((a.n + SKINNY_BM - 1) / SKINNY_BM, npts);
+  const bool batched = a.Bw && a.Yw && a.O32 && a.n <= 1024;
+  if (batched &&
+      (e = cudaFuncSetAttribute(k_refine_bwd_mm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes())))
+    return e;
+  const int mm_tiles = ((a.n + tc::CG_M / 2 - 1) / (tc::CG_M / 2)) * ((2 * a.nc * npts + tc::CG_N - 1) / tc::CG_N);
   auto backward = [&](int with_src) {
     for (int p = a.N; p >= 0; --p) {
       k_refine_bwd_a<<<rgrid, NT, smem, s>>>(a, p, with_src);
-      k_refine_bwd_b<<<rgrid, NT, smem, s>>>(a, p, with_src);
+      if (batched) {
+        k_refine_bwd_mm<<<mm_tiles, tc::CG_THREADS, tc::cg_smem_bytes(), s>>>(a, p, npts);
+        k_refine_bwd_c<<<rgrid, NT, 0, s>>>(a, p, with_src);
+      } else {
+        k_refine_bwd_b<<<rgrid, NT, smem, s>>>(a, p, with_src);
+      }
     }
   };
   auto forward = [&]() {
