@@ -88,6 +88,9 @@ __device__ void cta_gemm_t(int m, int n, int k, FA fa, FB fb, FE fe, cx<T> *smem
       }
       __syncthreads();
       if (l0 + BK < k) fetch(l0 + BK);
+      // the next tile's loads stay here, ahead of the math that hides their
+      // latency (a compiler fence: no memory access moves across it)
+      asm volatile("" ::: "memory");
 #pragma unroll 4
       for (int ll = 0; ll < BK; ++ll) {
         cx<T> a[TM], b[TN];
