@@ -323,6 +323,25 @@ def test_transmission_mixed_refined_junction(pw, iters):
     assert np.all(_rel(got, ref) < TOL_MIXED), (iters, got, ref)
 
 
+def test_transmission_mixed_refined_one_kpar(pw):
+    """Points that all share one k_par share their overlaps: [W|Y] then runs
+    for point pairs against one B tile and the refinement's backward product
+    is one tensor-core product for every point.  Four junction points, and an
+    odd count (the last point of the launch unpaired) on the minimal cell."""
+    inst = junction(ng=97, n_slices=60, n_e=4, n_k=4)
+    sel = [0, 1, 2, 3]   # the four energies of the first k_par
+    assert np.all(inst.kpar[sel] == inst.kpar[sel[0]])
+    ref = O.transmission(inst, points=sel)
+    got, _, _ = _gpu_T(pw, inst, 1, E=inst.energies[sel], k=inst.kpar[sel])
+    assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
+    E = np.array([0.5, 1.7, 2.3, 3.9, 5.5])
+    k = np.tile([[0.1, -0.2]], (5, 1))
+    inst = minimal_cell(energies=E, kpar=k)
+    ref = O.transmission(inst)
+    got, _, _ = _gpu_T(pw, inst, 1)
+    assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
+
+
 def test_transmission_mixed_refined_random_tables(pw):
     rng = np.random.default_rng(7)
     a = 4.0
