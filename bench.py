@@ -421,9 +421,9 @@ def main():
                     "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
         # every step is one k_par, so neighbouring points share their overlaps and the
         # tensor-core [W|Y] runs as kb_wy2_tc (point pairs sharing the B operand).  DRAM bytes
-        # of one launch (one interface, 128 points) from the ncu capture summarised in
-        # profiles/kb_wy2_tc_junction512_small.md; None for any other kernel or shape, and to
-        # be reset to None whenever the kernel changes
+        # of one launch (one interface, 128 points: dram__bytes_read.sum + dram__bytes_write.sum
+        # of an ncu capture of this kernel at this shape); None for any other kernel or shape,
+        # and to be reset to None whenever the kernel changes
         wy_traffic = 770.7e6 if (tensor and n == 512 and n_e == 128) else None
         wy_obj = {"bound": "tensor" if tensor else "alu",
                   "kernel": ("kb_wy2_tc (tcgen05 kind::tf32, hi/lo split, point pairs share the B operand)"
