@@ -417,7 +417,7 @@ def main():
                     "frac": heev_ach / heev_peak, "traffic": None,
                     "peak_source": ("FP32 FMA rate / 12 (12 FP32 instructions per double-float multiply-add)"
                                     if prec == pw.MIXED_FP32 else
-                                    "FP64 nominal 1.25 TFLOP/s (recipe table; no measured FP64 peak)"),
+                                    "FP64 nominal 1.25 TFLOP/s (GB300 dense FP64; no measured FP64 peak)"),
                     "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
         # every step is one k_par, so neighbouring points share their overlaps and the
         # tensor-core [W|Y] runs as kb_wy2_tc (point pairs sharing the B operand).  DRAM bytes
