@@ -795,7 +795,9 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   C *v = reinterpret_cast<C *>(smraw);
   C *pw_ = v + n;
   C *taus = pw_ + n;
-  C *cred = taus + n;                   // 33 complex: block reductions
+  C *vnx = taus + n;                    // the next step's reflector
+  C *pn = vnx + n;                      // A22 times it (the fused pass)
+  C *cred = pn + n;                     // 33 complex: block reductions
   double *d = reinterpret_cast<double *>(cred + 33);
   double *e = d + n;
   double *cs = e + n;
@@ -828,7 +830,18 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   }
 
   // ---- 1. Householder tridiagonalisation
-  for (int k = 0; k + 1 < n; ++k) {
+  // Step k reflects column k (below the diagonal) with v_k, tau_k, forms
+  // w_k = p - (Re(conj(tau) v^H p)/2) v with p = tau A22 v, and updates the
+  // trailing matrix A22 <- A22 - v w^H - w v^H.  The update is fused with the
+  // next step's product: column 0 of A22 is updated first, step k+1's
+  // reflector is formed from it, and one pass over A22[1:, 1:] both updates
+  // each element and accumulates A22[1:, 1:] v_{k+1} -- one read and one write
+  // of the trailing matrix per step instead of two reads and a write.
+  // Row 0 of A22 beyond its diagonal is never read again and is left as is.
+  C *vc = v, *vn = vnx;   // reflector of this step, of the next
+  // the reflector of column k from x = A[k+1:, k]: v (stored below the
+  // diagonal too), d[k], e[k], taus[k]; returns tau (FP64)
+  auto reflect = [&](int k, C *vv) -> zc {
     const int m = n - k - 1;
     C *x = A + (k + 1) + (size_t)k * n;
     C part = Ar::zero();
@@ -849,7 +862,7 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
     const C scl = Ar::from(skip ? czero<double>() : cinv(mkc<double>(alpha.re - beta, alpha.im)));
     for (int i = tid; i < m; i += NTH) {
       const C vi = i == 0 ? Ar::one() : Ar::mul(x[i], scl);
-      v[i] = vi;
+      vv[i] = vi;
       if (i > 0) x[i] = vi;   // kept for the back-transformation
     }
     if (tid == 0) {
@@ -858,33 +871,70 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
       taus[k] = Ar::from(tau);
     }
     __syncthreads();
-    if (skip) continue;
-    const C tauc = Ar::from(tau);
+    return tau;
+  };
+  zc tau = reflect(0, vc);
+  bool have_p = false;   // pn holds A22 v of this step (without tau)
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;
+    const bool skip = tau.re == 0.0 && tau.im == 0.0;
     C *A22 = A + (k + 1) + (size_t)(k + 1) * n;
+    if (skip) {
+      if (k + 2 < n) tau = reflect(k + 1, vc);
+      have_p = false;
+      continue;
+    }
+    const C tauc = Ar::from(tau);
     // p = tau A22 v
-    for (int i = tid; i < m; i += NTH) {
-      C acc = Ar::zero();
-      for (int j = 0; j < m; ++j) {
-        Ar::fma(acc, A22[i + (size_t)j * n], v[j]);
-        if ((j & 31) == 31) Ar::renorm(acc);
+    if (have_p) {
+      for (int i = tid; i < m; i += NTH) pw_[i] = Ar::mul(tauc, pn[i]);
+    } else {
+      for (int i = tid; i < m; i += NTH) {
+        C acc = Ar::zero();
+        for (int j = 0; j < m; ++j) {
+          Ar::fma(acc, A22[i + (size_t)j * n], vc[j]);
+          if ((j & 31) == 31) Ar::renorm(acc);
+        }
+        Ar::renorm(acc);
+        pw_[i] = Ar::mul(tauc, acc);
       }
-      Ar::renorm(acc);
-      pw_[i] = Ar::mul(tauc, acc);
     }
     __syncthreads();
     C vp = Ar::zero();
-    for (int i = tid; i < m; i += NTH) Ar::jfma(vp, v[i], pw_[i]);
+    for (int i = tid; i < m; i += NTH) Ar::jfma(vp, vc[i], pw_[i]);
     Ar::renorm(vp);
     const zc vhp = block_csum<R, NTH>(vp, cred);
     const double c = 0.5 * (tau.re * vhp.re + tau.im * vhp.im);   // Re(conj(tau) v^H p)
-    for (int i = tid; i < m; i += NTH) pw_[i] = Ar::sub_scaled(pw_[i], c, v[i]);
+    for (int i = tid; i < m; i += NTH) pw_[i] = Ar::sub_scaled(pw_[i], c, vc[i]);
     __syncthreads();
-    // A22 <- A22 - v w^H - w v^H
-    for (size_t q = tid; q < (size_t)m * m; q += NTH) {
-      const int i = q % m, j = q / m;
-      A22[i + (size_t)j * n] = Ar::rank2(A22[i + (size_t)j * n], v[i], pw_[j], pw_[i], v[j]);
+    // column 0 of A22 first: the next reflector comes from it
+    for (int i = tid; i < m; i += NTH) A22[i] = Ar::rank2(A22[i], vc[i], pw_[0], pw_[i], vc[0]);
+    __syncthreads();
+    if (k + 2 >= n) break;   // A22 was 1 x 1
+    const zc tau2 = reflect(k + 1, vn);
+    const bool fuse = !(tau2.re == 0.0 && tau2.im == 0.0);
+    // A22[1:, 1:] updated, and (fuse) pn = A22[1:, 1:] v_{k+1}, one row per thread
+    for (int r = 1 + tid; r < m; r += NTH) {
+      C acc = Ar::zero();
+      const C vr = vc[r], wr = pw_[r];
+      for (int j = 1; j < m; ++j) {
+        C *aij = A22 + r + (size_t)j * n;
+        const C a2 = Ar::rank2(*aij, vr, pw_[j], wr, vc[j]);
+        *aij = a2;
+        if (fuse) {
+          Ar::fma(acc, a2, vn[j - 1]);
+          if ((j & 31) == 0) Ar::renorm(acc);
+        }
+      }
+      Ar::renorm(acc);
+      pn[r - 1] = acc;
     }
     __syncthreads();
+    C *t = vc;
+    vc = vn;
+    vn = t;
+    tau = tau2;
+    have_p = fuse;
   }
   if (tid == 0) {
     d[n - 1] = Ar::to(A[(n - 1) + (size_t)(n - 1) * n]).re;
@@ -1037,7 +1087,7 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
 }
 
 size_t heev_smem(int n) {
-  return (size_t)3 * n * sizeof(zc) + 33 * sizeof(zc) + (size_t)4 * n * sizeof(double) +
+  return (size_t)5 * n * sizeof(zc) + 33 * sizeof(zc) + (size_t)4 * n * sizeof(double) +
          (size_t)2 * n * sizeof(double) + (8 + (size_t)n) * sizeof(int) + 64;
 }
 
