@@ -175,7 +175,16 @@ def cpu_oracle_rate(inst, n_e, sample_ifaces=24, sample_slices=24):
         "sample": f"1 point: {sample_slices + 1} slice eigendecompositions and {sample_ifaces} "
                   f"interface S + star products of N_G={m.n}, scaled to {m.N + 2} slices "
                   f"(amortised over {n_e} energies) and {m.N + 1} interfaces",
-        "seconds_per_point": per_point}
+        "seconds_per_point": per_point, "n": m.n, "N": m.N}
+
+
+def workload_config(name, n, N, n_e, n_k, world):
+    """The `config` object both arms report for the junction workloads."""
+    return {"workload": f"{name}: AB junction, N_G={n}, {N} slices, "
+                        f"{n_e} E x {n_k} k_par ({n_e * n_k} points); step = 1 k_par x {n_e} E",
+            "global_batch": n_e * world,
+            "l2": f"inputs larger than L2 (overlaps of one k_par: {(N + 1) * n * n * 16 / 1e9:.2f} GB)",
+            "parallelism": f"replicas over k_par x{world}"}
 
 
 def run_reference(args):
@@ -185,17 +194,21 @@ def run_reference(args):
         return
     inst, n_e, n_k = workload(args.config)
     cores = os.cpu_count()
-    rates = []
+    rates, secs = [], []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         r, info = cpu_oracle_rate(inst, n_e, sample_ifaces=8, sample_slices=8)
         if i >= args.warmup:
             rates.append(r)
+            secs.append(time.perf_counter() - t0)
     v = float(np.mean(rates))
+    config = workload_config(args.config, info["n"], info["N"], n_e, n_k, 1)
+    config["precision"] = "fp64 (CPU oracle)"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.config},
+            "config": config,
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
@@ -442,12 +455,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64" if prec == pw.MIXED_FP32 else "c128", "data": "synthetic",
-            "config": {"workload": f"{args.config}: AB junction, N_G={n}, {N} slices, "
-                                   f"{n_e} E x {n_k} k_par ({npts} points); step = 1 k_par x {n_e} E",
-                       "precision": args.precision, "global_batch": n_e * world,
-                       "l2": "inputs larger than L2 (overlaps of one k_par: "
-                             f"{(N + 1) * n * n * 16 / 1e9:.2f} GB)",
-                       "parallelism": f"replicas over k_par x{world}"},
+            "config": dict(workload_config(args.config, n, N, n_e, n_k, world), precision=args.precision),
             "roofline": dominant,
             "roofline_next": other,
             "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
