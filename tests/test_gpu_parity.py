@@ -342,6 +342,16 @@ def test_transmission_mixed_refined_one_kpar(pw):
     assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
 
 
+def test_transmission_largest_basis_mixed(pw):
+    """N_G = 1024, the largest basis pw_setup accepts (the panel LU then takes
+    its global-memory path, the eigensolver its largest shared-memory carves),
+    mixed form: two slices, two energies at one k_par."""
+    inst = junction(ng=1024, n_slices=2, n_e=2, n_k=1)
+    ref = O.transmission(inst)
+    got, _, _ = _gpu_T(pw, inst, 1)
+    assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
+
+
 def test_transmission_mixed_refined_random_tables(pw):
     rng = np.random.default_rng(7)
     a = 4.0
