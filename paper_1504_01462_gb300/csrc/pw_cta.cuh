@@ -243,77 +243,77 @@ __device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int 
       }
     }
     __syncthreads();
-    return;
-  }
-  __shared__ int s_src[NB], s_dpos[NB], s_dsrc[NB], s_piv[NB], s_nd;
-  // the pivots are read in parallel: the fold below is one thread's serial loop
-  for (int r = tid; r < nb; r += NTH) s_piv[r] = piv[j0 + r] - j0;
-  __syncthreads();
-  if (tid == 0) {
-    int nd = 0;
-    for (int r = 0; r < nb; ++r) s_src[r] = r;
-    for (int r = 0; r < nb; ++r) {
-      const int p = s_piv[r];
-      if (p < r || p >= R) {
-        atomicOr(flag, 4);
-        continue;
-      }
-      if (p == r) continue;
-      if (p < nb) {
+  } else {
+    __shared__ int s_src[NB], s_dpos[NB], s_dsrc[NB], s_piv[NB], s_nd;
+    // the pivots are read in parallel: the fold below is one thread's serial loop
+    for (int r = tid; r < nb; r += NTH) s_piv[r] = piv[j0 + r] - j0;
+    __syncthreads();
+    if (tid == 0) {
+      int nd = 0;
+      for (int r = 0; r < nb; ++r) s_src[r] = r;
+      for (int r = 0; r < nb; ++r) {
+        const int p = s_piv[r];
+        if (p < r || p >= R) {
+          atomicOr(flag, 4);
+          continue;
+        }
+        if (p == r) continue;
+        if (p < nb) {
+          const int t = s_src[r];
+          s_src[r] = s_src[p];
+          s_src[p] = t;
+          continue;
+        }
+        int k = 0;
+        while (k < nd && s_dpos[k] != p) ++k;
+        if (k == nd) {
+          s_dpos[nd] = p;
+          s_dsrc[nd] = p;
+          ++nd;
+        }
         const int t = s_src[r];
-        s_src[r] = s_src[p];
-        s_src[p] = t;
-        continue;
+        s_src[r] = s_dsrc[k];
+        s_dsrc[k] = t;
       }
-      int k = 0;
-      while (k < nd && s_dpos[k] != p) ++k;
-      if (k == nd) {
-        s_dpos[nd] = p;
-        s_dsrc[nd] = p;
-        ++nd;
-      }
-      const int t = s_src[r];
-      s_src[r] = s_dsrc[k];
-      s_dsrc[k] = t;
+      for (int k = 0; k < nd; ++k)
+        if (s_dsrc[k] >= nb) {
+          atomicOr(flag, 4);
+          nd = 0;
+          break;
+        }
+      s_nd = nd;
     }
-    for (int k = 0; k < nd; ++k)
-      if (s_dsrc[k] >= nb) {
-        atomicOr(flag, 4);
-        nd = 0;
-        break;
+    __syncthreads();
+    const int nd = s_nd;
+    for (int c = c_begin + tid; c < c_end; c += NTH) {
+      cx<T> *col = M + (size_t)c * ld + j0;
+      cx<T> x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[s_src[r]] : czero<T>();
+      // displaced rows: sources in [0, nb) (still original), targets >= nb
+      for (int k0 = 0; k0 < nd; k0 += 8) {
+        cx<T> y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[k] = k0 + k < nd ? col[s_dsrc[k0 + k]] : czero<T>();
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k0 + k < nd) col[s_dpos[k0 + k]] = y[k];
       }
-    s_nd = nd;
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+#pragma unroll
+        for (int s2 = 0; s2 < r; ++s2) {
+          const cx<T> l = Ls[r + s2 * NB];
+          x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
+          x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < nb) col[r] = x[r];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const int nd = s_nd;
-  for (int c = c_begin + tid; c < c_end; c += NTH) {
-    cx<T> *col = M + (size_t)c * ld + j0;
-    cx<T> x[NB];
-#pragma unroll
-    for (int r = 0; r < NB; ++r) x[r] = r < nb ? col[s_src[r]] : czero<T>();
-    // displaced rows: sources in [0, nb) (still original), targets >= nb
-    for (int k0 = 0; k0 < nd; k0 += 8) {
-      cx<T> y[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) y[k] = k0 + k < nd ? col[s_dsrc[k0 + k]] : czero<T>();
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (k0 + k < nd) col[s_dpos[k0 + k]] = y[k];
-    }
-#pragma unroll
-    for (int r = 1; r < NB; ++r) {
-#pragma unroll
-      for (int s2 = 0; s2 < r; ++s2) {
-        const cx<T> l = Ls[r + s2 * NB];
-        x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
-        x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < NB; ++r)
-      if (r < nb) col[r] = x[r];
-  }
-  __syncthreads();
 }
 
 // Pieces of a right-looking blocked LU with partial pivoting that eliminates on

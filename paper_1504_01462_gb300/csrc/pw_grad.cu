@@ -124,7 +124,6 @@ __global__ void __launch_bounds__(GT) k_grad_gamma(GammaArgs h, int slot) {
   const int ti = threadIdx.x % 16, tj = threadIdx.x / 16;
   const int m = i0 + ti, nn_ = j0 + tj;   // element (m, nn_) of Gamma_p
   __shared__ zc sP1[16][16], sP2[16][16], sA[16][16], sB[16][16];
-  __shared__ zc sW[16][16];
   __shared__ zc skm[16], skn[16], sem[16], sen[16];
   zc acc = czero<double>();
   const double dz = h.dz[p];

@@ -1096,10 +1096,6 @@ namespace {
 inline size_t ws_align(size_t b) { return (b + 255) & ~(size_t)255; }
 inline int heev_rot_cap(int n) { return 3 * n * n + 64; }
 inline int heev_step_cap(int n) { return 8 * n + 64; }
-size_t heev_ws_per(int n) {
-  return (size_t)n * (2 * sizeof(double) + sizeof(dfc)) + (size_t)heev_rot_cap(n) * sizeof(float4) +
-         (size_t)heev_step_cap(n) * sizeof(int2) + sizeof(int);
-}
 }  // namespace
 
 size_t heev_ws_bytes(int n, int nmat) {

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(NT) k_refine_bwd_a(RefineArgs a, int p, int wi
 // FP32 level like the rest of the preconditioner) serves every point;
 // k_refine_bwd_c combines it.  Grid (64 x 128 tiles of n x 2 nc npts).
 __global__ void __launch_bounds__(tc::CG_THREADS) k_refine_bwd_mm(RefineArgs a, int p, int npts) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
   const int n = a.n, ncol = 2 * a.nc * npts;
   const int tiles_m = (n + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), c0 = (blockIdx.x / tiles_m) * tc::CG_N;

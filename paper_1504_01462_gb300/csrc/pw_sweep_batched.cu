@@ -170,7 +170,8 @@ size_t wy_tc_smem_bytes(int n) { return tc::cg_smem_bytes() + 2 * (size_t)n * si
 
 // [W | Y] = [P | -Q] + [-R Q | R P]
 __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
   if (inactive(a, pt)) return;
   const PointDesc d = a.pts[pt];
@@ -220,7 +221,8 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_wy_tc(SweepArgs a, int p) {
 size_t wy2_tc_smem_bytes(int n) { return tc::c4_smem_bytes() + 4 * (size_t)n * sizeof(cc); }
 
 __global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc(SweepArgs a, int p, int npts) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
   const int pt0 = 2 * blockIdx.y, pt1 = pt0 + 1;
   const bool act0 = !inactive(a, pt0), act1 = pt1 < npts && !inactive(a, pt1);
   if (!act0 && !act1) return;
@@ -302,7 +304,8 @@ constexpr int RMW_TN = 64;
 
 // trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb)
 __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j0) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
   if (inactive(a, pt)) return;
   const int n = a.n, ncols = 2 * n + a.nc;
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
 
 // back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b
 __global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
   if (inactive(a, pt) || j0 <= 0) return;
   const int n = a.n, ncols = 2 * n + a.nc;
