@@ -122,3 +122,62 @@ def test_missing_switch_is_caught(monkeypatch):
     orig = O.doubling
     monkeypatch.setattr(O, "doubling", lambda elements, cond_max=O.COND_SWITCH: orig(elements, np.inf))
     _expect_failure(r2.test_doubling_matches_left_to_right_sweep, "junction")
+
+
+# ---------------------------------------------------------------------------
+# periodic electrodes (App. B complex bands, App. C)
+# ---------------------------------------------------------------------------
+def test_conjugated_tilt_phases_are_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import tests.test_oracle_periodic as per
+    orig = CB.tilt_phases
+    monkeypatch.setattr(CB, "tilt_phases", lambda G, a3: np.conj(orig(G, a3)))
+    _expect_failure(per.test_tilted_cell_perfect_crystal)
+
+
+def test_bloch_problem_sign_mistake_is_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import scipy.linalg
+    import tests.test_oracle_periodic as per
+
+    def bad(S):
+        S11, S12, S21, S22 = S
+        n = S11.shape[0]
+        Id, Z = np.eye(n, dtype=np.complex128), np.zeros((n, n), dtype=np.complex128)
+        return scipy.linalg.eig(np.block([[S11, Z], [S21, Id]]), np.block([[Id, -S12], [Z, -S22]]))
+    monkeypatch.setattr(CB, "complex_bands", bad)
+    # invisible for uniform cells (S12 = S21 = 0 there); random cells catch it
+    with pytest.raises((AssertionError, ValueError, np.linalg.LinAlgError)):
+        per.test_periodic_electrodes_conserve_flux_and_pair_bloch_factors(4, 3.7, (0.13, -0.21))
+
+
+def test_missing_flux_normalisation_is_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import tests.test_oracle_periodic as per
+    orig = CB.bloch_states
+
+    def unnormalised(lam, X, ref_mode, E, tol=1e-7):
+        st = orig(lam, X, ref_mode, E, tol)
+        for side in ("R", "L"):
+            p = st["prop" + side]
+            nrm = np.sqrt(np.sum(np.abs(st["a" + side][:, p]) ** 2 + np.abs(st["b" + side][:, p]) ** 2, axis=0))
+            st["a" + side][:, p] /= nrm
+            st["b" + side][:, p] /= nrm
+        return st
+    monkeypatch.setattr(CB, "bloch_states", unnormalised)
+    _expect_failure(per.test_periodic_electrodes_conserve_flux_and_pair_bloch_factors, 4, 3.7, (0.13, -0.21))
+
+
+def test_wrong_next_cell_in_the_right_electrode_is_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import tests.test_oracle_periodic as per
+    orig = CB.cell_smatrix
+    # every slice after the reference moved, as if the whole chain were the next cell
+    monkeypatch.setattr(CB, "cell_smatrix",
+                        lambda modes, dz, E, D=None, ref="last": orig(modes, dz, E, D, "last") if D is None
+                        else CB.chain_s(list(modes) + [(modes[0][0], D[:, None] * modes[0][1])],
+                                        [0.0] + list(dz[1:]) + [dz[0]], E) if ref == "last"
+                        else CB.chain_s([modes[0]] + [(m[0], D[:, None] * m[1]) for m in modes[1:]]
+                                        + [(modes[0][0], D[:, None] * modes[0][1])],
+                                        [0.0] + list(dz[1:]) + [dz[0]], E))
+    _expect_failure(per.test_tilted_cell_perfect_crystal)
