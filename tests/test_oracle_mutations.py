@@ -181,3 +181,38 @@ def test_wrong_next_cell_in_the_right_electrode_is_caught(monkeypatch):
                                         + [(modes[0][0], D[:, None] * modes[0][1])],
                                         [0.0] + list(dz[1:]) + [dz[0]], E))
     _expect_failure(per.test_tilted_cell_perfect_crystal)
+
+
+# ---------------------------------------------------------------------------
+# separable projector terms (Eqs. nloc, gsol_p0, calm_0)
+# ---------------------------------------------------------------------------
+def test_missing_cell_area_in_calm_is_caught(monkeypatch):
+    from oracle import separable as NL
+    import tests.test_oracle_separable as sep
+    orig = NL.transmission_nonlocal
+    monkeypatch.setattr(NL, "transmission_nonlocal",
+                        lambda modes, dz, E, projs, D, area, q=16: orig(modes, dz, E, projs, D, 1.0, q))
+    _expect_failure(sep.test_one_dimensional_separable_potential_closed_form, 0.9, (1, 4))
+
+
+def test_incoming_green_function_is_caught(monkeypatch):
+    from oracle import separable as NL
+    import tests.test_oracle_separable as sep
+    orig = NL._slice_terms
+
+    def incoming(U, k, za, zb, projs, q):   # e^{-ik|u|}: the other branch, no longer outgoing
+        return orig(U, -k, za, zb, projs, q)
+    monkeypatch.setattr(NL, "_slice_terms", incoming)
+    _expect_failure(sep.test_one_dimensional_separable_potential_closed_form, 0.9, (1, 4))
+
+
+def test_particular_derivatives_dropped_are_caught(monkeypatch):
+    from oracle import separable as NL
+    import tests.test_oracle_separable as sep
+    orig = NL._slice_terms
+
+    def no_deriv(U, k, za, zb, projs, q):
+        fa, dfa, fb, dfb, Ha, Hb, P = orig(U, k, za, zb, projs, q)
+        return fa, 0 * dfa, fb, 0 * dfb, Ha, Hb, P
+    monkeypatch.setattr(NL, "_slice_terms", no_deriv)
+    _expect_failure(sep.test_hermitian_projector_terms_conserve_flux, np.diag([0.8, -1.3]))
