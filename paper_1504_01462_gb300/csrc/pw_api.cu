@@ -795,7 +795,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.mirror = 0;
       a.wy_pairs = pw::points_pair_up(pd.data(), nb);
       CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
-      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision));
+      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant));
       for (int p = 0; p <= N; ++p) {
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }

@@ -328,7 +328,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   } else {
     for (int p = 0; p <= maxN; ++p) BCK(pw::launch_sweep_batched(a, m, p, b->precision, s, nullptr, nullptr, var));
   }
-  b->stats[7] += (double)(maxN + 1) * pw::sweep_batched_launches(n, b->precision);
+  b->stats[7] += (double)(maxN + 1) * pw::sweep_batched_launches(n, b->precision, var);
   BCK(cudaEventRecord(ev[4], s));
   if (refine) {
     pw::RefineArgs r;

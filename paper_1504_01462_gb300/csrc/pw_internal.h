@@ -210,7 +210,7 @@ void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t
 cudaError_t prepare_sweep_batched(int n, int precision, int variant);
 cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
                                  cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr, int variant = 0);
-int sweep_batched_launches(int n, int precision);
+int sweep_batched_launches(int n, int precision, int variant);
 int sweep_variants(int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p, u_p and the LU factors:
 // between min_iters and max_iters passes, stopping once every point's

@@ -323,14 +323,14 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
-// back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b
-__global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0) {
+// back-substitution update above block j0 (kb rows): M[0:j0, n:ncols] -= U[0:j0, b] X_b
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0, int kb) {
   extern __shared__ __align__(128) unsigned char smtc[];
   unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
   if (inactive(a, pt) || j0 <= 0) return;
   const int n = a.n, ncols = 2 * n + a.nc;
-  const int nb = min(Tile<float, 256>::NB, n - j0);
+  const int nb = min(kb, n - j0);
   const int m = j0, ncol = ncols - n;
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
@@ -342,6 +342,98 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j
       [=](int i, int j) { return M[i + (size_t)(n + j) * n]; },
       [=](int i, int j, cc acc, cc old) { M[i + (size_t)(n + j) * n] = csub(old, acc); }, smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
+}
+
+// Diagonal block of the back substitution with BS_FB rows (FP32, the
+// tensor-core form): X_b = U_bb^{-1} X_b for BS_COLS right-hand-side columns
+// per CTA.  U_bb and the columns are staged in shared memory; each warp
+// solves four columns at once (lane r holds rows r, r+32, r+64, r+96; the
+// solved value of row s passes by shuffle from its lane), so every element of
+// U_bb read serves four columns and the four recurrences interleave.  With
+// 128-row blocks the update above each block (kb_bsupd_tc) has K = 128 and
+// there are four blocks instead of sixteen at N_G = 512.
+constexpr int BS_FB = 128, BS_COLS = 32, BS_THREADS = 256;
+static_assert(BS_COLS == 4 * (BS_THREADS / 32), "four columns per warp");
+size_t bsdiag_big_smem() { return (size_t)BS_FB * BS_FB * sizeof(cc) + (size_t)BS_FB * BS_COLS * sizeof(cc); }
+
+__global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
+  const int fb = min(BS_FB, n - j0);
+  const int cf = blockIdx.x * BS_COLS;
+  if (cf >= nrhs) return;
+  const int ncl = min(BS_COLS, nrhs - cf);
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  cc *Us = reinterpret_cast<cc *>(smraw);     // Us[r + c fb], the upper triangle of U_bb
+  cc *Xs = Us + (size_t)BS_FB * BS_FB;       // Xs[r + q fb], the block rows of column cf + q
+  for (int e = threadIdx.x; e < fb * fb; e += BS_THREADS) {
+    const int r = e % fb, c = e / fb;
+    Us[e] = r <= c ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
+  }
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    Xs[e] = M[j0 + r + (size_t)(n + cf + q) * n];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = 4 * warp;   // this warp's four columns
+  if (q0 < ncl) {
+    cc x[4][4];   // [column][row slot t: row lane + 32 t]
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        x[c][t] = (q0 + c < ncl && r < fb) ? Xs[r + (q0 + c) * fb] : czero<float>();
+      }
+    for (int sb = (fb - 1) >> 5; sb >= 0; --sb) {       // row slot of s, from the bottom
+      for (int sl = min(31, fb - 1 - 32 * sb); sl >= 0; --sl) {
+        const int s = 32 * sb + sl;
+        const cc ud = Us[s + s * fb];
+        cc xs[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          cc v = x[c][0];
+#pragma unroll
+          for (int t = 1; t < 4; ++t)
+            if (t == sb) v = x[c][t];
+          if (lane == sl) {
+            v = cdiv(v, ud);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (t == sb) x[c][t] = v;
+          }
+          xs[c] = mkc<float>(__shfl_sync(0xffffffffu, v.re, sl), __shfl_sync(0xffffffffu, v.im, sl));
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = lane + 32 * t;
+          if (t <= sb && r < s) {
+            const cc u = Us[r + s * fb];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              x[c][t].re -= u.re * xs[c].re - u.im * xs[c].im;
+              x[c][t].im -= u.re * xs[c].im + u.im * xs[c].re;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        if (q0 + c < ncl && r < fb) Xs[r + (q0 + c) * fb] = x[c][t];
+      }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    M[j0 + r + (size_t)(n + cf + q) * n] = Xs[e];
+  }
 }
 
 template <typename T, int BT>
@@ -555,14 +647,19 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     }
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
-  for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
-    kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
-    if (j0 > 0) {
-      if (std::is_same<T, float>::value && tensor_core)
+  if (std::is_same<T, float>::value && tensor_core) {
+    // 128-row blocks: four diagonal solves and three K = 128 updates at N_G = 512
+    const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
+    for (int j0 = ((n - 1) / BS_FB) * BS_FB; j0 >= 0; j0 -= BS_FB) {
+      kb_bsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0);
+      if (j0 > 0)
         kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
-      else
-        kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB);
+    }
+  } else {
+    for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
+      kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
+      if (j0 > 0) kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
     }
   }
   kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p);
@@ -606,6 +703,8 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
     e = cudaFuncSetAttribute(kb_trail_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_bsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
   return e;
 }
 
@@ -621,13 +720,16 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
 
 int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 4; }
 
-int sweep_batched_launches(int n, int precision) {
+int sweep_batched_launches(int n, int precision, int variant) {
   const int NB = Tile<float, 256>::NB;
   const int panels = (n + NB - 1) / NB;
+  const bool fp32 = precision != PW_FP64, tensor = fp32 && (variant & 2);
   // vectors, [W|Y], finish; per panel: factorisation, trailing update (not
-  // after the last), the FP32 form's right-hand apply, diagonal solve and
-  // back-substitution update (not for the first block)
-  return 3 + 2 * panels - 1 + (precision == PW_FP64 ? 0 : panels) + 2 * panels - 1;
+  // after the last), the FP32 form's right-hand apply; the back substitution:
+  // a diagonal solve per block and an update above every block but the first
+  // (32-row blocks, or 128-row blocks in the tensor-core form)
+  const int bblocks = tensor ? (n + BS_FB - 1) / BS_FB : panels;
+  return 3 + 2 * panels - 1 + (fp32 ? panels : 0) + 2 * bblocks - 1;
 }
 
 }  // namespace pw
