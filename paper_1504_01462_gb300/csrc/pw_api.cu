@@ -836,6 +836,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.nc = nc;
         r.x_slots = (long long)nb * (N + 2);
         r.st_slots = (long long)nb * (N + 1);
+        r.lapack_piv = (ctx->sweep_variant & 2) ? 1 : 0;   // the stored factors' pivot order
         r.Bw = r.Yw = nullptr;
         if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32 &&
             (st = ensure(ctx, ctx->bw, (size_t)4 * nb * n * nc * sizeof(cc))) == PW_OK) {

@@ -90,6 +90,10 @@ struct SweepArgs {
                          //    overlap O_p -> O_{N-p}^T), used by the adjoint
   int wy_pairs;          // 1: points 2i and 2i+1 share overlaps and slice count (the
                          //    tensor-core [W|Y] then stages one B tile for both)
+  int lapack_piv;        // set by the sweep: 1 in the tensor-core FP32 form, where each
+                         //    panel's row swaps also reach the L columns left of it (so
+                         //    the stored factors satisfy P W = L U with P from piv in
+                         //    order) and the right-hand sides are eliminated after the LU
 };
 
 // 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and
@@ -128,6 +132,9 @@ struct RefineArgs {
   int n, N, nc;          // N: the most slices of any point
   long long x_slots;     // sum over points of N+2 (the Xa, Xb slots)
   long long st_slots;    // sum over points of N+1 (the Fr, Gr slots)
+  int lapack_piv;        // 1: the stored LU factors follow P W = L U (the sweep's
+                         //    tensor-core FP32 form); 0: each panel's swaps reach only
+                         //    the columns right of it (replayed panel by panel)
   cc *Bw, *Yw;           // null, or n x (2 nc npts) each: when every point shares its overlaps
                          //   and slice count, the backward pass's O products of all points
                          //   run as one tensor-core GEMM (operands Bw, result Yw)

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
   if (inactive(a, pt)) return;
   const int n = a.n, ncols = 2 * n + a.nc;
   const int nb = min(Tile<float, 256>::NB, n - j0), c0 = j0 + nb;
-  const int m = n - c0, ncol = ncols - c0;
+  const int m = n - c0, ncol = (a.lapack_piv ? n : ncols) - c0;   // lapack_piv: W's columns only
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
   if (q0 >= ncol) return;
@@ -436,6 +436,142 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
   }
 }
 
+// The right-hand sides of the tensor-core FP32 form after the LU of W
+// (P W = L U): X <- P X (kb_rhs_perm), then X <- L^{-1} X by 128-row blocks
+// (kb_fsdiag_big on the diagonal blocks, kb_fsupd_tc below them), then the
+// back substitution as before.  P applies the pivots in order: row j swaps
+// with piv[j] for j = 0 .. n-1.
+constexpr int RP_COLS = 16;   // right-hand-side columns per CTA of kb_rhs_perm
+size_t rhs_perm_smem(int n) { return (size_t)RP_COLS * n * sizeof(cc) + (size_t)n * sizeof(int); }
+
+__global__ void __launch_bounds__(256) kb_rhs_perm(SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
+  const int cf = blockIdx.x * RP_COLS;
+  if (cf >= nrhs) return;
+  const int ncl = min(RP_COLS, nrhs - cf);
+  cc *S = reinterpret_cast<cc *>(smraw);                         // S[r + q n]
+  int *perm = reinterpret_cast<int *>(S + (size_t)RP_COLS * n);   // row r of P X is row perm[r] of X
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  const int *piv = a.piv + (size_t)pt * n;
+  for (int e = threadIdx.x; e < n * ncl; e += 256) S[e] = M[e % n + (size_t)(n + cf + e / n) * n];
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < n; ++r) perm[r] = r;
+    for (int j = 0; j < n; ++j) {
+      const int p = piv[j];
+      if (p > j && p < n) {   // p < j or out of range cannot come from the factorisation
+        const int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * ncl; e += 256) {
+    const int r = e % n, q = e / n;
+    M[r + (size_t)(n + cf + q) * n] = S[perm[r] + q * n];
+  }
+}
+
+// X_b <- L_bb^{-1} X_b for one 128-row diagonal block (unit lower), the
+// schedule of kb_bsdiag_big run from the top.
+__global__ void __launch_bounds__(BS_THREADS, 1) kb_fsdiag_big(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
+  const int fb = min(BS_FB, n - j0);
+  const int cf = blockIdx.x * BS_COLS;
+  if (cf >= nrhs) return;
+  const int ncl = min(BS_COLS, nrhs - cf);
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  cc *Ls = reinterpret_cast<cc *>(smraw);     // Ls[r + c fb], the strict lower triangle of L_bb
+  cc *Xs = Ls + (size_t)BS_FB * BS_FB;
+  for (int e = threadIdx.x; e < fb * fb; e += BS_THREADS) {
+    const int r = e % fb, c = e / fb;
+    Ls[e] = r > c ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
+  }
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    Xs[e] = M[j0 + r + (size_t)(n + cf + q) * n];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = 4 * warp;
+  if (q0 < ncl) {
+    cc x[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        x[c][t] = (q0 + c < ncl && r < fb) ? Xs[r + (q0 + c) * fb] : czero<float>();
+      }
+    for (int sb = 0; 32 * sb < fb; ++sb) {
+      for (int sl = 0; sl < 32 && 32 * sb + sl < fb; ++sl) {
+        const int s = 32 * sb + sl;
+        cc xs[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          cc v = x[c][0];
+#pragma unroll
+          for (int t = 1; t < 4; ++t)
+            if (t == sb) v = x[c][t];
+          xs[c] = mkc<float>(__shfl_sync(0xffffffffu, v.re, sl), __shfl_sync(0xffffffffu, v.im, sl));
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = lane + 32 * t;
+          if (t >= sb && r > s && r < fb) {
+            const cc l = Ls[r + s * fb];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              x[c][t].re -= l.re * xs[c].re - l.im * xs[c].im;
+              x[c][t].im -= l.re * xs[c].im + l.im * xs[c].re;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        if (q0 + c < ncl && r < fb) Xs[r + (q0 + c) * fb] = x[c][t];
+      }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    M[j0 + r + (size_t)(n + cf + q) * n] = Xs[e];
+  }
+}
+
+// Forward update below block [j0, j0+kb): M[j0+kb:n, n:ncols] -= L[j0+kb:n, b] X_b
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_fsupd_tc(SweepArgs a, int j0, int kb) {
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int nb = min(kb, n - j0), c0 = j0 + nb;
+  const int m = n - c0, ncol = ncols - n;
+  if (m <= 0) return;
+  const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
+  if (q0 >= ncol) return;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  const bool ok = tc::cgemm_tile<true, true, RMW_TN>(
+      m, ncol, nb, r0, q0, [=](int i, int l) { return M[c0 + i + (size_t)(j0 + l) * n]; },
+      [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
+      [=](int i, int j) { return M[c0 + i + (size_t)(n + j) * n]; },
+      [=](int i, int j, cc acc, cc old) { M[c0 + i + (size_t)(n + j) * n] = csub(old, acc); }, smraw);
+  if (!ok && threadIdx.x == 0) a.status[pt] = 2;
+}
+
 template <typename T, int BT>
 __global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -480,7 +616,13 @@ __global__ void __launch_bounds__(BT) kb_panel_apply(SweepArgs a, int j0) {
   if (inactive(a, pt)) return;
   const int n = a.n, ncols = 2 * n + a.nc;
   const int nb = min(NB, n - j0), c0 = j0 + nb;
-  const int cb = c0 + blockIdx.x * BT, ce = min(ncols, cb + BT);
+  // lapack_piv: column blocks [0, j0) take the swaps only (the L columns of
+  // earlier panels), then [c0, n) swaps and the L11 solve; the right-hand
+  // sides are left to the elimination after the LU
+  const int nleft = a.lapack_piv ? (j0 + BT - 1) / BT : 0;
+  const bool left = (int)blockIdx.x < nleft;
+  const int cb = left ? blockIdx.x * BT : c0 + ((int)blockIdx.x - nleft) * BT;
+  const int ce = left ? min(j0, cb + BT) : min(a.lapack_piv ? n : ncols, cb + BT);
   if (cb >= ce) return;
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   for (int e = threadIdx.x; e < nb * nb; e += BT) {
@@ -489,7 +631,7 @@ __global__ void __launch_bounds__(BT) kb_panel_apply(SweepArgs a, int j0) {
   }
   if (threadIdx.x == 0) flag = 0;
   __syncthreads();
-  panel_right_apply<T, BT>(M, n, cb, ce, j0, nb, n - j0, a.piv + (size_t)pt * n, Ls, &flag);
+  panel_right_apply<T, BT>(M, n, cb, ce, j0, nb, n - j0, a.piv + (size_t)pt * n, Ls, &flag, !left);
   if (threadIdx.x == 0 && (flag & 4)) {
     printf("kb_panel_apply: pivot row out of range (point %d, panel %d)\n", pt, j0);
     a.status[pt] = 1;
@@ -633,17 +775,35 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
       kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
     if (wy1) cudaEventRecord(wy1, s);
   }
+  // tensor-core FP32 form: LAPACK-ordered pivots, the LU of W alone, then the
+  // right-hand sides eliminated in 128-row blocks (see kb_rhs_perm)
+  const bool lapack = std::is_same<T, float>::value && tensor_core;
+  a.lapack_piv = lapack ? 1 : 0;
+  const int ucols = lapack ? n : ncols;   // columns the LU updates
   for (int j0 = 0; j0 < n; j0 += NB) {
     kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0);
     const int c0 = j0 + min(NB, n - j0);
-    if constexpr (std::is_same<T, float>::value)
-      kb_panel_apply<T, BT><<<dim3((ncols - c0 + BT - 1) / BT, npts), BT, 0, s>>>(a, j0);
+    if constexpr (std::is_same<T, float>::value) {
+      const int blocks = (lapack ? (j0 + BT - 1) / BT : 0) + (ucols - c0 + BT - 1) / BT;
+      if (blocks > 0) kb_panel_apply<T, BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0);
+    }
     if (c0 < n) {
-      if (std::is_same<T, float>::value && tensor_core)
-        kb_trail_tc<<<dim3(tiles(n - c0, ncols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+      if (lapack)
+        kb_trail_tc<<<dim3(tiles(n - c0, ucols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
                       tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
       else
         kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
+    }
+  }
+  if (lapack) {
+    const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
+    kb_rhs_perm<<<dim3((ncols - n + RP_COLS - 1) / RP_COLS, npts), 256, rhs_perm_smem(n), s>>>(a);
+    for (int j0 = 0; j0 < n; j0 += BS_FB) {
+      kb_fsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0);
+      const int c1 = j0 + std::min(BS_FB, n - j0);
+      if (c1 < n)
+        kb_fsupd_tc<<<dim3(tiles(n - c1, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB);
     }
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
@@ -705,6 +865,12 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
     e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_bsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_fsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_fsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_rhs_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_perm_smem(n));
   return e;
 }
 
@@ -729,7 +895,10 @@ int sweep_batched_launches(int n, int precision, int variant) {
   // a diagonal solve per block and an update above every block but the first
   // (32-row blocks, or 128-row blocks in the tensor-core form)
   const int bblocks = tensor ? (n + BS_FB - 1) / BS_FB : panels;
-  return 3 + 2 * panels - 1 + (fp32 ? panels : 0) + 2 * bblocks - 1;
+  // the tensor-core form adds the right-hand sides' elimination: a
+  // permutation, a diagonal solve per 128-row block and an update below every
+  // block but the last
+  return 3 + 2 * panels - 1 + (fp32 ? panels : 0) + 2 * bblocks - 1 + (tensor ? 2 * bblocks : 0);
 }
 
 }  // namespace pw
