@@ -78,17 +78,21 @@ def heev_flops_per_matrix(n):
     return (16.0 / 3.0 + 4.5 + 8.0) * n ** 3
 
 
-def refine_launches(N, iters, batched=True):
+def refine_launches(N, iters, batched=True, sliced=True):
     """Launches of the mixed form's refinement: init; a backward pass; per pass
-    one residual launch and a forward pass (fwd_b at every interface, fwd_a
-    after the first), then (except after the last pass) a backward pass; the
-    finish.  A backward step is bwd_a + bwd_b per interface, or bwd_a, the
-    batched tensor-core product and its combine when every point of the launch
-    shares its overlaps (one k_par per step here)."""
+    the residual and a forward pass (fwd_b at every interface, fwd_a after the
+    first), then (except after the last pass) a backward pass; the finish.  A
+    backward step is bwd_a + bwd_b per interface, or bwd_a, the batched
+    tensor-core product and its combine when every point of the launch shares
+    its overlaps (one k_par per step here).  The residual is one launch, or,
+    as exact slice products on the tensor cores (shared overlaps, N_G a
+    multiple of 4 up to 512), four per interface (slice O, slice y, product,
+    combine)."""
     if iters <= 0:
         return 0
     bw = 3 if batched else 2
-    return 2 + bw * (N + 1) + iters * (1 + 2 * N + 1) + (iters - 1) * bw * (N + 1)
+    res = 4 * (N + 1) if sliced else 1
+    return 2 + bw * (N + 1) + iters * (res + 2 * N + 1) + (iters - 1) * bw * (N + 1)
 
 
 def sweep_flops_per_point(n, nopen_left):
@@ -467,7 +471,8 @@ def main():
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
             "gpu_launches": int(prof["sweep_launches"] + modes_launches * prof["modes_stages"]
-                                + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1))
+                                + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1),
+                                                   sliced=(n <= 512 and n % 4 == 0))
                                    * args.steps if prec == pw.MIXED_FP32 else 0)),
             "e2e": (None if args.no_e2e else
                     {"value": e2e_value, "unit": "points/s",

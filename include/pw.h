@@ -326,6 +326,20 @@ void pw_batch_destroy(pw_batch *b);
  * wait.  The paper has no counterpart; this is a deployment check. */
 pw_status pw_selftest_tensor_core(double *rel_err_tf32, double *rel_err_split);
 
+/* Self-test of the exact-slice product behind the mixed form's residual when
+ * every point shares its overlaps: O y as a sum of products of 7-bit slices
+ * (BF16 on the tensor cores, FP32 accumulation that is exact for 2n <= 1024
+ * inner terms, the slice pairs summed in double-float).  Runs that kernel on
+ * random slices for a basis of n functions (a multiple of 4, at most 512) and
+ * ncol columns (1..4096): first with only the leading slices non-zero and rows
+ * and columns at full scale, where *mismatches counts the results that differ
+ * from the exact integer product in any bit; then with every slice random,
+ * where *rel_err = max|Y - Y_exact| / max|Y_exact| on every 64th row (about
+ * 1e-14 expected).  Runs on the current device and synchronises it; returns
+ * PW_EINVAL for sizes out of range and PW_ETIMEOUT if a tensor-core wait ran
+ * out.  A deployment check with no counterpart in the paper. */
+pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, double *rel_err);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_get_profile", "pw_compose_noalloc", "pw_grad", "pw_setup_batch",
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
            "pw_batch_destroy", "pw_get_error_detail", "pw_selftest_tensor_core",
-           "pw_set_sweep_variant"]
+           "pw_set_sweep_variant", "pw_selftest_slice_product"]
 
 
 class PwError(RuntimeError):
@@ -97,6 +97,8 @@ def _load():
     lib.pw_batch_destroy.argtypes = [_vp]
     lib.pw_get_error_detail.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
     lib.pw_selftest_tensor_core.argtypes = [_dp, _dp]
+    lib.pw_selftest_slice_product.argtypes = [ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_longlong), _dp]
     lib.pw_set_sweep_variant.argtypes = [_vp, ctypes.c_int]
     lib.pw_batch_destroy.restype = None
     return lib
@@ -217,6 +219,17 @@ def selftest_tensor_core():
     b = np.zeros(1)
     _check_status(_lib.pw_selftest_tensor_core(_as_dp(a), _as_dp(b)), "pw_selftest_tensor_core")
     return float(a[0]), float(b[0])
+
+
+def selftest_slice_product(n, ncol):
+    """(results differing from the exact leading-slice product, relative error
+    of the full slice sum) from the library's exact-slice product self-test
+    (the residual's tensor-core path) for a basis of n and ncol columns."""
+    bad = ctypes.c_longlong(-1)
+    rel = np.zeros(1)
+    _check_status(_lib.pw_selftest_slice_product(int(n), int(ncol), ctypes.byref(bad), _as_dp(rel)),
+                  "pw_selftest_slice_product")
+    return int(bad.value), float(rel[0])
 
 
 def _check_status(st, where):

@@ -806,6 +806,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       s0.done();
       if (refine) {
         pw::RefineArgs r;
+        memset(&r, 0, sizeof(r));
         r.pts = a.pts;
         r.En = a.En;
         r.O = a.O;
@@ -837,11 +838,28 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.x_slots = (long long)nb * (N + 2);
         r.st_slots = (long long)nb * (N + 1);
         r.lapack_piv = (ctx->sweep_variant & 2) ? 1 : 0;   // the stored factors' pivot order
-        r.Bw = r.Yw = nullptr;
-        if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32 &&
-            (st = ensure(ctx, ctx->bw, (size_t)4 * nb * n * nc * sizeof(cc))) == PW_OK) {
-          r.Bw = (cc *)ctx->bw.p;
-          r.Yw = r.Bw + (size_t)2 * nb * n * nc;
+        if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32) {
+          // one buffer: the backward product's operands and result, then (when the
+          // residual runs on the tensor cores) O y, the slices and their exponents
+          auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+          const long long ncol = 2LL * nb * nc;
+          const bool sliced = ctx->d_O32lo && n <= 512 && n % 4 == 0;
+          const size_t b_bw = up((size_t)4 * nb * n * nc * sizeof(cc));
+          const size_t b_y = up((size_t)2 * n * ncol * sizeof(double));
+          const size_t b_sl = up(pw::rs_slice_bytes(n, ncol));
+          const size_t b_ex = ((size_t)2 * n + ncol) * sizeof(int);
+          if ((st = ensure(ctx, ctx->bw, b_bw + (sliced ? b_y + b_sl + b_ex : 0))) == PW_OK) {
+            unsigned char *base = (unsigned char *)ctx->bw.p;
+            r.Bw = (cc *)base;
+            r.Yw = r.Bw + (size_t)2 * nb * n * nc;
+            if (sliced) {
+              r.Yacc = (double *)(base + b_bw);
+              r.Osl = (uint16_t *)(base + b_bw + b_y);
+              r.Ysl = r.Osl + (size_t)pw::RS_SLICES * 4 * n * n;
+              r.Oexp = (int *)(base + b_bw + b_y + b_sl);
+              r.Yexp = r.Oexp + 2 * n;
+            }
+          }
         }
         if (st) return st;
         Stage s3(ctx, 3, 1);

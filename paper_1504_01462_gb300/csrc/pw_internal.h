@@ -135,10 +135,23 @@ struct RefineArgs {
   int lapack_piv;        // 1: the stored LU factors follow P W = L U (the sweep's
                          //    tensor-core FP32 form); 0: each panel's swaps reach only
                          //    the columns right of it (replayed panel by panel)
+  uint16_t *Osl, *Ysl;   // null, or the residual's exact slices (BF16 bit patterns, K-contiguous):
+                         //   RS_SLICES x 2n x 2n and RS_SLICES x (2 nc npts) x 2n, when every
+                         //   point shares its overlaps (the residual products run on the tensor cores)
+  int *Oexp, *Yexp;      //   their per-row / per-column power-of-two exponents (2n, 2 nc npts)
+  double *Yacc;          //   the products O y of all points, column-major 2n x (2 nc npts)
   cc *Bw, *Yw;           // null, or n x (2 nc npts) each: when every point shares its overlaps
                          //   and slice count, the backward pass's O products of all points
                          //   run as one tensor-core GEMM (operands Bw, result Yw)
 };
+
+constexpr int RS_SLICES = 7;   // slices per operand of the tensor-core residual
+constexpr int RS_BITS = 7;     // bits per slice
+constexpr int RS_PAIRS = RS_SLICES * (RS_SLICES + 1) / 2;   // slice pairs with s + t < RS_SLICES
+// bytes of the slice buffers for n basis functions and ncol = 2 nc npts columns
+inline size_t rs_slice_bytes(int n, long long ncol) {
+  return (size_t)RS_SLICES * 2 * n * (2 * (size_t)n + (size_t)ncol) * sizeof(uint16_t);
+}
 
 // 1 when every point of a launch has the same overlaps and slice count.
 inline int points_share_overlaps(const PointDesc *pd, int npts) {

@@ -25,6 +25,17 @@ def test_tcgen05_tile_product(pw):
     assert e3 < e1 / 50
 
 
+@pytest.mark.parametrize("n,ncol", [(512, 256), (100, 200), (4, 3)])
+def test_exact_slice_product(pw, n, ncol):
+    """The residual's slice product: 7-bit slices in BF16 on tcgen05 with FP32
+    accumulation are exact for 2n <= 1024 inner terms (sums up to 2^24 units at
+    n = 512); every slice pair summed in double-float is accurate to about
+    2^-48.  n = 100 and ncol = 200 leave ragged row, column and K tiles."""
+    bad, rel = pw.selftest_slice_product(n, ncol)
+    assert bad == 0, bad
+    assert rel < 1e-13, rel
+
+
 def _T(pw, inst, E, k, variant, refine_iters):
     T = torch.zeros(len(E), dtype=torch.float64, device="cuda")
     with pw.Context.from_instance(inst, pw.MIXED_FP32, refine_iters) as ctx:
