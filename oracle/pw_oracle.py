@@ -22,6 +22,9 @@ junction between two z-invariant electrodes:
 * App. A Eq. scatter: the interface scattering matrix S(p,p+1) from I.
 * Eq. recurrence (= App. A Eq. recurrence): the star product S(m,k) of
   S(m,n) and S(n,k), applied left to right over all interfaces.
+* Eq. recurrence2 (App. A, Sec. II A): layer doubling over the interfaces
+  with the transfer blocks I11, I12 and the scattering blocks S21, S22 while
+  cond(I11) stays below a criterion, then Eq. recurrence (``doubling``).
 * App. C: with z-invariant electrodes and no nonlocal terms the electrodes
   are slices 0 and N+1, so the junction's S(0,N+1) follows from two more
   interfaces; with A^0 = I and B^{N+1} = 0 the transmission amplitudes are
@@ -251,6 +254,75 @@ def star(Sa, Sb):
 
 
 # ---------------------------------------------------------------------------
+# Eq. recurrence2: layer doubling with transfer blocks I11, I12 and scattering
+# blocks S21, S22 while cond(I11) stays small (App. A, last part; Sec. II A)
+# ---------------------------------------------------------------------------
+COND_SWITCH = 1e4   # reading: the paper does not print its switching criterion
+
+
+def mixed_from_transfer(I11, I12, I21, I22):
+    """The mixed element (I11, I12, S21, S22) of one interface: the transfer
+    blocks of Eq. transfer and S21 = I21 I11^-1, S22 = I22 - I21 I11^-1 I12 of
+    Eq. scatter."""
+    _, _, S21, S22 = smatrix_from_transfer(I11, I12, I21, I22)
+    return I11, I12, S21, S22
+
+
+def star_mixed(Ta, Tb):
+    """Eq. recurrence2 (no nonlocal terms): the mixed element of (m,k) from
+    those of (m,n) = Ta and (n,k) = Tb, with X = I11(m,n) + I12(m,n) S21(n,k):
+    I11 = X I11(n,k), I12 = X I12(n,k) + I12(m,n) S22(n,k),
+    S21 = S21(m,n) + S22(m,n) S21(n,k) X^-1,
+    S22 = S22(m,n) S22(n,k) - S22(m,n) S21(n,k) X^-1 I12(m,n) S22(n,k)."""
+    a11, a12, a21, a22 = Ta
+    b11, b12, b21, b22 = Tb
+    X = a11 + a12 @ b21
+    Xinv = np.linalg.inv(X)
+    I11 = X @ b11
+    I12 = X @ b12 + a12 @ b22
+    S21 = a21 + a22 @ b21 @ Xinv
+    S22 = a22 @ b22 - a22 @ b21 @ Xinv @ a12 @ b22
+    return I11, I12, S21, S22
+
+
+def s_from_mixed(T):
+    """S11 = I11^-1 and S12 = -I11^-1 I12 (Eq. scatter); S21, S22 carried over."""
+    I11, I12, S21, S22 = T
+    S11 = np.linalg.inv(I11)
+    return S11, -S11 @ I12, S21, S22
+
+
+def doubling(elements, cond_max=COND_SWITCH):
+    """S of the whole stack from the mixed elements of its interfaces, in
+    order, by layer doubling: neighbours are combined pairwise, level by level
+    (an odd block moves up unchanged), with Eq. recurrence2 as long as every
+    block's I11 has a 2-norm condition number of at most cond_max; once one
+    exceeds it, every block is turned into its scattering matrix (Eq. scatter)
+    and the remaining levels use Eq. recurrence.  Returns (S, level), level =
+    the number of doubling levels done in the mixed form."""
+    blocks = list(elements)
+    mixed, level = True, 0
+
+    def too_ill(bs):
+        return max(np.linalg.cond(b[0]) for b in bs) > cond_max
+
+    if too_ill(blocks):
+        blocks, mixed = [s_from_mixed(b) for b in blocks], False
+    while len(blocks) > 1:
+        comb = star_mixed if mixed else star
+        nxt = [comb(blocks[i], blocks[i + 1]) for i in range(0, len(blocks) - 1, 2)]
+        if len(blocks) % 2:
+            nxt.append(blocks[-1])
+        blocks = nxt
+        if mixed:
+            level += 1
+            if too_ill(blocks):
+                blocks, mixed = [s_from_mixed(b) for b in blocks], False
+    S = s_from_mixed(blocks[0]) if mixed else blocks[0]
+    return S, level
+
+
+# ---------------------------------------------------------------------------
 # whole path for one instance and k_par
 # ---------------------------------------------------------------------------
 class Model:
@@ -285,6 +357,17 @@ class Model:
         O = overlap(Up, Uq)
         return smatrix_from_transfer(*transfer_matrix(O, kz(E, Ep), kz(E, Eq),
                                                       self.thickness(p + 1)))
+
+    def interface_mixed(self, modes, E, p):
+        """The mixed element (I11, I12, S21, S22) of interface (p, p+1)."""
+        (Ep, Up), (Eq, Uq) = modes[p], modes[p + 1]
+        O = overlap(Up, Uq)
+        return mixed_from_transfer(*transfer_matrix(O, kz(E, Ep), kz(E, Eq), self.thickness(p + 1)))
+
+    def total_s_doubling(self, modes, E, cond_max=COND_SWITCH):
+        """S(0, N+1) by layer doubling with Eq. recurrence2 while cond(I11) <=
+        cond_max, then Eq. recurrence; returns (S, mixed levels)."""
+        return doubling([self.interface_mixed(modes, E, p) for p in range(self.N + 1)], cond_max)
 
     def total_s(self, modes, E, p0=0, p1=None):
         """S(p0, p1) by applying Eq. recurrence left to right."""

@@ -88,3 +88,37 @@ def test_wrong_transfer_sign_is_caught(monkeypatch):
         return I11, I21, I12, I22
     monkeypatch.setattr(O, "transfer_matrix", bad)
     _expect_failure(pins.test_rectangular_barrier_closed_form, 0.5, 0.3, 1.3, (0.0, 0.0), 3)
+
+
+# ---------------------------------------------------------------------------
+# Eq. recurrence2 (layer doubling with transfer and scattering blocks)
+# ---------------------------------------------------------------------------
+def _star_mixed_variant(kind):
+    def f(Ta, Tb):
+        a11, a12, a21, a22 = Ta
+        b11, b12, b21, b22 = Tb
+        X = (a11 + b21 @ a12) if kind == "transposed_x" else (a11 + a12 @ b21)
+        Xinv = np.linalg.inv(X)
+        I11 = X @ b11
+        I12 = X @ b12 if kind == "dropped_term" else X @ b12 + a12 @ b22
+        S21 = (a21 + Xinv @ a22 @ b21) if kind == "inverse_side" else (a21 + a22 @ b21 @ Xinv)
+        sign = 1.0 if kind == "sign" else -1.0
+        S22 = a22 @ b22 + sign * a22 @ b21 @ Xinv @ a12 @ b22
+        return I11, I12, S21, S22
+    return f
+
+
+@pytest.mark.parametrize("kind", ["transposed_x", "dropped_term", "inverse_side", "sign"])
+def test_mixed_recurrence_mistakes_are_caught(monkeypatch, kind):
+    import tests.test_oracle_recurrence2 as r2
+    monkeypatch.setattr(O, "star_mixed", _star_mixed_variant(kind))
+    with pytest.raises(AssertionError):
+        r2.test_mixed_blocks_are_the_transfer_matrix_product()
+        r2.test_mixed_step_equals_star_product(3)
+
+
+def test_missing_switch_is_caught(monkeypatch):
+    import tests.test_oracle_recurrence2 as r2
+    orig = O.doubling
+    monkeypatch.setattr(O, "doubling", lambda elements, cond_max=O.COND_SWITCH: orig(elements, np.inf))
+    _expect_failure(r2.test_doubling_matches_left_to_right_sweep, "junction")
