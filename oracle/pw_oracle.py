@@ -260,6 +260,15 @@ def star(Sa, Sb):
 COND_SWITCH = 1e4   # reading: the paper does not print its switching criterion
 
 
+def i11_growth(I11):
+    """The switching measure of Eq. recurrence2: the 1-norm (largest absolute
+    column sum) of I11.  I11 = S11^-1 with S11 bounded by flux conservation
+    (its evanescent entries decay), so the norm of I11 tracks its condition
+    number: it grows with the exponentials of the evanescent modes that make
+    the transfer form unstable."""
+    return float(np.abs(I11).sum(axis=0).max())
+
+
 def mixed_from_transfer(I11, I12, I21, I22):
     """The mixed element (I11, I12, S21, S22) of one interface: the transfer
     blocks of Eq. transfer and S21 = I21 I11^-1, S22 = I22 - I21 I11^-1 I12 of
@@ -296,15 +305,15 @@ def doubling(elements, cond_max=COND_SWITCH):
     """S of the whole stack from the mixed elements of its interfaces, in
     order, by layer doubling: neighbours are combined pairwise, level by level
     (an odd block moves up unchanged), with Eq. recurrence2 as long as every
-    block's I11 has a 2-norm condition number of at most cond_max; once one
-    exceeds it, every block is turned into its scattering matrix (Eq. scatter)
-    and the remaining levels use Eq. recurrence.  Returns (S, level), level =
-    the number of doubling levels done in the mixed form."""
+    block's I11 has i11_growth at most cond_max; once one exceeds it, every
+    block is turned into its scattering matrix (Eq. scatter) and the remaining
+    levels use Eq. recurrence.  Returns (S, level), level = the number of
+    doubling levels done in the mixed form."""
     blocks = list(elements)
     mixed, level = True, 0
 
     def too_ill(bs):
-        return max(np.linalg.cond(b[0]) for b in bs) > cond_max
+        return max(i11_growth(b[0]) for b in bs) > cond_max
 
     if too_ill(blocks):
         blocks, mixed = [s_from_mixed(b) for b in blocks], False
@@ -365,8 +374,8 @@ class Model:
         return mixed_from_transfer(*transfer_matrix(O, kz(E, Ep), kz(E, Eq), self.thickness(p + 1)))
 
     def total_s_doubling(self, modes, E, cond_max=COND_SWITCH):
-        """S(0, N+1) by layer doubling with Eq. recurrence2 while cond(I11) <=
-        cond_max, then Eq. recurrence; returns (S, mixed levels)."""
+        """S(0, N+1) by layer doubling with Eq. recurrence2 while the growth of
+        I11 stays <= cond_max, then Eq. recurrence; returns (S, mixed levels)."""
         return doubling([self.interface_mixed(modes, E, p) for p in range(self.N + 1)], cond_max)
 
     def total_s(self, modes, E, p0=0, p1=None):

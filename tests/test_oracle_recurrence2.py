@@ -1,6 +1,6 @@
 """Pins of the oracle's layer doubling with Eq. recurrence2 (transfer blocks
 I11, I12 with scattering blocks S21, S22, switched to Eq. recurrence once
-cond(I11) grows).  Each test checks it against something other than itself:
+the norm of I11 grows).  Each test checks it against something other than itself:
 the plain product of the transfer matrices of Eq. transfer (the chain of
 Eq. smm1), the star product of Eq. recurrence, the dense solve of all matching
 conditions and the 40-digit matrix-exponential solve; and the instability the
@@ -104,7 +104,7 @@ def test_doubling_matches_left_to_right_sweep(which):
         assert abs(T - ref[i]) < 1e-10 * max(1.0, ref[i])
         assert 1 <= level
         if which == "junction":
-            assert level < levels   # cond(I11) grew past the criterion before the last level
+            assert level < levels   # I11 grew past the criterion before the last level
 
 
 def test_switch_is_needed():
@@ -132,7 +132,7 @@ def test_switch_is_needed():
 
 def test_single_interface_and_ill_conditioned_start():
     """One interface: the doubling is Eq. scatter itself.  A criterion below
-    every interface's cond(I11) turns the elements into scattering matrices
+    every interface's I11 norm turns the elements into scattering matrices
     before any mixed level, and the result is the left-to-right sweep's."""
     inst, _, _ = _tiny_random_instance(8, 2.2, (0.0, 0.3), nsl=3)
     m, E, md = _setup(inst)
@@ -144,3 +144,25 @@ def test_single_interface_and_ill_conditioned_start():
     assert lv == 0
     for x, y in zip(S, m.total_s(md, E)):
         assert _rel(x, y) < 1e-11
+
+
+def test_switching_measure_tracks_the_condition_number():
+    """The switching measure is the matrix 1-norm of I11 (largest column sum,
+    not the row sum), and on a junction it switches at the same level as the
+    2-norm condition number would."""
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5))
+    A[:, 2] *= 50.0
+    assert abs(O.i11_growth(A) - np.linalg.norm(A, 1)) < 1e-12 * np.linalg.norm(A, 1)
+    assert O.i11_growth(A) != pytest.approx(np.linalg.norm(A, np.inf))
+    inst = junction(ng=48, n_slices=40, n_e=1, n_k=1)
+    m, E, md = _setup(inst)
+    els = [m.interface_mixed(md, E, p) for p in range(m.N + 1)]
+    _, lv = O.doubling(els)
+    orig = O.i11_growth
+    try:
+        O.i11_growth = lambda I11: float(np.linalg.cond(I11))
+        _, lv2 = O.doubling(els)
+    finally:
+        O.i11_growth = orig
+    assert lv == lv2
