@@ -173,6 +173,44 @@ pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double 
 pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
                      pw_c128 *Sab_dev);
 
+/* The mixed element of interface (iface, iface+1) for layer doubling with
+ * App. A Eq. recurrence2: the transfer blocks I11 = P E-, I12 = Q E+ of
+ * Eq. transfer and the scattering blocks S21, S22 of Eq. scatter (P, Q the
+ * interface's matching blocks, E-+ = diag(e^{-+ik^{iface+1} dz})), for npts
+ * points: T_dev[npts * 4 * N_G * N_G], per point the blocks I11, I12, S21,
+ * S22 (column-major).  I11 carries the growing exponentials of evanescent
+ * modes.  FP64.  Returns PW_ESINGULAR if an interface's P has a zero pivot. */
+pw_status pw_slice_mixed(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface,
+                         pw_c128 *T_dev);
+
+/* One step of App. A Eq. recurrence2 (no nonlocal terms) for npts pairs of
+ * mixed elements (layout of pw_slice_mixed): with X = I11(m,n) + I12(m,n) S21(n,k),
+ *   I11(m,k) = X I11(n,k),  I12(m,k) = X I12(n,k) + I12(m,n) S22(n,k),
+ *   S21(m,k) = S21(m,n) + S22(m,n) S21(n,k) X^-1,
+ *   S22(m,k) = S22(m,n) S22(n,k) - S22(m,n) S21(n,k) X^-1 I12(m,n) S22(n,k).
+ * Tab_dev may not alias the inputs.  FP64; PW_ESINGULAR on a zero pivot of X. */
+pw_status pw_compose_mixed(pw_ctx *ctx, int npts, const pw_c128 *Ta_dev, const pw_c128 *Tb_dev,
+                           pw_c128 *Tab_dev);
+
+/* T(E, k_par) by layer doubling (App. A Eq. recurrence2, then Eq. recurrence):
+ * for each point the N+1 interfaces' mixed elements are combined pairwise,
+ * level by level (an odd last block moves up unchanged), with Eq. recurrence2
+ * while the 1-norm of every block's I11 (largest absolute column sum) stays
+ * at most cond_max; once one exceeds it (checked on the elements and after
+ * each level), every block becomes its scattering matrix by Eq. scatter
+ * (S11 = I11^-1, S12 = -I11^-1 I12) and the rest uses Eq. recurrence.  Then
+ * t and T as in pw_transmission.  T_dev: device, npts doubles; levels_host:
+ * NULL or npts ints, the mixed levels done per point (-1 at a threshold).
+ * FP64 throughout (any precision of the context), one point after another,
+ * synchronises the stream.  Device memory: the N+1 elements of a point and
+ * half as many for the next level (64 N_G^2 bytes each), and work for up to
+ * 2 x SMs combinations at a time (64 N_G^2 bytes each).
+ * cond_max <= 0 or NaN: PW_EINVAL.  PW_ETHRESH (T = NaN there) and
+ * PW_ESINGULAR as for pw_transmission.  A latency-oriented path (its
+ * combinations run one CTA each); pw_transmission is the throughput path. */
+pw_status pw_transmission_doubling(pw_ctx *ctx, int npts, const double *E, const double *kpar,
+                                   double cond_max, double *T_dev, int *levels_host);
+
 /* The forward hot path: for each point (E[i], kpar[2i..2i+1]) the junction's
  * S11(0,N+1) by a left-to-right sweep of star products over all N+1
  * interfaces, then t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels and

@@ -239,13 +239,31 @@ int sweep_variants(int precision);
 cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_iters, double tol,
                           cudaStream_t s, int *passes);
 size_t refine_smem_bytes(int n);
-// explicit interface S-matrices (FP64)
+// explicit interface S-matrices (FP64): npts CTAs, CTA b at point b and interface
+// iface, or (by_iface) at point 0 and interface iface + b; output blocks at
+// S + b * sstride (0: 4 n^2); mixed: the element (I11, I12, S21, S22) of Eq. recurrence2
 cudaError_t launch_slice_smatrix(const PointDesc *pts, const double *En, const zc *O, const double *dz,
                                  zc *work, int *piv, int *status, zc *S, int n, int N, int iface,
-                                 int npts, cudaStream_t s);
-// star products (FP64)
+                                 int npts, cudaStream_t s, int mixed = 0, size_t sstride = 0, int by_iface = 0);
+// element strides (complex values) of the operands and result of a batched combination
+struct Strides {
+  size_t a, b, c;
+};
+// star products (FP64); CTA i combines Sa + i str.a and Sb + i str.b into Sab + i str.c
+// (zero strides: 4 n^2 each)
 cudaError_t launch_compose(const zc *Sa, const zc *Sb, zc *Sab, zc *work, int *piv, int *status,
-                           int n, int npts, cudaStream_t s);
+                           int n, int npts, cudaStream_t s, Strides str = Strides{0, 0, 0});
+// layer doubling with Eq. recurrence2 (FP64): one step per pair (work n x 4n per pair)
+cudaError_t launch_compose_mixed(const zc *Ta, const zc *Tb, zc *Tab, zc *work, int *piv, int *status, int n,
+                                 int npairs, cudaStream_t s, Strides str);
+// Eq. scatter on mixed elements in place (work n x 3n per block)
+cudaError_t launch_mixed_to_s(zc *T, size_t stride, zc *work, int *piv, int *status, int n, int nblocks,
+                              cudaStream_t s);
+// the 1-norm of each block's I11 (the switching measure of Eq. recurrence2)
+cudaError_t launch_i11_norm(const zc *T, size_t stride, int n, int nblocks, double *out, cudaStream_t s);
+// T of one point from its S11 and the electrodes' ascending eigenvalues
+cudaError_t launch_t_from_s(const zc *S11, const double *EnL, const double *EnR, double E, int n, int nL, int nR,
+                            double *T_out, cudaStream_t s);
 
 // Read-only view of a one-problem context's geometry (pw_api.cu), for the
 // batch executor (pw_batch.cu).
