@@ -122,3 +122,97 @@ def test_missing_switch_is_caught(monkeypatch):
     orig = O.doubling
     monkeypatch.setattr(O, "doubling", lambda elements, cond_max=O.COND_SWITCH: orig(elements, np.inf))
     _expect_failure(r2.test_doubling_matches_left_to_right_sweep, "junction")
+
+
+# ---------------------------------------------------------------------------
+# periodic electrodes (App. B complex bands, App. C)
+# ---------------------------------------------------------------------------
+def test_conjugated_tilt_phases_are_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import tests.test_oracle_periodic as per
+    orig = CB.tilt_phases
+    monkeypatch.setattr(CB, "tilt_phases", lambda G, a3: np.conj(orig(G, a3)))
+    _expect_failure(per.test_tilted_cell_perfect_crystal)
+
+
+def test_bloch_problem_sign_mistake_is_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import scipy.linalg
+    import tests.test_oracle_periodic as per
+
+    def bad(S):
+        S11, S12, S21, S22 = S
+        n = S11.shape[0]
+        Id, Z = np.eye(n, dtype=np.complex128), np.zeros((n, n), dtype=np.complex128)
+        return scipy.linalg.eig(np.block([[S11, Z], [S21, Id]]), np.block([[Id, -S12], [Z, -S22]]))
+    monkeypatch.setattr(CB, "complex_bands", bad)
+    # invisible for uniform cells (S12 = S21 = 0 there); random cells catch it
+    with pytest.raises((AssertionError, ValueError, np.linalg.LinAlgError)):
+        per.test_periodic_electrodes_conserve_flux_and_pair_bloch_factors(4, 3.7, (0.13, -0.21))
+
+
+def test_missing_flux_normalisation_is_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import tests.test_oracle_periodic as per
+    orig = CB.bloch_states
+
+    def unnormalised(lam, X, ref_mode, E, tol=1e-7):
+        st = orig(lam, X, ref_mode, E, tol)
+        for side in ("R", "L"):
+            p = st["prop" + side]
+            nrm = np.sqrt(np.sum(np.abs(st["a" + side][:, p]) ** 2 + np.abs(st["b" + side][:, p]) ** 2, axis=0))
+            st["a" + side][:, p] /= nrm
+            st["b" + side][:, p] /= nrm
+        return st
+    monkeypatch.setattr(CB, "bloch_states", unnormalised)
+    _expect_failure(per.test_periodic_electrodes_conserve_flux_and_pair_bloch_factors, 4, 3.7, (0.13, -0.21))
+
+
+def test_wrong_next_cell_in_the_right_electrode_is_caught(monkeypatch):
+    from oracle import complex_bands as CB
+    import tests.test_oracle_periodic as per
+    orig = CB.cell_smatrix
+    # every slice after the reference moved, as if the whole chain were the next cell
+    monkeypatch.setattr(CB, "cell_smatrix",
+                        lambda modes, dz, E, D=None, ref="last": orig(modes, dz, E, D, "last") if D is None
+                        else CB.chain_s(list(modes) + [(modes[0][0], D[:, None] * modes[0][1])],
+                                        [0.0] + list(dz[1:]) + [dz[0]], E) if ref == "last"
+                        else CB.chain_s([modes[0]] + [(m[0], D[:, None] * m[1]) for m in modes[1:]]
+                                        + [(modes[0][0], D[:, None] * modes[0][1])],
+                                        [0.0] + list(dz[1:]) + [dz[0]], E))
+    _expect_failure(per.test_tilted_cell_perfect_crystal)
+
+
+# ---------------------------------------------------------------------------
+# separable projector terms (Eqs. nloc, gsol_p0, calm_0)
+# ---------------------------------------------------------------------------
+def test_missing_cell_area_in_calm_is_caught(monkeypatch):
+    from oracle import separable as NL
+    import tests.test_oracle_separable as sep
+    orig = NL.transmission_nonlocal
+    monkeypatch.setattr(NL, "transmission_nonlocal",
+                        lambda modes, dz, E, projs, D, area, q=16: orig(modes, dz, E, projs, D, 1.0, q))
+    _expect_failure(sep.test_one_dimensional_separable_potential_closed_form, 0.9, (1, 4))
+
+
+def test_incoming_green_function_is_caught(monkeypatch):
+    from oracle import separable as NL
+    import tests.test_oracle_separable as sep
+    orig = NL._slice_terms
+
+    def incoming(U, k, za, zb, projs, q):   # e^{-ik|u|}: the other branch, no longer outgoing
+        return orig(U, -k, za, zb, projs, q)
+    monkeypatch.setattr(NL, "_slice_terms", incoming)
+    _expect_failure(sep.test_one_dimensional_separable_potential_closed_form, 0.9, (1, 4))
+
+
+def test_particular_derivatives_dropped_are_caught(monkeypatch):
+    from oracle import separable as NL
+    import tests.test_oracle_separable as sep
+    orig = NL._slice_terms
+
+    def no_deriv(U, k, za, zb, projs, q):
+        fa, dfa, fb, dfb, Ha, Hb, P = orig(U, k, za, zb, projs, q)
+        return fa, 0 * dfa, fb, 0 * dfb, Ha, Hb, P
+    monkeypatch.setattr(NL, "_slice_terms", no_deriv)
+    _expect_failure(sep.test_hermitian_projector_terms_conserve_flux, np.diag([0.8, -1.3]))
