@@ -90,6 +90,8 @@ struct SweepArgs {
                          //    overlap O_p -> O_{N-p}^T), used by the adjoint
   int wy_pairs;          // 1: points 2i and 2i+1 share overlaps and slice count (the
                          //    tensor-core [W|Y] then stages one B tile for both)
+  int *rowexp;           // null, or per point 2n: the power-of-two row scales of R and of
+                         //   R K_p^{-1} for the FP16-split [W|Y] (sweep variant bit 2)
 };
 
 // 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and
