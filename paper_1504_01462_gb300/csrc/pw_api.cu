@@ -63,6 +63,7 @@ struct pw_ctx {
   int last_sweeps = 0;                       // most Jacobi sweeps of one matrix in the last eig
   // per-point workspaces
   DevBuf R, M, piv, pts, status, work, KV;
+  DevBuf rowexp;                   // row scales of the FP16-split [W|Y] (sweep variant bit 2)
   DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   DevBuf Xa_m, Xb_m, status_m, Tg, Gam, gtab, T1, dV0, wgt;   // adjoint (pw_grad)
   DevBuf corr;                     // refinement stopping test
@@ -547,7 +548,7 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
-                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p};
+                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -912,7 +913,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
           (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
           (st = ensure(ctx, ctx->KV, (size_t)nb * 3 * n * esz)) ||
           (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
-          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
+          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))) ||
+          ((ctx->sweep_variant & 4) && (st = ensure(ctx, ctx->rowexp, (size_t)nb * 2 * n * sizeof(int)))))
         return st;
       const size_t vec = (size_t)nb * n * nc;
       if (refine &&
@@ -931,6 +933,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
       CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
       pw::SweepArgs a;
+      memset(&a, 0, sizeof(a));
       a.pts = (const PointDesc *)ctx->pts.p;
       a.En = ctx->d_En;
       a.O = ctx->d_O;
@@ -955,8 +958,11 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.KV = ctx->KV.p;
       a.mirror = 0;
       a.wy_pairs = pw::points_pair_up(pd.data(), nb);
+      a.rowexp = (ctx->sweep_variant & 4) ? (int *)ctx->rowexp.p : nullptr;
       CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
-      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant));
+      // the FP16-split [W|Y] adds its row-scale kernel at every interface with a product (p >= 1)
+      const int f16_extra = (a.rowexp && a.wy_pairs && (ctx->sweep_variant & 6) == 6) ? N : 0;
+      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant) + f16_extra);
       for (int p = 0; p <= N; ++p) {
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }

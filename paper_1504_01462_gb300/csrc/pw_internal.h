@@ -94,6 +94,8 @@ struct SweepArgs {
                          //    panel's row swaps also reach the L columns left of it (so
                          //    the stored factors satisfy P W = L U with P from piv in
                          //    order) and the right-hand sides are eliminated after the LU
+  int *rowexp;           // null, or per point 2n: the power-of-two row scales of R and of
+                         //   R K_p^{-1} for the FP16-split [W|Y] (sweep variant bit 2)
 };
 
 // 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and

@@ -298,6 +298,114 @@ __global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc(SweepArgs a, int 
   }
 }
 
+// Row scales of the FP16-split [W|Y] (kb_wy2_tc16): for every point and row i,
+// rowexp[2i] = e with max_l |R_il| < 2^e (largest real or imaginary part) and
+// rowexp[2i+1] the same for R_il / k_l^p.  One thread per row (consecutive
+// rows are contiguous in R).
+__global__ void __launch_bounds__(256) kb_rowexp(SweepArgs a) {
+  const int pt = blockIdx.y, i = blockIdx.x * 256 + threadIdx.x;
+  if (inactive(a, pt) || i >= a.n) return;
+  const int n = a.n;
+  const cc *R = reinterpret_cast<const cc *>(a.R) + (size_t)pt * n * n;
+  const KVb<float> v = kv_of<float>(a, pt);
+  float m0 = 0.f, m1 = 0.f;
+  for (int l = 0; l < n; ++l) {
+    const cc r = R[i + (size_t)l * n];
+    const cc rs = cmul(r, v.kinvL[l]);
+    m0 = fmaxf(m0, fmaxf(fabsf(r.re), fabsf(r.im)));
+    m1 = fmaxf(m1, fmaxf(fabsf(rs.re), fabsf(rs.im)));
+  }
+  int e0 = 0, e1 = 0;
+  if (m0 > 0.f) frexpf(m0, &e0);
+  if (m1 > 0.f) frexpf(m1, &e1);
+  // keep the scales inside FP32's normal range (the values themselves are)
+  a.rowexp[(size_t)pt * 2 * n + 2 * i] = max(-100, min(100, e0));
+  a.rowexp[(size_t)pt * 2 * n + 2 * i + 1] = max(-100, min(100, e1));
+}
+
+// [W|Y] of point pairs as kb_wy2_tc, the products in the FP16 split with the
+// row scales of kb_rowexp (the overlap, the shared B, is bounded by 1).
+size_t wy2_tc16_smem_bytes(int n) { return tc::c4_smem_bytes16() + 4 * (size_t)n * sizeof(cc); }
+
+__global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc16(SweepArgs a, int p, int npts) {
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
+  const int pt0 = 2 * blockIdx.y, pt1 = pt0 + 1;
+  const bool act0 = !inactive(a, pt0), act1 = pt1 < npts && !inactive(a, pt1);
+  if (!act0 && !act1) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int tiles_m = (n + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), c0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const PointDesc d = a.pts[act0 ? pt0 : pt1];   // both points have this one's overlaps
+  const bool tr = a.mirror != 0;
+  const int pi = tr ? d.N - p : p;
+  const zc *O = overlap_of(a, d, p);
+  const cc *O32 = overlap32_of(a, d, p);
+  const cc *O32t = a.O32t ? a.O32t + ((size_t)d.o_off + pi) * n * n : nullptr;
+  auto ov = [=](int l, int j) -> cc {
+    if (tr) {
+      if (O32) return tc::ldg_cc(O32 + j + (size_t)l * n);
+      return ccast<float>(O[j + (size_t)l * n]);
+    }
+    if (O32t) return tc::ldg_cc(O32t + j + (size_t)l * n);
+    if (O32) return tc::ldg_cc(O32 + l + (size_t)j * n);
+    return ccast<float>(O[l + (size_t)j * n]);
+  };
+  auto ovc = [=](int l, int j) -> cc {
+    if (tr) {
+      if (O32t) return O32t[l + (size_t)j * n];
+      if (O32) return O32[j + (size_t)l * n];
+      return ccast<float>(O[j + (size_t)l * n]);
+    }
+    if (O32) return O32[l + (size_t)j * n];
+    return ccast<float>(O[l + (size_t)j * n]);
+  };
+  const int q1 = act1 ? pt1 : pt0;
+  const cc *R0 = reinterpret_cast<const cc *>(a.R) + (size_t)pt0 * n * n;
+  const cc *R1 = reinterpret_cast<const cc *>(a.R) + (size_t)q1 * n * n;
+  const int *X0 = a.rowexp + (size_t)pt0 * 2 * n, *X1 = a.rowexp + (size_t)q1 * 2 * n;
+  cc *M0 = reinterpret_cast<cc *>(a.M) + (size_t)pt0 * n * ncols;
+  cc *M1 = reinterpret_cast<cc *>(a.M) + (size_t)q1 * n * ncols;
+  cc *sk = reinterpret_cast<cc *>(smraw + tc::c4_smem_bytes16());   // kinvL0, kR0, kinvL1, kR1
+  const KVb<float> g0 = kv_of<float>(a, pt0), g1 = kv_of<float>(a, q1);
+  for (int i = threadIdx.x; i < n; i += tc::CG_THREADS) {
+    sk[i] = g0.kinvL[i];
+    sk[n + i] = g0.kR[i];
+    sk[2 * n + i] = g1.kinvL[i];
+    sk[3 * n + i] = g1.kR[i];
+  }
+  __syncthreads();
+  const unsigned amask = (act0 ? 3u : 0u) | (act1 ? 12u : 0u);
+  const bool ok = tc::cgemm_tile_shared_b_f16(
+      n, n, n, r0, c0, amask,
+      [=](int h, int i, int l) { return tc::ldg_cc((h ? R1 : R0) + i + (size_t)l * n); },
+      [=](int h, int l) { return sk[h * 2 * n + l]; },   // kinvL of point h
+      [=](int l, int j) { return ov(l, j); },
+      [=](int q, int i) { return ((q >> 1) ? X1 : X0)[2 * i + (q & 1)]; },
+      [=](int i, int j, const cc (&x)[4]) {
+        const cc o = ovc(i, j);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!((amask >> (2 * h)) & 1u)) continue;
+          const cc *kinv = sk + h * 2 * n, *kr = kinv + n;
+          const cc r = cmul(kr[j], kinv[i]);
+          const cc P = cmul(o, mkc<float>(0.5f * (1.f + r.re), 0.5f * r.im));
+          const cc Q = cmul(o, mkc<float>(0.5f * (1.f - r.re), -0.5f * r.im));
+          const cc t = cmul(kr[j], x[2 * h + 1]);
+          const cc rq = mkc<float>(0.5f * (x[2 * h].re - t.re), 0.5f * (x[2 * h].im - t.im));
+          const cc rp = mkc<float>(0.5f * (x[2 * h].re + t.re), 0.5f * (x[2 * h].im + t.im));
+          cc *M = h ? M1 : M0;
+          M[i + (size_t)j * n] = csub(P, rq);
+          M[i + (size_t)(n + j) * n] = csub(rp, Q);
+        }
+      },
+      smraw);
+  if (!ok && threadIdx.x == 0) {
+    if (act0) a.status[pt0] = 2;
+    if (act1) a.status[pt1] = 2;
+  }
+}
+
 // Tile width of the update kernels (read-modify-write of C): 64 complex
 // columns keep the prefetched C values of a thread in 32 registers.
 constexpr int RMW_TN = 64;
@@ -750,7 +858,7 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
 
 template <typename T, int BT>
 static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
-                              cudaEvent_t wy1, bool tensor_core) {
+                              cudaEvent_t wy1, bool tensor_core, bool f16 = false) {
   SweepArgs a = a0;
   a.p = p;
   const int n = a.n, ncols = 2 * n + a.nc;
@@ -765,7 +873,11 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   if (p > 0) {
     const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
     if (wy0) cudaEventRecord(wy0, s);
-    if (std::is_same<T, float>::value && tensor_core && a.wy_pairs)
+    if (std::is_same<T, float>::value && tensor_core && a.wy_pairs && f16 && a.rowexp) {
+      kb_rowexp<<<dim3((n + 255) / 256, npts), 256, 0, s>>>(a);
+      kb_wy2_tc16<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
+                    wy2_tc16_smem_bytes(n), s>>>(a, p, npts);
+    } else if (std::is_same<T, float>::value && tensor_core && a.wy_pairs)
       kb_wy2_tc<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
                   wy2_tc_smem_bytes(n), s>>>(a, p, npts);
     else if (std::is_same<T, float>::value && tensor_core)
@@ -871,6 +983,8 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
     e = cudaFuncSetAttribute(kb_fsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_rhs_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_perm_smem(n));
+  if (e == cudaSuccess && (variant & 6) == 6)
+    e = cudaFuncSetAttribute(kb_wy2_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wy2_tc16_smem_bytes(n));
   return e;
 }
 
@@ -880,11 +994,12 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
   if (precision == PW_FP64)
     return (variant & 1) ? sweep_step<double, 512>(a, npts, p, s, wy0, wy1, false)
                          : sweep_step<double, 256>(a, npts, p, s, wy0, wy1, false);
-  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore)
-                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore);
+  const bool f16 = (variant & 4) != 0;   // FP16 split for the paired [W|Y]
+  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore, f16)
+                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore, f16);
 }
 
-int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 4; }
+int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 8; }
 
 int sweep_batched_launches(int n, int precision, int variant) {
   const int NB = Tile<float, 256>::NB;

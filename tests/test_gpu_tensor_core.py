@@ -65,3 +65,25 @@ def test_sweep_with_tensor_core_products(pw, variant):
     assert np.all(np.abs(raw - simt) / scale < 1e-4)
     got = _T(pw, inst, E, k, variant, 4)
     assert np.all(np.abs(got - ref) / scale < 1e-8), (got, ref)
+
+
+@pytest.mark.parametrize("variant", [6, 7])
+def test_sweep_with_fp16_split_point_pairs(pw, variant):
+    """The paired [W|Y] in the FP16 split (sweep variant bit 2, four points of
+    one k_par so that pairs share the overlap): the unrefined sweep agrees
+    with the TF32-split sweep and the oracle at FP32 level, the refined one
+    meets 1e-8."""
+    import numpy as np
+    from oracle import pw_oracle as O
+    from synthetic import junction
+    inst = junction(ng=97, n_slices=60, n_e=4, n_k=1)
+    E, k = inst.energies, inst.kpar
+    ref = O.transmission(inst)
+    scale = np.maximum(1.0, np.abs(ref))
+    raw = _T(pw, inst, E, k, variant, -1)
+    assert np.all(np.abs(raw - ref) / scale < 1e-4), (raw, ref)
+    tf32 = _T(pw, inst, E, k, variant & 3, -1)
+    assert np.all(np.abs(raw - tf32) / scale < 1e-4)
+    got = _T(pw, inst, E, k, variant, 4)
+    assert np.all(np.abs(got - ref) / scale < 1e-8), (got, ref)
+
