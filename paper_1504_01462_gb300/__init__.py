@@ -34,7 +34,7 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_get_profile", "pw_compose_noalloc", "pw_grad", "pw_setup_batch",
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
            "pw_batch_destroy", "pw_get_error_detail", "pw_selftest_tensor_core",
-           "pw_set_sweep_variant"]
+           "pw_set_sweep_variant", "pw_selftest_f16_split"]
 
 
 class PwError(RuntimeError):
@@ -97,6 +97,7 @@ def _load():
     lib.pw_batch_destroy.argtypes = [_vp]
     lib.pw_get_error_detail.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
     lib.pw_selftest_tensor_core.argtypes = [_dp, _dp]
+    lib.pw_selftest_f16_split.argtypes = [_dp]
     lib.pw_set_sweep_variant.argtypes = [_vp, ctypes.c_int]
     lib.pw_batch_destroy.restype = None
     return lib
@@ -217,6 +218,14 @@ def selftest_tensor_core():
     b = np.zeros(1)
     _check_status(_lib.pw_selftest_tensor_core(_as_dp(a), _as_dp(b)), "pw_selftest_tensor_core")
     return float(a[0]), float(b[0])
+
+
+def selftest_f16_split():
+    """Relative error of one tile product in the FP16 split (sweep variant
+    bit 2) from the library's self-test on the current device."""
+    a = np.zeros(1)
+    _check_status(_lib.pw_selftest_f16_split(_as_dp(a)), "pw_selftest_f16_split")
+    return float(a[0])
 
 
 def _check_status(st, where):

@@ -25,6 +25,13 @@ def test_tcgen05_tile_product(pw):
     assert e3 < e1 / 50
 
 
+def test_fp16_split_tile_product(pw):
+    """The FP16 split's layout, descriptors and headroom on one tile: FP32-level
+    accuracy like the TF32 split."""
+    e = pw.selftest_f16_split()
+    assert e < 2e-6, e
+
+
 def _T(pw, inst, E, k, variant, refine_iters):
     T = torch.zeros(len(E), dtype=torch.float64, device="cuda")
     with pw.Context.from_instance(inst, pw.MIXED_FP32, refine_iters) as ctx:
