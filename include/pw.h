@@ -378,6 +378,15 @@ pw_status pw_selftest_tensor_core(double *rel_err_tf32, double *rel_err_split);
  * out.  A deployment check with no counterpart in the paper. */
 pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, double *rel_err);
 
+/* Self-test of the FP16 split used by sweep variant bit 2: the same 128 x 64
+ * tile product with K = 32 as hi/lo FP16 parts (kind::f16, three MMAs per K
+ * step of 16, operands scaled by the split's 2^8 headroom), against an FP64
+ * product of the same FP32 inputs: *rel_err = max|C - C_ref| / max|C_ref|
+ * (FP32 level, about 1e-7, expected).  Runs on the current device and
+ * synchronises it; PW_ETIMEOUT if the tensor core did not signal completion
+ * within its bounded wait.  A deployment check with no counterpart in the paper. */
+pw_status pw_selftest_f16_split(double *rel_err);
+
 #ifdef __cplusplus
 }
 #endif

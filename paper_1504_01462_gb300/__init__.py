@@ -35,7 +35,7 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
            "pw_batch_destroy", "pw_get_error_detail", "pw_selftest_tensor_core",
            "pw_set_sweep_variant", "pw_selftest_slice_product", "pw_slice_mixed", "pw_compose_mixed",
-           "pw_transmission_doubling"]
+           "pw_transmission_doubling", "pw_selftest_f16_split"]
 
 
 class PwError(RuntimeError):
@@ -103,6 +103,7 @@ def _load():
     lib.pw_selftest_tensor_core.argtypes = [_dp, _dp]
     lib.pw_selftest_slice_product.argtypes = [ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_longlong), _dp]
+    lib.pw_selftest_f16_split.argtypes = [_dp]
     lib.pw_set_sweep_variant.argtypes = [_vp, ctypes.c_int]
     lib.pw_batch_destroy.restype = None
     return lib
@@ -234,6 +235,14 @@ def selftest_slice_product(n, ncol):
     _check_status(_lib.pw_selftest_slice_product(int(n), int(ncol), ctypes.byref(bad), _as_dp(rel)),
                   "pw_selftest_slice_product")
     return int(bad.value), float(rel[0])
+
+
+def selftest_f16_split():
+    """Relative error of one tile product in the FP16 split (sweep variant
+    bit 2) from the library's self-test on the current device."""
+    a = np.zeros(1)
+    _check_status(_lib.pw_selftest_f16_split(_as_dp(a)), "pw_selftest_f16_split")
+    return float(a[0])
 
 
 def _check_status(st, where):

@@ -36,6 +36,13 @@ def test_exact_slice_product(pw, n, ncol):
     assert rel < 1e-13, rel
 
 
+def test_fp16_split_tile_product(pw):
+    """The FP16 split's layout, descriptors and headroom on one tile: FP32-level
+    accuracy like the TF32 split."""
+    e = pw.selftest_f16_split()
+    assert e < 2e-6, e
+
+
 def _T(pw, inst, E, k, variant, refine_iters):
     T = torch.zeros(len(E), dtype=torch.float64, device="cuda")
     with pw.Context.from_instance(inst, pw.MIXED_FP32, refine_iters) as ctx:
