@@ -1,5 +1,7 @@
 """The pins bite: plausible mistakes planted in the oracle (on the CPU, by
 monkeypatching) make at least one pin of test_oracle_pins fail."""
+import math
+
 import numpy as np
 import pytest
 
@@ -216,3 +218,18 @@ def test_particular_derivatives_dropped_are_caught(monkeypatch):
         return fa, 0 * dfa, fb, 0 * dfb, Ha, Hb, P
     monkeypatch.setattr(NL, "_slice_terms", no_deriv)
     _expect_failure(sep.test_hermitian_projector_terms_conserve_flux, np.diag([0.8, -1.3]))
+
+
+def test_continuum_pin_catches_a_misweighted_slice_average(monkeypatch):
+    """The slice average with sqrt(pi) in place of sqrt(pi/2) (each well's
+    z-weight off by sqrt 2) is caught by the continuum pin.  (Shifting every
+    well in z, or conjugating the tables - the transverse mirror image, with
+    T(-k) = T(k) for a real potential - leaves T unchanged: no T-based pin
+    sees those; the quadrature pin of the tables does.)"""
+    import tests.test_oracle_continuum as cont
+    orig = O.slice_vg_wells
+
+    def misweighted(a1, a2, half, wells, v0, sigma, z_lo, z_hi):
+        return math.sqrt(2.0) * orig(a1, a2, half, wells, v0, sigma, z_lo, z_hi)
+    monkeypatch.setattr(O, "slice_vg_wells", misweighted)
+    _expect_failure(cont.test_slice_model_converges_to_the_continuum, 3.4, (0.3, 0.2))
