@@ -107,3 +107,22 @@ def test_binding_marshals_batches_and_contexts(pw):
     with pytest.raises(pw.PwError) as e:
         pw.Context.from_instance(minimal_cell())
     assert e.value.code == 3      # PW_ECUDA
+
+
+def test_product_and_generators_never_use_the_oracle():
+    """The oracle is test infrastructure: no module of the package, the CUDA
+    sources or the shared input generators imports or names it, and the
+    oracle imports nothing from the package (the two share no code)."""
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b)|\boracle\.", re.M)
+    for base in ("paper_1504_01462_gb300", "synthetic"):
+        for dirpath, _, files in os.walk(os.path.join(ROOT, base)):
+            if "_build" in dirpath or "__pycache__" in dirpath:
+                continue
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".h")):
+                    src = open(os.path.join(dirpath, f)).read()
+                    assert not pat.search(src), os.path.join(dirpath, f)
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_1504_01462_gb300" not in src and "ctypes" not in src, f
