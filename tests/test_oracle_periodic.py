@@ -202,3 +202,38 @@ def test_band_folding_matches_the_supercell_problem():
     tb, rb, Tb = CB.transmission_from_states(mn, G, HALF, k, E, dev, dd, L2, R2, cell[1][0])
     assert abs(Ta - Tb) < 1e-12 * max(1.0, Ta)
     assert _flux_ok(tb, rb)
+
+
+@pytest.mark.parametrize("seed,E,k", [(21, 2.9, (0.17, -0.11)), (22, 1.4, (0.0, 0.25))])
+def test_bloch_factors_against_the_period_propagator(seed, E, k):
+    """The 2n Bloch factors of Eq. cmp (from the S-matrix chain of one period)
+    are the eigenvalues of the exact state propagator [c; c'](z + d) =
+    M [c; c'](z) over the period, M the product of the slices' matrix
+    exponentials evaluated with 40 digits (no modes, no S-matrices)."""
+    import mpmath as mp
+    rng = np.random.default_rng(seed)
+    mn, G = O.gvectors([A, 0.0], [0.0, A], 1.0 * B * B * (1 + 1e-9))
+    assert len(mn) == 5
+    tabs = random_tables(rng, 3, HALF, 0.5)
+    dz = [0.35, 0.5, 0.3]
+    kk = np.asarray(k)
+    _, st = CB.electrode_states(mn, G, HALF, kk, E, (tabs, dz), "last")
+    lam = np.concatenate([st["lamR"], st["lamL"]])
+    mp.mp.dps = 40
+    n = len(mn)
+    M = mp.eye(2 * n)
+    for t, d in zip(tabs, dz):
+        H = O.hamiltonian(mn, G, kk, t, HALF)
+        gen = mp.zeros(2 * n, 2 * n)
+        for i in range(n):
+            gen[i, n + i] = 1
+            for j in range(n):
+                gen[n + i, j] = mp.mpc(complex(H[i, j]))
+            gen[n + i, i] -= mp.mpf(E)
+        M = mp.expm(gen * mp.mpf(d)) * M
+    ev = mp.eig(M, left=False, right=False)
+    ref = np.array([complex(x) for x in ev])
+    for x in ref:
+        j = np.argmin(np.abs(lam - x))
+        assert abs(lam[j] - x) < 1e-11 * max(1.0, abs(x)), (x, lam[j])
+    assert len(lam) == len(ref) == 2 * n
