@@ -489,10 +489,10 @@ def main():
                     "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
         # every step is one k_par, so neighbouring points share their overlaps and the
         # tensor-core [W|Y] runs as kb_wy2_tc (point pairs sharing the B operand).  DRAM bytes
-        # of one launch (one interface, 128 points: dram__bytes_read.sum + dram__bytes_write.sum
-        # of an ncu capture of this kernel at this shape); None for any other kernel or shape,
-        # and to be reset to None whenever the kernel changes
-        wy_traffic = 770.7e6 if (tensor and n == 512 and n_e == 128) else None
+        # of one launch would come from an ncu capture of this kernel at this shape; the last
+        # capture (770.7 MB per launch) predates a change to the kernel's shared-memory
+        # declaration, so none is reported until the kernel is captured again
+        wy_traffic = None
         wy_obj = {"bound": "tensor" if tensor else "alu",
                   "kernel": ("kb_wy2_tc (tcgen05 kind::tf32, hi/lo split, point pairs share the B operand)"
                              if tensor else
