@@ -78,17 +78,21 @@ def heev_flops_per_matrix(n):
     return (16.0 / 3.0 + 4.5 + 8.0) * n ** 3
 
 
-def refine_launches(N, iters, batched=True):
+def refine_launches(N, iters, batched=True, sliced=True):
     """Launches of the mixed form's refinement: init; a backward pass; per pass
-    one residual launch and a forward pass (fwd_b at every interface, fwd_a
-    after the first), then (except after the last pass) a backward pass; the
-    finish.  A backward step is bwd_a + bwd_b per interface, or bwd_a, the
-    batched tensor-core product and its combine when every point of the launch
-    shares its overlaps (one k_par per step here)."""
+    the residual and a forward pass (fwd_b at every interface, fwd_a after the
+    first), then (except after the last pass) a backward pass; the finish.  A
+    backward step is bwd_a + bwd_b per interface, or bwd_a, the batched
+    tensor-core product and its combine when every point of the launch shares
+    its overlaps (one k_par per step here).  The residual is one launch, or,
+    as exact slice products on the tensor cores (shared overlaps, N_G a
+    multiple of 4 up to 512), four per interface (slice O, slice y, product,
+    combine)."""
     if iters <= 0:
         return 0
     bw = 3 if batched else 2
-    return 2 + bw * (N + 1) + iters * (1 + 2 * N + 1) + (iters - 1) * bw * (N + 1)
+    res = 4 * (N + 1) if sliced else 1
+    return 2 + bw * (N + 1) + iters * (res + 2 * N + 1) + (iters - 1) * bw * (N + 1)
 
 
 def sweep_flops_per_point(n, nopen_left):
@@ -265,6 +269,53 @@ def run_uneven(args, torch, pw, local):
     b.close()
 
 
+def run_doubling(args, torch, pw, local):
+    """The layer doubling of Eq. recurrence2 (FP64, one point after another)
+    on points of the chosen workload: a latency path, timed per point."""
+    inst, n_e, n_k = workload(args.config)
+    if args.slices:
+        inst.z_edges = np.linspace(inst.z_edges[0], inst.z_edges[-1], args.slices + 1)
+    stream = torch.cuda.current_stream()
+    ctx = pw.Context.from_instance(inst, precision=pw.FP64, stream=stream.cuda_stream)
+    npts = max(1, args.instances)
+    E, k = inst.energies[:npts], inst.kpar[:npts]
+    T = torch.empty(npts, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.transmission_doubling(E, k, T, allow_threshold=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    levels = None
+    for _ in range(args.steps):
+        levels = ctx.transmission_doubling(E, k, T, allow_threshold=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    # the same points by the sweep, for the comparison of T
+    Ts = torch.empty(npts, dtype=torch.float64, device="cuda")
+    ctx.transmission(E, k, Ts, allow_threshold=True)
+    torch.cuda.synchronize()
+    d = (T - Ts).abs() / Ts.abs().clamp(min=1.0)
+    line = {
+        "metric": "points/s by layer doubling (Eq. recurrence2, FP64)",
+        "value": args.steps * npts / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": f"{args.config}: N_G={ctx.ng}, {ctx.n_slices} slices, {npts} points",
+                   "composition": "doubling"},
+        "mixed_levels": [int(x) for x in levels],
+        "max_rel_diff_T_vs_sweep": float(torch.nan_to_num(d).max().item()),
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,6 +339,8 @@ def main():
                     help="skip the FP64 re-evaluation of sampled points of the last step")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the slice count (profiling of small cases only)")
+    ap.add_argument("--composition", default="sweep", choices=["sweep", "doubling"],
+                    help="doubling: time the layer doubling of Eq. recurrence2 (FP64, --instances points)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -304,6 +357,8 @@ def main():
     torch.cuda.set_device(local)
     if args.config == "uneven":
         return run_uneven(args, torch, pw, local)
+    if args.composition == "doubling":
+        return run_doubling(args, torch, pw, local)
     if world > 1:
         dist.init_process_group("nccl")
 
@@ -467,7 +522,8 @@ def main():
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
             "gpu_launches": int(prof["sweep_launches"] + modes_launches * prof["modes_stages"]
-                                + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1))
+                                + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1),
+                                                   sliced=(n <= 512 and n % 4 == 0))
                                    * args.steps if prec == pw.MIXED_FP32 else 0)),
             "e2e": (None if args.no_e2e else
                     {"value": e2e_value, "unit": "points/s",

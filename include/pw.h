@@ -173,6 +173,44 @@ pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double 
 pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
                      pw_c128 *Sab_dev);
 
+/* The mixed element of interface (iface, iface+1) for layer doubling with
+ * App. A Eq. recurrence2: the transfer blocks I11 = P E-, I12 = Q E+ of
+ * Eq. transfer and the scattering blocks S21, S22 of Eq. scatter (P, Q the
+ * interface's matching blocks, E-+ = diag(e^{-+ik^{iface+1} dz})), for npts
+ * points: T_dev[npts * 4 * N_G * N_G], per point the blocks I11, I12, S21,
+ * S22 (column-major).  I11 carries the growing exponentials of evanescent
+ * modes.  FP64.  Returns PW_ESINGULAR if an interface's P has a zero pivot. */
+pw_status pw_slice_mixed(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface,
+                         pw_c128 *T_dev);
+
+/* One step of App. A Eq. recurrence2 (no nonlocal terms) for npts pairs of
+ * mixed elements (layout of pw_slice_mixed): with X = I11(m,n) + I12(m,n) S21(n,k),
+ *   I11(m,k) = X I11(n,k),  I12(m,k) = X I12(n,k) + I12(m,n) S22(n,k),
+ *   S21(m,k) = S21(m,n) + S22(m,n) S21(n,k) X^-1,
+ *   S22(m,k) = S22(m,n) S22(n,k) - S22(m,n) S21(n,k) X^-1 I12(m,n) S22(n,k).
+ * Tab_dev may not alias the inputs.  FP64; PW_ESINGULAR on a zero pivot of X. */
+pw_status pw_compose_mixed(pw_ctx *ctx, int npts, const pw_c128 *Ta_dev, const pw_c128 *Tb_dev,
+                           pw_c128 *Tab_dev);
+
+/* T(E, k_par) by layer doubling (App. A Eq. recurrence2, then Eq. recurrence):
+ * for each point the N+1 interfaces' mixed elements are combined pairwise,
+ * level by level (an odd last block moves up unchanged), with Eq. recurrence2
+ * while the 1-norm of every block's I11 (largest absolute column sum) stays
+ * at most cond_max; once one exceeds it (checked on the elements and after
+ * each level), every block becomes its scattering matrix by Eq. scatter
+ * (S11 = I11^-1, S12 = -I11^-1 I12) and the rest uses Eq. recurrence.  Then
+ * t and T as in pw_transmission.  T_dev: device, npts doubles; levels_host:
+ * NULL or npts ints, the mixed levels done per point (-1 at a threshold).
+ * FP64 throughout (any precision of the context), one point after another,
+ * synchronises the stream.  Device memory: the N+1 elements of a point and
+ * half as many for the next level (64 N_G^2 bytes each), and work for up to
+ * 2 x SMs combinations at a time (64 N_G^2 bytes each).
+ * cond_max <= 0 or NaN: PW_EINVAL.  PW_ETHRESH (T = NaN there) and
+ * PW_ESINGULAR as for pw_transmission.  A latency-oriented path (its
+ * combinations run one CTA each); pw_transmission is the throughput path. */
+pw_status pw_transmission_doubling(pw_ctx *ctx, int npts, const double *E, const double *kpar,
+                                   double cond_max, double *T_dev, int *levels_host);
+
 /* The forward hot path: for each point (E[i], kpar[2i..2i+1]) the junction's
  * S11(0,N+1) by a left-to-right sweep of star products over all N+1
  * interfaces, then t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels and
@@ -325,6 +363,29 @@ void pw_batch_destroy(pw_batch *b);
  * PW_ETIMEOUT if the tensor core did not signal completion within its bounded
  * wait.  The paper has no counterpart; this is a deployment check. */
 pw_status pw_selftest_tensor_core(double *rel_err_tf32, double *rel_err_split);
+
+/* Self-test of the exact-slice product behind the mixed form's residual when
+ * every point shares its overlaps: O y as a sum of products of 7-bit slices
+ * (BF16 on the tensor cores, FP32 accumulation that is exact for 2n <= 1024
+ * inner terms, the slice pairs summed in double-float).  Runs that kernel on
+ * random slices for a basis of n functions (a multiple of 4, at most 512) and
+ * ncol columns (1..4096): first with only the leading slices non-zero and rows
+ * and columns at full scale, where *mismatches counts the results that differ
+ * from the exact integer product in any bit; then with every slice random,
+ * where *rel_err = max|Y - Y_exact| / max|Y_exact| on every 64th row (about
+ * 1e-14 expected).  Runs on the current device and synchronises it; returns
+ * PW_EINVAL for sizes out of range and PW_ETIMEOUT if a tensor-core wait ran
+ * out.  A deployment check with no counterpart in the paper. */
+pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, double *rel_err);
+
+/* Self-test of the FP16 split used by sweep variant bit 2: the same 128 x 64
+ * tile product with K = 32 as hi/lo FP16 parts (kind::f16, three MMAs per K
+ * step of 16, operands scaled by the split's 2^8 headroom), against an FP64
+ * product of the same FP32 inputs: *rel_err = max|C - C_ref| / max|C_ref|
+ * (FP32 level, about 1e-7, expected).  Runs on the current device and
+ * synchronises it; PW_ETIMEOUT if the tensor core did not signal completion
+ * within its bounded wait.  A deployment check with no counterpart in the paper. */
+pw_status pw_selftest_f16_split(double *rel_err);
 
 #ifdef __cplusplus
 }

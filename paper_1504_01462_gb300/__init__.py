@@ -34,7 +34,8 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_get_profile", "pw_compose_noalloc", "pw_grad", "pw_setup_batch",
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
            "pw_batch_destroy", "pw_get_error_detail", "pw_selftest_tensor_core",
-           "pw_set_sweep_variant"]
+           "pw_set_sweep_variant", "pw_selftest_slice_product", "pw_slice_mixed", "pw_compose_mixed",
+           "pw_transmission_doubling", "pw_selftest_f16_split"]
 
 
 class PwError(RuntimeError):
@@ -85,6 +86,9 @@ def _load():
     lib.pw_overlaps.argtypes = [_vp, _dp, _vp]
     lib.pw_slice_smatrix.argtypes = [_vp, ctypes.c_int, _dp, _dp, ctypes.c_int, _vp]
     lib.pw_compose.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+    lib.pw_slice_mixed.argtypes = lib.pw_slice_smatrix.argtypes
+    lib.pw_compose_mixed.argtypes = lib.pw_compose.argtypes
+    lib.pw_transmission_doubling.argtypes = [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, _vp, _ip]
     lib.pw_transmission.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp, _vp, _vp, _vp]
     lib.pw_compose_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
     lib.pw_grad.argtypes = [_vp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -97,6 +101,9 @@ def _load():
     lib.pw_batch_destroy.argtypes = [_vp]
     lib.pw_get_error_detail.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
     lib.pw_selftest_tensor_core.argtypes = [_dp, _dp]
+    lib.pw_selftest_slice_product.argtypes = [ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_longlong), _dp]
+    lib.pw_selftest_f16_split.argtypes = [_dp]
     lib.pw_set_sweep_variant.argtypes = [_vp, ctypes.c_int]
     lib.pw_batch_destroy.restype = None
     return lib
@@ -219,6 +226,25 @@ def selftest_tensor_core():
     return float(a[0]), float(b[0])
 
 
+def selftest_slice_product(n, ncol):
+    """(results differing from the exact leading-slice product, relative error
+    of the full slice sum) from the library's exact-slice product self-test
+    (the residual's tensor-core path) for a basis of n and ncol columns."""
+    bad = ctypes.c_longlong(-1)
+    rel = np.zeros(1)
+    _check_status(_lib.pw_selftest_slice_product(int(n), int(ncol), ctypes.byref(bad), _as_dp(rel)),
+                  "pw_selftest_slice_product")
+    return int(bad.value), float(rel[0])
+
+
+def selftest_f16_split():
+    """Relative error of one tile product in the FP16 split (sweep variant
+    bit 2) from the library's self-test on the current device."""
+    a = np.zeros(1)
+    _check_status(_lib.pw_selftest_f16_split(_as_dp(a)), "pw_selftest_f16_split")
+    return float(a[0])
+
+
 def _check_status(st, where):
     if st != 0:
         raise PwError(st, where)
@@ -304,6 +330,31 @@ class Context:
     def compose(self, npts, Sa, Sb, Sab):
         self._check(_lib.pw_compose(self._h, int(npts), _ptr(Sa), _ptr(Sb), _ptr(Sab)),
                     "pw_compose")
+
+    def slice_mixed(self, E, kpar, iface, T_out):
+        """Mixed elements (I11, I12, S21, S22) of one interface (Eq. recurrence2)."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        self._check(_lib.pw_slice_mixed(self._h, len(E), _as_dp(E), _as_dp(k), int(iface),
+                                        _ptr(T_out)), "pw_slice_mixed")
+
+    def compose_mixed(self, npts, Ta, Tb, Tab):
+        """One step of Eq. recurrence2 for npts pairs of mixed elements."""
+        self._check(_lib.pw_compose_mixed(self._h, int(npts), _ptr(Ta), _ptr(Tb), _ptr(Tab)),
+                    "pw_compose_mixed")
+
+    def transmission_doubling(self, E, kpar, T_out, cond_max=1e4, allow_threshold=False):
+        """T by layer doubling (Eq. recurrence2 while the 1-norm of I11 stays
+        <= cond_max, then Eq. recurrence) into T_out (device float64[npts]);
+        returns the mixed levels done per point (numpy int array)."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        levels = np.zeros(len(E), dtype=np.int32)
+        st = _lib.pw_transmission_doubling(self._h, len(E), _as_dp(E), _as_dp(k), float(cond_max),
+                                           _ptr(T_out), levels.ctypes.data_as(_ip))
+        if not (st == PW_ETHRESH and allow_threshold):
+            self._check(st, "pw_transmission_doubling")
+        return levels
 
     def transmission(self, E, kpar, T_out, t_out=None, nopen_out=None, err_out=None,
                      allow_threshold=False):

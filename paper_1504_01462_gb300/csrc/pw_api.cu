@@ -63,6 +63,7 @@ struct pw_ctx {
   int last_sweeps = 0;                       // most Jacobi sweeps of one matrix in the last eig
   // per-point workspaces
   DevBuf R, M, piv, pts, status, work, KV;
+  DevBuf rowexp;                   // row scales of the FP16-split [W|Y] (sweep variant bit 2)
   DevBuf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp;   // refinement of the mixed form
   DevBuf Xa_m, Xb_m, status_m, Tg, Gam, gtab, T1, dV0, wgt;   // adjoint (pw_grad)
   DevBuf corr;                     // refinement stopping test
@@ -547,7 +548,7 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
-                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p};
+                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -619,8 +620,21 @@ pw_status pw_overlaps(pw_ctx *ctx, const double *kpar, pw_c128 *O_dev) {
   return PW_OK;
 }
 
+pw_status slice_blocks(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface, pw_c128 *S_dev,
+                       int mixed);
+
 pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface,
                            pw_c128 *S_dev) {
+  return slice_blocks(ctx, npts, E, kpar, iface, S_dev, 0);
+}
+
+pw_status pw_slice_mixed(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface,
+                         pw_c128 *T_dev) {
+  return slice_blocks(ctx, npts, E, kpar, iface, T_dev, 1);
+}
+
+pw_status slice_blocks(pw_ctx *ctx, int npts, const double *E, const double *kpar, int iface, pw_c128 *S_dev,
+                       int mixed) {
   if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !S_dev))) return PW_EINVAL;
   if (ctx->err) return ctx->err;
   if (iface < 0 || iface > ctx->N) return PW_EINVAL;
@@ -649,7 +663,7 @@ pw_status pw_slice_smatrix(pw_ctx *ctx, int npts, const double *E, const double 
       CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
       CK(pw::launch_slice_smatrix((PointDesc *)ctx->pts.p, ctx->d_En, ctx->d_O, ctx->d_dz,
                                   (zc *)ctx->work.p, (int *)ctx->piv.p, (int *)ctx->status.p,
-                                  (zc *)ctx->M.p, n, ctx->N, iface, nb, ctx->stream));
+                                  (zc *)ctx->M.p, n, ctx->N, iface, nb, ctx->stream, mixed));
       // scatter the batch's S blocks to the caller's point order
       for (int i = 0; i < nb; ++i)
         CK(cudaMemcpyAsync(S_dev + (size_t)g[b0 + i] * 4 * nn, (zc *)ctx->M.p + (size_t)i * 4 * nn,
@@ -689,6 +703,154 @@ pw_status pw_compose(pw_ctx *ctx, int npts, const pw_c128 *Sa_dev, const pw_c128
       if (v) return latch(ctx, PW_ESINGULAR);
   }
   return PW_OK;
+}
+
+pw_status pw_compose_mixed(pw_ctx *ctx, int npts, const pw_c128 *Ta_dev, const pw_c128 *Tb_dev,
+                           pw_c128 *Tab_dev) {
+  if (!ctx || npts < 0 || (npts > 0 && (!Ta_dev || !Tb_dev || !Tab_dev))) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  const int n = ctx->n;
+  const size_t nn = (size_t)n * n;
+  const int bmax = std::max(1, std::min(npts, 2 * ctx->num_sms));
+  const pw::Strides str{4 * nn, 4 * nn, 4 * nn};
+  pw_status st;
+  for (int b0 = 0; b0 < npts; b0 += bmax) {
+    const int nb = std::min(npts - b0, bmax);
+    if ((st = ensure(ctx, ctx->work, (size_t)nb * 4 * nn * sizeof(zc))) ||
+        (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
+      return st;
+    CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
+    CK(pw::launch_compose_mixed((const zc *)Ta_dev + (size_t)b0 * 4 * nn, (const zc *)Tb_dev + (size_t)b0 * 4 * nn,
+                                (zc *)Tab_dev + (size_t)b0 * 4 * nn, (zc *)ctx->work.p, (int *)ctx->piv.p,
+                                (int *)ctx->status.p, n, nb, ctx->stream, str));
+    std::vector<int> st_h(nb);
+    CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int v : st_h)
+      if (v) return latch(ctx, PW_ESINGULAR);
+  }
+  return PW_OK;
+}
+
+// Layer doubling of one point's interface elements (FP64), one point at a
+// time: A holds the N+1 mixed elements, B half as many; each level combines
+// neighbours from one into the other (an odd last block is copied up).
+pw_status pw_transmission_doubling(pw_ctx *ctx, int npts, const double *E, const double *kpar,
+                                   double cond_max, double *T_dev, int *levels_host) {
+  if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev)) || !(cond_max > 0.0)) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  const int n = ctx->n, N = ctx->N, nblk = N + 1;
+  const size_t nn = (size_t)n * n, blk = 4 * nn;
+  const int cap = std::max(1, 2 * ctx->num_sms);   // CTAs per launch (bounds the work buffers)
+  std::vector<std::vector<int>> groups;
+  group_by_k(npts, kpar, groups);
+  pw_status result = PW_OK, st;
+  if ((st = alloc_slots(ctx))) return st;
+  DevBuf &A = ctx->M, &B = ctx->R;
+  if ((st = ensure(ctx, A, (size_t)nblk * blk * sizeof(zc))) ||
+      (st = ensure(ctx, B, (size_t)((nblk + 1) / 2) * blk * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->work, (size_t)std::min(cap, nblk) * blk * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->piv, (size_t)std::min(cap, nblk) * n * sizeof(int))) ||
+      (st = ensure(ctx, ctx->status, (size_t)std::min(cap, nblk) * sizeof(int))) ||
+      (st = ensure(ctx, ctx->corr, (size_t)nblk * sizeof(double))) ||
+      (st = ensure(ctx, ctx->pts, sizeof(PointDesc))))
+    return st;
+  int *stat = (int *)ctx->status.p;
+  int *piv = (int *)ctx->piv.p;
+  zc *work = (zc *)ctx->work.p;
+  double *norms = (double *)ctx->corr.p;
+  auto check_status = [&](int count) -> pw_status {
+    std::vector<int> h(count);
+    CK(cudaMemcpyAsync(h.data(), stat, count * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int v : h)
+      if (v) return latch(ctx, PW_ESINGULAR);
+    return PW_OK;
+  };
+  auto max_norm = [&](const zc *T, int count, double *out) -> pw_status {
+    CK(pw::launch_i11_norm(T, blk, n, count, norms, ctx->stream));
+    std::vector<double> h(count);
+    CK(cudaMemcpyAsync(h.data(), norms, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = 0.0;
+    for (double v : h) *out = std::max(*out, v);
+    return PW_OK;
+  };
+  auto to_s = [&](zc *T, int count) -> pw_status {
+    for (int b0 = 0; b0 < count; b0 += cap) {
+      const int nb = std::min(count - b0, cap);
+      CK(cudaMemsetAsync(stat, 0, nb * sizeof(int), ctx->stream));
+      CK(pw::launch_mixed_to_s(T + (size_t)b0 * blk, blk, work, piv, stat, n, nb, ctx->stream));
+      pw_status s2 = check_status(nb);
+      if (s2) return s2;
+    }
+    return PW_OK;
+  };
+  const double nan = std::nan("");
+  for (auto &g : groups) {
+    if ((st = ensure_kset(ctx, kpar + 2 * g[0]))) return st;
+    for (int idx : g) {
+      bool th = false;
+      const int nL = count_open(ctx->EL[0], E[idx], &th);
+      const int nR = count_open(ctx->ER[0], E[idx], &th);
+      if (levels_host) levels_host[idx] = -1;
+      if (th) {
+        result = PW_ETHRESH;
+        CK(cudaMemcpyAsync(T_dev + idx, &nan, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        continue;
+      }
+      const PointDesc pd = pw::make_point(E[idx], 0, nL, nR, idx, 0, N, 0);
+      CK(cudaMemcpyAsync(ctx->pts.p, &pd, sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      // the mixed elements of every interface, cap interfaces per launch
+      for (int f0 = 0; f0 < nblk; f0 += cap) {
+        const int nb = std::min(nblk - f0, cap);
+        CK(cudaMemsetAsync(stat, 0, nb * sizeof(int), ctx->stream));
+        CK(pw::launch_slice_smatrix((PointDesc *)ctx->pts.p, ctx->d_En, ctx->d_O, ctx->d_dz, work, piv, stat,
+                                    (zc *)A.p + (size_t)f0 * blk, n, N, f0, nb, ctx->stream, 1, blk, 1));
+        if ((st = check_status(nb))) return st;
+      }
+      zc *src = (zc *)A.p, *dst = (zc *)B.p;
+      int cnt = nblk, level = 0;
+      double g_max = 0.0;
+      if ((st = max_norm(src, cnt, &g_max))) return st;
+      bool mixed = g_max <= cond_max;
+      if (!mixed && (st = to_s(src, cnt))) return st;
+      while (cnt > 1) {
+        const int pairs = cnt / 2;
+        for (int i0 = 0; i0 < pairs; i0 += cap) {
+          const int nb = std::min(pairs - i0, cap);
+          const pw::Strides str{2 * blk, 2 * blk, blk};
+          const zc *a = src + (size_t)2 * i0 * blk, *b = a + blk;
+          zc *c = dst + (size_t)i0 * blk;
+          CK(cudaMemsetAsync(stat, 0, nb * sizeof(int), ctx->stream));
+          if (mixed) CK(pw::launch_compose_mixed(a, b, c, work, piv, stat, n, nb, ctx->stream, str));
+          else CK(pw::launch_compose(a, b, c, work, piv, stat, n, nb, ctx->stream, str));
+          if ((st = check_status(nb))) return st;
+        }
+        if (cnt & 1)
+          CK(cudaMemcpyAsync(dst + (size_t)pairs * blk, src + (size_t)(cnt - 1) * blk, blk * sizeof(zc),
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+        cnt = pairs + (cnt & 1);
+        std::swap(src, dst);
+        if (mixed) {
+          ++level;
+          if ((st = max_norm(src, cnt, &g_max))) return st;
+          if (g_max > cond_max) {
+            mixed = false;
+            if ((st = to_s(src, cnt))) return st;
+          }
+        }
+      }
+      if (mixed && (st = to_s(src, 1))) return st;
+      const double *EnL = ctx->d_En, *EnR = ctx->d_En + (size_t)(N + 1) * n;
+      CK(pw::launch_t_from_s(src, EnL, EnR, E[idx], n, nL, nR, T_dev + idx, ctx->stream));
+      if (levels_host) levels_host[idx] = level;
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return result;
 }
 
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev,
@@ -751,7 +913,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
           (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
           (st = ensure(ctx, ctx->KV, (size_t)nb * 3 * n * esz)) ||
           (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
-          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))))
+          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))) ||
+          ((ctx->sweep_variant & 4) && (st = ensure(ctx, ctx->rowexp, (size_t)nb * 2 * n * sizeof(int)))))
         return st;
       const size_t vec = (size_t)nb * n * nc;
       if (refine &&
@@ -770,6 +933,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       CK(cudaMemcpyAsync(ctx->pts.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
       CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
       pw::SweepArgs a;
+      memset(&a, 0, sizeof(a));
       a.pts = (const PointDesc *)ctx->pts.p;
       a.En = ctx->d_En;
       a.O = ctx->d_O;
@@ -794,8 +958,11 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.KV = ctx->KV.p;
       a.mirror = 0;
       a.wy_pairs = pw::points_pair_up(pd.data(), nb);
+      a.rowexp = (ctx->sweep_variant & 4) ? (int *)ctx->rowexp.p : nullptr;
       CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
-      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision));
+      // the FP16-split [W|Y] adds its row-scale kernel at every interface with a product (p >= 1)
+      const int f16_extra = (a.rowexp && a.wy_pairs && (ctx->sweep_variant & 6) == 6) ? N : 0;
+      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant) + f16_extra);
       for (int p = 0; p <= N; ++p) {
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
@@ -806,6 +973,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       s0.done();
       if (refine) {
         pw::RefineArgs r;
+        memset(&r, 0, sizeof(r));
         r.pts = a.pts;
         r.En = a.En;
         r.O = a.O;
@@ -836,11 +1004,29 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.nc = nc;
         r.x_slots = (long long)nb * (N + 2);
         r.st_slots = (long long)nb * (N + 1);
-        r.Bw = r.Yw = nullptr;
-        if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32 &&
-            (st = ensure(ctx, ctx->bw, (size_t)4 * nb * n * nc * sizeof(cc))) == PW_OK) {
-          r.Bw = (cc *)ctx->bw.p;
-          r.Yw = r.Bw + (size_t)2 * nb * n * nc;
+        r.lapack_piv = (ctx->sweep_variant & 2) ? 1 : 0;   // the stored factors' pivot order
+        if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32) {
+          // one buffer: the backward product's operands and result, then (when the
+          // residual runs on the tensor cores) O y, the slices and their exponents
+          auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+          const long long ncol = 2LL * nb * nc;
+          const bool sliced = ctx->d_O32lo && n <= 512 && n % 4 == 0;
+          const size_t b_bw = up((size_t)4 * nb * n * nc * sizeof(cc));
+          const size_t b_y = up((size_t)2 * n * ncol * sizeof(double));
+          const size_t b_sl = up(pw::rs_slice_bytes(n, ncol));
+          const size_t b_ex = ((size_t)2 * n + ncol) * sizeof(int);
+          if ((st = ensure(ctx, ctx->bw, b_bw + (sliced ? b_y + b_sl + b_ex : 0))) == PW_OK) {
+            unsigned char *base = (unsigned char *)ctx->bw.p;
+            r.Bw = (cc *)base;
+            r.Yw = r.Bw + (size_t)2 * nb * n * nc;
+            if (sliced) {
+              r.Yacc = (double *)(base + b_bw);
+              r.Osl = (uint16_t *)(base + b_bw + b_y);
+              r.Ysl = r.Osl + (size_t)pw::RS_SLICES * 4 * n * n;
+              r.Oexp = (int *)(base + b_bw + b_y + b_sl);
+              r.Yexp = r.Oexp + 2 * n;
+            }
+          }
         }
         if (st) return st;
         Stage s3(ctx, 3, 1);

@@ -47,6 +47,7 @@ struct pw_batch {
   std::map<int, int> variant;             // chosen sweep variant per N_G
   double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   Buf HU, V, En, stat, O, O32, O32t, O32lo, dz, pts, R, M, piv, KV, status;
+  Buf rowexp;   // row scales of the FP16-split [W|Y] (sweep variant bit 2)
   Buf Zst, Ust, LUst, PIVst, Xa, Xb, Fr, Gr, carry, tmp, corr;
   Buf eigws;                              // workspace of the double-float eigensolver
 };
@@ -85,7 +86,7 @@ pw_status grow(pw_batch *b, Buf &x, size_t bytes) {
 size_t held(const pw_batch *b) {
   const Buf *all[] = {&b->HU, &b->V, &b->En, &b->stat, &b->O, &b->O32, &b->O32t, &b->O32lo, &b->dz, &b->pts, &b->R, &b->M, &b->piv,
                       &b->KV, &b->status, &b->Zst, &b->Ust, &b->LUst, &b->PIVst, &b->Xa, &b->Xb,
-                      &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr, &b->eigws};
+                      &b->Fr, &b->Gr, &b->carry, &b->tmp, &b->corr, &b->eigws, &b->rowexp};
   size_t s = 0;
   for (const Buf *x : all) s += x->bytes;
   return s;
@@ -228,7 +229,8 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   const size_t vec = (size_t)m * n * nc;
   if ((st = grow(b, b->R, (size_t)m * nn * esz)) || (st = grow(b, b->M, (size_t)m * n * ncols * esz)) ||
       (st = grow(b, b->piv, (size_t)m * n * sizeof(int))) || (st = grow(b, b->KV, (size_t)m * 3 * n * esz)) ||
-      (st = grow(b, b->pts, (size_t)m * sizeof(PointDesc))) || (st = grow(b, b->status, (size_t)m * sizeof(int))))
+      (st = grow(b, b->pts, (size_t)m * sizeof(PointDesc))) || (st = grow(b, b->status, (size_t)m * sizeof(int))) ||
+      (mixed && (st = grow(b, b->rowexp, (size_t)m * 2 * n * sizeof(int)))))
     return st;
   if (refine &&
       ((st = grow(b, b->Zst, (size_t)nov * nn * sizeof(cc))) || (st = grow(b, b->LUst, (size_t)nov * nn * sizeof(cc))) ||
@@ -267,6 +269,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   a.KV = b->KV.p;
   a.mirror = 0;
   a.wy_pairs = pw::points_pair_up(pd.data(), m);
+  a.rowexp = mixed ? (int *)b->rowexp.p : nullptr;
   // tile variant: timed on the first interface steps of this chunk
   int var = b->force_variant;
   if (var < 0) {
@@ -328,7 +331,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
   } else {
     for (int p = 0; p <= maxN; ++p) BCK(pw::launch_sweep_batched(a, m, p, b->precision, s, nullptr, nullptr, var));
   }
-  b->stats[7] += (double)(maxN + 1) * pw::sweep_batched_launches(n, b->precision);
+  b->stats[7] += (double)(maxN + 1) * pw::sweep_batched_launches(n, b->precision, var);
   BCK(cudaEventRecord(ev[4], s));
   if (refine) {
     pw::RefineArgs r;
@@ -363,6 +366,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     r.nc = nc;
     r.x_slots = nmat;
     r.st_slots = nov;
+    r.lapack_piv = (var & 2) ? 1 : 0;   // the stored factors' pivot order
     int passes = 0;
     BCK(pw::launch_refine(r, m, std::min(2, b->refine_iters), b->refine_iters, pw::kRefineTolRel, s, &passes));
   }

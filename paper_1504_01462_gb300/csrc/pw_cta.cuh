@@ -204,8 +204,8 @@ __device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
 template <>
 __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
 
-// Right-hand columns [c_begin, c_end) of panel j0 (rows j0 ..; the panel
-// spans columns j0 .. j0+nb-1): the panel's row swaps, then U12 = L11^{-1} A12 with each column's nb
+// Columns [c_begin, c_end) of panel j0 (rows j0 ..; the panel spans columns
+// j0 .. j0+nb-1): the panel's row swaps, then (solve) U12 = L11^{-1} A12 with each column's nb
 // entries in registers (Ls: the factored nb x nb diagonal block, leading
 // dimension NB).  The swap sequence r <-> p_r (p_r >= r, in order r = 0 ..
 // nb-1) is first folded into a gather: row r < nb ends up holding original row
@@ -221,7 +221,7 @@ __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
 // NB FP64 complex values would not fit beside the rest of the kernel.
 template <typename T, int NTH = NT>
 __device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int j0, int nb, int R,
-                                  const int *piv, const cx<T> *Ls, int *flag) {
+                                  const int *piv, const cx<T> *Ls, int *flag, bool solve = true) {
   constexpr int NB = Tile<T, NTH>::NB;
   const int tid = threadIdx.x;
   if constexpr (sizeof(T) != 4) {
@@ -232,7 +232,7 @@ __device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int 
         if (p < r || p >= R) continue;   // cannot happen (flagged by the factorisation)
         if (p != r) { const cx<T> a = col[r]; col[r] = col[p]; col[p] = a; }
       }
-      for (int r = 1; r < nb; ++r) {
+      for (int r = 1; r < nb && solve; ++r) {
         cx<T> x = col[r];
         for (int s2 = 0; s2 < r; ++s2) {
           const cx<T> l = Ls[r + s2 * NB], y = col[s2];
@@ -299,13 +299,15 @@ __device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int 
         for (int k = 0; k < 8; ++k)
           if (k0 + k < nd) col[s_dpos[k0 + k]] = y[k];
       }
+      if (solve) {
 #pragma unroll
-      for (int r = 1; r < NB; ++r) {
+        for (int r = 1; r < NB; ++r) {
 #pragma unroll
-        for (int s2 = 0; s2 < r; ++s2) {
-          const cx<T> l = Ls[r + s2 * NB];
-          x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
-          x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
+          for (int s2 = 0; s2 < r; ++s2) {
+            const cx<T> l = Ls[r + s2 * NB];
+            x[r].re -= l.re * x[s2].re - l.im * x[s2].im;
+            x[r].im -= l.re * x[s2].im + l.im * x[s2].re;
+          }
         }
       }
 #pragma unroll
@@ -593,9 +595,12 @@ __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T>
 // (as in panel_right_apply) and each right-hand side is solved by one warp,
 // lane r holding row r (the diagonal block from shared memory, the solved
 // values passed by shuffles), so no step waits on a global-memory round trip.
+// lapack: the factors satisfy P A = L U (every panel's swaps reached the L
+// columns left of it, as the tensor-core FP32 sweep stores them): B <- P B
+// first, then the blocks without swaps.  Needs n <= 1024.
 template <typename T, int NTH = NT>
 __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, int ldb, int nrhs,
-                              cx<T> *smem) {
+                              cx<T> *smem, bool lapack = false) {
   constexpr int NB = Tile<T, NTH>::NB;
   static_assert(NB == 32, "one lane per row of a diagonal block");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -604,13 +609,36 @@ __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, 
   auto shfl = [](cx<T> v, int src) {
     return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
   };
+  if (lapack) {
+    __shared__ int s_perm[1024];
+    __shared__ cx<T> s_col[1024];
+    if (tid == 0) {
+      for (int r = 0; r < n; ++r) s_perm[r] = r;
+      for (int j = 0; j < n; ++j) {
+        const int p = piv[j];
+        if (p > j && p < n) {
+          const int t = s_perm[j];
+          s_perm[j] = s_perm[p];
+          s_perm[p] = t;
+        }
+      }
+    }
+    for (int c = 0; c < nrhs; ++c) {
+      __syncthreads();
+      for (int r = tid; r < n; r += NTH) s_col[r] = B[r + (size_t)c * ldb];
+      __syncthreads();
+      for (int r = tid; r < n; r += NTH) B[r + (size_t)c * ldb] = s_col[s_perm[r]];
+    }
+    __syncthreads();
+  }
   for (int j0 = 0; j0 < n; j0 += NB) {
     const int nb = min(NB, n - j0), R = n - j0;
     for (int e = tid; e < nb * nb; e += NTH) {
       const int r = e % nb, c = e / nb;
       Ls[r + c * NB] = LU[j0 + r + (size_t)(j0 + c) * n];
     }
-    if (tid < nb) s_piv[tid] = piv[j0 + tid] - j0;
+    // lapack: B is already in pivot order, so the block's swaps are identities
+    if (tid < nb) s_piv[tid] = lapack ? tid : piv[j0 + tid] - j0;
     __syncthreads();
     if (tid == 0) {
       int nd = 0;

@@ -90,6 +90,12 @@ struct SweepArgs {
                          //    overlap O_p -> O_{N-p}^T), used by the adjoint
   int wy_pairs;          // 1: points 2i and 2i+1 share overlaps and slice count (the
                          //    tensor-core [W|Y] then stages one B tile for both)
+  int lapack_piv;        // set by the sweep: 1 in the tensor-core FP32 form, where each
+                         //    panel's row swaps also reach the L columns left of it (so
+                         //    the stored factors satisfy P W = L U with P from piv in
+                         //    order) and the right-hand sides are eliminated after the LU
+  int *rowexp;           // null, or per point 2n: the power-of-two row scales of R and of
+                         //   R K_p^{-1} for the FP16-split [W|Y] (sweep variant bit 2)
 };
 
 // 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and
@@ -128,10 +134,26 @@ struct RefineArgs {
   int n, N, nc;          // N: the most slices of any point
   long long x_slots;     // sum over points of N+2 (the Xa, Xb slots)
   long long st_slots;    // sum over points of N+1 (the Fr, Gr slots)
+  int lapack_piv;        // 1: the stored LU factors follow P W = L U (the sweep's
+                         //    tensor-core FP32 form); 0: each panel's swaps reach only
+                         //    the columns right of it (replayed panel by panel)
+  uint16_t *Osl, *Ysl;   // null, or the residual's exact slices (BF16 bit patterns, K-contiguous):
+                         //   RS_SLICES x 2n x 2n and RS_SLICES x (2 nc npts) x 2n, when every
+                         //   point shares its overlaps (the residual products run on the tensor cores)
+  int *Oexp, *Yexp;      //   their per-row / per-column power-of-two exponents (2n, 2 nc npts)
+  double *Yacc;          //   the products O y of all points, column-major 2n x (2 nc npts)
   cc *Bw, *Yw;           // null, or n x (2 nc npts) each: when every point shares its overlaps
                          //   and slice count, the backward pass's O products of all points
                          //   run as one tensor-core GEMM (operands Bw, result Yw)
 };
+
+constexpr int RS_SLICES = 7;   // slices per operand of the tensor-core residual
+constexpr int RS_BITS = 7;     // bits per slice
+constexpr int RS_PAIRS = RS_SLICES * (RS_SLICES + 1) / 2;   // slice pairs with s + t < RS_SLICES
+// bytes of the slice buffers for n basis functions and ncol = 2 nc npts columns
+inline size_t rs_slice_bytes(int n, long long ncol) {
+  return (size_t)RS_SLICES * 2 * n * (2 * (size_t)n + (size_t)ncol) * sizeof(uint16_t);
+}
 
 // 1 when every point of a launch has the same overlaps and slice count.
 inline int points_share_overlaps(const PointDesc *pd, int npts) {
@@ -210,7 +232,7 @@ void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t
 cudaError_t prepare_sweep_batched(int n, int precision, int variant);
 cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precision, cudaStream_t s,
                                  cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr, int variant = 0);
-int sweep_batched_launches(int n, int precision);
+int sweep_batched_launches(int n, int precision, int variant);
 int sweep_variants(int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p, u_p and the LU factors:
 // between min_iters and max_iters passes, stopping once every point's
@@ -219,13 +241,31 @@ int sweep_variants(int precision);
 cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_iters, double tol,
                           cudaStream_t s, int *passes);
 size_t refine_smem_bytes(int n);
-// explicit interface S-matrices (FP64)
+// explicit interface S-matrices (FP64): npts CTAs, CTA b at point b and interface
+// iface, or (by_iface) at point 0 and interface iface + b; output blocks at
+// S + b * sstride (0: 4 n^2); mixed: the element (I11, I12, S21, S22) of Eq. recurrence2
 cudaError_t launch_slice_smatrix(const PointDesc *pts, const double *En, const zc *O, const double *dz,
                                  zc *work, int *piv, int *status, zc *S, int n, int N, int iface,
-                                 int npts, cudaStream_t s);
-// star products (FP64)
+                                 int npts, cudaStream_t s, int mixed = 0, size_t sstride = 0, int by_iface = 0);
+// element strides (complex values) of the operands and result of a batched combination
+struct Strides {
+  size_t a, b, c;
+};
+// star products (FP64); CTA i combines Sa + i str.a and Sb + i str.b into Sab + i str.c
+// (zero strides: 4 n^2 each)
 cudaError_t launch_compose(const zc *Sa, const zc *Sb, zc *Sab, zc *work, int *piv, int *status,
-                           int n, int npts, cudaStream_t s);
+                           int n, int npts, cudaStream_t s, Strides str = Strides{0, 0, 0});
+// layer doubling with Eq. recurrence2 (FP64): one step per pair (work n x 4n per pair)
+cudaError_t launch_compose_mixed(const zc *Ta, const zc *Tb, zc *Tab, zc *work, int *piv, int *status, int n,
+                                 int npairs, cudaStream_t s, Strides str);
+// Eq. scatter on mixed elements in place (work n x 3n per block)
+cudaError_t launch_mixed_to_s(zc *T, size_t stride, zc *work, int *piv, int *status, int n, int nblocks,
+                              cudaStream_t s);
+// the 1-norm of each block's I11 (the switching measure of Eq. recurrence2)
+cudaError_t launch_i11_norm(const zc *T, size_t stride, int n, int nblocks, double *out, cudaStream_t s);
+// T of one point from its S11 and the electrodes' ascending eigenvalues
+cudaError_t launch_t_from_s(const zc *S11, const double *EnL, const double *EnR, double E, int n, int nL, int nR,
+                            double *T_out, cudaStream_t s);
 
 // Read-only view of a one-problem context's geometry (pw_api.cu), for the
 // batch executor (pw_batch.cu).

@@ -19,6 +19,7 @@
 // FP64 from FP64 overlaps and wavenumbers, and M^{-1} the FP32 sweep (Z_p and
 // the LU factors of W_p kept from the first sweep, R_p = e_p Z_{p-1} e_p).
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(NT) k_refine_fwd_b(RefineArgs a, int p) {
     for (int e = threadIdx.x; e < n * nc; e += NT) rhs[e] = ccast<float>(csub(carry[e], F[e]));
     __syncthreads();
   }
-  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm);
+  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm, a.lapack_piv != 0);
   for (int e = threadIdx.x; e < n * nc; e += NT) {
     const int i = e % n;
     const cc u = rhs[e];
@@ -408,6 +409,333 @@ __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The residual's products O y by exact slices on the tensor cores, when every
+// point shares its overlaps (an error-free splitting in the manner of Ozaki et
+// al., Numer. Algorithms 59, 2012).  In real form the product is A' B' with
+//   A' = [[Re O, -Im O], [Im O, Re O]] (2n x 2n),  B' = [Re y; Im y] (2n x ncol),
+// ncol = 2 nc npts (the columns a_q + e b_q and K_q (a_q - e b_q) of every
+// point).  Row r of A' is scaled by 2^-ea_r and column j of B' by 2^-eb_j
+// (powers of two that bring every entry below 1 in magnitude) and cut into
+// RS_SLICES slices of RS_BITS bits: A' = 2^ea sum_s A_s, where A_s holds
+// integers of at most 2^7 in magnitude times 2^-7(s+1) (likewise B' and B_t).
+// Every slice is exact in BF16, every product of two slice entries is an
+// integer of at most 2^14 times 2^-7(s+t+2), and a sum of K = 2n <= 1024 of
+// them stays an integer of at most 2^24 units: the tensor core's FP32
+// accumulation of A_s B_t is exact.  The pairs with s + t < RS_SLICES are
+// summed in double-float in registers (the ones with s + t >= RS_SLICES lie
+// below 2^-56 of the result); the operands are the double-float overlap and y
+// rounded to double-float, so the products carry 48 bits like the CUDA-core
+// double-float residual, at tensor-core speed.
+namespace {
+constexpr int RS_THREADS = 256;
+
+// one block's maximum of a non-negative float
+__device__ float block_maxf(float v, float *red) {
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = 0.f;
+  for (int w = 0; w < RS_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+  __syncthreads();
+  return m;
+}
+
+// 2^-e for the scaling exponent e of a block whose largest magnitude is m
+__device__ __forceinline__ int scale_exponent(float m) {
+  int e = 0;
+  if (m > 0.f) frexpf(m, &e);   // m < 2^e
+  return e;
+}
+
+// The slices of the double-float x = hi + lo scaled by 2^-e (|x| < 2^e), as
+// BF16 bit patterns into out[s * stride].  Slice s is trunc(R 2^7(s+1)) 2^-7(s+1)
+// of the remainder R, taken from R's high part: every step is exact in FP32
+// (the truncation keeps the leading bits of hi, hi - c drops them, TwoSum
+// renormalises), so the slices sum to x up to the last remainder.
+__device__ __forceinline__ void cut_slices_df(float hi, float lo, int e, uint16_t *out, size_t stride) {
+  float h = ldexpf(hi, -e), l = ldexpf(lo, -e);
+#pragma unroll
+  for (int s = 0; s < RS_SLICES; ++s) {
+    const float up = __int_as_float((127 + RS_BITS * (s + 1)) << 23);    // 2^7(s+1)
+    const float down = __int_as_float((127 - RS_BITS * (s + 1)) << 23);  // 2^-7(s+1)
+    const float c = truncf(h * up) * down;
+    out[(size_t)s * stride] = (uint16_t)(__float_as_uint(c) >> 16);   // c has at most 8 significant bits
+    float sh, se;
+    two_sum(h - c, l, sh, se);
+    h = sh;
+    l = se;
+  }
+}
+
+// the slice pair (s, t) of step P, the pairs ordered by decreasing s + t
+__device__ __forceinline__ int rs_pair(int P, int &s, int &t) {
+  int d = RS_SLICES - 1;
+  while (P > d) {
+    P -= d + 1;
+    --d;
+  }
+  s = P;
+  t = d - P;
+  return d;
+}
+}  // namespace
+
+// A' of interface p: block i cuts rows i and i + n (one exponent: both hold
+// the values Re O_ik, Im O_ik up to sign).
+__global__ void __launch_bounds__(RS_THREADS) k_res_oslice(RefineArgs a, int p) {
+  __shared__ float red[RS_THREADS / 32];
+  const int n = a.n, i = blockIdx.x, K = 2 * n;
+  const size_t ooff = ((size_t)a.pts[0].o_off + p) * (size_t)n * n + i;
+  const cc *Oh = a.O32 + ooff, *Ol = a.O32lo + ooff;
+  float m = 0.f;
+  for (int k = threadIdx.x; k < n; k += RS_THREADS) {
+    const cc h = Oh[(size_t)k * n];
+    m = fmaxf(m, fmaxf(fabsf(h.re), fabsf(h.im)));
+  }
+  const int e = scale_exponent(block_maxf(m, red));
+  if (threadIdx.x == 0) {
+    a.Oexp[i] = e;
+    a.Oexp[i + n] = e;
+  }
+  const size_t stride = (size_t)K * K;
+  uint16_t *r1 = a.Osl + (size_t)i * K, *r2 = a.Osl + (size_t)(i + n) * K;
+  for (int k = threadIdx.x; k < n; k += RS_THREADS) {
+    const cc h = Oh[(size_t)k * n], l = Ol[(size_t)k * n];
+    // row i = [Re O, -Im O], row i + n = [Im O, Re O]; the slices of -x are those of x negated
+    cut_slices_df(h.re, l.re, e, r1 + k, stride);
+    cut_slices_df(h.im, l.im, e, r2 + k, stride);
+#pragma unroll
+    for (int s = 0; s < RS_SLICES; ++s) {
+      r2[(size_t)s * stride + n + k] = r1[(size_t)s * stride + k];
+      r1[(size_t)s * stride + n + k] = r2[(size_t)s * stride + k] ^ 0x8000u;
+    }
+  }
+}
+
+// B' of interface p: block j cuts column j = pt 2nc + c (c < nc: a_q + e b_q of
+// channel c; c >= nc: K_q (a_q - e b_q) of channel c - nc); zero for points
+// that are skipped, failed or shorter than p.
+__global__ void __launch_bounds__(RS_THREADS) k_res_yslice(RefineArgs a, int p) {
+  __shared__ float red[RS_THREADS / 32];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = a.n, nc = a.nc, K = 2 * n, ncol = gridDim.x;
+  const int j = blockIdx.x, pt = j / (2 * nc), c = j % (2 * nc), ch = c < nc ? c : c - nc;
+  const PointDesc d = a.pts[pt];
+  const size_t stride = (size_t)ncol * K;
+  uint16_t *out = a.Ysl + (size_t)j * K;
+  if (d.skip || a.status[pt] || p > d.N) {
+    for (int k = threadIdx.x; k < K; k += RS_THREADS)
+#pragma unroll
+      for (int s = 0; s < RS_SLICES; ++s) out[(size_t)s * stride + k] = 0;
+    if (threadIdx.x == 0) a.Yexp[j] = 0;
+    return;
+  }
+  KV v = carve_kv(smraw, 0, n);
+  load_kv(a, d, p, v);
+  const int q = p + 1;
+  const bool has_bq = q <= d.N;
+  const zc *aq = a.Xa + blk(a, d, q) + (size_t)ch * n;
+  const zc *bq = a.Xb + blk(a, d, q) + (size_t)ch * n;
+  auto yv = [&](int l) -> dfc {
+    const zc A = aq[l];
+    const zc eb = has_bq ? cmul(v.eR[l], bq[l]) : czero<double>();
+    return dfc_of(c < nc ? cadd(A, eb) : cmul(v.kR[l], csub(A, eb)));
+  };
+  float m = 0.f;
+  for (int l = threadIdx.x; l < n; l += RS_THREADS) {
+    const dfc y = yv(l);
+    m = fmaxf(m, fmaxf(fabsf(y.re.hi), fabsf(y.im.hi)));
+  }
+  const int e = scale_exponent(block_maxf(m, red));
+  if (threadIdx.x == 0) a.Yexp[j] = e;
+  for (int l = threadIdx.x; l < n; l += RS_THREADS) {
+    const dfc y = yv(l);
+    cut_slices_df(y.re.hi, y.re.lo, e, out + l, stride);
+    cut_slices_df(y.im.hi, y.im.lo, e, out + n + l, stride);
+  }
+}
+
+// Yacc = A' B' summed over the slice pairs.  One CTA per 128 x 128 tile of
+// A' B'; K in stages of 64 (four BF16 MMAs of M = N = 128, K = 16) through a
+// ring of RS_RING shared-memory stages filled by cp.async, so that RS_RING - 1
+// stages of operand loads are in flight while the tensor core multiplies.
+// Each pair accumulates in one of two TMEM buffers (128 columns each); the
+// finished pair's buffer is read back and added into the double-float
+// registers in eight column chunks spread over the next pair's stages, so the
+// read-back overlaps the next pair's products.  Warp w holds TMEM lanes
+// 32 (w % 4) .. + 31 (rows) and columns 64 (w / 4) .. + 63.
+constexpr int RS_TILE = 128, RS_KS = 64, RS_RING = 6;
+constexpr int RS_OPER = RS_TILE * RS_KS * 2;   // bytes of one operand per stage
+constexpr int RS_STAGE = 2 * RS_OPER;
+constexpr int RS_DF_BELOW = 4;                 // pairs with s + t < 4 add in double-float, the rest in FP32
+size_t res_mm_smem_bytes() { return (size_t)RS_RING * RS_STAGE + 128; }
+
+__global__ void __launch_bounds__(256, 1) k_res_mm(RefineArgs a, int ncol, int npts) {
+  extern __shared__ __align__(128) unsigned char smtc[];
+  const int n = a.n, M = 2 * n, K = 2 * n;
+  const int tiles_m = (M + RS_TILE - 1) / RS_TILE;
+  const int r0 = (blockIdx.x % tiles_m) * RS_TILE, j0 = (blockIdx.x / tiles_m) * RS_TILE;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smtc + RS_RING * RS_STAGE);   // [RS_RING]
+  uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + RS_RING);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ns = (K + RS_KS - 1) / RS_KS, G = RS_PAIRS * ns;
+  if (warp == 0) tc::tmem_alloc(slot, 2 * RS_TILE);
+  if (tid == 0)
+    for (int b = 0; b < RS_RING; ++b) tc::mbar_init(&mbar[b], 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+
+  // operand loads of stage g: 128 rows x 8 chunks of 16 bytes per operand;
+  // task u (4 per warp) covers rows 8 (u / 2) .. + 7 and chunks 4 (u % 2) .. + 3,
+  // lane -> row 8 (u / 2) + lane % 8, chunk 4 (u % 2) + lane / 8 (each 8-lane
+  // phase writes 8 distinct bank groups; each row's 64 bytes are contiguous)
+  auto load_stage = [&](int g) {
+    if (g < G) {
+      int s, t;
+      const int P = g / ns, k0 = (g - P * ns) * RS_KS;
+      rs_pair(P, s, t);
+      unsigned char *A = smtc + (g % RS_RING) * RS_STAGE, *B = A + RS_OPER;
+      const uint16_t *As = a.Osl + (size_t)s * M * K, *Bs = a.Ysl + (size_t)t * ncol * K;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int u = warp * 4 + i, row = 8 * (u >> 1) + (lane & 7), c = 4 * (u & 1) + (lane >> 3);
+        const int kk = k0 + 8 * c;
+        const uint32_t off = (uint32_t)(c >> 1) * (RS_TILE * 32) + (uint32_t)(row >> 3) * 256u +
+                             (uint32_t)(c & 1) * 128u + (uint32_t)(row & 7) * 16u;
+        const bool va = r0 + row < M && kk < K, vb = j0 + row < ncol && kk < K;
+        tc::cp_async16(A + off, va ? As + (size_t)(r0 + row) * K + kk : As, va);
+        tc::cp_async16(B + off, vb ? Bs + (size_t)(j0 + row) * K + kk : Bs, vb);
+      }
+    }
+    tc::cp_async_commit();   // one group per stage, empty past the end
+  };
+
+  float ah[8][8], al[8][8];   // double-float sums of this thread's 64 results
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ah[q][i] = al[q][i] = 0.f;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  // add chunk q of pair P's buffer into the sums
+  auto read_chunk = [&](int P, int q, float (&hq)[8], float (&lq)[8]) {
+    int s, t;
+    const int d = rs_pair(P, s, t);
+    float v[8];
+    tc::tmem_ld8(lane_base + (uint32_t)((P & 1) * RS_TILE + 8 * q), v);
+    const float unit = __int_as_float((127 - RS_BITS * (d + 2)) << 23);   // 2^-7(s+t+2), exact scaling
+    if (d >= RS_DF_BELOW) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) hq[i] += v[i] * unit;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float sh, se;
+        two_sum(hq[i], v[i] * unit, sh, se);
+        hq[i] = sh;
+        lq[i] += se;
+      }
+    }
+  };
+
+  for (int g = 0; g < RS_RING - 1; ++g) load_stage(g);
+  bool ok = true;
+  int last = -1;   // the last stage whose MMAs were issued
+  for (int g = 0; g < G; ++g) {
+    const int P = g / ns, st = g - P * ns;
+    tc::cp_async_wait<RS_RING - 2>();   // this thread's copies of stage g have landed
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const unsigned char *A = smtc + (g % RS_RING) * RS_STAGE, *B = A + RS_OPER;
+      const uint32_t d = tmem + (uint32_t)((P & 1) * RS_TILE);
+      constexpr uint32_t idesc = tc::idesc_bf16(RS_TILE, RS_TILE);
+#pragma unroll
+      for (int m = 0; m < RS_KS / 16; ++m)
+        tc::mma_bf16(d, tc::smem_desc(A + m * RS_TILE * 32, 128, 256), tc::smem_desc(B + m * RS_TILE * 32, 128, 256),
+                     idesc, (st > 0 || m > 0) ? 1u : 0u);
+      tc::mma_commit(&mbar[g % RS_RING]);
+    }
+    last = g;
+    // stage g - 1's slot is free once its MMAs are done: refill it with stage g + RS_RING - 1
+    if (g >= 1) ok = tc::mbar_wait(&mbar[(g - 1) % RS_RING], ((g - 1) / RS_RING) & 1) && ok;
+    tc::fence_after_sync();
+    if (ok) load_stage(g + RS_RING - 1);
+    else tc::cp_async_commit();
+    // pair P - 1 is complete (its last stage is g - 1 or earlier): read back the
+    // chunks q with q ns / 8 == st
+    if (P > 0 && __all_sync(0xffffffffu, ok)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if ((q * ns) / 8 == st) read_chunk(P - 1, q, ah[q], al[q]);
+    }
+  }
+  if (ok) {
+    ok = tc::mbar_wait(&mbar[(G - 1) % RS_RING], ((G - 1) / RS_RING) & 1);
+    tc::fence_after_sync();
+    if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) read_chunk(RS_PAIRS - 1, q, ah[q], al[q]);
+    }
+  }
+  tc::cp_async_wait<0>();
+  ok = __syncthreads_and(ok) != 0;
+  if (ok) {
+    const int row = r0 + 32 * (warp & 3) + lane;
+    if (row < M) {
+      const int er = a.Oexp[row];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int j = j0 + 64 * (warp >> 2) + 8 * q + i;
+          if (j < ncol) a.Yacc[(size_t)j * M + row] = ldexp((double)ah[q][i] + (double)al[q][i], er + a.Yexp[j]);
+        }
+    }
+  } else {
+    // a wait ran out: wait (bounded again) for the products still in flight, report
+    if (last >= 0) tc::mbar_wait(&mbar[last % RS_RING], (last / RS_RING) & 1, 1u << 16);
+    if (tid == 0)
+      for (int pt = 0; pt < npts; ++pt) a.status[pt] = 2;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * RS_TILE);
+}
+
+// The residual of interface p from Yacc (block pt): with y1 = O (a_q + e b_q)
+// and y2 = O K_q (a_q - e b_q),
+//   f_p = (y1 + K_p^-1 y2)/2 - e_p a_p,  g_p = (y1 - K_p^-1 y2)/2 - b_p.
+__global__ void __launch_bounds__(NT) k_res_finish(RefineArgs a, int p, int ncol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.x;
+  const PointDesc d = a.pts[pt];
+  if (d.skip || a.status[pt] || p > d.N) return;
+  const int n = a.n, nc = a.nc, M = 2 * n;
+  KV v = carve_kv(smraw, 0, n);
+  load_kv(a, d, p, v);
+  const zc *ap = a.Xa + blk(a, d, p);
+  const zc *bp = a.Xb + blk(a, d, p);
+  zc *F = a.Fr + iblk(a, d, p);
+  zc *G = a.Gr + iblk(a, d, p);
+  const double *Y1 = a.Yacc + (size_t)pt * 2 * nc * M;
+  for (int e = threadIdx.x; e < n * nc; e += NT) {
+    const int i = e % n, c = e / n;
+    const double *c1 = Y1 + (size_t)c * M, *c2 = Y1 + (size_t)(nc + c) * M;
+    const zc y1 = mkc<double>(c1[i], c1[i + n]);
+    const zc y2 = cmul(v.kinvL[i], mkc<double>(c2[i], c2[i + n]));
+    const zc fwd = mkc<double>(0.5 * (y1.re + y2.re), 0.5 * (y1.im + y2.im));
+    const zc bwd = mkc<double>(0.5 * (y1.re - y2.re), 0.5 * (y1.im - y2.im));
+    F[e] = csub(fwd, cmul(v.eL[i], ap[e]));
+    G[e] = csub(bwd, bp[e]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // t and T from the refined a_{N+1}.  The estimate of the relative error of T
 // left after the last pass is the relative change of T that pass made, times
 // the contraction c_i / c_{i-1} it showed (c = relative size of the
@@ -482,6 +810,17 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
       (e = cudaFuncSetAttribute(k_refine_bwd_mm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes())))
     return e;
   const int mm_tiles = ((a.n + tc::CG_M / 2 - 1) / (tc::CG_M / 2)) * ((2 * a.nc * npts + tc::CG_N - 1) / tc::CG_N);
+  // the residual by exact slices: every point shares its overlaps, K = 2n <= 1024 keeps
+  // the slice products exact in FP32, and 2n is a multiple of 8 (whole 16-byte chunks)
+  const bool sliced = a.Osl && a.Ysl && a.Oexp && a.Yexp && a.Yacc && a.O32 && a.O32lo && a.n <= 512 &&
+                      (a.n % 4) == 0;
+  const size_t kv_bytes = 4 * (size_t)a.n * sizeof(zc);
+  const int rs_tiles = ((2 * a.n + RS_TILE - 1) / RS_TILE) * ((2 * a.nc * npts + RS_TILE - 1) / RS_TILE);
+  if (sliced && ((e = cudaFuncSetAttribute(k_res_mm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)res_mm_smem_bytes())) ||
+                 (e = cudaFuncSetAttribute(k_res_yslice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv_bytes)) ||
+                 (e = cudaFuncSetAttribute(k_res_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv_bytes))))
+    return e;
   auto backward = [&](int with_src) {
     for (int p = a.N; p >= 0; --p) {
       k_refine_bwd_a<<<rgrid, NT, smem, s>>>(a, p, with_src);
@@ -516,7 +855,17 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
   std::vector<double> corr(npts), prev(npts, 0.0);
   int it = 0;
   for (; it < max_iters; ++it) {
-    k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a);
+    if (sliced) {
+      const int ncol = 2 * a.nc * npts;
+      for (int p = 0; p <= a.N; ++p) {
+        k_res_oslice<<<a.n, RS_THREADS, 0, s>>>(a, p);
+        k_res_yslice<<<ncol, RS_THREADS, kv_bytes, s>>>(a, p);
+        k_res_mm<<<rs_tiles, 256, res_mm_smem_bytes(), s>>>(a, ncol, npts);
+        k_res_finish<<<npts, NT, kv_bytes, s>>>(a, p, ncol);
+      }
+    } else {
+      k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a);
+    }
     if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
     forward();
     if (it + 1 >= max_iters) { ++it; break; }
@@ -542,3 +891,124 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
 }
 
 }  // namespace pw
+
+// ---------------------------------------------------------------------------
+// Self-test of the exact-slice product (k_res_mm) on random slices.
+extern "C" pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, double *rel_err) {
+  using namespace pw;
+  if (!mismatches || !rel_err || n < 4 || n > 512 || n % 4 || ncol < 1 || ncol > 4096) return PW_EINVAL;
+  const int M = 2 * n, K = 2 * n;
+  const size_t asz = (size_t)RS_SLICES * M * K, bsz = (size_t)RS_SLICES * ncol * K;
+  std::vector<int> IA(asz), IB(bsz);   // slice integers, |I| <= 128
+  std::vector<uint16_t> HA(asz), HB(bsz);
+  unsigned st = 2463534242u;
+  auto rnd = [&]() {   // xorshift32
+    st ^= st << 13;
+    st ^= st >> 17;
+    st ^= st << 5;
+    return st;
+  };
+  auto bits = [](int I, int s) {   // BF16 pattern of I 2^-7(s+1)
+    const float f = ldexpf((float)I, -RS_BITS * (s + 1));
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+  };
+  pw_status res = PW_OK;
+  uint16_t *dA = nullptr, *dB = nullptr;
+  int *dexp = nullptr, *dstat = nullptr;
+  double *dY = nullptr;
+  std::vector<double> Y((size_t)M * ncol);
+  if (cudaMalloc(&dA, asz * 2) || cudaMalloc(&dB, bsz * 2) || cudaMalloc(&dexp, (M + ncol) * sizeof(int)) ||
+      cudaMalloc(&dstat, sizeof(int)) || cudaMalloc(&dY, Y.size() * sizeof(double))) {
+    cudaGetLastError();
+    res = PW_ENOMEM;
+  }
+  RefineArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.Osl = dA;
+  a.Ysl = dB;
+  a.Oexp = dexp;
+  a.Yexp = dexp + M;
+  a.Yacc = dY;
+  a.status = dstat;
+  const int tiles = ((M + RS_TILE - 1) / RS_TILE) * ((ncol + RS_TILE - 1) / RS_TILE);
+  for (int round = 0; round < 2 && res == PW_OK; ++round) {
+    // round 0: only the leading slices, with full-scale rows 0 (all +128) and
+    // columns 0 (+128), 1 (-128) so that sums reach 2^24 units; round 1: every slice
+    for (size_t e = 0; e < asz; ++e) {
+      const int s = (int)(e / ((size_t)M * K)), r = (int)((e / K) % M);
+      int I = (int)(rnd() % 257u) - 128;
+      if (round == 0 && s > 0) I = 0;
+      if (s == 0 && r == 0) I = 128;
+      IA[e] = I;
+      HA[e] = bits(I, s);
+    }
+    for (size_t e = 0; e < bsz; ++e) {
+      const int t = (int)(e / ((size_t)ncol * K)), j = (int)((e / K) % ncol);
+      int I = (int)(rnd() % 257u) - 128;
+      if (round == 0 && t > 0) I = 0;
+      if (t == 0 && j < 2) I = j == 0 ? 128 : -128;
+      IB[e] = I;
+      HB[e] = bits(I, t);
+    }
+    if (cudaMemcpy(dA, HA.data(), asz * 2, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(dB, HB.data(), bsz * 2, cudaMemcpyHostToDevice) || cudaMemset(dexp, 0, (M + ncol) * sizeof(int)) ||
+        cudaMemset(dstat, 0, sizeof(int)) ||
+        cudaFuncSetAttribute(k_res_mm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_mm_smem_bytes())) {
+      res = PW_ECUDA;
+      break;
+    }
+    k_res_mm<<<tiles, 256, res_mm_smem_bytes()>>>(a, ncol, 1);
+    int hstat = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(Y.data(), dY, Y.size() * sizeof(double), cudaMemcpyDeviceToHost)) {
+      res = PW_ECUDA;
+      break;
+    }
+    if (hstat) {
+      res = PW_ETIMEOUT;
+      break;
+    }
+    if (round == 0) {
+      // the exact product of the leading slices, an integer times 2^-14, compared bit for bit
+      long long bad = 0;
+      for (int r = 0; r < M; ++r)
+        for (int j = 0; j < ncol; ++j) {
+          long long I = 0;
+          for (int k = 0; k < K; ++k) I += (long long)IA[(size_t)r * K + k] * IB[(size_t)j * K + k];
+          if (Y[(size_t)j * M + r] != ldexp((double)I, -2 * RS_BITS)) ++bad;
+        }
+      *mismatches = bad;
+    } else {
+      // every pair with s + t < RS_SLICES, on rows 0, 64, 128, ...: the integer sums
+      // X_d of each diagonal d = s + t are exact, their scaled sum is formed smallest first
+      double num = 0.0, den = 0.0;
+      for (int r = 0; r < M; r += 64)
+        for (int j = 0; j < ncol; ++j) {
+          long long X[RS_SLICES] = {0};
+          for (int s = 0; s < RS_SLICES; ++s)
+            for (int t = 0; s + t < RS_SLICES; ++t) {
+              const int *pa = &IA[((size_t)s * M + r) * K], *pb = &IB[((size_t)t * ncol + j) * K];
+              long long I = 0;
+              for (int k = 0; k < K; ++k) I += (long long)pa[k] * pb[k];
+              X[s + t] += I;
+            }
+          double ref = 0.0;
+          for (int d = RS_SLICES - 1; d >= 0; --d) ref += ldexp((double)X[d], -RS_BITS * (d + 2));
+          num = fmax(num, fabs(Y[(size_t)j * M + r] - ref));
+          den = fmax(den, fabs(ref));
+        }
+      *rel_err = num / fmax(den, 1e-300);
+    }
+  }
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dexp);
+  cudaFree(dstat);
+  cudaFree(dY);
+  return res;
+}
+

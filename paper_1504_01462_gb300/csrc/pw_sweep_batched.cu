@@ -298,6 +298,114 @@ __global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc(SweepArgs a, int 
   }
 }
 
+// Row scales of the FP16-split [W|Y] (kb_wy2_tc16): for every point and row i,
+// rowexp[2i] = e with max_l |R_il| < 2^e (largest real or imaginary part) and
+// rowexp[2i+1] the same for R_il / k_l^p.  One thread per row (consecutive
+// rows are contiguous in R).
+__global__ void __launch_bounds__(256) kb_rowexp(SweepArgs a) {
+  const int pt = blockIdx.y, i = blockIdx.x * 256 + threadIdx.x;
+  if (inactive(a, pt) || i >= a.n) return;
+  const int n = a.n;
+  const cc *R = reinterpret_cast<const cc *>(a.R) + (size_t)pt * n * n;
+  const KVb<float> v = kv_of<float>(a, pt);
+  float m0 = 0.f, m1 = 0.f;
+  for (int l = 0; l < n; ++l) {
+    const cc r = R[i + (size_t)l * n];
+    const cc rs = cmul(r, v.kinvL[l]);
+    m0 = fmaxf(m0, fmaxf(fabsf(r.re), fabsf(r.im)));
+    m1 = fmaxf(m1, fmaxf(fabsf(rs.re), fabsf(rs.im)));
+  }
+  int e0 = 0, e1 = 0;
+  if (m0 > 0.f) frexpf(m0, &e0);
+  if (m1 > 0.f) frexpf(m1, &e1);
+  // keep the scales inside FP32's normal range (the values themselves are)
+  a.rowexp[(size_t)pt * 2 * n + 2 * i] = max(-100, min(100, e0));
+  a.rowexp[(size_t)pt * 2 * n + 2 * i + 1] = max(-100, min(100, e1));
+}
+
+// [W|Y] of point pairs as kb_wy2_tc, the products in the FP16 split with the
+// row scales of kb_rowexp (the overlap, the shared B, is bounded by 1).
+size_t wy2_tc16_smem_bytes(int n) { return tc::c4_smem_bytes16() + 4 * (size_t)n * sizeof(cc); }
+
+__global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc16(SweepArgs a, int p, int npts) {
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
+  const int pt0 = 2 * blockIdx.y, pt1 = pt0 + 1;
+  const bool act0 = !inactive(a, pt0), act1 = pt1 < npts && !inactive(a, pt1);
+  if (!act0 && !act1) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int tiles_m = (n + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), c0 = (blockIdx.x / tiles_m) * tc::CG_N;
+  const PointDesc d = a.pts[act0 ? pt0 : pt1];   // both points have this one's overlaps
+  const bool tr = a.mirror != 0;
+  const int pi = tr ? d.N - p : p;
+  const zc *O = overlap_of(a, d, p);
+  const cc *O32 = overlap32_of(a, d, p);
+  const cc *O32t = a.O32t ? a.O32t + ((size_t)d.o_off + pi) * n * n : nullptr;
+  auto ov = [=](int l, int j) -> cc {
+    if (tr) {
+      if (O32) return tc::ldg_cc(O32 + j + (size_t)l * n);
+      return ccast<float>(O[j + (size_t)l * n]);
+    }
+    if (O32t) return tc::ldg_cc(O32t + j + (size_t)l * n);
+    if (O32) return tc::ldg_cc(O32 + l + (size_t)j * n);
+    return ccast<float>(O[l + (size_t)j * n]);
+  };
+  auto ovc = [=](int l, int j) -> cc {
+    if (tr) {
+      if (O32t) return O32t[l + (size_t)j * n];
+      if (O32) return O32[j + (size_t)l * n];
+      return ccast<float>(O[j + (size_t)l * n]);
+    }
+    if (O32) return O32[l + (size_t)j * n];
+    return ccast<float>(O[l + (size_t)j * n]);
+  };
+  const int q1 = act1 ? pt1 : pt0;
+  const cc *R0 = reinterpret_cast<const cc *>(a.R) + (size_t)pt0 * n * n;
+  const cc *R1 = reinterpret_cast<const cc *>(a.R) + (size_t)q1 * n * n;
+  const int *X0 = a.rowexp + (size_t)pt0 * 2 * n, *X1 = a.rowexp + (size_t)q1 * 2 * n;
+  cc *M0 = reinterpret_cast<cc *>(a.M) + (size_t)pt0 * n * ncols;
+  cc *M1 = reinterpret_cast<cc *>(a.M) + (size_t)q1 * n * ncols;
+  cc *sk = reinterpret_cast<cc *>(smraw + tc::c4_smem_bytes16());   // kinvL0, kR0, kinvL1, kR1
+  const KVb<float> g0 = kv_of<float>(a, pt0), g1 = kv_of<float>(a, q1);
+  for (int i = threadIdx.x; i < n; i += tc::CG_THREADS) {
+    sk[i] = g0.kinvL[i];
+    sk[n + i] = g0.kR[i];
+    sk[2 * n + i] = g1.kinvL[i];
+    sk[3 * n + i] = g1.kR[i];
+  }
+  __syncthreads();
+  const unsigned amask = (act0 ? 3u : 0u) | (act1 ? 12u : 0u);
+  const bool ok = tc::cgemm_tile_shared_b_f16(
+      n, n, n, r0, c0, amask,
+      [=](int h, int i, int l) { return tc::ldg_cc((h ? R1 : R0) + i + (size_t)l * n); },
+      [=](int h, int l) { return sk[h * 2 * n + l]; },   // kinvL of point h
+      [=](int l, int j) { return ov(l, j); },
+      [=](int q, int i) { return ((q >> 1) ? X1 : X0)[2 * i + (q & 1)]; },
+      [=](int i, int j, const cc (&x)[4]) {
+        const cc o = ovc(i, j);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!((amask >> (2 * h)) & 1u)) continue;
+          const cc *kinv = sk + h * 2 * n, *kr = kinv + n;
+          const cc r = cmul(kr[j], kinv[i]);
+          const cc P = cmul(o, mkc<float>(0.5f * (1.f + r.re), 0.5f * r.im));
+          const cc Q = cmul(o, mkc<float>(0.5f * (1.f - r.re), -0.5f * r.im));
+          const cc t = cmul(kr[j], x[2 * h + 1]);
+          const cc rq = mkc<float>(0.5f * (x[2 * h].re - t.re), 0.5f * (x[2 * h].im - t.im));
+          const cc rp = mkc<float>(0.5f * (x[2 * h].re + t.re), 0.5f * (x[2 * h].im + t.im));
+          cc *M = h ? M1 : M0;
+          M[i + (size_t)j * n] = csub(P, rq);
+          M[i + (size_t)(n + j) * n] = csub(rp, Q);
+        }
+      },
+      smraw);
+  if (!ok && threadIdx.x == 0) {
+    if (act0) a.status[pt0] = 2;
+    if (act1) a.status[pt1] = 2;
+  }
+}
+
 // Tile width of the update kernels (read-modify-write of C): 64 complex
 // columns keep the prefetched C values of a thread in 32 registers.
 constexpr int RMW_TN = 64;
@@ -310,7 +418,7 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
   if (inactive(a, pt)) return;
   const int n = a.n, ncols = 2 * n + a.nc;
   const int nb = min(Tile<float, 256>::NB, n - j0), c0 = j0 + nb;
-  const int m = n - c0, ncol = ncols - c0;
+  const int m = n - c0, ncol = (a.lapack_piv ? n : ncols) - c0;   // lapack_piv: W's columns only
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
   if (q0 >= ncol) return;
@@ -323,14 +431,14 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
-// back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b
-__global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0) {
+// back-substitution update above block j0 (kb rows): M[0:j0, n:ncols] -= U[0:j0, b] X_b
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0, int kb) {
   extern __shared__ __align__(128) unsigned char smtc[];
   unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
   if (inactive(a, pt) || j0 <= 0) return;
   const int n = a.n, ncols = 2 * n + a.nc;
-  const int nb = min(Tile<float, 256>::NB, n - j0);
+  const int nb = min(kb, n - j0);
   const int m = j0, ncol = ncols - n;
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
@@ -341,6 +449,234 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j
       [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
       [=](int i, int j) { return M[i + (size_t)(n + j) * n]; },
       [=](int i, int j, cc acc, cc old) { M[i + (size_t)(n + j) * n] = csub(old, acc); }, smraw);
+  if (!ok && threadIdx.x == 0) a.status[pt] = 2;
+}
+
+// Diagonal block of the back substitution with BS_FB rows (FP32, the
+// tensor-core form): X_b = U_bb^{-1} X_b for BS_COLS right-hand-side columns
+// per CTA.  U_bb and the columns are staged in shared memory; each warp
+// solves four columns at once (lane r holds rows r, r+32, r+64, r+96; the
+// solved value of row s passes by shuffle from its lane), so every element of
+// U_bb read serves four columns and the four recurrences interleave.  With
+// 128-row blocks the update above each block (kb_bsupd_tc) has K = 128 and
+// there are four blocks instead of sixteen at N_G = 512.
+constexpr int BS_FB = 128, BS_COLS = 32, BS_THREADS = 256;
+static_assert(BS_COLS == 4 * (BS_THREADS / 32), "four columns per warp");
+size_t bsdiag_big_smem() { return (size_t)BS_FB * BS_FB * sizeof(cc) + (size_t)BS_FB * BS_COLS * sizeof(cc); }
+
+__global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
+  const int fb = min(BS_FB, n - j0);
+  const int cf = blockIdx.x * BS_COLS;
+  if (cf >= nrhs) return;
+  const int ncl = min(BS_COLS, nrhs - cf);
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  cc *Us = reinterpret_cast<cc *>(smraw);     // Us[r + c fb], the upper triangle of U_bb
+  cc *Xs = Us + (size_t)BS_FB * BS_FB;       // Xs[r + q fb], the block rows of column cf + q
+  for (int e = threadIdx.x; e < fb * fb; e += BS_THREADS) {
+    const int r = e % fb, c = e / fb;
+    Us[e] = r <= c ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
+  }
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    Xs[e] = M[j0 + r + (size_t)(n + cf + q) * n];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = 4 * warp;   // this warp's four columns
+  if (q0 < ncl) {
+    cc x[4][4];   // [column][row slot t: row lane + 32 t]
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        x[c][t] = (q0 + c < ncl && r < fb) ? Xs[r + (q0 + c) * fb] : czero<float>();
+      }
+    for (int sb = (fb - 1) >> 5; sb >= 0; --sb) {       // row slot of s, from the bottom
+      for (int sl = min(31, fb - 1 - 32 * sb); sl >= 0; --sl) {
+        const int s = 32 * sb + sl;
+        const cc ud = Us[s + s * fb];
+        cc xs[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          cc v = x[c][0];
+#pragma unroll
+          for (int t = 1; t < 4; ++t)
+            if (t == sb) v = x[c][t];
+          if (lane == sl) {
+            v = cdiv(v, ud);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (t == sb) x[c][t] = v;
+          }
+          xs[c] = mkc<float>(__shfl_sync(0xffffffffu, v.re, sl), __shfl_sync(0xffffffffu, v.im, sl));
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = lane + 32 * t;
+          if (t <= sb && r < s) {
+            const cc u = Us[r + s * fb];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              x[c][t].re -= u.re * xs[c].re - u.im * xs[c].im;
+              x[c][t].im -= u.re * xs[c].im + u.im * xs[c].re;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        if (q0 + c < ncl && r < fb) Xs[r + (q0 + c) * fb] = x[c][t];
+      }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    M[j0 + r + (size_t)(n + cf + q) * n] = Xs[e];
+  }
+}
+
+// The right-hand sides of the tensor-core FP32 form after the LU of W
+// (P W = L U): X <- P X (kb_rhs_perm), then X <- L^{-1} X by 128-row blocks
+// (kb_fsdiag_big on the diagonal blocks, kb_fsupd_tc below them), then the
+// back substitution as before.  P applies the pivots in order: row j swaps
+// with piv[j] for j = 0 .. n-1.
+constexpr int RP_COLS = 16;   // right-hand-side columns per CTA of kb_rhs_perm
+size_t rhs_perm_smem(int n) { return (size_t)RP_COLS * n * sizeof(cc) + (size_t)n * sizeof(int); }
+
+__global__ void __launch_bounds__(256) kb_rhs_perm(SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
+  const int cf = blockIdx.x * RP_COLS;
+  if (cf >= nrhs) return;
+  const int ncl = min(RP_COLS, nrhs - cf);
+  cc *S = reinterpret_cast<cc *>(smraw);                         // S[r + q n]
+  int *perm = reinterpret_cast<int *>(S + (size_t)RP_COLS * n);   // row r of P X is row perm[r] of X
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  const int *piv = a.piv + (size_t)pt * n;
+  for (int e = threadIdx.x; e < n * ncl; e += 256) S[e] = M[e % n + (size_t)(n + cf + e / n) * n];
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < n; ++r) perm[r] = r;
+    for (int j = 0; j < n; ++j) {
+      const int p = piv[j];
+      if (p > j && p < n) {   // p < j or out of range cannot come from the factorisation
+        const int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * ncl; e += 256) {
+    const int r = e % n, q = e / n;
+    M[r + (size_t)(n + cf + q) * n] = S[perm[r] + q * n];
+  }
+}
+
+// X_b <- L_bb^{-1} X_b for one 128-row diagonal block (unit lower), the
+// schedule of kb_bsdiag_big run from the top.
+__global__ void __launch_bounds__(BS_THREADS, 1) kb_fsdiag_big(SweepArgs a, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
+  const int fb = min(BS_FB, n - j0);
+  const int cf = blockIdx.x * BS_COLS;
+  if (cf >= nrhs) return;
+  const int ncl = min(BS_COLS, nrhs - cf);
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  cc *Ls = reinterpret_cast<cc *>(smraw);     // Ls[r + c fb], the strict lower triangle of L_bb
+  cc *Xs = Ls + (size_t)BS_FB * BS_FB;
+  for (int e = threadIdx.x; e < fb * fb; e += BS_THREADS) {
+    const int r = e % fb, c = e / fb;
+    Ls[e] = r > c ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
+  }
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    Xs[e] = M[j0 + r + (size_t)(n + cf + q) * n];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = 4 * warp;
+  if (q0 < ncl) {
+    cc x[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        x[c][t] = (q0 + c < ncl && r < fb) ? Xs[r + (q0 + c) * fb] : czero<float>();
+      }
+    for (int sb = 0; 32 * sb < fb; ++sb) {
+      for (int sl = 0; sl < 32 && 32 * sb + sl < fb; ++sl) {
+        const int s = 32 * sb + sl;
+        cc xs[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          cc v = x[c][0];
+#pragma unroll
+          for (int t = 1; t < 4; ++t)
+            if (t == sb) v = x[c][t];
+          xs[c] = mkc<float>(__shfl_sync(0xffffffffu, v.re, sl), __shfl_sync(0xffffffffu, v.im, sl));
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = lane + 32 * t;
+          if (t >= sb && r > s && r < fb) {
+            const cc l = Ls[r + s * fb];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              x[c][t].re -= l.re * xs[c].re - l.im * xs[c].im;
+              x[c][t].im -= l.re * xs[c].im + l.im * xs[c].re;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        if (q0 + c < ncl && r < fb) Xs[r + (q0 + c) * fb] = x[c][t];
+      }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+    const int r = e % fb, q = e / fb;
+    M[j0 + r + (size_t)(n + cf + q) * n] = Xs[e];
+  }
+}
+
+// Forward update below block [j0, j0+kb): M[j0+kb:n, n:ncols] -= L[j0+kb:n, b] X_b
+__global__ void __launch_bounds__(tc::CG_THREADS) kb_fsupd_tc(SweepArgs a, int j0, int kb) {
+  extern __shared__ __align__(128) unsigned char smtc[];
+  unsigned char *smraw = smtc;
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int nb = min(kb, n - j0), c0 = j0 + nb;
+  const int m = n - c0, ncol = ncols - n;
+  if (m <= 0) return;
+  const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
+  const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
+  if (q0 >= ncol) return;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  const bool ok = tc::cgemm_tile<true, true, RMW_TN>(
+      m, ncol, nb, r0, q0, [=](int i, int l) { return M[c0 + i + (size_t)(j0 + l) * n]; },
+      [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
+      [=](int i, int j) { return M[c0 + i + (size_t)(n + j) * n]; },
+      [=](int i, int j, cc acc, cc old) { M[c0 + i + (size_t)(n + j) * n] = csub(old, acc); }, smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
@@ -388,7 +724,13 @@ __global__ void __launch_bounds__(BT) kb_panel_apply(SweepArgs a, int j0) {
   if (inactive(a, pt)) return;
   const int n = a.n, ncols = 2 * n + a.nc;
   const int nb = min(NB, n - j0), c0 = j0 + nb;
-  const int cb = c0 + blockIdx.x * BT, ce = min(ncols, cb + BT);
+  // lapack_piv: column blocks [0, j0) take the swaps only (the L columns of
+  // earlier panels), then [c0, n) swaps and the L11 solve; the right-hand
+  // sides are left to the elimination after the LU
+  const int nleft = a.lapack_piv ? (j0 + BT - 1) / BT : 0;
+  const bool left = (int)blockIdx.x < nleft;
+  const int cb = left ? blockIdx.x * BT : c0 + ((int)blockIdx.x - nleft) * BT;
+  const int ce = left ? min(j0, cb + BT) : min(a.lapack_piv ? n : ncols, cb + BT);
   if (cb >= ce) return;
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   for (int e = threadIdx.x; e < nb * nb; e += BT) {
@@ -397,7 +739,7 @@ __global__ void __launch_bounds__(BT) kb_panel_apply(SweepArgs a, int j0) {
   }
   if (threadIdx.x == 0) flag = 0;
   __syncthreads();
-  panel_right_apply<T, BT>(M, n, cb, ce, j0, nb, n - j0, a.piv + (size_t)pt * n, Ls, &flag);
+  panel_right_apply<T, BT>(M, n, cb, ce, j0, nb, n - j0, a.piv + (size_t)pt * n, Ls, &flag, !left);
   if (threadIdx.x == 0 && (flag & 4)) {
     printf("kb_panel_apply: pivot row out of range (point %d, panel %d)\n", pt, j0);
     a.status[pt] = 1;
@@ -516,7 +858,7 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
 
 template <typename T, int BT>
 static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
-                              cudaEvent_t wy1, bool tensor_core) {
+                              cudaEvent_t wy1, bool tensor_core, bool f16 = false) {
   SweepArgs a = a0;
   a.p = p;
   const int n = a.n, ncols = 2 * n + a.nc;
@@ -531,7 +873,11 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   if (p > 0) {
     const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
     if (wy0) cudaEventRecord(wy0, s);
-    if (std::is_same<T, float>::value && tensor_core && a.wy_pairs)
+    if (std::is_same<T, float>::value && tensor_core && a.wy_pairs && f16 && a.rowexp) {
+      kb_rowexp<<<dim3((n + 255) / 256, npts), 256, 0, s>>>(a);
+      kb_wy2_tc16<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
+                    wy2_tc16_smem_bytes(n), s>>>(a, p, npts);
+    } else if (std::is_same<T, float>::value && tensor_core && a.wy_pairs)
       kb_wy2_tc<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
                   wy2_tc_smem_bytes(n), s>>>(a, p, npts);
     else if (std::is_same<T, float>::value && tensor_core)
@@ -541,28 +887,51 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
       kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
     if (wy1) cudaEventRecord(wy1, s);
   }
+  // tensor-core FP32 form: LAPACK-ordered pivots, the LU of W alone, then the
+  // right-hand sides eliminated in 128-row blocks (see kb_rhs_perm)
+  const bool lapack = std::is_same<T, float>::value && tensor_core;
+  a.lapack_piv = lapack ? 1 : 0;
+  const int ucols = lapack ? n : ncols;   // columns the LU updates
   for (int j0 = 0; j0 < n; j0 += NB) {
     kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0);
     const int c0 = j0 + min(NB, n - j0);
-    if constexpr (std::is_same<T, float>::value)
-      kb_panel_apply<T, BT><<<dim3((ncols - c0 + BT - 1) / BT, npts), BT, 0, s>>>(a, j0);
+    if constexpr (std::is_same<T, float>::value) {
+      const int blocks = (lapack ? (j0 + BT - 1) / BT : 0) + (ucols - c0 + BT - 1) / BT;
+      if (blocks > 0) kb_panel_apply<T, BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0);
+    }
     if (c0 < n) {
-      if (std::is_same<T, float>::value && tensor_core)
-        kb_trail_tc<<<dim3(tiles(n - c0, ncols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+      if (lapack)
+        kb_trail_tc<<<dim3(tiles(n - c0, ucols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
                       tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
       else
         kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
     }
   }
+  if (lapack) {
+    const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
+    kb_rhs_perm<<<dim3((ncols - n + RP_COLS - 1) / RP_COLS, npts), 256, rhs_perm_smem(n), s>>>(a);
+    for (int j0 = 0; j0 < n; j0 += BS_FB) {
+      kb_fsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0);
+      const int c1 = j0 + std::min(BS_FB, n - j0);
+      if (c1 < n)
+        kb_fsupd_tc<<<dim3(tiles(n - c1, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB);
+    }
+  }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
-  for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
-    kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
-    if (j0 > 0) {
-      if (std::is_same<T, float>::value && tensor_core)
+  if (std::is_same<T, float>::value && tensor_core) {
+    // 128-row blocks: four diagonal solves and three K = 128 updates at N_G = 512
+    const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
+    for (int j0 = ((n - 1) / BS_FB) * BS_FB; j0 >= 0; j0 -= BS_FB) {
+      kb_bsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0);
+      if (j0 > 0)
         kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
-      else
-        kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB);
+    }
+  } else {
+    for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
+      kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
+      if (j0 > 0) kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
     }
   }
   kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p);
@@ -606,6 +975,16 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
     e = cudaFuncSetAttribute(kb_trail_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_bsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_fsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_fsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
+  if (e == cudaSuccess && (variant & 2))
+    e = cudaFuncSetAttribute(kb_rhs_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_perm_smem(n));
+  if (e == cudaSuccess && (variant & 6) == 6)
+    e = cudaFuncSetAttribute(kb_wy2_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wy2_tc16_smem_bytes(n));
   return e;
 }
 
@@ -615,19 +994,26 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
   if (precision == PW_FP64)
     return (variant & 1) ? sweep_step<double, 512>(a, npts, p, s, wy0, wy1, false)
                          : sweep_step<double, 256>(a, npts, p, s, wy0, wy1, false);
-  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore)
-                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore);
+  const bool f16 = (variant & 4) != 0;   // FP16 split for the paired [W|Y]
+  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore, f16)
+                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore, f16);
 }
 
-int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 4; }
+int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 8; }
 
-int sweep_batched_launches(int n, int precision) {
+int sweep_batched_launches(int n, int precision, int variant) {
   const int NB = Tile<float, 256>::NB;
   const int panels = (n + NB - 1) / NB;
+  const bool fp32 = precision != PW_FP64, tensor = fp32 && (variant & 2);
   // vectors, [W|Y], finish; per panel: factorisation, trailing update (not
-  // after the last), the FP32 form's right-hand apply, diagonal solve and
-  // back-substitution update (not for the first block)
-  return 3 + 2 * panels - 1 + (precision == PW_FP64 ? 0 : panels) + 2 * panels - 1;
+  // after the last), the FP32 form's right-hand apply; the back substitution:
+  // a diagonal solve per block and an update above every block but the first
+  // (32-row blocks, or 128-row blocks in the tensor-core form)
+  const int bblocks = tensor ? (n + BS_FB - 1) / BS_FB : panels;
+  // the tensor-core form adds the right-hand sides' elimination: a
+  // permutation, a diagonal solve per 128-row block and an update below every
+  // block but the last
+  return 3 + 2 * panels - 1 + (fp32 ? panels : 0) + 2 * bblocks - 1 + (tensor ? 2 * bblocks : 0);
 }
 
 }  // namespace pw

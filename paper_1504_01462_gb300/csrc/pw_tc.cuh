@@ -13,6 +13,7 @@
 //
 // Every wait is bounded: a wait that runs out records an error and returns.
 #pragma once
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "pw_cx.cuh"
@@ -43,6 +44,22 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
+// Instruction descriptor of kind::f16 with BF16 A and B, D FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                      // D format: FP32
+         | (1u << 7)                    // A format: BF16
+         | (1u << 10)                   // B format: BF16
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+// Instruction descriptor of kind::f16 with FP16 A and B, D FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4)                      // D format: FP32
+         | ((uint32_t)(N >> 3) << 17)   // N / 8 (A and B format 0: FP16)
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
 // TMEM allocation by one full warp; the address is written to *slot.
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
@@ -60,6 +77,40 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// D[tmem] (+)= A[smem] B[smem] with BF16 operands (K = 16 per instruction).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Asynchronous 16-byte global -> shared copy (cp.async, L2 only); with
+// valid == false nothing is read and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// every group of this thread but the newest N has landed
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// D[tmem] (+)= A[smem] B[smem], kind::f16 (16-bit A and B, K = 16 per instruction).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -505,6 +556,211 @@ __device__ bool cgemm_tile_shared_b(int m, int ncol, int k, int r0, int c0, unsi
 #pragma unroll
         for (int q = 0; q < C4; ++q)
           x[q] = eim ? mkc<float>(other[q][i + 4], vv[q][i + 4]) : mkc<float>(vv[q][i], other[q][i]);
+        if (er < m && jb + i < ncol) fe(er, jb + i, x);
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, C4 * TN);
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// The four-accumulator tile of cgemm_tile_shared_b with an FP16 split in
+// place of the TF32 one.  Each real operand value x becomes hi = fp16(x) and
+// lo = fp16(x - hi); A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 carries about
+// 22 bits, like the TF32 split, but kind::f16 runs at twice the rate of
+// kind::tf32 and the staged operands take half the bytes, so one K stage of 8
+// complex values (16 real) is one MMA step and three MMAs per accumulator.
+// FP16's range is kept by scaling: row r of accumulator q's A is multiplied by
+// 2^(F16_HEAD - fx(q, r)) before the split (fx(q, r) >= log2 of the row's
+// largest component) and B, which must be bounded by 1 in magnitude (an
+// overlap matrix), by 2^F16_HEAD; the result is scaled back by
+// 2^(fx(q, r) - 2 F16_HEAD).  The headroom keeps typical entries (about
+// 1/sqrt(n) of the largest) and their remainders in FP16's normal range, so
+// the split matches the TF32 split's accuracy relative to each row's scale
+// (entries far below it keep an absolute accuracy of 2^-24 of the scaled
+// range, FP16's subnormal step); the largest scaled value stays below 2^8.
+// Layout: K-major, no swizzle, 16-bit elements: core matrices of 8 rows x 8
+// values (16 bytes per row), LBO = 128 between the two K-halves of a step,
+// SBO = 256 between 8-row groups.
+// ---------------------------------------------------------------------------
+constexpr int CG_AB16 = CG_M * 2 * CG_KC * 2;                        // bytes of one A' part per stage
+__host__ __device__ constexpr int cg_bb16() { return CG_N * 2 * CG_KC * 2; }   // bytes of one B' part
+__host__ __device__ constexpr size_t c4_stage16() { return (size_t)C4 * 2 * CG_AB16 + 2 * (size_t)cg_bb16(); }
+__host__ __device__ constexpr size_t c4_smem_bytes16() { return 2 * c4_stage16() + 64; }
+
+// Byte offset of element (row, k), k < 16, of a 16-bit K-major operand stage.
+__host__ __device__ __forceinline__ uint32_t kmajor_offset16(int row, int k) {
+  return (uint32_t)(row >> 3) * 256u + (uint32_t)((k >> 3) & 1) * 128u + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(k & 7) * 2u;
+}
+
+// Four values (already scaled) as FP16 hi parts and FP16 remainders, 8 bytes each.
+__device__ __forceinline__ void store_split16(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, float a,
+                                              float b, float c, float d) {
+  const __half ha = __float2half_rn(a), hb = __float2half_rn(b), hc = __float2half_rn(c), hd = __float2half_rn(d);
+  const __half la = __float2half_rn(a - __half2float(ha)), lb = __float2half_rn(b - __half2float(hb));
+  const __half lc = __float2half_rn(c - __half2float(hc)), ld = __float2half_rn(d - __half2float(hd));
+  uint2 h, l;
+  h.x = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+  h.y = (uint32_t)__half_as_ushort(hc) | ((uint32_t)__half_as_ushort(hd) << 16);
+  l.x = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+  l.y = (uint32_t)__half_as_ushort(lc) | ((uint32_t)__half_as_ushort(ld) << 16);
+  *reinterpret_cast<uint2 *>(hi_base + off) = h;
+  *reinterpret_cast<uint2 *>(lo_base + off) = l;
+}
+
+// 2^e as a float (e within the normal range)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+constexpr int F16_HEAD = 8;   // power-of-two headroom of the FP16 split (see cgemm_tile_shared_b_f16)
+
+template <class FA, class FS, class FB, class FX, class FE>
+__device__ bool cgemm_tile_shared_b_f16(int m, int ncol, int k, int r0, int c0, unsigned amask, FA fa, FS fs,
+                                        FB fb, FX fx, FE fe, unsigned char *smem) {
+  constexpr int TN = CG_N, BB = cg_bb16();
+  constexpr size_t STAGE = c4_stage16();
+  constexpr int NCH = TN / 16;
+  unsigned char *stage0 = smem;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);   // [2]
+  uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const cc zero = czero<float>();
+  struct Stg {
+    cc a[2][2];   // A_h (r, l), (r, l+1)
+    cc b[4];
+  };
+  // this thread's staging row and its scales 2^-fx(q, r)
+  const int srr = tid % (CG_M / 2), slp = tid / (CG_M / 2);
+  float sdown[C4];
+#pragma unroll
+  for (int q = 0; q < C4; ++q)
+    sdown[q] = (r0 + srr < m && ((amask >> q) & 1u)) ? pow2f(F16_HEAD - fx(q, r0 + srr)) : 1.f;
+  const float bup = pow2f(F16_HEAD);
+  auto load = [&](int s, Stg &t) {
+    const int l0 = s * CG_KC;
+    const int r = r0 + srr, l = l0 + 2 * slp;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool on = (amask >> (2 * h)) & 3u;
+      t.a[h][0] = (on && r < m && l < k) ? fa(h, r, l) : zero;
+      t.a[h][1] = (on && r < m && l + 1 < k) ? fa(h, r, l + 1) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * CG_THREADS;
+      const int jj = e % TN, lq = e / TN;
+      const int j = c0 + jj, lb = l0 + 2 * lq;
+      t.b[2 * u] = (lb < k && j < ncol) ? fb(lb, j) : zero;
+      t.b[2 * u + 1] = (lb + 1 < k && j < ncol) ? fb(lb + 1, j) : zero;
+    }
+  };
+  auto store = [&](unsigned char *base, int s, const Stg &t) {
+    const int l = s * CG_KC + 2 * slp;
+#pragma unroll
+    for (int q = 0; q < C4; ++q) {
+      if (!((amask >> q) & 1u)) continue;
+      const int h = q >> 1;
+      cc a0 = t.a[h][0], a1 = t.a[h][1];
+      if (q & 1) {
+        if (l < k) a0 = cmul(a0, fs(h, l));
+        if (l + 1 < k) a1 = cmul(a1, fs(h, l + 1));
+      }
+      const float sc = sdown[q];
+      a0 = mkc<float>(a0.re * sc, a0.im * sc);
+      a1 = mkc<float>(a1.re * sc, a1.im * sc);
+      unsigned char *Ahi = base + (size_t)q * 2 * CG_AB16, *Alo = Ahi + CG_AB16;
+      store_split16(Ahi, Alo, kmajor_offset16(2 * srr, 4 * slp), a0.re, -a0.im, a1.re, -a1.im);
+      store_split16(Ahi, Alo, kmajor_offset16(2 * srr + 1, 4 * slp), a0.im, a0.re, a1.im, a1.re);
+    }
+    unsigned char *Bhi = base + (size_t)C4 * 2 * CG_AB16, *Blo = Bhi + BB;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * CG_THREADS;
+      const int jj = e % TN, lq = e / TN;
+      store_split16(Bhi, Blo, kmajor_offset16(jj, 4 * lq), t.b[2 * u].re * bup, t.b[2 * u].im * bup,
+                    t.b[2 * u + 1].re * bup, t.b[2 * u + 1].im * bup);
+    }
+  };
+  const int lrow = 32 * (warp & 3) + lane;
+  const int er = r0 + (lrow >> 1), eim = lrow & 1;
+  Stg st0, st1;
+  const int nstage = (k + CG_KC - 1) / CG_KC;
+  load(0, st0);
+  if (nstage > 1) load(1, st1);
+  if (warp == 0) tmem_alloc(slot, C4 * TN);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *slot;
+  bool ok = true;
+  auto step = [&](int s, Stg &t) {
+    const int b = s & 1;
+    unsigned char *base = stage0 + b * STAGE;
+    if (s >= 2) ok = mbar_wait(&mbar[b], ((s - 2) >> 1) & 1) && ok;   // buffer b is free again
+    store(base, s, t);
+    if (s + 2 < nstage) load(s + 2, t);
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      constexpr uint32_t idesc = idesc_f16(CG_M, TN);
+      const unsigned char *Bhi = base + (size_t)C4 * 2 * CG_AB16, *Blo = Bhi + BB;
+      const uint64_t bh = smem_desc(Bhi, 128, 256);
+      const uint64_t bl = smem_desc(Blo, 128, 256);
+#pragma unroll
+      for (int q = 0; q < C4; ++q) {
+        if (!((amask >> q) & 1u)) continue;
+        const unsigned char *Ahi = base + (size_t)q * 2 * CG_AB16, *Alo = Ahi + CG_AB16;
+        const uint32_t d = tmem + (uint32_t)(q * TN);
+        mma_f16(d, smem_desc(Ahi, 128, 256), bh, idesc, s > 0 ? 1u : 0u);
+        mma_f16(d, smem_desc(Ahi, 128, 256), bl, idesc, 1u);
+        mma_f16(d, smem_desc(Alo, 128, 256), bh, idesc, 1u);
+      }
+      mma_commit(&mbar[b]);
+    }
+  };
+  for (int s = 0; s < nstage; s += 2) {
+    step(s, st0);
+    if (s + 1 < nstage) step(s + 1, st1);
+  }
+  ok = mbar_wait(&mbar[(nstage - 1) & 1], ((nstage - 1) >> 1) & 1) && ok;
+  fence_after_sync();
+  if (ok) {
+    float sup[C4];
+#pragma unroll
+    for (int q = 0; q < C4; ++q) sup[q] = (er < m && ((amask >> q) & 1u)) ? pow2f(fx(q, er) - 2 * F16_HEAD) : 1.f;
+#pragma unroll 1
+    for (int qq = 0; qq < NCH; ++qq) {
+      float vv[C4][8], other[C4][8];
+#pragma unroll
+      for (int q = 0; q < C4; ++q) {
+        if ((amask >> q) & 1u) {
+          tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(q * TN + (TN / 2) * (warp >> 2) + 8 * qq),
+                   vv[q]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) vv[q][i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) other[q][i] = __shfl_xor_sync(0xffffffffu, vv[q][i], 1);
+      }
+      const int jb = c0 + (TN / 2) * (warp >> 2) + 8 * qq + (eim ? 4 : 0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        cc x[C4];
+#pragma unroll
+        for (int q = 0; q < C4; ++q) {
+          const cc v = eim ? mkc<float>(other[q][i + 4], vv[q][i + 4]) : mkc<float>(vv[q][i], other[q][i]);
+          x[q] = mkc<float>(v.re * sup[q], v.im * sup[q]);
+        }
         if (er < m && jb + i < ncol) fe(er, jb + i, x);
       }
     }

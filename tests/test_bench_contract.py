@@ -32,5 +32,9 @@ def test_refine_launch_count():
     # forward pass (2N+1 launches), and a backward pass after every pass but the last
     N = 10
     for batched, bw in ((True, 3), (False, 2)):
-        assert bench.refine_launches(N, 2, batched) == 2 + bw * (N + 1) + 2 * (2 * N + 2) + bw * (N + 1)
+        assert (bench.refine_launches(N, 2, batched, sliced=False)
+                == 2 + bw * (N + 1) + 2 * (2 * N + 2) + bw * (N + 1))
+    # the residual as slice products: four launches per interface in place of one
+    assert (bench.refine_launches(N, 2, True, sliced=True)
+            == bench.refine_launches(N, 2, True, sliced=False) + 2 * (4 * (N + 1) - 1))
     assert bench.refine_launches(N, 0) == 0

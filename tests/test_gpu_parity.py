@@ -342,6 +342,18 @@ def test_transmission_mixed_refined_one_kpar(pw):
     assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
 
 
+@pytest.mark.parametrize("ng,nsl", [(128, 40), (512, 6)])
+def test_transmission_mixed_sliced_residual(pw, ng, nsl):
+    """Points of one k_par with a basis that is a multiple of 4 and at most 512:
+    the refinement's residual products O y run as exact BF16 slice products on
+    the tensor cores.  N_G = 128 spans two row tiles and a ragged column tile;
+    N_G = 512 puts 1024 terms in each exact sum."""
+    inst = junction(ng=ng, n_slices=nsl, n_e=4, n_k=1)
+    ref = O.transmission(inst)
+    got, _, _ = _gpu_T(pw, inst, 1)
+    assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
+
+
 def test_transmission_largest_basis_mixed(pw):
     """N_G = 1024, the largest basis pw_setup accepts (the panel LU then takes
     its global-memory path, the eigensolver its largest shared-memory carves),

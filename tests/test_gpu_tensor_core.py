@@ -25,6 +25,24 @@ def test_tcgen05_tile_product(pw):
     assert e3 < e1 / 50
 
 
+@pytest.mark.parametrize("n,ncol", [(512, 256), (100, 200), (4, 3)])
+def test_exact_slice_product(pw, n, ncol):
+    """The residual's slice product: 7-bit slices in BF16 on tcgen05 with FP32
+    accumulation are exact for 2n <= 1024 inner terms (sums up to 2^24 units at
+    n = 512); every slice pair summed in double-float is accurate to about
+    2^-48.  n = 100 and ncol = 200 leave ragged row, column and K tiles."""
+    bad, rel = pw.selftest_slice_product(n, ncol)
+    assert bad == 0, bad
+    assert rel < 1e-13, rel
+
+
+def test_fp16_split_tile_product(pw):
+    """The FP16 split's layout, descriptors and headroom on one tile: FP32-level
+    accuracy like the TF32 split."""
+    e = pw.selftest_f16_split()
+    assert e < 2e-6, e
+
+
 def _T(pw, inst, E, k, variant, refine_iters):
     T = torch.zeros(len(E), dtype=torch.float64, device="cuda")
     with pw.Context.from_instance(inst, pw.MIXED_FP32, refine_iters) as ctx:
@@ -54,3 +72,25 @@ def test_sweep_with_tensor_core_products(pw, variant):
     assert np.all(np.abs(raw - simt) / scale < 1e-4)
     got = _T(pw, inst, E, k, variant, 4)
     assert np.all(np.abs(got - ref) / scale < 1e-8), (got, ref)
+
+
+@pytest.mark.parametrize("variant", [6, 7])
+def test_sweep_with_fp16_split_point_pairs(pw, variant):
+    """The paired [W|Y] in the FP16 split (sweep variant bit 2, four points of
+    one k_par so that pairs share the overlap): the unrefined sweep agrees
+    with the TF32-split sweep and the oracle at FP32 level, the refined one
+    meets 1e-8."""
+    import numpy as np
+    from oracle import pw_oracle as O
+    from synthetic import junction
+    inst = junction(ng=97, n_slices=60, n_e=4, n_k=1)
+    E, k = inst.energies, inst.kpar
+    ref = O.transmission(inst)
+    scale = np.maximum(1.0, np.abs(ref))
+    raw = _T(pw, inst, E, k, variant, -1)
+    assert np.all(np.abs(raw - ref) / scale < 1e-4), (raw, ref)
+    tf32 = _T(pw, inst, E, k, variant & 3, -1)
+    assert np.all(np.abs(raw - tf32) / scale < 1e-4)
+    got = _T(pw, inst, E, k, variant, 4)
+    assert np.all(np.abs(got - ref) / scale < 1e-8), (got, ref)
+
