@@ -38,6 +38,12 @@ from synthetic import junction, minimal_cell, uneven_batch  # noqa: E402
 
 METRIC = "(E,k∥)-points/s at N_G=512, 320 slices: mixed-precision vs FP64, at 1e-8 rel T"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+GOLDEN_512 = os.path.join(ROOT, "tests", "golden", "junction512_k5.json")
+PROFILE_STRIDE = 3      # every third launch of each kernel kind is bracketed by CUDA events
+T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
+# DRAM bytes per launch of kernels captured with ncu (read + write), with the capture they
+# come from; a kernel changed since its capture has no entry
+KERNEL_TRAFFIC = {}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -101,6 +107,72 @@ def sweep_flops_per_point(n, nopen_left):
     back substitution on n + n_open right-hand sides (n^2 (n + n_open));
     8 real flops per complex multiply-add."""
     return 8.0 * (2.0 * n ** 3 + n ** 3 / 3.0 + n * n * (n + nopen_left))
+
+
+def sweep_kind_totals(n, nc, npts, N, tensor, esz):
+    """Algorithmic work of one step's sweep per kernel kind (all N+1
+    interfaces, npts points): {kind: (flops, bytes)}.  CMA = 8 flop.  Bytes are
+    what each launch must move at least: the matrix region it updates read and
+    written once, its operands read once.  `tensor`: the tensor-core FP32 form
+    (LAPACK-ordered pivots, the LU updates W's columns only, the right-hand
+    sides n + nc eliminated in 128-row blocks after the LU); else the SIMT form
+    (32-row blocks, the LU updates all 2n + nc columns)."""
+    NB, FB = 32, 128
+    ncols, nrhs = 2 * n + nc, n + nc
+    ucols = n if tensor else ncols
+    tr_f = tr_b = pa_f = pn_f = 0.0
+    for j0 in range(0, n, NB):
+        nb = min(NB, n - j0)
+        c0 = j0 + nb
+        pn_f += (n - j0) * nb * nb / 2.0
+        pa_f += nb * nb / 2.0 * (ucols - c0)
+        if c0 < n:
+            tr_f += (n - c0) * (ucols - c0) * nb
+            tr_b += esz * (2.0 * (n - c0) * (ucols - c0) + (n - c0) * nb + nb * (ucols - c0))
+    bs = FB if tensor else NB
+    up_f = up_b = dg_f = fs_f = fs_b = fd_f = 0.0
+    for j0 in range(0, n, bs):
+        fb = min(bs, n - j0)
+        dg_f += fb * fb / 2.0 * nrhs
+        if j0 > 0:
+            up_f += j0 * nrhs * fb
+            up_b += esz * (2.0 * j0 * nrhs + j0 * fb + fb * nrhs)
+        if tensor:
+            fd_f += fb * fb / 2.0 * nrhs
+            c1 = j0 + fb
+            if c1 < n:
+                fs_f += (n - c1) * nrhs * fb
+                fs_b += esz * (2.0 * (n - c1) * nrhs + (n - c1) * fb + fb * nrhs)
+    I = (N + 1) * npts
+    out = {
+        "kb_wy": (8.0 * 2 * n ** 3 * N * npts, esz * (n * n + 2.0 * n * n) * N * npts),
+        "kb_trail": (8.0 * tr_f * I, tr_b * I),
+        "kb_panel": (8.0 * pn_f * I, None),
+        "kb_panel_apply": (8.0 * pa_f * I, None),
+        "kb_bsupd": (8.0 * up_f * I, up_b * I),
+        "kb_bsdiag": (8.0 * dg_f * I, None),
+    }
+    if tensor:
+        out["kb_fsupd_tc"] = (8.0 * fs_f * I, fs_b * I)
+        out["kb_fsdiag_big"] = (8.0 * fd_f * I, None)
+    return out
+
+
+def kernel_table(kprof, steps):
+    """Per-kernel totals of the timed region from the library's sampled CUDA
+    events: average launch time of the timed launches x all launches."""
+    rows = []
+    for name, (ms, timed, launches) in kprof.items():
+        if timed <= 0:
+            continue
+        avg = ms / timed
+        rows.append({"kernel": name, "launches_per_step": launches / steps, "avg_launch_ms": avg,
+                     "ms_per_step": avg * launches / steps, "timed_launches": timed})
+    tot = sum(r["ms_per_step"] for r in rows) or 1.0
+    for r in rows:
+        r["share"] = r["ms_per_step"] / tot
+    rows.sort(key=lambda r: -r["ms_per_step"])
+    return rows
 
 
 class ClockSampler:
@@ -180,6 +252,58 @@ def cpu_oracle_rate(inst, n_e, sample_ifaces=24, sample_slices=24):
                   f"interface S + star products of N_G={m.n}, scaled to {m.N + 2} slices "
                   f"(amortised over {n_e} energies) and {m.N + 1} interfaces",
         "seconds_per_point": per_point, "n": m.n, "N": m.N}
+
+
+def golden_junction512():
+    """Stored oracle T of the 128 energies at one k_par of the N_G = 512,
+    320-slice junction (None when the file is absent)."""
+    try:
+        with open(GOLDEN_512) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def fp64_sample(pw, torch, inst, n_e, stream, gold, npts):
+    """The plain FP64 GPU form on a bounded sample of one step: `npts`
+    energies of one k_par through the whole path (eigenmodes and overlaps of
+    the k_par in FP64, the FP64 sweep), timed with CUDA events.  Points/s for
+    a full step of n_e energies = n_e / (mode stage + n_e x sweep time per
+    point); the sampled T are compared with the stored oracle values."""
+    kk = gold["k_index"] if gold is not None else 0
+    sel = np.unique(np.linspace(0, n_e - 1, npts).astype(int))
+    idx = kk * n_e + sel
+    with pw.Context.from_instance(inst, precision=pw.FP64, stream=stream.cuda_stream) as c64:
+        T64 = torch.empty(len(sel), dtype=torch.float64, device="cuda")
+        c64.set_profiling(True)
+        c64.get_profile(reset=True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        c64.transmission(inst.energies[idx], inst.kpar[idx], T64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = c64.get_profile(reset=True)
+        kprof = c64.get_kernel_profile(reset=True)
+        c64.set_profiling(False)
+        T64 = T64.cpu().numpy()
+    total_ms = ev0.elapsed_time(ev1)
+    modes_ms = prof["modes_ms"] + prof["overlap_ms"]
+    sweep_ms = max(total_ms - modes_ms, 1e-9)
+    step_ms = modes_ms + n_e * sweep_ms / len(sel)
+    out = {"value": n_e / (step_ms / 1e3), "unit": "points/s", "step_ms_estimate": step_ms,
+           "sample": f"1 k_par (index {kk}) x {len(sel)} of its {n_e} energies through the whole FP64 path "
+                     f"(eigenmodes and overlaps of the k_par, FP64 sweep), CUDA events; a full step is the "
+                     f"mode stage plus {n_e} x the sweep time per point",
+           "modes_ms": modes_ms, "sweep_ms_per_point": sweep_ms / len(sel),
+           "kernels": kernel_table(kprof, 1)[:6]}
+    if gold is not None:
+        ref = np.array([gold["T"][i] if gold["T"][i] is not None else np.nan for i in sel])
+        rel = np.abs(T64 - ref) / np.maximum(np.abs(ref), T_FLOOR)
+        ok = ~np.isnan(ref)
+        out["vs_oracle"] = {"points": int(ok.sum()),
+                            "max_rel_err_T": float(np.max(rel[ok])) if ok.any() else None}
+    return out
 
 
 def workload_config(name, n, N, n_e, n_k, world):
@@ -336,7 +460,10 @@ def main():
                     help="sweep launch variant (bit 0: 512-thread SIMT tiles, bit 1: [W|Y], LU and "
                          "back-substitution GEMMs on the tcgen05 tensor cores); -1: library default")
     ap.add_argument("--no-accuracy", action="store_true",
-                    help="skip the FP64 re-evaluation of sampled points of the last step")
+                    help="skip the comparison with the stored oracle values and the FP64 sample")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU sample")
+    ap.add_argument("--fp64-points", type=int, default=16,
+                    help="energies of the FP64 GPU sample (one k_par)")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the slice count (profiling of small cases only)")
     ap.add_argument("--composition", default="sweep", choices=["sweep", "doubling"],
@@ -393,8 +520,11 @@ def main():
     barrier()
 
     # ---- device-timed region: K steps, CUDA events on the library's stream
-    ctx.set_profiling(True)
+    # (every PROFILE_STRIDE-th launch of each kernel kind is also bracketed by
+    # events, for the per-kernel table and the roofline of the dominant kernel)
+    ctx.set_profiling(True, stride=PROFILE_STRIDE)
     ctx.get_profile(reset=True)
+    ctx.get_kernel_profile(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -411,6 +541,7 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.get_profile(reset=True)
+    kprof = ctx.get_kernel_profile(reset=True)
     ctx.set_profiling(False)
     nopen_last = nop.cpu().numpy()
     err_max = float(err.max().item())
@@ -431,100 +562,107 @@ def main():
     e2e_s = max(time.perf_counter() - t0, 1e-9)
     e2e_value = total_points / reduce_max(e2e_s, world, "cuda")
 
-    # ---- accuracy of the mixed form at this size: sampled points of the last
-    # step re-evaluated by the FP64 GPU path (itself checked against the oracle
-    # to 1e-10 in the parity tests), outside every timed region
-    accuracy_vs_fp64 = None
-    if prec == pw.MIXED_FP32 and rank == 0 and not args.no_accuracy:
-        E_last, k_last = step_points(args.warmup + args.steps - 1)
-        T_mixed = T.cpu().numpy()
-        ctx.close()
-        torch.cuda.empty_cache()
-        sel = np.unique(np.linspace(0, n_e - 1, 8).astype(int))
-        with pw.Context.from_instance(inst, precision=pw.FP64, stream=stream.cuda_stream) as c64:
-            T64 = torch.empty(len(sel), dtype=torch.float64, device="cuda")
-            c64.transmission(E_last[sel], k_last[sel], T64)
-            T64 = T64.cpu().numpy()
-        rel = np.abs(T_mixed[sel] - T64) / np.maximum(1.0, np.abs(T64))
-        accuracy_vs_fp64 = {"points": int(len(sel)), "max_rel_err_T": float(rel.max()),
-                            "T_range": [float(T64.min()), float(T64.max())]}
+    # ---- accuracy and the FP64 GPU form, outside every timed region (rank 0):
+    # the stored oracle T of all 128 energies at the golden k_par (written by
+    # tests/golden/make_fullsize_golden.py) against this form's T, and the FP64
+    # GPU form timed on a bounded sample of the same step
+    accuracy_vs_oracle = None
+    fp64_arm = None
+    if rank == 0 and not args.no_accuracy and args.config == "junction512" and not args.slices:
+        gold = golden_junction512()
+        if gold is not None:
+            kk = gold["k_index"]
+            idx = np.arange(kk * n_e, (kk + 1) * n_e)
+            ctx.transmission(inst.energies[idx], inst.kpar[idx], T, None, nop, err)
+            torch.cuda.synchronize()
+            have = np.array([t is not None for t in gold["T"]])
+            ref = np.array([t if t is not None else np.nan for t in gold["T"]])
+            got = T.cpu().numpy()
+            rel = np.abs(got - ref) / np.maximum(np.abs(ref), T_FLOOR)
+            accuracy_vs_oracle = {"points": int(have.sum()), "k_index": int(kk),
+                                  "max_rel_err_T": float(np.nanmax(rel[have])) if have.any() else None,
+                                  "T_floor": T_FLOOR,
+                                  "T_min_nonzero": float(np.min(ref[have & (ref > 0)])) if (have & (ref > 0)).any()
+                                  else None}
+        if prec == pw.MIXED_FP32 and not args.no_fp64:
+            ctx.close()
+            torch.cuda.empty_cache()
+            fp64_arm = fp64_sample(pw, torch, inst, n_e, stream, gold, args.fp64_points)
 
     if rank == 0:
-        nq = N + 2
-        fp64_peak = 1.25
-        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
-        # per k-set: Hamiltonians, the eigensolver (five launches in double-float: reduction,
-        # QL stream, rotations, back-transformation, sort; one in FP64), overlaps, and the
-        # mixed form's FP32 copies of the overlaps (plain and transposed)
-        modes_launches = 1 + (5 if prec == pw.MIXED_FP32 else 1) + 1 + (2 if prec == pw.MIXED_FP32 else 0)
-        # eigensolver launch: one per step, nq matrices
-        heev_ms = prof["modes_ms"] / max(prof["modes_stages"], 1)
-        heev_flops = nq * heev_flops_per_matrix(n)
-        heev_ach = heev_flops / (heev_ms / 1e3) / 1e12
-        # [W|Y] GEMM launches of the sweep: npts x 2 n^3 complex multiply-adds each
-        wy_ms = prof["wy_ms"] / max(prof["wy_launches"], 1)
-        wy_flops = n_e * 8.0 * 2.0 * n ** 3
-        wy_ach = wy_flops / (wy_ms / 1e3) / 1e12 if prof["wy_launches"] else 0.0
         variant = args.sweep_variant if args.sweep_variant >= 0 else (2 if prec == pw.MIXED_FP32 else 0)
         tensor = prec == pw.MIXED_FP32 and (variant & 2) != 0
         peaks = measured_peaks()
-        # TF32 dense peak = measured bf16 x the nominal TF32/BF16 ratio (1.1 / 2.25); the hi/lo
+        hbm = peaks.get("hbm_gbs") or 6800.0
+        try:
+            own = pw.measure_peaks()
+        except Exception:       # noqa: BLE001  (reported as missing)
+            own = {}
+        fp32_peak = own.get("fp32_fma") or SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+        fp64_peak = max(own.get("fp64_fma") or 0.0, own.get("fp64_mma") or 0.0) or 1.25
+        # TF32 dense = measured bf16 x the nominal TF32/BF16 ratio (1.1 / 2.25); the hi/lo
         # split executes three TF32 products per algorithmic product
-        tf32_peak = (peaks.get("bf16_tflops") or 1900.0) * (1.1 / 2.25)
-        wy_peak = tf32_peak / 3.0 if tensor else (fp32_peak if prec == pw.MIXED_FP32 else fp64_peak)
-        # the mixed form's eigensolver runs in double-float on the FP32 pipe: about 12 FP32
-        # instructions per real multiply-add (2 algorithmic flops) against 2 flops per FMA
-        # instruction, so its ceiling is the FP32 rate / 12 in algorithmic flops
-        heev_peak = fp32_peak / 12.0 if prec == pw.MIXED_FP32 else fp64_peak
-        heev_obj = {"bound": "alu",
-                    "kernel": ("k_heev<df> + k_ql_df + k_rot_apply + k_backtransform + k_eig_sort "
-                               "(double-float eigensolver, five launches per step)"
-                               if prec == pw.MIXED_FP32 else
-                               "k_heev<double> (FP64 Householder + QL, one launch per step)"),
-                    "achieved": heev_ach, "peak": heev_peak, "unit": "TFLOP/s",
-                    "frac": heev_ach / heev_peak, "traffic": None,
-                    "peak_source": ("FP32 FMA rate / 12 (12 FP32 instructions per double-float multiply-add)"
-                                    if prec == pw.MIXED_FP32 else
-                                    "FP64 nominal 1.25 TFLOP/s (GB300 dense FP64; no measured FP64 peak)"),
-                    "avg_launch_ms": heev_ms, "total_ms": prof["modes_ms"]}
-        # every step is one k_par, so neighbouring points share their overlaps and the
-        # tensor-core [W|Y] runs as kb_wy2_tc (point pairs sharing the B operand).  DRAM bytes
-        # of one launch would come from an ncu capture of this kernel at this shape; the last
-        # capture (770.7 MB per launch) predates a change to the kernel's shared-memory
-        # declaration, so none is reported until the kernel is captured again
-        wy_traffic = None
-        wy_obj = {"bound": "tensor" if tensor else "alu",
-                  "kernel": ("kb_wy2_tc (tcgen05 kind::tf32, hi/lo split, point pairs share the B operand)"
-                             if tensor else
-                             f"kb_wy<{'float' if prec == pw.MIXED_FP32 else 'double'}>"),
-                  "achieved": wy_ach, "peak": wy_peak, "unit": "TFLOP/s", "frac": wy_ach / wy_peak,
-                  "traffic": wy_traffic,
-                  "peak_source": ("of measured: bf16 burst x 1.1/2.25 (nominal TF32/BF16) / 3 products"
-                                  if tensor else
-                                  "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz"
-                                  if prec == pw.MIXED_FP32 else "FP64 nominal 1.25 TFLOP/s"),
-                  "avg_launch_ms": wy_ms, "total_ms": prof["wy_ms"]}
-        dominant, other = ((heev_obj, wy_obj) if prof["modes_ms"] >= prof["wy_ms"] else (wy_obj, heev_obj))
+        tf32_split = (peaks.get("bf16_tflops") or 1900.0) * (1.1 / 2.25) / 3.0
+        esz = 8 if prec == pw.MIXED_FP32 else 16
+        nc = max(4, ((int(nopen_last[:, 0].max()) + 3) // 4) * 4) if len(nopen_last) else 4
+        rows = kernel_table(kprof, args.steps)
+        model = sweep_kind_totals(n, nc, n_e, N, tensor, esz)
+
+        def roof(row):
+            key = row["kernel"].split(" ")[0]
+            flops, nbytes = model.get(key, (None, None))
+            tsec = row["ms_per_step"] / 1e3
+            obj = {"kernel": row["kernel"], "avg_launch_ms": row["avg_launch_ms"],
+                   "launches_per_step": row["launches_per_step"], "ms_per_step": row["ms_per_step"],
+                   "share_of_kernel_time": row["share"], "traffic": KERNEL_TRAFFIC.get(key)}
+            if flops is None or tsec <= 0:
+                obj.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                            "note": "no algorithmic model for this kernel"})
+                return obj
+            on_tc = tensor and key in ("kb_wy", "kb_trail", "kb_bsupd", "kb_fsupd_tc")
+            cpeak = tf32_split if on_tc else (fp32_peak if prec == pw.MIXED_FP32 else fp64_peak)
+            csrc = ("of measured: bf16 burst x 1.1/2.25 (nominal TF32/BF16) / 3 products" if on_tc else
+                    "of measured: FP32 FMA microbenchmark (pw_measure_peaks)" if prec == pw.MIXED_FP32 else
+                    "of measured: FP64 microbenchmark, the faster of DFMA and DMMA (pw_measure_peaks)")
+            ai = flops / nbytes if nbytes else None
+            if ai is not None and ai * hbm / 1e3 < cpeak:
+                ach = nbytes / tsec / 1e9
+                obj.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                            "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
+                            "algorithmic_bytes_per_launch": nbytes / (row["launches_per_step"] or 1),
+                            "tflops": flops / tsec / 1e12, "intensity_flop_per_byte": ai})
+            else:
+                ach = flops / tsec / 1e12
+                obj.update({"bound": "tensor" if on_tc else "alu", "achieved": ach, "peak": cpeak,
+                            "unit": "TFLOP/s", "frac": ach / cpeak, "peak_source": csrc,
+                            "algorithmic_flops_per_launch": flops / (row["launches_per_step"] or 1)})
+            return obj
+
+        dominant = roof(rows[0]) if rows else None
+        runner_up = roof(rows[1]) if len(rows) > 1 else None
+        speedup = (value / fp64_arm["value"]) if fp64_arm else None
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64" if prec == pw.MIXED_FP32 else "c128", "data": "synthetic",
-            "config": dict(workload_config(args.config, n, N, n_e, n_k, world), precision=args.precision),
+            "config": dict(workload_config(args.config, n, N, n_e, n_k, world), precision=args.precision,
+                           sweep_variant=variant),
             "roofline": dominant,
-            "roofline_next": other,
+            "roofline_next": runner_up,
+            "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows[:12]],
             "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
                           "overlaps": prof["overlap_ms"], "refine": prof["refine_ms"]},
+            "fp64_gpu": fp64_arm,
+            "speedup_vs_fp64": speedup,
+            "measured_peaks_tflops": own or None,
             "accuracy": {"refine_passes_per_step": (prof["refine_stages"] / max(args.steps, 1)
                                                     if prec == pw.MIXED_FP32 else 0),
                          "err_est_max_last_step": err_max,
-                         "vs_fp64_gpu_sample": accuracy_vs_fp64,
+                         "vs_oracle": accuracy_vs_oracle,
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,
-            "gpu_launches": int(prof["sweep_launches"] + modes_launches * prof["modes_stages"]
-                                + (refine_launches(N, prof["refine_stages"] / max(args.steps, 1),
-                                                   sliced=(n <= 512 and n % 4 == 0))
-                                   * args.steps if prec == pw.MIXED_FP32 else 0)),
+            "gpu_launches": int(sum(c for (_, _, c) in kprof.values())),
             "e2e": (None if args.no_e2e else
                     {"value": e2e_value, "unit": "points/s",
                      "h2d_bytes_per_step": n_e * 32,

@@ -52,11 +52,15 @@ typedef enum {
 
 typedef struct { double re, im; } pw_c128;
 
-/* Arithmetic of the star-product sweep.  PW_FP64: every step in FP64.
- * PW_MIXED_FP32: the sweep in FP32, then passes of iterative refinement of
- * the whole interface-matching system with FP64 residuals until the estimated
- * remaining error of t falls below 1e-9 relative (the eigenmodes and overlaps
- * are FP64 in both forms). */
+/* Arithmetic of the path.  PW_FP64: every step in FP64.  PW_MIXED_FP32: the
+ * slice eigenmodes and the overlaps in double-float (a value is the sum of two
+ * FP32 numbers, 48 significant bits, on the FP32 pipe), the star-product sweep
+ * in FP32 (its GEMMs on the tensor cores as TF32 hi/lo products), then passes
+ * of iterative refinement of the whole interface-matching system whose
+ * residuals are formed in double-float (exact BF16 slice products on the
+ * tensor cores when all points of a launch share one k_par and N_G is a
+ * multiple of 4 up to 512) until the estimated remaining error of t falls
+ * below 1e-9 relative; T and t are accumulated in FP64. */
 enum { PW_FP64 = 0, PW_MIXED_FP32 = 1 };
 
 /*
@@ -257,10 +261,28 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
  *               by -/+ i (d^T Gd c' - d'^T Gd c), Gd = diag(G.delta), minus at
  *               the left contact and plus at the right one; that jump takes
  *               the place of the slice integral.
- * Synchronises the context's stream.  Device memory: about
- * (N+1)(n^2 + n n_c) + 4 (N+2) n n_c complex doubles per point of a batch. */
+ * The sweeps are recomputed in segments of C interfaces (pw_set_grad_checkpoint,
+ * default C = ceil(sqrt(N+1))): a first pass keeps only the sweep state (the
+ * accumulated S12 and the S11 columns) at the start of every segment; the
+ * backward pass then takes the segments from the right, recomputing each
+ * one's interfaces with their stores (Z_p, u_p) before stepping through it.
+ * Synchronises the context's stream.  Device memory per point of a batch, in
+ * complex doubles: (ceil((N+1)/C) - 1 + C)(n^2 + n n_c) for the checkpoints
+ * and one segment's stores (about 2 sqrt(N+1) n^2), plus 4 (N+2) n n_c for
+ * the amplitudes of both problems, plus the sweep's own n^2 + n (2n + n_c). */
 pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, const double *weight,
                   double *sumT_host, double *dV0_host, double *dgap_host);
+
+/* Segment length C of pw_grad's checkpointed recomputation: 0 (the default)
+ * takes C = ceil(sqrt(N+1)); C >= N+1 stores every interface in one pass (no
+ * recomputation).  PW_EINVAL for interval < 0.  The paper has no adjoint;
+ * this is a memory/compute trade-off of pw_grad only (results are the same). */
+pw_status pw_set_grad_checkpoint(pw_ctx *ctx, int interval);
+
+/* Bytes of device memory the context's per-call workspaces hold now (the
+ * buffers grown by pw_transmission, pw_grad and the mode stage; not the
+ * per-k_par mode cache set up by pw_setup), into *bytes. */
+pw_status pw_workspace_bytes(const pw_ctx *ctx, double *bytes);
 
 /* The star product of pw_compose for callers that must not allocate device
  * memory at all (no context, no cudaMalloc): for instance code running inside
@@ -307,6 +329,20 @@ pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant);
  * [W|Y] GEMM ms, [W|Y] GEMM launches}; reset != 0 clears the records. */
 pw_status pw_set_profiling(pw_ctx *ctx, int enable);
 pw_status pw_get_profile(pw_ctx *ctx, double *out, int reset);
+
+/* Per-kernel launch timing, gathered while profiling is on (enable >= 1 in
+ * pw_set_profiling; enable = k brackets every k-th launch of each kernel kind
+ * with CUDA events on the stream that kernel is launched on, and counts every
+ * launch).  Kinds are numbered 0 .. pw_kernel_kinds()-1 and named by
+ * pw_kernel_kind_name (a static string: the kernel, or the kernels that share
+ * a role).  pw_get_kernel_profile synchronises the context's stream and
+ * writes, for each kind k, out[3k] = summed ms of its timed launches,
+ * out[3k+1] = its timed launches, out[3k+2] = all its launches; reset != 0
+ * clears the counts.  Timing covers pw_transmission, pw_transmission_doubling
+ * and pw_grad; the paper has no counterpart (measurement only). */
+int pw_kernel_kinds(void);
+const char *pw_kernel_kind_name(int kind);
+pw_status pw_get_kernel_profile(pw_ctx *ctx, double *out, int reset);
 
 /* Uneven batches: many independent problems, each with its own cell, basis
  * size N_G, slicing and potential, evaluated at one (E, k_par) point each.
@@ -386,6 +422,15 @@ pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, doub
  * synchronises it; PW_ETIMEOUT if the tensor core did not signal completion
  * within its bounded wait.  A deployment check with no counterpart in the paper. */
 pw_status pw_selftest_f16_split(double *rel_err);
+
+/* Measured arithmetic peaks of the current device, in TFLOP/s:
+ * tflops[0] = FP64 FMA on the SIMT pipe (DFMA), tflops[1] = the warp-level FP64
+ * MMA (mma.sync m8n8k4, the FP64 tensor path sm_103a offers), tflops[2] = FP32
+ * FMA.  Each is timed with CUDA events over a few tens of milliseconds of
+ * independent FMA (or MMA) chains on every SM.  Allocates a small output
+ * buffer, synchronises the device; the paper has no counterpart (these are the
+ * roofline denominators of the FP64 form and of the double-float kernels). */
+pw_status pw_measure_peaks(double *tflops);
 
 #ifdef __cplusplus
 }

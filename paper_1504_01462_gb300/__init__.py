@@ -35,7 +35,9 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_transmission_batch", "pw_batch_set_options", "pw_batch_get_stats",
            "pw_batch_destroy", "pw_get_error_detail", "pw_selftest_tensor_core",
            "pw_set_sweep_variant", "pw_selftest_slice_product", "pw_slice_mixed", "pw_compose_mixed",
-           "pw_transmission_doubling", "pw_selftest_f16_split"]
+           "pw_transmission_doubling", "pw_selftest_f16_split", "pw_kernel_kinds",
+           "pw_kernel_kind_name", "pw_get_kernel_profile", "pw_measure_peaks",
+           "pw_set_grad_checkpoint", "pw_workspace_bytes"]
 
 
 class PwError(RuntimeError):
@@ -105,6 +107,13 @@ def _load():
                                               ctypes.POINTER(ctypes.c_longlong), _dp]
     lib.pw_selftest_f16_split.argtypes = [_dp]
     lib.pw_set_sweep_variant.argtypes = [_vp, ctypes.c_int]
+    lib.pw_kernel_kinds.argtypes = []
+    lib.pw_kernel_kind_name.argtypes = [ctypes.c_int]
+    lib.pw_kernel_kind_name.restype = ctypes.c_char_p
+    lib.pw_get_kernel_profile.argtypes = [_vp, _dp, ctypes.c_int]
+    lib.pw_measure_peaks.argtypes = [_dp]
+    lib.pw_set_grad_checkpoint.argtypes = [_vp, ctypes.c_int]
+    lib.pw_workspace_bytes.argtypes = [_vp, _dp]
     lib.pw_batch_destroy.restype = None
     return lib
 
@@ -243,6 +252,13 @@ def selftest_f16_split():
     a = np.zeros(1)
     _check_status(_lib.pw_selftest_f16_split(_as_dp(a)), "pw_selftest_f16_split")
     return float(a[0])
+
+
+def measure_peaks():
+    """Measured TFLOP/s of the current device: {'fp64_fma', 'fp64_mma', 'fp32_fma'}."""
+    out = np.zeros(3)
+    _check_status(_lib.pw_measure_peaks(_as_dp(out)), "pw_measure_peaks")
+    return {"fp64_fma": float(out[0]), "fp64_mma": float(out[1]), "fp32_fma": float(out[2])}
 
 
 def _check_status(st, where):
@@ -392,8 +408,30 @@ class Context:
         on the tcgen05 tensor cores (mixed form only)."""
         self._check(_lib.pw_set_sweep_variant(self._h, int(variant)), "pw_set_sweep_variant")
 
-    def set_profiling(self, on=True):
-        self._check(_lib.pw_set_profiling(self._h, int(bool(on))), "pw_set_profiling")
+    def set_profiling(self, on=True, stride=1):
+        """Stage and per-kernel launch timing; with `stride` k every k-th
+        launch of each kernel kind is bracketed by CUDA events."""
+        self._check(_lib.pw_set_profiling(self._h, max(1, int(stride)) if on else 0), "pw_set_profiling")
+
+    def set_grad_checkpoint(self, interval=0):
+        """Segment length of pw_grad's checkpointed recomputation (0: ceil(sqrt(N+1)))."""
+        self._check(_lib.pw_set_grad_checkpoint(self._h, int(interval)), "pw_set_grad_checkpoint")
+
+    def workspace_bytes(self):
+        """Device bytes the context's per-call workspaces hold now."""
+        out = np.zeros(1)
+        self._check(_lib.pw_workspace_bytes(self._h, _as_dp(out)), "pw_workspace_bytes")
+        return float(out[0])
+
+    def get_kernel_profile(self, reset=True):
+        """{kernel kind: (sampled ms, sampled launches, all launches)} since the
+        last reset, for every kind that launched."""
+        nk = _lib.pw_kernel_kinds()
+        out = np.zeros(3 * nk)
+        self._check(_lib.pw_get_kernel_profile(self._h, _as_dp(out), int(bool(reset))),
+                    "pw_get_kernel_profile")
+        return {_lib.pw_kernel_kind_name(k).decode(): (out[3 * k], int(out[3 * k + 1]), int(out[3 * k + 2]))
+                for k in range(nk) if out[3 * k + 2] > 0}
 
     def get_profile(self, reset=True):
         """{'sweep_ms', 'sweep_launches', 'modes_ms', 'modes_stages', 'overlap_ms',

@@ -16,6 +16,92 @@
 
 using pw::PointDesc;
 
+namespace pw {
+
+const char *kernel_kind_name(int kind) {
+  static const char *names[KK_COUNT] = {
+      "kb_vectors", "kb_wy ([W|Y] product: kb_wy, kb_wy_tc, kb_wy2_tc or kb_wy2_tc16)", "kb_rowexp",
+      "kb_panel", "kb_panel_apply", "kb_trail (kb_trail or kb_trail_tc)", "kb_rhs_perm", "kb_fsdiag_big",
+      "kb_fsupd_tc", "kb_bsdiag (kb_bsdiag or kb_bsdiag_big)", "kb_bsupd (kb_bsupd or kb_bsupd_tc)",
+      "kb_finish",
+      "k_refine_init", "k_refine_residual", "k_res_oslice", "k_res_yslice", "k_res_mm", "k_res_finish",
+      "k_refine_fwd_a", "k_refine_fwd_b", "k_refine_bwd_a", "k_refine_bwd_b", "k_refine_bwd_mm",
+      "k_refine_bwd_c", "k_refine_finish",
+      "k_tables", "k_assemble_h", "k_heev (k_heev<double>, or the reduction of k_heev<df>)", "k_ql_df",
+      "k_rot_apply", "k_backtransform", "k_eig_sort", "k_overlaps", "k_o32", "k_o32t"};
+  return (kind >= 0 && kind < KK_COUNT) ? names[kind] : "";
+}
+
+// Launch counts and sampled event pairs of one context (pw_set_profiling).
+struct KernelTimer {
+  int stride = 1;                      // every stride-th launch of a kind is timed
+  long long launches[KK_COUNT] = {};
+  long long sampled[KK_COUNT] = {};
+  double ms[KK_COUNT] = {};
+  struct Rec { cudaEvent_t a, b; int kind; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // adds the elapsed times of every recorded pair (each waited for) to ms
+  cudaError_t flush() {
+    cudaError_t first = cudaSuccess;
+    for (auto &r : recs) {
+      float t = 0.f;
+      cudaError_t e = cudaEventSynchronize(r.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+      if (e == cudaSuccess) {
+        ms[r.kind] += t;
+        sampled[r.kind] += 1;
+      } else if (first == cudaSuccess) {
+        first = e;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+    return first;
+  }
+  void reset() {
+    for (int k = 0; k < KK_COUNT; ++k) { launches[k] = 0; sampled[k] = 0; ms[k] = 0.0; }
+  }
+  ~KernelTimer() {
+    for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+thread_local KernelTimer *g_ktimer = nullptr;
+
+cudaEvent_t kt_begin(int kind, cudaStream_t s) {
+  KernelTimer *t = g_ktimer;
+  if (!t || kind < 0 || kind >= KK_COUNT) return nullptr;
+  const long long c = t->launches[kind]++;
+  if (c % t->stride) return nullptr;
+  cudaEvent_t e = t->take();
+  if (e) cudaEventRecord(e, s);
+  return e;
+}
+
+void kt_end(int kind, cudaEvent_t begin, cudaStream_t s) {
+  KernelTimer *t = g_ktimer;
+  if (!t || !begin) return;
+  cudaEvent_t e = t->take();
+  if (!e) return;
+  cudaEventRecord(e, s);
+  t->recs.push_back({begin, e, kind});
+}
+
+}  // namespace pw
+
 
 namespace {
 
@@ -84,6 +170,9 @@ struct pw_ctx {
   bool profiling = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> event_pool;
+  pw::KernelTimer *kt = nullptr;   // per-kernel launch timing (profiling only)
+  int grad_interval = 0;           // pw_grad checkpoint interval (0: ceil(sqrt(N+1)))
+  DevBuf ckR, ckT;                 // pw_grad checkpoints of the sweep state (R, Tacc)
 };
 
 namespace {
@@ -117,6 +206,24 @@ struct Stage {
     c->recs.push_back({a, b, kind, count});
     a = nullptr;
   }
+};
+
+// Interface count C of pw_grad's recomputed segments.
+int grad_interval_of(const pw_ctx *c) {
+  const int ni = c->N + 1;
+  if (c->grad_interval > 0) return std::min(c->grad_interval, ni);
+  int C = (int)ceil(sqrt((double)ni));
+  return std::max(1, std::min(C, ni));
+}
+
+// Installs the context's kernel timer on this host thread for the duration of
+// a profiled call (nothing when profiling is off).
+struct KtScope {
+  pw::KernelTimer *prev;
+  explicit KtScope(pw_ctx *c) : prev(pw::g_ktimer) {
+    if (c && c->profiling && c->kt) pw::g_ktimer = c->kt;
+  }
+  ~KtScope() { pw::g_ktimer = prev; }
 };
 
 pw_status latch(pw_ctx *c, pw_status s) {
@@ -548,11 +655,12 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
-                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p};
+                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p, ctx->ckR.p, ctx->ckT.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx->kt;
   delete ctx;
 }
 
@@ -563,8 +671,32 @@ pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant) {
 }
 
 pw_status pw_set_profiling(pw_ctx *ctx, int enable) {
-  if (!ctx) return PW_EINVAL;
+  if (!ctx || enable < 0) return PW_EINVAL;
   ctx->profiling = enable != 0;
+  if (enable) {
+    if (!ctx->kt) ctx->kt = new (std::nothrow) pw::KernelTimer;
+    if (!ctx->kt) return PW_ENOMEM;
+    ctx->kt->stride = enable;
+  }
+  return PW_OK;
+}
+
+int pw_kernel_kinds(void) { return pw::KK_COUNT; }
+
+const char *pw_kernel_kind_name(int kind) { return pw::kernel_kind_name(kind); }
+
+pw_status pw_get_kernel_profile(pw_ctx *ctx, double *out, int reset) {
+  if (!ctx || !out) return PW_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < pw::KK_COUNT; ++k) out[3 * k] = out[3 * k + 1] = out[3 * k + 2] = 0.0;
+  if (!ctx->kt) return PW_OK;
+  CK(ctx->kt->flush());
+  for (int k = 0; k < pw::KK_COUNT; ++k) {
+    out[3 * k] = ctx->kt->ms[k];
+    out[3 * k + 1] = (double)ctx->kt->sampled[k];
+    out[3 * k + 2] = (double)ctx->kt->launches[k];
+  }
+  if (reset) ctx->kt->reset();
   return PW_OK;
 }
 
@@ -740,6 +872,7 @@ pw_status pw_transmission_doubling(pw_ctx *ctx, int npts, const double *E, const
                                    double cond_max, double *T_dev, int *levels_host) {
   if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev)) || !(cond_max > 0.0)) return PW_EINVAL;
   if (ctx->err) return ctx->err;
+  KtScope kts(ctx);
   const int n = ctx->n, N = ctx->N, nblk = N + 1;
   const size_t nn = (size_t)n * n, blk = 4 * nn;
   const int cap = std::max(1, 2 * ctx->num_sms);   // CTAs per launch (bounds the work buffers)
@@ -857,6 +990,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
                           pw_c128 *t_dev, int *nopen_dev, double *err_dev) {
   if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev))) return PW_EINVAL;
   if (ctx->err) return ctx->err;
+  KtScope kts(ctx);
   const int n = ctx->n;
   const size_t nn = (size_t)n * n;
   const size_t esz = ctx->precision == PW_FP64 ? sizeof(zc) : sizeof(cc);
@@ -1041,6 +1175,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       std::vector<int> st_h(nb);
       CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
+      if (ctx->profiling && ctx->kt) CK(ctx->kt->flush());   // keeps the pending event pairs bounded
       for (int v : st_h) {
         if (v == 2) result = PW_ETIMEOUT;   // a tensor-core wait ran out (kept over a zero pivot)
         else if (v && result != PW_ETIMEOUT) result = PW_ESINGULAR;
@@ -1052,10 +1187,31 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
 }
 
 
+pw_status pw_set_grad_checkpoint(pw_ctx *ctx, int interval) {
+  if (!ctx || interval < 0) return PW_EINVAL;
+  ctx->grad_interval = interval;
+  return PW_OK;
+}
+
+pw_status pw_workspace_bytes(const pw_ctx *ctx, double *bytes) {
+  if (!ctx || !bytes) return PW_EINVAL;
+  const DevBuf *b[] = {&ctx->R, &ctx->M, &ctx->piv, &ctx->pts, &ctx->status, &ctx->work, &ctx->KV,
+                       &ctx->rowexp, &ctx->Zst, &ctx->Ust, &ctx->LUst, &ctx->PIVst, &ctx->Xa, &ctx->Xb,
+                       &ctx->Fr, &ctx->Gr, &ctx->carry, &ctx->tmp, &ctx->Xa_m, &ctx->Xb_m, &ctx->status_m,
+                       &ctx->Tg, &ctx->Gam, &ctx->gtab, &ctx->T1, &ctx->dV0, &ctx->wgt, &ctx->corr,
+                       &ctx->eigws, &ctx->bw, &ctx->dshift, &ctx->lead_scr, &ctx->lead_out, &ctx->ckR,
+                       &ctx->ckT};
+  double t = 0.0;
+  for (const DevBuf *x : b) t += (double)x->bytes;
+  *bytes = t;
+  return PW_OK;
+}
+
 pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, const double *weight,
                   double *sumT_host, double *dV0_host, double *dgap_host) {
   if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar)) || !sumT_host) return PW_EINVAL;
   if (ctx->err) return ctx->err;
+  KtScope kts(ctx);
   if (dgap_host && !ctx->has_shift) return PW_EINVAL;   // no geometry motion was given
   if (dV0_host && ctx->n_wells == 0) return PW_EINVAL;   // explicit tables have no wells
   const bool lead_shift = dgap_host && (ctx->lead_rate[0][0] != 0.0 || ctx->lead_rate[0][1] != 0.0 ||
@@ -1100,14 +1256,22 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
     nc = (nc + 3) & ~3;
     const int ncols = 2 * n + nc;
     const size_t vec = (size_t)n * nc;
-    // per point: FP64 sweep buffers, the stored Z_p and u_p, amplitudes of both problems
+    // checkpointed recomputation: the sweep state (R, Tacc) is kept at the start
+    // of every segment of C interfaces, and Z_p, u_p only for the C interfaces of
+    // the segment being recomputed, so the stores grow as (ceil((N+1)/C) - 1 + C)
+    // (n^2 + n nc), about 2 sqrt(N+1) (n^2 + n nc) for C = ceil(sqrt(N+1))
+    const int C = grad_interval_of(ctx);
+    const int K = (N + 1 + C - 1) / C;   // segments
+    // per point: FP64 sweep buffers, the stores of one segment, the checkpoints,
+    // amplitudes of both problems
     const size_t per_pt = (nn + (size_t)n * ncols + 3 * (size_t)n) * sizeof(zc) + n * sizeof(int) +
-                          (size_t)(N + 1) * (nn + vec) * sizeof(zc) + 4 * (size_t)(N + 2) * vec * sizeof(zc) +
-                          3 * vec * sizeof(zc) + 64;
+                          (size_t)C * (nn + vec) * sizeof(zc) + (size_t)(K - 1) * (nn + vec) * sizeof(zc) +
+                          4 * (size_t)(N + 2) * vec * sizeof(zc) + 3 * vec * sizeof(zc) + 64;
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     const size_t have = free_b + ctx->R.bytes + ctx->M.bytes + ctx->Zst.bytes + ctx->Ust.bytes +
-                        ctx->Xa.bytes + ctx->Xb.bytes + ctx->Xa_m.bytes + ctx->Xb_m.bytes;
+                        ctx->Xa.bytes + ctx->Xb.bytes + ctx->Xa_m.bytes + ctx->Xb_m.bytes + ctx->ckR.bytes +
+                        ctx->ckT.bytes;
     const int fit = (int)std::max<size_t>(1, (size_t)(0.8 * (double)have) / per_pt);
     const int bmax = std::max(1, std::min({(int)pts.size(), 3 * ctx->num_sms, fit}));
     for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
@@ -1127,8 +1291,10 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
           (st = ensure(ctx, ctx->pts, (size_t)2 * nb * sizeof(PointDesc))) ||
           (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))) ||
           (st = ensure(ctx, ctx->status_m, (size_t)nb * sizeof(int))) ||
-          (st = ensure(ctx, ctx->Zst, (size_t)nb * (N + 1) * nn * sizeof(zc))) ||
-          (st = ensure(ctx, ctx->Ust, (size_t)nb * (N + 1) * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Zst, (size_t)nb * C * nn * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Ust, (size_t)nb * C * vec * sizeof(zc))) ||
+          (K > 1 && (st = ensure(ctx, ctx->ckR, (size_t)(K - 1) * nb * nn * sizeof(zc)))) ||
+          (K > 1 && (st = ensure(ctx, ctx->ckT, (size_t)(K - 1) * nb * vec * sizeof(zc)))) ||
           (st = ensure(ctx, ctx->Xa, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
           (st = ensure(ctx, ctx->Xb, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
           (st = ensure(ctx, ctx->Xa_m, (size_t)nb * (N + 2) * vec * sizeof(zc))) ||
@@ -1151,6 +1317,8 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
       CK(cudaMemcpyAsync(d_pd, pd_local.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
       CK(cudaMemcpyAsync(d_pm, pm_local.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
       for (int mirror = 0; mirror < 2; ++mirror) {
+        std::vector<PointDesc> &loc = mirror ? pm_local : pd_local;
+        PointDesc *d_loc = mirror ? d_pm : d_pd;
         pw::SweepArgs a;
         memset(&a, 0, sizeof(a));
         a.pts = mirror ? d_pm : d_pd;
@@ -1170,7 +1338,26 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
         a.KV = ctx->KV.p;
         a.mirror = mirror;
         CK(pw::prepare_sweep_batched(n, PW_FP64, 0));
-        for (int p = 0; p <= N; ++p) CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream));
+        zc *Rb = (zc *)ctx->R.p, *Mb = (zc *)ctx->M.p;
+        zc *ckR = (zc *)ctx->ckR.p, *ckT = (zc *)ctx->ckT.p;
+        if (K > 1) {
+          // first pass: the whole sweep without stores, keeping the state
+          // (R, Tacc) before the first interface of every later segment
+          pw::SweepArgs a0 = a;
+          a0.Zst = nullptr;
+          a0.Ust = nullptr;
+          for (int p = 0; p <= N; ++p) {
+            CK(pw::launch_sweep_batched(a0, nb, p, PW_FP64, ctx->stream));
+            if ((p + 1) % C == 0 && p < N) {
+              const int k = (p + 1) / C - 1;
+              CK(cudaMemcpyAsync(ckR + (size_t)k * nb * nn, Rb, (size_t)nb * nn * sizeof(zc),
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+              CK(cudaMemcpy2DAsync(ckT + (size_t)k * nb * vec, vec * sizeof(zc), Mb + 2 * nn,
+                                   (size_t)n * ncols * sizeof(zc), vec * sizeof(zc), nb,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+            }
+          }
+        }
         pw::GradArgs g;
         g.pts = a.pts;
         g.En = ctx->d_En;
@@ -1187,7 +1374,22 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
         g.N = N;
         g.nc = nc;
         g.mirror = mirror;
-        CK(pw::launch_grad_backward(g, nb, ctx->stream));
+        // segments from the right: restore the state at the segment's start,
+        // recompute its interfaces with stores (slots st_off + p = i C + p - p0),
+        // then the backward pass over them (the carry links the segments)
+        for (int k = K - 1; k >= 0; --k) {
+          const int p0 = k * C, p1 = std::min(N, p0 + C - 1);
+          for (int i = 0; i < nb; ++i) loc[i].st_off = (long long)i * C - p0;
+          CK(cudaMemcpyAsync(d_loc, loc.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+          if (k > 0) {
+            CK(cudaMemcpyAsync(Rb, ckR + (size_t)(k - 1) * nb * nn, (size_t)nb * nn * sizeof(zc),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpy2DAsync(Mb + 2 * nn, (size_t)n * ncols * sizeof(zc), ckT + (size_t)(k - 1) * nb * vec,
+                                 vec * sizeof(zc), vec * sizeof(zc), nb, cudaMemcpyDeviceToDevice, ctx->stream));
+          }
+          for (int p = p0; p <= p1; ++p) CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream));
+          CK(pw::launch_grad_backward(g, nb, ctx->stream, p1, p0, k == K - 1));
+        }
       }
       pw::GammaArgs h;
       h.pts = d_pd;

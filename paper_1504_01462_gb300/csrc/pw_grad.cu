@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(GT) k_grad_backward(GradArgs g, int p) {
   __syncthreads();
   const zc *O = g.O + ((size_t)d.kset * (N + 1) + (g.mirror ? N - p : p)) * n * n;
   const bool tr = g.mirror != 0;
-  const zc *Z = g.Zst + ((size_t)pt * (N + 1) + p) * n * n;
-  const zc *U = g.Ust + ((size_t)pt * (N + 1) + p) * n * nc;
+  // the stores of interface p (a point's slot st_off + p: every interface, or
+  // the interfaces of the segment being recomputed)
+  const zc *Z = g.Zst + (size_t)(d.st_off + p) * n * n;
+  const zc *U = g.Ust + (size_t)(d.st_off + p) * n * nc;
   zc *carry = g.carry + (size_t)pt * n * nc;
   zc *tmp = g.tmp + (size_t)pt * 2 * n * nc;
   for (int e = threadIdx.x; e < n * nc; e += GT) {
@@ -387,17 +389,19 @@ __global__ void __launch_bounds__(GT) k_grad_leads(GammaArgs h, const zc *U_all,
   }
 }
 
-cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s) {
+cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s, int p_hi, int p_lo, bool init) {
   const size_t smem = skinny_smem_elems<double>() * sizeof(zc) + 3 * (size_t)g.n * sizeof(zc);
   cudaError_t e = cudaFuncSetAttribute(k_grad_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e) return e;
-  const size_t vec = (size_t)npts * g.n * g.nc * sizeof(zc);
-  if ((e = cudaMemsetAsync(g.Xa, 0, vec * (g.N + 2), s)) || (e = cudaMemsetAsync(g.Xb, 0, vec * (g.N + 2), s)) ||
-      (e = cudaMemsetAsync(g.carry, 0, vec, s)))
-    return e;
-  k_grad_init<<<npts, GT, 0, s>>>(g);
-  for (int p = g.N; p >= 0; --p) k_grad_backward<<<npts, GT, smem, s>>>(g, p);
+  if (init) {
+    const size_t vec = (size_t)npts * g.n * g.nc * sizeof(zc);
+    if ((e = cudaMemsetAsync(g.Xa, 0, vec * (g.N + 2), s)) || (e = cudaMemsetAsync(g.Xb, 0, vec * (g.N + 2), s)) ||
+        (e = cudaMemsetAsync(g.carry, 0, vec, s)))
+      return e;
+    k_grad_init<<<npts, GT, 0, s>>>(g);
+  }
+  for (int p = p_hi; p >= p_lo; --p) k_grad_backward<<<npts, GT, smem, s>>>(g, p);
   return cudaGetLastError();
 }
 

@@ -191,7 +191,10 @@ struct GammaArgs {
   int n, N, nc, npts;
 };
 
-cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s);
+// backward pass over interfaces p_hi down to p_lo (init: clear the amplitudes
+// and the carry and set the incident a_0 first; the carry links calls that
+// cover consecutive ranges from the right)
+cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s, int p_hi, int p_lo, bool init);
 cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, cudaStream_t s);
 cudaError_t launch_grad_fold(const GammaArgs &h, int slot, const zc *U, zc *T1, const int *mn, int Dm,
                              int Dn, cudaStream_t s);
@@ -278,6 +281,35 @@ struct CtxView {
   cudaStream_t stream;
 };
 CtxView ctx_view(const pw_ctx *c);
+
+// ---------------------------------------------------------------------------
+// Per-kernel launch timing (pw_set_profiling).  While a profiled call runs on
+// this host thread, g_ktimer points at the context's timer: every launch site
+// below counts its launches by kind, and every `stride`-th launch of a kind is
+// bracketed by CUDA events on the stream it is launched on.  With no timer set
+// (the default, and inside every stream capture) the sites cost one test.
+// ---------------------------------------------------------------------------
+enum KernelKind : int {
+  KK_VECTORS, KK_WY, KK_ROWEXP, KK_PANEL, KK_PANEL_APPLY, KK_TRAIL, KK_RHS_PERM, KK_FSDIAG, KK_FSUPD,
+  KK_BSDIAG, KK_BSUPD, KK_FINISH,
+  KK_REF_INIT, KK_REF_RESIDUAL, KK_RES_OSLICE, KK_RES_YSLICE, KK_RES_MM, KK_RES_FINISH, KK_REF_FWD_A,
+  KK_REF_FWD_B, KK_REF_BWD_A, KK_REF_BWD_B, KK_REF_BWD_MM, KK_REF_BWD_C, KK_REF_FINISH,
+  KK_TABLES, KK_ASSEMBLE, KK_HEEV, KK_QL, KK_ROT, KK_BACKT, KK_SORT, KK_OVERLAPS, KK_O32, KK_O32T,
+  KK_COUNT
+};
+const char *kernel_kind_name(int kind);
+struct KernelTimer;
+extern thread_local KernelTimer *g_ktimer;
+// counts the launch; returns an event recorded on s when this launch is sampled
+cudaEvent_t kt_begin(int kind, cudaStream_t s);
+void kt_end(int kind, cudaEvent_t begin, cudaStream_t s);
+// runs the launch statement(s) as one timed launch of `kind` on stream s
+#define PW_TIMED(kind, s, ...)                                                                 \
+  do {                                                                                         \
+    const cudaEvent_t pw_kt_a_ = ::pw::g_ktimer ? ::pw::kt_begin((kind), (s)) : nullptr;        \
+    __VA_ARGS__;                                                                               \
+    if (::pw::g_ktimer) ::pw::kt_end((kind), pw_kt_a_, (s));                                    \
+  } while (0)
 
 constexpr double kThresholdRy = 1e-10;     // electrode channel at threshold
 constexpr double kRefineTolRel = 1e-9;     // refinement stops below this estimated error of t

@@ -4,7 +4,12 @@
 //   k_tables      V^p(dG) of Gaussian wells averaged over each slice (Sec. II A:
 //                 the slice potential is taken z-independent inside a slice)
 //   k_assemble_h  H_p(G,G') = |k+G|^2 delta + V^p(G-G')          (Eq. loc)
-//   k_jacobi_eig  eigenpairs (E_n^p, phi_n^p) of every H_p       (Eq. loc / A8)
+//   k_heev        eigenpairs (E_n^p, phi_n^p) of every H_p       (Eq. loc / A8):
+//                 Householder tridiagonalisation, implicit QL, back-
+//                 transformation; the mixed form runs the same steps in
+//                 double-float as five launches (k_heev<df> reduction,
+//                 k_ql_df, k_rot_apply, k_backtransform, k_eig_sort)
+//   k_jacobi      a second, independent solver (cyclic two-sided Jacobi)
 //   k_overlaps    O_p = U_p^H U_{p+1} = sum_s (M^{p+1}_{js})^* M^p_{ns}
 //                 of App. A Eq. transfer
 #include <math.h>
@@ -74,7 +79,7 @@ __global__ void k_tables(TableArgs a) {
 void launch_tables(const TableArgs &a, cudaStream_t s) {
   const int tsz = (2 * a.Dm + 1) * (2 * a.Dn + 1);
   dim3 grid((tsz + 255) / 256, a.nq);
-  k_tables<<<grid, 256, 0, s>>>(a);
+  PW_TIMED(KK_TABLES, s, k_tables<<<grid, 256, 0, s>>>(a));
 }
 
 // ---------------------------------------------------------------------------
@@ -101,7 +106,7 @@ __global__ void k_assemble_h(zc *H, const zc *tab, const int *mn, const double *
 void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, double kx, double ky,
                        int n, int nq, int Dm, int Dn, cudaStream_t s) {
   dim3 grid((unsigned)(((size_t)n * n + 255) / 256), nq);
-  k_assemble_h<<<grid, 256, 0, s>>>(H, tab, mn, G, kx, ky, n, Dm, Dn);
+  PW_TIMED(KK_ASSEMBLE, s, k_assemble_h<<<grid, 256, 0, s>>>(H, tab, mn, G, kx, ky, n, Dm, Dn));
 }
 
 // ---------------------------------------------------------------------------
@@ -1125,7 +1130,7 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
       while (group > 0 && heev_ws_bytes(n, group) > ws_bytes) group = std::max(0, group - std::max(1, group / 8));
     }
     if (group <= 0) {
-      k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w);
+      PW_TIMED(KK_HEEV, s, k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w));
       return;
     }
     const size_t g = (size_t)group;
@@ -1159,12 +1164,15 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
     auto chain = [&](int m, int c, const HeevWS &wk, cudaStream_t st) {
       zc *H = HU + (size_t)m * nn;
       zc *Z = V + (size_t)m * nn;
-      k_ql_df<<<c, 32, 2 * (size_t)n * sizeof(df), st>>>(wk, status + m, n);
-      k_rot_apply<<<dim3((n + ROT_ROWS - 1) / ROT_ROWS, c), ROT_ROWS, 0, st>>>(wk, reinterpret_cast<dfc *>(Z),
-                                                                              status + m, n);
-      k_backtransform<<<dim3((n + BT_WARPS * BT_COLS - 1) / (BT_WARPS * BT_COLS), c), BT_WARPS * 32, bt_smem,
-                        st>>>(reinterpret_cast<const dfc *>(H), reinterpret_cast<dfc *>(Z), wk, n);
-      k_eig_sort<<<dim3((n + 7) / 8, c), 256, 0, st>>>(Z, H, En + (size_t)m * n, wk.d, status + m, n);
+      PW_TIMED(KK_QL, st, k_ql_df<<<c, 32, 2 * (size_t)n * sizeof(df), st>>>(wk, status + m, n));
+      PW_TIMED(KK_ROT, st,
+               k_rot_apply<<<dim3((n + ROT_ROWS - 1) / ROT_ROWS, c), ROT_ROWS, 0, st>>>(
+                   wk, reinterpret_cast<dfc *>(Z), status + m, n));
+      PW_TIMED(KK_BACKT, st,
+               k_backtransform<<<dim3((n + BT_WARPS * BT_COLS - 1) / (BT_WARPS * BT_COLS), c), BT_WARPS * 32,
+                                 bt_smem, st>>>(reinterpret_cast<const dfc *>(H), reinterpret_cast<dfc *>(Z), wk, n));
+      PW_TIMED(KK_SORT, st,
+               k_eig_sort<<<dim3((n + 7) / 8, c), 256, 0, st>>>(Z, H, En + (size_t)m * n, wk.d, status + m, n));
     };
     // The reduction runs two CTAs per SM.  When a group has more matrices than
     // that, the ones beyond the first full wave go through their own chain on
@@ -1193,13 +1201,15 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
         cudaEventRecord(fork, s);
         cudaStreamWaitEvent(s2, fork, 0);
       }
-      k_heev<df><<<a_cnt, HEEV_THREADS, smem, s>>>(HU + (size_t)m0 * nn, V + (size_t)m0 * nn, En + (size_t)m0 * n,
-                                                   status + m0, n, 1, w);
+      PW_TIMED(KK_HEEV, s,
+               k_heev<df><<<a_cnt, HEEV_THREADS, smem, s>>>(HU + (size_t)m0 * nn, V + (size_t)m0 * nn,
+                                                            En + (size_t)m0 * n, status + m0, n, 1, w));
       if (s2) {
         const int mb = m0 + nA, cb = cnt - nA;
         const HeevWS wb = shifted(nA);
-        k_heev<df><<<cb, HEEV_THREADS, smem, s2>>>(HU + (size_t)mb * nn, V + (size_t)mb * nn, En + (size_t)mb * n,
-                                                   status + mb, n, 1, wb);
+        PW_TIMED(KK_HEEV, s2,
+                 k_heev<df><<<cb, HEEV_THREADS, smem, s2>>>(HU + (size_t)mb * nn, V + (size_t)mb * nn,
+                                                            En + (size_t)mb * n, status + mb, n, 1, wb));
         chain(mb, cb, wb, s2);
         cudaEventRecord(join, s2);
       }
@@ -1213,7 +1223,7 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
     }
   } else {
     cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w);
+    PW_TIMED(KK_HEEV, s, k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w));
   }
 }
 
@@ -1279,19 +1289,19 @@ __global__ void __launch_bounds__(NT) k_o32t(const zc *O, cc *Ot, int n) {
 void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, cc *O32lo, int n, int count, cudaStream_t s) {
   const size_t nn = (size_t)n * n, total = (size_t)count * nn;
   const size_t blocks = (total + NT - 1) / NT;
-  k_o32<<<(unsigned)(blocks < 4096 ? blocks : 4096), NT, 0, s>>>(O, O32, O32lo, total);
+  PW_TIMED(KK_O32, s, k_o32<<<(unsigned)(blocks < 4096 ? blocks : 4096), NT, 0, s>>>(O, O32, O32lo, total));
   if (!O32t) return;
   const int tn = (n + 31) / 32;
   for (int c0 = 0; c0 < count; c0 += 65535) {   // grid.y limit
     const int c = count - c0 < 65535 ? count - c0 : 65535;
-    k_o32t<<<dim3(tn * tn, c), NT, 0, s>>>(O + c0 * nn, O32t + c0 * nn, n);
+    PW_TIMED(KK_O32T, s, k_o32t<<<dim3(tn * tn, c), NT, 0, s>>>(O + c0 * nn, O32t + c0 * nn, n));
   }
 }
 
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s, bool double_float) {
   const size_t smem = gemm_smem_elems<double>() * sizeof(zc);
-  if (double_float) k_overlaps<df><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq);
-  else k_overlaps<double><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq);
+  if (double_float) PW_TIMED(KK_OVERLAPS, s, k_overlaps<df><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq));
+  else PW_TIMED(KK_OVERLAPS, s, k_overlaps<double><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq));
 }
 
 }  // namespace pw

@@ -624,15 +624,16 @@ __global__ void __launch_bounds__(256, 1) k_res_mm(RefineArgs a, int ncol, int n
     const int d = rs_pair(P, s, t);
     float v[8];
     tc::tmem_ld8(lane_base + (uint32_t)((P & 1) * RS_TILE + 8 * q), v);
-    const float unit = __int_as_float((127 - RS_BITS * (d + 2)) << 23);   // 2^-7(s+t+2), exact scaling
+    // the slices carry their scale 2^-7(s+1), so the accumulator already holds
+    // the pair's product (a multiple of 2^-7(s+t+2), exact in FP32)
     if (d >= RS_DF_BELOW) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) hq[i] += v[i] * unit;
+      for (int i = 0; i < 8; ++i) hq[i] += v[i];
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         float sh, se;
-        two_sum(hq[i], v[i] * unit, sh, se);
+        two_sum(hq[i], v[i], sh, se);
         hq[i] = sh;
         lq[i] += se;
       }
@@ -823,19 +824,19 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
     return e;
   auto backward = [&](int with_src) {
     for (int p = a.N; p >= 0; --p) {
-      k_refine_bwd_a<<<rgrid, NT, smem, s>>>(a, p, with_src);
+      PW_TIMED(KK_REF_BWD_A, s, k_refine_bwd_a<<<rgrid, NT, smem, s>>>(a, p, with_src));
       if (batched) {
-        k_refine_bwd_mm<<<mm_tiles, tc::CG_THREADS, tc::cg_smem_bytes(), s>>>(a, p, npts);
-        k_refine_bwd_c<<<rgrid, NT, 0, s>>>(a, p, with_src);
+        PW_TIMED(KK_REF_BWD_MM, s, k_refine_bwd_mm<<<mm_tiles, tc::CG_THREADS, tc::cg_smem_bytes(), s>>>(a, p, npts));
+        PW_TIMED(KK_REF_BWD_C, s, k_refine_bwd_c<<<rgrid, NT, 0, s>>>(a, p, with_src));
       } else {
-        k_refine_bwd_b<<<rgrid, NT, smem, s>>>(a, p, with_src);
+        PW_TIMED(KK_REF_BWD_B, s, k_refine_bwd_b<<<rgrid, NT, smem, s>>>(a, p, with_src));
       }
     }
   };
   auto forward = [&]() {
     for (int p = 0; p <= a.N; ++p) {
-      if (p > 0) k_refine_fwd_a<<<rgrid, NT, smem, s>>>(a, p);
-      k_refine_fwd_b<<<npts, NT, smem, s>>>(a, p);
+      if (p > 0) PW_TIMED(KK_REF_FWD_A, s, k_refine_fwd_a<<<rgrid, NT, smem, s>>>(a, p));
+      PW_TIMED(KK_REF_FWD_B, s, k_refine_fwd_b<<<npts, NT, smem, s>>>(a, p));
     }
   };
   const size_t vec = (size_t)npts * a.n * a.nc * sizeof(zc);
@@ -845,7 +846,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
       (e = cudaMemsetAsync(a.corr, 0, npts * sizeof(double), s)) ||
       (e = cudaMemsetAsync(a.corr_prev, 0, npts * sizeof(double), s)))
     return e;
-  k_refine_init<<<npts, NT, 0, s>>>(a);
+  PW_TIMED(KK_REF_INIT, s, k_refine_init<<<npts, NT, 0, s>>>(a));
   // x0: backward pass over the first sweep's Z_p, u_p
   if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
   backward(0);
@@ -858,13 +859,13 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
     if (sliced) {
       const int ncol = 2 * a.nc * npts;
       for (int p = 0; p <= a.N; ++p) {
-        k_res_oslice<<<a.n, RS_THREADS, 0, s>>>(a, p);
-        k_res_yslice<<<ncol, RS_THREADS, kv_bytes, s>>>(a, p);
-        k_res_mm<<<rs_tiles, 256, res_mm_smem_bytes(), s>>>(a, ncol, npts);
-        k_res_finish<<<npts, NT, kv_bytes, s>>>(a, p, ncol);
+        PW_TIMED(KK_RES_OSLICE, s, k_res_oslice<<<a.n, RS_THREADS, 0, s>>>(a, p));
+        PW_TIMED(KK_RES_YSLICE, s, k_res_yslice<<<ncol, RS_THREADS, kv_bytes, s>>>(a, p));
+        PW_TIMED(KK_RES_MM, s, k_res_mm<<<rs_tiles, 256, res_mm_smem_bytes(), s>>>(a, ncol, npts));
+        PW_TIMED(KK_RES_FINISH, s, k_res_finish<<<npts, NT, kv_bytes, s>>>(a, p, ncol));
       }
     } else {
-      k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a);
+      PW_TIMED(KK_REF_RESIDUAL, s, k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a));
     }
     if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
     forward();
@@ -886,7 +887,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
     backward(1);
   }
   if (passes) *passes = it;
-  k_refine_finish<<<npts, NT, 0, s>>>(a);
+  PW_TIMED(KK_REF_FINISH, s, k_refine_finish<<<npts, NT, 0, s>>>(a));
   return cudaGetLastError();
 }
 

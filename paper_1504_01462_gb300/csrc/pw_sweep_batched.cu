@@ -869,22 +869,25 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   const size_t psm = a.panel_smem ? psm_big : panel_head_bytes<T, BT>();
   const size_t dsm = (size_t)2 * NB * NB * sizeof(cx<T>);
   auto tiles = [](int m, int nn, int bm, int bn) { return ((m + bm - 1) / bm) * ((nn + bn - 1) / bn); };
-  kb_vectors<T><<<npts, VT, 0, s>>>(a, p);
+  PW_TIMED(KK_VECTORS, s, kb_vectors<T><<<npts, VT, 0, s>>>(a, p));
   if (p > 0) {
     const size_t wsm = gsm + 2 * (size_t)n * sizeof(cx<T>);
     if (wy0) cudaEventRecord(wy0, s);
     if (std::is_same<T, float>::value && tensor_core && a.wy_pairs && f16 && a.rowexp) {
-      kb_rowexp<<<dim3((n + 255) / 256, npts), 256, 0, s>>>(a);
-      kb_wy2_tc16<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
-                    wy2_tc16_smem_bytes(n), s>>>(a, p, npts);
+      PW_TIMED(KK_ROWEXP, s, kb_rowexp<<<dim3((n + 255) / 256, npts), 256, 0, s>>>(a));
+      PW_TIMED(KK_WY, s,
+               kb_wy2_tc16<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
+                             wy2_tc16_smem_bytes(n), s>>>(a, p, npts));
     } else if (std::is_same<T, float>::value && tensor_core && a.wy_pairs)
-      kb_wy2_tc<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
-                  wy2_tc_smem_bytes(n), s>>>(a, p, npts);
+      PW_TIMED(KK_WY, s,
+               kb_wy2_tc<<<dim3(tiles(n, n, tc::CG_M / 2, tc::CG_N), (npts + 1) / 2), tc::CG_THREADS,
+                           wy2_tc_smem_bytes(n), s>>>(a, p, npts));
     else if (std::is_same<T, float>::value && tensor_core)
-      kb_wy_tc<<<dim3(tiles(n, 2 * n, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS, wy_tc_smem_bytes(n), s>>>(
-          a, p);
+      PW_TIMED(KK_WY, s,
+               kb_wy_tc<<<dim3(tiles(n, 2 * n, tc::CG_M / 2, tc::CG_N), npts), tc::CG_THREADS,
+                          wy_tc_smem_bytes(n), s>>>(a, p));
     else
-      kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p);
+      PW_TIMED(KK_WY, s, kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p));
     if (wy1) cudaEventRecord(wy1, s);
   }
   // tensor-core FP32 form: LAPACK-ordered pivots, the LU of W alone, then the
@@ -893,29 +896,32 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   a.lapack_piv = lapack ? 1 : 0;
   const int ucols = lapack ? n : ncols;   // columns the LU updates
   for (int j0 = 0; j0 < n; j0 += NB) {
-    kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0);
+    PW_TIMED(KK_PANEL, s, kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0));
     const int c0 = j0 + min(NB, n - j0);
     if constexpr (std::is_same<T, float>::value) {
       const int blocks = (lapack ? (j0 + BT - 1) / BT : 0) + (ucols - c0 + BT - 1) / BT;
-      if (blocks > 0) kb_panel_apply<T, BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0);
+      if (blocks > 0) PW_TIMED(KK_PANEL_APPLY, s, kb_panel_apply<T, BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0));
     }
     if (c0 < n) {
       if (lapack)
-        kb_trail_tc<<<dim3(tiles(n - c0, ucols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0);
+        PW_TIMED(KK_TRAIL, s,
+                 kb_trail_tc<<<dim3(tiles(n - c0, ucols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                               tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0));
       else
-        kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0);
+        PW_TIMED(KK_TRAIL, s, kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0));
     }
   }
   if (lapack) {
     const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
-    kb_rhs_perm<<<dim3((ncols - n + RP_COLS - 1) / RP_COLS, npts), 256, rhs_perm_smem(n), s>>>(a);
+    PW_TIMED(KK_RHS_PERM, s,
+             kb_rhs_perm<<<dim3((ncols - n + RP_COLS - 1) / RP_COLS, npts), 256, rhs_perm_smem(n), s>>>(a));
     for (int j0 = 0; j0 < n; j0 += BS_FB) {
-      kb_fsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0);
+      PW_TIMED(KK_FSDIAG, s, kb_fsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0));
       const int c1 = j0 + std::min(BS_FB, n - j0);
       if (c1 < n)
-        kb_fsupd_tc<<<dim3(tiles(n - c1, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB);
+        PW_TIMED(KK_FSUPD, s,
+                 kb_fsupd_tc<<<dim3(tiles(n - c1, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                               tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB));
     }
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
@@ -923,18 +929,20 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     // 128-row blocks: four diagonal solves and three K = 128 updates at N_G = 512
     const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
     for (int j0 = ((n - 1) / BS_FB) * BS_FB; j0 >= 0; j0 -= BS_FB) {
-      kb_bsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0);
+      PW_TIMED(KK_BSDIAG, s, kb_bsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0));
       if (j0 > 0)
-        kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
-                      tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB);
+        PW_TIMED(KK_BSUPD, s,
+                 kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                               tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB));
     }
   } else {
     for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
-      kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0);
-      if (j0 > 0) kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0);
+      PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0));
+      if (j0 > 0)
+        PW_TIMED(KK_BSUPD, s, kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0));
     }
   }
-  kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p);
+  PW_TIMED(KK_FINISH, s, kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p));
   return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@ import pytest
 
 from oracle import pw_oracle as O
 from tests.golden.cases import tiny_instance
+from tests.parity import rel_T
 
 with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "brute_tiny.json")) as _f:
     GOLDEN = json.load(_f)["cases"]
@@ -41,7 +42,7 @@ def _case(c):
 def test_oracle_matches_stored_brute_force(c):
     inst, kg2 = _case(c)
     T, ts = O.transmission(inst, return_t=True)
-    assert abs(T[0] - c["T"]) < 1e-12 * max(1.0, c["T"])
+    assert rel_T(T[0], c["T"]) < 1e-12
     assert np.abs(ts[0] - _brute_t_by_energy(c, kg2)).max() < 1e-12
 
 
@@ -70,7 +71,7 @@ def test_cuda_path_matches_stored_brute_force(pw, precision, tol):
             ctx.transmission(inst.energies, inst.kpar, T, t, nop)
             torch.cuda.synchronize()
             T, t, nop = T.cpu().numpy(), t.cpu().numpy(), nop.cpu().numpy()
-        assert abs(T[0] - c["T"]) < tol * max(1.0, c["T"]), (c["seed"], T[0], c["T"])
+        assert rel_T(T[0], c["T"]) < tol, (c["seed"], T[0], c["T"])
         nL, nR = int(nop[0, 0]), int(nop[0, 1])
         tb = _brute_t_by_energy(c, kg2)
         assert tb.shape == (nR, nL)

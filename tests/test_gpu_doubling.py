@@ -9,6 +9,7 @@ import pytest
 
 from oracle import pw_oracle as O
 from synthetic import junction, minimal_cell
+from tests.parity import TOL_FP64, rel_T
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -111,8 +112,8 @@ def test_doubling_transmission_and_levels(pw, which):
             S, lv = m.total_s_doubling(md, float(E[i]))
             _, Td = O.transmission_from_s(S, float(E[i]), md[0][0], md[-1][0])
             assert levels[i] == lv, (i, levels[i], lv)
-            assert abs(T[i] - Td) < 1e-10 * max(1.0, Td)
-            assert abs(T[i] - ref[i]) < 1e-10 * max(1.0, ref[i])
+            assert rel_T(T[i], Td) < TOL_FP64
+            assert rel_T(T[i], ref[i]) < TOL_FP64
 
 
 def test_doubling_criterion_and_fp64_sweep(pw):
@@ -129,7 +130,7 @@ def test_doubling_criterion_and_fp64_sweep(pw):
         torch.cuda.synchronize()
         T0, Ts = T0.cpu().numpy(), Ts.cpu().numpy()
     assert np.all(lv0 == 0)
-    assert np.all(np.abs(T0 - Ts) < 1e-10 * np.maximum(1.0, Ts))
+    assert np.all(rel_T(T0, Ts) < TOL_FP64)
 
 
 def test_doubling_threshold_and_invalid_criterion(pw):

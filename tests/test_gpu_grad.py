@@ -8,6 +8,7 @@ import pytest
 
 from oracle import pw_oracle as O
 from synthetic import junction, minimal_cell
+from tests.parity import TOL_FP64, rel_T
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -42,7 +43,7 @@ def test_grad_minimal_cell_against_oracle_adjoint_and_fd(pw):
     with pw.Context.from_instance(inst) as ctx:
         sumT, g = ctx.grad(E, k, w, n_wells=len(inst.v0))
     ref_T, ref_g = _oracle_grad(inst, E, k, w)
-    assert abs(sumT - ref_T) < 1e-10 * max(1.0, ref_T)
+    assert rel_T(sumT, ref_T) < TOL_FP64
     assert np.abs(g - ref_g).max() < 1e-9 * max(1.0, np.abs(ref_g).max())
     h = 1e-5
     for i in range(len(inst.v0)):
@@ -60,7 +61,7 @@ def test_grad_small_junction_against_oracle_adjoint(pw):
     with pw.Context.from_instance(inst) as ctx:
         sumT, g = ctx.grad(E, k, None, n_wells=len(inst.v0))
     ref_T, ref_g = _oracle_grad(inst, E, k, np.ones(len(sel)))
-    assert abs(sumT - ref_T) < 1e-10 * max(1.0, ref_T)
+    assert rel_T(sumT, ref_T) < TOL_FP64
     assert np.abs(g - ref_g).max() < 1e-8 * max(1.0, np.abs(ref_g).max())
 
 
@@ -87,7 +88,7 @@ def test_gap_derivative_small_junction(pw):
     with pw.Context.from_instance(inst) as ctx:
         sumT, dV0, dgap = ctx.grad(E, k, None, n_wells=len(inst.v0), gap=True)
     ref_T, ref_g = _oracle_gap(inst, E, k)
-    assert abs(sumT - ref_T) < 1e-10 * max(1.0, ref_T)
+    assert rel_T(sumT, ref_T) < TOL_FP64
     assert abs(dgap - ref_g) < 1e-8 * max(1.0, abs(ref_g))
     h = 1e-5
     vals = []
@@ -114,7 +115,7 @@ def test_shift_derivative_asymmetric_cell(pw):
     with pw.Context.from_instance(inst) as ctx:
         sumT, _, dgap = ctx.grad(E, k, None, gap=True)
     ref_T, ref_g = _oracle_gap(inst, E, k)
-    assert abs(sumT - ref_T) < 1e-10 * max(1.0, ref_T)
+    assert rel_T(sumT, ref_T) < TOL_FP64
     assert abs(ref_g) > 1e-3
     assert abs(dgap - ref_g) < 1e-9 * max(1.0, abs(ref_g))
     inst.gap_rate_wells = np.tile([0.3, 1.0], (len(inst.v0), 1))
@@ -162,10 +163,53 @@ def test_autograd_function_over_pw_grad(pw):
     out.backward()
     with make(base.v0, 3.35) as ctx:
         sumT, dV0, dgap = ctx.grad(E, k, None, n_wells=len(base.v0), gap=True)
-    assert abs(out.item() - sumT) < 1e-12 * max(1.0, sumT)
+    assert rel_T(out.item(), sumT) < 1e-12
     assert torch.allclose(v0.grad, torch.as_tensor(dV0), rtol=0, atol=1e-12)
     h = 1e-5
     with torch.no_grad():
         fp = summed_transmission(v0, gap + h, make, E, k).item()
         fm = summed_transmission(v0, gap - h, make, E, k).item()
     assert abs((fp - fm) / (2 * h) - gap.grad.item()) < 1e-6 * max(1.0, abs(gap.grad.item()))
+
+
+@pytest.mark.parametrize("interval", [1, 3, 0])
+def test_grad_checkpointed_recomputation_equals_stored_sweep(pw, interval):
+    """pw_grad recomputes its sweeps in segments of C interfaces from stored
+    states; every C (1, a ragged 3 on 17 interfaces, and the default
+    ceil(sqrt(17)) = 5) gives the same sum and gradient as storing every
+    interface (C = N + 1), and both match the oracle's adjoint."""
+    inst = junction(ng=48, n_slices=16, n_e=3, n_k=4)
+    sel = [1, 5, 6, 9]
+    E, k = inst.energies[sel], inst.kpar[sel]
+    nw = len(inst.v0)
+    with pw.Context.from_instance(inst) as ctx:
+        ctx.set_grad_checkpoint(inst.n_slices + 1)
+        s_full, g_full, dg_full = ctx.grad(E, k, n_wells=nw, gap=True)
+        ctx.set_grad_checkpoint(interval)
+        s_ck, g_ck, dg_ck = ctx.grad(E, k, n_wells=nw, gap=True)
+    assert rel_T(s_ck, s_full) < 1e-13
+    assert np.abs(g_ck - g_full).max() < 1e-12 * max(1.0, np.abs(g_full).max())
+    assert abs(dg_ck - dg_full) < 1e-12 * max(1.0, abs(dg_full))
+    ref_T, ref_g = _oracle_grad(inst, E, k, np.ones(len(E)))
+    assert rel_T(s_ck, ref_T) < TOL_FP64
+    assert np.abs(g_ck - ref_g).max() < 1e-9 * max(1.0, np.abs(ref_g).max())
+
+
+def test_grad_memory_grows_as_sqrt_of_slices(pw):
+    """Workspace of pw_grad for one point at 80 and 320 slices (N_G = 128):
+    with the default segments it grows by about sqrt(4) = 2 (the stores are
+    ~2 sqrt(N+1) n^2; only the n x n_c amplitudes grow linearly), storing
+    every interface grows it by about 4."""
+    out = {}
+    for ns in (80, 320):
+        inst = junction(ng=128, n_slices=ns, n_e=1, n_k=1)
+        for mode, interval in (("ckpt", 0), ("full", ns + 1)):
+            with pw.Context.from_instance(inst) as ctx:
+                ctx.set_grad_checkpoint(interval)
+                ctx.grad(inst.energies, inst.kpar, n_wells=len(inst.v0))
+                out[(mode, ns)] = ctx.workspace_bytes()
+    r_ck = out[("ckpt", 320)] / out[("ckpt", 80)]
+    r_full = out[("full", 320)] / out[("full", 80)]
+    assert r_ck < 2.6, out
+    assert r_full > 3.3, out
+    assert out[("ckpt", 320)] < 0.3 * out[("full", 320)], out

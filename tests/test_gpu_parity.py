@@ -11,11 +11,11 @@ import pytest
 from oracle import pw_oracle as O
 from synthetic import (explicit_barrier, explicit_tables, junction, minimal_cell,
                        random_tables)
+from tests.parity import TOL_FP64, TOL_MIXED, rel_T
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-TOL_FP64 = 1e-10
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def _gpu_T(pw, inst, precision=0, E=None, k=None, with_t=False, refine_iters=0, 
 
 
 def _rel(a, b):
-    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+    return rel_T(a, b)
 
 
 # ---------------------------------------------------------------------------
@@ -288,9 +288,6 @@ def test_empty_call(pw):
 # ---------------------------------------------------------------------------
 # mixed form: FP32 sweep, then FP64 iterative refinement of the whole system
 # ---------------------------------------------------------------------------
-TOL_MIXED = 1e-8
-
-
 def test_transmission_mixed_fp32_unrefined(pw):
     """The plain FP32 sweep (no refinement) is accurate to FP32 level only."""
     E = np.array([0.5, 2.3, 3.9, 5.5])

@@ -46,8 +46,42 @@ def test_noalloc_compose_matches_compose_twice(pw):
         assert np.abs(got - ref).max() < 1e-11 * scale
 
 
+def _pair_vs_compose(pw, ng, n_e):
+    """Interface S-matrices of a small junction with N_G = ng at n_e energies,
+    their star product by pw_compose, and by pw_compose_noalloc twice."""
+    from synthetic import junction
+    inst = junction(ng=ng, n_slices=3, n_e=n_e, n_k=1)
+    E, k = inst.energies, inst.kpar
+    with pw.Context.from_instance(inst) as ctx:
+        n = ctx.ng
+        assert n == ng
+        Sa = torch.zeros((len(E), 4, n, n), dtype=torch.complex128, device="cuda")
+        Sb = torch.zeros_like(Sa)
+        ref = torch.zeros_like(Sa)
+        ctx.slice_smatrix(E, k, 1, Sa)
+        ctx.slice_smatrix(E, k, 2, Sb)
+        ctx.compose(len(E), Sa, Sb, ref)
+        torch.cuda.synchronize()
+        ref = ref.cpu().numpy()
+    scale = max(1.0, np.abs(ref).max())
+    for _ in range(2):
+        out = torch.full_like(Sa, complex(np.nan, np.nan))
+        pw.compose_noalloc(n, len(E), Sa, Sb, out)
+        torch.cuda.synchronize()
+        assert np.abs(out.cpu().numpy() - ref).max() < 1e-11 * scale
+
+
+@pytest.mark.parametrize("ng,n_e", [(362, 2), (181, 8), (8, 300)])
+def test_noalloc_limits_and_chunks(pw, ng, n_e):
+    """N_G = 362, the largest size (one point per launch through the array);
+    N_G = 181 with 8 points (three points per launch, three launches); 300
+    points at N_G = 8 (more than the 256 points one launch takes)."""
+    _pair_vs_compose(pw, ng, n_e)
+
+
 def test_noalloc_rejects_oversize_before_device_work(pw):
     lib = pw.lib()
-    assert lib.pw_compose_noalloc(400, 1, 16, 16, 16, None) == 1     # n > 362
+    assert lib.pw_compose_noalloc(363, 1, 16, 16, 16, None) == 1     # n > 362
+    assert lib.pw_compose_noalloc(400, 1, 16, 16, 16, None) == 1
     assert lib.pw_compose_noalloc(0, 1, 16, 16, 16, None) == 1
     assert lib.pw_compose_noalloc(8, 0, None, None, None, None) == 0
