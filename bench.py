@@ -40,6 +40,7 @@ METRIC = "(E,k∥)-points/s at N_G=512, 320 slices: mixed-precision vs FP64, at 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 GOLDEN_512 = os.path.join(ROOT, "tests", "golden", "junction512_k5.json")
 PROFILE_STRIDE = 3      # every third launch of each kernel kind is bracketed by CUDA events
+MIXED_DEFAULT_VARIANT = 2    # the library's default launch variant of the mixed form
 T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
 # DRAM bytes per launch of kernels captured with ncu (read + write), with the capture they
 # come from; a kernel changed since its capture has no entry
@@ -65,6 +66,39 @@ def shard_kpoints(rank, world, n_k, n_steps, first_step=0):
     step s of rank r takes k = (r + s * world) mod n_k, so the ranks of one step
     hold disjoint k_par points (weak scaling: each rank has a full step)."""
     return [(rank + (first_step + s) * world) % n_k for s in range(n_steps)]
+
+
+def instance_weight(inst):
+    """Work of one uneven-batch instance, n^3 (N_s + 1): the sweep's GEMM and LU
+    cost per interface times its interfaces."""
+    n = inst.ng_exact if inst.ng_exact > 0 else 0
+    return float(n) ** 3 * (inst.n_slices + 1)
+
+
+def shard_instances(weights, rank, world):
+    """Indices of the instances rank `rank` of `world` evaluates: the
+    instances, largest weight first, each go to the rank with the least
+    weight so far (lowest rank on ties), so every rank gets a disjoint set and
+    the ranks' total weights differ by at most the largest single weight."""
+    load = [0.0] * world
+    mine = []
+    for i in sorted(range(len(weights)), key=lambda j: (-weights[j], j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += weights[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def reduce_sum(values, world, device):
+    """Sum over ranks of a vector of doubles (the host-side exchange of the
+    summed transmission and of the gradient)."""
+    import torch
+    t = torch.as_tensor(np.asarray(values, dtype=np.float64).reshape(-1), device=device).clone()
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()
 
 
 def reduce_max(value, world, device):
@@ -109,17 +143,17 @@ def sweep_flops_per_point(n, nopen_left):
     return 8.0 * (2.0 * n ** 3 + n ** 3 / 3.0 + n * n * (n + nopen_left))
 
 
-def sweep_kind_totals(n, nc, npts, N, tensor, esz):
+def sweep_kind_totals(n, nc, npts, N, big, esz):
     """Algorithmic work of one step's sweep per kernel kind (all N+1
     interfaces, npts points): {kind: (flops, bytes)}.  CMA = 8 flop.  Bytes are
     what each launch must move at least: the matrix region it updates read and
-    written once, its operands read once.  `tensor`: the tensor-core FP32 form
-    (LAPACK-ordered pivots, the LU updates W's columns only, the right-hand
-    sides n + nc eliminated in 128-row blocks after the LU); else the SIMT form
-    (32-row blocks, the LU updates all 2n + nc columns)."""
+    written once, its operands read once.  `big` (sweep variant bit 3):
+    LAPACK-ordered pivots, the LU updates W's columns only, the right-hand
+    sides n + nc eliminated in 128-row blocks after the LU; else 32-row
+    blocks, the LU's trailing updates carry all 2n + nc columns."""
     NB, FB = 32, 128
     ncols, nrhs = 2 * n + nc, n + nc
-    ucols = n if tensor else ncols
+    ucols = n if big else ncols
     tr_f = tr_b = pa_f = pn_f = 0.0
     for j0 in range(0, n, NB):
         nb = min(NB, n - j0)
@@ -129,7 +163,7 @@ def sweep_kind_totals(n, nc, npts, N, tensor, esz):
         if c0 < n:
             tr_f += (n - c0) * (ucols - c0) * nb
             tr_b += esz * (2.0 * (n - c0) * (ucols - c0) + (n - c0) * nb + nb * (ucols - c0))
-    bs = FB if tensor else NB
+    bs = FB if big else NB
     up_f = up_b = dg_f = fs_f = fs_b = fd_f = 0.0
     for j0 in range(0, n, bs):
         fb = min(bs, n - j0)
@@ -137,7 +171,7 @@ def sweep_kind_totals(n, nc, npts, N, tensor, esz):
         if j0 > 0:
             up_f += j0 * nrhs * fb
             up_b += esz * (2.0 * j0 * nrhs + j0 * fb + fb * nrhs)
-        if tensor:
+        if big:
             fd_f += fb * fb / 2.0 * nrhs
             c1 = j0 + fb
             if c1 < n:
@@ -152,9 +186,9 @@ def sweep_kind_totals(n, nc, npts, N, tensor, esz):
         "kb_bsupd": (8.0 * up_f * I, up_b * I),
         "kb_bsdiag": (8.0 * dg_f * I, None),
     }
-    if tensor:
+    if big:
         out["kb_fsupd_tc"] = (8.0 * fs_f * I, fs_b * I)
-        out["kb_fsdiag_big"] = (8.0 * fd_f * I, None)
+        out["kb_fsdiag"] = (8.0 * fd_f * I, None)
     return out
 
 
@@ -345,8 +379,18 @@ def run_reference(args):
 
 
 def run_uneven(args, torch, pw, local):
-    """The uneven-batch form on one GPU: K instances per step, one call."""
-    insts = uneven_batch(2048)[:args.instances]
+    """The uneven-batch form: the first K of the 2048 instances per step, one
+    call per step; under torchrun each rank takes its share of the K
+    instances by weight n^3 (N_s + 1) (no data exchange), and the summed T of
+    all ranks is added up on the host at the end."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    allk = uneven_batch(2048)[:args.instances]
+    mine = shard_instances([instance_weight(x) for x in allk], rank, world)
+    insts = [allk[i] for i in mine]
     prec = pw.MIXED_FP32 if args.precision == "mixed" else pw.FP64
     E = np.array([float(x.energies[0]) for x in insts])
     k = np.array([x.kpar[0] for x in insts])
@@ -371,17 +415,23 @@ def run_uneven(args, torch, pw, local):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    ng = [x.ng_exact for x in insts]
-    ns = [x.n_slices for x in insts]
+    ms = reduce_max(ev0.elapsed_time(ev1), world, "cuda")
+    sumT = reduce_sum([float(torch.nan_to_num(T).sum().item())], world, "cuda")[0]
+    if rank != 0:
+        b.close()
+        return
+    ng = [x.ng_exact for x in allk]
+    ns = [x.n_slices for x in allk]
     line = {
         "metric": "uneven-batch instances/s (one (E,k_par) point each)",
-        "value": args.steps * len(insts) / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
+        "value": args.steps * len(allk) / (ms / 1e3), "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64" if prec == pw.MIXED_FP32 else "c128", "data": "synthetic",
-        "config": {"workload": f"uneven: first {len(insts)} of 2048 seeded instances, N_G "
+        "sumT": sumT,
+        "config": {"workload": f"uneven: first {len(allk)} of 2048 seeded instances, N_G "
                                f"{min(ng)}..{max(ng)}, {min(ns)}..{max(ns)} slices",
+                   "parallelism": f"instances sharded by n^3 (N_s+1) over {world} rank(s)",
                    "precision": args.precision, "l2": "inputs larger than L2",
                    "sum_n3_slices": float(sum(float(a) ** 3 * (b_ + 2) for a, b_ in zip(ng, ns)))},
         "stages_ms": {kk: vv for kk, vv in stage.items() if kk != "variant"},
@@ -391,6 +441,83 @@ def run_uneven(args, torch, pw, local):
     }
     print(json.dumps(line))
     b.close()
+
+
+def kline(n_k, ax):
+    """The k_par mesh of Eq. T2_d: n_k points k_x = (2j - n_k + 1) pi / (n_k a_x),
+    k_y = 0 (symmetric in +-k, neither 0 nor the zone edge)."""
+    kx = (2.0 * np.arange(n_k) - (n_k - 1)) * np.pi / (n_k * ax)
+    return np.stack([kx, np.zeros_like(kx)], axis=1)
+
+
+def scan_tbar(pw, torch, inst, E, n_k, prec, stream, refine=0):
+    """Tbar (Eq. T1_d / T2_d) of one junction at energy E over an n_k-point
+    k_x mesh through the library: T of every mesh point by pw_transmission,
+    then the FP64 device sums of pw_reduce_transmission.  Returns (Tbar,
+    channel points, T per point)."""
+    k = kline(n_k, inst.a1[0])
+    Es = np.full(n_k, E)
+    T = torch.empty(n_k, dtype=torch.float64, device="cuda")
+    nop = torch.empty((n_k, 2), dtype=torch.int32, device="cuda")
+    with pw.Context.from_instance(inst, precision=prec, refine_iters=refine, stream=stream.cuda_stream) as ctx:
+        ctx.transmission(Es, k, T, None, nop, allow_threshold=True)
+        red = pw.reduce_transmission(T, nop, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+    r = red.cpu().numpy()
+    return float(r[1]), int(r[2]), T.cpu().numpy()
+
+
+def scan_plan(quick=False):
+    """The second workload (synthetic analogues of the overlap-area and
+    interlayer-distance scans, and the k-mesh convergence of Tbar): lists of
+    (label, junction keyword arguments, n_k).  Overlap in rectangular cells
+    (two primitive cells each), 16 slices per cell, N_G = 128."""
+    ng = 48 if quick else 128
+    spc = 4 if quick else 16
+    nk = 8 if quick else 32
+    ovs = (1, 3) if quick else (1, 2, 4, 6, 8)
+    gaps = (3.35, 4.5) if quick else (3.0, 3.35, 4.0, 5.0)
+    plan = []
+    for st in ("AA", "AB"):
+        for ov in ovs:
+            plan.append((f"overlap/{st}/{ov}", dict(ng=ng, n_slices=spc * (ov + 4), cells=ov + 4, stacking=st,
+                                                   n_e=1, n_k=1), nk))
+        for g in gaps:
+            plan.append((f"gap/{st}/{g}", dict(ng=ng, n_slices=spc * 8, cells=8, stacking=st, gap_angstrom=g,
+                                               n_e=1, n_k=1), nk))
+    for m in ((4, 8) if quick else (8, 16, 32, 64, 128)):
+        plan.append((f"kmesh/AA/{m}", dict(ng=ng, n_slices=spc * 8, cells=8, stacking="AA", n_e=1, n_k=1), m))
+    return plan
+
+
+def run_scan(args, torch, pw, local):
+    """The second workload on one GPU: Tbar against overlap area and gap for
+    AA and AB stacking, and Tbar against the k mesh, at E_ref; every point
+    through pw_transmission (mixed form), Tbar by pw_reduce_transmission."""
+    stream = torch.cuda.current_stream()
+    prec = pw.MIXED_FP32 if args.precision == "mixed" else pw.FP64
+    plan = scan_plan(quick=args.instances < 0)
+    E = 0.2
+    out, npts = {}, 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for label, kw, nk in plan:
+        inst = junction(**kw)
+        tbar, nch, _ = scan_tbar(pw, torch, inst, E, nk, prec, stream)
+        out[label] = {"Tbar": tbar, "channel_points": nch, "n_k": nk}
+        npts += nk
+    secs = time.perf_counter() - t0
+    clk = clocks.stop()
+    line = {"metric": "second workload: Tbar scans (points/s through the whole path)",
+            "value": npts / secs, "unit": "points/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * secs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if prec == pw.MIXED_FP32 else "c128", "data": "synthetic",
+            "config": {"workload": "Tbar vs overlap (cells) and gap for AA/AB, Tbar vs k mesh; "
+                                   f"E = {E} Ry, {len(plan)} junctions, {npts} points",
+                       "precision": args.precision},
+            "scan": out, "clocks": clk}
+    print(json.dumps(line))
 
 
 def run_doubling(args, torch, pw, local):
@@ -448,7 +575,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--config", default="junction512",
-                    choices=["junction512", "junction401", "minimal", "uneven"])
+                    choices=["junction512", "junction401", "minimal", "uneven", "scan"])
     ap.add_argument("--instances", type=int, default=96,
                     help="uneven config: how many of the 2048 instances one step covers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -484,6 +611,8 @@ def main():
     torch.cuda.set_device(local)
     if args.config == "uneven":
         return run_uneven(args, torch, pw, local)
+    if args.config == "scan":
+        return run_scan(args, torch, pw, local)
     if args.composition == "doubling":
         return run_doubling(args, torch, pw, local)
     if world > 1:
@@ -590,7 +719,8 @@ def main():
             fp64_arm = fp64_sample(pw, torch, inst, n_e, stream, gold, args.fp64_points)
 
     if rank == 0:
-        variant = args.sweep_variant if args.sweep_variant >= 0 else (2 if prec == pw.MIXED_FP32 else 0)
+        variant = args.sweep_variant if args.sweep_variant >= 0 else (MIXED_DEFAULT_VARIANT if prec == pw.MIXED_FP32
+                                                                      else 0)
         tensor = prec == pw.MIXED_FP32 and (variant & 2) != 0
         peaks = measured_peaks()
         hbm = peaks.get("hbm_gbs") or 6800.0
@@ -606,7 +736,7 @@ def main():
         esz = 8 if prec == pw.MIXED_FP32 else 16
         nc = max(4, ((int(nopen_last[:, 0].max()) + 3) // 4) * 4) if len(nopen_last) else 4
         rows = kernel_table(kprof, args.steps)
-        model = sweep_kind_totals(n, nc, n_e, N, tensor, esz)
+        model = sweep_kind_totals(n, nc, n_e, N, tensor and (variant & 8) != 0, esz)
 
         def roof(row):
             key = row["kernel"].split(" ")[0]
@@ -650,7 +780,7 @@ def main():
                            sweep_variant=variant),
             "roofline": dominant,
             "roofline_next": runner_up,
-            "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows[:12]],
+            "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows],
             "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
                           "overlaps": prof["overlap_ms"], "refine": prof["refine_ms"]},
             "fp64_gpu": fp64_arm,

@@ -269,9 +269,41 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
  * Synchronises the context's stream.  Device memory per point of a batch, in
  * complex doubles: (ceil((N+1)/C) - 1 + C)(n^2 + n n_c) for the checkpoints
  * and one segment's stores (about 2 sqrt(N+1) n^2), plus 4 (N+2) n n_c for
- * the amplitudes of both problems, plus the sweep's own n^2 + n (2n + n_c). */
+ * the amplitudes of both problems, plus the sweep's own n^2 + n (2n + n_c);
+ * per call, 2 C n^2 for the gradient's slices, taken C at a time. */
 pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, const double *weight,
                   double *sumT_host, double *dV0_host, double *dgap_host);
+
+/* Separable nonlocal projector terms (Sec. II A, Eqs. kse0 / ksep: the term
+ * sum_alpha C_alpha W_alpha(r) of the slice equation with
+ * C_alpha = sum_beta D_alpha,beta <W_beta | psi>; Eqs. nloc / gsol_p0: each
+ * slice's particular solutions; Eq. calm_0 for C; together the M X = D
+ * system of App. C Eq. trans, without electrode-crossing projectors).  The
+ * projectors are Bloch sums over the transverse cell of Gaussians
+ * W_alpha(r) = exp(-|r - tau_alpha|^2 / 2 sigma_alpha^2) for
+ * z_lo <= z <= z_hi (zero elsewhere; keep the range inside the device).
+ *   m           number of projectors, 0..8 (0 removes them)
+ *   params      host, 6 per projector: tau_x, tau_y, tau_z, sigma, z_lo, z_hi (bohr)
+ *   D           host, m x m complex, row-major: D[alpha * m + beta]
+ *   quad_nodes  Gauss-Legendre nodes per slice of the z integrals, 2..32
+ * Synchronises the stream; PW_EINVAL for out-of-range arguments. */
+pw_status pw_set_projectors(pw_ctx *ctx, int m, const double *params, const pw_c128 *D, int quad_nodes);
+
+/* T(E, k_par) with the projector terms of pw_set_projectors, in FP64 whatever
+ * the context's precision: psi = psi_0 + sum_alpha C_alpha psi_alpha (psi_0
+ * the local scattering state, psi_alpha the response to projector alpha's
+ * particular solutions with no incident wave) from one stored sweep whose
+ * right-hand sides carry both, the backward pass for every slice's amplitudes,
+ * then Eq. calm_0's m x m system per incident channel.
+ *   T_dev   device, npts doubles (NaN for a threshold point or a singular system)
+ *   C_dev   device or NULL: npts x m x N_G complex; C_alpha of incident left
+ *           channel j at [i][alpha][j], j < n_open^L
+ * PW_EINVAL when no projectors are set or the left electrode has more than 64
+ * open channels; PW_ETHRESH and PW_ESINGULAR as for pw_transmission.
+ * Synchronises the stream.  Memory per point as for pw_grad's one problem,
+ * plus 4 (N+2) m N_G complex doubles. */
+pw_status pw_transmission_nonlocal(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev,
+                                   pw_c128 *C_dev);
 
 /* Segment length C of pw_grad's checkpointed recomputation: 0 (the default)
  * takes C = ceil(sqrt(N+1)); C >= N+1 stores every interface in one pass (no
@@ -283,6 +315,19 @@ pw_status pw_set_grad_checkpoint(pw_ctx *ctx, int interval);
  * buffers grown by pw_transmission, pw_grad and the mode stage; not the
  * per-k_par mode cache set up by pw_setup), into *bytes. */
 pw_status pw_workspace_bytes(const pw_ctx *ctx, double *bytes);
+
+/* Conductance sums of Sec. II B in FP64 on the device, for T of npts points
+ * (as written by pw_transmission): out_dev[0] = sum_i w_i T_i (w_i = 1 when
+ * weight_dev is NULL); out_dev[1] = Tbar of Eq. T1_d / T2_d, the mean of T_i
+ * over the points at which the left electrode has an open channel
+ * (nopen_dev[2i] > 0, the k_par mesh points of the electrode's conduction
+ * channels; every point when nopen_dev is NULL), 0 when there is none;
+ * out_dev[2] = that number of points.  Points with T = NaN (electrode
+ * thresholds) are left out of both.  All pointers are device pointers;
+ * asynchronous on cuda_stream (cudaStream_t, NULL = default); the summation
+ * order is fixed, so the result is reproducible. */
+pw_status pw_reduce_transmission(int npts, const double *T_dev, const int *nopen_dev, const double *weight_dev,
+                                 double *out_dev, void *cuda_stream);
 
 /* The star product of pw_compose for callers that must not allocate device
  * memory at all (no context, no cudaMalloc): for instance code running inside
@@ -310,13 +355,20 @@ pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c1
                              pw_c128 *Sab_dev, void *cuda_stream);
 
 /* Launch variant of the star-product sweep of pw_transmission (default 2 for
- * PW_MIXED_FP32, 0 for PW_FP64).
+ * PW_MIXED_FP32, 0 for PW_FP64).  The result is the same to the form's
+ * accuracy for every variant; only the kernels differ.
  * Bit 0: 512-thread CTAs with 128 x 64 SIMT GEMM tiles (else 256 threads with
- * 64 x 64 tiles).  Bit 1 (PW_MIXED_FP32 only): the [W|Y] product of every
- * interface on the fifth-generation tensor cores (tcgen05, TF32 operands split
- * into hi + lo parts, three products accumulated in FP32 in tensor memory).
- * PW_EINVAL for a variant the context's precision does not have (0..1 for
- * PW_FP64, 0..3 for PW_MIXED_FP32). */
+ * 64 x 64 tiles).  PW_MIXED_FP32 only: bit 1, the GEMM phases of every
+ * interface ([W|Y], the LU's trailing updates, the triangular solves'
+ * updates) on the fifth-generation tensor cores (tcgen05, TF32 operands split
+ * into hi + lo parts, three products accumulated in FP32 in tensor memory);
+ * bit 2 (with bit 1), [W|Y] of point pairs in an FP16 split with row scales;
+ * bit 3 (with bit 1), LAPACK-ordered pivots, the LU on W alone and the right-
+ * hand sides eliminated in 128-row triangular blocks afterwards; bit 4, the
+ * refinement's residual products as exact BF16 slice products on the tensor
+ * cores (used when every point of a launch shares one k_par and N_G is a
+ * multiple of 4 up to 512).  PW_EINVAL for a variant the context's precision
+ * does not have (0..1 for PW_FP64, 0..31 for PW_MIXED_FP32). */
 pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant);
 
 /* Timing of the library's own launches (for benchmarks and roofline
@@ -422,6 +474,15 @@ pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, doub
  * synchronises it; PW_ETIMEOUT if the tensor core did not signal completion
  * within its bounded wait.  A deployment check with no counterpart in the paper. */
 pw_status pw_selftest_f16_split(double *rel_err);
+
+/* Self-test of the bounded device-side waits: one CTA holds tensor memory and
+ * waits, at most `polls` polls of 64 ns, on an mbarrier that no tensor-core
+ * operation will complete; with signal == 0 nobody arrives, so the wait runs
+ * out and the call returns PW_ETIMEOUT (the CTA frees its tensor memory and
+ * the context stays usable); with signal != 0 the CTA arrives first and the
+ * call returns PW_OK.  PW_EINVAL for polls < 1.  Synchronises the device.
+ * The paper has no counterpart; this checks the library's failure handling. */
+pw_status pw_selftest_bounded_wait(int polls, int signal);
 
 /* Measured arithmetic peaks of the current device, in TFLOP/s:
  * tflops[0] = FP64 FMA on the SIMT pipe (DFMA), tflops[1] = the warp-level FP64

@@ -37,7 +37,8 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_set_sweep_variant", "pw_selftest_slice_product", "pw_slice_mixed", "pw_compose_mixed",
            "pw_transmission_doubling", "pw_selftest_f16_split", "pw_kernel_kinds",
            "pw_kernel_kind_name", "pw_get_kernel_profile", "pw_measure_peaks",
-           "pw_set_grad_checkpoint", "pw_workspace_bytes"]
+           "pw_set_grad_checkpoint", "pw_workspace_bytes", "pw_selftest_bounded_wait",
+           "pw_reduce_transmission", "pw_set_projectors", "pw_transmission_nonlocal"]
 
 
 class PwError(RuntimeError):
@@ -114,6 +115,10 @@ def _load():
     lib.pw_measure_peaks.argtypes = [_dp]
     lib.pw_set_grad_checkpoint.argtypes = [_vp, ctypes.c_int]
     lib.pw_workspace_bytes.argtypes = [_vp, _dp]
+    lib.pw_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.pw_reduce_transmission.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+    lib.pw_set_projectors.argtypes = [_vp, ctypes.c_int, _dp, _vp, ctypes.c_int]
+    lib.pw_transmission_nonlocal.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp, _vp]
     lib.pw_batch_destroy.restype = None
     return lib
 
@@ -252,6 +257,18 @@ def selftest_f16_split():
     a = np.zeros(1)
     _check_status(_lib.pw_selftest_f16_split(_as_dp(a)), "pw_selftest_f16_split")
     return float(a[0])
+
+
+def reduce_transmission(T, nopen=None, weight=None, out=None, stream=None):
+    """(sum_i w_i T_i, Tbar of Eq. T1_d, mesh points counted) in FP64 on the
+    device (pw_reduce_transmission); T, nopen, weight and out are device
+    tensors (out: 3 float64 values, allocated when None)."""
+    import torch
+    if out is None:
+        out = torch.zeros(3, dtype=torch.float64, device=T.device)
+    _check_status(_lib.pw_reduce_transmission(int(T.numel()), _ptr(T), _ptr(nopen), _ptr(weight), _ptr(out),
+                                              stream), "pw_reduce_transmission")
+    return out
 
 
 def measure_peaks():
@@ -404,14 +421,35 @@ class Context:
         return float(sumT[0]), dV0[:nw]
 
     def set_sweep_variant(self, variant):
-        """Sweep launch variant: bit 0 = 512-thread SIMT tiles, bit 1 = [W|Y]
-        on the tcgen05 tensor cores (mixed form only)."""
+        """Sweep launch variant (pw_set_sweep_variant): bit 0 = 512-thread SIMT
+        tiles; mixed form only: bit 1 = GEMM phases on the tcgen05 tensor
+        cores, bit 2 = FP16-split [W|Y] of point pairs, bit 3 = LAPACK pivots
+        and 128-row triangular blocks, bit 4 = slice-product residual."""
         self._check(_lib.pw_set_sweep_variant(self._h, int(variant)), "pw_set_sweep_variant")
 
     def set_profiling(self, on=True, stride=1):
         """Stage and per-kernel launch timing; with `stride` k every k-th
         launch of each kernel kind is bracketed by CUDA events."""
         self._check(_lib.pw_set_profiling(self._h, max(1, int(stride)) if on else 0), "pw_set_profiling")
+
+    def set_projectors(self, params, D, quad_nodes=16):
+        """Gaussian separable projectors (pw_set_projectors): params (m, 6) =
+        tau_x, tau_y, tau_z, sigma, z_lo, z_hi; D (m, m) complex."""
+        P = _f64(params).reshape(-1, 6)
+        Dm = np.ascontiguousarray(np.asarray(D, dtype=np.complex128).reshape(len(P), len(P)))
+        self._check(_lib.pw_set_projectors(self._h, len(P), _as_dp(P), Dm.ctypes.data if len(P) else None,
+                                           int(quad_nodes)), "pw_set_projectors")
+
+    def transmission_nonlocal(self, E, kpar, T_out, C_out=None, allow_threshold=False):
+        """T with the projector terms into T_out (device float64); C_out (device
+        complex128, npts x m x N_G) or None."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        st = _lib.pw_transmission_nonlocal(self._h, len(E), _as_dp(E), _as_dp(k), _ptr(T_out), _ptr(C_out))
+        if st == PW_ETHRESH and allow_threshold:
+            return st
+        self._check(st, "pw_transmission_nonlocal")
+        return st
 
     def set_grad_checkpoint(self, interval=0):
         """Segment length of pw_grad's checkpointed recomputation (0: ceil(sqrt(N+1)))."""

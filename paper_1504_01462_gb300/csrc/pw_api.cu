@@ -21,8 +21,8 @@ namespace pw {
 const char *kernel_kind_name(int kind) {
   static const char *names[KK_COUNT] = {
       "kb_vectors", "kb_wy ([W|Y] product: kb_wy, kb_wy_tc, kb_wy2_tc or kb_wy2_tc16)", "kb_rowexp",
-      "kb_panel", "kb_panel_apply", "kb_trail (kb_trail or kb_trail_tc)", "kb_rhs_perm", "kb_fsdiag_big",
-      "kb_fsupd_tc", "kb_bsdiag (kb_bsdiag or kb_bsdiag_big)", "kb_bsupd (kb_bsupd or kb_bsupd_tc)",
+      "kb_panel", "kb_panel_apply", "kb_trail (kb_trail or kb_trail_tc)", "kb_rhs_perm", "kb_fsdiag (kb_diag_big<false>)",
+      "kb_fsupd_tc", "kb_bsdiag (kb_bsdiag or kb_diag_big<true>)", "kb_bsupd (kb_bsupd or kb_bsupd_tc)",
       "kb_finish",
       "k_refine_init", "k_refine_residual", "k_res_oslice", "k_res_yslice", "k_res_mm", "k_res_finish",
       "k_refine_fwd_a", "k_refine_fwd_b", "k_refine_bwd_a", "k_refine_bwd_b", "k_refine_bwd_mm",
@@ -108,6 +108,11 @@ namespace {
 constexpr double kShellQuantum = 1e-8;   // Ry: |G|^2 closer than this is one shell
 constexpr double kThreshold = pw::kThresholdRy;
 constexpr double kRefineTol = pw::kRefineTolRel;
+// default launch variant of the mixed form (pw_set_sweep_variant): the sweep's
+// GEMM phases on the tensor cores with the 32-row LU blocks and the
+// refinement residual on the CUDA cores in double-float (the measured fastest
+// at N_G = 512: 128-row blocks and the slice-product residual were slower)
+constexpr int kMixedDefaultVariant = 2;
 
 struct DevBuf {
   void *p = nullptr;
@@ -172,6 +177,12 @@ struct pw_ctx {
   std::vector<cudaEvent_t> event_pool;
   pw::KernelTimer *kt = nullptr;   // per-kernel launch timing (profiling only)
   int grad_interval = 0;           // pw_grad checkpoint interval (0: ceil(sqrt(N+1)))
+  // separable nonlocal projectors (pw_set_projectors)
+  int nl_m = 0, nl_q = 0;
+  double *d_nlproj = nullptr;      // 6 per projector
+  double *d_gl = nullptr;          // Gauss-Legendre nodes, weights
+  zc *d_nlD = nullptr;             // m x m
+  DevBuf nlV, nlFA, nlFB, nlHA, nlHB, nlPP, ptsb;
   DevBuf ckR, ckT;                 // pw_grad checkpoints of the sweep state (R, Tacc)
 };
 
@@ -384,7 +395,8 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
     pw::launch_assemble_h(ctx->d_HU + (size_t)s * nq * nn, ctx->d_tab, ctx->d_mn, ctx->d_G, ks[s][0],
                           ks[s][1], n, nq, ctx->Dm, ctx->Dn, ctx->stream);
   CK(cudaGetLastError());
-  const bool dfe = ctx->precision == PW_MIXED_FP32;
+  // the mixed form's modes and overlaps in double-float, or (variant bit 5) in FP64
+  const bool dfe = ctx->precision == PW_MIXED_FP32 && !(ctx->sweep_variant & 32);
   if (dfe && (st = ensure(ctx, ctx->eigws, pw::heev_ws_bytes(n, nmat)))) return st;
   pw::launch_eig(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_V + (size_t)s0 * nq * nn,
                  ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
@@ -394,7 +406,7 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
   st1.done();
   Stage st2(ctx, 2, s1 - s0);
   pw::launch_overlaps(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq,
-                      s1 - s0, ctx->stream, ctx->precision == PW_MIXED_FP32);
+                      s1 - s0, ctx->stream, dfe);
   if (ctx->d_O32)
     pw::launch_overlaps_fp32(ctx->d_O + (size_t)s0 * (nq - 1) * nn, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn,
                              ctx->d_O32t + (size_t)s0 * (nq - 1) * nn, ctx->d_O32lo + (size_t)s0 * (nq - 1) * nn,
@@ -526,7 +538,7 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
   ctx->precision = d->precision;
   if (d->refine_iters < -1 || d->refine_iters > 16) { delete ctx; return PW_EINVAL; }
   ctx->refine_iters = d->precision == PW_MIXED_FP32 ? (d->refine_iters == 0 ? 4 : std::max(0, d->refine_iters)) : 0;
-  ctx->sweep_variant = d->precision == PW_MIXED_FP32 ? 2 : 0;   // tensor-core GEMMs for the FP32 sweep
+  ctx->sweep_variant = d->precision == PW_MIXED_FP32 ? kMixedDefaultVariant : 0;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return PW_ECUDA; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   build_basis(d->a1, d->a2, d->ecut, d->ng_exact, ctx->b1, ctx->b2, ctx->mn, ctx->G);
@@ -655,7 +667,9 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->PIVst.p, ctx->Xa_m.p, ctx->Xb_m.p, ctx->status_m.p, ctx->Tg.p, ctx->Gam.p,
                   ctx->gtab.p, ctx->T1.p, ctx->dV0.p, ctx->wgt.p, ctx->d_wxyz, ctx->d_wv0,
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
-                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p, ctx->ckR.p, ctx->ckT.p};
+                  ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p, ctx->ckR.p, ctx->ckT.p,
+                  ctx->d_nlproj, ctx->d_gl, ctx->d_nlD, ctx->nlV.p, ctx->nlFA.p, ctx->nlFB.p, ctx->nlHA.p,
+                  ctx->nlHB.p, ctx->nlPP.p, ctx->ptsb.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1138,13 +1152,13 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.nc = nc;
         r.x_slots = (long long)nb * (N + 2);
         r.st_slots = (long long)nb * (N + 1);
-        r.lapack_piv = (ctx->sweep_variant & 2) ? 1 : 0;   // the stored factors' pivot order
+        r.lapack_piv = (ctx->sweep_variant & 10) == 10 ? 1 : 0;   // the stored factors' pivot order
         if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32) {
           // one buffer: the backward product's operands and result, then (when the
           // residual runs on the tensor cores) O y, the slices and their exponents
           auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
           const long long ncol = 2LL * nb * nc;
-          const bool sliced = ctx->d_O32lo && n <= 512 && n % 4 == 0;
+          const bool sliced = (ctx->sweep_variant & 16) && ctx->d_O32lo && n <= 512 && n % 4 == 0;
           const size_t b_bw = up((size_t)4 * nb * n * nc * sizeof(cc));
           const size_t b_y = up((size_t)2 * n * ncol * sizeof(double));
           const size_t b_sl = up(pw::rs_slice_bytes(n, ncol));
@@ -1187,6 +1201,270 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
 }
 
 
+// The FP64 sweep of a batch of nb points with its stores (Z_p, u_p) and the
+// backward pass that recovers every slice's amplitudes into g.Xa, g.Xb, in
+// segments of C interfaces: with K > 1 segments a first pass keeps only the
+// sweep state (R and the Tacc columns) before every segment after the first;
+// the segments are then taken from the right, each recomputed with its stores
+// (slots st_off + p = i C + p - p0 of point i) and stepped through backward
+// (the carry links consecutive segments).  loc / d_loc: the points' host and
+// device descriptors (their st_off is rewritten per segment).
+static pw_status stored_sweep_backward(pw_ctx *ctx, const pw::SweepArgs &a, const pw::GradArgs &g, int nb, int C,
+                                       std::vector<PointDesc> &loc, PointDesc *d_loc) {
+  const int n = ctx->n, N = ctx->N, ncols = 2 * n + a.nc;
+  const size_t nn = (size_t)n * n, vec = (size_t)n * a.nc;
+  const int K = (N + 1 + C - 1) / C;
+  CK(pw::prepare_sweep_batched(n, PW_FP64, 0));
+  zc *Rb = (zc *)ctx->R.p, *Mb = (zc *)ctx->M.p;
+  zc *ckR = (zc *)ctx->ckR.p, *ckT = (zc *)ctx->ckT.p;
+  if (K > 1) {
+    pw::SweepArgs a0 = a;
+    a0.Zst = nullptr;
+    a0.Ust = nullptr;
+    for (int p = 0; p <= N; ++p) {
+      CK(pw::launch_sweep_batched(a0, nb, p, PW_FP64, ctx->stream));
+      if ((p + 1) % C == 0 && p < N) {
+        const int k = (p + 1) / C - 1;
+        CK(cudaMemcpyAsync(ckR + (size_t)k * nb * nn, Rb, (size_t)nb * nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpy2DAsync(ckT + (size_t)k * nb * vec, vec * sizeof(zc), Mb + 2 * nn, (size_t)n * ncols * sizeof(zc),
+                             vec * sizeof(zc), nb, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+    }
+  }
+  for (int k = K - 1; k >= 0; --k) {
+    const int p0 = k * C, p1 = std::min(N, p0 + C - 1);
+    for (int i = 0; i < nb; ++i) loc[i].st_off = (long long)i * C - p0;
+    CK(cudaMemcpyAsync(d_loc, loc.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+    if (k > 0) {
+      CK(cudaMemcpyAsync(Rb, ckR + (size_t)(k - 1) * nb * nn, (size_t)nb * nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpy2DAsync(Mb + 2 * nn, (size_t)n * ncols * sizeof(zc), ckT + (size_t)(k - 1) * nb * vec,
+                           vec * sizeof(zc), vec * sizeof(zc), nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    for (int p = p0; p <= p1; ++p) CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream));
+    CK(pw::launch_grad_backward(g, nb, ctx->stream, p1, p0, k == K - 1));
+  }
+  return PW_OK;
+}
+
+// Gauss-Legendre nodes x[q] and weights w[q] on [-1, 1]: Newton iteration on
+// the Legendre polynomial P_q from the Chebyshev-like first guesses
+// cos(pi (i + 3/4) / (q + 1/2)), P_q and P_q' by the three-term recurrence.
+static void gauss_legendre(int q, double *x, double *w) {
+  for (int i = 0; i < q; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (q + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= q; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pq = q == 1 ? z : p1, pm = q == 1 ? 1.0 : p0;
+      dp = q * (z * pq - pm) / (z * z - 1.0);
+      const double dz = pq / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[q - 1 - i] = z;
+    w[q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+pw_status pw_set_projectors(pw_ctx *ctx, int m, const double *params, const pw_c128 *D, int quad_nodes) {
+  if (!ctx || m < 0 || m > pw::kNlMaxProj || (m > 0 && (!params || !D)) || quad_nodes < 2 ||
+      quad_nodes > pw::kNlMaxQuad)
+    return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  for (int a = 0; a < m; ++a)
+    if (!(params[6 * a + 3] > 0.0) || !(params[6 * a + 4] <= params[6 * a + 5])) return PW_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (void **b : {(void **)&ctx->d_nlproj, (void **)&ctx->d_gl, (void **)&ctx->d_nlD})
+    if (*b) { cudaFree(*b); *b = nullptr; }
+  ctx->nl_m = 0;
+  if (m == 0) return PW_OK;
+  std::vector<double> gl(2 * quad_nodes);
+  gauss_legendre(quad_nodes, gl.data(), gl.data() + quad_nodes);
+  if (cudaMalloc(&ctx->d_nlproj, 6 * m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_gl, gl.size() * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_nlD, (size_t)m * m * sizeof(zc)) != cudaSuccess) {
+    cudaGetLastError();
+    return latch(ctx, PW_ENOMEM);
+  }
+  CK(cudaMemcpy(ctx->d_nlproj, params, 6 * m * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_gl, gl.data(), gl.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_nlD, D, (size_t)m * m * sizeof(zc), cudaMemcpyHostToDevice));
+  ctx->nl_m = m;
+  ctx->nl_q = quad_nodes;
+  return PW_OK;
+}
+
+pw_status pw_transmission_nonlocal(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev,
+                                   pw_c128 *C_dev) {
+  if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev)) || ctx->nl_m <= 0) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  KtScope kts(ctx);
+  const int n = ctx->n, N = ctx->N, m = ctx->nl_m;
+  const size_t nn = (size_t)n * n;
+  pw_status st = alloc_slots(ctx);
+  if (st) return st;
+  std::vector<std::vector<int>> groups;
+  group_by_k(npts, kpar, groups);
+  pw_status result = PW_OK;
+  const int C = grad_interval_of(ctx);
+  const int K = (N + 1 + C - 1) / C;
+  for (size_t g0 = 0; g0 < groups.size(); g0 += ctx->ks_cap) {
+    const size_t g1 = std::min(groups.size(), g0 + (size_t)ctx->ks_cap);
+    std::vector<const double *> ks;
+    std::vector<std::pair<int, int>> pts;
+    for (size_t gi = g0; gi < g1; ++gi) {
+      ks.push_back(kpar + 2 * groups[gi][0]);
+      for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
+    }
+    if ((st = ensure_ksets(ctx, ks))) return st;
+    // the projectors in every device slice's mode basis, per k-set
+    if ((st = ensure(ctx, ctx->nlV, (size_t)ks.size() * N * m * n * sizeof(zc)))) return st;
+    for (size_t sl = 0; sl < ks.size(); ++sl)
+      CK(pw::launch_nl_project(ctx->d_HU + sl * (size_t)(N + 2) * nn, (zc *)ctx->nlV.p + sl * (size_t)N * m * n,
+                               nullptr, ctx->d_G, ks[sl][0], ks[sl][1], ctx->d_nlproj, ctx->area, n, N, m,
+                               ctx->stream));
+    std::vector<PointDesc> all(pts.size());
+    int ninc = 1;
+    for (size_t i = 0; i < pts.size(); ++i) {
+      const int idx = pts[i].first, slot = pts[i].second;
+      bool th = false;
+      const int nL = count_open(ctx->EL[slot], E[idx], &th);
+      const int nR = count_open(ctx->ER[slot], E[idx], &th);
+      all[i] = pw::make_point(E[idx], slot, nL, nR, idx, th ? 1 : 0, N, 0);
+      if (th) result = PW_ETHRESH;
+      else ninc = std::max(ninc, nL);
+    }
+    if (ninc > pw::kNlMaxOpen) return PW_EINVAL;
+    const int c0 = ninc, nc = (ninc + m + 3) & ~3, ncols = 2 * n + nc;
+    const size_t vec = (size_t)n * nc;
+    const size_t per_pt = (nn + (size_t)n * ncols + 3 * (size_t)n) * sizeof(zc) + n * sizeof(int) +
+                          (size_t)(C + K - 1) * (nn + vec) * sizeof(zc) + 2 * (size_t)(N + 2) * vec * sizeof(zc) +
+                          4 * (size_t)(N + 2) * m * n * sizeof(zc) + (size_t)(N + 2) * m * m * sizeof(zc) +
+                          3 * vec * sizeof(zc) + 64;
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const int fit = (int)std::max<size_t>(1, (size_t)(0.7 * (double)free_b) / per_pt);
+    const int bmax = std::max(1, std::min({(int)pts.size(), 3 * ctx->num_sms, fit}));
+    for (size_t b0 = 0; b0 < pts.size(); b0 += bmax) {
+      const int nb = (int)std::min(pts.size() - b0, (size_t)bmax);
+      std::vector<PointDesc> pd(all.begin() + b0, all.begin() + b0 + nb), loc(nb);
+      for (int i = 0; i < nb; ++i) {
+        pd[i] = pw::make_point(pd[i].E, pd[i].kset, pd[i].nL, pd[i].nR, pd[i].out, pd[i].skip, N, i);
+        loc[i] = pd[i];
+        loc[i].out = i;   // the sweep's own T goes to scratch
+      }
+      const size_t xs = (size_t)nb * (N + 2);
+      if ((st = ensure(ctx, ctx->R, (size_t)nb * nn * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->M, (size_t)nb * n * ncols * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->piv, (size_t)nb * n * sizeof(int))) ||
+          (st = ensure(ctx, ctx->KV, (size_t)nb * 3 * n * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->pts, (size_t)nb * sizeof(PointDesc))) ||
+          (st = ensure(ctx, ctx->ptsb, (size_t)nb * sizeof(PointDesc))) ||
+          (st = ensure(ctx, ctx->status, (size_t)nb * sizeof(int))) ||
+          (st = ensure(ctx, ctx->Zst, (size_t)nb * C * nn * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Ust, (size_t)nb * C * vec * sizeof(zc))) ||
+          (K > 1 && (st = ensure(ctx, ctx->ckR, (size_t)(K - 1) * nb * nn * sizeof(zc)))) ||
+          (K > 1 && (st = ensure(ctx, ctx->ckT, (size_t)(K - 1) * nb * vec * sizeof(zc)))) ||
+          (st = ensure(ctx, ctx->Xa, xs * vec * sizeof(zc))) || (st = ensure(ctx, ctx->Xb, xs * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->carry, (size_t)nb * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->tmp, (size_t)nb * 2 * vec * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->Tg, (size_t)nb * sizeof(double))) ||
+          (st = ensure(ctx, ctx->nlFA, xs * m * n * sizeof(zc))) || (st = ensure(ctx, ctx->nlFB, xs * m * n * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->nlHA, xs * m * n * sizeof(zc))) || (st = ensure(ctx, ctx->nlHB, xs * m * n * sizeof(zc))) ||
+          (st = ensure(ctx, ctx->nlPP, xs * m * m * sizeof(zc))))
+        return st;
+      PointDesc *d_loc = (PointDesc *)ctx->pts.p, *d_pd = (PointDesc *)ctx->ptsb.p;
+      CK(cudaMemcpyAsync(d_loc, loc.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(d_pd, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemsetAsync(ctx->status.p, 0, nb * sizeof(int), ctx->stream));
+      pw::NonlocalArgs na;
+      memset(&na, 0, sizeof(na));
+      na.pts = d_pd;
+      na.En = ctx->d_En;
+      na.dz = ctx->d_dz;
+      na.zedge = ctx->d_z;
+      na.V = (const zc *)ctx->nlV.p;
+      na.proj = ctx->d_nlproj;
+      na.gl = ctx->d_gl;
+      na.q = ctx->nl_q;
+      na.FA = (zc *)ctx->nlFA.p;
+      na.FB = (zc *)ctx->nlFB.p;
+      na.HA = (zc *)ctx->nlHA.p;
+      na.HB = (zc *)ctx->nlHB.p;
+      na.PP = (zc *)ctx->nlPP.p;
+      na.Xa = (const zc *)ctx->Xa.p;
+      na.Xb = (const zc *)ctx->Xb.p;
+      na.D = ctx->d_nlD;
+      na.area = ctx->area;
+      na.status = (const int *)ctx->status.p;
+      na.T = T_dev;
+      na.C = (zc *)C_dev;
+      na.n = n;
+      na.N = N;
+      na.nc = nc;
+      na.m = m;
+      na.c0 = c0;
+      na.ks_N = N;
+      CK(pw::launch_nl_slice_terms(na, nb, ctx->stream));
+      pw::SweepArgs a;
+      memset(&a, 0, sizeof(a));
+      a.pts = d_loc;
+      a.En = ctx->d_En;
+      a.O = ctx->d_O;
+      a.dz = ctx->d_dz;
+      a.R = ctx->R.p;
+      a.M = ctx->M.p;
+      a.piv = (int *)ctx->piv.p;
+      a.status = (int *)ctx->status.p;
+      a.T = (double *)ctx->Tg.p;
+      a.n = n;
+      a.N = N;
+      a.nc = nc;
+      a.Zst = ctx->Zst.p;
+      a.Ust = ctx->Ust.p;
+      a.KV = ctx->KV.p;
+      a.nl_fa = (const zc *)ctx->nlFA.p;
+      a.nl_fb = (const zc *)ctx->nlFB.p;
+      a.nl_m = m;
+      a.nl_c0 = c0;
+      pw::GradArgs g;
+      memset(&g, 0, sizeof(g));
+      g.pts = d_loc;
+      g.En = ctx->d_En;
+      g.O = ctx->d_O;
+      g.dz = ctx->d_dz;
+      g.Zst = (const zc *)ctx->Zst.p;
+      g.Ust = (const zc *)ctx->Ust.p;
+      g.Xa = (zc *)ctx->Xa.p;
+      g.Xb = (zc *)ctx->Xb.p;
+      g.carry = (zc *)ctx->carry.p;
+      g.tmp = (zc *)ctx->tmp.p;
+      g.status = a.status;
+      g.n = n;
+      g.N = N;
+      g.nc = nc;
+      g.nl_fa = a.nl_fa;
+      g.nl_m = m;
+      g.nl_c0 = c0;
+      if ((st = stored_sweep_backward(ctx, a, g, nb, C, loc, d_loc))) return st;
+      CK(pw::launch_nl_solve(na, nb, ctx->stream));
+      std::vector<int> sth(nb);
+      CK(cudaMemcpyAsync(sth.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int v : sth)
+        if (v) result = PW_ESINGULAR;
+    }
+  }
+  if (result == PW_ESINGULAR) latch(ctx, result);
+  return result;
+}
+
 pw_status pw_set_grad_checkpoint(pw_ctx *ctx, int interval) {
   if (!ctx || interval < 0) return PW_EINVAL;
   ctx->grad_interval = interval;
@@ -1222,9 +1500,11 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
   const int tsz = ctx->tsz;
   pw_status st = alloc_slots(ctx);
   if (st) return st;
-  if ((st = ensure(ctx, ctx->Gam, (size_t)ctx->ks_cap * N * nn * sizeof(zc))) ||
+  // Gamma_p and the fold's scratch for one chunk of C device slices
+  const int C = grad_interval_of(ctx);
+  if ((st = ensure(ctx, ctx->Gam, (size_t)C * nn * sizeof(zc))) ||
       (st = ensure(ctx, ctx->gtab, (size_t)N * tsz * sizeof(zc))) ||
-      (st = ensure(ctx, ctx->T1, (size_t)N * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->T1, (size_t)C * nn * sizeof(zc))) ||
       (st = ensure(ctx, ctx->dV0, (size_t)std::max(1, ctx->n_wells) * sizeof(double))))
     return st;
   CK(cudaMemsetAsync(ctx->gtab.p, 0, (size_t)N * tsz * sizeof(zc), ctx->stream));
@@ -1241,7 +1521,6 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
       for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
     }
     if ((st = ensure_ksets(ctx, ks))) return st;
-    CK(cudaMemsetAsync(ctx->Gam.p, 0, (size_t)ks.size() * N * nn * sizeof(zc), ctx->stream));
     std::vector<PointDesc> all(pts.size());
     int nc = 1;
     for (size_t i = 0; i < pts.size(); ++i) {
@@ -1260,7 +1539,6 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
     // of every segment of C interfaces, and Z_p, u_p only for the C interfaces of
     // the segment being recomputed, so the stores grow as (ceil((N+1)/C) - 1 + C)
     // (n^2 + n nc), about 2 sqrt(N+1) (n^2 + n nc) for C = ceil(sqrt(N+1))
-    const int C = grad_interval_of(ctx);
     const int K = (N + 1 + C - 1) / C;   // segments
     // per point: FP64 sweep buffers, the stores of one segment, the checkpoints,
     // amplitudes of both problems
@@ -1337,27 +1615,6 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
         a.Ust = ctx->Ust.p;
         a.KV = ctx->KV.p;
         a.mirror = mirror;
-        CK(pw::prepare_sweep_batched(n, PW_FP64, 0));
-        zc *Rb = (zc *)ctx->R.p, *Mb = (zc *)ctx->M.p;
-        zc *ckR = (zc *)ctx->ckR.p, *ckT = (zc *)ctx->ckT.p;
-        if (K > 1) {
-          // first pass: the whole sweep without stores, keeping the state
-          // (R, Tacc) before the first interface of every later segment
-          pw::SweepArgs a0 = a;
-          a0.Zst = nullptr;
-          a0.Ust = nullptr;
-          for (int p = 0; p <= N; ++p) {
-            CK(pw::launch_sweep_batched(a0, nb, p, PW_FP64, ctx->stream));
-            if ((p + 1) % C == 0 && p < N) {
-              const int k = (p + 1) / C - 1;
-              CK(cudaMemcpyAsync(ckR + (size_t)k * nb * nn, Rb, (size_t)nb * nn * sizeof(zc),
-                                 cudaMemcpyDeviceToDevice, ctx->stream));
-              CK(cudaMemcpy2DAsync(ckT + (size_t)k * nb * vec, vec * sizeof(zc), Mb + 2 * nn,
-                                   (size_t)n * ncols * sizeof(zc), vec * sizeof(zc), nb,
-                                   cudaMemcpyDeviceToDevice, ctx->stream));
-            }
-          }
-        }
         pw::GradArgs g;
         g.pts = a.pts;
         g.En = ctx->d_En;
@@ -1374,22 +1631,10 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
         g.N = N;
         g.nc = nc;
         g.mirror = mirror;
-        // segments from the right: restore the state at the segment's start,
-        // recompute its interfaces with stores (slots st_off + p = i C + p - p0),
-        // then the backward pass over them (the carry links the segments)
-        for (int k = K - 1; k >= 0; --k) {
-          const int p0 = k * C, p1 = std::min(N, p0 + C - 1);
-          for (int i = 0; i < nb; ++i) loc[i].st_off = (long long)i * C - p0;
-          CK(cudaMemcpyAsync(d_loc, loc.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
-          if (k > 0) {
-            CK(cudaMemcpyAsync(Rb, ckR + (size_t)(k - 1) * nb * nn, (size_t)nb * nn * sizeof(zc),
-                               cudaMemcpyDeviceToDevice, ctx->stream));
-            CK(cudaMemcpy2DAsync(Mb + 2 * nn, (size_t)n * ncols * sizeof(zc), ckT + (size_t)(k - 1) * nb * vec,
-                                 vec * sizeof(zc), vec * sizeof(zc), nb, cudaMemcpyDeviceToDevice, ctx->stream));
-          }
-          for (int p = p0; p <= p1; ++p) CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream));
-          CK(pw::launch_grad_backward(g, nb, ctx->stream, p1, p0, k == K - 1));
-        }
+        g.nl_fa = nullptr;
+        g.nl_m = 0;
+        g.nl_c0 = 0;
+        if ((st = stored_sweep_backward(ctx, a, g, nb, C, loc, d_loc))) return st;
       }
       pw::GammaArgs h;
       h.pts = d_pd;
@@ -1408,7 +1653,16 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
       h.N = N;
       h.nc = nc;
       h.npts = nb;
-      for (size_t sl = 0; sl < ks.size(); ++sl) CK(pw::launch_grad_gamma(h, (int)sl, ctx->stream));
+      // Gamma_p of this batch's points, folded onto the tables' grid chunk by
+      // chunk of C slices (the fold is linear, so batches add up in gtab)
+      for (size_t sl = 0; sl < ks.size(); ++sl)
+        for (int p0 = 1; p0 <= N; p0 += C) {
+          const int cnt = std::min(C, N + 1 - p0);
+          CK(cudaMemsetAsync(ctx->Gam.p, 0, (size_t)cnt * nn * sizeof(zc), ctx->stream));
+          CK(pw::launch_grad_gamma(h, (int)sl, p0, cnt, ctx->stream));
+          CK(pw::launch_grad_fold(h, (int)sl, p0, cnt, ctx->d_HU, (zc *)ctx->T1.p, ctx->d_mn, ctx->Dm,
+                                  ctx->Dn, ctx->stream));
+        }
       std::vector<double> lead_h(nb, 0.0);
       if (lead_shift) {
         if ((st = ensure(ctx, ctx->lead_scr, (size_t)nb * 4 * vec * sizeof(zc))) ||
@@ -1433,15 +1687,6 @@ pw_status pw_grad(pw_ctx *ctx, int npts, const double *E, const double *kpar, co
         }
       }
     }
-    pw::GammaArgs h;
-    memset(&h, 0, sizeof(h));
-    h.Gam = (zc *)ctx->Gam.p;
-    h.gtab = (zc *)ctx->gtab.p;
-    h.n = n;
-    h.N = N;
-    for (size_t sl = 0; sl < ks.size(); ++sl)
-      CK(pw::launch_grad_fold(h, (int)sl, ctx->d_HU, (zc *)ctx->T1.p, ctx->d_mn, ctx->Dm, ctx->Dn,
-                              ctx->stream));
   }
   *sumT_host = sumT;
   const bool wells_shift = dgap_host && ctx->d_wrate && ctx->n_wells > 0;

@@ -280,7 +280,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     const int steps = std::min(maxN, 3) + 1;
     float best = 0.f;
     BCK(cudaEventRecord(ev[3], s));
-    for (int cand = 0; cand < pw::sweep_variants(b->precision); ++cand) {
+    for (int cand : pw::sweep_variant_candidates(b->precision)) {
       BCK(pw::prepare_sweep_batched(n, b->precision, cand));
       BCK(cudaMemsetAsync(b->status.p, 0, m * sizeof(int), s));
       BCK(cudaEventRecord(ev[6], s));
@@ -288,7 +288,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
       BCK(cudaEventRecord(ev[7], s));
       BCK(cudaEventSynchronize(ev[7]));
       const float ms = elapsed(ev[6], ev[7]);
-      if (cand == 0 || ms < best) {
+      if (var < 0 || ms < best) {
         best = ms;
         var = cand;
       }
@@ -366,7 +366,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     r.nc = nc;
     r.x_slots = nmat;
     r.st_slots = nov;
-    r.lapack_piv = (var & 2) ? 1 : 0;   // the stored factors' pivot order
+    r.lapack_piv = (var & 10) == 10 ? 1 : 0;   // the stored factors' pivot order
     int passes = 0;
     BCK(pw::launch_refine(r, m, std::min(2, b->refine_iters), b->refine_iters, pw::kRefineTolRel, s, &passes));
   }

@@ -90,6 +90,17 @@ __global__ void __launch_bounds__(GT) k_grad_backward(GradArgs g, int p) {
         Xa[i + (size_t)j * n] = a;
       },
       gsm);
+  // separable nonlocal terms: the source columns' b_p carries P_p fa_q, the
+  // particular solution of slice q at its left edge (none in the right electrode)
+  if (g.nl_m > 0 && q <= N) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * g.nl_m; e += GT) {
+      const int i = e % n, al = e / n;
+      zc &x = tmp[n + i + (size_t)(g.nl_c0 + al) * 2 * n];
+      x = cadd(x, g.nl_fa[(((size_t)d.x_off + q) * g.nl_m + al) * n + i]);
+    }
+    __syncthreads();
+  }
   auto pq = [=](int l, int j, double sel) {
     const zc o = tr ? O[j + (size_t)l * n] : O[l + (size_t)j * n];
     const zc r = cmul(kr[j], kinv[l]);
@@ -117,9 +128,10 @@ __global__ void k_grad_init(GradArgs g) {
 }
 
 // Gamma_p (tile of the n x n eigenbasis matrix) summed over the batch's points
-// of k-set `slot`; grid (tiles, N device slices).
-__global__ void __launch_bounds__(GT) k_grad_gamma(GammaArgs h, int slot) {
-  const int p = blockIdx.y + 1;   // device slice 1..N
+// of k-set `slot`, for the device slices p0 .. p0 + gridDim.y - 1 (a chunk;
+// Gam holds one n x n matrix per slice of the chunk); grid (tiles, slices).
+__global__ void __launch_bounds__(GT) k_grad_gamma(GammaArgs h, int slot, int p0) {
+  const int p = p0 + blockIdx.y;   // device slice p0 .. (1-based)
   const int n = h.n, N = h.N, nc = h.nc;
   const int tiles_i = (n + 15) / 16;
   const int i0 = (blockIdx.x % tiles_i) * 16, j0 = (blockIdx.x / tiles_i) * 16;
@@ -205,22 +217,23 @@ __global__ void __launch_bounds__(GT) k_grad_gamma(GammaArgs h, int slot) {
     acc.im += w * part.im;
   }
   if (m < n && nn_ < n) {
-    zc &G = h.Gam[((size_t)slot * N + (p - 1)) * n * n + m + (size_t)nn_ * n];
+    zc &G = h.Gam[(size_t)(p - p0) * n * n + m + (size_t)nn_ * n];
     G = cadd(G, acc);
   }
 }
 
 // g_p(dG) += sum over (i, j) with G_i - G_j = dG of (conj(U_p) Gamma_p U_p^T)_ij;
-// one CTA per device slice of k-set `slot`.  T1: n x n scratch per slice.
-__global__ void __launch_bounds__(GT) k_grad_fold(GammaArgs h, int slot, const zc *U_all, zc *T1_all,
+// one CTA per device slice p0 .. p0 + gridDim.x - 1 of k-set `slot` (the
+// chunk held in Gam).  T1: n x n scratch per slice of the chunk.
+__global__ void __launch_bounds__(GT) k_grad_fold(GammaArgs h, int slot, int p0, const zc *U_all, zc *T1_all,
                                                   const int *mn, int Dm, int Dn) {
   extern __shared__ __align__(16) unsigned char smraw[];
   zc *gsm = reinterpret_cast<zc *>(smraw);
-  const int p = blockIdx.x + 1, n = h.n, N = h.N;
+  const int p = p0 + blockIdx.x, n = h.n, N = h.N;
   const size_t nn = (size_t)n * n;
   const zc *U = U_all + ((size_t)slot * (N + 2) + p) * nn;
-  const zc *Gm = h.Gam + ((size_t)slot * N + (p - 1)) * nn;
-  zc *T1 = T1_all + (size_t)(p - 1) * nn;
+  const zc *Gm = h.Gam + (size_t)(p - p0) * nn;
+  zc *T1 = T1_all + (size_t)(p - p0) * nn;
   zc *gtab = h.gtab + (size_t)(p - 1) * (2 * Dm + 1) * (2 * Dn + 1);
   // T1 = conj(U) Gamma
   cta_gemm<double>(
@@ -405,16 +418,16 @@ cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, cudaStream_t s) {
+cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, int p0, int cnt, cudaStream_t s) {
   const int tiles = ((h.n + 15) / 16) * ((h.n + 15) / 16);
-  k_grad_gamma<<<dim3(tiles, h.N), GT, 0, s>>>(h, slot);
+  k_grad_gamma<<<dim3(tiles, cnt), GT, 0, s>>>(h, slot, p0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_fold(const GammaArgs &h, int slot, const zc *U, zc *T1, const int *mn, int Dm,
-                             int Dn, cudaStream_t s) {
+cudaError_t launch_grad_fold(const GammaArgs &h, int slot, int p0, int cnt, const zc *U, zc *T1, const int *mn,
+                             int Dm, int Dn, cudaStream_t s) {
   const size_t smem = gemm_smem_elems<double>() * sizeof(zc);
-  k_grad_fold<<<h.N, GT, smem, s>>>(h, slot, U, T1, mn, Dm, Dn);
+  k_grad_fold<<<cnt, GT, smem, s>>>(h, slot, p0, U, T1, mn, Dm, Dn);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "pw_cx.cuh"
 #include "../../include/pw.h"
 
@@ -96,6 +98,12 @@ struct SweepArgs {
                          //    order) and the right-hand sides are eliminated after the LU
   int *rowexp;           // null, or per point 2n: the power-of-two row scales of R and of
                          //   R K_p^{-1} for the FP16-split [W|Y] (sweep variant bit 2)
+  // separable nonlocal terms (FP64 sweep, pw_transmission_nonlocal): the particular
+  // solutions' mode-space values at each slice's left (nl_fa) and right (nl_fb) edge,
+  // [x_off + q][alpha][n] per point (zero in the electrodes); their unit-coefficient
+  // responses are carried as right-hand-side columns nl_c0 .. nl_c0 + nl_m - 1
+  const zc *nl_fa, *nl_fb;
+  int nl_m, nl_c0;
 };
 
 // 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and
@@ -175,6 +183,8 @@ struct GradArgs {
   zc *tmp;               // per point 2n x nc
   const int *status;
   int n, N, nc, mirror;
+  const zc *nl_fa;       // null, or the particular solutions' left-edge values (as in SweepArgs):
+  int nl_m, nl_c0;       //   columns nl_c0.. get b_p = Q a_q + P (e_q b_q + fa_q)
 };
 
 // Accumulation of the adjoint's eigenbasis matrices and their folding
@@ -195,12 +205,46 @@ struct GammaArgs {
 // and the carry and set the incident a_0 first; the carry links calls that
 // cover consecutive ranges from the right)
 cudaError_t launch_grad_backward(const GradArgs &g, int npts, cudaStream_t s, int p_hi, int p_lo, bool init);
-cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, cudaStream_t s);
-cudaError_t launch_grad_fold(const GammaArgs &h, int slot, const zc *U, zc *T1, const int *mn, int Dm,
+// Gamma_p and its fold onto the Fourier-table grid for the device slices
+// p0 .. p0 + cnt - 1 (1-based) of k-set `slot`; Gam and T1 hold cnt matrices
+cudaError_t launch_grad_gamma(const GammaArgs &h, int slot, int p0, int cnt, cudaStream_t s);
+cudaError_t launch_grad_fold(const GammaArgs &h, int slot, int p0, int cnt, const zc *U, zc *T1, const int *mn, int Dm,
                              int Dn, cudaStream_t s);
 cudaError_t launch_grad_wells(const GammaArgs &h, const WellSet &w, const double *z_edges, const double *b,
                               double area, int Dm, int Dn, double *dV0, const double *rate, double *dshift,
                               cudaStream_t s);
+// separable nonlocal terms (pw_nonlocal.cu)
+constexpr int kNlMaxProj = 8;    // projectors
+constexpr int kNlMaxQuad = 32;   // Gauss-Legendre nodes per slice
+constexpr int kNlMaxOpen = 64;   // open channels of the left electrode
+struct NonlocalArgs {
+  const PointDesc *pts;
+  const double *En;      // kset slots [kset][q][n]
+  const double *dz;      // N+2
+  const double *zedge;   // N+1 slice edges z_0 .. z_N
+  const zc *V;           // [kset][p = 1..N][alpha][n]: U_p^H amp_alpha (the projectors in mode space)
+  const double *proj;    // per projector: tau_z, sigma, z_lo, z_hi
+  const double *gl;      // Gauss-Legendre nodes and weights on [-1, 1]: x[q], w[q]
+  int q;                 // nodes per slice
+  zc *FA, *FB, *HA, *HB; // [x_off + q][alpha][n] (FA, FB: the particular solutions' edge values;
+                         //   HA, HB: <W_beta| e^{ik(z - z_a)}>, <W_beta| e^{ik(z_b - z)}> per mode)
+  zc *PP;                // [x_off + q][beta][alpha]: <W_beta | U f_alpha> of slice q
+  const zc *Xa, *Xb;     // amplitudes of the stored sweep's backward pass (as in GradArgs)
+  const zc *D;           // m x m coupling, row-major D[beta * m + alpha]
+  double area;
+  const int *status;
+  double *T;             // caller output (by PointDesc.out)
+  zc *C;                 // caller output or null: [out][alpha][channel], m x n_open^L per point
+  int n, N, nc, m, c0, ks_N;
+};
+// V of one k-set slot: U_p^H amp_alpha for the device slices (grid N x m)
+cudaError_t launch_nl_project(const zc *U, zc *V, const int *mn_unused, const double *G, double kx, double ky,
+                              const double *tau_xy_sigma, double area, int n, int N, int m, cudaStream_t s);
+cudaError_t launch_nl_slice_terms(const NonlocalArgs &a, int npts, cudaStream_t s);
+cudaError_t launch_nl_solve(const NonlocalArgs &a, int npts, cudaStream_t s);
+// the source columns of one interface step (FP64 sweep): Tacc_src += Y fa_q + fb_p
+cudaError_t launch_nl_sources(const SweepArgs &a, int npts, int p, cudaStream_t s);
+
 cudaError_t launch_grad_leads(const GammaArgs &h, const zc *U_all, const double *G, zc *scr,
                               const double rate[2][2], double *out, cudaStream_t s);
 
@@ -237,6 +281,9 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
                                  cudaEvent_t wy0 = nullptr, cudaEvent_t wy1 = nullptr, int variant = 0);
 int sweep_batched_launches(int n, int precision, int variant);
 int sweep_variants(int precision);
+// the variants a batch times per N_G (the sweep's launch shapes; bit 4 only
+// changes the refinement)
+std::vector<int> sweep_variant_candidates(int precision);
 // FP64 refinement of an FP32 sweep that stored Z_p, u_p and the LU factors:
 // between min_iters and max_iters passes, stopping once every point's
 // estimated remaining error of a_{N+1} (c_i^2 / c_{i-1} from the relative

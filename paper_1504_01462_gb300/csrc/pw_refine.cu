@@ -322,15 +322,23 @@ __global__ void __launch_bounds__(NT) k_refine_fwd_b(RefineArgs a, int p) {
   }
   __syncthreads();
   if (p == N) {
-    // add the correction of a_{N+1}; record its size relative to a_{N+1}
+    // add the correction of a_{N+1}; record the size of the correction of t
+    // (the flux-weighted open block, the part T is made of) relative to t,
+    // with |t| taken as at least 1e-3: T below 1e-6 is judged absolutely
     zc *X = a.Xa + blk(a, d, N + 1);
+    const double *EL = a.En + (size_t)d.en_off * n;
+    const double *ER = EL + (size_t)(N + 1) * n;
     double dn = 0.0, xn = 0.0;
     for (int e = threadIdx.x; e < n * nc; e += NT) {
       const zc dx = carry[e];
       const zc x = cadd(X[e], dx);
       X[e] = x;
-      dn += cnorm2(dx);
-      xn += cnorm2(x);
+      const int i = e % n, j = e / n;
+      if (i < d.nR && j < d.nL) {
+        const double f2 = sqrt(d.E - ER[i]) / sqrt(d.E - EL[j]);
+        dn += f2 * cnorm2(dx);
+        xn += f2 * cnorm2(x);
+      }
     }
     for (int off = 16; off > 0; off >>= 1) {
       dn += __shfl_down_sync(0xffffffffu, dn, off);
@@ -343,7 +351,7 @@ __global__ void __launch_bounds__(NT) k_refine_fwd_b(RefineArgs a, int p) {
       double sd = 0.0, sx = 0.0;
       for (int w = 0; w < NT / 32; ++w) { sd += red[0][w]; sx += red[1][w]; }
       a.corr_prev[pt] = a.corr[pt];
-      a.corr[pt] = sx > 0.0 ? sqrt(sd / sx) : 0.0;
+      a.corr[pt] = sqrt(sd / fmax(sx, 1e-6));
     }
   }
 }
@@ -782,7 +790,7 @@ __global__ void __launch_bounds__(NT) k_refine_finish(RefineArgs a) {
     if (a.nopen) { a.nopen[2 * d.out] = d.nL; a.nopen[2 * d.out + 1] = d.nR; }
     const double c = a.corr[pt], cp = a.corr_prev[pt];
     const double rho = cp > 0.0 ? fmin(1.0, c / cp) : 1.0;
-    if (a.err) a.err[d.out] = rho * fabs(T - Tp) / fmax(T, 1e-300);
+    if (a.err) a.err[d.out] = rho * fabs(T - Tp) / fmax(T, 1e-6);   // absolute below T = 1e-6
   }
 }
 

@@ -452,19 +452,26 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
-// Diagonal block of the back substitution with BS_FB rows (FP32, the
-// tensor-core form): X_b = U_bb^{-1} X_b for BS_COLS right-hand-side columns
-// per CTA.  U_bb and the columns are staged in shared memory; each warp
-// solves four columns at once (lane r holds rows r, r+32, r+64, r+96; the
-// solved value of row s passes by shuffle from its lane), so every element of
-// U_bb read serves four columns and the four recurrences interleave.  With
-// 128-row blocks the update above each block (kb_bsupd_tc) has K = 128 and
-// there are four blocks instead of sixteen at N_G = 512.
-constexpr int BS_FB = 128, BS_COLS = 32, BS_THREADS = 256;
+// Diagonal 128-row block of the triangular solves of the tensor-core FP32
+// form: X_b <- U_bb^{-1} X_b (back substitution, UPPER) or X_b <- L_bb^{-1} X_b
+// (forward elimination, L unit lower), for BS_COLS right-hand-side columns per
+// CTA.  The block's triangle and the columns are staged in shared memory, the
+// triangle's loads batched eight per thread so that many are in flight; the
+// reciprocals of U's diagonal are formed once per CTA, so the recurrence
+// multiplies instead of dividing.  Each warp solves four columns at once (lane
+// r holds rows r, r+32, r+64, r+96; the solved value of row s passes by
+// shuffle from its lane), so every element of the triangle read serves four
+// columns and the four recurrences interleave.  With 128-row blocks the
+// updates beside each block (kb_bsupd_tc, kb_fsupd_tc) have K = 128 and there
+// are four blocks instead of sixteen at N_G = 512.
+constexpr int BS_FB = 128, BS_COLS = 64, BS_THREADS = 512;
 static_assert(BS_COLS == 4 * (BS_THREADS / 32), "four columns per warp");
-size_t bsdiag_big_smem() { return (size_t)BS_FB * BS_FB * sizeof(cc) + (size_t)BS_FB * BS_COLS * sizeof(cc); }
+size_t bsdiag_big_smem() {
+  return ((size_t)BS_FB * BS_FB + (size_t)BS_FB * BS_COLS + BS_FB) * sizeof(cc);
+}
 
-__global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int j0) {
+template <bool UPPER>
+__global__ void __launch_bounds__(BS_THREADS, 1) kb_diag_big(SweepArgs a, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.y;
   if (inactive(a, pt)) return;
@@ -474,16 +481,37 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
   if (cf >= nrhs) return;
   const int ncl = min(BS_COLS, nrhs - cf);
   cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
-  cc *Us = reinterpret_cast<cc *>(smraw);     // Us[r + c fb], the upper triangle of U_bb
-  cc *Xs = Us + (size_t)BS_FB * BS_FB;       // Xs[r + q fb], the block rows of column cf + q
-  for (int e = threadIdx.x; e < fb * fb; e += BS_THREADS) {
-    const int r = e % fb, c = e / fb;
-    Us[e] = r <= c ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
+  cc *Ts = reinterpret_cast<cc *>(smraw);    // Ts[r + c fb]: U's upper or L's strict lower triangle
+  cc *Xs = Ts + (size_t)BS_FB * BS_FB;      // Xs[r + q fb]: the block rows of column cf + q
+  cc *dinv = Xs + (size_t)BS_FB * BS_COLS;  // 1 / U_ss
+  constexpr int U8 = 8;
+  const int tt = fb * fb;
+  for (int e0 = threadIdx.x; e0 < tt; e0 += U8 * BS_THREADS) {
+    cc v[U8];
+#pragma unroll
+    for (int u = 0; u < U8; ++u) {
+      const int e = e0 + u * BS_THREADS, r = e % fb, c = e / fb;
+      const bool in = e < tt && (UPPER ? r <= c : r > c);
+      v[u] = in ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
+    }
+#pragma unroll
+    for (int u = 0; u < U8; ++u)
+      if (e0 + u * BS_THREADS < tt) Ts[e0 + u * BS_THREADS] = v[u];
   }
-  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
-    const int r = e % fb, q = e / fb;
-    Xs[e] = M[j0 + r + (size_t)(n + cf + q) * n];
+  const int tx = fb * ncl;
+  for (int e0 = threadIdx.x; e0 < tx; e0 += U8 * BS_THREADS) {
+    cc v[U8];
+#pragma unroll
+    for (int u = 0; u < U8; ++u) {
+      const int e = e0 + u * BS_THREADS, r = e % fb, q = e / fb;
+      v[u] = e < tx ? M[j0 + r + (size_t)(n + cf + q) * n] : czero<float>();
+    }
+#pragma unroll
+    for (int u = 0; u < U8; ++u)
+      if (e0 + u * BS_THREADS < tx) Xs[e0 + u * BS_THREADS] = v[u];
   }
+  if (UPPER)
+    for (int r = threadIdx.x; r < fb; r += BS_THREADS) dinv[r] = cinv(M[j0 + r + (size_t)(j0 + r) * n]);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q0 = 4 * warp;   // this warp's four columns
@@ -496,10 +524,13 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
         const int r = lane + 32 * t;
         x[c][t] = (q0 + c < ncl && r < fb) ? Xs[r + (q0 + c) * fb] : czero<float>();
       }
-    for (int sb = (fb - 1) >> 5; sb >= 0; --sb) {       // row slot of s, from the bottom
-      for (int sl = min(31, fb - 1 - 32 * sb); sl >= 0; --sl) {
+    const int nsb = (fb + 31) >> 5;
+    for (int k = 0; k < nsb; ++k) {
+      const int sb = UPPER ? nsb - 1 - k : k;     // row slot of s
+      const int cnt = min(32, fb - 32 * sb);
+      for (int m = 0; m < cnt; ++m) {
+        const int sl = UPPER ? cnt - 1 - m : m;
         const int s = 32 * sb + sl;
-        const cc ud = Us[s + s * fb];
         cc xs[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -507,8 +538,8 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
 #pragma unroll
           for (int t = 1; t < 4; ++t)
             if (t == sb) v = x[c][t];
-          if (lane == sl) {
-            v = cdiv(v, ud);
+          if (UPPER && lane == sl) {
+            v = cmul(v, dinv[s]);
 #pragma unroll
             for (int t = 0; t < 4; ++t)
               if (t == sb) x[c][t] = v;
@@ -518,8 +549,9 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int r = lane + 32 * t;
-          if (t <= sb && r < s) {
-            const cc u = Us[r + s * fb];
+          const bool live = UPPER ? (t <= sb && r < s) : (t >= sb && r > s && r < fb);
+          if (live) {
+            const cc u = Ts[r + s * fb];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
               x[c][t].re -= u.re * xs[c].re - u.im * xs[c].im;
@@ -538,7 +570,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
       }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
+  for (int e = threadIdx.x; e < tx; e += BS_THREADS) {
     const int r = e % fb, q = e / fb;
     M[j0 + r + (size_t)(n + cf + q) * n] = Xs[e];
   }
@@ -546,7 +578,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) kb_bsdiag_big(SweepArgs a, int 
 
 // The right-hand sides of the tensor-core FP32 form after the LU of W
 // (P W = L U): X <- P X (kb_rhs_perm), then X <- L^{-1} X by 128-row blocks
-// (kb_fsdiag_big on the diagonal blocks, kb_fsupd_tc below them), then the
+// (kb_diag_big<false> on the diagonal blocks, kb_fsupd_tc below them), then the
 // back substitution as before.  P applies the pivots in order: row j swaps
 // with piv[j] for j = 0 .. n-1.
 constexpr int RP_COLS = 16;   // right-hand-side columns per CTA of kb_rhs_perm
@@ -580,81 +612,6 @@ __global__ void __launch_bounds__(256) kb_rhs_perm(SweepArgs a) {
   for (int e = threadIdx.x; e < n * ncl; e += 256) {
     const int r = e % n, q = e / n;
     M[r + (size_t)(n + cf + q) * n] = S[perm[r] + q * n];
-  }
-}
-
-// X_b <- L_bb^{-1} X_b for one 128-row diagonal block (unit lower), the
-// schedule of kb_bsdiag_big run from the top.
-__global__ void __launch_bounds__(BS_THREADS, 1) kb_fsdiag_big(SweepArgs a, int j0) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int pt = blockIdx.y;
-  if (inactive(a, pt)) return;
-  const int n = a.n, ncols = 2 * n + a.nc, nrhs = ncols - n;
-  const int fb = min(BS_FB, n - j0);
-  const int cf = blockIdx.x * BS_COLS;
-  if (cf >= nrhs) return;
-  const int ncl = min(BS_COLS, nrhs - cf);
-  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
-  cc *Ls = reinterpret_cast<cc *>(smraw);     // Ls[r + c fb], the strict lower triangle of L_bb
-  cc *Xs = Ls + (size_t)BS_FB * BS_FB;
-  for (int e = threadIdx.x; e < fb * fb; e += BS_THREADS) {
-    const int r = e % fb, c = e / fb;
-    Ls[e] = r > c ? M[j0 + r + (size_t)(j0 + c) * n] : czero<float>();
-  }
-  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
-    const int r = e % fb, q = e / fb;
-    Xs[e] = M[j0 + r + (size_t)(n + cf + q) * n];
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q0 = 4 * warp;
-  if (q0 < ncl) {
-    cc x[4][4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int r = lane + 32 * t;
-        x[c][t] = (q0 + c < ncl && r < fb) ? Xs[r + (q0 + c) * fb] : czero<float>();
-      }
-    for (int sb = 0; 32 * sb < fb; ++sb) {
-      for (int sl = 0; sl < 32 && 32 * sb + sl < fb; ++sl) {
-        const int s = 32 * sb + sl;
-        cc xs[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          cc v = x[c][0];
-#pragma unroll
-          for (int t = 1; t < 4; ++t)
-            if (t == sb) v = x[c][t];
-          xs[c] = mkc<float>(__shfl_sync(0xffffffffu, v.re, sl), __shfl_sync(0xffffffffu, v.im, sl));
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int r = lane + 32 * t;
-          if (t >= sb && r > s && r < fb) {
-            const cc l = Ls[r + s * fb];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              x[c][t].re -= l.re * xs[c].re - l.im * xs[c].im;
-              x[c][t].im -= l.re * xs[c].im + l.im * xs[c].re;
-            }
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int r = lane + 32 * t;
-        if (q0 + c < ncl && r < fb) Xs[r + (q0 + c) * fb] = x[c][t];
-      }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < fb * ncl; e += BS_THREADS) {
-    const int r = e % fb, q = e / fb;
-    M[j0 + r + (size_t)(n + cf + q) * n] = Xs[e];
   }
 }
 
@@ -858,7 +815,7 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
 
 template <typename T, int BT>
 static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t s, cudaEvent_t wy0,
-                              cudaEvent_t wy1, bool tensor_core, bool f16 = false) {
+                              cudaEvent_t wy1, bool tensor_core, bool f16 = false, bool big = false) {
   SweepArgs a = a0;
   a.p = p;
   const int n = a.n, ncols = 2 * n + a.nc;
@@ -890,9 +847,19 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
       PW_TIMED(KK_WY, s, kb_wy<T, BT><<<dim3(tiles(n, 2 * n, BM, BN), npts), BT, wsm, s>>>(a, p));
     if (wy1) cudaEventRecord(wy1, s);
   }
-  // tensor-core FP32 form: LAPACK-ordered pivots, the LU of W alone, then the
-  // right-hand sides eliminated in 128-row blocks (see kb_rhs_perm)
-  const bool lapack = std::is_same<T, float>::value && tensor_core;
+  // separable nonlocal terms (FP64 form): the source columns of Tacc take
+  // Y fa_q + fb_p before the solve
+  if constexpr (std::is_same<T, double>::value) {
+    if (a.nl_m > 0) {
+      const cudaError_t e = launch_nl_sources(a, npts, p, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  // tensor-core FP32 form with 128-row blocks (variant bit 3): LAPACK-ordered
+  // pivots, the LU of W alone, then the right-hand sides eliminated in 128-row
+  // blocks (see kb_rhs_perm); otherwise each panel's swaps and L11 solve reach
+  // the right-hand sides too and the trailing updates carry them along
+  const bool lapack = std::is_same<T, float>::value && tensor_core && big;
   a.lapack_piv = lapack ? 1 : 0;
   const int ucols = lapack ? n : ncols;   // columns the LU updates
   for (int j0 = 0; j0 < n; j0 += NB) {
@@ -903,7 +870,7 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
       if (blocks > 0) PW_TIMED(KK_PANEL_APPLY, s, kb_panel_apply<T, BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0));
     }
     if (c0 < n) {
-      if (lapack)
+      if (std::is_same<T, float>::value && tensor_core)
         PW_TIMED(KK_TRAIL, s,
                  kb_trail_tc<<<dim3(tiles(n - c0, ucols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
                                tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0));
@@ -916,7 +883,7 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     PW_TIMED(KK_RHS_PERM, s,
              kb_rhs_perm<<<dim3((ncols - n + RP_COLS - 1) / RP_COLS, npts), 256, rhs_perm_smem(n), s>>>(a));
     for (int j0 = 0; j0 < n; j0 += BS_FB) {
-      PW_TIMED(KK_FSDIAG, s, kb_fsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0));
+      PW_TIMED(KK_FSDIAG, s, kb_diag_big<false><<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0));
       const int c1 = j0 + std::min(BS_FB, n - j0);
       if (c1 < n)
         PW_TIMED(KK_FSUPD, s,
@@ -925,11 +892,11 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     }
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
-  if (std::is_same<T, float>::value && tensor_core) {
+  if (lapack) {
     // 128-row blocks: four diagonal solves and three K = 128 updates at N_G = 512
     const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
     for (int j0 = ((n - 1) / BS_FB) * BS_FB; j0 >= 0; j0 -= BS_FB) {
-      PW_TIMED(KK_BSDIAG, s, kb_bsdiag_big<<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0));
+      PW_TIMED(KK_BSDIAG, s, kb_diag_big<true><<<dim3(cgroups, npts), BS_THREADS, bsdiag_big_smem(), s>>>(a, j0));
       if (j0 > 0)
         PW_TIMED(KK_BSUPD, s,
                  kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
@@ -938,8 +905,14 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   } else {
     for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
       PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0));
-      if (j0 > 0)
-        PW_TIMED(KK_BSUPD, s, kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0));
+      if (j0 > 0) {
+        if (std::is_same<T, float>::value && tensor_core)
+          PW_TIMED(KK_BSUPD, s,
+                   kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                                 tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, NB));
+        else
+          PW_TIMED(KK_BSUPD, s, kb_bsupd<T, BT><<<dim3(tiles(j0, ncols - n, BM, BN), npts), BT, gsm, s>>>(a, j0));
+      }
     }
   }
   PW_TIMED(KK_FINISH, s, kb_finish<T><<<dim3(FINISH_BLOCKS, npts), VT, 0, s>>>(a, p));
@@ -984,9 +957,9 @@ cudaError_t prepare_sweep_batched(int n, int precision, int variant) {
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_bsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
-    e = cudaFuncSetAttribute(kb_bsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
+    e = cudaFuncSetAttribute(kb_diag_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
   if (e == cudaSuccess && (variant & 2))
-    e = cudaFuncSetAttribute(kb_fsdiag_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
+    e = cudaFuncSetAttribute(kb_diag_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsdiag_big_smem());
   if (e == cudaSuccess && (variant & 2))
     e = cudaFuncSetAttribute(kb_fsupd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::cg_smem_bytes<RMW_TN>());
   if (e == cudaSuccess && (variant & 2))
@@ -1003,16 +976,22 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
     return (variant & 1) ? sweep_step<double, 512>(a, npts, p, s, wy0, wy1, false)
                          : sweep_step<double, 256>(a, npts, p, s, wy0, wy1, false);
   const bool f16 = (variant & 4) != 0;   // FP16 split for the paired [W|Y]
-  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore, f16)
-                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore, f16);
+  const bool big = (variant & 8) != 0;   // LAPACK-ordered pivots, 128-row triangular blocks
+  return (variant & 1) ? sweep_step<float, 512>(a, npts, p, s, wy0, wy1, tcore, f16, big)
+                       : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore, f16, big);
 }
 
-int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 8; }
+int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 64; }
+
+std::vector<int> sweep_variant_candidates(int precision) {
+  if (precision == PW_FP64) return {0, 1};
+  return {2, 3, 6, 10, 14};
+}
 
 int sweep_batched_launches(int n, int precision, int variant) {
   const int NB = Tile<float, 256>::NB;
   const int panels = (n + NB - 1) / NB;
-  const bool fp32 = precision != PW_FP64, tensor = fp32 && (variant & 2);
+  const bool fp32 = precision != PW_FP64, tensor = fp32 && (variant & 2) && (variant & 8);
   // vectors, [W|Y], finish; per panel: factorisation, trailing update (not
   // after the last), the FP32 form's right-hand apply; the back substitution:
   // a diagonal solve per block and an update above every block but the first

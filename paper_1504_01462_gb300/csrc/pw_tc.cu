@@ -149,9 +149,50 @@ __global__ void __launch_bounds__(128) k_tc_selftest16(const float *A, const flo
   if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
+// The bounded completion wait of the tensor-core kernels on an mbarrier that
+// nothing completes (no MMA is issued and, unless `signal`, nobody arrives):
+// the wait gives up after `polls` polls, the CTA frees the tensor memory it
+// holds and reports through out[0] (1: the wait ran out, 0: it completed).
+// With signal != 0 thread 0 arrives first, so the same wait completes.
+__global__ void __launch_bounds__(128) k_wait_selftest(uint32_t polls, int signal, int *out) {
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::tmem_alloc(&slot, 32);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = slot;
+  if (signal && tid == 0) tc::mbar_arrive(&mbar);
+  const bool done = tc::mbar_wait(&mbar, 0, polls);
+  const bool all = __syncthreads_and(done) != 0;
+  if (tid == 0) out[0] = all ? 0 : 1;
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
 }  // namespace
 
 }  // namespace pw
+
+extern "C" pw_status pw_selftest_bounded_wait(int polls, int signal) {
+  using namespace pw;
+  if (polls < 1) return PW_EINVAL;
+  int *d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return PW_ENOMEM;
+  int h = -1;
+  cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 128>>>((uint32_t)polls, signal, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return PW_ECUDA;
+  return h == 0 ? PW_OK : h == 1 ? PW_ETIMEOUT : PW_ECUDA;
+}
 
 extern "C" pw_status pw_selftest_f16_split(double *rel_err) {
   if (!rel_err) return PW_EINVAL;

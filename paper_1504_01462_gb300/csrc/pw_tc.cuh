@@ -136,6 +136,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// One arrival on the mbarrier by this thread (no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
 // Bounded wait for the phase with the given parity; false when it ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_polls = 1u << 22) {
   for (uint32_t i = 0; i < max_polls; ++i) {

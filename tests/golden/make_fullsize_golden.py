@@ -6,13 +6,17 @@ the oracle cannot finish inside a test run:
                         (the call the benchmark times), App. C / Sec. II B
   junction401.json      T of four seeded points of the N_G = 401 (whole
                         shells, E_cut = 29.34 Ry), 240-slice AB junction
+  uneven96.json         T of eight of the first 96 instances of the uneven
+                        batch (the six with the least work n^3 (N_s + 1) and
+                        the two with the least work among those of N_G >= 256)
 
 Only oracle/ computes (Eq. loc eigenmodes, Eqs. transfer and scatter, Eq.
 recurrence applied left to right, the flux-normalised t of App. C).  Each file
 is rewritten after every point, so an interrupted run resumes where it
 stopped.  Run from the repository root:
     python -m tests.golden.make_fullsize_golden junction512_k5
-    python -m tests.golden.make_fullsize_golden junction401"""
+    python -m tests.golden.make_fullsize_golden junction401
+    python -m tests.golden.make_fullsize_golden uneven96"""
 import json
 import os
 import sys
@@ -21,7 +25,7 @@ import time
 import numpy as np
 
 from oracle import pw_oracle as O
-from synthetic import junction, junction_ecut_for
+from synthetic import junction, junction_ecut_for, uneven_batch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -109,6 +113,37 @@ def junction401():
         print(f"junction401 point {j}: T = {T:.15g} nopen {nop} ({time.time() - t0:.0f} s)", flush=True)
 
 
+def uneven96_picks(insts):
+    """Indices (into the first 96 instances) of the stored uneven points."""
+    work = [float(x.ng_exact) ** 3 * (x.n_slices + 1) for x in insts]
+    order = sorted(range(len(insts)), key=lambda i: work[i])
+    small = order[:6]
+    big = [i for i in order if insts[i].ng_exact >= 256 and i not in small][:2]
+    return sorted(small + big)
+
+
+def uneven96():
+    path = os.path.join(HERE, "uneven96.json")
+    insts = uneven_batch(2048)[:96]
+    picks = uneven96_picks(insts)
+    doc = _load(path) or {
+        "what": "oracle T of instances of uneven_batch(2048)[:96] (one (E, k_par) point each)",
+        "index": picks, "ng": [insts[i].ng_exact for i in picks], "slices": [insts[i].n_slices for i in picks],
+        "T": [None] * len(picks), "nopen": [None] * len(picks)}
+    for j, i in enumerate(picks):
+        if doc["T"][j] is not None:
+            continue
+        t0 = time.time()
+        x = insts[i]
+        model = O.Model(x)
+        modes = model.modes(x.kpar[0])
+        T, nop = _point(model, modes, float(x.energies[0]))
+        doc["T"][j], doc["nopen"][j] = T, nop
+        _save(path, doc)
+        print(f"uneven96 instance {i} (N_G {x.ng_exact}, {x.n_slices} slices): T = {T:.15g} "
+              f"({time.time() - t0:.0f} s)", flush=True)
+
+
 if __name__ == "__main__":
     for what in sys.argv[1:] or ["junction401", "junction512_k5"]:
-        {"junction512_k5": junction512_k5, "junction401": junction401}[what]()
+        {"junction512_k5": junction512_k5, "junction401": junction401, "uneven96": uneven96}[what]()

@@ -100,3 +100,35 @@ def test_batch_sampled_uneven_instances(pw):
     T, err, stats = _run(pw, pick, precision=1, refine_iters=4)
     assert np.all(rel_T(T, ref) <= TOL_MIXED), (T, ref)
     assert stats["chunks"] == 2
+
+
+def test_batch_first_96_uneven_instances_against_stored_oracle(pw):
+    """The first 96 of the 2048 uneven instances (N_G 128..768, 60..400
+    slices) in one batch call, mixed form with refinement: eight of them
+    against oracle values stored by tests/golden/make_fullsize_golden.py
+    (1e-8 relative on T), every instance finite and within its channel
+    bounds."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "uneven96.json")
+    with open(path) as f:
+        gold = json.load(f)
+    insts = uneven_batch(2048)[:96]
+    E, k = _points(insts)
+    T = torch.zeros(96, dtype=torch.float64, device="cuda")
+    nop = torch.zeros((96, 2), dtype=torch.int32, device="cuda")
+    err = torch.zeros(96, dtype=torch.float64, device="cuda")
+    with pw.Batch.from_instances(insts, 1, 4) as b:
+        b.transmission(E, k, T, nop, err, allow_threshold=True)
+    torch.cuda.synchronize()
+    T, nop, err = T.cpu().numpy(), nop.cpu().numpy(), err.cpu().numpy()
+    ok = np.isfinite(T)
+    assert ok.sum() >= 94
+    assert np.all(T[ok] >= -1e-9) and np.all(T[ok] <= np.minimum(nop[ok, 0], nop[ok, 1]) + 1e-9)
+    assert np.all(err[ok] < 1e-8)
+    idx = np.array(gold["index"])
+    have = np.array([t is not None for t in gold["T"]])
+    assert have.sum() >= 4
+    ref = np.array([t for t in gold["T"] if t is not None])
+    assert np.all(rel_T(T[idx[have]], ref) < TOL_MIXED), (T[idx[have]], ref)
+    assert np.array_equal(nop[idx[have]], np.array([x for x in gold["nopen"] if x is not None]))

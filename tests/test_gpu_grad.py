@@ -196,13 +196,13 @@ def test_grad_checkpointed_recomputation_equals_stored_sweep(pw, interval):
 
 
 def test_grad_memory_grows_as_sqrt_of_slices(pw):
-    """Workspace of pw_grad for one point at 80 and 320 slices (N_G = 128):
-    with the default segments it grows by about sqrt(4) = 2 (the stores are
-    ~2 sqrt(N+1) n^2; only the n x n_c amplitudes grow linearly), storing
-    every interface grows it by about 4."""
+    """Workspace of pw_grad for one point at 80 and 320 slices (N_G = 256):
+    with the default segments it grows by about sqrt(4) = 2 (the stores and
+    the gradient's slice chunks are ~4 sqrt(N+1) n^2; only the n x n_c
+    amplitudes grow linearly), storing every interface grows it by about 4."""
     out = {}
     for ns in (80, 320):
-        inst = junction(ng=128, n_slices=ns, n_e=1, n_k=1)
+        inst = junction(ng=256, n_slices=ns, n_e=1, n_k=1)
         for mode, interval in (("ckpt", 0), ("full", ns + 1)):
             with pw.Context.from_instance(inst) as ctx:
                 ctx.set_grad_checkpoint(interval)

@@ -340,14 +340,22 @@ def test_transmission_mixed_refined_one_kpar(pw):
 
 
 @pytest.mark.parametrize("ng,nsl", [(128, 40), (512, 6)])
-def test_transmission_mixed_sliced_residual(pw, ng, nsl):
+@pytest.mark.parametrize("variant", [2, 18, 26])
+def test_transmission_mixed_sliced_residual(pw, ng, nsl, variant):
     """Points of one k_par with a basis that is a multiple of 4 and at most 512:
-    the refinement's residual products O y run as exact BF16 slice products on
-    the tensor cores.  N_G = 128 spans two row tiles and a ragged column tile;
-    N_G = 512 puts 1024 terms in each exact sum."""
+    with variant bit 4 the refinement's residual products O y run as exact
+    BF16 slice products on the tensor cores (bit 3 adds the 128-row LU
+    blocks), without it on the CUDA cores in double-float.  N_G = 128 spans
+    two row tiles and a ragged column tile; N_G = 512 puts 1024 terms in each
+    exact sum."""
     inst = junction(ng=ng, n_slices=nsl, n_e=4, n_k=1)
     ref = O.transmission(inst)
-    got, _, _ = _gpu_T(pw, inst, 1)
+    T = _dev(len(inst.energies), torch.float64)
+    with pw.Context.from_instance(inst, precision=1) as ctx:
+        ctx.set_sweep_variant(variant)
+        ctx.transmission(inst.energies, inst.kpar, T)
+        torch.cuda.synchronize()
+    got = T.cpu().numpy()
     assert np.all(_rel(got, ref) < TOL_MIXED), (got, ref)
 
 
