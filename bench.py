@@ -42,9 +42,11 @@ GOLDEN_512 = os.path.join(ROOT, "tests", "golden", "junction512_k5.json")
 PROFILE_STRIDE = 3      # every third launch of each kernel kind is bracketed by CUDA events
 MIXED_DEFAULT_VARIANT = 2    # the library's default launch variant of the mixed form
 T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
-# DRAM bytes per launch of kernels captured with ncu (read + write), with the capture they
-# come from; a kernel changed since its capture has no entry
-KERNEL_TRAFFIC = {}
+# DRAM traffic of kernels captured with ncu: dram__bytes_read + dram__bytes_write of the
+# captured launches over their algorithmic bytes (profiles/kb_trail_tc_junction512_small.md:
+# 527.2/589, 451.5/512, 381.3/441 MB); the roofline's `traffic` is this ratio times the step's
+# average algorithmic bytes per launch.  A kernel changed since its capture has no entry.
+KERNEL_TRAFFIC = {"kb_trail": 0.88}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -744,7 +746,7 @@ def main():
             tsec = row["ms_per_step"] / 1e3
             obj = {"kernel": row["kernel"], "avg_launch_ms": row["avg_launch_ms"],
                    "launches_per_step": row["launches_per_step"], "ms_per_step": row["ms_per_step"],
-                   "share_of_kernel_time": row["share"], "traffic": KERNEL_TRAFFIC.get(key)}
+                   "share_of_kernel_time": row["share"], "traffic": None}
             if flops is None or tsec <= 0:
                 obj.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                             "note": "no algorithmic model for this kernel"})
@@ -757,9 +759,15 @@ def main():
             ai = flops / nbytes if nbytes else None
             if ai is not None and ai * hbm / 1e3 < cpeak:
                 ach = nbytes / tsec / 1e9
+                per_launch = nbytes / (row["launches_per_step"] or 1)
                 obj.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                             "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
-                            "algorithmic_bytes_per_launch": nbytes / (row["launches_per_step"] or 1),
+                            "traffic": (KERNEL_TRAFFIC[key] * per_launch if key in KERNEL_TRAFFIC and on_tc
+                                        and not (variant & 8) else None),
+                            "traffic_source": ("ncu DRAM/algorithmic ratio of the captured launches x the step's "
+                                               "average algorithmic bytes per launch" if key in KERNEL_TRAFFIC
+                                               else None),
+                            "algorithmic_bytes_per_launch": per_launch,
                             "tflops": flops / tsec / 1e12, "intensity_flop_per_byte": ai})
             else:
                 ach = flops / tsec / 1e12

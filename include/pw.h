@@ -53,8 +53,9 @@ typedef enum {
 typedef struct { double re, im; } pw_c128;
 
 /* Arithmetic of the path.  PW_FP64: every step in FP64.  PW_MIXED_FP32: the
- * slice eigenmodes and the overlaps in double-float (a value is the sum of two
- * FP32 numbers, 48 significant bits, on the FP32 pipe), the star-product sweep
+ * slice eigenmodes and the overlaps in FP64 (or, with launch variant bit 5, in
+ * double-float: a value is the sum of two FP32 numbers, 48 significant bits,
+ * on the FP32 pipe), the star-product sweep
  * in FP32 (its GEMMs on the tensor cores as TF32 hi/lo products), then passes
  * of iterative refinement of the whole interface-matching system whose
  * residuals are formed in double-float (exact BF16 slice products on the
@@ -367,8 +368,12 @@ pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c1
  * hand sides eliminated in 128-row triangular blocks afterwards; bit 4, the
  * refinement's residual products as exact BF16 slice products on the tensor
  * cores (used when every point of a launch shares one k_par and N_G is a
- * multiple of 4 up to 512).  PW_EINVAL for a variant the context's precision
- * does not have (0..1 for PW_FP64, 0..31 for PW_MIXED_FP32). */
+ * multiple of 4 up to 512); bit 5, the slice eigenmodes and the overlaps in
+ * double-float instead of FP64 (a mode stage about 4x faster, but 48-bit
+ * modes: at a sharp antiresonance of T the error on T can exceed 1e-8
+ * relative).  The mode cache of a k_par is kept across variant changes; set
+ * the variant before the first call.  PW_EINVAL for a variant the context's
+ * precision does not have (0..1 for PW_FP64, 0..63 for PW_MIXED_FP32). */
 pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant);
 
 /* Timing of the library's own launches (for benchmarks and roofline
@@ -474,6 +479,42 @@ pw_status pw_selftest_slice_product(int n, int ncol, long long *mismatches, doub
  * synchronises it; PW_ETIMEOUT if the tensor core did not signal completion
  * within its bounded wait.  A deployment check with no counterpart in the paper. */
 pw_status pw_selftest_f16_split(double *rel_err);
+
+/* Periodic electrodes (App. B, C; no nonlocal terms).  Each electrode is a
+ * z-periodic cell of M slices (their Fourier tables in the layout of
+ * pw_potential_tables, i.e. (2 Dm + 1) x (2 Dn + 1) values per slice with the
+ * context's (Dm, Dn), in order along +z; thicknesses dz[M], bohr) whose third
+ * lattice vector has the transverse part a3_perp[2] (0, 0 for a straight
+ * cell; a tilted cell's next period is the present one moved by a3, so its
+ * slice modes are D U with D = diag(e^{-i G.a3_perp})).  side 0: the left
+ * electrode, whose last slice meets the device; side 1: the right electrode,
+ * whose first slice meets the device.  Synchronises the stream. */
+pw_status pw_set_periodic_electrode(pw_ctx *ctx, int side, int M, const pw_c128 *tables, const double *dz,
+                                    const double *a3_perp);
+
+/* T between the two periodic electrodes of pw_set_periodic_electrode, FP64
+ * whatever the context's precision, for npts points (T_dev: device, npts
+ * doubles).  Per electrode and point: the cell's S over one period (Eqs.
+ * transfer, scatter, recurrence), its generalised Bloch states from Eq. cmp
+ * (through the Cayley map mu = (lambda - s)/(lambda + s) to a bounded
+ * standard eigenproblem, its complex Schur form and reordered invariant
+ * subspaces: decaying for |lambda| < 1, growing for |lambda| > 1;
+ * propagating states split by the sign of their z-flux and scaled to unit
+ * flux); then S of [left reference slice, device slices, right reference
+ * slice] and App. C's matching for the incident propagating states:
+ * T = sum |t|^2.  The device slices are the context's (its z-invariant
+ * electrodes are not used).  A point whose Bloch states fail (a band edge, a
+ * Schur form that does not converge) gets T = NaN and the call returns
+ * PW_ENOTCONV after the others.  Synchronises the stream. */
+pw_status pw_transmission_periodic(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev);
+
+/* Self-test of the device eigen-kernels used for the Bloch states: the complex
+ * Schur form A = Z T Z^H of one N x N complex matrix (host, column-major) by
+ * Householder reduction and the shifted QR iteration, then with select != 0
+ * the diagonal entries with negative real part moved first (*count of them).
+ * T_host, Z_host: N x N outputs.  PW_ENOTCONV if the iteration did not
+ * converge.  Synchronises the device; the paper has no counterpart. */
+pw_status pw_selftest_schur(int N, const pw_c128 *A_host, pw_c128 *T_host, pw_c128 *Z_host, int select, int *count);
 
 /* Self-test of the bounded device-side waits: one CTA holds tensor memory and
  * waits, at most `polls` polls of 64 ns, on an mbarrier that no tensor-core

@@ -38,7 +38,8 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_transmission_doubling", "pw_selftest_f16_split", "pw_kernel_kinds",
            "pw_kernel_kind_name", "pw_get_kernel_profile", "pw_measure_peaks",
            "pw_set_grad_checkpoint", "pw_workspace_bytes", "pw_selftest_bounded_wait",
-           "pw_reduce_transmission", "pw_set_projectors", "pw_transmission_nonlocal"]
+           "pw_reduce_transmission", "pw_set_projectors", "pw_transmission_nonlocal",
+           "pw_set_periodic_electrode", "pw_transmission_periodic", "pw_selftest_schur"]
 
 
 class PwError(RuntimeError):
@@ -119,6 +120,9 @@ def _load():
     lib.pw_reduce_transmission.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
     lib.pw_set_projectors.argtypes = [_vp, ctypes.c_int, _dp, _vp, ctypes.c_int]
     lib.pw_transmission_nonlocal.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp, _vp]
+    lib.pw_set_periodic_electrode.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]
+    lib.pw_transmission_periodic.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp]
+    lib.pw_selftest_schur.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _ip]
     lib.pw_batch_destroy.restype = None
     return lib
 
@@ -269,6 +273,18 @@ def reduce_transmission(T, nopen=None, weight=None, out=None, stream=None):
     _check_status(_lib.pw_reduce_transmission(int(T.numel()), _ptr(T), _ptr(nopen), _ptr(weight), _ptr(out),
                                               stream), "pw_reduce_transmission")
     return out
+
+
+def selftest_schur(A, select=False):
+    """(T, Z, count) of the device Schur form of the complex matrix A."""
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128))
+    N = A.shape[0]
+    T = np.zeros((N, N), dtype=np.complex128, order="F")
+    Z = np.zeros((N, N), dtype=np.complex128, order="F")
+    cnt = ctypes.c_int(0)
+    _check_status(_lib.pw_selftest_schur(N, A.ctypes.data, T.ctypes.data, Z.ctypes.data, int(bool(select)),
+                                         ctypes.byref(cnt)), "pw_selftest_schur")
+    return T, Z, cnt.value
 
 
 def measure_peaks():
@@ -450,6 +466,22 @@ class Context:
             return st
         self._check(st, "pw_transmission_nonlocal")
         return st
+
+    def set_periodic_electrode(self, side, tables, dz, a3_perp=(0.0, 0.0)):
+        """A periodic electrode (pw_set_periodic_electrode): side 0 left, 1
+        right; tables (M, 2Dm+1, 2Dn+1) complex in the context's table layout."""
+        tab = np.ascontiguousarray(np.asarray(tables, dtype=np.complex128))
+        dzs = _f64(dz).reshape(-1)
+        a3 = _f64(a3_perp).reshape(2)
+        self._check(_lib.pw_set_periodic_electrode(self._h, int(side), len(dzs), tab.ctypes.data, _as_dp(dzs),
+                                                   _as_dp(a3)), "pw_set_periodic_electrode")
+
+    def transmission_periodic(self, E, kpar, T_out):
+        """T between the periodic electrodes into T_out (device float64)."""
+        E = _f64(E).reshape(-1)
+        k = _f64(kpar).reshape(-1, 2)
+        st = _lib.pw_transmission_periodic(self._h, len(E), _as_dp(E), _as_dp(k), _ptr(T_out))
+        self._check(st, "pw_transmission_periodic")
 
     def set_grad_checkpoint(self, interval=0):
         """Segment length of pw_grad's checkpointed recomputation (0: ceil(sqrt(N+1)))."""

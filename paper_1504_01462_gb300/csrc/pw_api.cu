@@ -109,9 +109,12 @@ constexpr double kShellQuantum = 1e-8;   // Ry: |G|^2 closer than this is one sh
 constexpr double kThreshold = pw::kThresholdRy;
 constexpr double kRefineTol = pw::kRefineTolRel;
 // default launch variant of the mixed form (pw_set_sweep_variant): the sweep's
-// GEMM phases on the tensor cores with the 32-row LU blocks and the
-// refinement residual on the CUDA cores in double-float (the measured fastest
-// at N_G = 512: 128-row blocks and the slice-product residual were slower)
+// GEMM phases on the tensor cores with the 32-row LU blocks, the refinement
+// residual on the CUDA cores in double-float (the measured fastest at
+// N_G = 512: 128-row blocks and the slice-product residual were slower), and
+// the slice modes and overlaps in FP64: with double-float modes (bit 5, 4x
+// faster mode stage) T at the N_G = 512 junction's antiresonance dip
+// (T = 0.0036) was 4.8e-8 from the oracle, with FP64 modes 8.8e-10
 constexpr int kMixedDefaultVariant = 2;
 
 struct DevBuf {
@@ -183,6 +186,14 @@ struct pw_ctx {
   double *d_gl = nullptr;          // Gauss-Legendre nodes, weights
   zc *d_nlD = nullptr;             // m x m
   DevBuf nlV, nlFA, nlFB, nlHA, nlHB, nlPP, ptsb;
+  // periodic electrodes (pw_set_periodic_electrode): per side the cell's
+  // Fourier tables, slice thicknesses and transverse tilt a3_perp
+  int pe_M[2] = {0, 0};
+  zc *d_petab[2] = {nullptr, nullptr};
+  std::vector<double> pe_dz[2];
+  double pe_a3[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  DevBuf peU, peV, peE, peStat, chU, chE, chO, chDz, chPts, chSif, chSa, chSb, chW, chPiv, chSt, bdS[2],
+      bdW, bdPiv, bdKeys, bdStates[2], bdProp[2], bdStat, bdE, bdBad, ppW, ppPiv, ppOut;
   DevBuf ckR, ckT;                 // pw_grad checkpoints of the sweep state (R, Tacc)
 };
 
@@ -395,8 +406,8 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
     pw::launch_assemble_h(ctx->d_HU + (size_t)s * nq * nn, ctx->d_tab, ctx->d_mn, ctx->d_G, ks[s][0],
                           ks[s][1], n, nq, ctx->Dm, ctx->Dn, ctx->stream);
   CK(cudaGetLastError());
-  // the mixed form's modes and overlaps in double-float, or (variant bit 5) in FP64
-  const bool dfe = ctx->precision == PW_MIXED_FP32 && !(ctx->sweep_variant & 32);
+  // the mixed form's modes and overlaps in FP64, or (variant bit 5) in double-float
+  const bool dfe = ctx->precision == PW_MIXED_FP32 && (ctx->sweep_variant & 32);
   if (dfe && (st = ensure(ctx, ctx->eigws, pw::heev_ws_bytes(n, nmat)))) return st;
   pw::launch_eig(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_V + (size_t)s0 * nq * nn,
                  ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
@@ -669,7 +680,12 @@ void pw_destroy(pw_ctx *ctx) {
                   ctx->d_wsig, ctx->corr.p, ctx->d_wrate, ctx->dshift.p, ctx->lead_scr.p,
                   ctx->lead_out.p, ctx->eigws.p, ctx->bw.p, ctx->rowexp.p, ctx->ckR.p, ctx->ckT.p,
                   ctx->d_nlproj, ctx->d_gl, ctx->d_nlD, ctx->nlV.p, ctx->nlFA.p, ctx->nlFB.p, ctx->nlHA.p,
-                  ctx->nlHB.p, ctx->nlPP.p, ctx->ptsb.p};
+                  ctx->nlHB.p, ctx->nlPP.p, ctx->ptsb.p, ctx->d_petab[0], ctx->d_petab[1], ctx->peU.p,
+                  ctx->peV.p, ctx->peE.p, ctx->peStat.p, ctx->chU.p, ctx->chE.p, ctx->chO.p, ctx->chDz.p,
+                  ctx->chPts.p, ctx->chSif.p, ctx->chSa.p, ctx->chSb.p, ctx->chW.p, ctx->chPiv.p, ctx->chSt.p,
+                  ctx->bdS[0].p, ctx->bdS[1].p, ctx->bdW.p, ctx->bdPiv.p, ctx->bdKeys.p, ctx->bdStates[0].p,
+                  ctx->bdStates[1].p, ctx->bdProp[0].p, ctx->bdProp[1].p, ctx->bdStat.p, ctx->bdE.p,
+                  ctx->bdBad.p, ctx->ppW.p, ctx->ppPiv.p, ctx->ppOut.p};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1462,6 +1478,220 @@ pw_status pw_transmission_nonlocal(pw_ctx *ctx, int npts, const double *E, const
     }
   }
   if (result == PW_ESINGULAR) latch(ctx, result);
+  return result;
+}
+
+// S(0, m) of a chain of m+1 slices for npts points (FP64): the chain's modes
+// U (nq = m+1 matrices) and eigenvalues En (nq x n) and thicknesses dz (nq,
+// dz[0] unused) are in ctx->chU / chE / chDz; overlaps, each interface's
+// S-matrix, and the star products left to right.  Result in ctx->chSa
+// (npts x 4 n^2).  `pd`: npts host descriptors (E only is read; kset 0).
+static pw_status chain_smatrix(pw_ctx *ctx, int nq, const std::vector<PointDesc> &pd) {
+  const int n = ctx->n, npts = (int)pd.size();
+  const size_t nn = (size_t)n * n, blk = (size_t)4 * nn * npts;
+  pw_status st;
+  if ((st = ensure(ctx, ctx->chO, (size_t)(nq - 1) * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->chPts, (size_t)npts * sizeof(PointDesc))) ||
+      (st = ensure(ctx, ctx->chSif, blk * sizeof(zc))) || (st = ensure(ctx, ctx->chSa, blk * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->chSb, blk * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->chW, (size_t)npts * 4 * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->chPiv, (size_t)npts * n * sizeof(int))) ||
+      (st = ensure(ctx, ctx->chSt, (size_t)npts * sizeof(int))))
+    return st;
+  CK(cudaMemcpyAsync(ctx->chPts.p, pd.data(), npts * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->chSt.p, 0, npts * sizeof(int), ctx->stream));
+  pw::launch_overlaps((const zc *)ctx->chU.p, (zc *)ctx->chO.p, n, nq, 1, ctx->stream, false);
+  CK(cudaGetLastError());
+  zc *acc = (zc *)ctx->chSa.p, *tmp = (zc *)ctx->chSb.p, *sif = (zc *)ctx->chSif.p;
+  for (int q = 0; q + 1 < nq; ++q) {
+    CK(pw::launch_slice_smatrix((const PointDesc *)ctx->chPts.p, (const double *)ctx->chE.p, (const zc *)ctx->chO.p,
+                                (const double *)ctx->chDz.p, (zc *)ctx->chW.p, (int *)ctx->chPiv.p,
+                                (int *)ctx->chSt.p, q == 0 ? acc : sif, n, nq - 2, q, npts, ctx->stream));
+    if (q > 0) {
+      CK(pw::launch_compose(acc, sif, tmp, (zc *)ctx->chW.p, (int *)ctx->chPiv.p, (int *)ctx->chSt.p, n, npts,
+                            ctx->stream));
+      std::swap(acc, tmp);
+    }
+  }
+  if (acc != (zc *)ctx->chSa.p)
+    CK(cudaMemcpyAsync(ctx->chSa.p, acc, blk * sizeof(zc), cudaMemcpyDeviceToDevice, ctx->stream));
+  return PW_OK;
+}
+
+pw_status pw_set_periodic_electrode(pw_ctx *ctx, int side, int M, const pw_c128 *tables, const double *dz,
+                                    const double *a3_perp) {
+  if (!ctx || side < 0 || side > 1 || M < 1 || !tables || !dz || !a3_perp) return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  for (int q = 0; q < M; ++q)
+    if (!(dz[q] > 0.0)) return PW_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->d_petab[side]) { cudaFree(ctx->d_petab[side]); ctx->d_petab[side] = nullptr; }
+  ctx->pe_M[side] = 0;
+  if (cudaMalloc(&ctx->d_petab[side], (size_t)M * ctx->tsz * sizeof(zc)) != cudaSuccess) {
+    cudaGetLastError();
+    return latch(ctx, PW_ENOMEM);
+  }
+  CK(cudaMemcpy(ctx->d_petab[side], tables, (size_t)M * ctx->tsz * sizeof(zc), cudaMemcpyHostToDevice));
+  ctx->pe_dz[side].assign(dz, dz + M);
+  ctx->pe_a3[side][0] = a3_perp[0];
+  ctx->pe_a3[side][1] = a3_perp[1];
+  ctx->pe_M[side] = M;
+  return PW_OK;
+}
+
+pw_status pw_transmission_periodic(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev) {
+  if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev)) || ctx->pe_M[0] < 1 || ctx->pe_M[1] < 1)
+    return PW_EINVAL;
+  if (ctx->err) return ctx->err;
+  KtScope kts(ctx);
+  const int n = ctx->n, N = ctx->N, ML = ctx->pe_M[0], MR = ctx->pe_M[1];
+  const size_t nn = (size_t)n * n;
+  const int Mmax = std::max(ML, MR);
+  const int nqmax = std::max(Mmax + 1, N + 2);
+  pw_status st = alloc_slots(ctx);
+  if (st) return st;
+  std::vector<std::vector<int>> groups;
+  group_by_k(npts, kpar, groups);
+  pw_status result = PW_OK;
+  if ((st = ensure(ctx, ctx->peU, (size_t)(ML + MR) * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->peV, (size_t)(ML + MR) * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->peE, (size_t)(ML + MR) * n * sizeof(double))) ||
+      (st = ensure(ctx, ctx->peStat, (size_t)(ML + MR) * sizeof(int))) ||
+      (st = ensure(ctx, ctx->chU, (size_t)nqmax * nn * sizeof(zc))) ||
+      (st = ensure(ctx, ctx->chE, (size_t)nqmax * n * sizeof(double))) ||
+      (st = ensure(ctx, ctx->chDz, (size_t)nqmax * sizeof(double))))
+    return st;
+  zc *U_cell[2] = {(zc *)ctx->peU.p, (zc *)ctx->peU.p + (size_t)ML * nn};
+  double *E_cell[2] = {(double *)ctx->peE.p, (double *)ctx->peE.p + (size_t)ML * n};
+  for (const auto &grp : groups) {
+    const double *k = kpar + 2 * grp[0];
+    if ((st = ensure_ksets(ctx, std::vector<const double *>{k}))) return st;
+    // modes of both electrode cells at this k_par (FP64)
+    for (int side = 0; side < 2; ++side) {
+      const int M = ctx->pe_M[side];
+      pw::launch_assemble_h(U_cell[side], ctx->d_petab[side], ctx->d_mn, ctx->d_G, k[0], k[1], n, M, ctx->Dm,
+                            ctx->Dn, ctx->stream);
+      pw::launch_eig(U_cell[side], (zc *)ctx->peV.p, E_cell[side], (int *)ctx->peStat.p, n, M, ctx->stream, false);
+      CK(cudaGetLastError());
+    }
+    const int np = (int)grp.size();
+    std::vector<PointDesc> pd(np);
+    std::vector<int> outs(np), bad(np, 0);
+    for (int i = 0; i < np; ++i) {
+      pd[i] = pw::make_point(E[grp[i]], 0, 0, 0, grp[i], 0, N, i);
+      outs[i] = grp[i];
+    }
+    const size_t blk = (size_t)4 * nn * np;
+    if ((st = ensure(ctx, ctx->bdS[0], blk * sizeof(zc))) || (st = ensure(ctx, ctx->bdS[1], blk * sizeof(zc))) ||
+        (st = ensure(ctx, ctx->bdW, (size_t)np * pw::band_work_elems(n) * sizeof(zc))) ||
+        (st = ensure(ctx, ctx->bdPiv, (size_t)np * 2 * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->bdKeys, (size_t)np * 8 * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->bdStates[0], blk * sizeof(zc))) || (st = ensure(ctx, ctx->bdStates[1], blk * sizeof(zc))) ||
+        (st = ensure(ctx, ctx->bdProp[0], (size_t)np * 2 * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->bdProp[1], (size_t)np * 2 * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->bdStat, (size_t)2 * np * sizeof(int))) ||
+        (st = ensure(ctx, ctx->bdE, (size_t)np * sizeof(double))) ||
+        (st = ensure(ctx, ctx->bdBad, (size_t)np * sizeof(int))) ||
+        (st = ensure(ctx, ctx->ppW, (size_t)np * pw::periodic_work_elems(n) * sizeof(zc))) ||
+        (st = ensure(ctx, ctx->ppPiv, (size_t)np * 2 * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->ppOut, (size_t)np * sizeof(int))))
+      return st;
+    std::vector<double> Eh(np);
+    for (int i = 0; i < np; ++i) Eh[i] = E[grp[i]];
+    CK(cudaMemcpyAsync(ctx->bdE.p, Eh.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->ppOut.p, outs.data(), np * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    // the cells' S over one period: left [c_M, c_1' .. c_M'], right [c_1 .. c_M, c_1']
+    // (primed: the next cell, its modes D U with D = diag(e^{-i G.a3_perp}))
+    for (int side = 0; side < 2; ++side) {
+      const int M = ctx->pe_M[side];
+      zc *cu = (zc *)ctx->chU.p;
+      double *ce = (double *)ctx->chE.p;
+      std::vector<double> dzc(M + 1, 0.0);
+      const double ax = ctx->pe_a3[side][0], ay = ctx->pe_a3[side][1];
+      if (side == 0) {
+        CK(cudaMemcpyAsync(cu, U_cell[0] + (size_t)(M - 1) * nn, nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(pw::launch_tilt_modes(U_cell[0], cu + nn, ctx->d_G, ax, ay, n, M, ctx->stream));
+        CK(cudaMemcpyAsync(ce, E_cell[0] + (size_t)(M - 1) * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ce + n, E_cell[0], (size_t)M * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        for (int q = 0; q < M; ++q) dzc[q + 1] = ctx->pe_dz[0][q];
+      } else {
+        CK(cudaMemcpyAsync(cu, U_cell[1], (size_t)M * nn * sizeof(zc), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(pw::launch_tilt_modes(U_cell[1], cu + (size_t)M * nn, ctx->d_G, ax, ay, n, 1, ctx->stream));
+        CK(cudaMemcpyAsync(ce, E_cell[1], (size_t)M * n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ce + (size_t)M * n, E_cell[1], n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        for (int q = 1; q < M; ++q) dzc[q] = ctx->pe_dz[1][q];
+        dzc[M] = ctx->pe_dz[1][0];
+      }
+      CK(cudaMemcpyAsync(ctx->chDz.p, dzc.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      if ((st = chain_smatrix(ctx, M + 1, pd))) return st;
+      CK(cudaMemcpyAsync(ctx->bdS[side].p, ctx->chSa.p, blk * sizeof(zc), cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));   // chDz is host-staged per side
+      pw::BandArgs ba;
+      ba.n = n;
+      ba.nprob = np;
+      ba.S = (const zc *)ctx->bdS[side].p;
+      ba.Eref = E_cell[side] + (size_t)(side == 0 ? M - 1 : 0) * n;
+      ba.Uref = U_cell[side] + (size_t)(side == 0 ? M - 1 : 0) * nn;
+      ba.ref_shared = 1;
+      ba.E = (const double *)ctx->bdE.p;
+      ba.work = (zc *)ctx->bdW.p;
+      ba.ipiv = (int *)ctx->bdPiv.p;
+      ba.keys = (int *)ctx->bdKeys.p;
+      ba.states = (zc *)ctx->bdStates[side].p;
+      ba.prop = (int *)ctx->bdProp[side].p;
+      ba.status = (int *)ctx->bdStat.p + (size_t)side * np;
+      CK(pw::launch_cbands(ba, ctx->stream));
+    }
+    std::vector<int> bst(2 * np);
+    CK(cudaMemcpyAsync(bst.data(), ctx->bdStat.p, 2 * np * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < np; ++i)
+      if (bst[i] || bst[np + i]) { bad[i] = 1; result = PW_ENOTCONV; }
+    CK(cudaMemcpyAsync(ctx->bdBad.p, bad.data(), np * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    // the device between the reference slices: [c_M (left), device slices, c_1 (right)]
+    {
+      zc *cu = (zc *)ctx->chU.p;
+      double *ce = (double *)ctx->chE.p;
+      const size_t so = 0;   // ensure_ksets put this k_par in slot 0
+      CK(cudaMemcpyAsync(cu, U_cell[0] + (size_t)(ML - 1) * nn, nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(cu + nn, ctx->d_HU + (so + 1) * nn, (size_t)N * nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(cu + (size_t)(N + 1) * nn, U_cell[1], nn * sizeof(zc), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(ce, E_cell[0] + (size_t)(ML - 1) * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(ce + n, ctx->d_En + (so + 1) * n, (size_t)N * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(ce + (size_t)(N + 1) * n, E_cell[1], n * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      std::vector<double> dzc(N + 2, 0.0);
+      for (int q = 1; q <= N; ++q) dzc[q] = ctx->dz[q];
+      dzc[N + 1] = ctx->pe_dz[1][0];
+      CK(cudaMemcpyAsync(ctx->chDz.p, dzc.data(), (N + 2) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      if ((st = chain_smatrix(ctx, N + 2, pd))) return st;
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    pw::PeriodicArgs pa;
+    pa.n = n;
+    pa.Sdev = (const zc *)ctx->chSa.p;
+    pa.statesL = (const zc *)ctx->bdStates[0].p;
+    pa.statesR = (const zc *)ctx->bdStates[1].p;
+    pa.propL = (const int *)ctx->bdProp[0].p;
+    pa.propR = (const int *)ctx->bdProp[1].p;
+    pa.bad = (const int *)ctx->bdBad.p;
+    pa.work = (zc *)ctx->ppW.p;
+    pa.ipiv = (int *)ctx->ppPiv.p;
+    pa.T = T_dev;
+    pa.out = (const int *)ctx->ppOut.p;
+    CK(pw::launch_periodic_solve(pa, np, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (result != PW_OK) latch(ctx, result);
   return result;
 }
 

@@ -245,6 +245,40 @@ cudaError_t launch_nl_solve(const NonlocalArgs &a, int npts, cudaStream_t s);
 // the source columns of one interface step (FP64 sweep): Tacc_src += Y fa_q + fb_p
 cudaError_t launch_nl_sources(const SweepArgs &a, int npts, int p, cudaStream_t s);
 
+// periodic electrodes (pw_bands.cu)
+struct BandArgs {
+  int n, nprob;
+  const zc *S;           // [prob][4][n*n]: S11, S12, S21, S22 of one electrode period
+  const double *Eref;    // [prob][n]: eigenvalues of the electrode's reference slice
+  const zc *Uref;        // [prob][n*n]: its modes
+  int ref_shared;        // 1: one reference slice (Eref, Uref) for every problem
+  const double *E;       // [prob]
+  zc *work;              // [prob][band_work_elems(n)]
+  int *ipiv;             // [prob][2n]
+  int *keys;             // [prob][8n]
+  zc *states;            // [prob][4][n*n]: aR, bR (right-going), aL, bL (left-going)
+  int *prop;             // [prob][2n]: 1 for propagating columns (right-going 0..n-1, left-going n..2n-1)
+  int *status;           // [prob]: 0 ok, 1 singular Cayley matrix, 2 no Schur form, 3 state counts, 4 band edge
+};
+__host__ __device__ size_t band_work_elems(int n);
+cudaError_t launch_cbands(const BandArgs &a, cudaStream_t s);
+struct PeriodicArgs {
+  int n;
+  const zc *Sdev;        // [pt][4][n*n]: S of [left reference slice, device, right reference slice]
+  const zc *statesL, *statesR;   // [pt][4][n*n] as BandArgs.states
+  const int *propL, *propR;      // [pt][2n]
+  const int *bad;        // [pt]: nonzero when either electrode's states failed
+  zc *work;              // [pt][periodic_work_elems(n)]
+  int *ipiv;             // [pt][2n]
+  double *T;             // caller output at index out[pt]
+  const int *out;
+};
+size_t periodic_work_elems(int n);
+cudaError_t launch_periodic_solve(const PeriodicArgs &a, int npts, cudaStream_t s);
+cudaError_t launch_tilt_modes(const zc *U, zc *Ut, const double *G, double ax, double ay, int n, int count,
+                              cudaStream_t s);
+cudaError_t schur_selftest(zc *A, zc *Z, zc *v, int N, int sel, int *keys, int *out);
+
 cudaError_t launch_grad_leads(const GammaArgs &h, const zc *U_all, const double *G, zc *scr,
                               const double rate[2][2], double *out, cudaStream_t s);
 

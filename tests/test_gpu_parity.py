@@ -94,8 +94,8 @@ def test_slice_modes_against_oracle_hamiltonians(pw, ng, nsl):
 
 @pytest.mark.parametrize("ng,nsl", [(21, 4), (64, 3), (512, 2), (21, 330)])
 def test_slice_modes_double_float_mixed_form(pw, ng, nsl):
-    """The mixed form's eigensolver and overlaps run in double-float
-    (48-bit) arithmetic on the FP32 pipe: same checks, 10x looser.  332
+    """The mixed form's double-float eigensolver and overlaps (launch variant
+    bit 5; 48-bit arithmetic on the FP32 pipe): same checks, 10x looser.  332
     matrices exceed two per SM on a 152-SM GPU, so the last case also covers
     the reduction tail on the second stream."""
     _check_slice_modes(pw, ng, nsl, precision=1, tol=10.0)
@@ -111,6 +111,8 @@ def _check_slice_modes(pw, ng, nsl, precision, tol):
     m = O.Model(inst)
     n, nq = m.n, m.N + 2
     with pw.Context.from_instance(inst, precision) as ctx:
+        if precision == 1:
+            ctx.set_sweep_variant(2 | 32)      # the double-float mode stage
         En = _dev((nq, n), torch.float64)
         U = _dev((nq, n, n), torch.complex128)
         Ov = _dev((nq - 1, n, n), torch.complex128)
