@@ -2,7 +2,8 @@
  * pw.h -- C ABI of the GB300 plane-wave multiple-scattering transport library.
  *
  * The library computes, for a slice model of a junction between two
- * z-invariant electrodes, the transmission T(E, k_par) = Tr(t^H t) of Li, Chu,
+ * electrodes (z-invariant, or z-periodic through pw_set_periodic_electrode),
+ * the transmission T(E, k_par) = Tr(t^H t) of Li, Chu,
  * Zhang & Cheng, "Electron transport in graphene/graphene side-contact junction
  * by plane-wave multiple scattering method" (PRB 2015):
  *   - Sec. II A / Eq. loc: 2D plane-wave basis {G_perp}, slice Hamiltonians
@@ -58,10 +59,11 @@ typedef struct { double re, im; } pw_c128;
  * on the FP32 pipe), the star-product sweep
  * in FP32 (its GEMMs on the tensor cores as TF32 hi/lo products), then passes
  * of iterative refinement of the whole interface-matching system whose
- * residuals are formed in double-float (exact BF16 slice products on the
- * tensor cores when all points of a launch share one k_par and N_G is a
- * multiple of 4 up to 512) until the estimated remaining error of t falls
- * below 1e-9 relative; T and t are accumulated in FP64. */
+ * residuals are formed in double-float (with launch variant bit 4, as exact
+ * BF16 slice products on the tensor cores when all points of a launch share
+ * one k_par and N_G is a multiple of 4 up to 512) until the estimated
+ * remaining error of t falls below 1e-9 relative; T and t are accumulated in
+ * FP64. */
 enum { PW_FP64 = 0, PW_MIXED_FP32 = 1 };
 
 /*
@@ -347,13 +349,35 @@ pw_status pw_reduce_transmission(int npts, const double *T_dev, const int *nopen
  * than the array run through it in chunks, and n above 362 (one point's
  * scratch would exceed 8 MiB) returns PW_EINVAL before any device work.  The
  * first call on each device looks up the array's device address (set-up
- * without allocation); make that first call before any stream capture.  All
- * calls share the one array, so calls whose work overlaps on the GPU (other
- * streams, other host threads) race; the call synchronises its stream before
- * returning (it reads back the pivot status), and returns PW_ESINGULAR on a
- * zero pivot. */
+ * without allocation).  The call cannot be recorded into a CUDA graph: it
+ * synchronises its stream before returning (it reads back the pivot status
+ * of every launch), which a stream under capture does not allow.  All calls
+ * share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race; PW_ESINGULAR on a zero pivot. */
 pw_status pw_compose_noalloc(int n, int npts, const pw_c128 *Sa_dev, const pw_c128 *Sb_dev,
                              pw_c128 *Sab_dev, void *cuda_stream);
+
+/* FP64 kept for near-singular blocks in the mixed form (PW_MIXED_FP32;
+ * Sec. II A's pivoted LU of the interface blocks, whose conditioning the
+ * evanescent channels' wavenumbers set).  After a batch's FP32 sweep and
+ * refinement, pw_transmission solves a point again with the FP64 sweep
+ * (every interface in FP64; its T, t, n_open then come from that solve and
+ * its error estimate is 0) when
+ *   - the LU factors of some interface block W_p have a diagonal spread
+ *     max|u_ii| / min|u_ii| above pivot_ratio_max (W_p's condition number is
+ *     then at least that large), or
+ *   - the refinement's estimated remaining error of the point is above
+ *     err_max after its last pass, or
+ *   - the FP32 sweep met a zero pivot.
+ * Defaults 1e6 and 1e-8.  pivot_ratio_max < 0 turns the fallback off;
+ * pivot_ratio_max = 0 sends every point to FP64.  PW_EINVAL for NaN or
+ * err_max < 0.  Host setting, no device work. */
+pw_status pw_set_fp64_fallback(pw_ctx *ctx, double pivot_ratio_max, double err_max);
+
+/* Of the last pw_transmission call: *points = how many points the FP64
+ * fallback solved again, *max_pivot_ratio = the largest diagonal spread of
+ * any W_p's FP32 LU factors over its points (0 in the FP64 form). */
+pw_status pw_get_fp64_fallback(const pw_ctx *ctx, int *points, double *max_pivot_ratio);
 
 /* Launch variant of the star-product sweep of pw_transmission (default 2 for
  * PW_MIXED_FP32, 0 for PW_FP64).  The result is the same to the form's
@@ -533,6 +557,15 @@ pw_status pw_selftest_bounded_wait(int polls, int signal);
  * buffer, synchronises the device; the paper has no counterpart (these are the
  * roofline denominators of the FP64 form and of the double-float kernels). */
 pw_status pw_measure_peaks(double *tflops);
+
+/* How many slice Hamiltonians of order n the FP64 eigensolver (Eq. loc, the
+ * slice eigenproblem) works on at once on the current device: the CTAs of
+ * one matrix each that fit on every SM together, times the SM count.  A mode
+ * stage of more matrices than this runs in waves; its partial last wave runs
+ * beside the overlaps (Eq. transfer's U_p^H U_{p+1}) of the slices already
+ * done.  *matrices = 0 when the solver cannot run at order n.  PW_EINVAL for
+ * n < 1 or a null pointer.  Host query; no device memory is touched. */
+pw_status pw_eig_wave(int n, int *matrices);
 
 #ifdef __cplusplus
 }

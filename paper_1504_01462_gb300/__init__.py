@@ -39,7 +39,8 @@ EXPORTS = ["pw_setup", "pw_destroy", "pw_status_str", "pw_get_error", "pw_ng", "
            "pw_kernel_kind_name", "pw_get_kernel_profile", "pw_measure_peaks",
            "pw_set_grad_checkpoint", "pw_workspace_bytes", "pw_selftest_bounded_wait",
            "pw_reduce_transmission", "pw_set_projectors", "pw_transmission_nonlocal",
-           "pw_set_periodic_electrode", "pw_transmission_periodic", "pw_selftest_schur"]
+           "pw_set_periodic_electrode", "pw_transmission_periodic", "pw_selftest_schur",
+           "pw_eig_wave", "pw_set_fp64_fallback", "pw_get_fp64_fallback"]
 
 
 class PwError(RuntimeError):
@@ -123,6 +124,9 @@ def _load():
     lib.pw_set_periodic_electrode.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]
     lib.pw_transmission_periodic.argtypes = [_vp, ctypes.c_int, _dp, _dp, _vp]
     lib.pw_selftest_schur.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _ip]
+    lib.pw_eig_wave.argtypes = [ctypes.c_int, _ip]
+    lib.pw_set_fp64_fallback.argtypes = [_vp, ctypes.c_double, ctypes.c_double]
+    lib.pw_get_fp64_fallback.argtypes = [_vp, _ip, _dp]
     lib.pw_batch_destroy.restype = None
     return lib
 
@@ -294,6 +298,14 @@ def measure_peaks():
     return {"fp64_fma": float(out[0]), "fp64_mma": float(out[1]), "fp32_fma": float(out[2])}
 
 
+def eig_wave(n):
+    """Slice Hamiltonians of order n the FP64 eigensolver works on at once on
+    the current device (resident CTAs x SMs)."""
+    out = ctypes.c_int(0)
+    _check_status(_lib.pw_eig_wave(int(n), ctypes.byref(out)), "pw_eig_wave")
+    return out.value
+
+
 def _check_status(st, where):
     if st != 0:
         raise PwError(st, where)
@@ -440,8 +452,25 @@ class Context:
         """Sweep launch variant (pw_set_sweep_variant): bit 0 = 512-thread SIMT
         tiles; mixed form only: bit 1 = GEMM phases on the tcgen05 tensor
         cores, bit 2 = FP16-split [W|Y] of point pairs, bit 3 = LAPACK pivots
-        and 128-row triangular blocks, bit 4 = slice-product residual."""
+        and 128-row triangular blocks, bit 4 = slice-product residual, bit 5 =
+        double-float eigenmodes and overlaps."""
         self._check(_lib.pw_set_sweep_variant(self._h, int(variant)), "pw_set_sweep_variant")
+
+    def set_fp64_fallback(self, pivot_ratio_max=1e6, err_max=1e-8):
+        """When the mixed form solves a point again in FP64
+        (pw_set_fp64_fallback): an LU diagonal spread above pivot_ratio_max,
+        an estimated error above err_max, or a zero FP32 pivot."""
+        self._check(_lib.pw_set_fp64_fallback(self._h, float(pivot_ratio_max), float(err_max)),
+                    "pw_set_fp64_fallback")
+
+    def fp64_fallback(self):
+        """(points solved again in FP64, largest LU diagonal spread) of the
+        last transmission call."""
+        pts = ctypes.c_int(0)
+        ratio = ctypes.c_double(0.0)
+        self._check(_lib.pw_get_fp64_fallback(self._h, ctypes.byref(pts), ctypes.byref(ratio)),
+                    "pw_get_fp64_fallback")
+        return pts.value, ratio.value
 
     def set_profiling(self, on=True, stride=1):
         """Stage and per-kernel launch timing; with `stride` k every k-th

@@ -28,7 +28,9 @@ const char *kernel_kind_name(int kind) {
       "k_refine_fwd_a", "k_refine_fwd_b", "k_refine_bwd_a", "k_refine_bwd_b", "k_refine_bwd_mm",
       "k_refine_bwd_c", "k_refine_finish",
       "k_tables", "k_assemble_h", "k_heev (k_heev<double>, or the reduction of k_heev<df>)", "k_ql_df",
-      "k_rot_apply", "k_backtransform", "k_eig_sort", "k_overlaps", "k_o32", "k_o32t"};
+      "k_rot_apply", "k_backtransform", "k_eig_sort", "k_overlaps", "k_o32", "k_o32t",
+      "k_heev_tail (the FP64 eigensolver's partial last wave on a side stream, beside k_overlaps; its time "
+      "includes the wait for free SMs)"};
   return (kind >= 0 && kind < KK_COUNT) ? names[kind] : "";
 }
 
@@ -195,6 +197,11 @@ struct pw_ctx {
   DevBuf peU, peV, peE, peStat, chU, chE, chO, chDz, chPts, chSif, chSa, chSb, chW, chPiv, chSt, bdS[2],
       bdW, bdPiv, bdKeys, bdStates[2], bdProp[2], bdStat, bdE, bdBad, ppW, ppPiv, ppOut;
   DevBuf ckR, ckT;                 // pw_grad checkpoints of the sweep state (R, Tacc)
+  // FP64 re-solve of the mixed form's ill-conditioned points (pw_set_fp64_fallback)
+  double fb_pivot_max = 1e6, fb_err_max = 1e-8;
+  int last_fp64_points = 0;
+  double last_pivot_ratio = 0.0;
+  DevBuf pivr, R64, M64, piv64, KV64, pts64, st64;
 };
 
 namespace {
@@ -409,15 +416,56 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
   // the mixed form's modes and overlaps in FP64, or (variant bit 5) in double-float
   const bool dfe = ctx->precision == PW_MIXED_FP32 && (ctx->sweep_variant & 32);
   if (dfe && (st = ensure(ctx, ctx->eigws, pw::heev_ws_bytes(n, nmat)))) return st;
-  pw::launch_eig(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_V + (size_t)s0 * nq * nn,
-                 ctx->d_En + (size_t)s0 * nq * n, ctx->d_eigstat + (size_t)s0 * nq, n, nmat,
-                 ctx->stream, dfe, dfe ? ctx->eigws.p : nullptr, dfe ? ctx->eigws.bytes : 0);
+  zc *HU0 = ctx->d_HU + (size_t)s0 * nq * nn, *V0 = ctx->d_V + (size_t)s0 * nq * nn;
+  double *En0 = ctx->d_En + (size_t)s0 * nq * n;
+  int *stat0 = ctx->d_eigstat + (size_t)s0 * nq;
+  // The FP64 solver runs one matrix per CTA.  When its grid ends in a partial
+  // wave, that wave's matrices go to a side stream, and the overlaps of every
+  // interface whose two slices are in the full waves run beside it on the SMs
+  // the partial wave leaves idle; the remaining overlaps follow both.
+  int nA = nmat;
+  if (!dfe) {
+    const int res = pw::heev_resident_per_sm(n) * ctx->num_sms;
+    if (res > 0 && nmat > res && nmat % res) nA = nmat - nmat % res;
+  }
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (nA < nmat) {
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();   // no side stream: one launch
+      if (side) cudaStreamDestroy(side);
+      if (fork) cudaEventDestroy(fork);
+      side = nullptr;
+      fork = nullptr;
+      nA = nmat;
+    } else {
+      CK(cudaEventRecord(fork, ctx->stream));
+      CK(cudaStreamWaitEvent(side, fork, 0));
+    }
+  }
+  pw::launch_eig(HU0, V0, En0, stat0, n, nA, ctx->stream, dfe, dfe ? ctx->eigws.p : nullptr,
+                 dfe ? ctx->eigws.bytes : 0);
+  if (side)
+    pw::launch_eig(HU0 + (size_t)nA * nn, V0 + (size_t)nA * nn, En0 + (size_t)nA * n, stat0 + nA, n, nmat - nA,
+                   side, false, nullptr, 0, true);
   CK(cudaGetLastError());
   SYNC_CHECK();
   st1.done();
   Stage st2(ctx, 2, s1 - s0);
-  pw::launch_overlaps(ctx->d_HU + (size_t)s0 * nq * nn, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq,
-                      s1 - s0, ctx->stream, dfe);
+  const int npairs = (s1 - s0) * (nq - 1);
+  int gA = 0;   // pairs g < gA have both slices among the first nA matrices
+  while (gA < npairs && (gA / (nq - 1)) * nq + gA % (nq - 1) + 1 < nA) ++gA;
+  pw::launch_overlaps(HU0, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq, s1 - s0, ctx->stream, dfe, 0, gA);
+  if (side) {
+    CK(cudaEventRecord(join, side));
+    CK(cudaStreamWaitEvent(ctx->stream, join, 0));
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+    cudaStreamDestroy(side);
+  }
+  pw::launch_overlaps(HU0, ctx->d_O + (size_t)s0 * (nq - 1) * nn, n, nq, s1 - s0, ctx->stream, dfe, gA, npairs);
   if (ctx->d_O32)
     pw::launch_overlaps_fp32(ctx->d_O + (size_t)s0 * (nq - 1) * nn, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn,
                              ctx->d_O32t + (size_t)s0 * (nq - 1) * nn, ctx->d_O32lo + (size_t)s0 * (nq - 1) * nn,
@@ -714,6 +762,18 @@ pw_status pw_set_profiling(pw_ctx *ctx, int enable) {
 int pw_kernel_kinds(void) { return pw::KK_COUNT; }
 
 const char *pw_kernel_kind_name(int kind) { return pw::kernel_kind_name(kind); }
+
+pw_status pw_eig_wave(int n, int *matrices) {
+  if (n < 1 || !matrices) return PW_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PW_ECUDA;
+  }
+  *matrices = pw::heev_resident_per_sm(n) * sms;
+  return PW_OK;
+}
 
 pw_status pw_get_kernel_profile(pw_ctx *ctx, double *out, int reset) {
   if (!ctx || !out) return PW_EINVAL;
@@ -1016,6 +1076,112 @@ pw_status pw_transmission_doubling(pw_ctx *ctx, int npts, const double *E, const
   return result;
 }
 
+// The FP64 sweep (every interface in FP64, from the FP64 modes and overlaps
+// of the points' k-set slots) of the points pts, writing their T, t, n_open
+// and a zero error estimate; status_out[i] is point i's sweep status.
+static pw_status fp64_sweep(pw_ctx *ctx, std::vector<PointDesc> pts, int nc, double *T_dev, pw_c128 *t_dev,
+                            int *nopen_dev, double *err_dev, std::vector<int> &status_out) {
+  const int n = ctx->n, N = ctx->N, ncols = 2 * n + nc;
+  const size_t nn = (size_t)n * n, esz = sizeof(zc);
+  status_out.assign(pts.size(), 0);
+  const int cap = std::max(1, 2 * ctx->num_sms);
+  pw_status st = PW_OK;
+  for (size_t b0 = 0; b0 < pts.size(); b0 += cap) {
+    const int nb = (int)std::min(pts.size() - b0, (size_t)cap);
+    std::vector<PointDesc> pd(pts.begin() + b0, pts.begin() + b0 + nb);
+    for (int i = 0; i < nb; ++i)
+      pd[i] = pw::make_point(pd[i].E, pd[i].kset, pd[i].nL, pd[i].nR, pd[i].out, 0, N, i);
+    if ((st = ensure(ctx, ctx->R64, (size_t)nb * nn * esz)) ||
+        (st = ensure(ctx, ctx->M64, (size_t)nb * n * ncols * esz)) ||
+        (st = ensure(ctx, ctx->piv64, (size_t)nb * n * sizeof(int))) ||
+        (st = ensure(ctx, ctx->KV64, (size_t)nb * 3 * n * esz)) ||
+        (st = ensure(ctx, ctx->pts64, (size_t)nb * sizeof(PointDesc))) ||
+        (st = ensure(ctx, ctx->st64, (size_t)nb * sizeof(int))))
+      return st;
+    CK(cudaMemcpyAsync(ctx->pts64.p, pd.data(), nb * sizeof(PointDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->st64.p, 0, nb * sizeof(int), ctx->stream));
+    pw::SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = (const PointDesc *)ctx->pts64.p;
+    a.En = ctx->d_En;
+    a.O = ctx->d_O;
+    a.dz = ctx->d_dz;
+    a.R = ctx->R64.p;
+    a.M = ctx->M64.p;
+    a.piv = (int *)ctx->piv64.p;
+    a.status = (int *)ctx->st64.p;
+    a.T = T_dev;
+    a.t = (zc *)t_dev;
+    a.nopen = nopen_dev;
+    a.err = err_dev;
+    a.n = n;
+    a.N = N;
+    a.nc = nc;
+    a.KV = ctx->KV64.p;
+    CK(pw::prepare_sweep_batched(n, PW_FP64, 0));
+    for (int p = 0; p <= N; ++p) {
+      CK(pw::launch_sweep_batched(a, nb, p, PW_FP64, ctx->stream, nullptr, nullptr, 0));
+      SYNC_CHECK();
+    }
+    CK(cudaMemcpyAsync(status_out.data() + b0, ctx->st64.p, nb * sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PW_OK;
+}
+
+// The mixed form's FP64 fallback for one batch after its sweep and refinement
+// (pd: the batch's descriptors; status: the FP32 sweep's per-point status,
+// updated for the points solved again).  A point is solved again by the FP64
+// sweep when an LU factor of some W_p has a diagonal spread max|u_ii| /
+// min|u_ii| above fb_pivot_max (then W_p's condition number is at least that
+// large), when its estimated error after the last refinement pass is above
+// fb_err_max, or when the FP32 sweep met a zero pivot.
+static pw_status fp64_fallback(pw_ctx *ctx, const std::vector<PointDesc> &pd, int nc, std::vector<int> &status,
+                               double *T_dev, pw_c128 *t_dev, int *nopen_dev, double *err_dev) {
+  const int nb = (int)pd.size();
+  if (ctx->fb_pivot_max < 0.0) return PW_OK;
+  std::vector<float> pr(nb);
+  std::vector<double> cr(2 * (size_t)nb);
+  CK(cudaMemcpyAsync(pr.data(), ctx->pivr.p, nb * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(cr.data(), ctx->corr.p, 2 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<PointDesc> redo;
+  std::vector<int> which;
+  for (int i = 0; i < nb; ++i) {
+    if (pd[i].skip || status[i] == 2) continue;   // threshold point; a timed-out wait stays an error
+    const double c = cr[i], cp = cr[nb + i];
+    const double est = cp > 0.0 ? c * c / cp : c;   // the refinement's own estimate
+    if (status[i] == 0) ctx->last_pivot_ratio = std::max(ctx->last_pivot_ratio, (double)pr[i]);
+    if (status[i] == 1 || !((double)pr[i] <= ctx->fb_pivot_max) || !(est <= ctx->fb_err_max)) {
+      redo.push_back(pd[i]);
+      which.push_back(i);
+    }
+  }
+  if (redo.empty()) return PW_OK;
+  std::vector<int> st64;
+  pw_status st = fp64_sweep(ctx, redo, nc, T_dev, t_dev, nopen_dev, err_dev, st64);
+  if (st) return st;
+  for (size_t j = 0; j < which.size(); ++j) status[which[j]] = st64[j];
+  ctx->last_fp64_points += (int)redo.size();
+  return PW_OK;
+}
+
+pw_status pw_set_fp64_fallback(pw_ctx *ctx, double pivot_ratio_max, double err_max) {
+  if (!ctx || pivot_ratio_max != pivot_ratio_max || !(err_max >= 0.0)) return PW_EINVAL;
+  ctx->fb_pivot_max = pivot_ratio_max;
+  ctx->fb_err_max = err_max;
+  return PW_OK;
+}
+
+pw_status pw_get_fp64_fallback(const pw_ctx *ctx, int *points, double *max_pivot_ratio) {
+  if (!ctx || !points || !max_pivot_ratio) return PW_EINVAL;
+  *points = ctx->last_fp64_points;
+  *max_pivot_ratio = ctx->last_pivot_ratio;
+  return PW_OK;
+}
+
 pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *kpar, double *T_dev,
                           pw_c128 *t_dev, int *nopen_dev, double *err_dev) {
   if (!ctx || npts < 0 || (npts > 0 && (!E || !kpar || !T_dev))) return PW_EINVAL;
@@ -1029,6 +1195,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
   pw_status result = PW_OK;
   pw_status st = alloc_slots(ctx);
   if (st) return st;
+  ctx->last_fp64_points = 0;
+  ctx->last_pivot_ratio = 0.0;
   for (size_t g0 = 0; g0 < groups.size(); g0 += ctx->ks_cap) {
     const size_t g1 = std::min(groups.size(), g0 + (size_t)ctx->ks_cap);
     std::vector<const double *> ks;
@@ -1123,6 +1291,11 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       a.mirror = 0;
       a.wy_pairs = pw::points_pair_up(pd.data(), nb);
       a.rowexp = (ctx->sweep_variant & 4) ? (int *)ctx->rowexp.p : nullptr;
+      if (refine) {
+        if ((st = ensure(ctx, ctx->pivr, (size_t)nb * sizeof(float)))) return st;
+        CK(cudaMemsetAsync(ctx->pivr.p, 0, nb * sizeof(float), ctx->stream));
+        a.pivratio = (float *)ctx->pivr.p;
+      }
       CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
       // the FP16-split [W|Y] adds its row-scale kernel at every interface with a product (p >= 1)
       const int f16_extra = (a.rowexp && a.wy_pairs && (ctx->sweep_variant & 6) == 6) ? N : 0;
@@ -1206,6 +1379,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       CK(cudaMemcpyAsync(st_h.data(), ctx->status.p, nb * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
       if (ctx->profiling && ctx->kt) CK(ctx->kt->flush());   // keeps the pending event pairs bounded
+      if (refine && (st = fp64_fallback(ctx, pd, nc, st_h, T_dev, t_dev, nopen_dev, err_dev))) return st;
       for (int v : st_h) {
         if (v == 2) result = PW_ETIMEOUT;   // a tensor-core wait ran out (kept over a zero pivot)
         else if (v && result != PW_ETIMEOUT) result = PW_ESINGULAR;

@@ -104,6 +104,9 @@ struct SweepArgs {
   // responses are carried as right-hand-side columns nl_c0 .. nl_c0 + nl_m - 1
   const zc *nl_fa, *nl_fb;
   int nl_m, nl_c0;
+  // null, or per point (launch index): the largest ratio max|u_ii| / min|u_ii|
+  // of the LU factors of W_p over the interfaces swept so far (FP32 sweep)
+  float *pivratio;
 };
 
 // 1 when every pair of points (2i, 2i+1) of a launch shares its overlaps and
@@ -291,17 +294,22 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
 // double_float: the mixed form's double-float solver; ws (ws_bytes >=
 // heev_ws_bytes(n, 1), else null) lets its QL recurrence run in double-float
 // as a separate launch over groups of as many matrices as the workspace holds
+// tail: the launch is a partial last wave run on a side stream (timed as its
+// own kernel kind)
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s,
-                bool double_float = false, void *ws = nullptr, size_t ws_bytes = 0);
+                bool double_float = false, void *ws = nullptr, size_t ws_bytes = 0, bool tail = false);
 size_t heev_ws_bytes(int n, int nmat);
+// CTAs of the FP64 eigensolver resident on one SM at once (order n)
+int heev_resident_per_sm(int n);
 // FP32 copies of `count` n x n overlaps, plain, (when O32t is not null)
 // transposed: O32t[j + l n] = O[l + j n], and (when O32lo is not null) the FP32
 // remainders O - O32 (O32 + O32lo is O as a double-float)
 void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, cc *O32lo, int n, int count, cudaStream_t s);
 // O_p = U_p^H U_{p+1}, p = 0..nq-2, for nslots consecutive k-set slots;
-// double_float: accumulate in double-float (48-bit) on the FP32 pipe
+// double_float: accumulate in double-float (48-bit) on the FP32 pipe.  Pairs
+// g = slot (nq-1) + p in [g0, g1) only (g1 < 0: all of them).
 void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s,
-                     bool double_float = false);
+                     bool double_float = false, int g0 = 0, int g1 = -1);
 // One interface step of the left-to-right sweep for every point of a batch,
 // as a sequence of launches over (tiles x points).  variant bit 0: 512-thread
 // CTAs with 128 x 64 GEMM tiles (else 256 threads, 64 x 64); bit 1 (FP32
@@ -376,6 +384,7 @@ enum KernelKind : int {
   KK_REF_INIT, KK_REF_RESIDUAL, KK_RES_OSLICE, KK_RES_YSLICE, KK_RES_MM, KK_RES_FINISH, KK_REF_FWD_A,
   KK_REF_FWD_B, KK_REF_BWD_A, KK_REF_BWD_B, KK_REF_BWD_MM, KK_REF_BWD_C, KK_REF_FINISH,
   KK_TABLES, KK_ASSEMBLE, KK_HEEV, KK_QL, KK_ROT, KK_BACKT, KK_SORT, KK_OVERLAPS, KK_O32, KK_O32T,
+  KK_HEEV_TAIL,
   KK_COUNT
 };
 const char *kernel_kind_name(int kind);

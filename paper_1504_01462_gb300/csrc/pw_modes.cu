@@ -318,11 +318,13 @@ struct HeevAr<double> {
   static __device__ __forceinline__ double norm2(C z) { return cnorm2(z); }
   static __device__ __forceinline__ C mul(C a, C b) { return cmul(a, b); }
   static __device__ __forceinline__ void fma(C &acc, C a, C b) { cfma(acc, a, b); }
-  // acc += conj(a) b
+  // acc += conj(a) b (the products and sums as fused multiply-adds, here and
+  // below: one FP64 instruction per real product)
   static __device__ __forceinline__ void jfma(C &acc, C a, C b) {
-    const zc t = cjmul(a, b);
-    acc.re += t.re;
-    acc.im += t.im;
+    acc.re = ::fma(a.re, b.re, acc.re);
+    acc.re = ::fma(a.im, b.im, acc.re);
+    acc.im = ::fma(a.re, b.im, acc.im);
+    acc.im = ::fma(-a.im, b.re, acc.im);
   }
   static __device__ __forceinline__ void renorm(C &) {}
   static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
@@ -330,16 +332,22 @@ struct HeevAr<double> {
   static __device__ __forceinline__ C sub_scaled(C a, double c, C v) { return csub(a, cscale(c, v)); }
   // a - v conj(w_j) - w conj(v_j)
   static __device__ __forceinline__ C rank2(C a, C v, C wj, C w, C vj) {
-    const zc t1 = cmul(v, cconj(wj)), t2 = cmul(w, cconj(vj));
-    a.re -= t1.re + t2.re;
-    a.im -= t1.im + t2.im;
+    a.re = ::fma(-v.re, wj.re, a.re);
+    a.re = ::fma(-v.im, wj.im, a.re);
+    a.re = ::fma(-w.re, vj.re, a.re);
+    a.re = ::fma(-w.im, vj.im, a.re);
+    a.im = ::fma(-v.im, wj.re, a.im);
+    a.im = ::fma(v.re, wj.im, a.im);
+    a.im = ::fma(-w.im, vj.re, a.im);
+    a.im = ::fma(w.re, vj.im, a.im);
     return a;
   }
   // a - v p
   static __device__ __forceinline__ C sub_mul(C a, C v, C p) {
-    const zc t = cmul(v, p);
-    a.re -= t.re;
-    a.im -= t.im;
+    a.re = ::fma(-v.re, p.re, a.re);
+    a.re = ::fma(v.im, p.im, a.re);
+    a.im = ::fma(-v.re, p.im, a.im);
+    a.im = ::fma(-v.im, p.re, a.im);
     return a;
   }
   typedef double Rot;
@@ -956,9 +964,16 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
       return;
     }
   }
+  // The tridiagonal is real (e_k = beta_k), so are its eigenvectors: in FP64
+  // they accumulate as a real n x n matrix in the first half of Z's storage
+  // (half the arithmetic and traffic of the rotations) and become complex
+  // before the back-transformation.
+  constexpr bool real_z = std::is_same<R, double>::value;
+  double *Zr = reinterpret_cast<double *>(Z);
   for (size_t q = tid; q < nn; q += NTH) {
     const int i = q % n, j = q / n;
-    Z[q] = i == j ? Ar::one() : Ar::zero();
+    if constexpr (real_z) Zr[q] = i == j ? 1.0 : 0.0;
+    else Z[q] = i == j ? Ar::one() : Ar::zero();
   }
   __syncthreads();
 
@@ -1033,7 +1048,17 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
         }
         break;
       }
-      if (formed && lo < m) {
+      if (formed && lo < m && real_z) {
+        for (int row = tid; row < n; row += NTH) {
+          double x = Zr[row + (size_t)m * n];
+          for (int i = m - 1; i >= lo; --i) {
+            const double y = Zr[row + (size_t)i * n], c = cs[i], s = sn[i];
+            Zr[row + (size_t)(i + 1) * n] = fma(s, y, c * x);
+            x = fma(c, y, -s * x);
+          }
+          Zr[row + (size_t)lo * n] = x;
+        }
+      } else if (formed && lo < m) {
         for (int row = tid; row < n; row += NTH) {
           C x = Z[row + (size_t)m * n];
           for (int i = m - 1; i >= lo; --i) {
@@ -1045,6 +1070,22 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
           }
           Z[row + (size_t)lo * n] = x;
         }
+      }
+      __syncthreads();
+    }
+  }
+
+  if constexpr (real_z) {
+    // real Z to complex in place, highest block of NTH entries first: block b
+    // writes doubles [2 b NTH, 2 (b+1) NTH), above every entry that a lower
+    // block has still to read
+    for (long long b = ((long long)nn - 1) / NTH; b >= 0; --b) {
+      const size_t q = (size_t)b * NTH + tid;
+      const double val = q < nn ? Zr[q] : 0.0;
+      __syncthreads();
+      if (q < nn) {
+        Zr[2 * q] = val;
+        Zr[2 * q + 1] = 0.0;
       }
       __syncthreads();
     }
@@ -1117,8 +1158,20 @@ size_t heev_ws_bytes(int n, int nmat) {
 // workspace (ws, ws_bytes >= heev_ws_bytes(n, 1)) the QL recurrence runs in
 // double-float too, split into three launches per group of matrices
 // (reduction, QL stream, vectors); without one, in FP64 inside k_heev.
+int heev_resident_per_sm(int n) {
+  const size_t smem = heev_smem(n);
+  cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heev<double>, HEEV_THREADS, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s, bool double_float,
-                void *ws, size_t ws_bytes) {
+                void *ws, size_t ws_bytes, bool tail) {
+  if (nmat <= 0) return;
   const size_t smem = heev_smem(n);
   const size_t nn = (size_t)n * n;
   HeevWS w{};
@@ -1223,7 +1276,8 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
     }
   } else {
     cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    PW_TIMED(KK_HEEV, s, k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w));
+    PW_TIMED(tail ? KK_HEEV_TAIL : KK_HEEV, s,
+             k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w));
   }
 }
 
@@ -1240,10 +1294,11 @@ void launch_eig_jacobi(zc *HU, zc *V, double *En, int *status, int n, int nmat, 
 // ---------------------------------------------------------------------------
 // A: the accumulation type (double, or double-float for the mixed form).
 template <typename A>
-__global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n, int nq) {
+__global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n, int nq, int g0) {
   extern __shared__ unsigned char smraw[];
   cx<A> *sm = reinterpret_cast<cx<A> *>(smraw);
-  const int slot = blockIdx.x / (nq - 1), p = blockIdx.x % (nq - 1);
+  const int g = g0 + blockIdx.x;
+  const int slot = g / (nq - 1), p = g % (nq - 1);
   const zc *Up = U + ((size_t)slot * nq + p) * n * n;
   const zc *Uq = Up + (size_t)n * n;
   zc *Op = O + ((size_t)slot * (nq - 1) + p) * n * n;
@@ -1298,10 +1353,15 @@ void launch_overlaps_fp32(const zc *O, cc *O32, cc *O32t, cc *O32lo, int n, int 
   }
 }
 
-void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s, bool double_float) {
+void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t s, bool double_float, int g0,
+                     int g1) {
   const size_t smem = gemm_smem_elems<double>() * sizeof(zc);
-  if (double_float) PW_TIMED(KK_OVERLAPS, s, k_overlaps<df><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq));
-  else PW_TIMED(KK_OVERLAPS, s, k_overlaps<double><<<nslots * (nq - 1), NT, smem, s>>>(U, O, n, nq));
+  const int total = nslots * (nq - 1);
+  if (g1 < 0 || g1 > total) g1 = total;
+  if (g0 < 0) g0 = 0;
+  if (g0 >= g1) return;
+  if (double_float) PW_TIMED(KK_OVERLAPS, s, k_overlaps<df><<<g1 - g0, NT, smem, s>>>(U, O, n, nq, g0));
+  else PW_TIMED(KK_OVERLAPS, s, k_overlaps<double><<<g1 - g0, NT, smem, s>>>(U, O, n, nq, g0));
 }
 
 }  // namespace pw

@@ -786,6 +786,28 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
     cx<T> &x = M[i + (size_t)(2 * n + c) * n];
     x = cmul(v.ep[i], x);
   }
+  if (a.pivratio) {
+    // the spread of U's diagonal (a lower bound on U's condition number)
+    float hi = 0.f, lo = INFINITY;
+    for (int i = tid; i < n; i += VT) {
+      const cx<T> u = M[i + (size_t)i * n];
+      const float m = hypotf(float(u.re), float(u.im));
+      hi = fmaxf(hi, m);
+      lo = fminf(lo, m);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      hi = fmaxf(hi, __shfl_down_sync(0xffffffffu, hi, off));
+      lo = fminf(lo, __shfl_down_sync(0xffffffffu, lo, off));
+    }
+    __shared__ float ext[2][VT / 32];
+    if ((tid & 31) == 0) { ext[0][tid >> 5] = hi; ext[1][tid >> 5] = lo; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < VT / 32; ++w) { hi = fmaxf(hi, ext[0][w]); lo = fminf(lo, ext[1][w]); }
+      const float r = lo > 0.f ? hi / lo : INFINITY;
+      a.pivratio[pt] = fmaxf(a.pivratio[pt], r);
+    }
+  }
   if (p < N) return;
   __syncthreads();
   // t_ij = sqrt(k_i^R / k_j^L) S11_ij on open channels, T = sum |t_ij|^2

@@ -87,8 +87,14 @@ def test_potential_tables_match_oracle(pw):
 # ---------------------------------------------------------------------------
 # a2, a3: eigenmodes and overlaps
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("ng,nsl", [(21, 16), (97, 6)])
+@pytest.mark.parametrize("ng,nsl", [(21, 16), (97, 6), (21, 330)])
 def test_slice_modes_against_oracle_hamiltonians(pw, ng, nsl):
+    """FP64 eigenmodes and overlaps.  The last case's 332 matrices are more
+    than the solver holds at once (pw_eig_wave: two per SM at this order on a
+    152-SM GPU), so its partial last wave runs on the side stream beside the
+    overlaps of the slices done before it, and the remaining overlaps follow."""
+    if nsl == 330:
+        assert 0 < pw.eig_wave(21) < nsl + 2
     _check_slice_modes(pw, ng, nsl, precision=0, tol=1.0)
 
 
