@@ -10,6 +10,9 @@ points, and T = Tr(t^H t).  Metric: (E, k_par)-points/s.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
     python bench.py --impl reference   # the CPU oracle on the host cores
     python bench.py --config uneven [--instances K]   # uneven-batch form
+    python bench.py --config grad [--grad-points P]   # adjoint form (FP64)
+    python bench.py --config scan                     # second workload (Tbar scans)
+    python bench.py --composition doubling --instances P   # Eq. recurrence2 (FP64)
 
 The uneven-batch line times pw_transmission_batch over the first K of the
 2048 seeded instances of uneven N_G (128..768) and slice count (60..400), one
@@ -545,6 +548,59 @@ def run_scan(args, torch, pw, local):
     print(json.dumps(line))
 
 
+def run_grad(args, torch, pw, local):
+    """The adjoint form (pw_grad, FP64, checkpointed recomputation): the summed
+    T of one k_par x P energies of the N_G = 512, 320-slice junction (its
+    64 E x 16 k_par gradient workload) and the derivatives of that sum by
+    every well depth and by the sheet gap; one step is one call."""
+    inst = junction(ng=512, n_slices=320, n_e=64, n_k=16)
+    P = max(1, min(args.grad_points, 64))
+    stream = torch.cuda.current_stream()
+    ctx = pw.Context.from_instance(inst, precision=pw.FP64, stream=stream.cuda_stream)
+    nw = len(inst.v0)
+
+    def pts(s):
+        kk = s % 16
+        idx = np.arange(kk * 64, kk * 64 + P)
+        return inst.energies[idx], inst.kpar[idx]
+
+    for s in range(args.warmup):
+        ctx.grad(*pts(s), n_wells=nw, gap=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res = None
+    for s in range(args.steps):
+        res = ctx.grad(*pts(args.warmup + s), n_wells=nw, gap=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ws = ctx.workspace_bytes()
+    n, N = ctx.ng, ctx.n_slices
+    nc = 8   # incident columns of these points, padded to 4 (n_open <= 5)
+    full = 16.0 * ((N + 1) * (n * n + n * nc) + 4 * (N + 2) * n * nc)
+    line = {
+        "metric": "points/s of the adjoint (sum of T and its derivatives by 48 well depths and the gap, FP64)",
+        "value": args.steps * P / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": f"junction512 gradient: AB junction, N_G={n}, {N} slices, 64 E x 16 k_par; "
+                               f"step = 1 k_par x {P} E",
+                   "checkpoint_interval": "ceil(sqrt(N+1))"},
+        "sum_T_last_step": res[0], "dgap_last_step": res[2],
+        "memory": {"workspace_bytes": ws, "per_point_bytes": ws / P,
+                   "store_every_interface_per_point_bytes": full},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    ctx.close()
+
+
 def run_doubling(args, torch, pw, local):
     """The layer doubling of Eq. recurrence2 (FP64, one point after another)
     on points of the chosen workload: a latency path, timed per point."""
@@ -575,7 +631,7 @@ def run_doubling(args, torch, pw, local):
     Ts = torch.empty(npts, dtype=torch.float64, device="cuda")
     ctx.transmission(E, k, Ts, allow_threshold=True)
     torch.cuda.synchronize()
-    d = (T - Ts).abs() / Ts.abs().clamp(min=1.0)
+    d = (T - Ts).abs() / Ts.abs().clamp(min=T_FLOOR)
     line = {
         "metric": "points/s by layer doubling (Eq. recurrence2, FP64)",
         "value": args.steps * npts / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
@@ -600,7 +656,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--config", default="junction512",
-                    choices=["junction512", "junction401", "minimal", "uneven", "scan"])
+                    choices=["junction512", "junction401", "minimal", "uneven", "scan", "grad"])
+    ap.add_argument("--grad-points", type=int, default=8,
+                    help="grad config: energies of one k_par per pw_grad call")
     ap.add_argument("--instances", type=int, default=96,
                     help="uneven config: how many of the 2048 instances one step covers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -638,6 +696,8 @@ def main():
         return run_uneven(args, torch, pw, local)
     if args.config == "scan":
         return run_scan(args, torch, pw, local)
+    if args.config == "grad":
+        return run_grad(args, torch, pw, local)
     if args.composition == "doubling":
         return run_doubling(args, torch, pw, local)
     if world > 1:
@@ -699,6 +759,7 @@ def main():
     ctx.set_profiling(False)
     nopen_last = nop.cpu().numpy()
     err_max = float(err.max().item())
+    fb_points, fb_spread = ctx.fp64_fallback()
     flops_per_launch = sum(sweep_flops_per_point(n, int(nl)) for nl in nopen_last[:, 0])
     ms_max = reduce_max(ms, world, "cuda")
     total_points = args.steps * n_e * world
@@ -836,6 +897,7 @@ def main():
             "accuracy": {"refine_passes_per_step": (prof["refine_stages"] / max(args.steps, 1)
                                                     if prec == pw.MIXED_FP32 else 0),
                          "err_est_max_last_step": err_max,
+                         "fp64_fallback_last_step": {"points": fb_points, "max_lu_diag_spread": fb_spread},
                          "vs_oracle": accuracy_vs_oracle,
                          "target_rel_T": 1e-8 if prec == pw.MIXED_FP32 else 1e-10},
             "clocks": clk,

