@@ -12,6 +12,7 @@ points, and T = Tr(t^H t).  Metric: (E, k_par)-points/s.
     python bench.py --config uneven [--instances K]   # uneven-batch form
     python bench.py --config grad [--grad-points P]   # adjoint form (FP64)
     python bench.py --config scan                     # second workload (Tbar scans)
+    python bench.py --config modes [--slices N]       # the mode stage alone (FP64)
     python bench.py --composition doubling --instances P   # Eq. recurrence2 (FP64)
 
 The uneven-batch line times pw_transmission_batch over the first K of the
@@ -50,6 +51,10 @@ T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
 # 527.2/589, 451.5/512, 381.3/441 MB); the roofline's `traffic` is this ratio times the step's
 # average algorithmic bytes per launch.  A kernel changed since its capture has no entry.
 KERNEL_TRAFFIC = {"kb_trail": 0.88}
+# DRAM bytes per matrix of the FP64 eigensolver from its ncu capture (64 matrices of
+# N_G = 512, one launch: 186.2 + 152.3 MB, profiles/k_heev_junction512_64matrices.md);
+# the roofline's `traffic` is this times the matrices of the timed launch
+KERNEL_TRAFFIC_PER_MATRIX = {"k_heev": (186.19e6 + 152.32e6) / 64}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -59,6 +64,8 @@ def workload(name):
         return junction(ng=512, n_slices=320, n_e=128, n_k=32), 128, 32
     if name == "junction401":
         return junction(ng=0, ecut=29.34, n_slices=240, n_e=128, n_k=32), 128, 32
+    if name == "junction48":
+        return junction(ng=48, n_slices=16, n_e=128, n_k=32), 128, 32
     if name == "minimal":
         inst = minimal_cell(energies=np.linspace(0.3, 6.0, 128),
                             kpar=np.zeros((128, 2)))
@@ -548,6 +555,65 @@ def run_scan(args, torch, pw, local):
     print(json.dumps(line))
 
 
+def run_modes(args, torch, pw, local):
+    """The mode stage alone (rows a2, a3): the N + 2 slice eigendecompositions
+    and N + 1 overlaps of one k_par of the N_G = 512 junction in FP64
+    (pw_slice_modes, the same kernels in both forms); a step is one k_par."""
+    inst, n_e, n_k = workload("junction512")
+    if args.slices:
+        inst.z_edges = np.linspace(inst.z_edges[0], inst.z_edges[-1], args.slices + 1)
+    stream = torch.cuda.current_stream()
+    ctx = pw.Context.from_instance(inst, precision=pw.FP64, stream=stream.cuda_stream)
+    n, N = ctx.ng, ctx.n_slices
+    nq = N + 2
+
+    def kpar(s):
+        return inst.kpar[(s % n_k) * n_e]
+
+    for s in range(args.warmup):
+        ctx.slice_modes(kpar(s))
+    torch.cuda.synchronize()
+    ctx.set_profiling(True, stride=1)
+    ctx.get_kernel_profile(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(args.steps):
+        ctx.slice_modes(kpar(args.warmup + s))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    rows = kernel_table(ctx.get_kernel_profile(reset=True), args.steps)
+    ctx.set_profiling(False)
+    flops = heev_flops_per_matrix(n) * nq + overlap_flops_per_pair(n) * (nq - 1)
+    try:
+        own = pw.measure_peaks()
+    except Exception:       # noqa: BLE001  (reported as missing)
+        own = {}
+    fp64_peak = max(own.get("fp64_fma") or 0.0, own.get("fp64_mma") or 0.0) or None
+    tf = flops / (ms / args.steps / 1e3) / 1e12
+    line = {
+        "metric": "slice eigendecompositions per second (mode stage: eigenmodes and overlaps, FP64)",
+        "value": args.steps * nq / (ms / 1e3), "unit": "matrices/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": f"junction512 mode stage: N_G={n}, {nq} slice Hamiltonians and {nq - 1} "
+                               f"overlaps of one k_par; step = 1 k_par",
+                   "eig_wave": pw.eig_wave(n)},
+        "tflops": tf, "fp64_peak_tflops": fp64_peak,
+        "frac_of_fp64_peak": tf / fp64_peak if fp64_peak else None,
+        "algorithmic_flops_per_step": flops,
+        "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows],
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    ctx.close()
+
+
 def run_grad(args, torch, pw, local):
     """The adjoint form (pw_grad, FP64, checkpointed recomputation): the summed
     T of one k_par x P energies of the N_G = 512, 320-slice junction (its
@@ -560,8 +626,9 @@ def run_grad(args, torch, pw, local):
     nw = len(inst.v0)
 
     def pts(s):
-        kk = s % 16
-        idx = np.arange(kk * 64, kk * 64 + P)
+        # energies from the middle of the window, where both electrodes have open channels
+        kk = 5 + s % 8
+        idx = np.arange(kk * 64 + 32, kk * 64 + 32 + P) % (64 * 16)
         return inst.energies[idx], inst.kpar[idx]
 
     for s in range(args.warmup):
@@ -656,7 +723,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--config", default="junction512",
-                    choices=["junction512", "junction401", "minimal", "uneven", "scan", "grad"])
+                    choices=["junction512", "junction401", "junction48", "minimal", "uneven", "scan", "grad",
+                             "modes"])
     ap.add_argument("--grad-points", type=int, default=8,
                     help="grad config: energies of one k_par per pw_grad call")
     ap.add_argument("--instances", type=int, default=96,
@@ -698,6 +766,8 @@ def main():
         return run_scan(args, torch, pw, local)
     if args.config == "grad":
         return run_grad(args, torch, pw, local)
+    if args.config == "modes":
+        return run_modes(args, torch, pw, local)
     if args.composition == "doubling":
         return run_doubling(args, torch, pw, local)
     if world > 1:
@@ -874,6 +944,10 @@ def main():
                 obj.update({"bound": "tensor" if on_tc else "alu", "achieved": ach, "peak": cpeak,
                             "unit": "TFLOP/s", "frac": ach / cpeak, "peak_source": csrc,
                             "algorithmic_flops_per_launch": flops / (row["launches_per_step"] or 1)})
+                if key in KERNEL_TRAFFIC_PER_MATRIX and fp64_modes and n == 512:
+                    obj.update({"traffic": KERNEL_TRAFFIC_PER_MATRIX[key] * n_main,
+                                "traffic_source": "ncu DRAM bytes per matrix of a 64-matrix capture x the "
+                                                  "matrices of the timed launch"})
             return obj
 
         dominant = roof(rows[0]) if rows else None

@@ -458,7 +458,9 @@ pw_status pw_transmission_batch(pw_batch *b, const double *E, const double *kpar
 
 /* Options of a batch: use_graph (1 = record and replay each chunk's sweep as a
  * CUDA graph, 0 = launch it directly), variant (-1 = autotune per N_G, else a
- * sweep variant as for pw_set_sweep_variant, for every size). */
+ * sweep variant as for pw_set_sweep_variant, for every size).  The mixed
+ * form's eigenmodes and overlaps are FP64 unless a forced variant has bit 5
+ * (double-float). */
 pw_status pw_batch_set_options(pw_batch *b, int use_graph, int variant);
 
 /* Stage times of the last pw_transmission_batch, out[8] = {slice-mode ms,

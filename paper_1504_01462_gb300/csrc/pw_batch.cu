@@ -148,11 +148,14 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
       (st = grow(b, b->dz, (size_t)nmat * sizeof(double))))
     return st;
   const bool mixed = b->precision == PW_MIXED_FP32;
+  // the mixed form's modes and overlaps in FP64, or, when every size is forced
+  // to a variant with bit 5, in double-float
+  const bool dfe = mixed && b->force_variant >= 0 && (b->force_variant & 32);
   if (mixed && ((st = grow(b, b->O32, (size_t)nov * nn * sizeof(cc))) ||
                 (st = grow(b, b->O32t, (size_t)nov * nn * sizeof(cc))) ||
-                (st = grow(b, b->O32lo, (size_t)nov * nn * sizeof(cc))) ||
-                (st = grow(b, b->eigws, pw::heev_ws_bytes(n, (int)nmat)))))
+                (st = grow(b, b->O32lo, (size_t)nov * nn * sizeof(cc)))))
     return st;
+  if (dfe && (st = grow(b, b->eigws, pw::heev_ws_bytes(n, (int)nmat)))) return st;
   zc *HU = (zc *)b->HU.p, *O = (zc *)b->O.p;
   double *En = (double *)b->En.p;
   std::vector<double> dzh((size_t)nmat);
@@ -177,13 +180,12 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     pw::launch_assemble_h(HU + mb[j] * nn, v.tab, v.mn, v.G, kpar[2 * i], kpar[2 * i + 1], n, v.N + 2, v.Dm,
                           v.Dn, s);
   }
-  pw::launch_eig(HU, (zc *)b->V.p, En, (int *)b->stat.p, n, (int)nmat, s, b->precision == PW_MIXED_FP32,
-                 mixed ? b->eigws.p : nullptr, mixed ? b->eigws.bytes : 0);
+  pw::launch_eig(HU, (zc *)b->V.p, En, (int *)b->stat.p, n, (int)nmat, s, dfe, dfe ? b->eigws.p : nullptr,
+                 dfe ? b->eigws.bytes : 0);
   BCK(cudaGetLastError());
   BCK(cudaEventRecord(ev[1], s));
   for (int j = 0; j < m; ++j)
-    pw::launch_overlaps(HU + mb[j] * nn, O + ob[j] * nn, n, b->view[ids[j]].N + 2, 1, s,
-                        b->precision == PW_MIXED_FP32);
+    pw::launch_overlaps(HU + mb[j] * nn, O + ob[j] * nn, n, b->view[ids[j]].N + 2, 1, s, dfe);
   if (mixed) pw::launch_overlaps_fp32(O, (cc *)b->O32.p, (cc *)b->O32t.p, (cc *)b->O32lo.p, n, (int)nov, s);
   BCK(cudaGetLastError());
   BCK(cudaEventRecord(ev[2], s));

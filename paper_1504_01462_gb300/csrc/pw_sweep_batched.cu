@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc16(SweepArgs a, in
 constexpr int RMW_TN = 64;
 
 // trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb)
-__global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j0) {
+__global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_trail_tc(SweepArgs a, int j0) {
   extern __shared__ __align__(128) unsigned char smtc[];
   unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_trail_tc(SweepArgs a, int j
 }
 
 // back-substitution update above block j0 (kb rows): M[0:j0, n:ncols] -= U[0:j0, b] X_b
-__global__ void __launch_bounds__(tc::CG_THREADS) kb_bsupd_tc(SweepArgs a, int j0, int kb) {
+__global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_bsupd_tc(SweepArgs a, int j0, int kb) {
   extern __shared__ __align__(128) unsigned char smtc[];
   unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
