@@ -853,8 +853,8 @@ def main():
     # GPU form timed on a bounded sample of the same step
     accuracy_vs_oracle = None
     fp64_arm = None
-    if rank == 0 and not args.no_accuracy and args.config == "junction512" and not args.slices:
-        gold = golden_junction512()
+    if rank == 0 and not args.no_accuracy and args.config in ("junction512", "junction401") and not args.slices:
+        gold = golden_junction512() if args.config == "junction512" else None
         if gold is not None:
             kk = gold["k_index"]
             idx = np.arange(kk * n_e, (kk + 1) * n_e)
@@ -869,6 +869,19 @@ def main():
                                   "T_floor": T_FLOOR,
                                   "T_min_nonzero": float(np.min(ref[have & (ref > 0)])) if (have & (ref > 0)).any()
                                   else None}
+        if args.config == "junction401":
+            path = os.path.join(ROOT, "tests", "golden", "junction401.json")
+            if os.path.exists(path):
+                with open(path) as f:
+                    g4 = json.load(f)
+                E4, k4 = np.array(g4["energies"]), np.array(g4["kpar"]).reshape(-1, 2)
+                T4 = torch.empty(len(E4), dtype=torch.float64, device="cuda")
+                ctx.transmission(E4, k4, T4)
+                torch.cuda.synchronize()
+                ref = np.array(g4["T"], dtype=np.float64)
+                rel = np.abs(T4.cpu().numpy() - ref) / np.maximum(np.abs(ref), T_FLOOR)
+                accuracy_vs_oracle = {"points": len(E4), "max_rel_err_T": float(rel.max()), "T_floor": T_FLOOR,
+                                      "stored": "tests/golden/junction401.json"}
         if prec == pw.MIXED_FP32 and not args.no_fp64:
             ctx.close()
             torch.cuda.empty_cache()

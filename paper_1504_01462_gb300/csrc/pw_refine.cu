@@ -520,59 +520,78 @@ __global__ void __launch_bounds__(RS_THREADS) k_res_oslice(RefineArgs a, int p) 
   }
 }
 
-// B' of interface p: block j cuts column j = pt 2nc + c (c < nc: a_q + e b_q of
-// channel c; c >= nc: K_q (a_q - e b_q) of channel c - nc); zero for points
-// that are skipped, failed or shorter than p.
+// B' of interface p: block (pt, h) cuts the nc columns j = pt 2nc + h nc + ch,
+// ch < nc (h = 0: a_q + e b_q of channel ch; h = 1: K_q (a_q - e b_q)); zero
+// for points that are skipped, failed or shorter than p.  The wavenumbers and
+// phases of slice q = p + 1 (FP64 square roots and exponentials) are formed
+// once per block for its nc columns.
 __global__ void __launch_bounds__(RS_THREADS) k_res_yslice(RefineArgs a, int p) {
   __shared__ float red[RS_THREADS / 32];
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n = a.n, nc = a.nc, K = 2 * n, ncol = gridDim.x;
-  const int j = blockIdx.x, pt = j / (2 * nc), c = j % (2 * nc), ch = c < nc ? c : c - nc;
+  const int n = a.n, nc = a.nc, K = 2 * n, ncol = gridDim.x * 2 * nc;
+  const int pt = blockIdx.x, h = blockIdx.y, jb = pt * 2 * nc + h * nc;
   const PointDesc d = a.pts[pt];
   const size_t stride = (size_t)ncol * K;
-  uint16_t *out = a.Ysl + (size_t)j * K;
   if (d.skip || a.status[pt] || p > d.N) {
-    for (int k = threadIdx.x; k < K; k += RS_THREADS)
+    for (int ch = 0; ch < nc; ++ch) {
+      uint16_t *out = a.Ysl + (size_t)(jb + ch) * K;
+      for (int k = threadIdx.x; k < K; k += RS_THREADS)
 #pragma unroll
-      for (int s = 0; s < RS_SLICES; ++s) out[(size_t)s * stride + k] = 0;
-    if (threadIdx.x == 0) a.Yexp[j] = 0;
+        for (int s = 0; s < RS_SLICES; ++s) out[(size_t)s * stride + k] = 0;
+      if (threadIdx.x == 0) a.Yexp[jb + ch] = 0;
+    }
     return;
   }
   KV v = carve_kv(smraw, 0, n);
-  load_kv(a, d, p, v);
   const int q = p + 1;
-  const bool has_bq = q <= d.N;
-  const zc *aq = a.Xa + blk(a, d, q) + (size_t)ch * n;
-  const zc *bq = a.Xb + blk(a, d, q) + (size_t)ch * n;
-  auto yv = [&](int l) -> dfc {
-    const zc A = aq[l];
-    const zc eb = has_bq ? cmul(v.eR[l], bq[l]) : czero<double>();
-    return dfc_of(c < nc ? cadd(A, eb) : cmul(v.kR[l], csub(A, eb)));
-  };
-  float m = 0.f;
-  for (int l = threadIdx.x; l < n; l += RS_THREADS) {
-    const dfc y = yv(l);
-    m = fmaxf(m, fmaxf(fabsf(y.re.hi), fabsf(y.im.hi)));
+  {
+    const double *Eq = a.En + ((size_t)d.en_off + q) * n;
+    const double dzq = a.dz[d.dz_off + q];
+    for (int i = threadIdx.x; i < n; i += RS_THREADS) {
+      const zc kr = kz_branch(d.E, Eq[i]);
+      v.kR[i] = kr;
+      v.eR[i] = phase_fwd(kr, dzq);
+    }
+    __syncthreads();
   }
-  const int e = scale_exponent(block_maxf(m, red));
-  if (threadIdx.x == 0) a.Yexp[j] = e;
-  for (int l = threadIdx.x; l < n; l += RS_THREADS) {
-    const dfc y = yv(l);
-    cut_slices_df(y.re.hi, y.re.lo, e, out + l, stride);
-    cut_slices_df(y.im.hi, y.im.lo, e, out + n + l, stride);
+  const bool has_bq = q <= d.N;
+  for (int ch = 0; ch < nc; ++ch) {
+    const int j = jb + ch;
+    uint16_t *out = a.Ysl + (size_t)j * K;
+    const zc *aq = a.Xa + blk(a, d, q) + (size_t)ch * n;
+    const zc *bq = a.Xb + blk(a, d, q) + (size_t)ch * n;
+    auto yv = [&](int l) -> dfc {
+      const zc A = aq[l];
+      const zc eb = has_bq ? cmul(v.eR[l], bq[l]) : czero<double>();
+      return dfc_of(h == 0 ? cadd(A, eb) : cmul(v.kR[l], csub(A, eb)));
+    };
+    float m = 0.f;
+    for (int l = threadIdx.x; l < n; l += RS_THREADS) {
+      const dfc y = yv(l);
+      m = fmaxf(m, fmaxf(fabsf(y.re.hi), fabsf(y.im.hi)));
+    }
+    const int e = scale_exponent(block_maxf(m, red));
+    if (threadIdx.x == 0) a.Yexp[j] = e;
+    for (int l = threadIdx.x; l < n; l += RS_THREADS) {
+      const dfc y = yv(l);
+      cut_slices_df(y.re.hi, y.re.lo, e, out + l, stride);
+      cut_slices_df(y.im.hi, y.im.lo, e, out + n + l, stride);
+    }
   }
 }
 
 // Yacc = A' B' summed over the slice pairs.  One CTA per 128 x 128 tile of
 // A' B'; K in stages of 64 (four BF16 MMAs of M = N = 128, K = 16) through a
-// ring of RS_RING shared-memory stages filled by cp.async, so that RS_RING - 1
-// stages of operand loads are in flight while the tensor core multiplies.
+// ring of RS_RING shared-memory stages filled by cp.async: RS_AHEAD stages of
+// operand loads are in flight, and a stage's slot is refilled once the MMAs
+// of the stage two back have completed, so that up to three stages of MMAs
+// queue on the tensor core instead of one.
 // Each pair accumulates in one of two TMEM buffers (128 columns each); the
 // finished pair's buffer is read back and added into the double-float
 // registers in eight column chunks spread over the next pair's stages, so the
 // read-back overlaps the next pair's products.  Warp w holds TMEM lanes
 // 32 (w % 4) .. + 31 (rows) and columns 64 (w / 4) .. + 63.
-constexpr int RS_TILE = 128, RS_KS = 64, RS_RING = 6;
+constexpr int RS_TILE = 128, RS_KS = 64, RS_RING = 6, RS_AHEAD = RS_RING - 2;
 constexpr int RS_OPER = RS_TILE * RS_KS * 2;   // bytes of one operand per stage
 constexpr int RS_STAGE = 2 * RS_OPER;
 constexpr int RS_DF_BELOW = 4;                 // pairs with s + t < 4 add in double-float, the rest in FP32
@@ -648,12 +667,12 @@ __global__ void __launch_bounds__(256, 1) k_res_mm(RefineArgs a, int ncol, int n
     }
   };
 
-  for (int g = 0; g < RS_RING - 1; ++g) load_stage(g);
+  for (int g = 0; g < RS_AHEAD; ++g) load_stage(g);
   bool ok = true;
   int last = -1;   // the last stage whose MMAs were issued
   for (int g = 0; g < G; ++g) {
     const int P = g / ns, st = g - P * ns;
-    tc::cp_async_wait<RS_RING - 2>();   // this thread's copies of stage g have landed
+    tc::cp_async_wait<RS_AHEAD - 1>();   // this thread's copies of stage g have landed
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     ok = __syncthreads_and(ok) != 0;
@@ -670,13 +689,19 @@ __global__ void __launch_bounds__(256, 1) k_res_mm(RefineArgs a, int ncol, int n
       tc::mma_commit(&mbar[g % RS_RING]);
     }
     last = g;
-    // stage g - 1's slot is free once its MMAs are done: refill it with stage g + RS_RING - 1
-    if (g >= 1) ok = tc::mbar_wait(&mbar[(g - 1) % RS_RING], ((g - 1) / RS_RING) & 1) && ok;
+    // stage g - 2's slot is free once its MMAs are done: refill it with stage
+    // g + RS_AHEAD (the slots of stages g - 1 .. g + RS_AHEAD - 1 stay in use)
+    if (g >= 2) ok = tc::mbar_wait(&mbar[(g - 2) % RS_RING], ((g - 2) / RS_RING) & 1) && ok;
     tc::fence_after_sync();
-    if (ok) load_stage(g + RS_RING - 1);
+    if (ok) load_stage(g + RS_AHEAD);
     else tc::cp_async_commit();
-    // pair P - 1 is complete (its last stage is g - 1 or earlier): read back the
-    // chunks q with q ns / 8 == st
+    // pair P - 1's last stage is g - st - 1, complete once st >= 1 (stage g - 2
+    // waited for above); at st == 0 it is stage g - 1, waited for here
+    if (P > 0 && st == 0 && ok) {
+      ok = tc::mbar_wait(&mbar[(g - 1) % RS_RING], ((g - 1) / RS_RING) & 1) && ok;
+      tc::fence_after_sync();
+    }
+    // read back pair P - 1's chunks q with q ns / 8 == st
     if (P > 0 && __all_sync(0xffffffffu, ok)) {
 #pragma unroll
       for (int q = 0; q < 8; ++q)
@@ -868,7 +893,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
       const int ncol = 2 * a.nc * npts;
       for (int p = 0; p <= a.N; ++p) {
         PW_TIMED(KK_RES_OSLICE, s, k_res_oslice<<<a.n, RS_THREADS, 0, s>>>(a, p));
-        PW_TIMED(KK_RES_YSLICE, s, k_res_yslice<<<ncol, RS_THREADS, kv_bytes, s>>>(a, p));
+        PW_TIMED(KK_RES_YSLICE, s, k_res_yslice<<<dim3(npts, 2), RS_THREADS, kv_bytes, s>>>(a, p));
         PW_TIMED(KK_RES_MM, s, k_res_mm<<<rs_tiles, 256, res_mm_smem_bytes(), s>>>(a, ncol, npts));
         PW_TIMED(KK_RES_FINISH, s, k_res_finish<<<npts, NT, kv_bytes, s>>>(a, p, ncol));
       }
