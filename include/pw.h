@@ -395,9 +395,12 @@ pw_status pw_get_fp64_fallback(const pw_ctx *ctx, int *points, double *max_pivot
  * multiple of 4 up to 512); bit 5, the slice eigenmodes and the overlaps in
  * double-float instead of FP64 (a mode stage about 4x faster, but 48-bit
  * modes: at a sharp antiresonance of T the error on T can exceed 1e-8
- * relative).  The mode cache of a k_par is kept across variant changes; set
+ * relative); bit 6, a batch of 32 points or more swept as two point groups
+ * on two streams (the context's stream and a second one the context owns),
+ * so that one group's latency-bound kernels run beside the other's wide
+ * ones.  The mode cache of a k_par is kept across variant changes; set
  * the variant before the first call.  PW_EINVAL for a variant the context's
- * precision does not have (0..1 for PW_FP64, 0..63 for PW_MIXED_FP32). */
+ * precision does not have (0..1 for PW_FP64, 0..127 for PW_MIXED_FP32). */
 pw_status pw_set_sweep_variant(pw_ctx *ctx, int variant);
 
 /* Timing of the library's own launches (for benchmarks and roofline

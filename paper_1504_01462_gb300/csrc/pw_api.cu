@@ -202,6 +202,10 @@ struct pw_ctx {
   int last_fp64_points = 0;
   double last_pivot_ratio = 0.0;
   DevBuf pivr, R64, M64, piv64, KV64, pts64, st64;
+  // second stream and its fork/join events for the two point groups of the
+  // sweep (sweep variant bit 6)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -719,6 +723,12 @@ pw_status pw_setup(const pw_setup_desc *d, void *cuda_stream, pw_ctx **out) {
 void pw_destroy(pw_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
                   ctx->d_O, ctx->d_O32, ctx->d_O32t, ctx->d_O32lo, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
@@ -1299,13 +1309,52 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       CK(pw::prepare_sweep_batched(n, ctx->precision, ctx->sweep_variant));
       // the FP16-split [W|Y] adds its row-scale kernel at every interface with a product (p >= 1)
       const int f16_extra = (a.rowexp && a.wy_pairs && (ctx->sweep_variant & 6) == 6) ? N : 0;
-      Stage s0(ctx, 0, (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant) + f16_extra);
+      // Sweep variant bit 6: the batch as two point groups, each swept on its
+      // own stream, so that one group's latency-bound kernels (panels,
+      // diagonal blocks, one CTA per point) run beside the other group's
+      // wide update kernels.  The groups share no per-point state.
+      int hA = nb;
+      cudaStream_t s2 = nullptr;
+      if ((ctx->sweep_variant & 64) && nb >= 32) {
+        hA = (nb / 2) & ~1;
+        if (!ctx->side) {
+          if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+              cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return latch(ctx, PW_ECUDA);
+          }
+        }
+        s2 = ctx->side;
+      }
+      pw::SweepArgs aB = a;
+      if (s2) {
+        a.wy_pairs = pw::points_pair_up(pd.data(), hA);
+        aB.wy_pairs = pw::points_pair_up(pd.data() + hA, nb - hA);
+        aB.pts = a.pts + hA;
+        aB.R = (unsigned char *)a.R + (size_t)hA * nn * esz;
+        aB.M = (unsigned char *)a.M + (size_t)hA * n * ncols * esz;
+        aB.piv = a.piv + (size_t)hA * n;
+        aB.status = a.status + hA;
+        aB.KV = (unsigned char *)a.KV + (size_t)hA * 3 * n * esz;
+        if (a.rowexp) aB.rowexp = a.rowexp + (size_t)hA * 2 * n;
+        if (a.pivratio) aB.pivratio = a.pivratio + hA;
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
+      }
+      Stage s0(ctx, 0, (s2 ? 2 : 1) * (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant) +
+                           f16_extra);
       for (int p = 0; p <= N; ++p) {
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
-        CK(pw::launch_sweep_batched(a, nb, p, ctx->precision, ctx->stream, w0, w1, ctx->sweep_variant));
+        CK(pw::launch_sweep_batched(a, hA, p, ctx->precision, ctx->stream, w0, w1, ctx->sweep_variant));
         if (w0) ctx->recs.push_back({w0, w1, 4, 1});
+        if (s2) CK(pw::launch_sweep_batched(aB, nb - hA, p, ctx->precision, s2, nullptr, nullptr, ctx->sweep_variant));
         SYNC_CHECK();
+      }
+      if (s2) {
+        CK(cudaEventRecord(ctx->ev_join, s2));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
       }
       s0.done();
       if (refine) {

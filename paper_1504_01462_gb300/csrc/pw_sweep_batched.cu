@@ -1003,7 +1003,7 @@ cudaError_t launch_sweep_batched(const SweepArgs &a, int npts, int p, int precis
                        : sweep_step<float, 256>(a, npts, p, s, wy0, wy1, tcore, f16, big);
 }
 
-int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 64; }
+int sweep_variants(int precision) { return precision == PW_FP64 ? 2 : 128; }
 
 std::vector<int> sweep_variant_candidates(int precision) {
   if (precision == PW_FP64) return {0, 1};

@@ -111,3 +111,21 @@ def test_bounded_wait_runs_out_and_reports(pw):
     assert lib.pw_selftest_bounded_wait(0, 0) == 1        # PW_EINVAL
     e1, e3 = pw.selftest_tensor_core()
     assert e3 < 1e-5
+
+
+def test_sweep_as_two_point_groups(pw):
+    """Sweep variant bit 6: 40 points of one k_par swept as two groups of 20
+    on two streams give the T of one group (each point runs the same kernels,
+    and the point pairs of the [W|Y] product stay together), and meet 1e-8
+    against the oracle."""
+    import numpy as np
+    from oracle import pw_oracle as O
+    from synthetic import junction
+    inst = junction(ng=97, n_slices=30, n_e=40, n_k=1)
+    E, k = inst.energies, inst.kpar
+    one = _T(pw, inst, E, k, 2, 4)
+    two = _T(pw, inst, E, k, 2 | 64, 4)
+    assert np.all(np.abs(one - two) <= 1e-14 * np.maximum(1.0, np.abs(one))), np.abs(one - two).max()
+    sel = [3, 17, 25, 38]
+    ref = O.transmission(inst, points=sel)
+    assert np.all(rel_T(two[sel], ref) < 1e-8), (two[sel], ref)
