@@ -48,9 +48,9 @@ MIXED_DEFAULT_VARIANT = 2    # the library's default launch variant of the mixed
 T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
 # DRAM traffic of kernels captured with ncu: dram__bytes_read + dram__bytes_write of the
 # captured launches over their algorithmic bytes (profiles/kb_trail_tc_junction512_small.md:
-# 527.2/589, 451.5/512, 381.3/441 MB); the roofline's `traffic` is this ratio times the step's
+# 567.4/589, 490.1/512, 411.3/441 MB); the roofline's `traffic` is this ratio times the step's
 # average algorithmic bytes per launch.  A kernel changed since its capture has no entry.
-KERNEL_TRAFFIC = {"kb_trail": 0.88}
+KERNEL_TRAFFIC = {"kb_trail": 0.95}
 # DRAM bytes per matrix of the FP64 eigensolver from its ncu capture (64 matrices of
 # N_G = 512, one launch: 186.2 + 152.3 MB, profiles/k_heev_junction512_64matrices.md);
 # the roofline's `traffic` is this times the matrices of the timed launch

@@ -206,6 +206,13 @@ struct pw_ctx {
   // sweep (sweep variant bit 6)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the mode stage's partial wave left running for pw_transmission (ensure_ksets
+  // with defer): its stream, the event after its matrices, overlaps and FP32
+  // copies, the first interface that needs them, and its matrices' range
+  cudaStream_t tail_stream = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_tail = nullptr;
+  bool tail_pending = false;
+  int tail_iface = 0, tail_m0 = 0, tail_m1 = 0;
 };
 
 namespace {
@@ -395,12 +402,40 @@ pw_status alloc_slots(pw_ctx *ctx) {
   return PW_OK;
 }
 
+// Orders the context's stream after a partial wave left running by
+// ensure_ksets (defer) and checks its matrices' convergence.
+pw_status join_tail(pw_ctx *ctx) {
+  if (!ctx->tail_pending) return PW_OK;
+  ctx->tail_pending = false;
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_tail, 0));
+  const int cnt = ctx->tail_m1 - ctx->tail_m0;
+  std::vector<int> stat(cnt);
+  CK(cudaMemcpyAsync(stat.data(), ctx->d_eigstat + ctx->tail_m0, cnt * sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int v : stat) {
+    if (v < 0) {
+      ctx->slot_valid.assign(ctx->slot_valid.size(), 0);
+      return latch(ctx, PW_ENOTCONV);
+    }
+  }
+  return PW_OK;
+}
+
 // Eigenmodes and overlaps of every slice for the k values ks[0..K-1] in slots
 // 0..K-1 (K <= ks_cap).  Slots that already hold their k are kept; the others
 // are recomputed with one eigensolver launch over all their matrices.
-pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
+// defer (one slot, FP64 solver): when the solver's grid ends in a partial
+// wave, that wave takes the slot's last device slices (the electrodes stay in
+// the full waves), and it, the overlaps that need its slices and their FP32
+// copies are left running on the tail stream: on return ctx->tail_pending is
+// set, interfaces p < ctx->tail_iface are ready on the context's stream, and
+// the caller makes its stream wait for ctx->ev_tail before interface
+// ctx->tail_iface and then calls join_tail.
+pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks, bool defer = false) {
   pw_status st = alloc_slots(ctx);
   if (st) return st;
+  if ((st = join_tail(ctx))) return st;
   const int n = ctx->n, nq = ctx->nq, K = (int)ks.size();
   const size_t nn = (size_t)n * n;
   int s0 = K, s1 = 0;
@@ -431,6 +466,68 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks) {
   if (!dfe) {
     const int res = pw::heev_resident_per_sm(n) * ctx->num_sms;
     if (res > 0 && nmat > res && nmat % res) nA = nmat - nmat % res;
+  }
+  if (defer && !dfe && s1 - s0 == 1 && nA < nmat && nA >= 3) {
+    // the partial wave beside the sweep: matrices nA-1 .. nq-2 (device slices)
+    // on the tail stream; the full waves take 0 .. nA-2 and the right
+    // electrode nq-1 (the grid's last CTA)
+    if (!ctx->tail_stream &&
+        (cudaStreamCreateWithFlags(&ctx->tail_stream, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->ev_tail, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      return latch(ctx, PW_ECUDA);
+    }
+    cudaStream_t ts = ctx->tail_stream;
+    zc *O0 = ctx->d_O + (size_t)s0 * (nq - 1) * nn;
+    const int gT = nA - 2;   // pairs g < gT use the full waves' slices only
+    CK(cudaEventRecord(ctx->ev_main, ctx->stream));   // the Hamiltonians are assembled
+    CK(cudaStreamWaitEvent(ts, ctx->ev_main, 0));
+    pw::launch_eig(HU0, V0, En0, stat0, n, nA, ctx->stream, false, nullptr, 0, false, nq - 1);
+    pw::launch_eig(HU0 + (size_t)(nA - 1) * nn, V0 + (size_t)(nA - 1) * nn, En0 + (size_t)(nA - 1) * n,
+                   stat0 + (nA - 1), n, nmat - nA, ts, false, nullptr, 0, true);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ctx->ev_main, ctx->stream));   // the full waves' modes (and the right electrode's)
+    st1.done();
+    Stage st2(ctx, 2, 1);
+    pw::launch_overlaps(HU0, O0, n, nq, 1, ctx->stream, false, 0, gT);
+    if (ctx->d_O32)
+      pw::launch_overlaps_fp32(O0, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn, ctx->d_O32t + (size_t)s0 * (nq - 1) * nn,
+                               ctx->d_O32lo + (size_t)s0 * (nq - 1) * nn, n, gT, ctx->stream);
+    CK(cudaStreamWaitEvent(ts, ctx->ev_main, 0));
+    pw::launch_overlaps(HU0, O0, n, nq, 1, ts, false, gT, nq - 1);
+    if (ctx->d_O32)
+      pw::launch_overlaps_fp32(O0 + (size_t)gT * nn, ctx->d_O32 + ((size_t)s0 * (nq - 1) + gT) * nn,
+                               ctx->d_O32t + ((size_t)s0 * (nq - 1) + gT) * nn,
+                               ctx->d_O32lo + ((size_t)s0 * (nq - 1) + gT) * nn, n, nq - 1 - gT, ts);
+    CK(cudaEventRecord(ctx->ev_tail, ts));
+    CK(cudaGetLastError());
+    st2.done();
+    // the full waves' convergence and the electrodes' eigenvalues now; the
+    // partial wave's convergence in join_tail
+    std::vector<int> stat(nA);
+    CK(cudaMemcpyAsync(stat.data(), stat0, (nA - 1) * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(stat.data() + nA - 1, stat0 + nq - 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->EL[s0].data(), En0, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->ER[s0].data(), En0 + (size_t)(nq - 1) * n, n * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->last_sweeps = 0;
+    for (int v : stat) {
+      if (v < 0) {
+        CK(cudaStreamSynchronize(ts));
+        return latch(ctx, PW_ENOTCONV);
+      }
+      ctx->last_sweeps = std::max(ctx->last_sweeps, v);
+    }
+    ctx->tail_pending = true;
+    ctx->tail_iface = gT;
+    ctx->tail_m0 = s0 * nq + nA - 1;
+    ctx->tail_m1 = s0 * nq + nq - 1;
+    ctx->slot_k[2 * s0] = ks[s0][0];
+    ctx->slot_k[2 * s0 + 1] = ks[s0][1];
+    ctx->slot_valid[s0] = 1;
+    return PW_OK;
   }
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -729,6 +826,12 @@ void pw_destroy(pw_ctx *ctx) {
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->tail_stream) {
+    cudaStreamSynchronize(ctx->tail_stream);
+    cudaStreamDestroy(ctx->tail_stream);
+  }
+  if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
+  if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
                   ctx->d_O, ctx->d_O32, ctx->d_O32t, ctx->d_O32lo, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
@@ -1215,7 +1318,9 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       ks.push_back(kpar + 2 * groups[gi][0]);
       for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
     }
-    if ((st = ensure_ksets(ctx, ks))) return st;
+    // one k_par: the eigensolver's partial wave runs beside the first
+    // interfaces of the sweep (the sweep waits for it at ctx->tail_iface)
+    if ((st = ensure_ksets(ctx, ks, ks.size() == 1))) return st;
     // point descriptors and the padded incident-column count of the chunk
     std::vector<PointDesc> all(pts.size());
     int nc = 1;
@@ -1345,6 +1450,10 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       Stage s0(ctx, 0, (s2 ? 2 : 1) * (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant) +
                            f16_extra);
       for (int p = 0; p <= N; ++p) {
+        if (ctx->tail_pending && p == ctx->tail_iface) {   // the partial wave's slices from here on
+          CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_tail, 0));
+          if (s2) CK(cudaStreamWaitEvent(s2, ctx->ev_tail, 0));
+        }
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
         CK(pw::launch_sweep_batched(a, hA, p, ctx->precision, ctx->stream, w0, w1, ctx->sweep_variant));
@@ -1434,6 +1543,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         else if (v && result != PW_ETIMEOUT) result = PW_ESINGULAR;
       }
     }
+    if ((st = join_tail(ctx))) return st;
   }
   if (result == PW_ESINGULAR || result == PW_ETIMEOUT) latch(ctx, result);
   return result;

@@ -295,9 +295,11 @@ void launch_assemble_h(zc *H, const zc *tab, const int *mn, const double *G, dou
 // heev_ws_bytes(n, 1), else null) lets its QL recurrence run in double-float
 // as a separate launch over groups of as many matrices as the workspace holds
 // tail: the launch is a partial last wave run on a side stream (timed as its
-// own kernel kind)
+// own kernel kind); remap_last >= 0 (FP64 solver): the grid's last CTA takes
+// matrix remap_last (relative to HU) instead of matrix nmat - 1
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s,
-                bool double_float = false, void *ws = nullptr, size_t ws_bytes = 0, bool tail = false);
+                bool double_float = false, void *ws = nullptr, size_t ws_bytes = 0, bool tail = false,
+                int remap_last = -1);
 size_t heev_ws_bytes(int n, int nmat);
 // CTAs of the FP64 eigensolver resident on one SM at once (order n)
 int heev_resident_per_sm(int n);

@@ -793,13 +793,16 @@ __global__ void __launch_bounds__(32) k_ql_df(HeevWS ws, int *status, int n) {
 // k_eig_sort).
 template <typename R>
 __global__ void __launch_bounds__(HEEV_THREADS, 2) k_heev(zc *HU_all, zc *Z_all, double *En_all,
-                                                       int *status, int n, int part, HeevWS ws) {
+                                                       int *status, int n, int part, HeevWS ws,
+                                                       int remap_last) {
   typedef HeevAr<R> Ar;
   typedef typename Ar::C C;
   typedef typename Ar::Rot Rot;
   constexpr int NTH = HEEV_THREADS;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int mat = blockIdx.x, tid = threadIdx.x;
+  // remap_last >= 0: the grid's last CTA takes matrix remap_last instead
+  const int mat = (remap_last >= 0 && blockIdx.x == gridDim.x - 1) ? remap_last : (int)blockIdx.x;
+  const int tid = threadIdx.x;
   const size_t nn = (size_t)n * n;
   zc *A64 = HU_all + mat * nn;
   C *A = reinterpret_cast<C *>(A64);          // the matrix in the solver's format, in place
@@ -1196,7 +1199,7 @@ int heev_resident_per_sm(int n) {
 }
 
 void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStream_t s, bool double_float,
-                void *ws, size_t ws_bytes, bool tail) {
+                void *ws, size_t ws_bytes, bool tail, int remap_last) {
   if (nmat <= 0) return;
   const size_t smem = heev_smem(n);
   const size_t nn = (size_t)n * n;
@@ -1209,7 +1212,7 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
       while (group > 0 && heev_ws_bytes(n, group) > ws_bytes) group = std::max(0, group - std::max(1, group / 8));
     }
     if (group <= 0) {
-      PW_TIMED(KK_HEEV, s, k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w));
+      PW_TIMED(KK_HEEV, s, k_heev<df><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w, -1));
       return;
     }
     const size_t g = (size_t)group;
@@ -1282,13 +1285,13 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
       }
       PW_TIMED(KK_HEEV, s,
                k_heev<df><<<a_cnt, HEEV_THREADS, smem, s>>>(HU + (size_t)m0 * nn, V + (size_t)m0 * nn,
-                                                            En + (size_t)m0 * n, status + m0, n, 1, w));
+                                                            En + (size_t)m0 * n, status + m0, n, 1, w, -1));
       if (s2) {
         const int mb = m0 + nA, cb = cnt - nA;
         const HeevWS wb = shifted(nA);
         PW_TIMED(KK_HEEV, s2,
                  k_heev<df><<<cb, HEEV_THREADS, smem, s2>>>(HU + (size_t)mb * nn, V + (size_t)mb * nn,
-                                                            En + (size_t)mb * n, status + mb, n, 1, wb));
+                                                            En + (size_t)mb * n, status + mb, n, 1, wb, -1));
         chain(mb, cb, wb, s2);
         cudaEventRecord(join, s2);
       }
@@ -1303,7 +1306,7 @@ void launch_eig(zc *HU, zc *V, double *En, int *status, int n, int nmat, cudaStr
   } else {
     cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     PW_TIMED(tail ? KK_HEEV_TAIL : KK_HEEV, s,
-             k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w));
+             k_heev<double><<<nmat, HEEV_THREADS, smem, s>>>(HU, V, En, status, n, 0, w, remap_last));
   }
 }
 

@@ -272,6 +272,32 @@ def test_transmission_small_junction_fp64(pw):
     assert np.all(_rel(got, ref) < TOL_FP64), (got, ref)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_MIXED)])
+def test_transmission_sweep_beside_eigensolver_partial_wave(pw, precision, tol):
+    """332 slice Hamiltonians of one k_par (N_G = 48, 330 slices) are more
+    than the eigensolver holds at once, so pw_transmission leaves the partial
+    wave (the last device slices) running beside the first interfaces of the
+    sweep, the right electrode in the full wave (its last CTA); T against the
+    oracle, and the slice modes afterwards (the wave joined) against LAPACK."""
+    assert 0 < pw.eig_wave(48) < 332
+    inst = junction(ng=48, n_slices=330, n_e=5, n_k=1)
+    sel = [0, 2, 4]
+    E, k = inst.energies[sel], inst.kpar[sel]
+    ref = O.transmission(inst, points=sel)
+    with pw.Context.from_instance(inst, precision=precision) as ctx:
+        T = _dev(len(E), torch.float64)
+        ctx.transmission(E, k, T)
+        En = _dev((332, 48), torch.float64)
+        ctx.slice_modes(k[0], En)
+        torch.cuda.synchronize()
+        got, En = T.cpu().numpy(), En.cpu().numpy()
+    assert np.all(_rel(got, ref) < tol), (got, ref)
+    m = O.Model(inst)
+    for q in (0, 300, 331):
+        H = O.hamiltonian(m.mn, m.G, k[0], m.all_tables()[q], m.half)
+        assert np.abs(En[q] - np.linalg.eigvalsh(H)).max() < 1e-11
+
+
 def test_threshold_point_reports_and_continues(pw):
     inst = minimal_cell(energies=(2.0,), kpar=((0.0, 0.0),))
     b = 2 * math.pi / 5.0
