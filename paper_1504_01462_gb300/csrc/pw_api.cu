@@ -209,10 +209,13 @@ struct pw_ctx {
   // the mode stage's partial wave left running for pw_transmission (ensure_ksets
   // with defer): its stream, the event after its matrices, overlaps and FP32
   // copies, the first interface that needs them, and its matrices' range
-  cudaStream_t tail_stream = nullptr;
+  cudaStream_t tail_stream = nullptr, ovl_stream = nullptr;
   cudaEvent_t ev_main = nullptr, ev_tail = nullptr;
+  static constexpr int kOvlChunks = 8;
+  cudaEvent_t ev_ovl[kOvlChunks] = {};   // after the overlaps (and FP32 copies) of chunk c
   bool tail_pending = false;
-  int tail_iface = 0, tail_m0 = 0, tail_m1 = 0;
+  int tail_m0 = 0, tail_m1 = 0;
+  int ovl_chunk = 0, ovl_nchunks = 0;     // interfaces per chunk, chunks
 };
 
 namespace {
@@ -407,7 +410,7 @@ pw_status alloc_slots(pw_ctx *ctx) {
 pw_status join_tail(pw_ctx *ctx) {
   if (!ctx->tail_pending) return PW_OK;
   ctx->tail_pending = false;
-  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_tail, 0));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_ovl[ctx->ovl_nchunks - 1], 0));
   const int cnt = ctx->tail_m1 - ctx->tail_m0;
   std::vector<int> stat(cnt);
   CK(cudaMemcpyAsync(stat.data(), ctx->d_eigstat + ctx->tail_m0, cnt * sizeof(int), cudaMemcpyDeviceToHost,
@@ -427,11 +430,11 @@ pw_status join_tail(pw_ctx *ctx) {
 // are recomputed with one eigensolver launch over all their matrices.
 // defer (one slot, FP64 solver): when the solver's grid ends in a partial
 // wave, that wave takes the slot's last device slices (the electrodes stay in
-// the full waves), and it, the overlaps that need its slices and their FP32
-// copies are left running on the tail stream: on return ctx->tail_pending is
-// set, interfaces p < ctx->tail_iface are ready on the context's stream, and
-// the caller makes its stream wait for ctx->ev_tail before interface
-// ctx->tail_iface and then calls join_tail.
+// the full waves) and runs on the tail stream, and the overlaps (with their
+// FP32 copies) run on the overlap stream in chunks of consecutive interfaces,
+// the last ones after the partial wave: on return ctx->tail_pending is set,
+// and the caller makes its stream wait for ctx->ev_ovl[c] before interface
+// c ctx->ovl_chunk (c < ctx->ovl_nchunks), then calls join_tail.
 pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks, bool defer = false) {
   pw_status st = alloc_slots(ctx);
   if (st) return st;
@@ -471,14 +474,19 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks, bool 
     // the partial wave beside the sweep: matrices nA-1 .. nq-2 (device slices)
     // on the tail stream; the full waves take 0 .. nA-2 and the right
     // electrode nq-1 (the grid's last CTA)
-    if (!ctx->tail_stream &&
-        (cudaStreamCreateWithFlags(&ctx->tail_stream, cudaStreamNonBlocking) != cudaSuccess ||
-         cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&ctx->ev_tail, cudaEventDisableTiming) != cudaSuccess)) {
-      cudaGetLastError();
-      return latch(ctx, PW_ECUDA);
+    if (!ctx->tail_stream) {
+      bool ok = cudaStreamCreateWithFlags(&ctx->tail_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaStreamCreateWithFlags(&ctx->ovl_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_tail, cudaEventDisableTiming) == cudaSuccess;
+      for (int c = 0; ok && c < pw_ctx::kOvlChunks; ++c)
+        ok = cudaEventCreateWithFlags(&ctx->ev_ovl[c], cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        return latch(ctx, PW_ECUDA);
+      }
     }
-    cudaStream_t ts = ctx->tail_stream;
+    cudaStream_t ts = ctx->tail_stream, os = ctx->ovl_stream;
     zc *O0 = ctx->d_O + (size_t)s0 * (nq - 1) * nn;
     const int gT = nA - 2;   // pairs g < gT use the full waves' slices only
     CK(cudaEventRecord(ctx->ev_main, ctx->stream));   // the Hamiltonians are assembled
@@ -486,23 +494,31 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks, bool 
     pw::launch_eig(HU0, V0, En0, stat0, n, nA, ctx->stream, false, nullptr, 0, false, nq - 1);
     pw::launch_eig(HU0 + (size_t)(nA - 1) * nn, V0 + (size_t)(nA - 1) * nn, En0 + (size_t)(nA - 1) * n,
                    stat0 + (nA - 1), n, nmat - nA, ts, false, nullptr, 0, true);
+    CK(cudaEventRecord(ctx->ev_tail, ts));
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->ev_main, ctx->stream));   // the full waves' modes (and the right electrode's)
     st1.done();
-    Stage st2(ctx, 2, 1);
-    pw::launch_overlaps(HU0, O0, n, nq, 1, ctx->stream, false, 0, gT);
-    if (ctx->d_O32)
-      pw::launch_overlaps_fp32(O0, ctx->d_O32 + (size_t)s0 * (nq - 1) * nn, ctx->d_O32t + (size_t)s0 * (nq - 1) * nn,
-                               ctx->d_O32lo + (size_t)s0 * (nq - 1) * nn, n, gT, ctx->stream);
-    CK(cudaStreamWaitEvent(ts, ctx->ev_main, 0));
-    pw::launch_overlaps(HU0, O0, n, nq, 1, ts, false, gT, nq - 1);
-    if (ctx->d_O32)
-      pw::launch_overlaps_fp32(O0 + (size_t)gT * nn, ctx->d_O32 + ((size_t)s0 * (nq - 1) + gT) * nn,
-                               ctx->d_O32t + ((size_t)s0 * (nq - 1) + gT) * nn,
-                               ctx->d_O32lo + ((size_t)s0 * (nq - 1) + gT) * nn, n, nq - 1 - gT, ts);
-    CK(cudaEventRecord(ctx->ev_tail, ts));
+    // overlaps in chunks on the overlap stream, beside the sweep: interface p
+    // needs only O_p (and the modes of slices p, p+1)
+    const int npairs = nq - 1, nch = std::min(pw_ctx::kOvlChunks, npairs);
+    const int L = (npairs + nch - 1) / nch;
+    CK(cudaStreamWaitEvent(os, ctx->ev_main, 0));
+    bool waited_tail = false;
+    int c = 0;
+    for (int g0 = 0; g0 < npairs; g0 += L, ++c) {
+      const int g1 = std::min(npairs, g0 + L);
+      if (g1 > gT && !waited_tail) {   // pairs from gT on need the partial wave's slices
+        CK(cudaStreamWaitEvent(os, ctx->ev_tail, 0));
+        waited_tail = true;
+      }
+      pw::launch_overlaps(HU0, O0, n, nq, 1, os, false, g0, g1);
+      if (ctx->d_O32)
+        pw::launch_overlaps_fp32(O0 + (size_t)g0 * nn, ctx->d_O32 + ((size_t)s0 * (nq - 1) + g0) * nn,
+                                 ctx->d_O32t + ((size_t)s0 * (nq - 1) + g0) * nn,
+                                 ctx->d_O32lo + ((size_t)s0 * (nq - 1) + g0) * nn, n, g1 - g0, os);
+      CK(cudaEventRecord(ctx->ev_ovl[c], os));
+    }
     CK(cudaGetLastError());
-    st2.done();
     // the full waves' convergence and the electrodes' eigenvalues now; the
     // partial wave's convergence in join_tail
     std::vector<int> stat(nA);
@@ -515,13 +531,14 @@ pw_status ensure_ksets(pw_ctx *ctx, const std::vector<const double *> &ks, bool 
     ctx->last_sweeps = 0;
     for (int v : stat) {
       if (v < 0) {
-        CK(cudaStreamSynchronize(ts));
+        CK(cudaStreamSynchronize(os));
         return latch(ctx, PW_ENOTCONV);
       }
       ctx->last_sweeps = std::max(ctx->last_sweeps, v);
     }
     ctx->tail_pending = true;
-    ctx->tail_iface = gT;
+    ctx->ovl_chunk = L;
+    ctx->ovl_nchunks = c;
     ctx->tail_m0 = s0 * nq + nA - 1;
     ctx->tail_m1 = s0 * nq + nq - 1;
     ctx->slot_k[2 * s0] = ks[s0][0];
@@ -826,12 +843,16 @@ void pw_destroy(pw_ctx *ctx) {
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-  if (ctx->tail_stream) {
-    cudaStreamSynchronize(ctx->tail_stream);
-    cudaStreamDestroy(ctx->tail_stream);
+  for (cudaStream_t t : {ctx->tail_stream, ctx->ovl_stream}) {
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
   }
   if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
   if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
+  for (cudaEvent_t e : ctx->ev_ovl)
+    if (e) cudaEventDestroy(e);
   void *bufs[] = {ctx->d_mn, ctx->d_G, ctx->d_dz, ctx->d_z, ctx->d_tab, ctx->d_HU, ctx->d_V,
                   ctx->d_O, ctx->d_O32, ctx->d_O32t, ctx->d_O32lo, ctx->d_En, ctx->d_eigstat, ctx->R.p, ctx->M.p, ctx->piv.p,
                   ctx->pts.p, ctx->status.p, ctx->work.p, ctx->KV.p, ctx->Zst.p, ctx->Ust.p, ctx->Xa.p,
@@ -1318,8 +1339,8 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       ks.push_back(kpar + 2 * groups[gi][0]);
       for (int idx : groups[gi]) pts.emplace_back(idx, (int)(gi - g0));
     }
-    // one k_par: the eigensolver's partial wave runs beside the first
-    // interfaces of the sweep (the sweep waits for it at ctx->tail_iface)
+    // one k_par: the eigensolver's partial wave and the overlaps run beside
+    // the first interfaces of the sweep (which waits for each chunk of them)
     if ((st = ensure_ksets(ctx, ks, ks.size() == 1))) return st;
     // point descriptors and the padded incident-column count of the chunk
     std::vector<PointDesc> all(pts.size());
@@ -1450,9 +1471,12 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
       Stage s0(ctx, 0, (s2 ? 2 : 1) * (N + 1) * pw::sweep_batched_launches(n, ctx->precision, ctx->sweep_variant) +
                            f16_extra);
       for (int p = 0; p <= N; ++p) {
-        if (ctx->tail_pending && p == ctx->tail_iface) {   // the partial wave's slices from here on
-          CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_tail, 0));
-          if (s2) CK(cudaStreamWaitEvent(s2, ctx->ev_tail, 0));
+        if (ctx->tail_pending && p % ctx->ovl_chunk == 0 && p / ctx->ovl_chunk < ctx->ovl_nchunks) {
+          // the overlaps of interfaces p .. p + ovl_chunk - 1 (and the partial
+          // wave's modes they need) are ready after this chunk's event
+          const cudaEvent_t e = ctx->ev_ovl[p / ctx->ovl_chunk];
+          CK(cudaStreamWaitEvent(ctx->stream, e, 0));
+          if (s2) CK(cudaStreamWaitEvent(s2, e, 0));
         }
         cudaEvent_t w0 = nullptr, w1 = nullptr;
         if (ctx->profiling && p > 0) { w0 = take_event(ctx); w1 = take_event(ctx); }
