@@ -362,7 +362,9 @@ __global__ void __launch_bounds__(NT) k_refine_fwd_b(RefineArgs a, int p) {
 //   f_p = -(e_p a_p - (y1 + K_p^{-1} y2)/2),  g_p = -(b_p - (y1 - K_p^{-1} y2)/2).
 __global__ void __launch_bounds__(NT) k_refine_residual(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int p = blockIdx.x, pt = blockIdx.y;
+  // grid (points, interfaces): the CTAs that run together share one
+  // interface's overlap in L2
+  const int pt = blockIdx.x, p = blockIdx.y;
   const PointDesc d = a.pts[pt];
   if (d.skip || a.status[pt] || p > d.N) return;
   const int n = a.n, nc = a.nc, N = d.N, q = p + 1;
@@ -898,7 +900,7 @@ cudaError_t launch_refine(const RefineArgs &a, int npts, int min_iters, int max_
         PW_TIMED(KK_RES_FINISH, s, k_res_finish<<<npts, NT, kv_bytes, s>>>(a, p, ncol));
       }
     } else {
-      PW_TIMED(KK_REF_RESIDUAL, s, k_refine_residual<<<dim3(a.N + 1, npts), NT, smem, s>>>(a));
+      PW_TIMED(KK_REF_RESIDUAL, s, k_refine_residual<<<dim3(npts, a.N + 1), NT, smem, s>>>(a));
     }
     if ((e = cudaMemsetAsync(a.carry, 0, vec, s))) return e;
     forward();
