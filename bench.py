@@ -977,7 +977,10 @@ def main():
             "roofline_next": runner_up,
             "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows],
             "stages_ms": {"sweep": prof["sweep_ms"], "modes": prof["modes_ms"],
-                          "overlaps": prof["overlap_ms"], "refine": prof["refine_ms"]},
+                          "overlaps": prof["overlap_ms"], "refine": prof["refine_ms"],
+                          "note": "totals over the timed steps; with one k_par per call the eigensolver's "
+                                  "partial wave and the overlaps run on their own streams beside the sweep, "
+                                  "so their time is inside the sweep stage"},
             "fp64_gpu": fp64_arm,
             "speedup_vs_fp64": speedup,
             "measured_peaks_tflops": own or None,
