@@ -758,18 +758,16 @@ __global__ void __launch_bounds__(VT) kb_finish(SweepArgs a, int p) {
   const KVb<T> v = kv_of<T>(a, pt);
   const size_t nn = (size_t)n * n;
   const size_t e0 = nn * blk / nblk, e1 = nn * (blk + 1) / nblk;
-  if (a.Zst) {
-    cx<T> *Zs = reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)d.st_off + p) * nn;
-    for (size_t e = e0 + tid; e < e1; e += VT) Zs[e] = M[nn + e];
-  }
-  if (a.LUst) {
-    cx<T> *Ls = reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)d.st_off + p) * nn;
-    for (size_t e = e0 + tid; e < e1; e += VT) Ls[e] = M[e];
-  }
-  // R <- E+ Z_Y E+
+  // R <- E+ Z_Y E+, with the stores of Z_Y and of W's LU factors for the
+  // refinement in the same pass (Z_Y's element read once)
+  cx<T> *Zs = a.Zst ? reinterpret_cast<cx<T> *>(a.Zst) + ((size_t)d.st_off + p) * nn : nullptr;
+  cx<T> *Ls = a.LUst ? reinterpret_cast<cx<T> *>(a.LUst) + ((size_t)d.st_off + p) * nn : nullptr;
   for (size_t e = e0 + tid; e < e1; e += VT) {
     const int i = e % n, j = e / n;
-    R[e] = cmul(cmul(v.ep[i], M[i + (size_t)(n + j) * n]), v.ep[j]);
+    const cx<T> z = M[nn + e];   // Z_Y(i, j) = M(i, n + j)
+    if (Zs) Zs[e] = z;
+    if (Ls) Ls[e] = M[e];
+    R[e] = cmul(cmul(v.ep[i], z), v.ep[j]);
   }
   if (blk != 0) return;
   if (a.Zst) {

@@ -38,3 +38,40 @@ def test_refine_launch_count():
     assert (bench.refine_launches(N, 2, True, sliced=True)
             == bench.refine_launches(N, 2, True, sliced=False) + 2 * (4 * (N + 1) - 1))
     assert bench.refine_launches(N, 0) == 0
+
+
+def test_kernel_table_keeps_side_stream_launches_out_of_the_shares():
+    """The per-kernel table: average launch time x launches per step, shares
+    of the summed time; a launch on the side stream (the eigensolver's partial
+    wave, whose events include its wait for free SMs) is listed last, without
+    a share."""
+    import bench
+    kprof = {"kb_trail (x)": (30.0, 3, 6), "k_heev (x)": (1000.0, 1, 1),
+             "k_heev_tail (x)": (1500.0, 1, 1), "kb_panel": (1.0, 2, 4)}
+    rows = bench.kernel_table(kprof, steps=2)
+    names = [r["kernel"] for r in rows]
+    assert names[0] == "k_heev (x)" and names[-1] == "k_heev_tail (x)"
+    assert rows[-1]["share"] is None
+    tot = 500.0 + 30.0 + 1.0            # per step: 1000 x 1 / 2, 10 x 6 / 2, 0.5 x 4 / 2
+    assert abs(rows[0]["share"] - 500.0 / tot) < 1e-12
+    assert abs(sum(r["share"] for r in rows[:-1]) - 1.0) < 1e-12
+
+
+def test_algorithmic_counts():
+    """The roofline's algorithmic counts: the eigensolver's (16/3 + 6 x 0.97 +
+    8) n^3 flops per matrix, an overlap's n^3 complex multiply-adds, and the
+    sweep's per-kind totals add up to the per-point formula (the trailing
+    update's n^3/3 and the back substitution's n^2 (n + n_c)/2 multiply-adds
+    among them)."""
+    import bench
+    n = 512
+    assert abs(bench.heev_flops_per_matrix(n) - (16 / 3 + 5.82 + 8) * n ** 3) < 1e-6 * n ** 3
+    assert bench.overlap_flops_per_pair(n) == 8.0 * n ** 3
+    nc, npts, N = 8, 4, 3
+    tot = bench.sweep_kind_totals(n, nc, npts, N, False, 8)
+    flops = sum(f for (f, _) in tot.values())
+    # [W|Y] on N interfaces; LU (panel, panel apply, trailing) and back
+    # substitution on N + 1, 8 flop per complex multiply-add
+    lu_tri = (n ** 3 / 3.0 + n * n * (n + nc) / 2.0) * 8.0 * (N + 1) * npts
+    assert flops > 8.0 * 2 * n ** 3 * N * npts + 0.9 * lu_tri
+    assert tot["kb_trail"][1] > 0 and tot["kb_bsupd"][1] > 0
