@@ -549,6 +549,73 @@ __device__ void lu_bs_diag(cx<T> *M, int ld, int n, int j0, int c_first, int c_l
   __syncthreads();
 }
 
+// lu_bs_diag for the FP32 sweep with its right-hand-side columns staged in
+// shared memory: the columns [c_first, c_last) of rows j0 .. j0+nb-1 are read
+// and written back row-contiguous (coalesced), each thread solves one column
+// from the padded staging copy, and the inverse of the diagonal block is
+// formed with the diagonal's reciprocals taken once.  smem: 2 NB^2 + NB +
+// (c_last - c_first) (NB + 1) complex.
+template <int NTH>
+__device__ void lu_bs_diag_staged(cc *M, int ld, int n, int j0, int c_first, int c_last, cc *smem) {
+  constexpr int NT = NTH, NB = Tile<float, NTH>::NB, LDB = NB + 1;
+  static_assert(NB == 32, "one lane per row of a diagonal block");
+  cc *Ls = smem, *Ui = Ls + NB * NB, *dinv = Ui + NB * NB, *Bs = dinv + NB;
+  const int tid = threadIdx.x, nb = min(NB, n - j0), ncol = c_last - c_first;
+  for (int e = tid; e < nb * nb; e += NT) {
+    const int r = e % nb, s2 = e / nb;
+    Ls[r + s2 * NB] = M[j0 + r + (size_t)(j0 + s2) * ld];
+  }
+  if (tid < nb) dinv[tid] = cinv(M[j0 + tid + (size_t)(j0 + tid) * ld]);
+  for (int e = tid; e < nb * ncol; e += NT) {
+    const int r = e % nb, c = e / nb;
+    Bs[r + c * LDB] = M[j0 + r + (size_t)(c_first + c) * ld];
+  }
+  __syncthreads();
+  // U11^{-1}, column j by back substitution on e_j (one warp per column, lane
+  // r holding row r, solved values passed by shuffles)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int j = warp; j < nb; j += NT / 32) {
+    cc x = mkc<float>(lane == j ? 1.f : 0.f, 0.f);
+    for (int s2 = j; s2 >= 0; --s2) {
+      if (lane == s2) x = cmul(x, dinv[s2]);
+      const cc xs = mkc<float>(__shfl_sync(0xffffffffu, x.re, s2), __shfl_sync(0xffffffffu, x.im, s2));
+      if (lane < s2) {
+        const cc u = Ls[lane + s2 * NB];
+        x.re -= u.re * xs.re - u.im * xs.im;
+        x.im -= u.re * xs.im + u.im * xs.re;
+      }
+    }
+    if (lane < nb) Ui[lane + j * NB] = lane <= j ? x : czero<float>();
+  }
+  __syncthreads();
+  for (int c = tid; c < ncol; c += NT) {
+    cc *col = Bs + c * LDB;
+    cc x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = czero<float>();
+#pragma unroll
+    for (int s2 = 0; s2 < NB; ++s2) {
+      if (s2 < nb) {
+        const cc b = col[s2];
+#pragma unroll
+        for (int r = 0; r <= s2; ++r) cfma(x[r], Ui[r + s2 * NB], b);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r < nb) col[r] = x[r];
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * ncol; e += NT) {
+    const int r = e % nb, c = e / nb;
+    M[j0 + r + (size_t)(c_first + c) * ld] = Bs[r + c * LDB];
+  }
+}
+
+inline size_t lu_bs_diag_staged_smem(int ncol) {
+  return ((size_t)2 * 32 * 32 + 32 + (size_t)ncol * 33) * sizeof(cc);
+}
+
 // Back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b.
 template <typename T, int NTH = NT>
 __device__ void lu_bs_update(cx<T> *M, int ld, int n, int ncols, int j0, cx<T> *gsm, int t_first = 0,

@@ -722,7 +722,11 @@ __global__ void __launch_bounds__(BT) kb_bsdiag(SweepArgs a, int j0) {
   cx<T> *M = reinterpret_cast<cx<T> *>(a.M) + (size_t)pt * n * ncols;
   const int per = (ncols - n + gridDim.x - 1) / gridDim.x;
   const int c0 = n + blockIdx.x * per, c1 = min(ncols, c0 + per);
-  lu_bs_diag<T, BT>(M, n, n, j0, c0, c1, reinterpret_cast<cx<T> *>(smraw));
+  if constexpr (std::is_same<T, float>::value) {
+    if (c0 < c1) lu_bs_diag_staged<BT>(M, n, n, j0, c0, c1, reinterpret_cast<cc *>(smraw));
+  } else {
+    lu_bs_diag<T, BT>(M, n, n, j0, c0, c1, reinterpret_cast<cx<T> *>(smraw));
+  }
 }
 
 template <typename T, int BT>
@@ -912,6 +916,10 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     }
   }
   const int rhs_blocks = max(1, (ncols - n + BT - 1) / BT);
+  // FP32: the diagonal solves stage their right-hand-side columns in shared memory
+  const size_t bsm = std::is_same<T, float>::value
+                         ? lu_bs_diag_staged_smem((ncols - n + rhs_blocks - 1) / rhs_blocks)
+                         : dsm;
   if (lapack) {
     // 128-row blocks: four diagonal solves and three K = 128 updates at N_G = 512
     const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
@@ -924,7 +932,7 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
     }
   } else {
     for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
-      PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, dsm, s>>>(a, j0));
+      PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, bsm, s>>>(a, j0));
       if (j0 > 0) {
         if (std::is_same<T, float>::value && tensor_core)
           PW_TIMED(KK_BSUPD, s,
@@ -955,6 +963,12 @@ static cudaError_t sweep_prepare(int n) {
     const cudaError_t ep =
         cudaFuncSetAttribute(kb_panel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm_big);
     if (ep != cudaSuccess) return ep;
+  }
+  if (std::is_same<T, float>::value) {
+    // the staged diagonal solves: at most BT columns a CTA
+    const cudaError_t eb = cudaFuncSetAttribute(kb_bsdiag<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)lu_bs_diag_staged_smem(BT));
+    if (eb != cudaSuccess) return eb;
   }
   cudaError_t e = cudaFuncSetAttribute(kb_wy<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
   if (e == cudaSuccess)
