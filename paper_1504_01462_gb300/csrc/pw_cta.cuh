@@ -616,6 +616,7 @@ inline size_t lu_bs_diag_staged_smem(int ncol) {
   return ((size_t)2 * 32 * 32 + 32 + (size_t)ncol * 33) * sizeof(cc);
 }
 
+
 // Back-substitution update above block j0: M[0:j0, n:ncols] -= U[0:j0, b] X_b.
 template <typename T, int NTH = NT>
 __device__ void lu_bs_update(cx<T> *M, int ld, int n, int ncols, int j0, cx<T> *gsm, int t_first = 0,

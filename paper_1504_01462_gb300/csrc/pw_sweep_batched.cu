@@ -432,21 +432,23 @@ __global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_trail_tc(SweepArgs a, in
 }
 
 // back-substitution update above block j0 (kb rows): M[0:j0, n:ncols] -= U[0:j0, b] X_b
-__global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_bsupd_tc(SweepArgs a, int j0, int kb) {
+// (rows lo .. j0-1 only when lo > 0)
+__global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_bsupd_tc(SweepArgs a, int j0, int kb, int lo = 0) {
   extern __shared__ __align__(128) unsigned char smtc[];
   unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
-  if (inactive(a, pt) || j0 <= 0) return;
+  if (inactive(a, pt) || j0 <= lo) return;
   const int n = a.n, ncols = 2 * n + a.nc;
   const int nb = min(kb, n - j0);
-  const int m = j0, ncol = ncols - n;
+  const int m = j0 - lo, ncol = ncols - n;
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
   if (q0 >= ncol) return;
-  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols + lo;   // row lo as row 0
+  const cc *X = M - lo;
   const bool ok = tc::cgemm_tile<true, true, RMW_TN>(
       m, ncol, nb, r0, q0, [=](int i, int l) { return M[i + (size_t)(j0 + l) * n]; },
-      [=](int l, int j) { return M[j0 + l + (size_t)(n + j) * n]; },
+      [=](int l, int j) { return X[j0 + l + (size_t)(n + j) * n]; },
       [=](int i, int j) { return M[i + (size_t)(n + j) * n]; },
       [=](int i, int j, cc acc, cc old) { M[i + (size_t)(n + j) * n] = csub(old, acc); }, smraw);
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
@@ -930,6 +932,24 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
                  kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
                                tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, BS_FB));
     }
+  } else if (std::is_same<T, float>::value && tensor_core) {
+    // blocks in pairs from the bottom: block b, the 32 rows of block b-1
+    // updated from it, block b-1, then one update of the rows above both with
+    // K = 32 + (rows of b) instead of two with K = 32 over all of them
+    for (int jb = ((n - 1) / NB) * NB; jb >= 0; jb -= 2 * NB) {
+      PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, bsm, s>>>(a, jb));
+      if (jb == 0) break;
+      const int j0 = jb - NB;
+      // block b-1's rows take block b's contribution (32 rows, K = rows of b)
+      PW_TIMED(KK_BSUPD, s,
+               kb_bsupd_tc<<<dim3(tiles(NB, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                             tc::cg_smem_bytes<RMW_TN>(), s>>>(a, jb, NB, j0));
+      PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, bsm, s>>>(a, j0));
+      if (j0 > 0)
+        PW_TIMED(KK_BSUPD, s,
+                 kb_bsupd_tc<<<dim3(tiles(j0, ncols - n, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
+                               tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, 2 * NB));
+    }
   } else {
     for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
       PW_TIMED(KK_BSDIAG, s, kb_bsdiag<T, BT><<<dim3(rhs_blocks, npts), BT, bsm, s>>>(a, j0));
@@ -966,8 +986,8 @@ static cudaError_t sweep_prepare(int n) {
   }
   if (std::is_same<T, float>::value) {
     // the staged diagonal solves: at most BT columns a CTA
-    const cudaError_t eb = cudaFuncSetAttribute(kb_bsdiag<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)lu_bs_diag_staged_smem(BT));
+    cudaError_t eb = cudaFuncSetAttribute(kb_bsdiag<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)lu_bs_diag_staged_smem(BT));
     if (eb != cudaSuccess) return eb;
   }
   cudaError_t e = cudaFuncSetAttribute(kb_wy<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
@@ -1031,10 +1051,14 @@ int sweep_batched_launches(int n, int precision, int variant) {
   // a diagonal solve per block and an update above every block but the first
   // (32-row blocks, or 128-row blocks in the tensor-core form)
   const int bblocks = tensor ? (n + BS_FB - 1) / BS_FB : panels;
+  // the tensor-core form without LAPACK pivots pairs the 32-row blocks: a
+  // 32-row update inside every pair and one update above every pair but the
+  // lowest-placed
+  const int bsupd = (fp32 && (variant & 2) && !tensor) ? panels / 2 + (panels + 1) / 2 - 1 : bblocks - 1;
   // the tensor-core form adds the right-hand sides' elimination: a
   // permutation, a diagonal solve per 128-row block and an update below every
   // block but the last
-  return 3 + 2 * panels - 1 + (fp32 ? panels : 0) + 2 * bblocks - 1 + (tensor ? 2 * bblocks : 0);
+  return 3 + 2 * panels - 1 + (fp32 ? panels : 0) + bblocks + bsupd + (tensor ? 2 * bblocks : 0);
 }
 
 }  // namespace pw
