@@ -173,14 +173,17 @@ def sweep_flops_per_point(n, nopen_left):
     return 8.0 * (2.0 * n ** 3 + n ** 3 / 3.0 + n * n * (n + nopen_left))
 
 
-def sweep_kind_totals(n, nc, npts, N, big, esz):
+def sweep_kind_totals(n, nc, npts, N, big, esz, paired=False):
     """Algorithmic work of one step's sweep per kernel kind (all N+1
     interfaces, npts points): {kind: (flops, bytes)}.  CMA = 8 flop.  Bytes are
     what each launch must move at least: the matrix region it updates read and
     written once, its operands read once.  `big` (sweep variant bit 3):
     LAPACK-ordered pivots, the LU updates W's columns only, the right-hand
     sides n + nc eliminated in 128-row blocks after the LU; else 32-row
-    blocks, the LU's trailing updates carry all 2n + nc columns."""
+    blocks, the LU's trailing updates carry all 2n + nc columns.  `paired`
+    (the tensor-core form without bit 3): the back substitution's 32-row
+    blocks in pairs from the bottom, a 32-row update inside each pair and one
+    update of the rows above it with K = 64."""
     NB, FB = 32, 128
     ncols, nrhs = 2 * n + nc, n + nc
     ucols = n if big else ncols
@@ -195,12 +198,25 @@ def sweep_kind_totals(n, nc, npts, N, big, esz):
             tr_b += esz * (2.0 * (n - c0) * (ucols - c0) + (n - c0) * nb + nb * (ucols - c0))
     bs = FB if big else NB
     up_f = up_b = dg_f = fs_f = fs_b = fd_f = 0.0
+
+    def update(rows, k):   # rows x nrhs -= (rows x k) (k x nrhs)
+        nonlocal up_f, up_b
+        up_f += rows * nrhs * k
+        up_b += esz * (2.0 * rows * nrhs + rows * k + k * nrhs)
     for j0 in range(0, n, bs):
         fb = min(bs, n - j0)
         dg_f += fb * fb / 2.0 * nrhs
-        if j0 > 0:
-            up_f += j0 * nrhs * fb
-            up_b += esz * (2.0 * j0 * nrhs + j0 * fb + fb * nrhs)
+        if j0 > 0 and not paired:
+            update(j0, fb)
+    if paired:
+        jb = ((n - 1) // NB) * NB
+        while jb > 0:
+            j0 = jb - NB
+            kb = min(NB, n - jb)
+            update(NB, kb)              # block b-1 from block b
+            if j0 > 0:
+                update(j0, NB + kb)     # the rows above the pair
+            jb = j0 - NB
         if big:
             fd_f += fb * fb / 2.0 * nrhs
             c1 = j0 + fb
@@ -905,7 +921,8 @@ def main():
         esz = 8 if prec == pw.MIXED_FP32 else 16
         nc = max(4, ((int(nopen_last[:, 0].max()) + 3) // 4) * 4) if len(nopen_last) else 4
         rows = kernel_table(kprof, args.steps)
-        model = sweep_kind_totals(n, nc, n_e, N, tensor and (variant & 8) != 0, esz)
+        model = sweep_kind_totals(n, nc, n_e, N, tensor and (variant & 8) != 0, esz,
+                                  paired=tensor and not (variant & 8))
         # the mode stage of one k_par: N + 2 slice Hamiltonians, the FP64
         # solver's main launch taking the full waves (the rest on the side
         # stream), and N + 1 overlaps
