@@ -181,21 +181,40 @@ def sweep_kind_totals(n, nc, npts, N, big, esz, paired=False):
     LAPACK-ordered pivots, the LU updates W's columns only, the right-hand
     sides n + nc eliminated in 128-row blocks after the LU; else 32-row
     blocks, the LU's trailing updates carry all 2n + nc columns.  `paired`
-    (the tensor-core form without bit 3): the back substitution's 32-row
-    blocks in pairs from the bottom, a 32-row update inside each pair and one
-    update of the rows above it with K = 64."""
+    (the tensor-core form without bit 3): the LU's 32-column panels in pairs,
+    the first panel's update reaching only the second panel's columns and its
+    32 rows (in the second panel's apply), the rest with K = 64; and the back
+    substitution's 32-row blocks in pairs from the bottom, a 32-row update
+    inside each pair and one update of the rows above it with K = 64."""
     NB, FB = 32, 128
     ncols, nrhs = 2 * n + nc, n + nc
     ucols = n if big else ncols
     tr_f = tr_b = pa_f = pn_f = 0.0
-    for j0 in range(0, n, NB):
+
+    def trail(r0, c0, k, cend):   # M[r0:n, c0:cend] -= (rows x k) (k x cols)
+        nonlocal tr_f, tr_b
+        rows, cols = n - r0, cend - c0
+        tr_f += rows * cols * k
+        tr_b += esz * (2.0 * rows * cols + rows * k + k * cols)
+    j0 = 0
+    while j0 < n:
         nb = min(NB, n - j0)
         c0 = j0 + nb
         pn_f += (n - j0) * nb * nb / 2.0
         pa_f += nb * nb / 2.0 * (ucols - c0)
+        if paired and c0 < n:
+            j1, nb2 = c0, min(NB, n - c0)
+            c1 = j1 + nb2
+            trail(j1, j1, nb, c1)                                 # the second panel's columns
+            pn_f += (n - j1) * nb2 * nb2 / 2.0
+            pa_f += (nb2 * nb + nb2 * nb2 / 2.0) * (ucols - c1)   # its 32 rows, then the solve
+            if c1 < n:
+                trail(c1, c1, nb + nb2, ucols)
+            j0 = c1
+            continue
         if c0 < n:
-            tr_f += (n - c0) * (ucols - c0) * nb
-            tr_b += esz * (2.0 * (n - c0) * (ucols - c0) + (n - c0) * nb + nb * (ucols - c0))
+            trail(c0, c0, nb, ucols)
+        j0 = c0
     bs = FB if big else NB
     up_f = up_b = dg_f = fs_f = fs_b = fd_f = 0.0
 
@@ -208,6 +227,12 @@ def sweep_kind_totals(n, nc, npts, N, big, esz, paired=False):
         dg_f += fb * fb / 2.0 * nrhs
         if j0 > 0 and not paired:
             update(j0, fb)
+        if big:
+            fd_f += fb * fb / 2.0 * nrhs
+            c1 = j0 + fb
+            if c1 < n:
+                fs_f += (n - c1) * nrhs * fb
+                fs_b += esz * (2.0 * (n - c1) * nrhs + (n - c1) * fb + fb * nrhs)
     if paired:
         jb = ((n - 1) // NB) * NB
         while jb > 0:
@@ -217,12 +242,6 @@ def sweep_kind_totals(n, nc, npts, N, big, esz, paired=False):
             if j0 > 0:
                 update(j0, NB + kb)     # the rows above the pair
             jb = j0 - NB
-        if big:
-            fd_f += fb * fb / 2.0 * nrhs
-            c1 = j0 + fb
-            if c1 < n:
-                fs_f += (n - c1) * nrhs * fb
-                fs_b += esz * (2.0 * (n - c1) * nrhs + (n - c1) * fb + fb * nrhs)
     I = (N + 1) * npts
     out = {
         "kb_wy": (8.0 * 2 * n ** 3 * N * npts, esz * (n * n + 2.0 * n * n) * N * npts),

@@ -1523,7 +1523,7 @@ pw_status pw_transmission(pw_ctx *ctx, int npts, const double *E, const double *
         r.nc = nc;
         r.x_slots = (long long)nb * (N + 2);
         r.st_slots = (long long)nb * (N + 1);
-        r.lapack_piv = (ctx->sweep_variant & 10) == 10 ? 1 : 0;   // the stored factors' pivot order
+        r.piv_order = pw::stored_piv_order(ctx->sweep_variant);   // the stored factors' pivot order
         if (pw::points_share_overlaps(pd.data(), nb) && ctx->d_O32) {
           // one buffer: the backward product's operands and result, then (when the
           // residual runs on the tensor cores) O y, the slices and their exponents

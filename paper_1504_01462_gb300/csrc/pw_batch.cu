@@ -368,7 +368,7 @@ pw_status run_chunk(pw_batch *b, const std::vector<int> &ids, int n, const doubl
     r.nc = nc;
     r.x_slots = nmat;
     r.st_slots = nov;
-    r.lapack_piv = (var & 10) == 10 ? 1 : 0;   // the stored factors' pivot order
+    r.piv_order = pw::stored_piv_order(var);   // the stored factors' pivot order
     int passes = 0;
     BCK(pw::launch_refine(r, m, std::min(2, b->refine_iters), b->refine_iters, pw::kRefineTolRel, s, &passes));
   }

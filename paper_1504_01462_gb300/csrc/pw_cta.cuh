@@ -219,9 +219,15 @@ __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
 // factorisation).
 // FP64 keeps the sequential swaps and an in-place solve: a register column of
 // NB FP64 complex values would not fit beside the rest of the kernel.
+// L1s (FP32 only, optional): the second panel of a pair.  The columns have
+// not yet taken the first panel's update, so the swapped rows take
+// x -= L1s U1 before the solve, with L1s the first panel's L rows j0 .. j0+nb-1
+// (NB x NB in shared memory, already in this panel's row order) and U1 the
+// column's NB rows from row ju (the first panel's U12).
 template <typename T, int NTH = NT>
 __device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int j0, int nb, int R,
-                                  const int *piv, const cx<T> *Ls, int *flag, bool solve = true) {
+                                  const int *piv, const cx<T> *Ls, int *flag, bool solve = true,
+                                  const cx<T> *L1s = nullptr, int ju = 0) {
   constexpr int NB = Tile<T, NTH>::NB;
   const int tid = threadIdx.x;
   if constexpr (sizeof(T) != 4) {
@@ -298,6 +304,18 @@ __device__ void panel_right_apply(cx<T> *M, int ld, int c_begin, int c_end, int 
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           if (k0 + k < nd) col[s_dpos[k0 + k]] = y[k];
+      }
+      if (L1s) {
+        const cx<T> *u1 = M + (size_t)c * ld + ju;
+        for (int k = 0; k < NB; ++k) {
+          const cx<T> uk = u1[k];
+#pragma unroll
+          for (int r = 0; r < NB; ++r) {
+            const cx<T> l = L1s[r + k * NB];
+            x[r].re -= l.re * uk.re - l.im * uk.im;
+            x[r].im -= l.re * uk.im + l.im * uk.re;
+          }
+        }
       }
       if (solve) {
 #pragma unroll
@@ -663,12 +681,20 @@ __device__ void cta_lu_solve(cx<T> *M, int ld, int n, int ncols, int *piv, cx<T>
 // (as in panel_right_apply) and each right-hand side is solved by one warp,
 // lane r holding row r (the diagonal block from shared memory, the solved
 // values passed by shuffles), so no step waits on a global-memory round trip.
-// lapack: the factors satisfy P A = L U (every panel's swaps reached the L
-// columns left of it, as the tensor-core FP32 sweep stores them): B <- P B
-// first, then the blocks without swaps.  Needs n <= 1024.
+// order says how the factors were stored:
+//   0  each panel's swaps reached only the columns right of it;
+//   1  (lapack) P A = L U: every panel's swaps reached the L columns left of
+//      it (the tensor-core FP32 sweep with 128-row blocks): B <- P B first,
+//      then the blocks without swaps;
+//   2  panels in pairs (the tensor-core FP32 sweep's default): the second
+//      panel of a pair also swapped the first panel's L rows below it, so the
+//      replay applies the second block's swaps before the first block's
+//      update of the rows below, and none at the second block.
+// Needs n <= 1024.
 template <typename T, int NTH = NT>
 __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, int ldb, int nrhs,
-                              cx<T> *smem, bool lapack = false) {
+                              cx<T> *smem, int order = 0) {
+  const bool lapack = order == 1;
   constexpr int NB = Tile<T, NTH>::NB;
   static_assert(NB == 32, "one lane per row of a diagonal block");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -699,6 +725,36 @@ __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, 
     }
     __syncthreads();
   }
+  // the swaps of rows jb .. jb+nbb-1 (piv relative to jb, R rows from jb) as
+  // a gather: s_src, and s_nd displaced rows s_dpos <- s_dsrc (tid 0)
+  auto fold = [&](int nbb, int R) {
+    int nd = 0;
+    for (int r = 0; r < nbb; ++r) s_src[r] = r;
+    for (int r = 0; r < nbb; ++r) {
+      const int p = s_piv[r];
+      if (p <= r || p >= R) continue;   // p < r or out of range cannot come from the factorisation
+      if (p < nbb) {
+        const int t = s_src[r];
+        s_src[r] = s_src[p];
+        s_src[p] = t;
+        continue;
+      }
+      int k = 0;
+      while (k < nd && s_dpos[k] != p) ++k;
+      if (k == nd) {
+        s_dpos[nd] = p;
+        s_dsrc[nd] = p;
+        ++nd;
+      }
+      const int t = s_src[r];
+      s_src[r] = s_dsrc[k];
+      s_dsrc[k] = t;
+    }
+    for (int k = 0; k < nd; ++k)
+      if (s_dsrc[k] >= nbb) nd = 0;   // cannot happen (the fold keeps displaced sources in the block)
+    s_nd = nd;
+  };
+  bool ahead = false;   // order 2: this block's swaps were applied with the block before
   for (int j0 = 0; j0 < n; j0 += NB) {
     const int nb = min(NB, n - j0), R = n - j0;
     for (int e = tid; e < nb * nb; e += NTH) {
@@ -706,35 +762,9 @@ __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, 
       Ls[r + c * NB] = LU[j0 + r + (size_t)(j0 + c) * n];
     }
     // lapack: B is already in pivot order, so the block's swaps are identities
-    if (tid < nb) s_piv[tid] = lapack ? tid : piv[j0 + tid] - j0;
+    if (tid < nb) s_piv[tid] = (lapack || ahead) ? tid : piv[j0 + tid] - j0;
     __syncthreads();
-    if (tid == 0) {
-      int nd = 0;
-      for (int r = 0; r < nb; ++r) s_src[r] = r;
-      for (int r = 0; r < nb; ++r) {
-        const int p = s_piv[r];
-        if (p <= r || p >= R) continue;   // p < r or out of range cannot come from the factorisation
-        if (p < nb) {
-          const int t = s_src[r];
-          s_src[r] = s_src[p];
-          s_src[p] = t;
-          continue;
-        }
-        int k = 0;
-        while (k < nd && s_dpos[k] != p) ++k;
-        if (k == nd) {
-          s_dpos[nd] = p;
-          s_dsrc[nd] = p;
-          ++nd;
-        }
-        const int t = s_src[r];
-        s_src[r] = s_dsrc[k];
-        s_dsrc[k] = t;
-      }
-      for (int k = 0; k < nd; ++k)
-        if (s_dsrc[k] >= nb) nd = 0;   // cannot happen (the fold keeps displaced sources in the block)
-      s_nd = nd;
-    }
+    if (tid == 0) fold(nb, R);
     __syncthreads();
     const int nd = s_nd;
     for (int c = warp; c < nrhs; c += NTH / 32) {
@@ -755,6 +785,26 @@ __device__ void cta_lu_replay(const cx<T> *LU, int n, const int *piv, cx<T> *B, 
       if (lane < nb) col[lane] = x;
     }
     __syncthreads();
+    // order 2, first block of a pair: the rows below take the second block's
+    // swaps now, matching the first block's L rows (which took them too)
+    ahead = order == 2 && !ahead && (j0 / NB) % 2 == 0 && j0 + NB < n;
+    if (ahead) {
+      const int j1 = j0 + NB, nb1 = min(NB, n - j1);
+      if (tid < nb1) s_piv[tid] = piv[j1 + tid] - j1;
+      __syncthreads();
+      if (tid == 0) fold(nb1, n - j1);
+      __syncthreads();
+      const int nd1 = s_nd;
+      for (int c = warp; c < nrhs; c += NTH / 32) {
+        cx<T> *col = B + (size_t)c * ldb + j1;
+        const cx<T> x = lane < nb1 ? col[s_src[lane]] : czero<T>();
+        const cx<T> y = lane < nd1 ? col[s_dsrc[lane]] : czero<T>();
+        __syncwarp();
+        if (lane < nd1) col[s_dpos[lane]] = y;
+        if (lane < nb1) col[lane] = x;
+      }
+      __syncthreads();
+    }
     if (j0 + nb < n) {
       const int c0 = j0 + nb;
       cta_gemm_skinny<T, NTH>(

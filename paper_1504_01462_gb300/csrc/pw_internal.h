@@ -117,6 +117,11 @@ inline int points_pair_up(const PointDesc *pd, int npts) {
   return 1;
 }
 
+// How the FP32 sweep of a variant stores the row swaps of its LU factors
+// (piv_order of RefineArgs): the tensor-core form (bit 1) factors panels in
+// pairs, or with LAPACK-ordered pivots when bit 3 is set too.
+inline int stored_piv_order(int variant) { return (variant & 10) == 10 ? 1 : (variant & 2) ? 2 : 0; }
+
 // Buffers of the FP64 refinement around the FP32 sweep (pw_refine.cu).
 struct RefineArgs {
   const PointDesc *pts;
@@ -145,9 +150,11 @@ struct RefineArgs {
   int n, N, nc;          // N: the most slices of any point
   long long x_slots;     // sum over points of N+2 (the Xa, Xb slots)
   long long st_slots;    // sum over points of N+1 (the Fr, Gr slots)
-  int lapack_piv;        // 1: the stored LU factors follow P W = L U (the sweep's
-                         //    tensor-core FP32 form); 0: each panel's swaps reach only
-                         //    the columns right of it (replayed panel by panel)
+  int piv_order;         // how the stored LU factors hold their row swaps (the order
+                         //    argument of cta_lu_replay): 0 each panel's swaps reach only
+                         //    the columns right of it; 1 P W = L U (the tensor-core FP32
+                         //    form with 128-row blocks); 2 panels in pairs (the
+                         //    tensor-core FP32 form's default); see stored_piv_order
   uint16_t *Osl, *Ysl;   // null, or the residual's exact slices (BF16 bit patterns, K-contiguous):
                          //   RS_SLICES x 2n x 2n and RS_SLICES x (2 nc npts) x 2n, when every
                          //   point shares its overlaps (the residual products run on the tensor cores)

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(NT) k_refine_fwd_b(RefineArgs a, int p) {
     for (int e = threadIdx.x; e < n * nc; e += NT) rhs[e] = ccast<float>(csub(carry[e], F[e]));
     __syncthreads();
   }
-  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm, a.lapack_piv != 0);
+  cta_lu_replay<float>(LU, n, piv, rhs, n, nc, gsm, a.piv_order);
   for (int e = threadIdx.x; e < n * nc; e += NT) {
     const int i = e % n;
     const cc u = rhs[e];

@@ -35,6 +35,9 @@ __host__ __device__ constexpr size_t panel_head_bytes() {
 }
 
 int g_smem_optin = 0;   // opt-in shared memory per block of the device (set by prepare)
+// kb_panel's static shared memory (the row-swap fold of the pair's L swap)
+// comes out of the same per-block limit as its staged panel
+constexpr size_t PANEL_STATIC_RESERVE = 1024;
 constexpr int FINISH_BLOCKS = 8;   // blocks per point of kb_finish
 
 template <typename T>
@@ -410,15 +413,16 @@ __global__ void __launch_bounds__(tc::CG_THREADS, 1) kb_wy2_tc16(SweepArgs a, in
 // columns keep the prefetched C values of a thread in 32 registers.
 constexpr int RMW_TN = 64;
 
-// trailing update of panel j0: M[c0:n, c0:ncols] -= L21 U12 (c0 = j0 + nb)
-__global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_trail_tc(SweepArgs a, int j0) {
+// trailing update of the kb columns from j0: M[c0:n, c0:ncols] -= L21 U12
+// (c0 = j0 + kb; kb = 64 for a pair of panels), or of columns c0 .. c0+cmax-1 only
+__global__ void __launch_bounds__(tc::CG_THREADS, 3) kb_trail_tc(SweepArgs a, int j0, int kb, int cmax) {
   extern __shared__ __align__(128) unsigned char smtc[];
   unsigned char *smraw = smtc;
   const int pt = blockIdx.y;
   if (inactive(a, pt)) return;
   const int n = a.n, ncols = 2 * n + a.nc;
-  const int nb = min(Tile<float, 256>::NB, n - j0), c0 = j0 + nb;
-  const int m = n - c0, ncol = (a.lapack_piv ? n : ncols) - c0;   // lapack_piv: W's columns only
+  const int nb = min(kb, n - j0), c0 = j0 + nb;
+  const int m = n - c0, ncol = min(cmax, (a.lapack_piv ? n : ncols) - c0);   // lapack_piv: W's columns only
   const int tiles_m = (m + tc::CG_M / 2 - 1) / (tc::CG_M / 2);
   const int r0 = (blockIdx.x % tiles_m) * (tc::CG_M / 2), q0 = (blockIdx.x / tiles_m) * RMW_TN;
   if (q0 >= ncol) return;
@@ -639,8 +643,12 @@ __global__ void __launch_bounds__(tc::CG_THREADS) kb_fsupd_tc(SweepArgs a, int j
   if (!ok && threadIdx.x == 0) a.status[pt] = 2;
 }
 
+// left0 >= 0 (FP32, the second panel of a pair): after the factorisation the
+// panel's row swaps also reach the first panel's L columns left0 .. j0-1
+// (rows j0 and below), so that they match the rows the pair's K = 64
+// trailing update reaches
 template <typename T, int BT>
-__global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
+__global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0, int left0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int pt = blockIdx.x;
   if (inactive(a, pt)) return;
@@ -665,6 +673,9 @@ __global__ void __launch_bounds__(BT) kb_panel(SweepArgs a, int j0) {
     if (a.panel_smem && fits)
       lu_panel_smem<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, P, Ls, sval, sidx, flag, false);
     else lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag, false);
+    if (left0 >= 0)
+      panel_right_apply<T, BT>(M, n, left0, j0, j0, min(NB, n - j0), n - j0, a.piv + (size_t)pt * n, Ls, flag,
+                               false);
   } else {
     lu_panel<T, BT>(M, n, n, ncols, j0, a.piv + (size_t)pt * n, Ls, sval, sidx, flag);
   }
@@ -701,6 +712,38 @@ __global__ void __launch_bounds__(BT) kb_panel_apply(SweepArgs a, int j0) {
   panel_right_apply<T, BT>(M, n, cb, ce, j0, nb, n - j0, a.piv + (size_t)pt * n, Ls, &flag, !left);
   if (threadIdx.x == 0 && (flag & 4)) {
     printf("kb_panel_apply: pivot row out of range (point %d, panel %d)\n", pt, j0);
+    a.status[pt] = 1;
+  }
+}
+
+// Right-hand columns of the second panel of a pair (j0, j1 = j0 + NB) after
+// kb_panel(j1): the panel's row swaps, the first panel's update of the 32
+// swapped rows (A23 - L21 U13, with L21 already in the second panel's row
+// order), then U23 = L22^{-1} (A23 - L21 U13); the rows below keep the first
+// panel's update for the pair's K = 64 trailing update.  Grid (column blocks
+// of [j1 + nb, ncols), points).
+template <int BT>
+__global__ void __launch_bounds__(BT) kb_panel_apply_pair(SweepArgs a, int j0) {
+  constexpr int NB = Tile<float, BT>::NB;
+  __shared__ cc Ls[NB * NB], L1s[NB * NB];
+  __shared__ int flag;
+  const int pt = blockIdx.y;
+  if (inactive(a, pt)) return;
+  const int n = a.n, ncols = 2 * n + a.nc;
+  const int j1 = j0 + NB, nb = min(NB, n - j1), c1 = j1 + nb;
+  const int cb = c1 + blockIdx.x * BT, ce = min(ncols, cb + BT);
+  if (cb >= ce) return;
+  cc *M = reinterpret_cast<cc *>(a.M) + (size_t)pt * n * ncols;
+  for (int e = threadIdx.x; e < NB * NB; e += BT) {
+    const int r = e % NB, s2 = e / NB;
+    Ls[e] = (r < nb && s2 < nb) ? M[j1 + r + (size_t)(j1 + s2) * n] : czero<float>();
+    L1s[e] = r < nb ? M[j1 + r + (size_t)(j0 + s2) * n] : czero<float>();
+  }
+  if (threadIdx.x == 0) flag = 0;
+  __syncthreads();
+  panel_right_apply<float, BT>(M, n, cb, ce, j1, nb, n - j1, a.piv + (size_t)pt * n, Ls, &flag, true, L1s, j0);
+  if (threadIdx.x == 0 && (flag & 4)) {
+    printf("kb_panel_apply_pair: pivot row out of range (point %d, panel %d)\n", pt, j1);
     a.status[pt] = 1;
   }
 }
@@ -848,7 +891,7 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   constexpr int BM = Tile<T, BT>::BM, BN = Tile<T, BT>::BN, NB = Tile<T, BT>::NB;
   const size_t gsm = gemm_smem_elems<T, BT>() * sizeof(cx<T>);
   const size_t psm_big = panel_head_bytes<T, BT>() + (size_t)n * NB * sizeof(cx<T>);
-  a.panel_smem = std::is_same<T, float>::value && psm_big <= (size_t)g_smem_optin;
+  a.panel_smem = std::is_same<T, float>::value && psm_big + PANEL_STATIC_RESERVE <= (size_t)g_smem_optin;
   const size_t psm = a.panel_smem ? psm_big : panel_head_bytes<T, BT>();
   const size_t dsm = (size_t)2 * NB * NB * sizeof(cx<T>);
   auto tiles = [](int m, int nn, int bm, int bn) { return ((m + bm - 1) / bm) * ((nn + bn - 1) / bn); };
@@ -888,21 +931,44 @@ static cudaError_t sweep_step(const SweepArgs &a0, int npts, int p, cudaStream_t
   const bool lapack = std::is_same<T, float>::value && tensor_core && big;
   a.lapack_piv = lapack ? 1 : 0;
   const int ucols = lapack ? n : ncols;   // columns the LU updates
-  for (int j0 = 0; j0 < n; j0 += NB) {
-    PW_TIMED(KK_PANEL, s, kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0));
+  // tensor-core FP32 form without LAPACK pivots: panels in pairs (j0, j1 =
+  // j0 + 32).  The first panel's update reaches only the second panel's
+  // columns (a 32-column update) and, at the second panel's apply, its 32
+  // rows; the rest of the matrix takes both panels at once (K = 64), so the
+  // trailing matrix is read and written once per pair instead of per panel
+  const bool paired = std::is_same<T, float>::value && tensor_core && !lapack;
+  const int TAIL = 1 << 30;
+  for (int j0 = 0; j0 < n;) {
+    PW_TIMED(KK_PANEL, s, kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j0, -1));
     const int c0 = j0 + min(NB, n - j0);
     if constexpr (std::is_same<T, float>::value) {
       const int blocks = (lapack ? (j0 + BT - 1) / BT : 0) + (ucols - c0 + BT - 1) / BT;
       if (blocks > 0) PW_TIMED(KK_PANEL_APPLY, s, kb_panel_apply<T, BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0));
     }
+    if (paired && c0 < n) {
+      const int j1 = c0, c1 = j1 + min(NB, n - j1);
+      const dim3 gn(tiles(n - j1, c1 - j1, tc::CG_M / 2, RMW_TN), npts);
+      PW_TIMED(KK_TRAIL, s, kb_trail_tc<<<gn, tc::CG_THREADS, tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, NB, c1 - j1));
+      PW_TIMED(KK_PANEL, s, kb_panel<T, BT><<<npts, BT, psm, s>>>(a, j1, j0));
+      const int blocks = (ncols - c1 + BT - 1) / BT;
+      if (blocks > 0)
+        PW_TIMED(KK_PANEL_APPLY, s, kb_panel_apply_pair<BT><<<dim3(blocks, npts), BT, 0, s>>>(a, j0));
+      if (c1 < n) {
+        const dim3 gw(tiles(n - c1, ncols - c1, tc::CG_M / 2, RMW_TN), npts);
+        PW_TIMED(KK_TRAIL, s, kb_trail_tc<<<gw, tc::CG_THREADS, tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, 2 * NB, TAIL));
+      }
+      j0 = c1;
+      continue;
+    }
     if (c0 < n) {
       if (std::is_same<T, float>::value && tensor_core)
         PW_TIMED(KK_TRAIL, s,
                  kb_trail_tc<<<dim3(tiles(n - c0, ucols - c0, tc::CG_M / 2, RMW_TN), npts), tc::CG_THREADS,
-                               tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0));
+                               tc::cg_smem_bytes<RMW_TN>(), s>>>(a, j0, NB, TAIL));
       else
         PW_TIMED(KK_TRAIL, s, kb_trail<T, BT><<<dim3(tiles(n - c0, ncols - c0, BM, BN), npts), BT, gsm, s>>>(a, j0));
     }
+    j0 = c0;
   }
   if (lapack) {
     const int cgroups = (ncols - n + BS_COLS - 1) / BS_COLS;
@@ -979,7 +1045,7 @@ static cudaError_t sweep_prepare(int n) {
     cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   }
   const size_t psm_big = panel_head_bytes<T, BT>() + (size_t)n * Tile<T, BT>::NB * sizeof(cx<T>);
-  if (std::is_same<T, float>::value && psm_big <= (size_t)g_smem_optin) {
+  if (std::is_same<T, float>::value && psm_big + PANEL_STATIC_RESERVE <= (size_t)g_smem_optin) {
     const cudaError_t ep =
         cudaFuncSetAttribute(kb_panel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm_big);
     if (ep != cudaSuccess) return ep;
