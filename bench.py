@@ -47,10 +47,11 @@ PROFILE_STRIDE = 3      # every third launch of each kernel kind is bracketed by
 MIXED_DEFAULT_VARIANT = 2    # the library's default launch variant of the mixed form
 T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
 # DRAM traffic of kernels captured with ncu: dram__bytes_read + dram__bytes_write of the
-# captured launches over their algorithmic bytes (profiles/kb_trail_tc_junction512_small.md:
-# 567.4/589, 490.1/512, 411.3/441 MB); the roofline's `traffic` is this ratio times the step's
-# average algorithmic bytes per launch.  A kernel changed since its capture has no entry.
-KERNEL_TRAFFIC = {"kb_trail": 0.95}
+# captured launches over their algorithmic bytes (profiles/kb_trail_tc_junction512_small.md,
+# panels in pairs: 596.3/626.5, 20.0/29.4, 437.0/474.5 MB); the roofline's `traffic` is this
+# ratio times the step's average algorithmic bytes per launch.  A kernel changed since its
+# capture has no entry.
+KERNEL_TRAFFIC = {"kb_trail": 0.93}
 # DRAM bytes per matrix of the FP64 eigensolver from its ncu capture (64 matrices of
 # N_G = 512, one launch: 186.2 + 152.3 MB, profiles/k_heev_junction512_64matrices.md);
 # the roofline's `traffic` is this times the matrices of the timed launch
