@@ -43,7 +43,11 @@ from synthetic import junction, minimal_cell, uneven_batch  # noqa: E402
 METRIC = "(E,k∥)-points/s at N_G=512, 320 slices: mixed-precision vs FP64, at 1e-8 rel T"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 GOLDEN_512 = os.path.join(ROOT, "tests", "golden", "junction512_k5.json")
-PROFILE_STRIDE = 3      # every third launch of each kernel kind is bracketed by CUDA events
+# every 11th launch of each kernel kind is bracketed by CUDA events: a prime, so that
+# the sample walks through every position of the per-interface launch patterns (15
+# trailing and back-substitution updates, 16 panels, applies and diagonal blocks, 8
+# overlap chunks), with few events in the timed region
+PROFILE_STRIDE = 11
 MIXED_DEFAULT_VARIANT = 2    # the library's default launch variant of the mixed form
 T_FLOOR = 1e-6          # relative error of T is taken against max(|T|, T_FLOOR)
 # DRAM traffic of kernels captured with ncu: dram__bytes_read + dram__bytes_write of the

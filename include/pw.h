@@ -386,7 +386,9 @@ pw_status pw_get_fp64_fallback(const pw_ctx *ctx, int *points, double *max_pivot
  * 64 x 64 tiles).  PW_MIXED_FP32 only: bit 1, the GEMM phases of every
  * interface ([W|Y], the LU's trailing updates, the triangular solves'
  * updates) on the fifth-generation tensor cores (tcgen05, TF32 operands split
- * into hi + lo parts, three products accumulated in FP32 in tensor memory);
+ * into hi + lo parts, three products accumulated in FP32 in tensor memory),
+ * with the LU's 32-column panels and the back substitution's 32-row blocks
+ * taken in pairs so that the wide updates run with K = 64;
  * bit 2 (with bit 1), [W|Y] of point pairs in an FP16 split with row scales;
  * bit 3 (with bit 1), LAPACK-ordered pivots, the LU on W alone and the right-
  * hand sides eliminated in 128-row triangular blocks afterwards; bit 4, the

@@ -453,7 +453,8 @@ class Context:
         tiles; mixed form only: bit 1 = GEMM phases on the tcgen05 tensor
         cores, bit 2 = FP16-split [W|Y] of point pairs, bit 3 = LAPACK pivots
         and 128-row triangular blocks, bit 4 = slice-product residual, bit 5 =
-        double-float eigenmodes and overlaps."""
+        double-float eigenmodes and overlaps, bit 6 = the batch as two point
+        groups on two streams."""
         self._check(_lib.pw_set_sweep_variant(self._h, int(variant)), "pw_set_sweep_variant")
 
     def set_fp64_fallback(self, pivot_ratio_max=1e6, err_max=1e-8):
