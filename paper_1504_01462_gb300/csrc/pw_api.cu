@@ -21,7 +21,7 @@ namespace pw {
 const char *kernel_kind_name(int kind) {
   static const char *names[KK_COUNT] = {
       "kb_vectors", "kb_wy ([W|Y] product: kb_wy, kb_wy_tc, kb_wy2_tc or kb_wy2_tc16)", "kb_rowexp",
-      "kb_panel", "kb_panel_apply", "kb_trail (kb_trail or kb_trail_tc)", "kb_rhs_perm", "kb_fsdiag (kb_diag_big<false>)",
+      "kb_panel", "kb_panel_apply (kb_panel_apply or kb_panel_apply_pair)", "kb_trail (kb_trail or kb_trail_tc)", "kb_rhs_perm", "kb_fsdiag (kb_diag_big<false>)",
       "kb_fsupd_tc", "kb_bsdiag (kb_bsdiag or kb_diag_big<true>)", "kb_bsupd (kb_bsupd or kb_bsupd_tc)",
       "kb_finish",
       "k_refine_init", "k_refine_residual", "k_res_oslice", "k_res_yslice", "k_res_mm", "k_res_finish",

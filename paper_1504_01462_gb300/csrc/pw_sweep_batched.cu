@@ -9,8 +9,11 @@
 //   bs_diag   diagonal block of the back substitution
 //   bs_upd    back-substitution update               (GEMM tiles x points)
 //   finish    R <- E+ Z_Y E+, Tacc <- E+ Z_T, refinement storage, t and T
-// The arithmetic of each element is the same as in the one-CTA-per-point
-// kernel (same tile loops and accumulation order).
+// In the FP64 form the arithmetic of each element is the same as in the
+// one-CTA-per-point kernel (same tile loops and accumulation order).  The
+// tensor-core FP32 form takes the LU's 32-column panels and the back
+// substitution's 32-row blocks in pairs, so that its wide updates run with
+// K = 64 (see the panel loop and the back substitution in sweep_step).
 #include <math.h>
 #include <stdio.h>
 
@@ -1113,7 +1116,9 @@ int sweep_batched_launches(int n, int precision, int variant) {
   const int panels = (n + NB - 1) / NB;
   const bool fp32 = precision != PW_FP64, tensor = fp32 && (variant & 2) && (variant & 8);
   // vectors, [W|Y], finish; per panel: factorisation, trailing update (not
-  // after the last), the FP32 form's right-hand apply; the back substitution:
+  // after the last), the FP32 form's right-hand apply (panels in pairs: the
+  // 32-column update of the second panel and the pair's K = 64 update, none
+  // after the last pair, give the same count); the back substitution:
   // a diagonal solve per block and an update above every block but the first
   // (32-row blocks, or 128-row blocks in the tensor-core form)
   const int bblocks = tensor ? (n + BS_FB - 1) / BS_FB : panels;
