@@ -75,3 +75,30 @@ def test_algorithmic_counts():
     lu_tri = (n ** 3 / 3.0 + n * n * (n + nc) / 2.0) * 8.0 * (N + 1) * npts
     assert flops > 8.0 * 2 * n ** 3 * N * npts + 0.9 * lu_tri
     assert tot["kb_trail"][1] > 0 and tot["kb_bsupd"][1] > 0
+
+
+def test_paired_blocks_move_fewer_bytes_for_the_same_updates():
+    """Panels and back-substitution blocks in pairs (the tensor-core form):
+    the LU does the same multiply-adds as one panel at a time, with the first
+    panel's update of the second panel's 32 rows moved from the trailing
+    update into the second panel's apply; the back-substitution updates do
+    the same multiply-adds; the wide read-modify-write passes happen about
+    half as often, so their bytes drop by nearly half.  Ragged sizes keep the
+    identities."""
+    import bench
+    nc, npts, N = 8, 2, 1
+    for n in (64, 96, 100, 512):
+        one = bench.sweep_kind_totals(n, nc, npts, N, False, 8, paired=False)
+        two = bench.sweep_kind_totals(n, nc, npts, N, False, 8, paired=True)
+        lu1 = one["kb_trail"][0] + one["kb_panel_apply"][0]
+        lu2 = two["kb_trail"][0] + two["kb_panel_apply"][0]
+        assert abs(lu1 - lu2) <= 1e-9 * lu1, n
+        assert two["kb_panel_apply"][0] > one["kb_panel_apply"][0]
+        assert abs(one["kb_bsupd"][0] - two["kb_bsupd"][0]) <= 1e-9 * one["kb_bsupd"][0], n
+        # (at n = 64 the back substitution's one pair is the one update)
+        assert two["kb_trail"][1] < one["kb_trail"][1], n
+        assert two["kb_bsupd"][1] < one["kb_bsupd"][1] or (n == 64 and two["kb_bsupd"] == one["kb_bsupd"]), n
+        assert two["kb_panel"][0] == one["kb_panel"][0]
+    one = bench.sweep_kind_totals(512, nc, npts, N, False, 8, paired=False)
+    two = bench.sweep_kind_totals(512, nc, npts, N, False, 8, paired=True)
+    assert 0.45 < two["kb_trail"][1] / one["kb_trail"][1] < 0.6
