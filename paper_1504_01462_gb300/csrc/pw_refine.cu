@@ -970,13 +970,13 @@ extern "C" pw_status pw_selftest_slice_product(int n, int ncol, long long *misma
   a.Yacc = dY;
   a.status = dstat;
   const int tiles = ((M + RS_TILE - 1) / RS_TILE) * ((ncol + RS_TILE - 1) / RS_TILE);
-  for (int round = 0; round < 2 && res == PW_OK; ++round) {
-    // round 0: only the leading slices, with full-scale rows 0 (all +128) and
-    // columns 0 (+128), 1 (-128) so that sums reach 2^24 units; round 1: every slice
+  for (int pattern = 0; pattern < 2 && res == PW_OK; ++pattern) {
+    // pattern 0: only the leading slices, with full-scale rows 0 (all +128) and
+    // columns 0 (+128), 1 (-128) so that sums reach 2^24 units; pattern 1: every slice
     for (size_t e = 0; e < asz; ++e) {
       const int s = (int)(e / ((size_t)M * K)), r = (int)((e / K) % M);
       int I = (int)(rnd() % 257u) - 128;
-      if (round == 0 && s > 0) I = 0;
+      if (pattern == 0 && s > 0) I = 0;
       if (s == 0 && r == 0) I = 128;
       IA[e] = I;
       HA[e] = bits(I, s);
@@ -984,7 +984,7 @@ extern "C" pw_status pw_selftest_slice_product(int n, int ncol, long long *misma
     for (size_t e = 0; e < bsz; ++e) {
       const int t = (int)(e / ((size_t)ncol * K)), j = (int)((e / K) % ncol);
       int I = (int)(rnd() % 257u) - 128;
-      if (round == 0 && t > 0) I = 0;
+      if (pattern == 0 && t > 0) I = 0;
       if (t == 0 && j < 2) I = j == 0 ? 128 : -128;
       IB[e] = I;
       HB[e] = bits(I, t);
@@ -1008,7 +1008,7 @@ extern "C" pw_status pw_selftest_slice_product(int n, int ncol, long long *misma
       res = PW_ETIMEOUT;
       break;
     }
-    if (round == 0) {
+    if (pattern == 0) {
       // the exact product of the leading slices, an integer times 2^-14, compared bit for bit
       long long bad = 0;
       for (int r = 0; r < M; ++r)
