@@ -292,7 +292,12 @@ size_t jacobi_smem(int n) {
 //      A <- A - v w^H - w v^H.
 //   2. Implicit QL with Wilkinson-type shifts on (d, e), rotations accumulated
 //      into Z (each thread streams its rows; the rotation sequence of a QL
-//      step is formed once in shared memory).
+//      step is formed once in shared memory).  The QL step is the published
+//      algorithm of H. Bowdler, R. S. Martin, C. Reinsch and J. H. Wilkinson,
+//      "The QR and QL algorithms for symmetric matrices", Numer. Math. 11
+//      (1968) 293-306 (tql2 in EISPACK): a shift from the leading 2 x 2 block
+//      of the unreduced part, then plane rotations chasing the bulge from its
+//      bottom up; written here from that description.
 //   3. Back-transformation U = Q_0 Q_1 ... Q_{n-2} Z, then ascending sort.
 // Memory traffic is O(n^3) bytes per matrix in total (the two-sided Jacobi
 // streams the matrix every round), so this route is FP64-bound.
@@ -701,8 +706,9 @@ __global__ void __launch_bounds__(256) k_eig_sort(const zc *U_all, zc *HU_all, d
 // matrix per 32-thread block (thread 0 runs the scalar recurrence; GB300's
 // FP64 pipe retires a scalar FP64 operation far slower than the FP32 pipe
 // retires the ~10 FP32 operations of its double-float counterpart).  Same
-// implicit QL as part 0 (shift from the leading 2 x 2 block, rotations from
-// the bottom of the unreduced block up); the deflation test uses the
+// implicit QL as part 0 (Bowdler, Martin, Reinsch and Wilkinson, 1968: shift
+// from the leading 2 x 2 block, rotations from the bottom of the unreduced
+// block up); the deflation test uses the
 // double-float resolution (4e-15 relative).  Writes the eigenvalues into
 // ws.d, the step list and the rotations; status -1 when an eigenvalue needs
 // more than 60 iterations or the stream exceeds its capacity.
